@@ -1,0 +1,746 @@
+/*
+ * FP64 CPU oracle of the coupled lattice-Boltzmann PEMFC-cathode time step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file: it is used by the tests, by the package smoke check and by
+ * the benchmark's CPU-baseline leg, nowhere else.  It shares no code, header,
+ * table or constant with the CUDA library.
+ *
+ * What it computes, in the paper's order and notation (arXiv 2103.01444):
+ *   stream  : f_i(x, t+1) <- f*_i(x - e_i, t)               (Eq. 1 LHS, Eq. 2)
+ *             g_i(x, t+1) <- g*_i(x - e_i, t)               (Eq. 9, Eq. 10 LHS)
+ *             with the boundary links of Sec. 4 (bounce-back walls, inlet,
+ *             outlet, catalyst-layer reaction, Eq. 12-17)
+ *   macros  : v = sum e_i f_i / rho0, u = v / (l0 + sqrt(l0^2 + l1 |v|)),
+ *             p = (0.6/phi) sum_{i>=1} f_i - 6 rho0 |u|^2 / (15 phi^2)  (Eq. 8)
+ *             C = sum_i g_i                                          (Eq. 11)
+ *   collide : m = M f;  m* = m - S (m - m_eq) + (I - S/2) G;  f* = M^-1 m*
+ *                                                             (Eq. 1, 3-7)
+ *             n = N g;  n* = n - Q (n - n_eq);  g* = N^-1 n*  (Eq. 10)
+ *             + volumetric catalyst sink when the catalyst layer has rows.
+ *
+ * Readings taken where the paper is silent or garbled (each listed in the
+ * design notes):
+ *   - Eq. 6 prints G7 with a minus sign and G8 = (ux Fx + uy Fy)/phi; the
+ *     moments of Guo's velocity-space forcing give G7 = +2 rho0 (ux Fx -
+ *     uy Fy)/phi and G8 = rho0 (ux Fy + uy Fx)/phi.  The derived form is used.
+ *   - The inlet carries a parabolic velocity (Ladd moving-wall bounce-back,
+ *     velocity taken where the link crosses the inlet plane) over the
+ *     channel rows; GDL/CL rows at the inlet are walls.  Scalars:
+ *     anti-bounce-back Dirichlet at the inlet channel rows.
+ *   - Outlet: fully developed (the virtual column nx repeats column nx-1);
+ *     for the flow, the virtual cell's equilibrium pressure part is moved to
+ *     the specified outlet pressure phi p = rho0/3 (Sec. 5), which anchors
+ *     the pressure level.
+ *   - The mass moment relaxes at s_0 = 1/tau, like e and zeta: the printed S
+ *     has s_0 = 0, with which sum_{i>=1} f_i (the pressure invariant of the
+ *     incompressible equilibrium of Eq. 5/8) is not conserved and the scheme
+ *     is linearly unstable.
+ *   - Surface reaction (thin catalyst film at y = -1/2): the Tafel rate is
+ *     linear in C, J = k(T) C_w with C_w = (g_down* + g_up)/(2 w), solved
+ *     implicitly: g_up = g_down* (1 - kappa)/(1 + kappa), kappa = k/(2w).
+ *     Water gets +2J (Eq. 12); temperature gets the heat of Eq. 15.
+ *   - Volumetric catalyst rows: backward-Euler sink S = -k_v C/(1 + k_v),
+ *     added after collision as w_i(b) S.
+ *   - k(T), C and T in the reaction terms use the cell's previous
+ *     post-collision sums (C^n = sum g*(x)).
+ *
+ * Storage: f[q][y][x] (9 planes), g[s][q][y][x] (3 scalars x 5 planes),
+ * s = 0 temperature, 1 O2 mole fraction, 2 H2O mole fraction.  Full values,
+ * never deviations.  Built with plain gcc, no fast-math.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---------------------------------------------------------------- lattices */
+
+/* D2Q9 velocity set, Eq. 2: rest, four axis links, four diagonals. */
+static const int EX9[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int EY9[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const double W9[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                             1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+/* D2Q5 velocity set, Eq. 9. */
+static const int EX5[5] = {0, 1, 0, -1, 0};
+static const int EY5[5] = {0, 0, 1, 0, -1};
+
+/* Transformation matrix M, Eq. 3. */
+static const double M9[9][9] = {
+    {1, 1, 1, 1, 1, 1, 1, 1, 1},
+    {-4, -1, -1, -1, -1, 2, 2, 2, 2},
+    {4, -2, -2, -2, -2, 1, 1, 1, 1},
+    {0, 1, 0, -1, 0, 1, -1, -1, 1},
+    {0, -2, 0, 2, 0, 1, -1, -1, 1},
+    {0, 0, 1, 0, -1, 1, 1, -1, -1},
+    {0, 0, -2, 0, 2, 1, 1, -1, -1},
+    {0, 1, -1, 1, -1, 0, 0, 0, 0},
+    {0, 0, 0, 0, 0, 1, -1, 1, -1}};
+
+/* Transformation matrix N, Eq. 10. */
+static const double N5[5][5] = {
+    {1, 1, 1, 1, 1},
+    {0, 1, 0, -1, 0},
+    {0, 0, 1, 0, -1},
+    {-4, 1, 1, 1, 1},
+    {0, 1, -1, 1, -1}};
+
+static int opposite9(int i) {
+  for (int j = 0; j < 9; ++j)
+    if (EX9[j] == -EX9[i] && EY9[j] == -EY9[i]) return j;
+  return -1;
+}
+static int opposite5(int i) {
+  for (int j = 0; j < 5; ++j)
+    if (EX5[j] == -EX5[i] && EY5[j] == -EY5[i]) return j;
+  return -1;
+}
+
+/* Gauss-Jordan inverse with partial pivoting of an n x n row-major matrix. */
+static int invert(int n, const double *a, double *inv) {
+  double w[9 * 18];
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < 2 * n; ++c)
+      w[r * 2 * n + c] = c < n ? a[r * n + c] : (c - n == r ? 1.0 : 0.0);
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabs(w[r * 2 * n + c]) > fabs(w[piv * 2 * n + c])) piv = r;
+    if (fabs(w[piv * 2 * n + c]) < 1e-12) return -1;
+    if (piv != c)
+      for (int k = 0; k < 2 * n; ++k) {
+        double t = w[c * 2 * n + k];
+        w[c * 2 * n + k] = w[piv * 2 * n + k];
+        w[piv * 2 * n + k] = t;
+      }
+    double d = w[c * 2 * n + c];
+    for (int k = 0; k < 2 * n; ++k) w[c * 2 * n + k] /= d;
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      double s = w[r * 2 * n + c];
+      for (int k = 0; k < 2 * n; ++k) w[r * 2 * n + k] -= s * w[c * 2 * n + k];
+    }
+  }
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) inv[r * n + c] = w[r * 2 * n + n + c];
+  return 0;
+}
+
+static double MINV9[9][9];
+static double NINV5[5][5];
+static int g_inverted = 0;
+
+static void ensure_inverses(void) {
+  if (g_inverted) return;
+  invert(9, &M9[0][0], &MINV9[0][0]);
+  invert(5, &N5[0][0], &NINV5[0][0]);
+  g_inverted = 1;
+}
+
+/* ------------------------------------------------------------- problem */
+
+/* Operating point, constants and flags (lattice units unless noted). */
+typedef struct {
+  int32_t nx, ny;
+  int32_t ny_cl, ny_gdl;    /* rows counted from the bottom (y = 0) */
+  int32_t reaction_mode;    /* 0 thin-film surface at y=-1/2, 1 volumetric CL rows */
+  int32_t periodic_x;       /* 1: x wraps (closed-form tests), 0: inlet/outlet */
+  int32_t forchheimer;      /* 1: Eq. 7 with the Forchheimer term, 0: Darcy only */
+  int32_t top_dirichlet;    /* scalars at the top wall: 0 insulated, 1 Dirichlet */
+  double nu;                /* kinematic viscosity; 3 nu = tau - 1/2 (Eq. 8) */
+  double u_in_avg;          /* mean inlet velocity over the channel rows */
+  double body_force_x;      /* uniform body force per unit mass (tests only) */
+  double V_op, T_in, C_O2_in, C_H2O_in;
+  double T_top, C_O2_top, C_H2O_top;
+  double aj0_ref;           /* A/cm^3 at T_ref_kin (Eq. 13, 17) */
+  double T_ref_kin, E_act;  /* 353.15 K, 16456 K (Eq. 17) */
+  double alpha_c, F, R;     /* Eq. 13 */
+  double dU0dT, U0_0;       /* Eq. 16 */
+  double x_ref;             /* reference O2 mole fraction (C_O2,ref) */
+  double dx_cm, dt_s, delta_cl_cm, c_tot, rho_cp_f;
+} orc_params;
+
+/* Per-cell material, lattice units. K = +inf marks clear fluid. */
+typedef struct {
+  const double *phi, *K, *alpha_T, *D_O2, *D_H2O;
+  const double *u_imposed; /* optional [2][ny][nx]: freeze flow (tests) */
+} orc_material;
+
+/* Mask bits (one byte per cell). */
+enum {
+  REG_CLEAR = 0, REG_POROUS = 1, REG_CATALYST = 2, REG_SOLID = 3,
+  B_XLO = 1 << 2, B_XHI = 1 << 3, B_YHI = 1 << 4, B_YLO = 1 << 5,
+  B_INLET = 1 << 6, B_NEAR_SOLID = 1 << 7
+};
+
+#define IDX(x, y) ((size_t)(y) * (size_t)nx + (size_t)(x))
+
+/* Node types from the geometry: rows [0, ny_cl) catalyst (volumetric mode),
+ * [ny_cl, ny_cl + ny_gdl) porous GDL, the rest clear channel; explicit
+ * solid cells override.  Boundary bits follow the cell's position. */
+void orc_build_mask(const orc_params *P, const uint8_t *solid, uint8_t *mask) {
+  int nx = P->nx, ny = P->ny;
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      int reg;
+      if (solid && solid[IDX(x, y)]) reg = REG_SOLID;
+      else if (y < P->ny_cl) reg = REG_CATALYST;
+      else if (y < P->ny_cl + P->ny_gdl) reg = REG_POROUS;
+      else reg = REG_CLEAR;
+      uint8_t m = (uint8_t)reg;
+      if (x == 0) m |= B_XLO;
+      if (x == nx - 1) m |= B_XHI;
+      if (y == ny - 1) m |= B_YHI;
+      if (y == 0) m |= B_YLO;
+      if (reg == REG_CLEAR && x == 0 && !P->periodic_x) m |= B_INLET;
+      mask[IDX(x, y)] = m;
+    }
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      if ((mask[IDX(x, y)] & 3) == REG_SOLID) continue;
+      for (int i = 1; i < 9; ++i) {
+        int sx = x - EX9[i], sy = y - EY9[i];
+        if (sy < 0 || sy >= ny) continue;
+        if (P->periodic_x) sx = (sx + nx) % nx;
+        if (sx < 0 || sx >= nx) continue;
+        if ((mask[IDX(sx, sy)] & 3) == REG_SOLID) mask[IDX(x, y)] |= B_NEAR_SOLID;
+      }
+    }
+}
+
+/* ------------------------------------------------------- closures (Sec. 4) */
+
+/* Eq. 16 */
+double orc_U0(const orc_params *P, double T) { return P->dU0dT * T + P->U0_0; }
+/* Eq. 14 */
+double orc_eta(const orc_params *P, double T) { return P->V_op - orc_U0(P, T); }
+/* Eq. 17 */
+double orc_aj0(const orc_params *P, double T) {
+  return P->aj0_ref * exp(-P->E_act * (1.0 / T - 1.0 / P->T_ref_kin));
+}
+/* Eq. 13: volumetric current density (A/cm^3, negative = cathodic) at O2
+ * mole fraction x and temperature T. */
+double orc_tafel_j(const orc_params *P, double x, double T) {
+  return -orc_aj0(P, T) * (x / P->x_ref) *
+         exp(-P->alpha_c * P->F / (P->R * T) * orc_eta(P, T));
+}
+/* Eq. 15: heat per unit volume (W/cm^3) released by current j at T. */
+double orc_heat_Q(const orc_params *P, double j, double T) {
+  return -j * (orc_eta(P, T) + T * P->dU0dT);
+}
+
+/* Lattice rate constant of the thin film: O2 mole-fraction flux per step
+ * through one wall link, per unit wall mole fraction. */
+static double k_surface(const orc_params *P, double T) {
+  double j1 = -orc_tafel_j(P, P->x_ref, T) / P->x_ref; /* A/cm^3 per unit x */
+  double flux = j1 * P->delta_cl_cm / (4.0 * P->F * P->c_tot); /* cm/s */
+  return flux * P->dt_s / P->dx_cm;
+}
+/* Lattice rate of the volumetric catalyst: fraction of O2 per step. */
+static double k_volume(const orc_params *P, double T) {
+  double j1 = -orc_tafel_j(P, P->x_ref, T) / P->x_ref;
+  return j1 / (4.0 * P->F * P->c_tot) * P->dt_s;
+}
+/* Temperature rise (K) per unit of O2 mole fraction consumed, Eq. 15 with
+ * j = -4 F c_tot (consumed flux). */
+static double heat_per_O2(const orc_params *P, double T) {
+  return 4.0 * P->F * P->c_tot * (orc_eta(P, T) + T * P->dU0dT) / P->rho_cp_f;
+}
+
+/* ------------------------------------------------- moment-space pieces */
+
+/* b of Eq. 10 for diffusivity alpha */
+double orc_b_of_alpha(double alpha) { return 20.0 * sqrt(3.0) * alpha - 4.0; }
+
+/* D2Q5 equilibrium populations N^-1 n_eq for value C, velocity u, b. */
+static void d2q5_equilibrium(double C, double ux, double uy, double b, double geq[5]) {
+  double neq[5] = {C, ux * C, uy * C, b * C, 0.0};
+  for (int i = 0; i < 5; ++i) {
+    geq[i] = 0;
+    for (int k = 0; k < 5; ++k) geq[i] += NINV5[i][k] * neq[k];
+  }
+}
+
+/* Eq. 5 equilibrium moments. */
+static void flow_meq(double phi, double p, double ux, double uy, double meq[9]) {
+  const double rho0 = 1.0;
+  double u2 = ux * ux + uy * uy;
+  meq[0] = rho0;
+  meq[1] = -4 * rho0 + 6 * phi * p + 3 * rho0 * u2 / phi;
+  meq[2] = 4 * rho0 - 9 * phi * p - 3 * rho0 * u2 / phi;
+  meq[3] = rho0 * ux;
+  meq[4] = -rho0 * ux;
+  meq[5] = rho0 * uy;
+  meq[6] = -rho0 * uy;
+  meq[7] = rho0 * (ux * ux - uy * uy) / phi;
+  meq[8] = rho0 * ux * uy / phi;
+}
+
+/* Eq. 6 forcing moments (G7, G8 in the form derived from Guo's forcing). */
+static void flow_G(double phi, double ux, double uy, double Fx, double Fy, double G[9]) {
+  const double rho0 = 1.0;
+  double uF = ux * Fx + uy * Fy;
+  G[0] = 0;
+  G[1] = 6 * rho0 * uF / phi;
+  G[2] = -6 * rho0 * uF / phi;
+  G[3] = rho0 * Fx;
+  G[4] = -rho0 * Fx;
+  G[5] = rho0 * Fy;
+  G[6] = -rho0 * Fy;
+  G[7] = 2 * rho0 * (ux * Fx - uy * Fy) / phi;
+  G[8] = rho0 * (ux * Fy + uy * Fx) / phi;
+}
+
+/* Relaxation rates S (Sec. 2.1) for relaxation time tau.  The printed S has
+ * s_0 = 0, but Eq. 5 sets m_0^eq = rho0, which differs from m_0 = sum f in
+ * this pressure-based incompressible model; with s_0 = 0 the scheme is
+ * linearly unstable (von Neumann amplification 1.43 at tau = 0.65).  The
+ * mass moment relaxes at 1/tau instead, as in the BGK limit of the same
+ * incompressible equilibrium. */
+static void flow_S(double tau, double S[9]) {
+  double sq = 8.0 * (2.0 - 1.0 / tau) / (8.0 - 1.0 / tau);
+  double s[9] = {1 / tau, 1 / tau, 1 / tau, 0, sq, 0, sq, 1 / tau, 1 / tau};
+  memcpy(S, s, sizeof s);
+}
+
+/* Q of Eq. 10. */
+static void scalar_Q(double Q[5]) {
+  double a = 6.0 / (3.0 + sqrt(3.0)), c = 6.0 / (3.0 + 2.0 * sqrt(3.0));
+  double q[5] = {0, a, a, c, c};
+  memcpy(Q, q, sizeof q);
+}
+
+/* Darcy-Forchheimer coefficients of Eq. 7/8 for one cell. */
+typedef struct { double phi, darcy, forch, l0, l1; } porous_coef;
+static porous_coef porous(const orc_params *P, double phi, double K) {
+  porous_coef c;
+  c.phi = phi;
+  if (isinf(K)) {
+    c.darcy = 0; c.forch = 0;
+  } else {
+    double Fphi = 0.143 * pow(phi, -1.5);
+    c.darcy = phi * P->nu / K;
+    c.forch = P->forchheimer ? phi * Fphi / sqrt(K) : 0.0;
+  }
+  /* l0 = (2K + phi nu dt)/(4K), l1 = phi dt F_phi/(2 sqrt K), dt = 1 */
+  c.l0 = 0.5 + 0.25 * c.darcy;
+  c.l1 = 0.5 * c.forch;
+  return c;
+}
+
+/* Eq. 8: velocity from the auxiliary velocity v. */
+void orc_velocity(double l0, double l1, double vx, double vy, double *ux, double *uy) {
+  double vn = sqrt(vx * vx + vy * vy);
+  double den = l0 + sqrt(l0 * l0 + l1 * vn);
+  *ux = vx / den;
+  *uy = vy / den;
+}
+
+/* Inlet velocity profile: parabola over the channel rows, mean u_in_avg,
+ * evaluated at height y (cell centres at integer y, channel from y0 - 1/2
+ * to ny - 1/2); zero outside the channel. */
+static double inlet_u(const orc_params *P, double y) {
+  int y0 = P->ny_cl + P->ny_gdl;
+  double h = P->ny - y0;
+  double s = (y - y0 + 0.5) / h;
+  if (s <= 0.0 || s >= 1.0) return 0.0;
+  return 6.0 * P->u_in_avg * s * (1.0 - s);
+}
+
+/* --------------------------------------------------------------- state */
+
+/* Initial state: f = w rho0 (rest), g = D2Q5 equilibrium of the inlet values
+ * at rest with the cell's own b. */
+void orc_init(const orc_params *P, const orc_material *mat, const uint8_t *mask,
+              double *f, double *g) {
+  ensure_inverses();
+  int nx = P->nx, ny = P->ny;
+  size_t n = (size_t)nx * ny;
+  double Cin[3] = {P->T_in, P->C_O2_in, P->C_H2O_in};
+  for (size_t c = 0; c < n; ++c) {
+    if ((mask[c] & 3) == REG_SOLID) {
+      for (int i = 0; i < 9; ++i) f[i * n + c] = 0;
+      for (int k = 0; k < 15; ++k) g[k * n + c] = 0;
+      continue;
+    }
+    for (int i = 0; i < 9; ++i) f[i * n + c] = W9[i];
+    double alpha[3] = {mat->alpha_T[c], mat->D_O2[c], mat->D_H2O[c]};
+    for (int s = 0; s < 3; ++s) {
+      double geq[5];
+      d2q5_equilibrium(Cin[s], 0, 0, orc_b_of_alpha(alpha[s]), geq);
+      for (int i = 0; i < 5; ++i) g[(s * 5 + i) * n + c] = geq[i];
+    }
+  }
+}
+
+/* d f_i^eq / d(phi p) of the Eq. 5 equilibrium (M^-1 applied to the p
+ * column of m_eq): 1/3 on axis links, 1/12 on diagonals. */
+static double pressure_weight(int i) {
+  double dm[9] = {0, 6, -9, 0, 0, 0, 0, 0, 0}, v = 0;
+  for (int k = 0; k < 9; ++k) v += MINV9[i][k] * dm[k];
+  return v;
+}
+/* phi p of a cell's post-collision populations (Eq. 8 applied to f*). */
+static double post_pressure(double phi, const double *fs, size_t n, size_t c) {
+  double jx = 0, jy = 0, s18 = 0;
+  for (int k = 0; k < 9; ++k) {
+    jx += EX9[k] * fs[k * n + c];
+    jy += EY9[k] * fs[k * n + c];
+    if (k >= 1) s18 += fs[k * n + c];
+  }
+  return phi * (0.6 / phi * s18 - 6.0 * (jx * jx + jy * jy) / (15.0 * phi * phi));
+}
+
+/* Diagnostics of one stream: index layout of the diag[] vector. */
+enum {
+  D_J = 0,          /* O2 consumed by reaction, sum over the catalyst (lattice) */
+  D_HEAT = 1,       /* temperature added by reaction heat (lattice K) */
+  D_IN = 2,         /* 2..5: net inflow at the inlet  (mass, T, O2, H2O) */
+  D_OUT = 6,        /* 6..9: net inflow at the outlet (mass, T, O2, H2O) */
+  D_NDIAG = 10
+};
+
+/* Stream with boundary links (f, g post-collision at t -> post-stream at t+1).
+ * Also records the reaction terms applied in this stream: the surface
+ * fluxes go into the incoming links; the volumetric sinks (S per cell and
+ * scalar) are returned in src[3][ny][nx] for the collision to add. */
+static void stream(const orc_params *P, const orc_material *mat, const uint8_t *mask,
+                   const double *fs, const double *gs, double *f, double *g,
+                   double *src, double *diag, double *Jx, double *qx) {
+  int nx = P->nx, ny = P->ny;
+  size_t n = (size_t)nx * ny;
+  double Cin[3] = {P->T_in, P->C_O2_in, P->C_H2O_in};
+  double Ctop[3] = {P->T_top, P->C_O2_top, P->C_H2O_top};
+  for (int k = 0; k < D_NDIAG; ++k) diag[k] = 0;
+  if (Jx) for (int x = 0; x < nx; ++x) Jx[x] = 0;
+  if (qx) for (int x = 0; x < nx; ++x) qx[x] = 0;
+  memset(src, 0, sizeof(double) * 3 * n);
+
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      size_t c = IDX(x, y);
+      uint8_t m = mask[c];
+      if ((m & 3) == REG_SOLID) {
+        for (int i = 0; i < 9; ++i) f[i * n + c] = 0;
+        for (int k = 0; k < 15; ++k) g[k * n + c] = 0;
+        continue;
+      }
+      /* previous post-collision sums at this cell (C^n, T^n) */
+      double Cn[3];
+      for (int s = 0; s < 3; ++s) {
+        Cn[s] = 0;
+        for (int i = 0; i < 5; ++i) Cn[s] += gs[(s * 5 + i) * n + c];
+      }
+      double bcell[3] = {orc_b_of_alpha(mat->alpha_T[c]), orc_b_of_alpha(mat->D_O2[c]),
+                         orc_b_of_alpha(mat->D_H2O[c])};
+
+      /* ---- D2Q9 flow links */
+      for (int i = 0; i < 9; ++i) {
+        int sx = x - EX9[i], sy = y - EY9[i], io = opposite9(i);
+        double val;
+        if (sy < 0 || sy >= ny) {
+          val = fs[io * n + c];                               /* wall */
+        } else {
+          if (P->periodic_x) sx = (sx + nx) % nx;
+          if (sx < 0) {
+            if (m & B_INLET) {                                /* moving-wall inlet */
+              /* link crosses the inlet plane at height y - e_iy/2 */
+              double uin = inlet_u(P, y - 0.5 * EY9[i]);
+              val = fs[io * n + c] + 6.0 * W9[i] * 1.0 * (EX9[i] * uin);
+              diag[D_IN + 0] += val - fs[io * n + c];
+            } else {
+              val = fs[io * n + c];
+            }
+          } else if (sx >= nx) {
+            /* outlet: the virtual column nx repeats column nx-1 (fully
+             * developed flow), with its equilibrium pressure part moved to
+             * the specified outlet pressure phi p = rho0/3 (Sec. 5) */
+            size_t cv = IDX(nx - 1, sy);
+            val = fs[i * n + cv] + pressure_weight(i) * (1.0 / 3.0 - post_pressure(mat->phi[cv], fs, n, cv));
+            diag[D_OUT + 0] += val;
+          } else if ((mask[IDX(sx, sy)] & 3) == REG_SOLID) {
+            val = fs[io * n + c];
+          } else {
+            val = fs[i * n + IDX(sx, sy)];
+          }
+        }
+        f[i * n + c] = val;
+      }
+
+      /* populations leaving through the outlet */
+      if (!P->periodic_x) {
+        for (int i = 0; i < 9; ++i) {
+          int dx = x + EX9[i], dy = y + EY9[i];
+          if (dy < 0 || dy >= ny) continue;
+          if (dx >= nx) diag[D_OUT + 0] -= fs[i * n + c];
+        }
+      }
+
+      /* ---- reaction rate at this cell (uses T^n and C^n) */
+      double kS = 0, kV = 0;
+      int surface = (P->reaction_mode == 0) && (m & B_YLO);
+      int volume = (P->reaction_mode == 1) && ((m & 3) == REG_CATALYST);
+      if (surface) kS = k_surface(P, Cn[0]);
+      if (volume) kV = k_volume(P, Cn[0]);
+      double hpo = (surface || volume) ? heat_per_O2(P, Cn[0]) : 0.0;
+
+      /* ---- D2Q5 scalar links */
+      double Jsurf = 0;
+      for (int s = 0; s < 3; ++s) {
+        double w1 = (4.0 + bcell[s]) / 20.0;
+        for (int i = 0; i < 5; ++i) {
+          int sx = x - EX5[i], sy = y - EY5[i], io = opposite5(i);
+          const double *gq = gs + (size_t)(s * 5) * n;
+          double own_out = gq[io * n + c];
+          double val;
+          if (sy < 0) {
+            if (surface) {
+              if (s == 1) {
+                double kappa = kS / (2.0 * w1);
+                val = own_out * (1.0 - kappa) / (1.0 + kappa);
+                Jsurf = own_out - val;
+              } else {
+                val = own_out; /* completed after O2 below */
+              }
+            } else {
+              val = own_out;
+            }
+          } else if (sy >= ny) {
+            if (P->top_dirichlet) val = -own_out + 2.0 * w1 * Ctop[s];
+            else val = own_out;
+          } else {
+            if (P->periodic_x) sx = (sx + nx) % nx;
+            if (sx < 0) {
+              if (m & B_INLET) {
+                val = -own_out + 2.0 * w1 * Cin[s];
+                diag[D_IN + 1 + s] += val - own_out;
+              } else {
+                val = own_out;
+              }
+            } else if (sx >= nx) {
+              int x2 = nx - 2, tx = x2 - EX5[i], ty = y - EY5[i];
+              size_t c2 = IDX(x2, y);
+              if ((mask[IDX(tx, ty)] & 3) == REG_SOLID) val = gq[io * n + c2];
+              else val = gq[i * n + IDX(tx, ty)];
+              diag[D_OUT + 1 + s] += val;
+            } else if ((mask[IDX(sx, sy)] & 3) == REG_SOLID) {
+              val = own_out;
+            } else {
+              val = gq[i * n + IDX(sx, sy)];
+            }
+          }
+          g[(s * 5 + i) * n + c] = val;
+        }
+        if (!P->periodic_x) {
+          for (int i = 0; i < 5; ++i) {
+            const double *gq = gs + (size_t)(s * 5) * n;
+            if (x + EX5[i] >= nx) diag[D_OUT + 1 + s] -= gq[i * n + c];
+          }
+        }
+      }
+      if (surface) {
+        /* Eq. 12: two H2O per O2; Eq. 15: heat into the temperature link */
+        int up = 2; /* the D2Q5 link arriving from below, e = (0, 1) */
+        g[(2 * 5 + up) * n + c] += 2.0 * Jsurf;
+        g[(0 * 5 + up) * n + c] += hpo * Jsurf;
+        diag[D_J] += Jsurf;
+        diag[D_HEAT] += hpo * Jsurf;
+        if (Jx) Jx[x] += Jsurf;
+        if (qx) qx[x] += hpo * Jsurf;
+      }
+      if (volume) {
+        double S = -kV * Cn[1] / (1.0 + kV);
+        src[0 * n + c] = -S * hpo;
+        src[1 * n + c] = S;
+        src[2 * n + c] = -2.0 * S;
+        diag[D_J] += -S;
+        diag[D_HEAT] += -S * hpo;
+        if (Jx) Jx[x] += -S;
+        if (qx) qx[x] += -S * hpo;
+      }
+    }
+}
+
+/* Macroscopic fields of a post-stream state (Eq. 8, 11).  out may be NULL. */
+typedef struct { double ux, uy, p, C[3], usx, usy; } cell_macro;
+
+static cell_macro macros_at(const orc_params *P, const orc_material *mat, size_t n, size_t c,
+                            const double *f, const double *g) {
+  cell_macro r;
+  porous_coef pc = porous(P, mat->phi[c], mat->K[c]);
+  const double rho0 = 1.0;
+  double vx = 0, vy = 0, s18 = 0;
+  for (int i = 0; i < 9; ++i) {
+    vx += EX9[i] * f[i * n + c] / rho0;
+    vy += EY9[i] * f[i * n + c] / rho0;
+    if (i >= 1) s18 += f[i * n + c];
+  }
+  vx += 0.5 * pc.phi * P->body_force_x;
+  orc_velocity(pc.l0, pc.l1, vx, vy, &r.ux, &r.uy);
+  /* velocity carried by the scalars: the flow's, or an imposed one (tests) */
+  r.usx = mat->u_imposed ? mat->u_imposed[c] : r.ux;
+  r.usy = mat->u_imposed ? mat->u_imposed[n + c] : r.uy;
+  double u2 = r.ux * r.ux + r.uy * r.uy;
+  r.p = 0.6 / pc.phi * s18 - 6.0 * rho0 * u2 / (15.0 * pc.phi * pc.phi);
+  for (int s = 0; s < 3; ++s) {
+    r.C[s] = 0;
+    for (int i = 0; i < 5; ++i) r.C[s] += g[(s * 5 + i) * n + c];
+  }
+  return r;
+}
+
+/* One coupled time step: (fs, gs) post-collision at t -> (fo, go) at t+1.
+ * diag[D_NDIAG], Jx[nx], qx[nx] may be NULL. */
+void orc_step(const orc_params *P, const orc_material *mat, const uint8_t *mask,
+              const double *fs, const double *gs, double *fo, double *go, double *diag,
+              double *Jx, double *qx) {
+  ensure_inverses();
+  int nx = P->nx, ny = P->ny;
+  size_t n = (size_t)nx * ny;
+  double *f = malloc(sizeof(double) * 9 * n);
+  double *g = malloc(sizeof(double) * 15 * n);
+  double *src = malloc(sizeof(double) * 3 * n);
+  double dloc[D_NDIAG];
+  stream(P, mat, mask, fs, gs, f, g, src, dloc, Jx, qx);
+  if (diag) memcpy(diag, dloc, sizeof dloc);
+
+  double tau = 3.0 * P->nu + 0.5, S[9], Q[5];
+  flow_S(tau, S);
+  scalar_Q(Q);
+
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      size_t c = IDX(x, y);
+      if ((mask[c] & 3) == REG_SOLID) {
+        for (int i = 0; i < 9; ++i) fo[i * n + c] = 0;
+        for (int k = 0; k < 15; ++k) go[k * n + c] = 0;
+        continue;
+      }
+      cell_macro mc = macros_at(P, mat, n, c, f, g);
+      porous_coef pc = porous(P, mat->phi[c], mat->K[c]);
+      /* Eq. 7 force (plus the optional uniform body force) */
+      double un = sqrt(mc.ux * mc.ux + mc.uy * mc.uy);
+      double Fx = -pc.darcy * mc.ux - pc.forch * un * mc.ux + pc.phi * P->body_force_x;
+      double Fy = -pc.darcy * mc.uy - pc.forch * un * mc.uy;
+      /* Eq. 1 in moment space */
+      double m[9], meq[9], G[9], ms[9];
+      for (int k = 0; k < 9; ++k) {
+        m[k] = 0;
+        for (int i = 0; i < 9; ++i) m[k] += M9[k][i] * f[i * n + c];
+      }
+      flow_meq(pc.phi, mc.p, mc.ux, mc.uy, meq);
+      flow_G(pc.phi, mc.ux, mc.uy, Fx, Fy, G);
+      for (int k = 0; k < 9; ++k)
+        ms[k] = m[k] - S[k] * (m[k] - meq[k]) + (1.0 - 0.5 * S[k]) * G[k];
+      for (int i = 0; i < 9; ++i) {
+        double v = 0;
+        for (int k = 0; k < 9; ++k) v += MINV9[i][k] * ms[k];
+        fo[i * n + c] = v;
+      }
+      /* Eq. 10 for T, O2, H2O */
+      double alpha[3] = {mat->alpha_T[c], mat->D_O2[c], mat->D_H2O[c]};
+      for (int s = 0; s < 3; ++s) {
+        double b = orc_b_of_alpha(alpha[s]);
+        double C = mc.C[s];
+        double nv[5], neq[5] = {C, mc.usx * C, mc.usy * C, b * C, 0.0}, ns[5];
+        for (int k = 0; k < 5; ++k) {
+          nv[k] = 0;
+          for (int i = 0; i < 5; ++i) nv[k] += N5[k][i] * g[(s * 5 + i) * n + c];
+        }
+        for (int k = 0; k < 5; ++k) ns[k] = nv[k] - Q[k] * (nv[k] - neq[k]);
+        double wsrc[5] = {(1.0 - b) / 5.0, (4.0 + b) / 20.0, (4.0 + b) / 20.0,
+                          (4.0 + b) / 20.0, (4.0 + b) / 20.0};
+        for (int i = 0; i < 5; ++i) {
+          double v = 0;
+          for (int k = 0; k < 5; ++k) v += NINV5[i][k] * ns[k];
+          go[(s * 5 + i) * n + c] = v + wsrc[i] * src[s * n + c];
+        }
+      }
+    }
+  free(f);
+  free(g);
+  free(src);
+}
+
+/* Fields after a step, from the state before it: stream (fs, gs) and take the
+ * macroscopic values the collision of that step uses.
+ * out: [6][ny][nx] = ux, uy, p, T, C_O2, C_H2O.  Solid cells give zeros. */
+void orc_fields(const orc_params *P, const orc_material *mat, const uint8_t *mask,
+                const double *fs, const double *gs, double *out, double *diag, double *Jx,
+                double *qx) {
+  ensure_inverses();
+  int nx = P->nx, ny = P->ny;
+  size_t n = (size_t)nx * ny;
+  double *f = malloc(sizeof(double) * 9 * n);
+  double *g = malloc(sizeof(double) * 15 * n);
+  double *src = malloc(sizeof(double) * 3 * n);
+  double dloc[D_NDIAG];
+  stream(P, mat, mask, fs, gs, f, g, src, dloc, Jx, qx);
+  if (diag) memcpy(diag, dloc, sizeof dloc);
+  for (size_t c = 0; c < n; ++c) {
+    if ((mask[c] & 3) == REG_SOLID) {
+      for (int k = 0; k < 6; ++k) out[k * n + c] = 0;
+      continue;
+    }
+    cell_macro mc = macros_at(P, mat, n, c, f, g);
+    out[0 * n + c] = mc.ux;
+    out[1 * n + c] = mc.uy;
+    out[2 * n + c] = mc.p;
+    for (int s = 0; s < 3; ++s) out[(3 + s) * n + c] = mc.C[s];
+  }
+  free(f);
+  free(g);
+  free(src);
+}
+
+/* Moments of a post-collision state used by the steady-state residual:
+ * out [5][ny][nx] = sum e_x f*, sum e_y f*, sum g*_T, sum g*_O2, sum g*_H2O. */
+void orc_state_moments(const orc_params *P, const uint8_t *mask, const double *fs,
+                       const double *gs, double *out) {
+  int nx = P->nx, ny = P->ny;
+  size_t n = (size_t)nx * ny;
+  for (size_t c = 0; c < n; ++c) {
+    double jx = 0, jy = 0, C[3] = {0, 0, 0};
+    if ((mask[c] & 3) != REG_SOLID) {
+      for (int i = 0; i < 9; ++i) {
+        jx += EX9[i] * fs[i * n + c];
+        jy += EY9[i] * fs[i * n + c];
+      }
+      for (int s = 0; s < 3; ++s)
+        for (int i = 0; i < 5; ++i) C[s] += gs[(s * 5 + i) * n + c];
+    }
+    out[0 * n + c] = jx;
+    out[1 * n + c] = jy;
+    for (int s = 0; s < 3; ++s) out[(2 + s) * n + c] = C[s];
+  }
+}
+
+/* ----------------------------------------- exposed pieces for the pins */
+
+void orc_matrices(double *M, double *Minv, double *N, double *Ninv) {
+  ensure_inverses();
+  memcpy(M, M9, sizeof M9);
+  memcpy(Minv, MINV9, sizeof MINV9);
+  memcpy(N, N5, sizeof N5);
+  memcpy(Ninv, NINV5, sizeof NINV5);
+}
+void orc_flow_meq(double phi, double p, double ux, double uy, double *meq) {
+  flow_meq(phi, p, ux, uy, meq);
+}
+void orc_flow_G(double phi, double ux, double uy, double Fx, double Fy, double *G) {
+  flow_G(phi, ux, uy, Fx, Fy, G);
+}
+void orc_flow_S(double tau, double *S) { flow_S(tau, S); }
+void orc_scalar_Q(double *Q) { scalar_Q(Q); }
+void orc_d2q5_eq(double C, double ux, double uy, double b, double *geq) {
+  ensure_inverses();
+  d2q5_equilibrium(C, ux, uy, b, geq);
+}
+double orc_k_surface(const orc_params *P, double T) { return k_surface(P, T); }
+double orc_k_volume(const orc_params *P, double T) { return k_volume(P, T); }
+double orc_heat_per_O2(const orc_params *P, double T) { return heat_per_O2(P, T); }
+void orc_porous(const orc_params *P, double phi, double K, double *out5) {
+  porous_coef c = porous(P, phi, K);
+  out5[0] = c.phi; out5[1] = c.darcy; out5[2] = c.forch; out5[3] = c.l0; out5[4] = c.l1;
+}

@@ -1,0 +1,181 @@
+"""ctypes wrapper around the FP64 C oracle (``lbm_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the
+benchmark's CPU-baseline leg.  Shares no code with the CUDA library.
+
+The state is kept as full (not deviation) FP64 populations:
+``f`` has shape (9, ny, nx) and ``g`` has shape (3, 5, ny, nx) with the
+scalar index 0 = temperature, 1 = O2 mole fraction, 2 = H2O mole fraction.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lbm_oracle.c")
+_OUT = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build_oracle(force: bool = False) -> str:
+    """Compile the oracle with plain gcc (no fast-math) into oracle/_build."""
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
+        tmp = _OUT + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _OUT)
+    return _OUT
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32), ("ny_cl", C.c_int32), ("ny_gdl", C.c_int32),
+        ("reaction_mode", C.c_int32), ("periodic_x", C.c_int32),
+        ("forchheimer", C.c_int32), ("top_dirichlet", C.c_int32),
+        ("nu", C.c_double), ("u_in_avg", C.c_double), ("body_force_x", C.c_double),
+        ("V_op", C.c_double), ("T_in", C.c_double), ("C_O2_in", C.c_double),
+        ("C_H2O_in", C.c_double),
+        ("T_top", C.c_double), ("C_O2_top", C.c_double), ("C_H2O_top", C.c_double),
+        ("aj0_ref", C.c_double), ("T_ref_kin", C.c_double), ("E_act", C.c_double),
+        ("alpha_c", C.c_double), ("F", C.c_double), ("R", C.c_double),
+        ("dU0dT", C.c_double), ("U0_0", C.c_double), ("x_ref", C.c_double),
+        ("dx_cm", C.c_double), ("dt_s", C.c_double), ("delta_cl_cm", C.c_double),
+        ("c_tot", C.c_double), ("rho_cp_f", C.c_double),
+    ]
+
+
+class Material(C.Structure):
+    _fields_ = [(k, C.POINTER(C.c_double)) for k in
+                ("phi", "K", "alpha_T", "D_O2", "D_H2O", "u_imposed")]
+
+
+_P = C.POINTER
+_d = C.POINTER(C.c_double)
+_u8 = C.POINTER(C.c_uint8)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build_oracle())
+            L.orc_build_mask.argtypes = [_P(Params), _u8, _u8]
+            L.orc_init.argtypes = [_P(Params), _P(Material), _u8, _d, _d]
+            L.orc_step.argtypes = [_P(Params), _P(Material), _u8, _d, _d, _d, _d, _d, _d, _d]
+            L.orc_fields.argtypes = [_P(Params), _P(Material), _u8, _d, _d, _d, _d, _d, _d]
+            L.orc_state_moments.argtypes = [_P(Params), _u8, _d, _d, _d]
+            L.orc_matrices.argtypes = [_d, _d, _d, _d]
+            L.orc_flow_meq.argtypes = [C.c_double] * 4 + [_d]
+            L.orc_flow_G.argtypes = [C.c_double] * 5 + [_d]
+            L.orc_flow_S.argtypes = [C.c_double, _d]
+            L.orc_scalar_Q.argtypes = [_d]
+            L.orc_d2q5_eq.argtypes = [C.c_double] * 4 + [_d]
+            L.orc_velocity.argtypes = [C.c_double] * 4 + [_d, _d]
+            L.orc_porous.argtypes = [_P(Params), C.c_double, C.c_double, _d]
+            for name in ("orc_U0", "orc_eta", "orc_aj0", "orc_k_surface", "orc_k_volume",
+                         "orc_heat_per_O2"):
+                getattr(L, name).argtypes = [_P(Params), C.c_double]
+                getattr(L, name).restype = C.c_double
+            L.orc_tafel_j.argtypes = [_P(Params), C.c_double, C.c_double]
+            L.orc_tafel_j.restype = C.c_double
+            L.orc_heat_Q.argtypes = [_P(Params), C.c_double, C.c_double]
+            L.orc_heat_Q.restype = C.c_double
+            L.orc_b_of_alpha.argtypes = [C.c_double]
+            L.orc_b_of_alpha.restype = C.c_double
+            _lib = L
+    return _lib
+
+
+def _ptr(a, t=C.c_double):
+    return a.ctypes.data_as(C.POINTER(t))
+
+
+# Index layout of the per-step diagnostics vector.
+DIAG = {"J": 0, "heat": 1, "in_mass": 2, "in_T": 3, "in_O2": 4, "in_H2O": 5,
+        "out_mass": 6, "out_T": 7, "out_O2": 8, "out_H2O": 9}
+
+
+class Oracle:
+    """One lattice problem: parameters, material, mask and a ping-pong state.
+
+    ``params`` is a dict of the ``Params`` fields; ``material`` a dict with
+    per-cell arrays phi, K, alpha_T, D_O2, D_H2O (lattice units, shape
+    (ny, nx)) and optionally ``u_imposed`` of shape (2, ny, nx).
+    """
+
+    def __init__(self, params: dict, material: dict, solid=None):
+        self.L = lib()
+        self.P = Params(**params)
+        nx, ny = self.P.nx, self.P.ny
+        self.nx, self.ny = nx, ny
+        self._mat_arrays = {}
+        for k in ("phi", "K", "alpha_T", "D_O2", "D_H2O"):
+            a = np.ascontiguousarray(np.broadcast_to(np.asarray(material[k], np.float64),
+                                                     (ny, nx)))
+            self._mat_arrays[k] = a
+        ui = material.get("u_imposed")
+        if ui is not None:
+            self._mat_arrays["u_imposed"] = np.ascontiguousarray(ui, np.float64)
+        self.M = Material(**{k: _ptr(v) for k, v in self._mat_arrays.items()})
+        self.solid = None if solid is None else np.ascontiguousarray(solid, np.uint8)
+        self.mask = np.zeros((ny, nx), np.uint8)
+        self.L.orc_build_mask(C.byref(self.P),
+                              None if self.solid is None else _ptr(self.solid, C.c_uint8),
+                              _ptr(self.mask, C.c_uint8))
+        self.f = np.zeros((9, ny, nx))
+        self.g = np.zeros((3, 5, ny, nx))
+        self.L.orc_init(C.byref(self.P), C.byref(self.M), _ptr(self.mask, C.c_uint8),
+                        _ptr(self.f), _ptr(self.g))
+        self.f_prev, self.g_prev = self.f.copy(), self.g.copy()
+        self.steps = 0
+        self.diag = np.zeros(10)
+        self.Jx = np.zeros(nx)
+        self.qx = np.zeros(nx)
+
+    def step(self, n: int = 1):
+        fo = np.empty_like(self.f)
+        go = np.empty_like(self.g)
+        for _ in range(n):
+            self.L.orc_step(C.byref(self.P), C.byref(self.M), _ptr(self.mask, C.c_uint8),
+                            _ptr(self.f), _ptr(self.g), _ptr(fo), _ptr(go), _ptr(self.diag),
+                            _ptr(self.Jx), _ptr(self.qx))
+            self.f_prev, self.f, fo = self.f, fo, self.f_prev
+            self.g_prev, self.g, go = self.g, go, self.g_prev
+            self.steps += 1
+        return self
+
+    def fields(self):
+        """Macroscopic fields of the last step: dict ux, uy, p, T, C_O2, C_H2O,
+        computed from the post-stream state the last collision used."""
+        out = np.zeros((6, self.ny, self.nx))
+        diag = np.zeros(10)
+        Jx, qx = np.zeros(self.nx), np.zeros(self.nx)
+        self.L.orc_fields(C.byref(self.P), C.byref(self.M), _ptr(self.mask, C.c_uint8),
+                          _ptr(self.f_prev), _ptr(self.g_prev), _ptr(out), _ptr(diag),
+                          _ptr(Jx), _ptr(qx))
+        names = ("ux", "uy", "p", "T", "C_O2", "C_H2O")
+        d = {k: out[i] for i, k in enumerate(names)}
+        d["Jx"], d["qx"], d["diag"] = Jx, qx, diag
+        return d
+
+    def state_moments(self):
+        out = np.zeros((5, self.ny, self.nx))
+        self.L.orc_state_moments(C.byref(self.P), _ptr(self.mask, C.c_uint8), _ptr(self.f),
+                                 _ptr(self.g), _ptr(out))
+        return out
+
+    # -- reported quantities (Sec. 5 performance outputs)
+    def current_density(self):
+        """(i_avg A/cm^2, heat W/cm^2, i(x) A/cm^2) of the last step's reaction."""
+        P = self.P
+        scale = 4.0 * P.F * P.c_tot * P.dx_cm / P.dt_s
+        ix = self.Jx * scale
+        heat = self.qx * P.rho_cp_f * P.dx_cm / P.dt_s
+        return float(ix.mean()), float(heat.mean()), ix

@@ -1,0 +1,437 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: values the
+paper prints, textbook definitions of the moment bases, Guo's velocity-space
+forcing, closed-form steady solutions (Poiseuille, Brinkman, linear and
+exponential diffusion profiles, the cosh reaction-diffusion profile) and
+exact discrete invariants (stoichiometric and energy balances).
+"""
+import ctypes
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from oracle.oracle import DIAG
+from oracle.params import base_params, uniform_material, bruggeman, alpha_eff, lattice_problem
+from paper_2103_01444_gb300 import workloads
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_values.txt")
+
+
+def golden():
+    vals = {}
+    for line in open(GOLDEN):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()[:2]
+            vals[k] = float(v)
+    return vals
+
+
+# Eq. 2 velocity formula, evaluated independently of the oracle's tables.
+def d2q9_velocities():
+    e = [(0, 0)]
+    for i in range(1, 5):
+        a = (i - 1) * math.pi / 2
+        e.append((round(math.cos(a)), round(math.sin(a))))
+    for i in range(5, 9):
+        a = (i - 5) * math.pi / 2 + math.pi / 4
+        e.append((round(math.sqrt(2) * math.cos(a)), round(math.sqrt(2) * math.sin(a))))
+    return np.array(e, float)
+
+
+def matrices(L):
+    M = np.zeros((9, 9)); Mi = np.zeros((9, 9)); N = np.zeros((5, 5)); Ni = np.zeros((5, 5))
+    p = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))  # noqa: E731
+    L.orc_matrices(p(M), p(Mi), p(N), p(Ni))
+    return M, Mi, N, Ni
+
+
+def dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# ------------------------------------------------------------ algebra
+
+def test_moment_basis_matches_textbook_polynomials(oracle_lib):
+    """Rows of M (Eq. 3) are the Lallemand-Luo moment polynomials of the
+    Eq. 2 velocities; rows of N (Eq. 10) the D2Q5 ones."""
+    M, Mi, N, Ni = matrices(oracle_lib)
+    e = d2q9_velocities()
+    ex, ey = e[:, 0], e[:, 1]
+    e2 = ex ** 2 + ey ** 2
+    rows = [np.ones(9), -4 + 3 * e2, 4 - 10.5 * e2 + 4.5 * e2 ** 2, ex, (-5 + 3 * e2) * ex, ey,
+            (-5 + 3 * e2) * ey, ex ** 2 - ey ** 2, ex * ey]
+    np.testing.assert_array_equal(M, np.array(rows))
+    e5 = e[:5]
+    rows5 = [np.ones(5), e5[:, 0], e5[:, 1], -4 + 5 * (e5 ** 2).sum(1), e5[:, 0] ** 2 - e5[:, 1] ** 2]
+    np.testing.assert_array_equal(N, np.array(rows5))
+    np.testing.assert_allclose(M @ Mi, np.eye(9), atol=1e-14)
+    np.testing.assert_allclose(N @ Ni, np.eye(5), atol=1e-14)
+
+
+@pytest.mark.parametrize("phi", [1.0, 0.6, 0.4])
+def test_equilibrium_consistent_with_pressure_and_velocity(oracle_lib, phi):
+    """f_eq = M^-1 m_eq (Eq. 5) carries momentum rho0 u and gives back p
+    through Eq. 8; the rest state f = w rho0 is the equilibrium of p = 1/(3 phi)."""
+    M, Mi, _, _ = matrices(oracle_lib)
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        p, ux, uy = 1 / (3 * phi) + 0.01 * rng.standard_normal(), *(0.05 * rng.standard_normal(2))
+        meq = np.zeros(9)
+        oracle_lib.orc_flow_meq(phi, p, ux, uy, dptr(meq))
+        feq = Mi @ meq
+        e = d2q9_velocities()
+        assert abs(feq.sum() - 1.0) < 1e-14
+        np.testing.assert_allclose(e.T @ feq, [ux, uy], atol=1e-14)
+        p_back = 0.6 / phi * feq[1:].sum() - 6 * (ux * ux + uy * uy) / (15 * phi * phi)
+        assert abs(p_back - p) < 1e-14
+    meq = np.zeros(9)
+    oracle_lib.orc_flow_meq(phi, 1 / (3 * phi), 0.0, 0.0, dptr(meq))
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    np.testing.assert_allclose(Mi @ meq, w, atol=1e-15)
+
+
+def test_forcing_moments_equal_guo_velocity_space_forcing(oracle_lib):
+    """M^-1 G equals Guo's forcing w_i rho0 [3 e.F + 9 (e.u)(e.F)/phi - 3 u.F/phi]
+    (pins the sign of G7 and the form of G8, which Eq. 6 prints garbled)."""
+    _, Mi, _, _ = matrices(oracle_lib)
+    e = d2q9_velocities()
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    rng = np.random.default_rng(2)
+    for _ in range(10):
+        phi = rng.uniform(0.3, 1.0)
+        ux, uy, Fx, Fy = 0.1 * rng.standard_normal(4)
+        G = np.zeros(9)
+        oracle_lib.orc_flow_G(phi, ux, uy, Fx, Fy, dptr(G))
+        eu = e @ [ux, uy]
+        eF = e @ [Fx, Fy]
+        guo = w * (3 * eF + 9 * eu * eF / phi - 3 * (ux * Fx + uy * Fy) / phi)
+        np.testing.assert_allclose(Mi @ G, guo, atol=1e-15)
+
+
+def test_d2q5_equilibrium_moments_and_diffusivity(oracle_lib):
+    """Sum g_eq = C, sum e g_eq = u C, sum e_x^2 g_eq = (4+b) C/10, and the
+    relaxation rates of Eq. 10 with b = 20 sqrt3 alpha - 4 give diffusivity
+    c_s^2 (1/s_1 - 1/2) = alpha."""
+    e5 = d2q9_velocities()[:5]
+    Q = np.zeros(5)
+    oracle_lib.orc_scalar_Q(dptr(Q))
+    for alpha in (0.005, 0.03, 0.1, 0.14):
+        b = oracle_lib.orc_b_of_alpha(alpha)
+        geq = np.zeros(5)
+        C, ux, uy = 0.7, 0.03, -0.02
+        oracle_lib.orc_d2q5_eq(C, ux, uy, b, dptr(geq))
+        assert abs(geq.sum() - C) < 1e-15
+        np.testing.assert_allclose(e5.T @ geq, [ux * C, uy * C], atol=1e-15)
+        assert abs((e5[:, 0] ** 2) @ geq - (4 + b) * C / 10) < 1e-15
+        cs2 = (4 + b) / 10
+        assert abs(cs2 * (1 / Q[1] - 0.5) - alpha) < 1e-15
+    # Eq. 10 rates: magic products of the flux and energy rates
+    assert abs((1 / Q[1] - 0.5) * (1 / Q[3] - 0.5) - 1 / 6) < 1e-15
+
+
+def test_flow_relaxation_rates(oracle_lib):
+    """Sec. 2.1: s_q = 8(2 - 1/tau)/(8 - 1/tau) gives Lambda = 3/16 for any tau;
+    nu = (tau - 1/2)/3."""
+    for tau in (0.55, 0.65, 1.0, 1.7):
+        S = np.zeros(9)
+        oracle_lib.orc_flow_S(tau, dptr(S))
+        assert S[1] == S[2] == S[7] == S[8] == pytest.approx(1 / tau)
+        assert S[3] == S[5] == 0
+        lam = (1 / S[7] - 0.5) * (1 / S[4] - 0.5)
+        assert abs(lam - 3 / 16) < 1e-14
+
+
+def test_implicit_velocity_solves_darcy_forchheimer(oracle_lib):
+    """Eq. 8 u = v/(l0 + sqrt(l0^2 + l1 |v|)) solves v = u - F(u)/2 with the
+    Eq. 7 drag F = -phi nu u/K - phi F_phi |u| u/sqrt(K)."""
+    P = Oracle(base_params(4, 4), uniform_material(4, 4)).P
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        phi = rng.uniform(0.3, 1.0)
+        K = 10 ** rng.uniform(-3, 2)
+        c = np.zeros(5)
+        oracle_lib.orc_porous(ctypes.byref(P), phi, K, dptr(c))
+        vx, vy = 0.05 * rng.standard_normal(2)
+        ux = ctypes.c_double(); uy = ctypes.c_double()
+        oracle_lib.orc_velocity(c[3], c[4], vx, vy, ctypes.byref(ux), ctypes.byref(uy))
+        u = np.array([ux.value, uy.value])
+        Fphi = 0.143 * phi ** -1.5
+        F = -phi * P.nu / K * u - phi * Fphi / math.sqrt(K) * np.linalg.norm(u) * u
+        np.testing.assert_allclose(u - 0.5 * F, [vx, vy], rtol=1e-13, atol=1e-16)
+
+
+# ------------------------------------------------------------- closures
+
+def test_kinetics_special_cases_and_heat_identity(oracle_lib):
+    """Eq. 17 at its reference temperature returns the Nomenclature value;
+    Eq. 15 with Eq. 16 reduces to Q = -j (V_op - 0.2329) at any T; a hand
+    evaluation of Eqs. 13-17 at 0.6 V and 343 K."""
+    gv = golden()
+    P = Oracle(base_params(4, 4, aj0_ref=gv["aj0_ref_A_cm3"]), uniform_material(4, 4)).P
+    assert oracle_lib.orc_aj0(ctypes.byref(P), gv["T_ref_kin_K"]) == pytest.approx(1e-4, rel=1e-15)
+    for T in (323.0, 343.0, 353.0, 373.0):
+        j = oracle_lib.orc_tafel_j(ctypes.byref(P), 0.21, T)
+        Q = oracle_lib.orc_heat_Q(ctypes.byref(P), j, T)
+        assert Q == pytest.approx(-j * (P.V_op - gv["U0_intercept_V"]), rel=1e-13)
+    # hand evaluation at V = 0.6 V, T = 343 K, C = C_ref
+    assert oracle_lib.orc_U0(ctypes.byref(P), 343.0) == pytest.approx(1.0904, abs=1e-12)
+    assert oracle_lib.orc_eta(ctypes.byref(P), 343.0) == pytest.approx(-0.4904, abs=1e-12)
+    assert oracle_lib.orc_aj0(ctypes.byref(P), 343.0) == pytest.approx(2.5185e-5, rel=2e-4)
+    j = oracle_lib.orc_tafel_j(ctypes.byref(P), 0.21, 343.0)
+    assert j == pytest.approx(-404.79, rel=2e-4)
+    # cathodic: the rate grows as the voltage drops
+    P.V_op = 0.3
+    assert oracle_lib.orc_tafel_j(ctypes.byref(P), 0.21, 343.0) < j
+
+
+def test_bruggeman_matches_fig5_caption_and_tables():
+    """Eq. 18 at phi = 0.4 gives the Fig. 5 caption's D_O2,eff; Table 1 has one
+    Re/U_avg ratio and Table 2 one K/Da ratio, the latter fixing the GDL
+    thickness used by the workloads."""
+    gv = golden()
+    D = bruggeman(gv["phi_gdl"], gv["D_O2_cm2_s"])
+    assert round(D, 4) == pytest.approx(gv["D_O2_eff_fig5_cm2_s"], abs=1e-12)
+    ratios = [gv[f"table1_re{k}"] / gv[f"table1_u{k}"] for k in (1, 2, 3)]
+    assert max(ratios) / min(ratios) - 1 < 5e-4
+    kd = [gv[f"table2_K{k}_cm2"] / gv[f"table2_Da{k}"] for k in (1, 2, 3)]
+    assert max(kd) / min(kd) - 1 < 5e-3
+    assert math.sqrt(np.mean(kd)) == pytest.approx(workloads.H_GDL_CM, rel=2e-3)
+    # Eq. 19: solid conduction raises, solid heat capacity lowers alpha_eff
+    assert alpha_eff(1.0, 0.07) == pytest.approx(0.07)
+    assert alpha_eff(0.4, 0.07) < 0.07
+
+
+# ------------------------------------------------------------ geometry
+
+def test_mask_layout():
+    case = workloads.small_cathode(nx=16, ny=12, reaction_mode=1, random_material=False)
+    params, material, solid = lattice_problem(case)
+    o = Oracle(params, material, solid)
+    m = o.mask
+    ny_cl, ny_gdl = case["ny_cl"], case["ny_gdl"]
+    assert (m[:ny_cl] & 3 == 2).all()
+    assert (m[ny_cl:ny_cl + ny_gdl] & 3 == 1).all()
+    assert (m[ny_cl + ny_gdl:] & 3 == 0).all()
+    assert (m[:, 0] & 4).all() and not (m[:, 1:] & 4).any()
+    assert (m[:, -1] & 8).all() and not (m[:, :-1] & 8).any()
+    assert (m[-1] & 16).all() and (m[0] & 32).all()
+    inlet = (m & 64) != 0
+    assert inlet[ny_cl + ny_gdl:, 0].all() and inlet.sum() == case["ny"] - ny_cl - ny_gdl
+    solid = np.zeros((12, 16), np.uint8)
+    solid[5, 7] = 1
+    o = Oracle(params, material, solid)
+    near = (o.mask & 128) != 0
+    assert o.mask[5, 7] & 3 == 3
+    assert near.sum() == 8 and near[4:7, 6:9].sum() == 8
+
+
+# ----------------------------------------------------- steady solutions
+
+def test_rest_state_is_a_fixed_point():
+    for phi, K in ((1.0, math.inf), (0.4, 0.3), (0.7, 20.0)):
+        o = Oracle(base_params(6, 8), uniform_material(6, 8, phi=phi, K=K))
+        f0, g0 = o.f.copy(), o.g.copy()
+        o.step(50)
+        np.testing.assert_allclose(o.f, f0, atol=1e-15)
+        np.testing.assert_allclose(o.g, g0, rtol=1e-14)
+
+
+def test_perturbations_decay():
+    """Small random perturbations of the rest state die out (the mass moment
+    relaxes at 1/tau; with the printed s_0 = 0 this grows without bound)."""
+    o = Oracle(base_params(8, 8), uniform_material(8, 8, phi=0.8, K=2.0))
+    w = o.f.copy()
+    o.f = o.f + 1e-6 * np.random.default_rng(0).standard_normal(o.f.shape)
+    o.step(1)
+    d0 = np.abs(o.f - w).max()
+    o.step(800)
+    assert np.abs(o.f - w).max() < 0.05 * d0
+
+
+def test_poiseuille_exact():
+    """Clear channel, periodic x, bounce-back walls, body force g: the steady
+    profile is g/(2 nu) y (H - y) from the halfway walls, exact up to O(u^2)."""
+    nx, ny, g, nu = 4, 16, 1e-7, 0.05
+    o = Oracle(base_params(nx, ny, body_force_x=g, nu=nu), uniform_material(nx, ny))
+    o.step(12000)
+    u = o.fields()["ux"][:, 0]
+    y = np.arange(ny) + 0.5
+    ex = g / (2 * nu) * y * (ny - y)
+    assert np.abs(u - ex).max() / ex.max() < 1e-8
+
+
+def brinkman_error(H, phi=0.5):
+    g, nu = 1e-6, 0.05
+    K = phi * H * H / 16.0
+    o = Oracle(base_params(4, H, body_force_x=g, forchheimer=0),
+               uniform_material(4, H, phi=phi, K=K))
+    o.step(int(14 * H * H))
+    u = o.fields()["ux"][:, 0]
+    y = np.arange(H) + 0.5
+    r = math.sqrt(phi / K)
+    ex = g * K / nu * (1 - np.cosh(r * (y - H / 2)) / np.cosh(r * H / 2))
+    return np.abs(u - ex).max() / ex.max()
+
+
+def test_brinkman_second_order():
+    """Fully porous channel with Darcy drag (Eq. 7 without the Forchheimer
+    term): u = (gK/nu)[1 - cosh(r(y - H/2))/cosh(rH/2)], r = sqrt(phi/K)."""
+    e16, e32 = brinkman_error(16), brinkman_error(32)
+    assert e32 < 3e-4
+    assert 3.5 < e16 / e32 < 4.5
+
+
+def scalar_case(H, reaction_mode=0, **kw):
+    p = base_params(4, H, reaction_mode=reaction_mode, top_dirichlet=1, C_O2_top=1.0,
+                    V_op=0.2329, E_act=0.0, **kw)
+    return p
+
+
+def test_linear_diffusion_and_surface_reaction_exact(oracle_lib):
+    """No flow, Dirichlet C = 1 at the top wall, reactive bottom wall with
+    rate k (Tafel, linear in C): C = C_w + (k C_w / D) y with
+    C_w = 1/(1 + k H/D); k -> infinity is the linear Dirichlet profile."""
+    for H, aj0, D in ((8, 1e30, 0.03), (12, 1e-4, 0.05), (12, 3e-5, 0.02)):
+        p = scalar_case(H, aj0_ref=aj0)
+        o = Oracle(p, uniform_material(4, H, D_O2=D))
+        k = oracle_lib.orc_k_surface(ctypes.byref(o.P), 343.0)
+        o.step(int(12 * H * H / D))
+        C = o.fields()["C_O2"][:, 0]
+        Cw = 1 / (1 + k * H / D)
+        y = np.arange(H) + 0.5
+        np.testing.assert_allclose(C, Cw + k * Cw / D * y, atol=1e-12)
+
+
+def test_layered_diffusion_alpha_C_linear():
+    """Per-cell b with a fixed Q (Eq. 10 as printed): the steady diffusive
+    flux is -d(alpha C)/dy, so alpha C is linear across two layers."""
+    for H in (8, 12):
+        a1, a2 = 0.02, 0.05
+        mat = uniform_material(4, H, D_O2=a2)
+        mat["D_O2"][: H // 2] = a1
+        o = Oracle(scalar_case(H, aj0_ref=1e30), mat)
+        o.step(int(10 * H * H / a1))
+        C = o.fields()["C_O2"][:, 0]
+        y = np.arange(H) + 0.5
+        np.testing.assert_allclose(mat["D_O2"][:, 0] * C, a2 * y / H, atol=1e-12)
+
+
+def advection_error(H, Pe):
+    a = 0.05
+    mat = uniform_material(4, H, D_O2=a)
+    ui = np.zeros((2, H, 4))
+    ui[1] = Pe * a / H
+    mat["u_imposed"] = ui
+    o = Oracle(scalar_case(H, aj0_ref=1e30), mat)
+    o.step(int(6 * H * H / a))
+    C = o.fields()["C_O2"][:, 0]
+    s = (np.arange(H) + 0.5) / H
+    ex = (np.exp(Pe * s) - 1) / (np.exp(Pe) - 1)
+    return np.abs(C - ex).max()
+
+
+@pytest.mark.parametrize("Pe", [4.0, -4.0])
+def test_advection_diffusion_second_order(Pe):
+    """Uniform imposed u_y, C = 0 and 1 on the walls:
+    C = (exp(Pe s) - 1)/(exp(Pe) - 1), Pe = u H/alpha."""
+    e16, e32 = advection_error(16, Pe), advection_error(32, Pe)
+    assert e32 < 2.5e-3
+    assert 3.3 < e16 / e32 < 4.5
+
+
+def cosh_error(H, oracle_lib):
+    D = 0.05
+    p = scalar_case(H, reaction_mode=1, ny_cl=H, aj0_ref=1e-4)
+    kv0 = oracle_lib.orc_k_volume(ctypes.byref(Oracle(p, uniform_material(4, H)).P), 343.0)
+    p["dt_s"] *= (4.0 * D / (H * H)) / kv0
+    o = Oracle(p, uniform_material(4, H, D_O2=D))
+    kv = oracle_lib.orc_k_volume(ctypes.byref(o.P), 343.0)
+    o.step(int(6 * H * H / D))
+    C = o.fields()["C_O2"][:, 0]
+    y = np.arange(H) + 0.5
+    m = math.sqrt(kv / (1 + kv) / D)
+    return np.abs(C - np.cosh(m * y) / np.cosh(m * H)).max()
+
+
+def test_volumetric_reaction_cosh_profile(oracle_lib):
+    """Catalyst rows with first-order volumetric sink, insulated bottom,
+    C = 1 on top: C = cosh(m y)/cosh(m H), m = sqrt(k_eff/D), k_eff = k/(1+k)."""
+    e16, e32 = cosh_error(16, oracle_lib), cosh_error(32, oracle_lib)
+    assert e32 < 6e-5
+    assert 3.5 < e16 / e32 < 4.5
+
+
+# --------------------------------------------------------------- balances
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_closed_box_stoichiometric_and_energy_invariants(mode, oracle_lib):
+    """Periodic x, insulated walls, reaction on: every O2 consumed makes two
+    H2O (Eq. 12) and releases Eq. 15's heat, so sum(C_H2O + 2 C_O2) and
+    sum(T + h C_O2) stay constant, and so does the flow mass."""
+    nx, ny = 12, 10
+    p = base_params(nx, ny, reaction_mode=mode, ny_cl=3 if mode else 0, V_op=0.5,
+                    aj0_ref=1e-4, dt_s=2e-5, dx_cm=2e-3, body_force_x=1e-5)
+    o = Oracle(p, uniform_material(nx, ny, phi=0.6, K=1.0, D_O2=0.03, D_H2O=0.04,
+                                   alpha_T=0.02))
+    h = oracle_lib.orc_heat_per_O2(ctypes.byref(o.P), 343.0)
+    tot = lambda: (o.g[2].sum() + 2 * o.g[1].sum(), o.g[0].sum() + h * o.g[1].sum(),  # noqa
+                   o.f.sum())
+    a0 = tot()
+    o.step(200)
+    a1 = tot()
+    assert o.g[1].sum() < 0.99 * 0.21 * nx * ny  # the reaction did consume O2
+    for x0, x1 in zip(a0, a1):
+        assert abs(x1 - x0) <= 1e-12 * abs(x0)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_open_cathode_balances_per_step(mode):
+    """With inlet and outlet: per step, the change of each total equals the
+    inflow at the inlet plus the outlet plus the reaction terms."""
+    case = workloads.small_cathode(nx=40, ny=16, reaction_mode=mode, V_op=0.4)
+    params, material, solid = lattice_problem(case)
+    o = Oracle(params, material, solid)
+    o.step(30)
+    for _ in range(5):
+        g0 = o.g.sum(axis=(1, 2, 3))
+        o.step(1)
+        d = o.diag
+        g1 = o.g.sum(axis=(1, 2, 3))
+        J, heat = d[DIAG["J"]], d[DIAG["heat"]]
+        assert J > 0
+        np.testing.assert_allclose(g1[1] - g0[1], d[DIAG["in_O2"]] + d[DIAG["out_O2"]] - J,
+                                   rtol=0, atol=1e-12 * g0[1])
+        np.testing.assert_allclose(g1[2] - g0[2],
+                                   d[DIAG["in_H2O"]] + d[DIAG["out_H2O"]] + 2 * J,
+                                   rtol=0, atol=1e-12 * max(g0[1], 1))
+        np.testing.assert_allclose(g1[0] - g0[0], d[DIAG["in_T"]] + d[DIAG["out_T"]] + heat,
+                                   rtol=0, atol=1e-12 * g0[0])
+
+
+def test_clear_channel_inlet_outlet():
+    """A clear channel fed by the parabolic inlet and left at the outlet
+    pressure: the steady flow is the Poiseuille parabola with the inlet's
+    flux in every column, the pressure level does not drift, and the inlet
+    values of the scalars stay uniform."""
+    nx, ny = 48, 12
+    p = base_params(nx, ny, periodic_x=0, u_in_avg=0.02, reaction_mode=0, aj0_ref=0.0)
+    o = Oracle(p, uniform_material(nx, ny, alpha_T=0.04, D_O2=0.05, D_H2O=0.06))
+    o.step(9000)
+    fl = o.fields()
+    for k, v in (("T", 343.0), ("C_O2", 0.21)):
+        np.testing.assert_allclose(fl[k], v, rtol=1e-3)
+    np.testing.assert_allclose(fl["C_H2O"], 0.0, atol=1e-14)
+    p0 = fl["p"].copy()
+    o.step(200)
+    assert np.abs(o.fields()["p"] - p0).max() < 1e-9
+    flux = fl["ux"].sum(axis=0)
+    assert np.abs(flux[2:-2] / flux[nx // 2] - 1).max() < 1e-6
+    y = np.arange(ny) + 0.5
+    par = y * (ny - y)
+    u = fl["ux"][:, nx // 2]
+    np.testing.assert_allclose(u / u.sum(), par / par.sum(), atol=2e-3)
+    assert np.abs(fl["uy"][:, nx // 2]).max() < 1e-6
