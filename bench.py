@@ -1,0 +1,360 @@
+"""Benchmark of the coupled cathode LBM step on GB300.
+
+Default workload: the 4096 x 1024 production-shaped cathode in FP32 storage
+(40/55/5 % channel/GDL/catalyst rows, GDL porosity and permeability drawn
+per 32 x 32 block, volumetric catalyst, Re 50, 343 K, 0.5 V).  A step is one
+coupled update of every cell (D2Q9 MRT flow + three D2Q5 scalars +
+catalyst reaction).  The metric is MLUPS (million lattice-cell updates per
+second), whole job over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) each rank steps an independent replica of the
+workload on its own GPU (weak scaling); timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2103_01444_gb300 import workloads  # noqa: E402
+
+METRIC = "coupled MLUPS"
+UNIT = "MLUPS"
+NX, NY = 4096, 1024
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16", "fp16"])
+    ap.add_argument("--nx", type=int, default=NX)
+    ap.add_argument("--ny", type=int, default=NY)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def max_over_ranks(value: float, pg, device=None) -> float:
+    """Max of a float over all ranks (identity without a process group)."""
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(pg, device=None):
+    if pg is not None:
+        import torch
+        t = torch.zeros(1, device=device)
+        pg.all_reduce(t)
+
+
+def workload(args):
+    return workloads.cathode_blocks(nx=args.nx, ny=args.ny)
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            j = json.load(open(path))
+            for k in ("hbm_gbs", "hbm_GBps", "copy_gbs"):
+                if k in j:
+                    return float(j[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = None
+
+    def __enter__(self):
+        try:
+            self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.out is None:
+            return None
+        self.out.flush()
+        rows = [r.split(",") for r in open(self.out.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.out.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                for k, name in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(name)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_from_profiles():
+    """DRAM bytes per launch of the step kernel from the committed ncu
+    summary of this workload, if one exists for the current kernel."""
+    path = os.path.join(ROOT, "profiles", "k_step_cathode-4096x1024-fp32.json")
+    if os.path.exists(path):
+        try:
+            j = json.load(open(path))
+            if j.get("kernel_source_hash") == kernel_source_hash():
+                return float(j["dram_bytes_per_launch"])
+        except Exception:
+            pass
+    return None
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2103_01444_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def cpu_baseline(case, seconds_target=15.0):
+    """The FP64 oracle as it stands, on the host cores, over a bounded number
+    of steps of the same workload; returns (MLUPS, cores, sample text)."""
+    from oracle import Oracle
+    from oracle.params import lattice_problem
+    params, material, solid = lattice_problem(case)
+    o = Oracle(params, material, solid)
+    cells = case["nx"] * case["ny"]
+    t0 = time.perf_counter()
+    o.step(1)
+    t1 = time.perf_counter()
+    n = max(1, int(seconds_target / max(t1 - t0, 1e-6)) - 1)
+    n = min(n, 50)
+    t2 = time.perf_counter()
+    o.step(n)
+    dt = time.perf_counter() - t2
+    cores = int(os.environ.get("OMP_NUM_THREADS", len(os.sched_getaffinity(0))))
+    return cells * n / dt / 1e6, cores, f"{n} oracle steps of the {case['nx']}x{case['ny']} lattice after 1 warm-up step"
+
+
+def reference_sample(args, budget_s=90.0):
+    """Largest lattice of the same recipe (halving nx and ny from the bench
+    size) whose W + K oracle steps fit the time budget."""
+    from oracle import Oracle
+    from oracle.params import lattice_problem
+    nx, ny = args.nx, args.ny
+    total = max(args.warmup, 3) + max(args.steps, 1)
+    while True:
+        case = workloads.cathode_blocks(nx=nx, ny=ny)
+        params, material, solid = lattice_problem(case)
+        o = Oracle(params, material, solid)
+        t0 = time.perf_counter()
+        o.step(1)
+        t = time.perf_counter() - t0
+        if t * total <= budget_s or (nx <= 128 and ny <= 64):
+            return case, o
+        nx, ny = max(128, nx // 2), max(64, ny // 2)
+
+
+def run_reference(args):
+    world, rank, local, pg = dist_setup(args)
+    if rank != 0:
+        return
+    W, K = max(args.warmup, 3), max(args.steps, 1)
+    case, o = reference_sample(args)
+    cells = case["nx"] * case["ny"]
+    o.step(W)
+    t0 = time.perf_counter()
+    o.step(K)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", len(os.sched_getaffinity(0))))
+    v = cells * K / dt / 1e6
+    sample = (f"each step one FP64 oracle step of a {case['nx']}x{case['ny']} lattice of the "
+              f"same recipe as the {args.nx}x{args.ny} workload (host cores)")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": K, "warmup": W, "ms_per_step": dt / K * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"cathode-{args.nx}x{args.ny}-blocks",
+                       "sample_nx": case["nx"], "sample_ny": case["ny"], "storage": "fp64"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    world, rank, local, pg = dist_setup(args)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (there is no CPU fallback)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2103_01444_gb300.build import build
+    if rank == 0:
+        build()
+    barrier(pg, dev)
+    build()
+    from paper_2103_01444_gb300.lbm import Domain
+    case = workload(args)
+    cells = case["nx"] * case["ny"]
+    stream = torch.cuda.Stream(device=dev)
+    d = Domain.from_case(case, precision=args.precision, stream=stream.cuda_stream)
+    W, K = max(args.warmup, 3), max(args.steps, 1)
+    d.step(W)
+    torch.cuda.synchronize()
+    barrier(pg, dev)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ms = d.time_steps(K)          # CUDA events on the domain's stream
+    torch.cuda.synchronize()
+    barrier(pg, dev)
+    ms_max = max_over_ranks(ms, pg, dev)
+    clocks = clk.summary()
+    # sanity of the state after the timed run
+    i_avg, heat, _ = d.current_density(profile=False)
+    res = d.residual()
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = end_to_end(case, args.precision, K, stream)
+        e2e_s = max_over_ranks(e2e.pop("seconds"), pg, dev)
+        e2e["value"] = world * cells * K / e2e_s / 1e6
+
+    if rank != 0:
+        return
+    ms_step = ms_max / K
+    value = world * cells * K / (ms_max * 1e-3) / 1e6
+    bpc = d.bytes_per_cell()
+    achieved = bpc * cells / (ms_step * 1e-3) / 1e9
+    peak, peak_kind = measured_peak()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
+        "data": "synthetic",
+        "config": {"workload": case["name"], "nx": case["nx"], "ny": case["ny"],
+                   "storage": args.precision, "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (two population buffers of "
+                         f"{24 * cells * d_esize(args.precision) / 1e6:.0f} MB)",
+                   "reaction": "volumetric catalyst rows", "V_op": case["V_op"],
+                   "Re": case["Re"], "T_in": case["T_in"]},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic_from_profiles(),
+                     "peak_source": peak_kind, "bytes_per_cell": bpc,
+                     "kernel": "k_step (coupled collide+stream)"},
+        "gpu_launches": K,
+        "clocks": clocks,
+        "state_check": {"i_avg_A_cm2": i_avg, "heat_W_cm2": heat, "residual": res},
+    }
+    if e2e is not None:
+        line["e2e"] = e2e
+    if world == 1 and not args.no_cpu_baseline:
+        v, cores, sample = cpu_baseline(case)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": sample}
+    print(json.dumps(line), flush=True)
+
+
+def d_esize(precision):
+    return {"fp64": 8, "fp32": 4, "bf16": 2, "fp16": 2}[precision]
+
+
+def end_to_end(case, precision, K, stream):
+    """The user's job through the public API with host buffers: upload the
+    material from pinned host memory, reset, then K steps each followed by a
+    device->host read of the current density, and a final read of the
+    fields.  MLUPS over the wall-clock of the whole job."""
+    import torch
+    from paper_2103_01444_gb300.units import cathode_params
+    from paper_2103_01444_gb300.lbm import Domain
+    params, fields, geo = cathode_params(case)
+    pinned = {k: torch.from_numpy(v).pin_memory().numpy() for k, v in fields.items()}
+    cells = case["nx"] * case["ny"]
+    d = Domain(precision=precision, stream=stream.cuda_stream, **geo)
+    d.set_params(params)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d.set_fields(**pinned)
+    d.reset()
+    for _ in range(K):
+        d.step(1)
+        d.current_density(profile=False)
+    out = d.fields()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    assert np.isfinite(out["T"]).all()
+    h2d = 5 * 8 * cells + 2 * cells   # material arrays + palette indices
+    d2h = K * 2 * 8 + 6 * 8 * cells
+    d.close()
+    return {"seconds": dt, "unit": UNIT,
+            "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
+            "includes": "material upload, reset, per-step current-density read, final fields read"}
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

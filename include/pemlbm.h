@@ -1,0 +1,192 @@
+/*
+ * pemlbm: coupled lattice-Boltzmann time step of a PEM fuel-cell cathode
+ * (gas channel over a porous gas-diffusion layer over a catalyst layer) on
+ * one GB300 GPU (sm_103a).
+ *
+ * Method: arXiv 2103.01444, "Simulation of Coupled Heat and Mass Transport
+ * With Reaction in PEM Fuel Cell Cathode using Lattice Boltzmann Method".
+ *   flow     : D2Q9 MRT generalized lattice-Boltzmann equation for porous
+ *              media with the Darcy-Forchheimer force (Sec. 2.1, Eq. 1-8)
+ *   scalars  : three D2Q5 MRT advection-diffusion lattices for temperature,
+ *              O2 and H2O mole fractions (Sec. 2.2, Eq. 9-11)
+ *   reaction : Tafel oxygen reduction at the catalyst layer with its heat
+ *              release (Sec. 4, Eq. 12-17); Bruggeman and effective thermal
+ *              diffusivity (Eq. 18-19) are the caller's material inputs.
+ *
+ * Conventions of every entry point:
+ *   - Returns an lbm_status; no C++ exception crosses the ABI.  On failure
+ *     lbm_last_error() gives a message (thread-local, valid until the next
+ *     call on the same thread).
+ *   - Inputs are copied: the caller keeps ownership of every pointer passed.
+ *     Outputs go to caller-allocated buffers.
+ *   - Host arrays over the lattice are row-major [ny][nx], x (the flow
+ *     direction, inlet at x = -1/2) fastest, y = 0 the bottom row next to
+ *     the catalyst wall, y = ny-1 the top row under the channel wall.
+ *   - A domain owns all its device memory; work runs asynchronously on the
+ *     domain's stream.  Calls that return host values synchronise it.
+ *   - Lattice units: dx = dt = 1, rho0 = 1.
+ */
+#ifndef PEMLBM_H
+#define PEMLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_EINVAL = 1,    /* invalid argument or parameter outside the stable range */
+  LBM_ENOMEM = 2,    /* device or host allocation failed */
+  LBM_ECUDA = 3,     /* a CUDA runtime call failed */
+  LBM_ESTATE = 4,    /* call not valid in the domain's current state */
+  LBM_EDIVERGED = 5, /* non-finite values found in the state */
+  LBM_ETIMEOUT = 6   /* a bounded device-side wait gave up */
+} lbm_status;
+
+/* Storage type of the 24 populations per cell; arithmetic is FP64 for
+ * LBM_FP64 and FP32 otherwise. */
+typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_BF16 = 2, LBM_FP16 = 3 } lbm_precision;
+
+/* Geometry of one cathode lattice (Sec. 4, Fig. 4). */
+typedef struct {
+  int32_t nx, ny;          /* lattice cells; nx >= 4, ny >= 3 */
+  int32_t ny_cl;           /* catalyst rows at the bottom (volumetric mode only, else 0) */
+  int32_t ny_gdl;          /* porous GDL rows above them; the channel takes the rest */
+  int32_t reaction_mode;   /* 0: thin catalyst film on the bottom wall (the paper's
+                              negligible-thickness layer); 1: volumetric catalyst rows */
+  int32_t periodic_x;      /* 1: x is periodic (closed-form tests); 0: inlet/outlet */
+  int32_t precision;       /* lbm_precision */
+  int32_t reserved;        /* must be 0 */
+  const uint8_t *solid;    /* optional host [ny][nx] pore-scale solid cells (1 = solid);
+                              NULL = none.  Solids may not touch column 0 or the last
+                              two columns. */
+  void *cuda_stream;       /* borrowed cudaStream_t; NULL = the library's own stream */
+} lbm_domain_desc;
+
+/* Operating point and closure constants.  Lattice units unless a unit is
+ * given.  Physical constants enter only the reaction terms. */
+typedef struct {
+  double nu;                   /* kinematic viscosity, 3 nu = tau - 1/2 (Eq. 8); > 0 */
+  double u_in_avg;             /* mean inlet velocity over the channel rows (parabola) */
+  double body_force_x;         /* uniform body force per unit mass (tests; 0 in use) */
+  double V_op;                 /* cell operating potential, V (Eq. 14) */
+  double T_in, C_O2_in, C_H2O_in;   /* inlet temperature (K) and mole fractions */
+  double T_top, C_O2_top, C_H2O_top; /* top-wall values when top_dirichlet = 1 */
+  double aj0_ref;              /* A/cm^3 at T_ref_kin (Eq. 13, 17) */
+  double T_ref_kin;            /* K, reference temperature of Eq. 17 */
+  double E_act;                /* K, activation temperature of Eq. 17 (16456) */
+  double alpha_c, F, R;        /* transfer coefficient, C/mol, J/(mol K) (Eq. 13) */
+  double dU0dT, U0_0;          /* Eq. 16: U0 = dU0dT T + U0_0 (V/K, V) */
+  double x_ref;                /* reference O2 mole fraction (C_O2,ref of Eq. 13) */
+  double dx_cm, dt_s;          /* lattice spacing (cm) and time step (s) */
+  double delta_cl_cm;          /* catalyst film thickness (cm), thin-film mode */
+  double c_tot;                /* total gas concentration, mol/cm^3 */
+  double rho_cp_f;             /* gas volumetric heat capacity, J/(cm^3 K) */
+  int32_t forchheimer;         /* 1: Eq. 7 with the Forchheimer term; 0: Darcy only */
+  int32_t top_dirichlet;       /* scalars at the top wall: 0 insulated, 1 fixed values */
+} lbm_params;
+
+typedef struct lbm_domain lbm_domain; /* opaque */
+
+/* Allocates a domain (two population buffers, node mask, material palette,
+ * reduction scratch) and builds the node mask on the device.  The state is
+ * undefined until lbm_set_params, lbm_set_fields and lbm_reset are called.
+ * EINVAL: bad sizes, reserved != 0, solids on the inlet/outlet columns.
+ * ENOMEM: device allocation failed. */
+lbm_status lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out);
+
+/* Frees every resource of d (synchronises its stream first).  NULL is OK. */
+lbm_status lbm_destroy_domain(lbm_domain *d);
+
+/* Copies the operating point (Sec. 4-5).  EINVAL unless nu > 0,
+ * sqrt(3) * 1.5 * u_in_avg < 0.3, T_in > 0, dx_cm > 0, dt_s > 0. */
+lbm_status lbm_set_params(lbm_domain *d, const lbm_params *p);
+
+/* Per-cell material, host arrays [ny][nx] of doubles, lattice units:
+ *   phi      porosity, 0 < phi <= 1 (Eq. 5, 7)
+ *   K        permeability; +INFINITY marks clear fluid (no drag) (Eq. 7)
+ *   alpha_T  effective thermal diffusivity (Eq. 19)
+ *   D_O2     effective O2 diffusivity (Eq. 18)
+ *   D_H2O    effective H2O diffusivity
+ * Each diffusivity must lie in (0, 5/(20 sqrt 3)] so that the D2Q5 rest
+ * weight (1-b)/5 of Eq. 10 is non-negative.  Solid cells are ignored.
+ * Distinct material tuples are collected into a palette of at most 65535
+ * entries (EINVAL beyond that). */
+lbm_status lbm_set_fields(lbm_domain *d, const double *phi, const double *K,
+                          const double *alpha_T, const double *D_O2, const double *D_H2O);
+
+/* Initial state: f_i = w_i rho0 (rest), g = D2Q5 equilibrium of the inlet
+ * values at rest with each cell's own b.  Step counter := 0. */
+lbm_status lbm_reset(lbm_domain *d);
+
+/* Advances nsteps coupled steps (Eq. 1, 10 with the Sec. 4 boundary links):
+ * stream with boundary links -> macroscopic values (Eq. 8, 11) ->
+ * collisions -> catalyst sources.  Asynchronous on the domain's stream;
+ * long runs are replayed from a captured CUDA graph. */
+lbm_status lbm_step(lbm_domain *d, int64_t nsteps);
+
+/* Reaction of the last step (Sec. 5 outputs): mean current density over the
+ * catalyst (A/cm^2), mean heat release (W/cm^2) and, if profile_nx is not
+ * NULL, the local current density i(x) along the catalyst (A/cm^2, nx
+ * floats).  Accumulated in FP64.  Synchronises the stream.  ESTATE before
+ * the first step. */
+lbm_status lbm_current_density(lbm_domain *d, double *i_avg_A_cm2, double *heat_W_cm2,
+                               float *profile_nx);
+
+/* Steady-state residual: r = max over X in {j_x, j_y, T - T_in, C_O2, C_H2O}
+ * (moments of the post-collision state) of ||X - X_prev|| / ||X||, where
+ * X_prev is the snapshot taken by the previous call (or by lbm_reset); the
+ * snapshot is then replaced.  FP64 accumulation.  EDIVERGED on non-finite
+ * values. */
+lbm_status lbm_residual(lbm_domain *d, double *res);
+
+/* Macroscopic fields of the last step (the values its collision used):
+ * out = [6][ny][nx] doubles: u_x, u_y, p (Eq. 8), T, C_O2, C_H2O (Eq. 11);
+ * zeros in solid cells.  on_device = 1: out is a device pointer written on
+ * the domain's stream (asynchronous); 0: host pointer (synchronises). */
+lbm_status lbm_get_fields(lbm_domain *d, double *out, int32_t on_device);
+
+/* Current post-collision populations as full values (deviation storage
+ * removed): out = [24][ny][nx] doubles, planes f_0..f_8, g_T0..4, g_O2 0..4,
+ * g_H2O 0..4 (Eq. 2 and Eq. 9 orders).  Host pointer; synchronises. */
+lbm_status lbm_get_state(lbm_domain *d, double *out);
+
+/* Overwrites both population buffers with the given full values (same
+ * layout as lbm_get_state); the step counter is kept. */
+lbm_status lbm_set_state(lbm_domain *d, const double *in);
+
+/* Node mask, [ny][nx] bytes: bits 0-1 region (0 channel, 1 GDL, 2 catalyst
+ * rows, 3 solid); bit 2 x = 0; bit 3 x = nx-1; bit 4 y = ny-1; bit 5 y = 0;
+ * bit 6 open inlet (x = 0 channel row, not periodic); bit 7 a D2Q9
+ * neighbour is solid. */
+lbm_status lbm_get_mask(lbm_domain *d, uint8_t *mask_host);
+
+/* Number of steps taken since lbm_reset. */
+lbm_status lbm_get_step(lbm_domain *d, int64_t *steps);
+
+/* Checkpoint of the state: with buf == NULL, *bytes receives the size; else
+ * writes a header (sizes, precision, step) and the raw populations of both
+ * buffers.  lbm_load_state restores a blob taken from a domain of the same
+ * geometry and precision (EINVAL otherwise). */
+lbm_status lbm_save_state(lbm_domain *d, void *buf, size_t *bytes);
+lbm_status lbm_load_state(lbm_domain *d, const void *buf, size_t bytes);
+
+/* Average device time per launch of the coupled-step kernel over the last
+ * lbm_step call that was timed with lbm_time_steps (ms), for roofline
+ * reporting: runs nsteps steps bracketed by CUDA events on the domain's
+ * stream and returns the elapsed device time. */
+lbm_status lbm_time_steps(lbm_domain *d, int64_t nsteps, double *elapsed_ms);
+
+/* Bytes the method must move per cell update for this domain's storage
+ * (24 populations read and written once, plus the 1-byte node mask). */
+lbm_status lbm_bytes_per_cell(lbm_domain *d, double *bytes);
+
+const char *lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PEMLBM_H */

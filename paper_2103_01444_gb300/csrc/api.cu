@@ -1,0 +1,590 @@
+// C ABI of the coupled cathode step: domain lifetime, parameters, material
+// palette, time stepping (with CUDA-graph replay) and read-outs.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/pemlbm.h"
+#include "lbm_core.cuh"
+#include "lbm_launch.h"
+
+using namespace pemlbm;
+
+namespace {
+
+thread_local std::string g_err;
+
+lbm_status fail(lbm_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return fail(LBM_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                  __LINE__);                                                          \
+  } while (0)
+
+constexpr int kGraphSteps = 64;   // even: a replay returns to the same buffer
+constexpr int kMaxPalette = 65535;
+
+size_t elem_size(int prec) {
+  switch (prec) {
+    case LBM_FP64: return 8;
+    case LBM_FP32: return 4;
+    default: return 2;
+  }
+}
+
+}  // namespace
+
+struct lbm_domain {
+  lbm_domain_desc desc{};
+  lbm_params prm{};
+  bool have_params = false, have_fields = false, have_state = false;
+  int nx = 0, ny = 0, nxp = 0;
+  long long plane = 0;
+  size_t esize = 4;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  void *pop[2] = {nullptr, nullptr};
+  int cur = 0;                 // buffer holding the latest state
+  int64_t steps = 0;
+  uint8_t *mask = nullptr;
+  uint16_t *mid = nullptr;
+  void *pal = nullptr;
+  MatRaw *raw = nullptr;
+  int npal = 0;
+  double *snap = nullptr;      // residual snapshot [5][ny][nx]
+  double *partial = nullptr;   // residual block partials
+  int nres_blocks = 0;
+  double *dsmall = nullptr;    // device results (16 doubles)
+  int *dbad = nullptr;
+  double *hsmall = nullptr;    // pinned host mirror
+  double *scratch = nullptr;   // [24][ny][nx] doubles, lazily allocated
+  float *dprofile = nullptr;   // [nx]
+  // references of the deviation storage, fixed at reset
+  double Cref[3] = {0, 0, 0}, bref[3] = {0, 0, 0};
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+bool fp64(const lbm_domain *d) { return d->desc.precision == LBM_FP64; }
+
+KArgs make_args(const lbm_domain *d) {
+  const lbm_params &p = d->prm;
+  KArgs a{};
+  a.nx = d->nx;
+  a.ny = d->ny;
+  a.nxp = d->nxp;
+  a.periodic = d->desc.periodic_x;
+  a.plane = d->plane;
+  a.mode = d->desc.reaction_mode;
+  a.ny_cl = d->desc.ny_cl;
+  a.y_ch0 = d->desc.ny_cl + d->desc.ny_gdl;
+  a.top_dirichlet = p.top_dirichlet;
+  const double tau = 3.0 * p.nu + 0.5;
+  a.s_nu = 1.0 / tau;
+  a.s_q = 8.0 * (2.0 - 1.0 / tau) / (8.0 - 1.0 / tau);
+  a.body_g = p.body_force_x;
+  a.u_in_avg = p.u_in_avg;
+  a.h_ch = d->ny - a.y_ch0;
+  a.Q1 = 6.0 / (3.0 + std::sqrt(3.0));
+  a.Q3 = 6.0 / (3.0 + 2.0 * std::sqrt(3.0));
+  const double Cin[3] = {p.T_in, p.C_O2_in, p.C_H2O_in};
+  const double Ctop[3] = {p.T_top, p.C_O2_top, p.C_H2O_top};
+  for (int s = 0; s < 3; ++s) {
+    a.Cref[s] = d->Cref[s];
+    a.bref[s] = d->bref[s];
+    a.wr0[s] = (1.0 - d->bref[s]) / 5.0;
+    a.wr1[s] = (4.0 + d->bref[s]) / 20.0;
+    a.Cin[s] = Cin[s];
+    a.Ctop[s] = Ctop[s];
+  }
+  // Tafel rate (Eq. 13, 14, 16, 17) per unit O2 mole fraction:
+  //   k(T) = A exp(-E (1/T - 1/T_ref) + alpha_c F (U0(T) - V)/(R T))
+  //        = A exp(c0 + c1/T),  c0 = E/T_ref + alpha_c F dU0dT / R,
+  //                             c1 = -E + alpha_c F (U0_0 - V)/R,
+  // written around T_in: k = A exp(e_in - c1 (T - T_in)/(T T_in)).
+  const double four_F_c = 4.0 * p.F * p.c_tot;
+  a.kA_surf = p.aj0_ref * p.delta_cl_cm / (p.x_ref * four_F_c) * p.dt_s / p.dx_cm;
+  a.kA_vol = p.aj0_ref / (p.x_ref * four_F_c) * p.dt_s;
+  const double c0 = p.E_act / p.T_ref_kin + p.alpha_c * p.F * p.dU0dT / p.R;
+  const double c1 = -p.E_act + p.alpha_c * p.F * (p.U0_0 - p.V_op) / p.R;
+  a.k_ein = c0 + c1 / p.T_in;
+  a.k_c1 = c1;
+  a.T_in = p.T_in;
+  // Eq. 15 with Eq. 16: eta + T dU0/dT = V - U0_0, so the heat per O2
+  // consumed does not depend on T.
+  a.hpo = four_F_c * (p.V_op - p.U0_0) / p.rho_cp_f;
+  return a;
+}
+
+DevGeom geom(const lbm_domain *d) { return DevGeom{d->mask, d->mid, d->pal}; }
+
+template <typename F>
+void dispatch(int prec, F &&f) {
+  switch (prec) {
+    case LBM_FP64: f((double *)nullptr); break;
+    case LBM_FP32: f((float *)nullptr); break;
+    case LBM_BF16: f((__nv_bfloat16 *)nullptr); break;
+    default: f((__half *)nullptr); break;
+  }
+}
+
+void drop_graphs(lbm_domain *d) {
+  for (auto &g : d->graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+lbm_status launch_steps(lbm_domain *d, int64_t n) {
+  const KArgs a = make_args(d);
+  const DevGeom g = geom(d);
+  for (int64_t k = 0; k < n; ++k) {
+    dispatch(d->desc.precision, [&](auto *tag) {
+      using S = std::remove_pointer_t<decltype(tag)>;
+      launch_step<S>(d->pop[d->cur], d->pop[d->cur ^ 1], g, a, d->stream);
+    });
+    d->cur ^= 1;
+  }
+  CK(cudaGetLastError());
+  return LBM_OK;
+}
+
+lbm_status ensure_graph(lbm_domain *d) {
+  if (d->graph[d->cur]) return LBM_OK;
+  const int start = d->cur;
+  cudaGraph_t gr = nullptr;
+  CK(cudaStreamBeginCapture(d->stream, cudaStreamCaptureModeThreadLocal));
+  lbm_status s = launch_steps(d, kGraphSteps);
+  cudaError_t e = cudaStreamEndCapture(d->stream, &gr);
+  d->cur = start;
+  if (s != LBM_OK) return s;
+  if (e != cudaSuccess) return fail(LBM_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&d->graph[start], gr, 0);
+  cudaGraphDestroy(gr);
+  if (e != cudaSuccess) return fail(LBM_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+lbm_status ensure_scratch(lbm_domain *d) {
+  if (!d->scratch) CK(cudaMalloc(&d->scratch, sizeof(double) * 24 * (size_t)d->nx * d->ny));
+  return LBM_OK;
+}
+
+lbm_status check_ready(lbm_domain *d) {
+  if (!d) return fail(LBM_EINVAL, "null domain");
+  if (!d->have_params || !d->have_fields || !d->have_state)
+    return fail(LBM_ESTATE, "call lbm_set_params, lbm_set_fields and lbm_reset first");
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lbm_last_error(void) { return g_err.c_str(); }
+
+lbm_status lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
+  if (!desc || !out) return fail(LBM_EINVAL, "null argument");
+  *out = nullptr;
+  const lbm_domain_desc &D = *desc;
+  if (D.nx < 4 || D.ny < 3) return fail(LBM_EINVAL, "lattice must be at least 4 x 3 (got %d x %d)", D.nx, D.ny);
+  if ((long long)D.nx * D.ny > (1LL << 31)) return fail(LBM_EINVAL, "lattice too large");
+  if (D.reserved != 0) return fail(LBM_EINVAL, "reserved must be 0");
+  if (D.precision < LBM_FP64 || D.precision > LBM_FP16) return fail(LBM_EINVAL, "bad precision %d", D.precision);
+  if (D.reaction_mode != 0 && D.reaction_mode != 1) return fail(LBM_EINVAL, "reaction_mode must be 0 or 1");
+  if (D.reaction_mode == 0 && D.ny_cl != 0) return fail(LBM_EINVAL, "thin-film mode takes ny_cl = 0");
+  if (D.reaction_mode == 1 && D.ny_cl < 1) return fail(LBM_EINVAL, "volumetric mode needs ny_cl >= 1");
+  if (D.ny_cl < 0 || D.ny_gdl < 0 || D.ny_cl + D.ny_gdl > D.ny - (D.periodic_x ? 0 : 1))
+    return fail(LBM_EINVAL, "row split leaves no channel rows");
+  if (D.solid && !D.periodic_x) {
+    for (int y = 0; y < D.ny; ++y)
+      for (int x : {0, D.nx - 2, D.nx - 1})
+        if (D.solid[(size_t)y * D.nx + x]) return fail(LBM_EINVAL, "solid cell on inlet/outlet column x=%d", x);
+  }
+  lbm_domain *d = new lbm_domain();
+  d->desc = D;
+  d->desc.solid = nullptr;
+  d->nx = D.nx;
+  d->ny = D.ny;
+  const int align = 64;   // 128-byte rows for every storage type
+  d->nxp = (D.nx + align - 1) / align * align;
+  d->plane = (long long)d->nxp * D.ny;
+  d->esize = elem_size(D.precision);
+  auto cleanup = [&](lbm_status s) { lbm_destroy_domain(d); return s; };
+  if (D.cuda_stream) {
+    d->stream = (cudaStream_t)D.cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&d->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return cleanup(fail(LBM_ECUDA, "cudaStreamCreate failed"));
+    d->own_stream = true;
+  }
+  const size_t pop_bytes = 24 * (size_t)d->plane * d->esize;
+  const size_t cells = (size_t)d->plane;
+  const size_t coef = fp64(d) ? sizeof(MatCoef<double>) : sizeof(MatCoef<float>);
+  d->nres_blocks = 4 * 152;
+  if (cudaMalloc(&d->pop[0], pop_bytes) != cudaSuccess || cudaMalloc(&d->pop[1], pop_bytes) != cudaSuccess ||
+      cudaMalloc(&d->mask, cells) != cudaSuccess || cudaMalloc(&d->mid, cells * 2) != cudaSuccess ||
+      cudaMalloc(&d->pal, coef * kMaxPalette) != cudaSuccess ||
+      cudaMalloc(&d->raw, sizeof(MatRaw) * kMaxPalette) != cudaSuccess ||
+      cudaMalloc(&d->snap, sizeof(double) * 5 * (size_t)D.nx * D.ny) != cudaSuccess ||
+      cudaMalloc(&d->partial, sizeof(double) * 10 * d->nres_blocks) != cudaSuccess ||
+      cudaMalloc(&d->dsmall, sizeof(double) * 16) != cudaSuccess || cudaMalloc(&d->dbad, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&d->dprofile, sizeof(float) * D.nx) != cudaSuccess ||
+      cudaMallocHost(&d->hsmall, sizeof(double) * 16) != cudaSuccess) {
+    cudaGetLastError();
+    return cleanup(fail(LBM_ENOMEM, "device allocation of %.1f MB failed", 2.0 * pop_bytes / 1e6));
+  }
+  if (cudaEventCreate(&d->ev0) != cudaSuccess || cudaEventCreate(&d->ev1) != cudaSuccess)
+    return cleanup(fail(LBM_ECUDA, "cudaEventCreate failed"));
+  uint8_t *dsolid = nullptr;
+  if (D.solid) {
+    if (cudaMalloc(&dsolid, (size_t)D.nx * D.ny) != cudaSuccess) return cleanup(fail(LBM_ENOMEM, "solid mask"));
+    cudaMemcpyAsync(dsolid, D.solid, (size_t)D.nx * D.ny, cudaMemcpyHostToDevice, d->stream);
+  }
+  cudaMemsetAsync(d->mid, 0, cells * 2, d->stream);
+  launch_build_mask(d->mask, dsolid, D.nx, D.ny, d->nxp, D.ny_cl, D.ny_gdl, D.reaction_mode,
+                    D.periodic_x, d->stream);
+  cudaError_t e = cudaStreamSynchronize(d->stream);
+  if (dsolid) cudaFree(dsolid);
+  if (e != cudaSuccess) return cleanup(fail(LBM_ECUDA, "mask build: %s", cudaGetErrorString(e)));
+  *out = d;
+  return LBM_OK;
+}
+
+lbm_status lbm_destroy_domain(lbm_domain *d) {
+  if (!d) return LBM_OK;
+  if (d->stream) cudaStreamSynchronize(d->stream);
+  drop_graphs(d);
+  for (void *p : {d->pop[0], d->pop[1], (void *)d->mask, (void *)d->mid, d->pal, (void *)d->raw,
+                  (void *)d->snap, (void *)d->partial, (void *)d->dsmall, (void *)d->dbad,
+                  (void *)d->scratch, (void *)d->dprofile})
+    if (p) cudaFree(p);
+  if (d->hsmall) cudaFreeHost(d->hsmall);
+  if (d->ev0) cudaEventDestroy(d->ev0);
+  if (d->ev1) cudaEventDestroy(d->ev1);
+  if (d->own_stream && d->stream) cudaStreamDestroy(d->stream);
+  delete d;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_params(lbm_domain *d, const lbm_params *p) {
+  if (!d || !p) return fail(LBM_EINVAL, "null argument");
+  if (!(p->nu > 0)) return fail(LBM_EINVAL, "nu must be > 0");
+  if (!(std::sqrt(3.0) * 1.5 * std::fabs(p->u_in_avg) < 0.3))
+    return fail(LBM_EINVAL, "inlet Mach number too high (u_in_avg = %g)", p->u_in_avg);
+  if (!(p->T_in > 0) || !(p->dx_cm > 0) || !(p->dt_s > 0) || !(p->c_tot > 0) || !(p->rho_cp_f > 0) ||
+      !(p->x_ref > 0) || !(p->R > 0) || !(p->F > 0) || !(p->T_ref_kin > 0) || !(p->aj0_ref >= 0))
+    return fail(LBM_EINVAL, "non-positive physical constant");
+  d->prm = *p;
+  d->have_params = true;
+  drop_graphs(d);
+  return LBM_OK;
+}
+
+lbm_status lbm_set_fields(lbm_domain *d, const double *phi, const double *K, const double *alpha_T,
+                          const double *D_O2, const double *D_H2O) {
+  if (!d || !phi || !K || !alpha_T || !D_O2 || !D_H2O) return fail(LBM_EINVAL, "null argument");
+  if (!d->have_params) return fail(LBM_ESTATE, "call lbm_set_params before lbm_set_fields");
+  const int nx = d->nx, ny = d->ny;
+  std::vector<uint8_t> mask((size_t)d->plane);
+  CK(cudaMemcpyAsync(mask.data(), d->mask, mask.size(), cudaMemcpyDeviceToHost, d->stream));
+  CK(cudaStreamSynchronize(d->stream));
+  const double amax = 5.0 / (20.0 * std::sqrt(3.0));
+  std::map<std::tuple<double, double, double, double, double>, int> index;
+  std::vector<MatRaw> raw;
+  std::vector<uint16_t> mid((size_t)d->plane, 0);
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      const size_t o = (size_t)y * nx + x;
+      if ((mask[(size_t)y * d->nxp + x] & REG_MASK) == REG_SOLID) continue;
+      const double f[5] = {phi[o], K[o], alpha_T[o], D_O2[o], D_H2O[o]};
+      if (!(f[0] > 0 && f[0] <= 1)) return fail(LBM_EINVAL, "porosity %g at (%d,%d) outside (0,1]", f[0], x, y);
+      if (!(f[1] > 0)) return fail(LBM_EINVAL, "permeability %g at (%d,%d) must be > 0", f[1], x, y);
+      for (int s = 2; s < 5; ++s)
+        if (!(f[s] > 0 && f[s] <= amax))
+          return fail(LBM_EINVAL, "diffusivity %g at (%d,%d) outside (0, %g]", f[s], x, y, amax);
+      auto key = std::make_tuple(f[0], f[1], f[2], f[3], f[4]);
+      auto it = index.find(key);
+      int k;
+      if (it == index.end()) {
+        k = (int)raw.size();
+        if (k >= kMaxPalette) return fail(LBM_EINVAL, "more than %d distinct materials", kMaxPalette);
+        index.emplace(key, k);
+        raw.push_back(MatRaw{f[0], f[1], {f[2], f[3], f[4]}});
+      } else {
+        k = it->second;
+      }
+      mid[(size_t)y * d->nxp + x] = (uint16_t)k;
+    }
+  if (raw.empty()) return fail(LBM_EINVAL, "no fluid cells");
+  // cells that carry no material (solids, padding) point at entry 0
+  CK(cudaMemcpyAsync(d->raw, raw.data(), sizeof(MatRaw) * raw.size(), cudaMemcpyHostToDevice, d->stream));
+  CK(cudaMemcpyAsync(d->mid, mid.data(), mid.size() * 2, cudaMemcpyHostToDevice, d->stream));
+  launch_prep_palette(d->pal, d->raw, (int)raw.size(), d->prm.nu, d->prm.forchheimer, fp64(d), d->stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(d->stream));
+  d->npal = (int)raw.size();
+  // reference b per scalar: the material of the first open inlet cell (the
+  // channel gas), else of the first fluid cell
+  int ref = -1;
+  for (int y = ny - 1; y >= 0 && ref < 0; --y)
+    if ((mask[(size_t)y * d->nxp] & REG_MASK) != REG_SOLID) ref = mid[(size_t)y * d->nxp];
+  const MatRaw &r = raw[ref < 0 ? 0 : ref];
+  for (int s = 0; s < 3; ++s) d->bref[s] = 20.0 * std::sqrt(3.0) * r.alpha[s] - 4.0;
+  d->have_fields = true;
+  drop_graphs(d);
+  return LBM_OK;
+}
+
+lbm_status lbm_reset(lbm_domain *d) {
+  if (!d) return fail(LBM_EINVAL, "null domain");
+  if (!d->have_params || !d->have_fields) return fail(LBM_ESTATE, "call lbm_set_params and lbm_set_fields first");
+  d->Cref[0] = d->prm.T_in;
+  d->Cref[1] = d->prm.C_O2_in;
+  d->Cref[2] = d->prm.C_H2O_in;
+  const KArgs a = make_args(d);
+  const DevGeom g = geom(d);
+  dispatch(d->desc.precision, [&](auto *tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    launch_init<S>(d->pop[0], g, a, d->stream);
+    launch_init<S>(d->pop[1], g, a, d->stream);
+  });
+  CK(cudaGetLastError());
+  d->cur = 0;
+  d->steps = 0;
+  d->have_state = true;
+  drop_graphs(d);
+  double r;
+  lbm_status s = lbm_residual(d, &r);   // takes the first snapshot
+  if (s != LBM_OK) return s;
+  return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_domain *d, int64_t nsteps) {
+  lbm_status s = check_ready(d);
+  if (s != LBM_OK) return s;
+  if (nsteps < 0) return fail(LBM_EINVAL, "nsteps < 0");
+  int64_t left = nsteps;
+  while (left >= 2 * kGraphSteps) {
+    if ((s = ensure_graph(d)) != LBM_OK) return s;
+    CK(cudaGraphLaunch(d->graph[d->cur], d->stream));
+    left -= kGraphSteps;
+  }
+  if ((s = launch_steps(d, left)) != LBM_OK) return s;
+  d->steps += nsteps;
+  return LBM_OK;
+}
+
+lbm_status lbm_time_steps(lbm_domain *d, int64_t nsteps, double *elapsed_ms) {
+  lbm_status s = check_ready(d);
+  if (s != LBM_OK) return s;
+  if (!elapsed_ms) return fail(LBM_EINVAL, "null argument");
+  CK(cudaEventRecord(d->ev0, d->stream));
+  if ((s = lbm_step(d, nsteps)) != LBM_OK) return s;
+  CK(cudaEventRecord(d->ev1, d->stream));
+  CK(cudaEventSynchronize(d->ev1));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, d->ev0, d->ev1));
+  *elapsed_ms = ms;
+  return LBM_OK;
+}
+
+lbm_status lbm_current_density(lbm_domain *d, double *i_avg, double *heat, float *profile) {
+  lbm_status s = check_ready(d);
+  if (s != LBM_OK) return s;
+  if (d->steps < 1) return fail(LBM_ESTATE, "no step taken yet");
+  const lbm_params &p = d->prm;
+  const double i_scale = 4.0 * p.F * p.c_tot * p.dx_cm / p.dt_s;
+  const double q_scale = p.rho_cp_f * p.dx_cm / p.dt_s;
+  const KArgs a = make_args(d);
+  dispatch(d->desc.precision, [&](auto *tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    launch_catalyst<S>(d->pop[d->cur ^ 1], geom(d), a, i_scale, profile ? d->dprofile : nullptr,
+                       d->dsmall, d->stream);
+  });
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(d->hsmall, d->dsmall, 2 * sizeof(double), cudaMemcpyDeviceToHost, d->stream));
+  if (profile) CK(cudaMemcpyAsync(profile, d->dprofile, sizeof(float) * d->nx, cudaMemcpyDeviceToHost, d->stream));
+  CK(cudaStreamSynchronize(d->stream));
+  if (i_avg) *i_avg = d->hsmall[0] * i_scale / d->nx;
+  if (heat) *heat = d->hsmall[1] * q_scale / d->nx;
+  return LBM_OK;
+}
+
+lbm_status lbm_residual(lbm_domain *d, double *res) {
+  if (!d || !res) return fail(LBM_EINVAL, "null argument");
+  if (!d->have_state) return fail(LBM_ESTATE, "call lbm_reset first");
+  const KArgs a = make_args(d);
+  CK(cudaMemsetAsync(d->dbad, 0, sizeof(int), d->stream));
+  dispatch(d->desc.precision, [&](auto *tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    launch_residual<S>(d->pop[d->cur], geom(d), a, d->snap, d->partial, d->nres_blocks, d->dbad,
+                       d->dsmall, d->stream);
+  });
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(d->hsmall, d->dsmall, 10 * sizeof(double), cudaMemcpyDeviceToHost, d->stream));
+  CK(cudaMemcpyAsync(d->hsmall + 10, d->dbad, sizeof(int), cudaMemcpyDeviceToHost, d->stream));
+  CK(cudaStreamSynchronize(d->stream));
+  int bad;
+  std::memcpy(&bad, d->hsmall + 10, sizeof(int));
+  double r = 0.0;
+  for (int k = 0; k < 5; ++k) {
+    const double num = d->hsmall[k], den = d->hsmall[5 + k];
+    const double rk = den > 0 ? std::sqrt(num / den) : (num > 0 ? INFINITY : 0.0);
+    r = std::fmax(r, rk);
+  }
+  *res = r;
+  if (bad || !std::isfinite(r)) return fail(LBM_EDIVERGED, "non-finite values in the state");
+  return LBM_OK;
+}
+
+lbm_status lbm_get_fields(lbm_domain *d, double *out, int32_t on_device) {
+  lbm_status s = check_ready(d);
+  if (s != LBM_OK) return s;
+  if (!out) return fail(LBM_EINVAL, "null argument");
+  double *dst = out;
+  if (!on_device) {
+    if ((s = ensure_scratch(d)) != LBM_OK) return s;
+    dst = d->scratch;
+  }
+  const KArgs a = make_args(d);
+  dispatch(d->desc.precision, [&](auto *tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    launch_fields<S>(d->pop[d->cur ^ 1], geom(d), a, dst, d->stream);
+  });
+  CK(cudaGetLastError());
+  if (!on_device) {
+    CK(cudaMemcpyAsync(out, dst, sizeof(double) * 6 * (size_t)d->nx * d->ny, cudaMemcpyDeviceToHost, d->stream));
+    CK(cudaStreamSynchronize(d->stream));
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_get_state(lbm_domain *d, double *out) {
+  lbm_status s = check_ready(d);
+  if (s != LBM_OK) return s;
+  if (!out) return fail(LBM_EINVAL, "null argument");
+  if ((s = ensure_scratch(d)) != LBM_OK) return s;
+  const KArgs a = make_args(d);
+  dispatch(d->desc.precision, [&](auto *tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    launch_get_state<S>(d->pop[d->cur], geom(d), a, d->scratch, d->stream);
+  });
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(out, d->scratch, sizeof(double) * 24 * (size_t)d->nx * d->ny, cudaMemcpyDeviceToHost, d->stream));
+  CK(cudaStreamSynchronize(d->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_set_state(lbm_domain *d, const double *in) {
+  lbm_status s = check_ready(d);
+  if (s != LBM_OK) return s;
+  if (!in) return fail(LBM_EINVAL, "null argument");
+  if ((s = ensure_scratch(d)) != LBM_OK) return s;
+  CK(cudaMemcpyAsync(d->scratch, in, sizeof(double) * 24 * (size_t)d->nx * d->ny, cudaMemcpyHostToDevice, d->stream));
+  const KArgs a = make_args(d);
+  dispatch(d->desc.precision, [&](auto *tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    launch_set_state<S>(d->pop[0], geom(d), a, d->scratch, d->stream);
+    launch_set_state<S>(d->pop[1], geom(d), a, d->scratch, d->stream);
+  });
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(d->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_get_mask(lbm_domain *d, uint8_t *mask_host) {
+  if (!d || !mask_host) return fail(LBM_EINVAL, "null argument");
+  CK(cudaMemcpy2DAsync(mask_host, d->nx, d->mask, d->nxp, d->nx, d->ny, cudaMemcpyDeviceToHost, d->stream));
+  CK(cudaStreamSynchronize(d->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_get_step(lbm_domain *d, int64_t *steps) {
+  if (!d || !steps) return fail(LBM_EINVAL, "null argument");
+  *steps = d->steps;
+  return LBM_OK;
+}
+
+struct StateHeader {
+  char magic[8];
+  int32_t nx, ny, precision, cur;
+  int64_t steps;
+  double Cref[3], bref[3];
+};
+
+lbm_status lbm_save_state(lbm_domain *d, void *buf, size_t *bytes) {
+  lbm_status s = check_ready(d);
+  if (s != LBM_OK) return s;
+  if (!bytes) return fail(LBM_EINVAL, "null argument");
+  const size_t pop_bytes = 24 * (size_t)d->plane * d->esize;
+  const size_t need = sizeof(StateHeader) + 2 * pop_bytes;
+  if (!buf) {
+    *bytes = need;
+    return LBM_OK;
+  }
+  if (*bytes < need) return fail(LBM_EINVAL, "buffer of %zu bytes, need %zu", *bytes, need);
+  StateHeader h{};
+  std::memcpy(h.magic, "PEMLBM1", 8);
+  h.nx = d->nx; h.ny = d->ny; h.precision = d->desc.precision; h.cur = d->cur; h.steps = d->steps;
+  for (int k = 0; k < 3; ++k) { h.Cref[k] = d->Cref[k]; h.bref[k] = d->bref[k]; }
+  std::memcpy(buf, &h, sizeof h);
+  char *p = (char *)buf + sizeof h;
+  CK(cudaMemcpyAsync(p, d->pop[0], pop_bytes, cudaMemcpyDeviceToHost, d->stream));
+  CK(cudaMemcpyAsync(p + pop_bytes, d->pop[1], pop_bytes, cudaMemcpyDeviceToHost, d->stream));
+  CK(cudaStreamSynchronize(d->stream));
+  *bytes = need;
+  return LBM_OK;
+}
+
+lbm_status lbm_load_state(lbm_domain *d, const void *buf, size_t bytes) {
+  if (!d || !buf) return fail(LBM_EINVAL, "null argument");
+  if (!d->have_params || !d->have_fields) return fail(LBM_ESTATE, "call lbm_set_params and lbm_set_fields first");
+  const size_t pop_bytes = 24 * (size_t)d->plane * d->esize;
+  StateHeader h;
+  if (bytes != sizeof h + 2 * pop_bytes) return fail(LBM_EINVAL, "blob of %zu bytes does not match this domain", bytes);
+  std::memcpy(&h, buf, sizeof h);
+  if (std::memcmp(h.magic, "PEMLBM1", 8) || h.nx != d->nx || h.ny != d->ny || h.precision != d->desc.precision)
+    return fail(LBM_EINVAL, "blob was taken from another geometry or precision");
+  const char *p = (const char *)buf + sizeof h;
+  CK(cudaMemcpyAsync(d->pop[0], p, pop_bytes, cudaMemcpyHostToDevice, d->stream));
+  CK(cudaMemcpyAsync(d->pop[1], p + pop_bytes, pop_bytes, cudaMemcpyHostToDevice, d->stream));
+  CK(cudaStreamSynchronize(d->stream));
+  d->cur = h.cur;
+  d->steps = h.steps;
+  for (int k = 0; k < 3; ++k) { d->Cref[k] = h.Cref[k]; d->bref[k] = h.bref[k]; }
+  d->have_state = true;
+  drop_graphs(d);
+  return LBM_OK;
+}
+
+lbm_status lbm_bytes_per_cell(lbm_domain *d, double *bytes) {
+  if (!d || !bytes) return fail(LBM_EINVAL, "null argument");
+  *bytes = 48.0 * d->esize + 1.0;
+  return LBM_OK;
+}
+
+}  // extern "C"

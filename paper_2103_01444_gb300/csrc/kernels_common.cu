@@ -1,0 +1,100 @@
+// Type-independent kernels: node mask, material palette, partial sums.
+#include "lbm_kernels.cuh"
+
+namespace pemlbm {
+
+// Node mask (Sec. 4 geometry): region by rows, boundary bits by position,
+// explicit solids, and a flag for cells with a solid D2Q9 neighbour.
+__global__ void k_build_mask(uint8_t *__restrict__ mask, const uint8_t *__restrict__ solid, int nx,
+                             int ny, int nxp, int ny_cl, int ny_gdl, int mode, int periodic) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= nxp || y >= ny) return;
+  const long long c = (long long)y * nxp + x;
+  if (x >= nx) {
+    mask[c] = REG_SOLID;   // padding: never updated, never a pull source
+    return;
+  }
+  auto is_solid = [&](int xx, int yy) { return solid && solid[(long long)yy * nx + xx]; };
+  uint8_t reg;
+  if (is_solid(x, y)) reg = REG_SOLID;
+  else if (mode == 1 && y < ny_cl) reg = REG_CATALYST;
+  else if (y < ny_cl + ny_gdl) reg = REG_POROUS;
+  else reg = REG_CLEAR;
+  uint8_t m = reg;
+  if (x == 0) m |= M_XLO;
+  if (x == nx - 1) m |= M_XHI;
+  if (y == ny - 1) m |= M_YHI;
+  if (y == 0) m |= M_YLO;
+  if (reg == REG_CLEAR && x == 0 && !periodic) m |= M_INLET;
+  if (reg != REG_SOLID && solid) {
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        if (!dx && !dy) continue;
+        int sx = x + dx, sy = y + dy;
+        if (sy < 0 || sy >= ny) continue;
+        if (periodic) sx = (sx + nx) % nx;
+        if (sx < 0 || sx >= nx) continue;
+        if (is_solid(sx, sy)) m |= M_NEAR_SOLID;
+      }
+  }
+  mask[c] = m;
+}
+
+void launch_build_mask(uint8_t *mask, const uint8_t *solid, int nx, int ny, int nxp, int ny_cl,
+                       int ny_gdl, int mode, int periodic, cudaStream_t st) {
+  dim3 grid((nxp + 127) / 128, ny);
+  k_build_mask<<<grid, 128, 0, st>>>(mask, solid, nx, ny, nxp, ny_cl, ny_gdl, mode, periodic);
+}
+
+// Per-material coefficients: Darcy and Forchheimer terms of Eq. 7, the l0,
+// l1 of Eq. 8 (dt = 1), and b = 20 sqrt(3) alpha - 4 of Eq. 10 per scalar.
+template <typename R>
+__global__ void k_prep_palette(MatCoef<R> *__restrict__ pal, const MatRaw *__restrict__ raw,
+                               int npal, double nu, int forchheimer) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= npal) return;
+  const MatRaw r = raw[k];
+  MatCoef<R> c;
+  const double phi = r.phi;
+  double darcy = 0.0, forch = 0.0;
+  if (!isinf(r.K)) {
+    darcy = phi * nu / r.K;
+    if (forchheimer) forch = phi * (0.143 * pow(phi, -1.5)) / sqrt(r.K);
+  }
+  c.phi = R(phi);
+  c.inv_phi = R(1.0 / phi);
+  c.darcy = R(darcy);
+  c.forch = R(forch);
+  c.l0 = R(0.5 + 0.25 * darcy);
+  c.l1 = R(0.5 * forch);
+  for (int s = 0; s < 3; ++s) {
+    const double b = 20.0 * sqrt(3.0) * r.alpha[s] - 4.0;
+    c.b[s] = R(b);
+    c.w1[s] = R((4.0 + b) / 20.0);
+  }
+  for (int s = 0; s < 4; ++s) c.pad[s] = R(0);
+  pal[k] = c;
+}
+
+void launch_prep_palette(void *pal, const MatRaw *raw, int npal, double nu, int forchheimer,
+                         bool fp64, cudaStream_t st) {
+  const int nb = (npal + 127) / 128;
+  if (fp64)
+    k_prep_palette<double><<<nb, 128, 0, st>>>((MatCoef<double> *)pal, raw, npal, nu, forchheimer);
+  else
+    k_prep_palette<float><<<nb, 128, 0, st>>>((MatCoef<float> *)pal, raw, npal, nu, forchheimer);
+}
+
+__global__ void __launch_bounds__(kReduceThreads)
+k_sum_partials(const double *__restrict__ partial, int nblocks, double *__restrict__ out) {
+  __shared__ double sm[10 * 32];
+  double acc[10];
+  for (int k = 0; k < 10; ++k) acc[k] = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+    for (int k = 0; k < 10; ++k) acc[k] += partial[(long long)b * 10 + k];
+  block_sum<10>(acc, sm);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 10; ++k) out[k] = acc[k];
+}
+
+}  // namespace pemlbm

@@ -1,0 +1,351 @@
+// Device core of the coupled cathode lattice-Boltzmann step (sm_103a).
+//
+// One thread updates one cell: it pulls the 24 populations that stream into
+// the cell (9 D2Q9 flow + 3 x 5 D2Q5 scalar populations, Eq. 1 and 10 left-
+// hand sides), applies the boundary links of Sec. 4 where the source lies
+// outside the fluid, forms the macroscopic values (Eq. 8, 11), relaxes in
+// moment space (Eq. 1, 3-7 for the flow; Eq. 10 for T, O2, H2O), adds the
+// catalyst sources (Eq. 12-17) and writes the 24 post-collision values to
+// the other buffer.
+//
+// Storage: structure of arrays, 24 planes of ny rows x nxp (padded) columns,
+// x fastest.  Each plane holds DEVIATIONS from a fixed per-direction
+// reference: f_i - w_i rho0 for the flow and g_i - wref_{s,i} Cref_s for
+// scalar s, where wref are the D2Q5 equilibrium weights of one reference b
+// per scalar.  The references do not depend on the cell, so a pull never
+// needs the source cell's material, and all arithmetic runs on small
+// numbers (the collision is written directly in deviation moments).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pemlbm {
+
+// ------------------------------------------------------------------ mask
+enum : uint8_t {
+  REG_MASK = 3, REG_CLEAR = 0, REG_POROUS = 1, REG_CATALYST = 2, REG_SOLID = 3,
+  M_XLO = 1 << 2, M_XHI = 1 << 3, M_YHI = 1 << 4, M_YLO = 1 << 5,
+  M_INLET = 1 << 6, M_NEAR_SOLID = 1 << 7,
+  M_EDGE = M_XLO | M_XHI | M_YHI | M_YLO | M_NEAR_SOLID
+};
+
+// --------------------------------------------------------------- storage
+template <typename S> struct Real { using type = float; };
+template <> struct Real<double> { using type = double; };
+
+__device__ __forceinline__ float ld_r(const float *p) { return __ldg(p); }
+__device__ __forceinline__ double ld_r(const double *p) { return __ldg(p); }
+__device__ __forceinline__ float ld_r(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+__device__ __forceinline__ float ld_r(const __half *p) { return __half2float(*p); }
+
+__device__ __forceinline__ void st_r(float *p, float v) { *p = v; }
+__device__ __forceinline__ void st_r(double *p, double v) { *p = v; }
+__device__ __forceinline__ void st_r(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+__device__ __forceinline__ void st_r(__half *p, float v) { *p = __float2half_rn(v); }
+
+// Material coefficients of one palette entry, derived from (phi, K, alpha)
+// by k_prep_palette: 16 values so an entry is 4 x 16-byte vectors in FP32.
+template <typename R> struct alignas(16 * sizeof(R) >= 64 ? 64 : 16) MatCoef {
+  R phi, inv_phi;   // porosity and 1/phi
+  R darcy, forch;   // phi nu / K and phi F_phi / sqrt(K) of Eq. 7
+  R l0, l1;         // Eq. 8
+  R b[3];           // b of Eq. 10 for T, O2, H2O
+  R w1[3];          // (4 + b)/20: D2Q5 equilibrium weight of the moving links
+  R pad[4];
+};
+
+// Raw material tuple as given by the caller (lattice units).
+struct MatRaw { double phi, K, alpha[3]; };
+
+// Launch-invariant arguments (passed by value: constant bank).
+struct KArgs {
+  int nx, ny, nxp, periodic;
+  long long plane;          // elements per population plane
+  int mode;                 // 0 thin film, 1 volumetric catalyst rows
+  int ny_cl, y_ch0;         // catalyst rows; first channel row
+  int top_dirichlet;
+  double s_nu, s_q;         // 1/tau and the q-moment rate of Sec. 2.1
+  double body_g;            // body force per unit mass along x
+  double u_in_avg, h_ch;    // inlet parabola
+  double Q1, Q3;            // Eq. 10 rates of the flux and energy moments
+  double Cref[3], wr0[3], wr1[3], bref[3];  // deviation references
+  double Cin[3], Ctop[3];
+  // kinetics: k(T) = A exp(e_in - c1 (T - T_in)/(T T_in)), Eq. 13, 14, 16, 17
+  double kA_surf, kA_vol, k_ein, k_c1, T_in;
+  double hpo;               // temperature per unit O2 consumed (Eq. 15, 16)
+};
+
+// Velocity sets, Eq. 2 and Eq. 9 orders (folded by the compiler once the
+// loops over links are unrolled).
+#define EX9_TAB {0, 1, 0, -1, 0, 1, -1, -1, 1}
+#define EY9_TAB {0, 0, 1, 0, -1, 1, 1, -1, -1}
+#define OP9_TAB {0, 3, 4, 1, 2, 7, 8, 5, 6}
+
+template <typename R> __device__ __forceinline__ R w9(int i) {
+  return i == 0 ? R(4.0 / 9.0) : (i < 5 ? R(1.0 / 9.0) : R(1.0 / 36.0));
+}
+// d f_i^eq / d(phi p) of the Eq. 5 equilibrium: 1/3 (axis), 1/12 (diagonal).
+template <typename R> __device__ __forceinline__ R lam9(int i) {
+  return i == 0 ? R(-5.0 / 3.0) : (i < 5 ? R(1.0 / 3.0) : R(1.0 / 12.0));
+}
+
+template <typename S> struct Pops {
+  const S *__restrict__ p;
+  long long plane;
+  int nxp;
+  __device__ __forceinline__ auto at(int q, int x, int y) const {
+    return ld_r(p + (long long)q * plane + (long long)y * nxp + x);
+  }
+};
+
+// Inlet parabola at height yh (cell centres at integer y).
+template <typename R> __device__ __forceinline__ R inlet_u(const KArgs &a, R yh) {
+  R s = (yh - R(a.y_ch0) + R(0.5)) / R(a.h_ch);
+  return (s <= R(0) || s >= R(1)) ? R(0) : R(6) * R(a.u_in_avg) * s * (R(1) - s);
+}
+
+// ------------------------------------------------------------------ pull
+// Flow link i into cell (x, y) whose source lies outside the plain fluid.
+template <typename S, typename R>
+__device__ R pull_flow_edge(const Pops<S> &src, const KArgs &a, const uint8_t *__restrict__ mask,
+                            const uint16_t *__restrict__ mid, const MatCoef<R> *__restrict__ pal,
+                            int i, int x, int y, uint8_t m) {
+  const int EX[9] = EX9_TAB, EY[9] = EY9_TAB, OP[9] = OP9_TAB;
+  int sx = x - EX[i], sy = y - EY[i];
+  if (sy < 0 || sy >= a.ny) return R(src.at(OP[i], x, y));            // wall
+  if (a.periodic) {
+    sx = sx < 0 ? sx + a.nx : (sx >= a.nx ? sx - a.nx : sx);
+  } else if (sx < 0) {                                                // inlet
+    R v = R(src.at(OP[i], x, y));
+    if (m & M_INLET) v += R(6) * w9<R>(i) * R(EX[i]) * inlet_u<R>(a, R(y) - R(0.5) * R(EY[i]));
+    return v;
+  } else if (sx >= a.nx) {                                            // outlet
+    const int vx = a.nx - 1;
+    R d[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) d[k] = R(src.at(k, vx, sy));
+    R jx = d[1] - d[3] + d[5] - d[6] - d[7] + d[8];
+    R jy = d[2] - d[4] + d[5] + d[6] - d[7] - d[8];
+    R s18 = d[1] + d[2] + d[3] + d[4] + d[5] + d[6] + d[7] + d[8];
+    R inv_phi = pal[mid[(long long)sy * a.nxp + vx]].inv_phi;
+    R dP = R(-0.6) * s18 + R(0.4) * (jx * jx + jy * jy) * inv_phi;   // 1/3 - phi p*
+    return d[i] + lam9<R>(i) * dP;
+  }
+  if ((m & M_NEAR_SOLID) && (mask[(long long)sy * a.nxp + sx] & REG_MASK) == REG_SOLID)
+    return R(src.at(OP[i], x, y));                                    // solid grain
+  return R(src.at(i, sx, sy));
+}
+
+// Scalar link i of scalar s into cell (x, y) whose source is outside.  The
+// bottom wall returns the insulated value; the reaction is applied after.
+template <typename S, typename R>
+__device__ R pull_scalar_edge(const Pops<S> &src, const KArgs &a, const uint8_t *__restrict__ mask,
+                              const MatCoef<R> &mc, int s, int i, int x, int y, uint8_t m) {
+  const int EX[5] = {0, 1, 0, -1, 0}, EY[5] = {0, 0, 1, 0, -1}, OP[5] = {0, 3, 4, 1, 2};
+  const int q = 9 + 5 * s;
+  int sx = x - EX[i], sy = y - EY[i];
+  if (sy < 0) return R(src.at(q + OP[i], x, y));
+  if (sy >= a.ny) {
+    R v = R(src.at(q + OP[i], x, y));
+    if (a.top_dirichlet)
+      v = -v + R(2) * mc.w1[s] * R(a.Ctop[s]) - R(2) * R(a.wr1[s]) * R(a.Cref[s]);
+    return v;
+  }
+  if (a.periodic) {
+    sx = sx < 0 ? sx + a.nx : (sx >= a.nx ? sx - a.nx : sx);
+  } else if (sx < 0) {
+    R v = R(src.at(q + OP[i], x, y));
+    if (m & M_INLET) v = -v + R(2) * mc.w1[s] * R(a.Cin[s]) - R(2) * R(a.wr1[s]) * R(a.Cref[s]);
+    return v;
+  } else if (sx >= a.nx) {
+    return R(src.at(q + i, a.nx - 1, y));                             // fully developed
+  }
+  if ((m & M_NEAR_SOLID) && (mask[(long long)sy * a.nxp + sx] & REG_MASK) == REG_SOLID)
+    return R(src.at(q + OP[i], x, y));
+  return R(src.at(q + i, sx, sy));
+}
+
+// The 24 post-stream deviations of one cell.
+template <typename R> struct Cell {
+  R f[9];
+  R g[3][5];
+};
+
+// Rate constant of the catalyst at temperature deviation theta = T - T_in:
+// A exp(e_in - c1 theta / (T T_in)) with T = T_in + theta.
+template <typename R> __device__ __forceinline__ R rate(const KArgs &a, R A, R theta) {
+  R T = R(a.T_in) + theta;
+  return A * exp(R(a.k_ein) - R(a.k_c1) * theta / (T * R(a.T_in)));
+}
+
+// Sum of the cell's own post-collision deviations of scalar s.
+template <typename S, typename R>
+__device__ __forceinline__ R own_sum(const Pops<S> &src, int s, int x, int y) {
+  R t = 0;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) t += R(src.at(9 + 5 * s + k, x, y));
+  return t;
+}
+
+// Surface reaction of the thin film at a bottom cell (Sec. 4): the implicit
+// Tafel link.  Returns the O2 consumed J (lattice units) and modifies the
+// three upward links.  theta_n = T^n - T_in from the cell's own state.
+template <typename S, typename R>
+__device__ __forceinline__ R surface_reaction(const Pops<S> &src, const KArgs &a,
+                                              const MatCoef<R> &mc, int x, Cell<R> &c) {
+  R theta = own_sum<S, R>(src, 0, x, 0) + R(a.Cref[0] - a.T_in);
+  R k = rate<R>(a, R(a.kA_surf), theta);
+  R kappa = k / (R(2) * mc.w1[1]);
+  R gdown = c.g[1][2] + R(a.wr1[1]) * R(a.Cref[1]);   // full g*_4 of O2 (bounced)
+  R J = gdown * (R(2) * kappa) / (R(1) + kappa);
+  c.g[1][2] -= J;
+  c.g[0][2] += R(a.hpo) * J;
+  c.g[2][2] += R(2) * J;
+  return J;
+}
+
+// Volumetric catalyst sink of a catalyst cell (backward Euler in C).
+template <typename S, typename R>
+__device__ __forceinline__ R volume_sink(const Pops<S> &src, const KArgs &a, int x, int y) {
+  R theta = own_sum<S, R>(src, 0, x, y) + R(a.Cref[0] - a.T_in);
+  R C = own_sum<S, R>(src, 1, x, y) + R(a.Cref[1]);
+  R k = rate<R>(a, R(a.kA_vol), theta);
+  return -k * C / (R(1) + k);
+}
+
+// Pull all 24 populations of cell (x, y).  Returns false for solid cells.
+template <typename S, typename R>
+__device__ __forceinline__ void pull_cell(const Pops<S> &src, const KArgs &a,
+                                          const uint8_t *__restrict__ mask,
+                                          const uint16_t *__restrict__ mid,
+                                          const MatCoef<R> *__restrict__ pal,
+                                          const MatCoef<R> &mc, int x, int y, uint8_t m,
+                                          Cell<R> &c) {
+  if (!(m & M_EDGE)) {
+    const long long base = (long long)y * a.nxp + x, P = a.plane, W = a.nxp;
+    const S *p = src.p + base;
+    c.f[0] = ld_r(p);
+    c.f[1] = ld_r(p + 1 * P - 1);
+    c.f[2] = ld_r(p + 2 * P - W);
+    c.f[3] = ld_r(p + 3 * P + 1);
+    c.f[4] = ld_r(p + 4 * P + W);
+    c.f[5] = ld_r(p + 5 * P - W - 1);
+    c.f[6] = ld_r(p + 6 * P - W + 1);
+    c.f[7] = ld_r(p + 7 * P + W + 1);
+    c.f[8] = ld_r(p + 8 * P + W - 1);
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      const S *q = p + (9 + 5 * s) * P;
+      c.g[s][0] = ld_r(q);
+      c.g[s][1] = ld_r(q + 1 * P - 1);
+      c.g[s][2] = ld_r(q + 2 * P - W);
+      c.g[s][3] = ld_r(q + 3 * P + 1);
+      c.g[s][4] = ld_r(q + 4 * P + W);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) c.f[i] = pull_flow_edge<S, R>(src, a, mask, mid, pal, i, x, y, m);
+#pragma unroll
+    for (int s = 0; s < 3; ++s)
+#pragma unroll
+      for (int i = 0; i < 5; ++i) c.g[s][i] = pull_scalar_edge<S, R>(src, a, mask, mc, s, i, x, y, m);
+  }
+}
+
+// Macroscopic values of a post-stream cell (Eq. 8, 11).
+template <typename R> struct Macro {
+  R ux, uy, Pdev;   // velocity; phi p - rho0/3
+  R C[3];           // deviation sums (value - Cref)
+};
+
+template <typename R>
+__device__ __forceinline__ Macro<R> macros(const KArgs &a, const MatCoef<R> &mc, const Cell<R> &c) {
+  Macro<R> r;
+  const R *d = c.f;
+  R vx = d[1] - d[3] + d[5] - d[6] - d[7] + d[8] + R(0.5) * mc.phi * R(a.body_g);
+  R vy = d[2] - d[4] + d[5] + d[6] - d[7] - d[8];
+  R vn = sqrt(vx * vx + vy * vy);
+  R den = mc.l0 + sqrt(mc.l0 * mc.l0 + mc.l1 * vn);
+  r.ux = vx / den;
+  r.uy = vy / den;
+  R s18 = d[1] + d[2] + d[3] + d[4] + d[5] + d[6] + d[7] + d[8];
+  r.Pdev = R(0.6) * s18 - R(0.4) * (r.ux * r.ux + r.uy * r.uy) * mc.inv_phi;
+#pragma unroll
+  for (int s = 0; s < 3; ++s) r.C[s] = c.g[s][0] + c.g[s][1] + c.g[s][2] + c.g[s][3] + c.g[s][4];
+  return r;
+}
+
+// D2Q9 MRT collision with the porous force, in deviation moments (Eq. 1, 3-7).
+template <typename R>
+__device__ __forceinline__ void collide_flow(const KArgs &a, const MatCoef<R> &mc, const Macro<R> &u,
+                                             const R d[9], R o[9]) {
+  const R sn = R(a.s_nu), sq = R(a.s_q);
+  R ux = u.ux, uy = u.uy, u2 = ux * ux + uy * uy, un = sqrt(u2), ip = mc.inv_phi;
+  R Fx = -mc.darcy * ux - mc.forch * un * ux + mc.phi * R(a.body_g);
+  R Fy = -mc.darcy * uy - mc.forch * un * uy;
+  R ax = d[1] + d[2] + d[3] + d[4], dg = d[5] + d[6] + d[7] + d[8];
+  R m0 = d[0] + ax + dg;
+  R m1 = R(-4) * d[0] - ax + R(2) * dg;
+  R m2 = R(4) * d[0] - R(2) * ax + dg;
+  R m3 = d[1] - d[3] + d[5] - d[6] - d[7] + d[8];
+  R m4 = R(-2) * (d[1] - d[3]) + d[5] - d[6] - d[7] + d[8];
+  R m5 = d[2] - d[4] + d[5] + d[6] - d[7] - d[8];
+  R m6 = R(-2) * (d[2] - d[4]) + d[5] + d[6] - d[7] - d[8];
+  R m7 = d[1] - d[2] + d[3] - d[4];
+  R m8 = d[5] - d[6] + d[7] - d[8];
+  R uF = ux * Fx + uy * Fy;
+  // m* = m - S (m - m_eq) + (1 - S/2) G, equilibria relative to the rest state
+  R half_n = R(1) - R(0.5) * sn, half_q = R(1) - R(0.5) * sq;
+  m0 = m0 - sn * m0;
+  m1 = m1 - sn * (m1 - (R(6) * u.Pdev + R(3) * u2 * ip)) + half_n * (R(6) * uF * ip);
+  m2 = m2 - sn * (m2 - (R(-9) * u.Pdev - R(3) * u2 * ip)) + half_n * (R(-6) * uF * ip);
+  m3 = m3 + Fx;
+  m4 = m4 - sq * (m4 + ux) + half_q * (-Fx);
+  m5 = m5 + Fy;
+  m6 = m6 - sq * (m6 + uy) + half_q * (-Fy);
+  m7 = m7 - sn * (m7 - (ux * ux - uy * uy) * ip) + half_n * (R(2) * (ux * Fx - uy * Fy) * ip);
+  m8 = m8 - sn * (m8 - ux * uy * ip) + half_n * ((ux * Fy + uy * Fx) * ip);
+  // f* = M^-1 m*, M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
+  R a0 = m0 * R(1.0 / 9), a1 = m1 * R(1.0 / 36), a2 = m2 * R(1.0 / 36);
+  R a3 = m3 * R(1.0 / 6), a4 = m4 * R(1.0 / 12), a5 = m5 * R(1.0 / 6), a6 = m6 * R(1.0 / 12);
+  R a7 = m7 * R(0.25), a8 = m8 * R(0.25);
+  R axs = a0 - a1 - R(2) * a2, dgs = a0 + R(2) * a1 + a2;
+  o[0] = a0 - R(4) * a1 + R(4) * a2;
+  o[1] = axs + a3 - R(2) * a4 + a7;
+  o[2] = axs + a5 - R(2) * a6 - a7;
+  o[3] = axs - a3 + R(2) * a4 + a7;
+  o[4] = axs - a5 + R(2) * a6 - a7;
+  o[5] = dgs + a3 + a4 + a5 + a6 + a8;
+  o[6] = dgs - a3 - a4 + a5 + a6 - a8;
+  o[7] = dgs - a3 - a4 - a5 - a6 + a8;
+  o[8] = dgs + a3 + a4 - a5 - a6 - a8;
+}
+
+// D2Q5 MRT collision of scalar s in deviation moments (Eq. 10), plus a
+// volumetric source src added with the cell's equilibrium weights.
+template <typename R>
+__device__ __forceinline__ void collide_scalar(const KArgs &a, const MatCoef<R> &mc, int s,
+                                               R ux, R uy, R Cdev, const R d[5], R srcv, R o[5]) {
+  const R Q1 = R(a.Q1), Q3 = R(a.Q3);
+  R C = Cdev + R(a.Cref[s]);
+  R n0 = Cdev;
+  R n1 = d[1] - d[3], n2 = d[2] - d[4];
+  R n3 = R(-4) * d[0] + d[1] + d[2] + d[3] + d[4];
+  R n4 = d[1] - d[2] + d[3] - d[4];
+  R b = mc.b[s];
+  n1 -= Q1 * (n1 - ux * C);
+  n2 -= Q1 * (n2 - uy * C);
+  n3 -= Q3 * (n3 - (b * Cdev + (b - R(a.bref[s])) * R(a.Cref[s])));
+  n4 -= Q3 * n4;
+  R w1 = mc.w1[s], w0 = R(1) - R(4) * w1;
+  R c0 = n0 * R(0.2), c3 = n3 * R(0.05);
+  o[0] = (n0 - n3) * R(0.2) + w0 * srcv;
+  o[1] = c0 + R(0.5) * n1 + c3 + R(0.25) * n4 + w1 * srcv;
+  o[3] = c0 - R(0.5) * n1 + c3 + R(0.25) * n4 + w1 * srcv;
+  o[2] = c0 + R(0.5) * n2 + c3 - R(0.25) * n4 + w1 * srcv;
+  o[4] = c0 - R(0.5) * n2 + c3 - R(0.25) * n4 + w1 * srcv;
+}
+
+}  // namespace pemlbm

@@ -1,0 +1,229 @@
+"""Python binding of libpemlbm (argument marshalling only: every step of the
+coupled cathode update runs in the library's CUDA kernels).
+
+The names mirror the C ABI of include/pemlbm.h.  Importing this module on a
+machine without the built library raises; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpemlbm.so")
+
+FP64, FP32, BF16, FP16 = 0, 1, 2, 3
+PRECISION = {"fp64": FP64, "fp32": FP32, "bf16": BF16, "fp16": FP16}
+STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM_ESTATE",
+          5: "LBM_EDIVERGED", 6: "LBM_ETIMEOUT"}
+
+# Every symbol the header declares (the CPU tests check the exports).
+EXPORTS = ("lbm_create_domain", "lbm_destroy_domain", "lbm_set_params", "lbm_set_fields",
+           "lbm_reset", "lbm_step", "lbm_current_density", "lbm_residual", "lbm_get_fields",
+           "lbm_get_state", "lbm_set_state", "lbm_get_mask", "lbm_get_step", "lbm_save_state",
+           "lbm_load_state", "lbm_time_steps", "lbm_bytes_per_cell", "lbm_last_error")
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class lbm_domain_desc(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("ny_cl", C.c_int32),
+                ("ny_gdl", C.c_int32), ("reaction_mode", C.c_int32), ("periodic_x", C.c_int32),
+                ("precision", C.c_int32), ("reserved", C.c_int32),
+                ("solid", C.POINTER(C.c_uint8)), ("cuda_stream", C.c_void_p)]
+
+
+_PARAM_DOUBLES = ("nu", "u_in_avg", "body_force_x", "V_op", "T_in", "C_O2_in", "C_H2O_in",
+                  "T_top", "C_O2_top", "C_H2O_top", "aj0_ref", "T_ref_kin", "E_act", "alpha_c",
+                  "F", "R", "dU0dT", "U0_0", "x_ref", "dx_cm", "dt_s", "delta_cl_cm", "c_tot",
+                  "rho_cp_f")
+
+
+class lbm_params(C.Structure):
+    _fields_ = [(k, C.c_double) for k in _PARAM_DOUBLES] + [("forchheimer", C.c_int32),
+                                                            ("top_dirichlet", C.c_int32)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libpemlbm.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_2103_01444_gb300.build.build()")
+    L = C.CDLL(path)
+    P, d = C.c_void_p, C.POINTER(C.c_double)
+    sig = {
+        "lbm_create_domain": [C.POINTER(lbm_domain_desc), C.POINTER(P)],
+        "lbm_destroy_domain": [P],
+        "lbm_set_params": [P, C.POINTER(lbm_params)],
+        "lbm_set_fields": [P, d, d, d, d, d],
+        "lbm_reset": [P],
+        "lbm_step": [P, C.c_int64],
+        "lbm_current_density": [P, d, d, C.POINTER(C.c_float)],
+        "lbm_residual": [P, d],
+        "lbm_get_fields": [P, C.c_void_p, C.c_int32],
+        "lbm_get_state": [P, d],
+        "lbm_set_state": [P, d],
+        "lbm_get_mask": [P, C.POINTER(C.c_uint8)],
+        "lbm_get_step": [P, C.POINTER(C.c_int64)],
+        "lbm_save_state": [P, C.c_void_p, C.POINTER(C.c_size_t)],
+        "lbm_load_state": [P, C.c_void_p, C.c_size_t],
+        "lbm_time_steps": [P, C.c_int64, d],
+        "lbm_bytes_per_cell": [P, d],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    L.lbm_last_error.argtypes = []
+    L.lbm_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _check(status):
+    if status != 0:
+        raise LbmError(status, _lib.lbm_last_error().decode())
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class Domain:
+    """One cathode lattice on the GPU (wraps an lbm_domain handle)."""
+
+    def __init__(self, nx, ny, ny_cl=0, ny_gdl=0, reaction_mode=0, periodic_x=0,
+                 precision="fp32", solid=None, stream=None):
+        self.L = load_library()
+        self.nx, self.ny = int(nx), int(ny)
+        self._solid = None if solid is None else np.ascontiguousarray(solid, np.uint8)
+        desc = lbm_domain_desc(
+            nx=self.nx, ny=self.ny, ny_cl=int(ny_cl), ny_gdl=int(ny_gdl),
+            reaction_mode=int(reaction_mode), periodic_x=int(periodic_x),
+            precision=PRECISION[precision] if isinstance(precision, str) else int(precision),
+            reserved=0,
+            solid=None if self._solid is None else self._solid.ctypes.data_as(C.POINTER(C.c_uint8)),
+            cuda_stream=None if stream is None else C.c_void_p(int(stream)))
+        h = C.c_void_p()
+        _check(self.L.lbm_create_domain(C.byref(desc), C.byref(h)))
+        self.h = h
+        self.precision = desc.precision
+
+    @classmethod
+    def from_case(cls, case: dict, precision="fp32", forchheimer: int = 1, stream=None,
+                  reset: bool = True):
+        from .units import cathode_params
+        params, fields, geo = cathode_params(case, forchheimer)
+        d = cls(precision=precision, stream=stream, **geo)
+        d.set_params(params)
+        d.set_fields(**fields)
+        if reset:
+            d.reset()
+        return d
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.lbm_destroy_domain(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- set-up
+    def set_params(self, params: dict):
+        self.params = dict(params)
+        _check(self.L.lbm_set_params(self.h, C.byref(lbm_params(**params))))
+
+    def set_fields(self, phi, K, alpha_T, D_O2, D_H2O):
+        arrs = [np.ascontiguousarray(np.broadcast_to(np.asarray(a, np.float64), (self.ny, self.nx)))
+                for a in (phi, K, alpha_T, D_O2, D_H2O)]
+        _check(self.L.lbm_set_fields(self.h, *[_dp(a) for a in arrs]))
+
+    def reset(self):
+        _check(self.L.lbm_reset(self.h))
+
+    # -- stepping
+    def step(self, n: int = 1):
+        _check(self.L.lbm_step(self.h, int(n)))
+        return self
+
+    def time_steps(self, n: int) -> float:
+        ms = C.c_double()
+        _check(self.L.lbm_time_steps(self.h, int(n), C.byref(ms)))
+        return ms.value
+
+    @property
+    def steps(self) -> int:
+        s = C.c_int64()
+        _check(self.L.lbm_get_step(self.h, C.byref(s)))
+        return s.value
+
+    # -- read-outs
+    def current_density(self, profile: bool = True):
+        i_avg, heat = C.c_double(), C.c_double()
+        prof = np.zeros(self.nx, np.float32) if profile else None
+        _check(self.L.lbm_current_density(
+            self.h, C.byref(i_avg), C.byref(heat),
+            None if prof is None else prof.ctypes.data_as(C.POINTER(C.c_float))))
+        return i_avg.value, heat.value, prof
+
+    def residual(self) -> float:
+        r = C.c_double()
+        _check(self.L.lbm_residual(self.h, C.byref(r)))
+        return r.value
+
+    def fields(self, out=None):
+        """dict of [ny][nx] float64 arrays ux, uy, p, T, C_O2, C_H2O; with a
+        CUDA tensor ``out`` of shape (6, ny, nx) float64 they are written there
+        on the domain's stream instead."""
+        if out is not None:
+            _check(self.L.lbm_get_fields(self.h, C.c_void_p(out.data_ptr()), 1))
+            return out
+        a = np.empty((6, self.ny, self.nx))
+        _check(self.L.lbm_get_fields(self.h, a.ctypes.data_as(C.c_void_p), 0))
+        return dict(zip(("ux", "uy", "p", "T", "C_O2", "C_H2O"), a))
+
+    def state(self):
+        """Full post-collision populations, (24, ny, nx) float64."""
+        a = np.empty((24, self.ny, self.nx))
+        _check(self.L.lbm_get_state(self.h, _dp(a)))
+        return a
+
+    def set_state(self, pops):
+        a = np.ascontiguousarray(pops, np.float64)
+        assert a.shape == (24, self.ny, self.nx)
+        _check(self.L.lbm_set_state(self.h, _dp(a)))
+
+    def mask(self):
+        m = np.empty((self.ny, self.nx), np.uint8)
+        _check(self.L.lbm_get_mask(self.h, m.ctypes.data_as(C.POINTER(C.c_uint8))))
+        return m
+
+    def save_state(self) -> bytes:
+        n = C.c_size_t()
+        _check(self.L.lbm_save_state(self.h, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        _check(self.L.lbm_save_state(self.h, buf, C.byref(n)))
+        return buf.raw
+
+    def load_state(self, blob: bytes):
+        _check(self.L.lbm_load_state(self.h, blob, len(blob)))
+
+    def bytes_per_cell(self) -> float:
+        b = C.c_double()
+        _check(self.L.lbm_bytes_per_cell(self.h, C.byref(b)))
+        return b.value

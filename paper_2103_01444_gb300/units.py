@@ -1,0 +1,80 @@
+"""Physical cathode description -> lattice parameters and per-cell material.
+
+Constants from arXiv 2103.01444 (Nomenclature, Eqs. 13-19); lattice scales
+where the paper gives none:
+  * gas viscosity nu = 0.05 (tau = 0.65) and O2 diffusivity 0.05 in lattice
+    units (Schmidt number 1), H2O diffusivity 1.3 x O2, Prandtl number 0.7;
+  * dx = GDL thickness / GDL rows, dt = 0.05 dx^2 / D_O2 (D_O2 = 5.2197e-2
+    cm^2/s, Nomenclature);
+  * solid/gas heat-capacity ratio 1500 and conductivity ratio 1.5/0.026
+    (Nomenclature) in Eq. 19; catalyst film 10 um thick;
+  * c_tot = C_O2,ref / 0.21 with C_O2,ref = 17.808e-6 mol/cm^3, and a gas
+    molar heat capacity of 29.3 J/(mol K);
+  * Eq. 17's reference temperature 353.15 K.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+PAPER = dict(
+    aj0_ref=1.0e-4,        # A/cm^3 (exchange current density x area)
+    C_O2_ref=17.808e-6,    # mol/cm^3
+    alpha_c=1.0,
+    F=96487.0,
+    R=8.314,
+    D_O2_cm2_s=5.2197e-2,
+    k_f=0.026, k_s=1.5,    # W/(m K)
+    E_act=16456.0, T_ref_kin=353.15,   # Eq. 17
+    dU0dT=0.0025, U0_0=0.2329,         # Eq. 16
+)
+
+LATTICE = dict(nu=0.05, D_O2=0.05, h2o_over_o2=1.3, prandtl=0.7, heat_capacity_ratio=1500.0,
+               delta_cl_cm=10e-4, gas_cp_J_molK=29.3, x_ref=0.21)
+
+
+def effective_diffusivity(phi, D):
+    """Bruggeman correlation, Eq. 18."""
+    return D * phi ** 1.5
+
+
+def effective_thermal_diffusivity(phi, alpha_gas):
+    """Eq. 19 with the gas diffusivity k_f/(rho c_p)_f factored out."""
+    kr = PAPER["k_s"] / PAPER["k_f"]
+    cr = LATTICE["heat_capacity_ratio"]
+    return alpha_gas * (phi + kr * (1.0 - phi)) / (phi + cr * (1.0 - phi))
+
+
+def cathode_params(case: dict, forchheimer: int = 1):
+    """Returns (params dict matching lbm_params, fields dict of [ny][nx]
+    float64 arrays phi, K, alpha_T, D_O2, D_H2O, geometry dict)."""
+    nx, ny = int(case["nx"]), int(case["ny"])
+    ny_cl, ny_gdl = int(case["ny_cl"]), int(case["ny_gdl"])
+    L = LATTICE
+    dx = case["h_gdl_cm"] / ny_gdl
+    dt = L["D_O2"] * dx ** 2 / PAPER["D_O2_cm2_s"]
+    c_tot = PAPER["C_O2_ref"] / L["x_ref"]
+    channel_rows = ny - ny_cl - ny_gdl
+    phi = np.ascontiguousarray(case["phi"], dtype=np.float64)
+    K_cm2 = np.asarray(case["K_cm2"], dtype=np.float64)
+    K = np.ascontiguousarray(np.where(np.isfinite(K_cm2), K_cm2 / dx ** 2, np.inf))
+    alpha_gas = L["nu"] / L["prandtl"]
+    fields = dict(
+        phi=phi, K=K,
+        alpha_T=np.ascontiguousarray(effective_thermal_diffusivity(phi, alpha_gas)),
+        D_O2=np.ascontiguousarray(effective_diffusivity(phi, L["D_O2"])),
+        D_H2O=np.ascontiguousarray(effective_diffusivity(phi, L["h2o_over_o2"] * L["D_O2"])),
+    )
+    params = dict(
+        nu=L["nu"], u_in_avg=case["Re"] * L["nu"] / channel_rows, body_force_x=0.0,
+        V_op=case["V_op"], T_in=case["T_in"], C_O2_in=case["C_O2_in"], C_H2O_in=case["C_H2O_in"],
+        T_top=case["T_in"], C_O2_top=case["C_O2_in"], C_H2O_top=case["C_H2O_in"],
+        aj0_ref=PAPER["aj0_ref"], T_ref_kin=PAPER["T_ref_kin"], E_act=PAPER["E_act"],
+        alpha_c=PAPER["alpha_c"], F=PAPER["F"], R=PAPER["R"], dU0dT=PAPER["dU0dT"],
+        U0_0=PAPER["U0_0"], x_ref=L["x_ref"], dx_cm=dx, dt_s=dt, delta_cl_cm=L["delta_cl_cm"],
+        c_tot=c_tot, rho_cp_f=L["gas_cp_J_molK"] * c_tot, forchheimer=forchheimer,
+        top_dirichlet=0,
+    )
+    geometry = dict(nx=nx, ny=ny, ny_cl=ny_cl, ny_gdl=ny_gdl,
+                    reaction_mode=int(case["reaction_mode"]),
+                    periodic_x=int(case.get("periodic_x", 0)), solid=case.get("solid"))
+    return params, fields, geometry

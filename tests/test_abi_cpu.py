@@ -1,0 +1,86 @@
+"""CPU checks of the C ABI and the host-side parameter mapping (no GPU)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2103_01444_gb300 import workloads
+from paper_2103_01444_gb300.units import cathode_params
+from paper_2103_01444_gb300 import lbm
+from oracle.params import lattice_problem
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pemlbm.h")
+
+
+def declared_symbols():
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:lbm_status|const char \*)\s*(lbm_\w+)\s*\(", src, re.M)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2103_01444_gb300.build import build
+    return build()
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    syms = declared_symbols()
+    assert len(syms) >= 17
+    L = ctypes.CDLL(libpath)
+    for s in syms:
+        assert hasattr(L, s), s
+    assert set(syms) == set(lbm.EXPORTS)
+
+
+def test_binding_loads_without_gpu(libpath):
+    L = lbm.load_library(libpath)
+    assert L.lbm_last_error() is not None
+
+
+def test_param_structs_match_header():
+    src = open(HEADER).read()
+    p = src[src.index("} lbm_domain_desc;"):src.index("} lbm_params;")]
+    doubles = re.findall(r"double ([\w, ]+);", p)
+    names = [n.strip() for grp in doubles for n in grp.split(",")]
+    assert names == list(lbm._PARAM_DOUBLES)
+    assert ctypes.sizeof(lbm.lbm_params) == 8 * len(names) + 8
+    assert ctypes.sizeof(lbm.lbm_domain_desc) == 8 * 4 + 16
+
+
+@pytest.mark.parametrize("case", [workloads.cathode_200x40(),
+                                  workloads.small_cathode(nx=40, ny=20, reaction_mode=1),
+                                  workloads.cathode_blocks(nx=256, ny=128)])
+def test_product_and_oracle_unit_mappings_agree(case):
+    """The product's unit helper and the oracle's independent mapping turn
+    the same physical workload into the same lattice problem."""
+    p1, f1, g1 = cathode_params(case)
+    p2, m2, _ = lattice_problem(case)
+    for k, v in p1.items():
+        if k in p2:
+            assert v == pytest.approx(p2[k], rel=1e-13), k
+    for k in ("phi", "K", "alpha_T", "D_O2", "D_H2O"):
+        np.testing.assert_allclose(f1[k], m2[k], rtol=1e-13)
+    assert g1["ny_cl"] == p2["ny_cl"] and g1["ny_gdl"] == p2["ny_gdl"]
+
+
+def test_workloads_are_seeded_and_shaped():
+    a, b = workloads.cathode_blocks(512, 256), workloads.cathode_blocks(512, 256)
+    np.testing.assert_array_equal(a["phi"], b["phi"])
+    ny_cl, ny_gdl = a["ny_cl"], a["ny_gdl"]
+    assert (ny_cl, ny_gdl) == (13, 141)
+    gdl = a["phi"][ny_cl:ny_cl + ny_gdl]
+    assert 0.4 <= gdl.min() and gdl.max() <= 0.8
+    # one value per 32 x 32 block
+    blk = a["phi"][32:64, 32:64]
+    assert np.unique(blk).size == 1
+    Kg = a["K_cm2"][ny_cl:ny_cl + ny_gdl] * 1e-4
+    assert 1e-12 <= Kg.min() and Kg.max() <= 1e-10
+    assert np.isinf(a["K_cm2"][ny_cl + ny_gdl:]).all()
+    cases = workloads.sweep_cases(8)
+    assert all(c["nx"] % 32 == 0 and c["ny"] % 32 == 0 for c in cases)
+    g = workloads.cathode_grains(256, 64)
+    assert g["solid"][:, :4].sum() == 0 and g["solid"][:, -4:].sum() == 0
+    assert 0.2 < g["solid"][:g["ny_gdl"]].mean() < 0.4

@@ -1,0 +1,259 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Masks and boundary classification must match bit for bit.  Fields, states
+and the current density must match within the stated tolerances: FP64
+storage to round-off, FP32 storage within relative L2 1e-5 after the stated
+step counts.
+"""
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from oracle.params import lattice_problem
+from paper_2103_01444_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2103_01444_gb300.build import build
+    build()
+
+
+def gpu_domain(case, precision, forchheimer=1):
+    from paper_2103_01444_gb300.lbm import Domain
+    return Domain.from_case(case, precision=precision, forchheimer=forchheimer)
+
+
+def oracle_of(case, forchheimer=1):
+    params, material, solid = lattice_problem(case, forchheimer)
+    return Oracle(params, material, solid)
+
+
+def rel_l2(a, b, mask=None):
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    if mask is not None:
+        a, b = a[mask], b[mask]
+    den = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (den if den > 0 else 1.0)
+
+
+def oracle_state(o):
+    return np.concatenate([o.f, o.g.reshape(15, o.ny, o.nx)], axis=0)
+
+
+CASES = {
+    "film-64x16": lambda: workloads.small_cathode(nx=64, ny=16, reaction_mode=0),
+    "vol-77x20": lambda: workloads.small_cathode(nx=77, ny=20, reaction_mode=1, seed=5),
+    "grains-70x24": lambda: workloads.small_cathode(nx=70, ny=24, reaction_mode=0, grains=True,
+                                                    seed=9),
+    "film-200x40": lambda: workloads.cathode_200x40(),
+    "blocks-300x64": lambda: workloads.cathode_blocks(nx=300, ny=64),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_mask_bit_exact(name):
+    case = CASES[name]()
+    d = gpu_domain(case, "fp32")
+    o = oracle_of(case)
+    np.testing.assert_array_equal(d.mask(), o.mask)
+
+
+def test_mask_periodic_bit_exact():
+    case = workloads.small_cathode(nx=40, ny=12, reaction_mode=0, grains=True, seed=4)
+    case["periodic_x"] = 1
+    d = gpu_domain(case, "fp64")
+    o = oracle_of(case)
+    np.testing.assert_array_equal(d.mask(), o.mask)
+
+
+@pytest.mark.parametrize("name", ["film-64x16", "vol-77x20", "grains-70x24"])
+def test_initial_state(name):
+    case = CASES[name]()
+    d = gpu_domain(case, "fp64")
+    o = oracle_of(case)
+    live = (o.mask & 3) != 3
+    st = d.state()
+    ref = oracle_state(o)
+    np.testing.assert_allclose(st[:, live], ref[:, live], rtol=1e-14, atol=1e-14)
+
+
+@pytest.mark.parametrize("name,steps", [("film-64x16", 300), ("vol-77x20", 300),
+                                        ("grains-70x24", 300), ("blocks-300x64", 120)])
+def test_fp64_state_matches_oracle(name, steps):
+    """FP64 storage: every population agrees with the oracle to round-off."""
+    case = CASES[name]()
+    case["V_op"] = 0.4   # strong reaction: exercises the implicit Tafel links
+    d = gpu_domain(case, "fp64")
+    o = oracle_of(case)
+    d.step(steps)
+    o.step(steps)
+    live = (o.mask & 3) != 3
+    st, ref = d.state(), oracle_state(o)
+    for q in range(24):
+        scale = np.abs(ref[q][live]).max()
+        np.testing.assert_allclose(st[q][live], ref[q][live], rtol=0, atol=1e-11 * scale,
+                                   err_msg=f"population plane {q}")
+    fg, fo = d.fields(), o.fields()
+    for k in ("ux", "uy", "p", "T", "C_O2", "C_H2O"):
+        assert rel_l2(fg[k], fo[k], live) < 1e-11, k
+    i_g, h_g, prof_g = d.current_density()
+    i_o, h_o, prof_o = o.current_density()
+    assert i_g == pytest.approx(i_o, rel=1e-11)
+    assert h_g == pytest.approx(h_o, rel=1e-11)
+    np.testing.assert_allclose(prof_g, prof_o, rtol=1e-6)
+
+
+@pytest.fixture(scope="module")
+def cathode_200x40_oracle():
+    case = workloads.cathode_200x40()
+    o = oracle_of(case)
+    o.step(case["steps"])
+    return case, o
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("fp64", 1e-11)])
+def test_cathode_200x40_after_5000_steps(cathode_200x40_oracle, precision, tol):
+    """The 200 x 40 cathode (GDL phi 0.6, Da 1e-3, Re 20, 343 K, 0.6 V, thin
+    film) after 5000 steps: relative L2 error of u, T, C_O2, C_H2O and the
+    current density within tol of the FP64 oracle."""
+    case, o = cathode_200x40_oracle
+    d = gpu_domain(case, precision)
+    d.step(case["steps"])
+    fg, fo = d.fields(), o.fields()
+    u_g = np.stack([fg["ux"], fg["uy"]])
+    u_o = np.stack([fo["ux"], fo["uy"]])
+    assert rel_l2(u_g, u_o) < tol
+    assert rel_l2(fg["T"] - case["T_in"], fo["T"] - case["T_in"]) < tol
+    for k in ("C_O2", "C_H2O"):
+        assert rel_l2(fg[k], fo[k]) < tol, k
+    i_g, h_g, prof_g = d.current_density()
+    i_o, h_o, prof_o = o.current_density()
+    assert abs(i_g - i_o) / abs(i_o) < tol
+    assert abs(h_g - h_o) / abs(h_o) < tol
+    assert rel_l2(prof_g, prof_o) < max(tol, 2e-7)
+
+
+def test_fp32_volumetric_and_grains_short_runs():
+    for name, steps in (("vol-77x20", 1500), ("grains-70x24", 1500)):
+        case = CASES[name]()
+        d = gpu_domain(case, "fp32")
+        o = oracle_of(case)
+        d.step(steps)
+        o.step(steps)
+        live = (o.mask & 3) != 3
+        fg, fo = d.fields(), o.fields()
+        for k in ("ux", "uy"):
+            assert rel_l2(np.stack([fg["ux"], fg["uy"]]), np.stack([fo["ux"], fo["uy"]]),
+                          np.stack([live, live])) < 1e-5
+        assert rel_l2(fg["T"] - 343.0, fo["T"] - 343.0, live) < 1e-5
+        for k in ("C_O2", "C_H2O"):
+            assert rel_l2(fg[k], fo[k], live) < 1e-5, (name, k)
+        i_g, _, _ = d.current_density()
+        i_o, _, _ = o.current_density()
+        assert abs(i_g - i_o) / abs(i_o) < 1e-5
+
+
+def test_periodic_closed_box_invariants_on_gpu():
+    """Closed periodic box with reaction: sum(C_H2O + 2 C_O2) is conserved
+    by the GPU step too (FP64 storage)."""
+    case = workloads.small_cathode(nx=48, ny=16, reaction_mode=1, V_op=0.35)
+    case["periodic_x"] = 1
+    d = gpu_domain(case, "fp64")
+    s0 = d.state()
+    d.step(400)
+    s1 = d.state()
+    tot = lambda s: s[19:24].sum() + 2 * s[14:19].sum()  # noqa: E731
+    assert s1[14:19].sum() < 0.999 * s0[14:19].sum()
+    assert abs(tot(s1) - tot(s0)) < 1e-11 * tot(s0)
+
+
+def test_tiny_and_degenerate_lattices():
+    """4 x 3 lattice (one GDL row, one catalyst row) and an all-channel
+    periodic strip: parity with the oracle in FP64."""
+    case = workloads.small_cathode(nx=4, ny=3, reaction_mode=1, random_material=False)
+    case.update(ny_cl=1, ny_gdl=1, Re=1.0)
+    d = gpu_domain(case, "fp64")
+    o = oracle_of(case)
+    d.step(50)
+    o.step(50)
+    np.testing.assert_allclose(d.state(), oracle_state(o), rtol=0, atol=1e-12 * 343)
+    case = workloads.small_cathode(nx=33, ny=5, reaction_mode=0, random_material=False)
+    case["periodic_x"] = 1
+    d = gpu_domain(case, "fp64")
+    o = oracle_of(case)
+    d.step(80)
+    o.step(80)
+    np.testing.assert_allclose(d.state(), oracle_state(o), rtol=0, atol=1e-12 * 343)
+
+
+def test_graph_replay_equals_direct_launches():
+    """lbm_step replays a captured CUDA graph for long runs; the state must be
+    bit-identical to the same number of single launches."""
+    case = workloads.small_cathode(nx=96, ny=24, reaction_mode=1)
+    a = gpu_domain(case, "fp32")
+    b = gpu_domain(case, "fp32")
+    a.step(300)
+    for _ in range(300):
+        b.step(1)
+    np.testing.assert_array_equal(a.state(), b.state())
+
+
+def test_save_load_roundtrip():
+    case = workloads.small_cathode(nx=40, ny=16, reaction_mode=0)
+    a = gpu_domain(case, "fp32")
+    a.step(37)
+    blob = a.save_state()
+    a.step(20)
+    ref = a.state()
+    b = gpu_domain(case, "fp32")
+    b.load_state(blob)
+    assert b.steps == 37
+    b.step(20)
+    np.testing.assert_array_equal(b.state(), ref)
+
+
+def test_residual_decreases_and_detects_divergence():
+    case = workloads.small_cathode(nx=64, ny=16, reaction_mode=0)
+    d = gpu_domain(case, "fp32")
+    d.step(100)
+    r1 = d.residual()
+    d.step(4000)
+    d.residual()
+    d.step(100)
+    r2 = d.residual()
+    assert 0 < r2 < r1
+    st = d.state()
+    st[3, 5, 7] = np.nan
+    d.set_state(st)
+    from paper_2103_01444_gb300.lbm import LbmError
+    with pytest.raises(LbmError, match="EDIVERGED"):
+        d.residual()
+
+
+def test_invalid_arguments_are_rejected():
+    from paper_2103_01444_gb300.lbm import Domain, LbmError
+    with pytest.raises(LbmError, match="EINVAL"):
+        Domain(3, 3)
+    with pytest.raises(LbmError, match="EINVAL"):
+        Domain(16, 8, ny_cl=2, reaction_mode=0)
+    solid = np.zeros((8, 16), np.uint8)
+    solid[3, 15] = 1
+    with pytest.raises(LbmError, match="EINVAL"):
+        Domain(16, 8, ny_gdl=4, solid=solid)
+    d = Domain(16, 8, ny_gdl=4)
+    with pytest.raises(LbmError, match="ESTATE"):
+        d.step(1)
+    case = workloads.small_cathode(nx=16, ny=8)
+    from paper_2103_01444_gb300.units import cathode_params
+    p, f, g = cathode_params(case)
+    d.set_params(p)
+    bad = dict(f)
+    bad["D_O2"] = np.full((8, 16), 0.2)   # b > 1: negative rest weight
+    with pytest.raises(LbmError, match="EINVAL"):
+        d.set_fields(**bad)
+    p2 = dict(p, nu=-1.0)
+    with pytest.raises(LbmError, match="EINVAL"):
+        d.set_params(p2)
