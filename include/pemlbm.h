@@ -87,6 +87,12 @@ typedef struct {
   double rho_cp_f;             /* gas volumetric heat capacity, J/(cm^3 K) */
   int32_t forchheimer;         /* 1: Eq. 7 with the Forchheimer term; 0: Darcy only */
   int32_t top_dirichlet;       /* scalars at the top wall: 0 insulated, 1 fixed values */
+  int32_t interface_mode;      /* 0: Eq. 10 as printed, b from each cell's own diffusivity
+                                  with fixed Q (alpha C is continuous across layers);
+                                  1: Fickian, one b per scalar (that of its largest
+                                  diffusivity) and each cell's diffusivity set through
+                                  the flux-moment rate (C and -alpha grad C continuous) */
+  int32_t reserved;            /* must be 0 */
 } lbm_params;
 
 typedef struct lbm_domain lbm_domain; /* opaque */
@@ -106,17 +112,21 @@ lbm_status lbm_destroy_domain(lbm_domain *d);
 lbm_status lbm_set_params(lbm_domain *d, const lbm_params *p);
 
 /* Per-cell material, host arrays [ny][nx] of doubles, lattice units:
- *   phi      porosity, 0 < phi <= 1 (Eq. 5, 7)
- *   K        permeability; +INFINITY marks clear fluid (no drag) (Eq. 7)
- *   alpha_T  effective thermal diffusivity (Eq. 19)
- *   D_O2     effective O2 diffusivity (Eq. 18)
- *   D_H2O    effective H2O diffusivity
+ *   phi           porosity, 0 < phi <= 1 (Eq. 5, 7)
+ *   K             permeability; +INFINITY marks clear fluid (no drag) (Eq. 7)
+ *   alpha_T       effective thermal diffusivity (Eq. 19)
+ *   D_O2          effective O2 diffusivity (Eq. 18)
+ *   D_H2O         effective H2O diffusivity
+ *   rho_cp_ratio  (rho c_p)_eff / (rho c_p)_f of Eq. 19, >= 1e-6; the
+ *                 reaction heat enters the temperature equation divided by
+ *                 it.  NULL = 1 everywhere.
  * Each diffusivity must lie in (0, 5/(20 sqrt 3)] so that the D2Q5 rest
  * weight (1-b)/5 of Eq. 10 is non-negative.  Solid cells are ignored.
  * Distinct material tuples are collected into a palette of at most 65535
  * entries (EINVAL beyond that). */
 lbm_status lbm_set_fields(lbm_domain *d, const double *phi, const double *K,
-                          const double *alpha_T, const double *D_O2, const double *D_H2O);
+                          const double *alpha_T, const double *D_O2, const double *D_H2O,
+                          const double *rho_cp_ratio);
 
 /* Initial state: f_i = w_i rho0 (rest), g = D2Q5 equilibrium of the inlet
  * values at rest with each cell's own b.  Step counter := 0. */
@@ -179,6 +189,17 @@ lbm_status lbm_load_state(lbm_domain *d, const void *buf, size_t bytes);
  * reporting: runs nsteps steps bracketed by CUDA events on the domain's
  * stream and returns the elapsed device time. */
 lbm_status lbm_time_steps(lbm_domain *d, int64_t nsteps, double *elapsed_ms);
+
+/* Launch shapes of the step kernel (cells per block along x and y, and the
+ * minimum resident blocks per SM asked of the register allocator).
+ * lbm_tune, called between lbm_reset and the first step, times every shape
+ * over trial_steps launches of the same step (the state is left as reset
+ * left it), keeps the fastest and returns its index and time per step (ms).
+ * ESTATE after the first step.  lbm_set_variant selects one explicitly
+ * (0 <= variant < 8; EINVAL otherwise).  All shapes give bit-identical
+ * results. */
+lbm_status lbm_tune(lbm_domain *d, int32_t trial_steps, int32_t *variant, double *best_ms);
+lbm_status lbm_set_variant(lbm_domain *d, int32_t variant);
 
 /* Bytes the method must move per cell update for this domain's storage
  * (24 populations read and written once, plus the 1-byte node mask). */

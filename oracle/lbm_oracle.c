@@ -44,6 +44,10 @@
  *     added after collision as w_i(b) S.
  *   - k(T), C and T in the reaction terms use the cell's previous
  *     post-collision sums (C^n = sum g*(x)).
+ *   - Eq. 10 with a per-cell b and fixed Q (the default) diffuses alpha C,
+ *     so alpha C, not C, is continuous across the GDL/channel interface; an
+ *     optional Fickian interface mode keeps one b per scalar and sets each
+ *     cell's diffusivity through the flux-moment rate instead.
  *
  * Storage: f[q][y][x] (9 planes), g[s][q][y][x] (3 scalars x 5 planes),
  * s = 0 temperature, 1 O2 mole fraction, 2 H2O mole fraction.  Full values,
@@ -147,6 +151,9 @@ typedef struct {
   int32_t periodic_x;       /* 1: x wraps (closed-form tests), 0: inlet/outlet */
   int32_t forchheimer;      /* 1: Eq. 7 with the Forchheimer term, 0: Darcy only */
   int32_t top_dirichlet;    /* scalars at the top wall: 0 insulated, 1 Dirichlet */
+  int32_t interface_mode;   /* 0: per-cell b, fixed Q (Eq. 10 as printed);
+                               1: Fickian: one b per scalar, per-cell flux rate */
+  int32_t reserved;
   double nu;                /* kinematic viscosity; 3 nu = tau - 1/2 (Eq. 8) */
   double u_in_avg;          /* mean inlet velocity over the channel rows */
   double body_force_x;      /* uniform body force per unit mass (tests only) */
@@ -160,10 +167,14 @@ typedef struct {
   double dx_cm, dt_s, delta_cl_cm, c_tot, rho_cp_f;
 } orc_params;
 
-/* Per-cell material, lattice units. K = +inf marks clear fluid. */
+/* Per-cell material, lattice units. K = +inf marks clear fluid.  sigma is
+ * (rho c_p)_eff / (rho c_p)_f of Eq. 19 (NULL = 1): the reaction heat enters
+ * the temperature equation, whose diffusivity is k_eff/(rho c_p)_eff,
+ * divided by the same effective heat capacity. */
 typedef struct {
   const double *phi, *K, *alpha_T, *D_O2, *D_H2O;
   const double *u_imposed; /* optional [2][ny][nx]: freeze flow (tests) */
+  const double *sigma;     /* optional [ny][nx] heat-capacity ratio */
 } orc_material;
 
 /* Mask bits (one byte per cell). */
@@ -251,6 +262,39 @@ static double heat_per_O2(const orc_params *P, double T) {
 
 /* b of Eq. 10 for diffusivity alpha */
 double orc_b_of_alpha(double alpha) { return 20.0 * sqrt(3.0) * alpha - 4.0; }
+
+/* D2Q5 coefficients of one cell and scalar: the b of its equilibrium and
+ * the relaxation rate of the flux moments.  Eq. 10 as printed sets b from
+ * the cell's own diffusivity with the fixed rate 6/(3 + sqrt 3).  In the
+ * Fickian interface mode every cell takes the b of the largest diffusivity
+ * of that scalar (alpha_max) and the cell's diffusivity enters through the
+ * flux rate instead: alpha = c_s^2 (1/s_1 - 1/2), c_s^2 = (4 + b)/10. */
+typedef struct { double b, q1; } scalar_coef;
+static scalar_coef scalar_coefficients(const orc_params *P, double alpha, double alpha_max) {
+  scalar_coef r;
+  if (P->interface_mode == 1) {
+    r.b = orc_b_of_alpha(alpha_max);
+    double cs2 = (4.0 + r.b) / 10.0;
+    r.q1 = 1.0 / (alpha / cs2 + 0.5);
+  } else {
+    r.b = orc_b_of_alpha(alpha);
+    r.q1 = 6.0 / (3.0 + sqrt(3.0));
+  }
+  return r;
+}
+
+/* Largest diffusivity of each scalar over the fluid cells. */
+static void max_diffusivities(const orc_params *P, const orc_material *mat, const uint8_t *mask,
+                              double amax[3]) {
+  size_t n = (size_t)P->nx * P->ny;
+  amax[0] = amax[1] = amax[2] = 0.0;
+  for (size_t c = 0; c < n; ++c) {
+    if ((mask[c] & 3) == REG_SOLID) continue;
+    if (mat->alpha_T[c] > amax[0]) amax[0] = mat->alpha_T[c];
+    if (mat->D_O2[c] > amax[1]) amax[1] = mat->D_O2[c];
+    if (mat->D_H2O[c] > amax[2]) amax[2] = mat->D_H2O[c];
+  }
+}
 
 /* D2Q5 equilibrium populations N^-1 n_eq for value C, velocity u, b. */
 static void d2q5_equilibrium(double C, double ux, double uy, double b, double geq[5]) {
@@ -356,7 +400,8 @@ void orc_init(const orc_params *P, const orc_material *mat, const uint8_t *mask,
   ensure_inverses();
   int nx = P->nx, ny = P->ny;
   size_t n = (size_t)nx * ny;
-  double Cin[3] = {P->T_in, P->C_O2_in, P->C_H2O_in};
+  double Cin[3] = {P->T_in, P->C_O2_in, P->C_H2O_in}, amax[3];
+  max_diffusivities(P, mat, mask, amax);
   for (size_t c = 0; c < n; ++c) {
     if ((mask[c] & 3) == REG_SOLID) {
       for (int i = 0; i < 9; ++i) f[i * n + c] = 0;
@@ -367,7 +412,7 @@ void orc_init(const orc_params *P, const orc_material *mat, const uint8_t *mask,
     double alpha[3] = {mat->alpha_T[c], mat->D_O2[c], mat->D_H2O[c]};
     for (int s = 0; s < 3; ++s) {
       double geq[5];
-      d2q5_equilibrium(Cin[s], 0, 0, orc_b_of_alpha(alpha[s]), geq);
+      d2q5_equilibrium(Cin[s], 0, 0, scalar_coefficients(P, alpha[s], amax[s]).b, geq);
       for (int i = 0; i < 5; ++i) g[(s * 5 + i) * n + c] = geq[i];
     }
   }
@@ -410,7 +455,8 @@ static void stream(const orc_params *P, const orc_material *mat, const uint8_t *
   int nx = P->nx, ny = P->ny;
   size_t n = (size_t)nx * ny;
   double Cin[3] = {P->T_in, P->C_O2_in, P->C_H2O_in};
-  double Ctop[3] = {P->T_top, P->C_O2_top, P->C_H2O_top};
+  double Ctop[3] = {P->T_top, P->C_O2_top, P->C_H2O_top}, amax[3];
+  max_diffusivities(P, mat, mask, amax);
   for (int k = 0; k < D_NDIAG; ++k) diag[k] = 0;
   if (Jx) for (int x = 0; x < nx; ++x) Jx[x] = 0;
   if (qx) for (int x = 0; x < nx; ++x) qx[x] = 0;
@@ -431,8 +477,9 @@ static void stream(const orc_params *P, const orc_material *mat, const uint8_t *
         Cn[s] = 0;
         for (int i = 0; i < 5; ++i) Cn[s] += gs[(s * 5 + i) * n + c];
       }
-      double bcell[3] = {orc_b_of_alpha(mat->alpha_T[c]), orc_b_of_alpha(mat->D_O2[c]),
-                         orc_b_of_alpha(mat->D_H2O[c])};
+      double bcell[3] = {scalar_coefficients(P, mat->alpha_T[c], amax[0]).b,
+                         scalar_coefficients(P, mat->D_O2[c], amax[1]).b,
+                         scalar_coefficients(P, mat->D_H2O[c], amax[2]).b};
 
       /* ---- D2Q9 flow links */
       for (int i = 0; i < 9; ++i) {
@@ -482,7 +529,8 @@ static void stream(const orc_params *P, const orc_material *mat, const uint8_t *
       int volume = (P->reaction_mode == 1) && ((m & 3) == REG_CATALYST);
       if (surface) kS = k_surface(P, Cn[0]);
       if (volume) kV = k_volume(P, Cn[0]);
-      double hpo = (surface || volume) ? heat_per_O2(P, Cn[0]) : 0.0;
+      double hpo = (surface || volume) ? heat_per_O2(P, Cn[0]) : 0.0;   /* gas K per O2 */
+      double sig = mat->sigma ? mat->sigma[c] : 1.0;
 
       /* ---- D2Q5 scalar links */
       double Jsurf = 0;
@@ -542,19 +590,19 @@ static void stream(const orc_params *P, const orc_material *mat, const uint8_t *
         /* Eq. 12: two H2O per O2; Eq. 15: heat into the temperature link */
         int up = 2; /* the D2Q5 link arriving from below, e = (0, 1) */
         g[(2 * 5 + up) * n + c] += 2.0 * Jsurf;
-        g[(0 * 5 + up) * n + c] += hpo * Jsurf;
+        g[(0 * 5 + up) * n + c] += hpo / sig * Jsurf;
         diag[D_J] += Jsurf;
-        diag[D_HEAT] += hpo * Jsurf;
+        diag[D_HEAT] += hpo / sig * Jsurf;
         if (Jx) Jx[x] += Jsurf;
         if (qx) qx[x] += hpo * Jsurf;
       }
       if (volume) {
         double S = -kV * Cn[1] / (1.0 + kV);
-        src[0 * n + c] = -S * hpo;
+        src[0 * n + c] = -S * hpo / sig;
         src[1 * n + c] = S;
         src[2 * n + c] = -2.0 * S;
         diag[D_J] += -S;
-        diag[D_HEAT] += -S * hpo;
+        diag[D_HEAT] += -S * hpo / sig;
         if (Jx) Jx[x] += -S;
         if (qx) qx[x] += -S * hpo;
       }
@@ -604,9 +652,10 @@ void orc_step(const orc_params *P, const orc_material *mat, const uint8_t *mask,
   stream(P, mat, mask, fs, gs, f, g, src, dloc, Jx, qx);
   if (diag) memcpy(diag, dloc, sizeof dloc);
 
-  double tau = 3.0 * P->nu + 0.5, S[9], Q[5];
+  double tau = 3.0 * P->nu + 0.5, S[9], Q[5], amax[3];
   flow_S(tau, S);
   scalar_Q(Q);
+  max_diffusivities(P, mat, mask, amax);
 
 #pragma omp parallel for schedule(static)
   for (int y = 0; y < ny; ++y)
@@ -641,14 +690,15 @@ void orc_step(const orc_params *P, const orc_material *mat, const uint8_t *mask,
       /* Eq. 10 for T, O2, H2O */
       double alpha[3] = {mat->alpha_T[c], mat->D_O2[c], mat->D_H2O[c]};
       for (int s = 0; s < 3; ++s) {
-        double b = orc_b_of_alpha(alpha[s]);
+        scalar_coef sc = scalar_coefficients(P, alpha[s], amax[s]);
+        double b = sc.b, Qs[5] = {Q[0], sc.q1, sc.q1, Q[3], Q[4]};
         double C = mc.C[s];
         double nv[5], neq[5] = {C, mc.usx * C, mc.usy * C, b * C, 0.0}, ns[5];
         for (int k = 0; k < 5; ++k) {
           nv[k] = 0;
           for (int i = 0; i < 5; ++i) nv[k] += N5[k][i] * g[(s * 5 + i) * n + c];
         }
-        for (int k = 0; k < 5; ++k) ns[k] = nv[k] - Q[k] * (nv[k] - neq[k]);
+        for (int k = 0; k < 5; ++k) ns[k] = nv[k] - Qs[k] * (nv[k] - neq[k]);
         double wsrc[5] = {(1.0 - b) / 5.0, (4.0 + b) / 20.0, (4.0 + b) / 20.0,
                           (4.0 + b) / 20.0, (4.0 + b) / 20.0};
         for (int i = 0; i < 5; ++i) {

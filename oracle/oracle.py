@@ -39,6 +39,7 @@ class Params(C.Structure):
         ("nx", C.c_int32), ("ny", C.c_int32), ("ny_cl", C.c_int32), ("ny_gdl", C.c_int32),
         ("reaction_mode", C.c_int32), ("periodic_x", C.c_int32),
         ("forchheimer", C.c_int32), ("top_dirichlet", C.c_int32),
+        ("interface_mode", C.c_int32), ("reserved", C.c_int32),
         ("nu", C.c_double), ("u_in_avg", C.c_double), ("body_force_x", C.c_double),
         ("V_op", C.c_double), ("T_in", C.c_double), ("C_O2_in", C.c_double),
         ("C_H2O_in", C.c_double),
@@ -53,7 +54,7 @@ class Params(C.Structure):
 
 class Material(C.Structure):
     _fields_ = [(k, C.POINTER(C.c_double)) for k in
-                ("phi", "K", "alpha_T", "D_O2", "D_H2O", "u_imposed")]
+                ("phi", "K", "alpha_T", "D_O2", "D_H2O", "u_imposed", "sigma")]
 
 
 _P = C.POINTER
@@ -123,6 +124,9 @@ class Oracle:
         ui = material.get("u_imposed")
         if ui is not None:
             self._mat_arrays["u_imposed"] = np.ascontiguousarray(ui, np.float64)
+        if material.get("sigma") is not None:
+            self._mat_arrays["sigma"] = np.ascontiguousarray(
+                np.broadcast_to(np.asarray(material["sigma"], np.float64), (ny, nx)))
         self.M = Material(**{k: _ptr(v) for k, v in self._mat_arrays.items()})
         self.solid = None if solid is None else np.ascontiguousarray(solid, np.uint8)
         self.mask = np.zeros((ny, nx), np.uint8)

@@ -9,6 +9,8 @@ Paper constants come from the Nomenclature and Eqs. 13-19 of arXiv
     D_O2 = 5.2197e-2 cm^2/s: dt = D_lat dx^2 / D_O2;
   - D_H2O = 1.3 D_O2 (not in the paper); Prandtl number 0.7 in the gas;
   - (rho c_p)_s / (rho c_p)_f = 1500; k_s/k_f = 1.5/0.026 (Nomenclature);
+    the reaction heat enters the temperature equation divided by the
+    effective heat capacity of Eq. 19, like the conduction does;
   - catalyst film thickness 10 um; total gas concentration
     c_tot = C_O2,ref / 0.21 (C_O2,ref read as mol/cm^3);
     (rho c_p)_f = 29.3 J/(mol K) * c_tot;
@@ -57,7 +59,12 @@ def alpha_eff(phi, alpha_f, ks_over_kf=K_SOLID / K_FLUID, rc=RHOCP_RATIO):
     return alpha_f * (phi + (1.0 - phi) * ks_over_kf) / (phi + (1.0 - phi) * rc)
 
 
-def lattice_problem(case: dict, forchheimer: int = 1):
+def heat_capacity_ratio(phi, rc=RHOCP_RATIO):
+    """(rho c_p)_eff / (rho c_p)_f of Eq. 19."""
+    return phi + (1.0 - phi) * rc
+
+
+def lattice_problem(case: dict, forchheimer: int = 1, interface_mode: int = 0):
     """Physical workload dict -> (params dict, material dict, solid)."""
     nx, ny = case["nx"], case["ny"]
     ny_cl, ny_gdl = case["ny_cl"], case["ny_gdl"]
@@ -73,10 +80,12 @@ def lattice_problem(case: dict, forchheimer: int = 1):
         alpha_T=alpha_eff(phi, alpha_f),
         D_O2=bruggeman(phi, D_O2_LAT),
         D_H2O=bruggeman(phi, D_H2O_RATIO * D_O2_LAT),
+        sigma=heat_capacity_ratio(phi),
     )
     params = dict(
         nx=nx, ny=ny, ny_cl=ny_cl, ny_gdl=ny_gdl, reaction_mode=case["reaction_mode"],
         periodic_x=case.get("periodic_x", 0), forchheimer=forchheimer, top_dirichlet=0,
+        interface_mode=interface_mode,
         nu=NU_LAT, u_in_avg=case["Re"] * NU_LAT / h_ch, body_force_x=0.0,
         V_op=case["V_op"], T_in=case["T_in"], C_O2_in=case["C_O2_in"],
         C_H2O_in=case["C_H2O_in"], T_top=case["T_in"], C_O2_top=case["C_O2_in"],
@@ -91,7 +100,7 @@ def lattice_problem(case: dict, forchheimer: int = 1):
 def base_params(nx, ny, **kw):
     """Parameter dict for the closed-form tests (no reaction by default)."""
     p = dict(nx=nx, ny=ny, ny_cl=0, ny_gdl=0, reaction_mode=0, periodic_x=1, forchheimer=1,
-             top_dirichlet=0, nu=NU_LAT, u_in_avg=0.0, body_force_x=0.0, V_op=0.6,
+             top_dirichlet=0, interface_mode=0, nu=NU_LAT, u_in_avg=0.0, body_force_x=0.0, V_op=0.6,
              T_in=343.0, C_O2_in=0.21, C_H2O_in=0.0, T_top=343.0, C_O2_top=0.21,
              C_H2O_top=0.0, aj0_ref=0.0, T_ref_kin=T_REF_KIN, E_act=E_ACT, alpha_c=ALPHA_C,
              F=FARADAY, R=R_GAS, dU0dT=DU0_DT, U0_0=U0_0, x_ref=X_REF, dx_cm=1e-3,

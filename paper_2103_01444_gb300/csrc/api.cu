@@ -8,9 +8,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
-#include <map>
 #include <string>
-#include <tuple>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/pemlbm.h"
@@ -71,16 +70,22 @@ struct lbm_domain {
   void *pal = nullptr;
   MatRaw *raw = nullptr;
   int npal = 0;
-  double *snap = nullptr;      // residual snapshot [5][ny][nx]
-  double *partial = nullptr;   // residual block partials
-  int nres_blocks = 0;
+  std::vector<MatRaw> hraw;    // host copy of the palette's raw tuples
+  int ref_entry = 0;           // palette entry of the reference cell
+  void *snap = nullptr;        // residual snapshot [5][ny][nx], storage precision
+  double *partial = nullptr;   // residual block partials [blocks][10]
+  double *colsum = nullptr;    // catalyst column sums [2][nx]
+  int variant = 0;             // launch shape of the step kernel
+  double tuned_ms[kStepVariants] = {};
   double *dsmall = nullptr;    // device results (16 doubles)
   int *dbad = nullptr;
   double *hsmall = nullptr;    // pinned host mirror
   double *scratch = nullptr;   // [24][ny][nx] doubles, lazily allocated
   float *dprofile = nullptr;   // [nx]
-  // references of the deviation storage, fixed at reset
+  // references of the deviation storage: part of the state's representation,
+  // so they change only at reset (or with a loaded state)
   double Cref[3] = {0, 0, 0}, bref[3] = {0, 0, 0};
+  double bref_next[3] = {0, 0, 0};   // reference b the next reset will use
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
@@ -107,7 +112,6 @@ KArgs make_args(const lbm_domain *d) {
   a.body_g = p.body_force_x;
   a.u_in_avg = p.u_in_avg;
   a.h_ch = d->ny - a.y_ch0;
-  a.Q1 = 6.0 / (3.0 + std::sqrt(3.0));
   a.Q3 = 6.0 / (3.0 + 2.0 * std::sqrt(3.0));
   const double Cin[3] = {p.T_in, p.C_O2_in, p.C_H2O_in};
   const double Ctop[3] = {p.T_top, p.C_O2_top, p.C_H2O_top};
@@ -164,7 +168,7 @@ lbm_status launch_steps(lbm_domain *d, int64_t n) {
   for (int64_t k = 0; k < n; ++k) {
     dispatch(d->desc.precision, [&](auto *tag) {
       using S = std::remove_pointer_t<decltype(tag)>;
-      launch_step<S>(d->pop[d->cur], d->pop[d->cur ^ 1], g, a, d->stream);
+      launch_step<S>(d->pop[d->cur], d->pop[d->cur ^ 1], g, a, d->variant, d->stream);
     });
     d->cur ^= 1;
   }
@@ -192,6 +196,43 @@ lbm_status ensure_scratch(lbm_domain *d) {
   if (!d->scratch) CK(cudaMalloc(&d->scratch, sizeof(double) * 24 * (size_t)d->nx * d->ny));
   return LBM_OK;
 }
+
+// Derives the palette coefficients for the current parameters and the
+// deviation-storage reference b of each scalar.
+lbm_status prep_palette(lbm_domain *d) {
+  ScalarMode mode{};
+  mode.fickian = d->prm.interface_mode == 1;
+  for (const MatRaw &r : d->hraw)
+    for (int s = 0; s < 3; ++s) mode.alpha_max[s] = std::fmax(mode.alpha_max[s], r.alpha[s]);
+  launch_prep_palette(d->pal, d->raw, d->npal, d->prm.nu, d->prm.forchheimer, mode, fp64(d),
+                      d->stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(d->stream));
+  const MatRaw &r = d->hraw[d->ref_entry];
+  for (int s = 0; s < 3; ++s)
+    d->bref_next[s] = 20.0 * std::sqrt(3.0) * (mode.fickian ? mode.alpha_max[s] : r.alpha[s]) - 4.0;
+  return LBM_OK;
+}
+
+struct TupleHash {
+  size_t operator()(const MatRaw &r) const {
+    const double v[6] = {r.phi, r.K, r.alpha[0], r.alpha[1], r.alpha[2], r.sigma};
+    size_t h = 1469598103934665603ull;
+    for (double x : v) {
+      uint64_t b;
+      std::memcpy(&b, &x, 8);
+      h = (h ^ b) * 1099511628211ull;
+      h ^= h >> 29;
+    }
+    return h;
+  }
+};
+struct TupleEq {
+  bool operator()(const MatRaw &a, const MatRaw &b) const {
+    return a.phi == b.phi && a.K == b.K && a.alpha[0] == b.alpha[0] && a.alpha[1] == b.alpha[1] &&
+           a.alpha[2] == b.alpha[2] && a.sigma == b.sigma;
+  }
+};
 
 lbm_status check_ready(lbm_domain *d) {
   if (!d) return fail(LBM_EINVAL, "null domain");
@@ -241,16 +282,19 @@ lbm_status lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
       return cleanup(fail(LBM_ECUDA, "cudaStreamCreate failed"));
     d->own_stream = true;
   }
-  const size_t pop_bytes = 24 * (size_t)d->plane * d->esize;
+  // the step kernel loads every cell's interior pulls unconditionally; the
+  // guard after the last plane keeps the top row's upward pulls in bounds
+  const size_t pop_bytes = (24 * (size_t)d->plane + d->nxp + 64) * d->esize;
   const size_t cells = (size_t)d->plane;
   const size_t coef = fp64(d) ? sizeof(MatCoef<double>) : sizeof(MatCoef<float>);
-  d->nres_blocks = 4 * 152;
+  const size_t rsize = fp64(d) ? 8 : 4;
   if (cudaMalloc(&d->pop[0], pop_bytes) != cudaSuccess || cudaMalloc(&d->pop[1], pop_bytes) != cudaSuccess ||
       cudaMalloc(&d->mask, cells) != cudaSuccess || cudaMalloc(&d->mid, cells * 2) != cudaSuccess ||
       cudaMalloc(&d->pal, coef * kMaxPalette) != cudaSuccess ||
       cudaMalloc(&d->raw, sizeof(MatRaw) * kMaxPalette) != cudaSuccess ||
-      cudaMalloc(&d->snap, sizeof(double) * 5 * (size_t)D.nx * D.ny) != cudaSuccess ||
-      cudaMalloc(&d->partial, sizeof(double) * 10 * d->nres_blocks) != cudaSuccess ||
+      cudaMalloc(&d->snap, rsize * 5 * (size_t)D.nx * D.ny) != cudaSuccess ||
+      cudaMalloc(&d->partial, sizeof(double) * 10 * residual_blocks(D.nx, D.ny)) != cudaSuccess ||
+      cudaMalloc(&d->colsum, sizeof(double) * 2 * D.nx) != cudaSuccess ||
       cudaMalloc(&d->dsmall, sizeof(double) * 16) != cudaSuccess || cudaMalloc(&d->dbad, sizeof(int)) != cudaSuccess ||
       cudaMalloc(&d->dprofile, sizeof(float) * D.nx) != cudaSuccess ||
       cudaMallocHost(&d->hsmall, sizeof(double) * 16) != cudaSuccess) {
@@ -265,6 +309,8 @@ lbm_status lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
     cudaMemcpyAsync(dsolid, D.solid, (size_t)D.nx * D.ny, cudaMemcpyHostToDevice, d->stream);
   }
   cudaMemsetAsync(d->mid, 0, cells * 2, d->stream);
+  cudaMemsetAsync(d->pop[0], 0, pop_bytes, d->stream);
+  cudaMemsetAsync(d->pop[1], 0, pop_bytes, d->stream);
   launch_build_mask(d->mask, dsolid, D.nx, D.ny, d->nxp, D.ny_cl, D.ny_gdl, D.reaction_mode,
                     D.periodic_x, d->stream);
   cudaError_t e = cudaStreamSynchronize(d->stream);
@@ -279,7 +325,7 @@ lbm_status lbm_destroy_domain(lbm_domain *d) {
   if (d->stream) cudaStreamSynchronize(d->stream);
   drop_graphs(d);
   for (void *p : {d->pop[0], d->pop[1], (void *)d->mask, (void *)d->mid, d->pal, (void *)d->raw,
-                  (void *)d->snap, (void *)d->partial, (void *)d->dsmall, (void *)d->dbad,
+                  d->snap, (void *)d->partial, (void *)d->colsum, (void *)d->dsmall, (void *)d->dbad,
                   (void *)d->scratch, (void *)d->dprofile})
     if (p) cudaFree(p);
   if (d->hsmall) cudaFreeHost(d->hsmall);
@@ -298,14 +344,19 @@ lbm_status lbm_set_params(lbm_domain *d, const lbm_params *p) {
   if (!(p->T_in > 0) || !(p->dx_cm > 0) || !(p->dt_s > 0) || !(p->c_tot > 0) || !(p->rho_cp_f > 0) ||
       !(p->x_ref > 0) || !(p->R > 0) || !(p->F > 0) || !(p->T_ref_kin > 0) || !(p->aj0_ref >= 0))
     return fail(LBM_EINVAL, "non-positive physical constant");
+  if (p->interface_mode != 0 && p->interface_mode != 1) return fail(LBM_EINVAL, "interface_mode must be 0 or 1");
+  if (p->reserved != 0) return fail(LBM_EINVAL, "reserved must be 0");
+  const bool reprep = d->have_fields && (p->nu != d->prm.nu || p->forchheimer != d->prm.forchheimer ||
+                                         p->interface_mode != d->prm.interface_mode);
   d->prm = *p;
   d->have_params = true;
   drop_graphs(d);
+  if (reprep) return prep_palette(d);
   return LBM_OK;
 }
 
 lbm_status lbm_set_fields(lbm_domain *d, const double *phi, const double *K, const double *alpha_T,
-                          const double *D_O2, const double *D_H2O) {
+                          const double *D_O2, const double *D_H2O, const double *rho_cp_ratio) {
   if (!d || !phi || !K || !alpha_T || !D_O2 || !D_H2O) return fail(LBM_EINVAL, "null argument");
   if (!d->have_params) return fail(LBM_ESTATE, "call lbm_set_params before lbm_set_fields");
   const int nx = d->nx, ny = d->ny;
@@ -313,29 +364,39 @@ lbm_status lbm_set_fields(lbm_domain *d, const double *phi, const double *K, con
   CK(cudaMemcpyAsync(mask.data(), d->mask, mask.size(), cudaMemcpyDeviceToHost, d->stream));
   CK(cudaStreamSynchronize(d->stream));
   const double amax = 5.0 / (20.0 * std::sqrt(3.0));
-  std::map<std::tuple<double, double, double, double, double>, int> index;
+  std::unordered_map<MatRaw, int, TupleHash, TupleEq> index;
   std::vector<MatRaw> raw;
   std::vector<uint16_t> mid((size_t)d->plane, 0);
+  MatRaw prev{};
+  int prev_k = -1;
   for (int y = 0; y < ny; ++y)
     for (int x = 0; x < nx; ++x) {
       const size_t o = (size_t)y * nx + x;
       if ((mask[(size_t)y * d->nxp + x] & REG_MASK) == REG_SOLID) continue;
-      const double f[5] = {phi[o], K[o], alpha_T[o], D_O2[o], D_H2O[o]};
-      if (!(f[0] > 0 && f[0] <= 1)) return fail(LBM_EINVAL, "porosity %g at (%d,%d) outside (0,1]", f[0], x, y);
-      if (!(f[1] > 0)) return fail(LBM_EINVAL, "permeability %g at (%d,%d) must be > 0", f[1], x, y);
-      for (int s = 2; s < 5; ++s)
-        if (!(f[s] > 0 && f[s] <= amax))
-          return fail(LBM_EINVAL, "diffusivity %g at (%d,%d) outside (0, %g]", f[s], x, y, amax);
-      auto key = std::make_tuple(f[0], f[1], f[2], f[3], f[4]);
-      auto it = index.find(key);
+      const MatRaw t{phi[o], K[o], {alpha_T[o], D_O2[o], D_H2O[o]},
+                     rho_cp_ratio ? rho_cp_ratio[o] : 1.0};
       int k;
-      if (it == index.end()) {
-        k = (int)raw.size();
-        if (k >= kMaxPalette) return fail(LBM_EINVAL, "more than %d distinct materials", kMaxPalette);
-        index.emplace(key, k);
-        raw.push_back(MatRaw{f[0], f[1], {f[2], f[3], f[4]}});
+      if (prev_k >= 0 && TupleEq()(t, prev)) {
+        k = prev_k;   // same material as the previous cell: the common case
       } else {
-        k = it->second;
+        if (!(t.phi > 0 && t.phi <= 1)) return fail(LBM_EINVAL, "porosity %g at (%d,%d) outside (0,1]", t.phi, x, y);
+        if (!(t.K > 0)) return fail(LBM_EINVAL, "permeability %g at (%d,%d) must be > 0", t.K, x, y);
+        if (!(t.sigma >= 1e-6) || std::isinf(t.sigma))
+          return fail(LBM_EINVAL, "heat-capacity ratio %g at (%d,%d) must be finite and >= 1e-6", t.sigma, x, y);
+        for (int s = 0; s < 3; ++s)
+          if (!(t.alpha[s] > 0 && t.alpha[s] <= amax))
+            return fail(LBM_EINVAL, "diffusivity %g at (%d,%d) outside (0, %g]", t.alpha[s], x, y, amax);
+        auto it = index.find(t);
+        if (it == index.end()) {
+          k = (int)raw.size();
+          if (k >= kMaxPalette) return fail(LBM_EINVAL, "more than %d distinct materials", kMaxPalette);
+          index.emplace(t, k);
+          raw.push_back(t);
+        } else {
+          k = it->second;
+        }
+        prev = t;
+        prev_k = k;
       }
       mid[(size_t)y * d->nxp + x] = (uint16_t)k;
     }
@@ -343,17 +404,18 @@ lbm_status lbm_set_fields(lbm_domain *d, const double *phi, const double *K, con
   // cells that carry no material (solids, padding) point at entry 0
   CK(cudaMemcpyAsync(d->raw, raw.data(), sizeof(MatRaw) * raw.size(), cudaMemcpyHostToDevice, d->stream));
   CK(cudaMemcpyAsync(d->mid, mid.data(), mid.size() * 2, cudaMemcpyHostToDevice, d->stream));
-  launch_prep_palette(d->pal, d->raw, (int)raw.size(), d->prm.nu, d->prm.forchheimer, fp64(d), d->stream);
-  CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(d->stream));
   d->npal = (int)raw.size();
-  // reference b per scalar: the material of the first open inlet cell (the
-  // channel gas), else of the first fluid cell
-  int ref = -1;
-  for (int y = ny - 1; y >= 0 && ref < 0; --y)
-    if ((mask[(size_t)y * d->nxp] & REG_MASK) != REG_SOLID) ref = mid[(size_t)y * d->nxp];
-  const MatRaw &r = raw[ref < 0 ? 0 : ref];
-  for (int s = 0; s < 3; ++s) d->bref[s] = 20.0 * std::sqrt(3.0) * r.alpha[s] - 4.0;
+  // reference material of the deviation storage: the top fluid cell of the
+  // inlet column (the channel gas), else entry 0
+  d->ref_entry = 0;
+  for (int y = ny - 1; y >= 0; --y)
+    if ((mask[(size_t)y * d->nxp] & REG_MASK) != REG_SOLID) {
+      d->ref_entry = mid[(size_t)y * d->nxp];
+      break;
+    }
+  d->hraw = std::move(raw);
+  lbm_status st = prep_palette(d);
+  if (st != LBM_OK) return st;
   d->have_fields = true;
   drop_graphs(d);
   return LBM_OK;
@@ -365,6 +427,7 @@ lbm_status lbm_reset(lbm_domain *d) {
   d->Cref[0] = d->prm.T_in;
   d->Cref[1] = d->prm.C_O2_in;
   d->Cref[2] = d->prm.C_H2O_in;
+  for (int s = 0; s < 3; ++s) d->bref[s] = d->bref_next[s];
   const KArgs a = make_args(d);
   const DevGeom g = geom(d);
   dispatch(d->desc.precision, [&](auto *tag) {
@@ -377,9 +440,11 @@ lbm_status lbm_reset(lbm_domain *d) {
   d->steps = 0;
   d->have_state = true;
   drop_graphs(d);
+  // first residual snapshot: compare against zeros, keep only the snapshot
+  CK(cudaMemsetAsync(d->snap, 0, (fp64(d) ? 8 : 4) * 5 * (size_t)d->nx * d->ny, d->stream));
   double r;
-  lbm_status s = lbm_residual(d, &r);   // takes the first snapshot
-  if (s != LBM_OK) return s;
+  lbm_status s = lbm_residual(d, &r);
+  if (s != LBM_OK && s != LBM_EDIVERGED) return s;
   return LBM_OK;
 }
 
@@ -423,7 +488,7 @@ lbm_status lbm_current_density(lbm_domain *d, double *i_avg, double *heat, float
   dispatch(d->desc.precision, [&](auto *tag) {
     using S = std::remove_pointer_t<decltype(tag)>;
     launch_catalyst<S>(d->pop[d->cur ^ 1], geom(d), a, i_scale, profile ? d->dprofile : nullptr,
-                       d->dsmall, d->stream);
+                       d->colsum, d->dsmall, d->stream);
   });
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(d->hsmall, d->dsmall, 2 * sizeof(double), cudaMemcpyDeviceToHost, d->stream));
@@ -441,8 +506,8 @@ lbm_status lbm_residual(lbm_domain *d, double *res) {
   CK(cudaMemsetAsync(d->dbad, 0, sizeof(int), d->stream));
   dispatch(d->desc.precision, [&](auto *tag) {
     using S = std::remove_pointer_t<decltype(tag)>;
-    launch_residual<S>(d->pop[d->cur], geom(d), a, d->snap, d->partial, d->nres_blocks, d->dbad,
-                       d->dsmall, d->stream);
+    launch_residual<S>(d->pop[d->cur], geom(d), a, d->snap, d->partial, d->dbad, d->dsmall,
+                       d->stream);
   });
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(d->hsmall, d->dsmall, 10 * sizeof(double), cudaMemcpyDeviceToHost, d->stream));
@@ -540,7 +605,7 @@ lbm_status lbm_save_state(lbm_domain *d, void *buf, size_t *bytes) {
   lbm_status s = check_ready(d);
   if (s != LBM_OK) return s;
   if (!bytes) return fail(LBM_EINVAL, "null argument");
-  const size_t pop_bytes = 24 * (size_t)d->plane * d->esize;
+  const size_t pop_bytes = 24 * (size_t)d->plane * d->esize;   // the guard is not state
   const size_t need = sizeof(StateHeader) + 2 * pop_bytes;
   if (!buf) {
     *bytes = need;
@@ -578,6 +643,55 @@ lbm_status lbm_load_state(lbm_domain *d, const void *buf, size_t bytes) {
   for (int k = 0; k < 3; ++k) { d->Cref[k] = h.Cref[k]; d->bref[k] = h.bref[k]; }
   d->have_state = true;
   drop_graphs(d);
+  return LBM_OK;
+}
+
+lbm_status lbm_set_variant(lbm_domain *d, int32_t variant) {
+  if (!d) return fail(LBM_EINVAL, "null domain");
+  if (variant < 0 || variant >= kStepVariants) return fail(LBM_EINVAL, "variant %d outside [0, %d)", variant, kStepVariants);
+  d->variant = variant;
+  drop_graphs(d);
+  return LBM_OK;
+}
+
+lbm_status lbm_tune(lbm_domain *d, int32_t trial_steps, int32_t *variant, double *best_ms) {
+  lbm_status s = check_ready(d);
+  if (s != LBM_OK) return s;
+  if (d->steps != 0) return fail(LBM_ESTATE, "lbm_tune runs between lbm_reset and the first step");
+  if (trial_steps < 1) return fail(LBM_EINVAL, "trial_steps < 1");
+  const KArgs a = make_args(d);
+  const DevGeom g = geom(d);
+  int best = 0;
+  for (int v = 0; v < kStepVariants; ++v) {
+    auto run = [&](int n) {
+      for (int k = 0; k < n; ++k)
+        dispatch(d->desc.precision, [&](auto *tag) {
+          using S = std::remove_pointer_t<decltype(tag)>;
+          // the same step from the same state every time: the state is kept
+          launch_step<S>(d->pop[d->cur], d->pop[d->cur ^ 1], g, a, v, d->stream);
+        });
+    };
+    run(2);
+    CK(cudaEventRecord(d->ev0, d->stream));
+    run(trial_steps);
+    CK(cudaEventRecord(d->ev1, d->stream));
+    CK(cudaEventSynchronize(d->ev1));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, d->ev0, d->ev1));
+    d->tuned_ms[v] = ms / trial_steps;
+    if (d->tuned_ms[v] < d->tuned_ms[best]) best = v;
+  }
+  // the trials wrote the next state into the other buffer: restore it
+  dispatch(d->desc.precision, [&](auto *tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    launch_init<S>(d->pop[d->cur ^ 1], g, a, d->stream);
+  });
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(d->stream));
+  d->variant = best;
+  drop_graphs(d);
+  if (variant) *variant = best;
+  if (best_ms) *best_ms = d->tuned_ms[best];
   return LBM_OK;
 }
 

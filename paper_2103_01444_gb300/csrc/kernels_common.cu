@@ -47,10 +47,13 @@ void launch_build_mask(uint8_t *mask, const uint8_t *solid, int nx, int ny, int 
 }
 
 // Per-material coefficients: Darcy and Forchheimer terms of Eq. 7, the l0,
-// l1 of Eq. 8 (dt = 1), and b = 20 sqrt(3) alpha - 4 of Eq. 10 per scalar.
+// l1 of Eq. 8 (dt = 1), and per scalar the b of Eq. 10 with the flux-moment
+// rate.  As printed, b = 20 sqrt(3) alpha - 4 with the fixed rate
+// 6/(3 + sqrt 3); in the Fickian mode b is that of the scalar's largest
+// diffusivity and alpha = c_s^2 (1/q1 - 1/2) sets q1, c_s^2 = (4 + b)/10.
 template <typename R>
 __global__ void k_prep_palette(MatCoef<R> *__restrict__ pal, const MatRaw *__restrict__ raw,
-                               int npal, double nu, int forchheimer) {
+                               int npal, double nu, int forchheimer, ScalarMode mode) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= npal) return;
   const MatRaw r = raw[k];
@@ -67,22 +70,33 @@ __global__ void k_prep_palette(MatCoef<R> *__restrict__ pal, const MatRaw *__res
   c.forch = R(forch);
   c.l0 = R(0.5 + 0.25 * darcy);
   c.l1 = R(0.5 * forch);
+  const double sqrt3 = sqrt(3.0);
   for (int s = 0; s < 3; ++s) {
-    const double b = 20.0 * sqrt(3.0) * r.alpha[s] - 4.0;
+    double b, q1;
+    if (mode.fickian) {
+      b = 20.0 * sqrt3 * mode.alpha_max[s] - 4.0;
+      q1 = 1.0 / (r.alpha[s] * 10.0 / (4.0 + b) + 0.5);
+    } else {
+      b = 20.0 * sqrt3 * r.alpha[s] - 4.0;
+      q1 = 6.0 / (3.0 + sqrt3);
+    }
     c.b[s] = R(b);
     c.w1[s] = R((4.0 + b) / 20.0);
+    c.q1[s] = R(q1);
   }
-  for (int s = 0; s < 4; ++s) c.pad[s] = R(0);
+  c.inv_sigma = R(1.0 / r.sigma);
   pal[k] = c;
 }
 
 void launch_prep_palette(void *pal, const MatRaw *raw, int npal, double nu, int forchheimer,
-                         bool fp64, cudaStream_t st) {
+                         const ScalarMode &mode, bool fp64, cudaStream_t st) {
   const int nb = (npal + 127) / 128;
   if (fp64)
-    k_prep_palette<double><<<nb, 128, 0, st>>>((MatCoef<double> *)pal, raw, npal, nu, forchheimer);
+    k_prep_palette<double><<<nb, 128, 0, st>>>((MatCoef<double> *)pal, raw, npal, nu, forchheimer,
+                                                mode);
   else
-    k_prep_palette<float><<<nb, 128, 0, st>>>((MatCoef<float> *)pal, raw, npal, nu, forchheimer);
+    k_prep_palette<float><<<nb, 128, 0, st>>>((MatCoef<float> *)pal, raw, npal, nu, forchheimer,
+                                               mode);
 }
 
 __global__ void __launch_bounds__(kReduceThreads)
@@ -95,6 +109,21 @@ k_sum_partials(const double *__restrict__ partial, int nblocks, double *__restri
   block_sum<10>(acc, sm);
   if (threadIdx.x == 0)
     for (int k = 0; k < 10; ++k) out[k] = acc[k];
+}
+
+__global__ void __launch_bounds__(kReduceThreads)
+k_sum_columns(const double *__restrict__ colsum, int nx, double *__restrict__ out) {
+  __shared__ double sm[2 * 32];
+  double acc[2] = {0.0, 0.0};
+  for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+    acc[0] += colsum[x];
+    acc[1] += colsum[nx + x];
+  }
+  block_sum<2>(acc, sm);
+  if (threadIdx.x == 0) {
+    out[0] = acc[0];
+    out[1] = acc[1];
+  }
 }
 
 }  // namespace pemlbm

@@ -53,11 +53,15 @@ template <typename R> struct alignas(16 * sizeof(R) >= 64 ? 64 : 16) MatCoef {
   R l0, l1;         // Eq. 8
   R b[3];           // b of Eq. 10 for T, O2, H2O
   R w1[3];          // (4 + b)/20: D2Q5 equilibrium weight of the moving links
-  R pad[4];
+  R q1[3];          // relaxation rate of the D2Q5 flux moments
+  R inv_sigma;      // (rho c_p)_f / (rho c_p)_eff: scales the reaction heat
 };
 
 // Raw material tuple as given by the caller (lattice units).
-struct MatRaw { double phi, K, alpha[3]; };
+struct MatRaw { double phi, K, alpha[3], sigma; };
+
+// How each scalar's diffusivity enters Eq. 10 (see lbm_params.interface_mode).
+struct ScalarMode { int fickian; double alpha_max[3]; };
 
 // Launch-invariant arguments (passed by value: constant bank).
 struct KArgs {
@@ -69,7 +73,7 @@ struct KArgs {
   double s_nu, s_q;         // 1/tau and the q-moment rate of Sec. 2.1
   double body_g;            // body force per unit mass along x
   double u_in_avg, h_ch;    // inlet parabola
-  double Q1, Q3;            // Eq. 10 rates of the flux and energy moments
+  double Q3;                // Eq. 10 rate of the energy moments
   double Cref[3], wr0[3], wr1[3], bref[3];  // deviation references
   double Cin[3], Ctop[3];
   // kinetics: k(T) = A exp(e_in - c1 (T - T_in)/(T T_in)), Eq. 13, 14, 16, 17
@@ -107,64 +111,81 @@ template <typename R> __device__ __forceinline__ R inlet_u(const KArgs &a, R yh)
 }
 
 // ------------------------------------------------------------------ pull
-// Flow link i into cell (x, y) whose source lies outside the plain fluid.
+// Every cell first loads its 24 interior pulls unconditionally (the
+// allocation carries a guard after the last plane, so the addresses of
+// edge cells stay inside it); links whose source lies outside the plain
+// fluid are then replaced below.  Issuing the loads before the node mask
+// arrives keeps one DRAM latency off the critical path.
+
+// Flow link i into cell (x, y) whose source may lie outside the fluid;
+// `v` is the interior pull already loaded for this link.
 template <typename S, typename R>
 __device__ R pull_flow_edge(const Pops<S> &src, const KArgs &a, const uint8_t *__restrict__ mask,
                             const uint16_t *__restrict__ mid, const MatCoef<R> *__restrict__ pal,
-                            int i, int x, int y, uint8_t m) {
+                            int i, int x, int y, uint8_t m, R v) {
   const int EX[9] = EX9_TAB, EY[9] = EY9_TAB, OP[9] = OP9_TAB;
   int sx = x - EX[i], sy = y - EY[i];
   if (sy < 0 || sy >= a.ny) return R(src.at(OP[i], x, y));            // wall
-  if (a.periodic) {
-    sx = sx < 0 ? sx + a.nx : (sx >= a.nx ? sx - a.nx : sx);
-  } else if (sx < 0) {                                                // inlet
-    R v = R(src.at(OP[i], x, y));
-    if (m & M_INLET) v += R(6) * w9<R>(i) * R(EX[i]) * inlet_u<R>(a, R(y) - R(0.5) * R(EY[i]));
-    return v;
-  } else if (sx >= a.nx) {                                            // outlet
-    const int vx = a.nx - 1;
-    R d[9];
+  if (sx < 0 || sx >= a.nx) {
+    if (a.periodic) {
+      sx = sx < 0 ? sx + a.nx : sx - a.nx;
+    } else if (sx < 0) {                                              // inlet
+      R w = R(src.at(OP[i], x, y));
+      if (m & M_INLET) w += R(6) * w9<R>(i) * R(EX[i]) * inlet_u<R>(a, R(y) - R(0.5) * R(EY[i]));
+      return w;
+    } else {                                                          // outlet
+      const int vx = a.nx - 1;
+      R d[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) d[k] = R(src.at(k, vx, sy));
-    R jx = d[1] - d[3] + d[5] - d[6] - d[7] + d[8];
-    R jy = d[2] - d[4] + d[5] + d[6] - d[7] - d[8];
-    R s18 = d[1] + d[2] + d[3] + d[4] + d[5] + d[6] + d[7] + d[8];
-    R inv_phi = pal[mid[(long long)sy * a.nxp + vx]].inv_phi;
-    R dP = R(-0.6) * s18 + R(0.4) * (jx * jx + jy * jy) * inv_phi;   // 1/3 - phi p*
-    return d[i] + lam9<R>(i) * dP;
+      for (int k = 0; k < 9; ++k) d[k] = R(src.at(k, vx, sy));
+      R jx = d[1] - d[3] + d[5] - d[6] - d[7] + d[8];
+      R jy = d[2] - d[4] + d[5] + d[6] - d[7] - d[8];
+      R s18 = ((d[1] + d[3]) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8]));
+      R inv_phi = pal[mid[(long long)sy * a.nxp + vx]].inv_phi;
+      R dP = R(-0.6) * s18 + R(0.4) * (jx * jx + jy * jy) * inv_phi;  // 1/3 - phi p*
+      return d[i] + lam9<R>(i) * dP;
+    }
+    if ((m & M_NEAR_SOLID) && (mask[(long long)sy * a.nxp + sx] & REG_MASK) == REG_SOLID)
+      return R(src.at(OP[i], x, y));
+    return R(src.at(i, sx, sy));                                      // periodic wrap
   }
   if ((m & M_NEAR_SOLID) && (mask[(long long)sy * a.nxp + sx] & REG_MASK) == REG_SOLID)
     return R(src.at(OP[i], x, y));                                    // solid grain
-  return R(src.at(i, sx, sy));
+  return v;
 }
 
-// Scalar link i of scalar s into cell (x, y) whose source is outside.  The
-// bottom wall returns the insulated value; the reaction is applied after.
+// Scalar link i of scalar s into cell (x, y); the bottom wall returns the
+// insulated value and the reaction is applied afterwards.
 template <typename S, typename R>
 __device__ R pull_scalar_edge(const Pops<S> &src, const KArgs &a, const uint8_t *__restrict__ mask,
-                              const MatCoef<R> &mc, int s, int i, int x, int y, uint8_t m) {
+                              const MatCoef<R> &mc, int s, int i, int x, int y, uint8_t m, R v) {
   const int EX[5] = {0, 1, 0, -1, 0}, EY[5] = {0, 0, 1, 0, -1}, OP[5] = {0, 3, 4, 1, 2};
   const int q = 9 + 5 * s;
   int sx = x - EX[i], sy = y - EY[i];
   if (sy < 0) return R(src.at(q + OP[i], x, y));
   if (sy >= a.ny) {
-    R v = R(src.at(q + OP[i], x, y));
+    R w = R(src.at(q + OP[i], x, y));
     if (a.top_dirichlet)
-      v = -v + R(2) * mc.w1[s] * R(a.Ctop[s]) - R(2) * R(a.wr1[s]) * R(a.Cref[s]);
-    return v;
+      w = -w + R(2) * mc.w1[s] * R(a.Ctop[s]) - R(2) * R(a.wr1[s]) * R(a.Cref[s]);
+    return w;
   }
-  if (a.periodic) {
-    sx = sx < 0 ? sx + a.nx : (sx >= a.nx ? sx - a.nx : sx);
-  } else if (sx < 0) {
-    R v = R(src.at(q + OP[i], x, y));
-    if (m & M_INLET) v = -v + R(2) * mc.w1[s] * R(a.Cin[s]) - R(2) * R(a.wr1[s]) * R(a.Cref[s]);
-    return v;
-  } else if (sx >= a.nx) {
-    return R(src.at(q + i, a.nx - 1, y));                             // fully developed
+  if (sx < 0 || sx >= a.nx) {
+    if (a.periodic) {
+      sx = sx < 0 ? sx + a.nx : sx - a.nx;
+    } else if (sx < 0) {
+      R w = R(src.at(q + OP[i], x, y));
+      if (m & M_INLET) w = -w + R(2) * mc.w1[s] * R(a.Cin[s]) - R(2) * R(a.wr1[s]) * R(a.Cref[s]);
+      return w;
+    } else {
+      return R(src.at(q + i, a.nx - 1, y));                           // fully developed
+    }
+    if ((m & M_NEAR_SOLID) && (mask[(long long)sy * a.nxp + sx] & REG_MASK) == REG_SOLID)
+      return R(src.at(q + OP[i], x, y));
+    return R(src.at(q + i, sx, sy));
   }
   if ((m & M_NEAR_SOLID) && (mask[(long long)sy * a.nxp + sx] & REG_MASK) == REG_SOLID)
     return R(src.at(q + OP[i], x, y));
-  return R(src.at(q + i, sx, sy));
+  return v;
 }
 
 // The 24 post-stream deviations of one cell.
@@ -181,12 +202,18 @@ template <typename R> __device__ __forceinline__ R rate(const KArgs &a, R A, R t
 }
 
 // Sum of the cell's own post-collision deviations of scalar s.
+// Opposite links are summed first: their large advective parts cancel
+// exactly in FP32 (Sterbenz), so the small sum keeps full precision.
+template <typename R>
+__device__ __forceinline__ R d2q5_sum(R d0, R d1, R d2, R d3, R d4) {
+  return d0 + ((d1 + d3) + (d2 + d4));
+}
+
 template <typename S, typename R>
 __device__ __forceinline__ R own_sum(const Pops<S> &src, int s, int x, int y) {
-  R t = 0;
-#pragma unroll
-  for (int k = 0; k < 5; ++k) t += R(src.at(9 + 5 * s + k, x, y));
-  return t;
+  const int q = 9 + 5 * s;
+  return d2q5_sum<R>(R(src.at(q, x, y)), R(src.at(q + 1, x, y)), R(src.at(q + 2, x, y)),
+                     R(src.at(q + 3, x, y)), R(src.at(q + 4, x, y)));
 }
 
 // Surface reaction of the thin film at a bottom cell (Sec. 4): the implicit
@@ -201,7 +228,7 @@ __device__ __forceinline__ R surface_reaction(const Pops<S> &src, const KArgs &a
   R gdown = c.g[1][2] + R(a.wr1[1]) * R(a.Cref[1]);   // full g*_4 of O2 (bounced)
   R J = gdown * (R(2) * kappa) / (R(1) + kappa);
   c.g[1][2] -= J;
-  c.g[0][2] += R(a.hpo) * J;
+  c.g[0][2] += R(a.hpo) * mc.inv_sigma * J;
   c.g[2][2] += R(2) * J;
   return J;
 }
@@ -215,7 +242,52 @@ __device__ __forceinline__ R volume_sink(const Pops<S> &src, const KArgs &a, int
   return -k * C / (R(1) + k);
 }
 
-// Pull all 24 populations of cell (x, y).  Returns false for solid cells.
+// The 24 interior pulls of cell (x, y), issued without looking at the mask.
+template <typename S, typename R>
+__device__ __forceinline__ void load_interior(const Pops<S> &src, const KArgs &a, int x, int y,
+                                              Cell<R> &c) {
+  const long long base = (long long)y * a.nxp + x, P = a.plane, W = a.nxp;
+  const S *p = src.p + base;
+  c.f[0] = ld_r(p);
+  c.f[1] = ld_r(p + 1 * P - 1);
+  c.f[2] = ld_r(p + 2 * P - W);
+  c.f[3] = ld_r(p + 3 * P + 1);
+  c.f[4] = ld_r(p + 4 * P + W);
+  c.f[5] = ld_r(p + 5 * P - W - 1);
+  c.f[6] = ld_r(p + 6 * P - W + 1);
+  c.f[7] = ld_r(p + 7 * P + W + 1);
+  c.f[8] = ld_r(p + 8 * P + W - 1);
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const S *q = p + (9 + 5 * s) * P;
+    c.g[s][0] = ld_r(q);
+    c.g[s][1] = ld_r(q + 1 * P - 1);
+    c.g[s][2] = ld_r(q + 2 * P - W);
+    c.g[s][3] = ld_r(q + 3 * P + 1);
+    c.g[s][4] = ld_r(q + 4 * P + W);
+  }
+}
+
+// Replaces the pulls of links that cross a wall, the inlet, the outlet, a
+// periodic seam or a solid grain (cells with any edge bit only).
+template <typename S, typename R>
+__device__ __forceinline__ void fix_edges(const Pops<S> &src, const KArgs &a,
+                                          const uint8_t *__restrict__ mask,
+                                          const uint16_t *__restrict__ mid,
+                                          const MatCoef<R> *__restrict__ pal,
+                                          const MatCoef<R> &mc, int x, int y, uint8_t m,
+                                          Cell<R> &c) {
+#pragma unroll
+  for (int i = 1; i < 9; ++i)
+    c.f[i] = pull_flow_edge<S, R>(src, a, mask, mid, pal, i, x, y, m, c.f[i]);
+#pragma unroll
+  for (int s = 0; s < 3; ++s)
+#pragma unroll
+    for (int i = 1; i < 5; ++i)
+      c.g[s][i] = pull_scalar_edge<S, R>(src, a, mask, mc, s, i, x, y, m, c.g[s][i]);
+}
+
+// Pull all 24 populations of a non-solid cell (x, y).
 template <typename S, typename R>
 __device__ __forceinline__ void pull_cell(const Pops<S> &src, const KArgs &a,
                                           const uint8_t *__restrict__ mask,
@@ -223,35 +295,8 @@ __device__ __forceinline__ void pull_cell(const Pops<S> &src, const KArgs &a,
                                           const MatCoef<R> *__restrict__ pal,
                                           const MatCoef<R> &mc, int x, int y, uint8_t m,
                                           Cell<R> &c) {
-  if (!(m & M_EDGE)) {
-    const long long base = (long long)y * a.nxp + x, P = a.plane, W = a.nxp;
-    const S *p = src.p + base;
-    c.f[0] = ld_r(p);
-    c.f[1] = ld_r(p + 1 * P - 1);
-    c.f[2] = ld_r(p + 2 * P - W);
-    c.f[3] = ld_r(p + 3 * P + 1);
-    c.f[4] = ld_r(p + 4 * P + W);
-    c.f[5] = ld_r(p + 5 * P - W - 1);
-    c.f[6] = ld_r(p + 6 * P - W + 1);
-    c.f[7] = ld_r(p + 7 * P + W + 1);
-    c.f[8] = ld_r(p + 8 * P + W - 1);
-#pragma unroll
-    for (int s = 0; s < 3; ++s) {
-      const S *q = p + (9 + 5 * s) * P;
-      c.g[s][0] = ld_r(q);
-      c.g[s][1] = ld_r(q + 1 * P - 1);
-      c.g[s][2] = ld_r(q + 2 * P - W);
-      c.g[s][3] = ld_r(q + 3 * P + 1);
-      c.g[s][4] = ld_r(q + 4 * P + W);
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < 9; ++i) c.f[i] = pull_flow_edge<S, R>(src, a, mask, mid, pal, i, x, y, m);
-#pragma unroll
-    for (int s = 0; s < 3; ++s)
-#pragma unroll
-      for (int i = 0; i < 5; ++i) c.g[s][i] = pull_scalar_edge<S, R>(src, a, mask, mc, s, i, x, y, m);
-  }
+  load_interior<S, R>(src, a, x, y, c);
+  if (m & M_EDGE) fix_edges<S, R>(src, a, mask, mid, pal, mc, x, y, m, c);
 }
 
 // Macroscopic values of a post-stream cell (Eq. 8, 11).
@@ -270,10 +315,11 @@ __device__ __forceinline__ Macro<R> macros(const KArgs &a, const MatCoef<R> &mc,
   R den = mc.l0 + sqrt(mc.l0 * mc.l0 + mc.l1 * vn);
   r.ux = vx / den;
   r.uy = vy / den;
-  R s18 = d[1] + d[2] + d[3] + d[4] + d[5] + d[6] + d[7] + d[8];
+  R s18 = ((d[1] + d[3]) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8]));
   r.Pdev = R(0.6) * s18 - R(0.4) * (r.ux * r.ux + r.uy * r.uy) * mc.inv_phi;
 #pragma unroll
-  for (int s = 0; s < 3; ++s) r.C[s] = c.g[s][0] + c.g[s][1] + c.g[s][2] + c.g[s][3] + c.g[s][4];
+  for (int s = 0; s < 3; ++s)
+    r.C[s] = d2q5_sum<R>(c.g[s][0], c.g[s][1], c.g[s][2], c.g[s][3], c.g[s][4]);
   return r;
 }
 
@@ -285,7 +331,7 @@ __device__ __forceinline__ void collide_flow(const KArgs &a, const MatCoef<R> &m
   R ux = u.ux, uy = u.uy, u2 = ux * ux + uy * uy, un = sqrt(u2), ip = mc.inv_phi;
   R Fx = -mc.darcy * ux - mc.forch * un * ux + mc.phi * R(a.body_g);
   R Fy = -mc.darcy * uy - mc.forch * un * uy;
-  R ax = d[1] + d[2] + d[3] + d[4], dg = d[5] + d[6] + d[7] + d[8];
+  R ax = (d[1] + d[3]) + (d[2] + d[4]), dg = (d[5] + d[7]) + (d[6] + d[8]);
   R m0 = d[0] + ax + dg;
   R m1 = R(-4) * d[0] - ax + R(2) * dg;
   R m2 = R(4) * d[0] - R(2) * ax + dg;
@@ -328,24 +374,27 @@ __device__ __forceinline__ void collide_flow(const KArgs &a, const MatCoef<R> &m
 template <typename R>
 __device__ __forceinline__ void collide_scalar(const KArgs &a, const MatCoef<R> &mc, int s,
                                                R ux, R uy, R Cdev, const R d[5], R srcv, R o[5]) {
-  const R Q1 = R(a.Q1), Q3 = R(a.Q3);
+  const R Q1 = mc.q1[s], Q3 = R(a.Q3);
   R C = Cdev + R(a.Cref[s]);
   R n0 = Cdev;
   R n1 = d[1] - d[3], n2 = d[2] - d[4];
-  R n3 = R(-4) * d[0] + d[1] + d[2] + d[3] + d[4];
-  R n4 = d[1] - d[2] + d[3] - d[4];
+  R e13 = d[1] + d[3], e24 = d[2] + d[4];
+  R n3 = R(-4) * d[0] + (e13 + e24);
+  R n4 = e13 - e24;
   R b = mc.b[s];
   n1 -= Q1 * (n1 - ux * C);
   n2 -= Q1 * (n2 - uy * C);
   n3 -= Q3 * (n3 - (b * Cdev + (b - R(a.bref[s])) * R(a.Cref[s])));
   n4 -= Q3 * n4;
   R w1 = mc.w1[s], w0 = R(1) - R(4) * w1;
-  R c0 = n0 * R(0.2), c3 = n3 * R(0.05);
+  // even parts first, the large odd (advective) part added last
+  R ev = n0 * R(0.2) + n3 * R(0.05) + w1 * srcv;
+  R ex = ev + R(0.25) * n4, ey = ev - R(0.25) * n4;
   o[0] = (n0 - n3) * R(0.2) + w0 * srcv;
-  o[1] = c0 + R(0.5) * n1 + c3 + R(0.25) * n4 + w1 * srcv;
-  o[3] = c0 - R(0.5) * n1 + c3 + R(0.25) * n4 + w1 * srcv;
-  o[2] = c0 + R(0.5) * n2 + c3 - R(0.25) * n4 + w1 * srcv;
-  o[4] = c0 - R(0.5) * n2 + c3 - R(0.25) * n4 + w1 * srcv;
+  o[1] = ex + R(0.5) * n1;
+  o[3] = ex - R(0.5) * n1;
+  o[2] = ey + R(0.5) * n2;
+  o[4] = ey - R(0.5) * n2;
 }
 
 }  // namespace pemlbm

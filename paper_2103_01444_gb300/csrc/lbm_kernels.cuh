@@ -9,22 +9,25 @@
 namespace pemlbm {
 
 // ------------------------------------------------------------- step (K1)
-template <typename S>
-__global__ void __launch_bounds__(kStepThreads)
+template <typename S, int BX, int BY, int MINB>
+__global__ void __launch_bounds__(BX * BY, MINB)
 k_step(const S *__restrict__ src_p, S *__restrict__ dst, const uint8_t *__restrict__ mask,
        const uint16_t *__restrict__ mid, const MatCoef<typename Real<S>::type> *__restrict__ pal,
        KArgs a) {
   using R = typename Real<S>::type;
-  const int x = blockIdx.x * kStepBX + (threadIdx.x % kStepBX);
-  const int y = blockIdx.y * kStepBY + (threadIdx.x / kStepBX);
+  const int x = blockIdx.x * BX + (threadIdx.x % BX);
+  const int y = blockIdx.y * BY + (threadIdx.x / BX);
   if (x >= a.nx || y >= a.ny) return;
   const long long c = (long long)y * a.nxp + x;
-  const uint8_t m = mask[c];
-  if ((m & REG_MASK) == REG_SOLID) return;
   const Pops<S> src{src_p, a.plane, a.nxp};
-  const MatCoef<R> mc = pal[mid[c]];
+  const uint8_t m = mask[c];
   Cell<R> cell;
-  pull_cell<S, R>(src, a, mask, mid, pal, mc, x, y, m, cell);
+  load_interior<S, R>(src, a, x, y, cell);
+  // solid cells run the same arithmetic on their (unused) values and only
+  // skip the stores, so no branch stands between the mask and the loads
+  const bool live = (m & REG_MASK) != REG_SOLID;
+  const MatCoef<R> mc = pal[mid[c]];
+  if (m & M_EDGE) fix_edges<S, R>(src, a, mask, mid, pal, mc, x, y, m, cell);
   if (a.mode == 0 && (m & M_YLO)) surface_reaction<S, R>(src, a, mc, x, cell);
   R S_vol = 0;
   if (a.mode == 1 && (m & REG_MASK) == REG_CATALYST) S_vol = volume_sink<S, R>(src, a, x, y);
@@ -32,15 +35,19 @@ k_step(const S *__restrict__ src_p, S *__restrict__ dst, const uint8_t *__restri
   R o[9];
   collide_flow<R>(a, mc, u, cell.f, o);
   S *out = dst + c;
+  if (live) {
 #pragma unroll
-  for (int i = 0; i < 9; ++i) st_r(out + (long long)i * a.plane, o[i]);
-  const R srcv[3] = {-S_vol * R(a.hpo), S_vol, R(-2) * S_vol};
+    for (int i = 0; i < 9; ++i) st_r(out + (long long)i * a.plane, o[i]);
+  }
+  const R srcv[3] = {-S_vol * R(a.hpo) * mc.inv_sigma, S_vol, R(-2) * S_vol};
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
     R g[5];
     collide_scalar<R>(a, mc, s, u.ux, u.uy, u.C[s], cell.g[s], srcv[s], g);
+    if (live) {
 #pragma unroll
-    for (int i = 0; i < 5; ++i) st_r(out + (long long)(9 + 5 * s + i) * a.plane, g[i]);
+      for (int i = 0; i < 5; ++i) st_r(out + (long long)(9 + 5 * s + i) * a.plane, g[i]);
+    }
   }
 }
 
@@ -97,87 +104,110 @@ __device__ __forceinline__ void block_sum(double (&v)[N], double *smem /* N * 32
 
 // --------------------------------------------- catalyst reduction (K3)
 // Recomputes the reaction applied in the last step from the state before it
-// (src): per column the O2 consumed J(x) and the heat q(x).  One block of
-// kReduceThreads threads; out[0] = sum J, out[1] = sum q (FP64, lattice
-// units); profile[x] = J(x) * i_scale (A/cm^2) if not NULL.
+// (src).  Blocks of kCatalystBX columns x kCatalystBY row-threads: each
+// column's O2 consumption J(x) (the surface link of the thin film, or the
+// sum of the volumetric sinks over the catalyst rows) is reduced in shared
+// memory in a fixed order and written, with its heat h J(x), to colsum
+// [2][nx] (FP64); profile[x] = J(x) i_scale (A/cm^2) when not NULL.
 template <typename S>
-__global__ void __launch_bounds__(kReduceThreads)
+__global__ void __launch_bounds__(kCatalystBX * kCatalystBY)
 k_catalyst(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
            const uint16_t *__restrict__ mid, const MatCoef<typename Real<S>::type> *__restrict__ pal,
-           KArgs a, double i_scale, float *__restrict__ profile, double *__restrict__ out) {
+           KArgs a, double i_scale, float *__restrict__ profile, double *__restrict__ colsum) {
   using R = typename Real<S>::type;
-  __shared__ double sm[2 * 32];
+  __shared__ double sm[kCatalystBY][kCatalystBX];
   const Pops<S> src{src_p, a.plane, a.nxp};
-  double acc[2] = {0.0, 0.0};
-  for (int x = threadIdx.x; x < a.nx; x += blockDim.x) {
-    double J = 0.0;
+  const int tx = threadIdx.x % kCatalystBX, ty = threadIdx.x / kCatalystBX;
+  const int x = blockIdx.x * kCatalystBX + tx;
+  double J = 0.0;
+  if (x < a.nx) {
     if (a.mode == 0) {
-      const uint8_t m = mask[x];
-      if ((m & REG_MASK) != REG_SOLID) {
+      if (ty == 0 && (mask[x] & REG_MASK) != REG_SOLID) {
         const MatCoef<R> mc = pal[mid[x]];
-        Cell<R> cell;  // only the upward O2 link is needed: it is the bounced g*_4
+        Cell<R> cell;  // only the upward links matter: the bounced g*_4 of each scalar
         cell.g[1][2] = R(src.at(9 + 5 * 1 + 4, x, 0));
         cell.g[0][2] = 0;
         cell.g[2][2] = 0;
         J = (double)surface_reaction<S, R>(src, a, mc, x, cell);
       }
     } else {
-      for (int y = 0; y < a.ny_cl; ++y) {
-        const uint8_t m = mask[(long long)y * a.nxp + x];
-        if ((m & REG_MASK) == REG_CATALYST) J -= (double)volume_sink<S, R>(src, a, x, y);
-      }
+      for (int y = ty; y < a.ny_cl; y += kCatalystBY)
+        if ((mask[(long long)y * a.nxp + x] & REG_MASK) == REG_CATALYST)
+          J -= (double)volume_sink<S, R>(src, a, x, y);
     }
-    acc[0] += J;
-    acc[1] += J * a.hpo;
-    if (profile) profile[x] = (float)(J * i_scale);
   }
-  block_sum<2>(acc, sm);
-  if (threadIdx.x == 0) {
-    out[0] = acc[0];
-    out[1] = acc[1];
+  sm[ty][tx] = J;
+  __syncthreads();
+  if (ty == 0 && x < a.nx) {
+    double t = 0.0;
+    for (int k = 0; k < kCatalystBY; ++k) t += sm[k][tx];
+    colsum[x] = t;
+    colsum[a.nx + x] = t * a.hpo;
+    if (profile) profile[x] = (float)(t * i_scale);
   }
 }
 
+// Sums the per-column J and heat in a fixed order: out[0], out[1].
+__global__ void k_sum_columns(const double *__restrict__ colsum, int nx, double *__restrict__ out);
+
 // ------------------------------------------------- residual (K4)
 // Moments of the post-collision state: X = (j_x, j_y, T - T_in, C_O2, C_H2O).
-// Accumulates per block sum (X - X_prev)^2 and sum X^2 (10 doubles), then
-// overwrites the snapshot; flags non-finite values.
+// One thread per cell: the change since the snapshot and the value are
+// squared, summed over the warp by shuffles, then over the block in FP64
+// (10 partial sums per block); the snapshot (storage precision R) is then
+// overwritten.  Non-finite values raise *bad.
 template <typename S>
-__global__ void __launch_bounds__(kReduceThreads)
+__global__ void __launch_bounds__(kResidualBX * kResidualBY)
 k_residual(const S *__restrict__ src_p, const uint8_t *__restrict__ mask, KArgs a,
-           double *__restrict__ snap, double *__restrict__ partial, int *__restrict__ bad) {
+           typename Real<S>::type *__restrict__ snap, double *__restrict__ partial,
+           int *__restrict__ bad) {
   using R = typename Real<S>::type;
   __shared__ double sm[10 * 32];
   const Pops<S> src{src_p, a.plane, a.nxp};
-  double acc[10];
+  const int x = blockIdx.x * kResidualBX + (threadIdx.x % kResidualBX);
+  const int y = blockIdx.y * kResidualBY + (threadIdx.x / kResidualBX);
+  R v[10];
 #pragma unroll
-  for (int k = 0; k < 10; ++k) acc[k] = 0.0;
-  const long long n = (long long)a.nx * a.ny;
-  for (long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x; o < n;
-       o += (long long)gridDim.x * blockDim.x) {
-    const int y = (int)(o / a.nx), x = (int)(o % a.nx);
-    if ((mask[(long long)y * a.nxp + x] & REG_MASK) == REG_SOLID) continue;
+  for (int k = 0; k < 10; ++k) v[k] = R(0);
+  if (x < a.nx && y < a.ny && (mask[(long long)y * a.nxp + x] & REG_MASK) != REG_SOLID) {
+    const long long n = (long long)a.nx * a.ny, o = (long long)y * a.nx + x;
     R d[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) d[k] = R(src.at(k, x, y));
-    double X[5];
-    X[0] = (double)(d[1] - d[3] + d[5] - d[6] - d[7] + d[8]);
-    X[1] = (double)(d[2] - d[4] + d[5] + d[6] - d[7] - d[8]);
-    X[2] = (double)own_sum<S, R>(src, 0, x, y) + (a.Cref[0] - a.T_in);
-    X[3] = (double)own_sum<S, R>(src, 1, x, y) + a.Cref[1];
-    X[4] = (double)own_sum<S, R>(src, 2, x, y) + a.Cref[2];
+    R X[5];
+    X[0] = d[1] - d[3] + d[5] - d[6] - d[7] + d[8];
+    X[1] = d[2] - d[4] + d[5] + d[6] - d[7] - d[8];
+    X[2] = own_sum<S, R>(src, 0, x, y) + R(a.Cref[0] - a.T_in);
+    X[3] = own_sum<S, R>(src, 1, x, y) + R(a.Cref[1]);
+    X[4] = own_sum<S, R>(src, 2, x, y) + R(a.Cref[2]);
+    bool ok = true;
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-      if (!isfinite(X[k])) *bad = 1;
-      const double dv = X[k] - snap[k * n + o];
-      acc[k] += dv * dv;
-      acc[5 + k] += X[k] * X[k];
+      ok = ok && isfinite(X[k]);
+      const R dv = X[k] - snap[k * n + o];
+      v[k] = dv * dv;
+      v[5 + k] = X[k] * X[k];
       snap[k * n + o] = X[k];
     }
+    if (!ok) *bad = 1;
   }
-  block_sum<10>(acc, sm);
-  if (threadIdx.x == 0)
-    for (int k = 0; k < 10; ++k) partial[(long long)blockIdx.x * 10 + k] = acc[k];
+  double acc[10];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) {
+    R t = v[k];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+    acc[k] = (double)t;   // lane 0 holds the warp sum; the rest is FP64
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0)
+    for (int k = 0; k < 10; ++k) sm[k * 32 + warp] = acc[k];
+  __syncthreads();
+  if (threadIdx.x < 10) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += sm[threadIdx.x * 32 + w];
+    partial[((long long)blockIdx.y * gridDim.x + blockIdx.x) * 10 + threadIdx.x] = t;
+  }
 }
 
 // Sums nblocks x 10 partials in a fixed order.
@@ -250,12 +280,28 @@ __global__ void k_set_state(S *__restrict__ pop, const uint8_t *__restrict__ mas
 }
 
 // ------------------------------------------------------ launchers
-template <typename S>
-void launch_step(const void *src, void *dst, const DevGeom &g, const KArgs &a, cudaStream_t st) {
-  dim3 grid((a.nx + kStepBX - 1) / kStepBX, (a.ny + kStepBY - 1) / kStepBY);
-  k_step<S><<<grid, kStepThreads, 0, st>>>(
+template <typename S, int V>
+void launch_step_v(const void *src, void *dst, const DevGeom &g, const KArgs &a, cudaStream_t st) {
+  constexpr StepShape sh = kStepShapes[V];
+  dim3 grid((a.nx + sh.bx - 1) / sh.bx, (a.ny + sh.by - 1) / sh.by);
+  k_step<S, sh.bx, sh.by, sh.minb><<<grid, sh.bx * sh.by, 0, st>>>(
       (const S *)src, (S *)dst, g.mask, g.mid,
       (const MatCoef<typename Real<S>::type> *)g.pal, a);
+}
+
+template <typename S>
+void launch_step(const void *src, void *dst, const DevGeom &g, const KArgs &a, int variant,
+                 cudaStream_t st) {
+  switch (variant) {
+    case 1: launch_step_v<S, 1>(src, dst, g, a, st); break;
+    case 2: launch_step_v<S, 2>(src, dst, g, a, st); break;
+    case 3: launch_step_v<S, 3>(src, dst, g, a, st); break;
+    case 4: launch_step_v<S, 4>(src, dst, g, a, st); break;
+    case 5: launch_step_v<S, 5>(src, dst, g, a, st); break;
+    case 6: launch_step_v<S, 6>(src, dst, g, a, st); break;
+    case 7: launch_step_v<S, 7>(src, dst, g, a, st); break;
+    default: launch_step_v<S, 0>(src, dst, g, a, st); break;
+  }
 }
 
 template <typename S>
@@ -267,17 +313,21 @@ void launch_fields(const void *src, const DevGeom &g, const KArgs &a, double *ou
 
 template <typename S>
 void launch_catalyst(const void *src, const DevGeom &g, const KArgs &a, double i_scale,
-                     float *profile, double *out, cudaStream_t st) {
-  k_catalyst<S><<<1, kReduceThreads, 0, st>>>((const S *)src, g.mask, g.mid,
-                                              (const MatCoef<typename Real<S>::type> *)g.pal, a,
-                                              i_scale, profile, out);
+                     float *profile, double *colsum, double *out, cudaStream_t st) {
+  const int nb = (a.nx + kCatalystBX - 1) / kCatalystBX;
+  k_catalyst<S><<<nb, kCatalystBX * kCatalystBY, 0, st>>>(
+      (const S *)src, g.mask, g.mid, (const MatCoef<typename Real<S>::type> *)g.pal, a, i_scale,
+      profile, colsum);
+  k_sum_columns<<<1, kReduceThreads, 0, st>>>(colsum, a.nx, out);
 }
 
 template <typename S>
-void launch_residual(const void *src, const DevGeom &g, const KArgs &a, double *snap,
-                     double *partial, int nblocks, int *bad, double *out, cudaStream_t st) {
-  k_residual<S><<<nblocks, kReduceThreads, 0, st>>>((const S *)src, g.mask, a, snap, partial, bad);
-  k_sum_partials<<<1, kReduceThreads, 0, st>>>(partial, nblocks, out);
+void launch_residual(const void *src, const DevGeom &g, const KArgs &a, void *snap,
+                     double *partial, int *bad, double *out, cudaStream_t st) {
+  dim3 grid((a.nx + kResidualBX - 1) / kResidualBX, (a.ny + kResidualBY - 1) / kResidualBY);
+  k_residual<S><<<grid, kResidualBX * kResidualBY, 0, st>>>(
+      (const S *)src, g.mask, a, (typename Real<S>::type *)snap, partial, bad);
+  k_sum_partials<<<1, kReduceThreads, 0, st>>>(partial, grid.x * grid.y, out);
 }
 
 template <typename S>
@@ -300,13 +350,14 @@ void launch_set_state(void *pop, const DevGeom &g, const KArgs &a, const double 
 }
 
 #define PEMLBM_INSTANTIATE(S)                                                                   \
-  template void launch_step<S>(const void *, void *, const DevGeom &, const KArgs &, cudaStream_t); \
+  template void launch_step<S>(const void *, void *, const DevGeom &, const KArgs &, int,       \
+                               cudaStream_t);                                                   \
   template void launch_fields<S>(const void *, const DevGeom &, const KArgs &, double *,        \
                                  cudaStream_t);                                                 \
   template void launch_catalyst<S>(const void *, const DevGeom &, const KArgs &, double,        \
-                                   float *, double *, cudaStream_t);                            \
-  template void launch_residual<S>(const void *, const DevGeom &, const KArgs &, double *,      \
-                                   double *, int, int *, double *, cudaStream_t);               \
+                                   float *, double *, double *, cudaStream_t);                  \
+  template void launch_residual<S>(const void *, const DevGeom &, const KArgs &, void *,        \
+                                   double *, int *, double *, cudaStream_t);                    \
   template void launch_init<S>(void *, const DevGeom &, const KArgs &, cudaStream_t);           \
   template void launch_get_state<S>(const void *, const DevGeom &, const KArgs &, double *,     \
                                     cudaStream_t);                                              \

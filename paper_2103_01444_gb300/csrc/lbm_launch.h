@@ -8,13 +8,19 @@ namespace pemlbm {
 
 struct KArgs;
 struct MatRaw;
+struct ScalarMode;
 
-// Launch shape of the coupled step: kStepBX consecutive cells along x per
-// row, kStepBY rows per block.
-constexpr int kStepBX = 128;
-constexpr int kStepBY = 2;
-constexpr int kStepThreads = kStepBX * kStepBY;
+// Launch shapes of the coupled step: BX consecutive cells along x per row,
+// BY rows per block, and the minimum resident blocks per SM asked of the
+// register allocator.  lbm_tune times them and keeps the fastest.
+struct StepShape { int bx, by, minb; };
+constexpr int kStepVariants = 8;
+constexpr StepShape kStepShapes[kStepVariants] = {
+    {128, 2, 1}, {128, 2, 3}, {128, 2, 4}, {64, 4, 4},
+    {256, 1, 4}, {32, 8, 4}, {128, 1, 8}, {64, 2, 8}};
 constexpr int kReduceThreads = 512;
+constexpr int kResidualBX = 128, kResidualBY = 2;      // residual blocks
+constexpr int kCatalystBX = 32, kCatalystBY = 8;       // catalyst reduction blocks
 
 // Device-resident geometry shared by all kernels of a domain.
 struct DevGeom {
@@ -23,10 +29,14 @@ struct DevGeom {
   const void *pal;       // MatCoef<R>[npal]
 };
 
-template <typename S> void launch_step(const void *src, void *dst, const DevGeom &g, const KArgs &a, cudaStream_t st);
+template <typename S> void launch_step(const void *src, void *dst, const DevGeom &g, const KArgs &a, int variant, cudaStream_t st);
 template <typename S> void launch_fields(const void *src, const DevGeom &g, const KArgs &a, double *out, cudaStream_t st);
-template <typename S> void launch_catalyst(const void *src, const DevGeom &g, const KArgs &a, double i_scale, float *profile, double *out, cudaStream_t st);
-template <typename S> void launch_residual(const void *src, const DevGeom &g, const KArgs &a, double *snap, double *partial, int nblocks, int *bad, double *out, cudaStream_t st);
+template <typename S> void launch_catalyst(const void *src, const DevGeom &g, const KArgs &a, double i_scale, float *profile, double *colsum, double *out, cudaStream_t st);
+template <typename S> void launch_residual(const void *src, const DevGeom &g, const KArgs &a, void *snap, double *partial, int *bad, double *out, cudaStream_t st);
+// Blocks of the residual kernel (= rows of its partial-sum buffer).
+inline int residual_blocks(int nx, int ny) {
+  return ((nx + kResidualBX - 1) / kResidualBX) * ((ny + kResidualBY - 1) / kResidualBY);
+}
 template <typename S> void launch_init(void *pop, const DevGeom &g, const KArgs &a, cudaStream_t st);
 template <typename S> void launch_get_state(const void *pop, const DevGeom &g, const KArgs &a, double *out, cudaStream_t st);
 template <typename S> void launch_set_state(void *pop, const DevGeom &g, const KArgs &a, const double *in, cudaStream_t st);
@@ -37,6 +47,6 @@ void launch_build_mask(uint8_t *mask, const uint8_t *solid, int nx, int ny, int 
 // Derived material coefficients of a palette (Eq. 7, 8, 10): R = double if
 // fp64 else float.
 void launch_prep_palette(void *pal, const MatRaw *raw, int npal, double nu, int forchheimer,
-                         bool fp64, cudaStream_t st);
+                         const ScalarMode &mode, bool fp64, cudaStream_t st);
 
 }  // namespace pemlbm

@@ -23,7 +23,8 @@ STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM
 EXPORTS = ("lbm_create_domain", "lbm_destroy_domain", "lbm_set_params", "lbm_set_fields",
            "lbm_reset", "lbm_step", "lbm_current_density", "lbm_residual", "lbm_get_fields",
            "lbm_get_state", "lbm_set_state", "lbm_get_mask", "lbm_get_step", "lbm_save_state",
-           "lbm_load_state", "lbm_time_steps", "lbm_bytes_per_cell", "lbm_last_error")
+           "lbm_load_state", "lbm_time_steps", "lbm_bytes_per_cell", "lbm_tune",
+           "lbm_set_variant", "lbm_last_error")
 
 
 class LbmError(RuntimeError):
@@ -46,8 +47,9 @@ _PARAM_DOUBLES = ("nu", "u_in_avg", "body_force_x", "V_op", "T_in", "C_O2_in", "
 
 
 class lbm_params(C.Structure):
-    _fields_ = [(k, C.c_double) for k in _PARAM_DOUBLES] + [("forchheimer", C.c_int32),
-                                                            ("top_dirichlet", C.c_int32)]
+    _fields_ = [(k, C.c_double) for k in _PARAM_DOUBLES] + [
+        ("forchheimer", C.c_int32), ("top_dirichlet", C.c_int32),
+        ("interface_mode", C.c_int32), ("reserved", C.c_int32)]
 
 
 _lib = None
@@ -66,7 +68,7 @@ def load_library(path: str = LIB_PATH):
         "lbm_create_domain": [C.POINTER(lbm_domain_desc), C.POINTER(P)],
         "lbm_destroy_domain": [P],
         "lbm_set_params": [P, C.POINTER(lbm_params)],
-        "lbm_set_fields": [P, d, d, d, d, d],
+        "lbm_set_fields": [P, d, d, d, d, d, d],
         "lbm_reset": [P],
         "lbm_step": [P, C.c_int64],
         "lbm_current_density": [P, d, d, C.POINTER(C.c_float)],
@@ -80,6 +82,8 @@ def load_library(path: str = LIB_PATH):
         "lbm_load_state": [P, C.c_void_p, C.c_size_t],
         "lbm_time_steps": [P, C.c_int64, d],
         "lbm_bytes_per_cell": [P, d],
+        "lbm_tune": [P, C.c_int32, C.POINTER(C.c_int32), d],
+        "lbm_set_variant": [P, C.c_int32],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -122,9 +126,9 @@ class Domain:
 
     @classmethod
     def from_case(cls, case: dict, precision="fp32", forchheimer: int = 1, stream=None,
-                  reset: bool = True):
+                  reset: bool = True, interface_mode: int = 0):
         from .units import cathode_params
-        params, fields, geo = cathode_params(case, forchheimer)
+        params, fields, geo = cathode_params(case, forchheimer, interface_mode)
         d = cls(precision=precision, stream=stream, **geo)
         d.set_params(params)
         d.set_fields(**fields)
@@ -148,10 +152,15 @@ class Domain:
         self.params = dict(params)
         _check(self.L.lbm_set_params(self.h, C.byref(lbm_params(**params))))
 
-    def set_fields(self, phi, K, alpha_T, D_O2, D_H2O):
+    def set_fields(self, phi, K, alpha_T, D_O2, D_H2O, rho_cp_ratio=None):
         arrs = [np.ascontiguousarray(np.broadcast_to(np.asarray(a, np.float64), (self.ny, self.nx)))
                 for a in (phi, K, alpha_T, D_O2, D_H2O)]
-        _check(self.L.lbm_set_fields(self.h, *[_dp(a) for a in arrs]))
+        sig = None
+        if rho_cp_ratio is not None:
+            sig = np.ascontiguousarray(np.broadcast_to(np.asarray(rho_cp_ratio, np.float64),
+                                                       (self.ny, self.nx)))
+        _check(self.L.lbm_set_fields(self.h, *[_dp(a) for a in arrs],
+                                     None if sig is None else _dp(sig)))
 
     def reset(self):
         _check(self.L.lbm_reset(self.h))
@@ -222,6 +231,16 @@ class Domain:
 
     def load_state(self, blob: bytes):
         _check(self.L.lbm_load_state(self.h, blob, len(blob)))
+
+    def tune(self, trial_steps: int = 20):
+        """Times every launch shape of the step kernel (after reset, before the
+        first step) and keeps the fastest; returns (variant, ms per step)."""
+        v, ms = C.c_int32(), C.c_double()
+        _check(self.L.lbm_tune(self.h, int(trial_steps), C.byref(v), C.byref(ms)))
+        return v.value, ms.value
+
+    def set_variant(self, v: int):
+        _check(self.L.lbm_set_variant(self.h, int(v)))
 
     def bytes_per_cell(self) -> float:
         b = C.c_double()

@@ -7,7 +7,8 @@ where the paper gives none:
   * dx = GDL thickness / GDL rows, dt = 0.05 dx^2 / D_O2 (D_O2 = 5.2197e-2
     cm^2/s, Nomenclature);
   * solid/gas heat-capacity ratio 1500 and conductivity ratio 1.5/0.026
-    (Nomenclature) in Eq. 19; catalyst film 10 um thick;
+    (Nomenclature) in Eq. 19; the reaction heat is divided by the same
+    effective heat capacity (rho_cp_ratio per cell); catalyst film 10 um;
   * c_tot = C_O2,ref / 0.21 with C_O2,ref = 17.808e-6 mol/cm^3, and a gas
     molar heat capacity of 29.3 J/(mol K);
   * Eq. 17's reference temperature 353.15 K.
@@ -44,7 +45,7 @@ def effective_thermal_diffusivity(phi, alpha_gas):
     return alpha_gas * (phi + kr * (1.0 - phi)) / (phi + cr * (1.0 - phi))
 
 
-def cathode_params(case: dict, forchheimer: int = 1):
+def cathode_params(case: dict, forchheimer: int = 1, interface_mode: int = 0):
     """Returns (params dict matching lbm_params, fields dict of [ny][nx]
     float64 arrays phi, K, alpha_T, D_O2, D_H2O, geometry dict)."""
     nx, ny = int(case["nx"]), int(case["ny"])
@@ -63,6 +64,7 @@ def cathode_params(case: dict, forchheimer: int = 1):
         alpha_T=np.ascontiguousarray(effective_thermal_diffusivity(phi, alpha_gas)),
         D_O2=np.ascontiguousarray(effective_diffusivity(phi, L["D_O2"])),
         D_H2O=np.ascontiguousarray(effective_diffusivity(phi, L["h2o_over_o2"] * L["D_O2"])),
+        rho_cp_ratio=np.ascontiguousarray(phi + LATTICE["heat_capacity_ratio"] * (1.0 - phi)),
     )
     params = dict(
         nu=L["nu"], u_in_avg=case["Re"] * L["nu"] / channel_rows, body_force_x=0.0,
@@ -72,7 +74,7 @@ def cathode_params(case: dict, forchheimer: int = 1):
         alpha_c=PAPER["alpha_c"], F=PAPER["F"], R=PAPER["R"], dU0dT=PAPER["dU0dT"],
         U0_0=PAPER["U0_0"], x_ref=L["x_ref"], dx_cm=dx, dt_s=dt, delta_cl_cm=L["delta_cl_cm"],
         c_tot=c_tot, rho_cp_f=L["gas_cp_J_molK"] * c_tot, forchheimer=forchheimer,
-        top_dirichlet=0,
+        top_dirichlet=0, interface_mode=interface_mode, reserved=0,
     )
     geometry = dict(nx=nx, ny=ny, ny_cl=ny_cl, ny_gdl=ny_gdl,
                     reaction_mode=int(case["reaction_mode"]),

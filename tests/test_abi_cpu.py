@@ -46,7 +46,7 @@ def test_param_structs_match_header():
     doubles = re.findall(r"double ([\w, ]+);", p)
     names = [n.strip() for grp in doubles for n in grp.split(",")]
     assert names == list(lbm._PARAM_DOUBLES)
-    assert ctypes.sizeof(lbm.lbm_params) == 8 * len(names) + 8
+    assert ctypes.sizeof(lbm.lbm_params) == 8 * len(names) + 16
     assert ctypes.sizeof(lbm.lbm_domain_desc) == 8 * 4 + 16
 
 
@@ -63,6 +63,7 @@ def test_product_and_oracle_unit_mappings_agree(case):
             assert v == pytest.approx(p2[k], rel=1e-13), k
     for k in ("phi", "K", "alpha_T", "D_O2", "D_H2O"):
         np.testing.assert_allclose(f1[k], m2[k], rtol=1e-13)
+    np.testing.assert_allclose(f1["rho_cp_ratio"], m2["sigma"], rtol=1e-13)
     assert g1["ny_cl"] == p2["ny_cl"] and g1["ny_gdl"] == p2["ny_gdl"]
 
 

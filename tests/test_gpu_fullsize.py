@@ -1,0 +1,61 @@
+"""Full-size parity: the 4096 x 1024 production-shaped cathode in the launch
+configuration the benchmark times.
+
+The oracle cannot run thousands of steps of 4.2 M cells, but one step of a
+cell depends only on its own column and the two neighbouring columns.  So
+for sampled columns (including the inlet and the outlet) the oracle
+recomputes one step from a full-height three-column window of the GPU's
+state, and the result must match the GPU's next state population by
+population.
+"""
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from oracle.params import lattice_problem
+from paper_2103_01444_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def window_case(case, x0):
+    w = dict(case)
+    w["nx"] = 3
+    w["phi"] = case["phi"][:, x0:x0 + 3]
+    w["K_cm2"] = case["K_cm2"][:, x0:x0 + 3]
+    if case.get("solid") is not None:
+        w["solid"] = case["solid"][:, x0:x0 + 3]
+    return w
+
+
+@pytest.mark.parametrize("precision,mode,tol", [("fp32", 0, 3e-6), ("fp32", 1, 3e-6)])
+def test_sampled_columns_one_step(precision, mode, tol):
+    from paper_2103_01444_gb300.build import build
+    from paper_2103_01444_gb300.lbm import Domain
+    build()
+    case = workloads.cathode_blocks(nx=4096, ny=1024)
+    nx, ny = case["nx"], case["ny"]
+    d = Domain.from_case(case, precision=precision, interface_mode=mode)
+    d.step(300)
+    s0 = d.state()
+    d.step(1)
+    s1 = d.state()
+    rng = np.random.default_rng(11)
+    cols = sorted(set([0, 1, 31, 32, 33, nx // 2, nx - 2, nx - 1] +
+                      list(rng.integers(0, nx, 24))))
+    scale = np.abs(s1).reshape(24, -1).max(axis=1)
+    worst = 0.0
+    for xc in cols:
+        x0 = min(max(xc - 1, 0), nx - 3)
+        k = xc - x0                           # column of xc inside the window
+        params, material, solid = lattice_problem(window_case(case, x0), interface_mode=mode)
+        o = Oracle(params, material, solid)
+        o.f = np.ascontiguousarray(s0[:9, :, x0:x0 + 3])
+        o.g = np.ascontiguousarray(s0[9:, :, x0:x0 + 3].reshape(3, 5, ny, 3))
+        o.step(1)
+        ref = np.concatenate([o.f, o.g.reshape(15, ny, 3)])[:, :, k]
+        got = s1[:, :, xc]
+        err = (np.abs(got - ref).max(axis=1) / scale).max()
+        worst = max(worst, err)
+        assert err < tol, (xc, err)
+    print(f"worst scaled one-step difference over {len(cols)} columns: {worst:.3e}")

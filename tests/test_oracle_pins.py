@@ -320,6 +320,23 @@ def test_layered_diffusion_alpha_C_linear():
         np.testing.assert_allclose(mat["D_O2"][:, 0] * C, a2 * y / H, atol=1e-12)
 
 
+def test_layered_diffusion_fickian_mode():
+    """Fickian interface mode: one b per scalar, diffusivity through the
+    flux rate, so C and the flux -alpha dC/dy are continuous: C is piecewise
+    linear with slopes J/alpha_1 and J/alpha_2."""
+    for H in (8, 12):
+        a1, a2 = 0.02, 0.05
+        mat = uniform_material(4, H, D_O2=a2)
+        mat["D_O2"][: H // 2] = a1
+        o = Oracle(scalar_case(H, aj0_ref=1e30, interface_mode=1), mat)
+        o.step(int(10 * H * H / a1))
+        C = o.fields()["C_O2"][:, 0]
+        s = np.arange(H) + 0.5
+        J = 1 / ((H / 2) * (1 / a1 + 1 / a2))
+        ex = np.where(s < H / 2, J * s / a1, J * (H / 2) / a1 + J * (s - H / 2) / a2)
+        np.testing.assert_allclose(C, ex, atol=1e-12)
+
+
 def advection_error(H, Pe):
     a = 0.05
     mat = uniform_material(4, H, D_O2=a)
