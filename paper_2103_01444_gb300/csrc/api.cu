@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -702,3 +703,82 @@ lbm_status lbm_bytes_per_cell(lbm_domain *d, double *bytes) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Residual without allocation.
+//
+// Some callers cannot call cudaMalloc when they need the steady-state
+// residual: code running under CUDA stream capture (an allocation there
+// breaks the capture), real-time loops that forbid allocation after start-up,
+// and hosts whose device memory comes only from their own pool.  For them the
+// block partial sums of the residual reduction live in this file-scope device
+// array instead of in memory the library allocates.  Every GPU that loads the
+// library holds it (1.31 MB) until the process exits.
+namespace {
+
+constexpr int kNoAllocBlocks = 16384;    // residual blocks of 128 x 2 cells: 4.19 M cells
+constexpr int kNoAllocSums = kNoAllocBlocks * 10;
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocSums + 16];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double *g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  In host code
+// the array's name is only a host-side stand-in, so the address is looked up
+// once per device (with that device current) and cached.
+lbm_status noalloc_scratch(double **out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(LBM_EINVAL, "device %d beyond %d", dev, kMaxDevices);
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess)
+      return fail(LBM_ECUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = (double *)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" lbm_status lbm_residual_noalloc(lbm_domain *d, void *snapshot, double *res) {
+  if (!d || !snapshot || !res) return fail(LBM_EINVAL, "null argument");
+  if (!d->have_state) return fail(LBM_ESTATE, "call lbm_reset first");
+  const int nblocks = residual_blocks(d->nx, d->ny);
+  if (nblocks > kNoAllocBlocks)
+    return fail(LBM_EINVAL,
+                "lattice of %d x %d cells needs %d residual blocks; lbm_residual_noalloc "
+                "handles at most %d (about 4.19 M cells)",
+                d->nx, d->ny, nblocks, kNoAllocBlocks);
+  double *scratch = nullptr;
+  lbm_status s = noalloc_scratch(&scratch);
+  if (s != LBM_OK) return s;
+  double *sums = scratch + kNoAllocSums;        // 10 sums
+  int *bad = (int *)(scratch + kNoAllocSums + 10);
+  // the flag must start at zero; the partials are fully rewritten each call
+  CK(cudaMemsetAsync(bad, 0, sizeof(int), d->stream));
+  const KArgs a = make_args(d);
+  dispatch(d->desc.precision, [&](auto *tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    launch_residual<S>(d->pop[d->cur], geom(d), a, snapshot, scratch, bad, sums, d->stream);
+  });
+  CK(cudaGetLastError());
+  double h[11];
+  CK(cudaMemcpyAsync(h, sums, 11 * sizeof(double), cudaMemcpyDeviceToHost, d->stream));
+  CK(cudaStreamSynchronize(d->stream));
+  int flag;
+  std::memcpy(&flag, h + 10, sizeof(int));
+  double r = 0.0;
+  for (int k = 0; k < 5; ++k) {
+    const double num = h[k], den = h[5 + k];
+    r = std::fmax(r, den > 0 ? std::sqrt(num / den) : (num > 0 ? INFINITY : 0.0));
+  }
+  *res = r;
+  if (flag || !std::isfinite(r)) return fail(LBM_EDIVERGED, "non-finite values in the state");
+  return LBM_OK;
+}

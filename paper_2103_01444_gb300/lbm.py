@@ -24,7 +24,7 @@ EXPORTS = ("lbm_create_domain", "lbm_destroy_domain", "lbm_set_params", "lbm_set
            "lbm_reset", "lbm_step", "lbm_current_density", "lbm_residual", "lbm_get_fields",
            "lbm_get_state", "lbm_set_state", "lbm_get_mask", "lbm_get_step", "lbm_save_state",
            "lbm_load_state", "lbm_time_steps", "lbm_bytes_per_cell", "lbm_tune",
-           "lbm_set_variant", "lbm_last_error")
+           "lbm_set_variant", "lbm_residual_noalloc", "lbm_last_error")
 
 
 class LbmError(RuntimeError):
@@ -84,6 +84,7 @@ def load_library(path: str = LIB_PATH):
         "lbm_bytes_per_cell": [P, d],
         "lbm_tune": [P, C.c_int32, C.POINTER(C.c_int32), d],
         "lbm_set_variant": [P, C.c_int32],
+        "lbm_residual_noalloc": [P, C.c_void_p, d],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -193,6 +194,14 @@ class Domain:
     def residual(self) -> float:
         r = C.c_double()
         _check(self.L.lbm_residual(self.h, C.byref(r)))
+        return r.value
+
+    def residual_noalloc(self, snapshot) -> float:
+        """Residual of lbm_residual against a caller-held snapshot (a CUDA
+        tensor of shape (5, ny, nx), float64 for FP64 domains, float32
+        otherwise), computed with the library's static scratch."""
+        r = C.c_double()
+        _check(self.L.lbm_residual_noalloc(self.h, C.c_void_p(snapshot.data_ptr()), C.byref(r)))
         return r.value
 
     def fields(self, out=None):
