@@ -47,6 +47,13 @@ def parse():
     ap.add_argument("--ny", type=int, default=NY)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the batched operating-point sweep measurement")
+    ap.add_argument("--sweep-cases", type=int, default=64)
+    ap.add_argument("--sweep-steps", type=int, default=256)
+    ap.add_argument("--workload", default="blocks", choices=["blocks", "grains"],
+                    help="blocks: 4096x1024 GDL blocks + volumetric catalyst; grains: "
+                         "8192x2048 pore-scale grains + thin film")
     ap.add_argument("--interface", type=int, default=0, choices=[0, 1],
                     help="0: Eq. 10 as printed (per-cell b); 1: Fickian interfaces")
     return ap.parse_args()
@@ -86,6 +93,10 @@ def barrier(pg, device=None):
 
 
 def workload(args):
+    if args.workload == "grains":
+        nx = args.nx if args.nx != NX else 8192
+        ny = args.ny if args.ny != NY else 2048
+        return workloads.cathode_grains(nx=nx, ny=ny)
     return workloads.cathode_blocks(nx=args.nx, ny=args.ny)
 
 
@@ -303,7 +314,9 @@ def run_ours(args):
                    "storage": args.precision, "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (two population buffers of "
                          f"{24 * cells * d_esize(args.precision) / 1e6:.0f} MB)",
-                   "reaction": "volumetric catalyst rows", "interface_mode": args.interface,
+                   "reaction": ("volumetric catalyst rows" if case["reaction_mode"] == 1
+                                else "thin catalyst film"),
+                   "interface_mode": args.interface,
                    "step_variant": variant,
                    "V_op": case["V_op"],
                    "Re": case["Re"], "T_in": case["T_in"]},
@@ -317,11 +330,47 @@ def run_ours(args):
     }
     if e2e is not None:
         line["e2e"] = e2e
+    if not args.no_sweep and args.workload == "blocks":
+        line["sweep"] = sweep(args, stream)
     if world == 1 and not args.no_cpu_baseline:
         v, cores, sample = cpu_baseline(case)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": sample}
     print(json.dumps(line), flush=True)
+
+
+def sweep(args, stream):
+    """The operating-point sweep: ncases cathodes of uneven size (512..2048
+    x 128..512, V, T, Re, K drawn from a seed) advanced together.  Reports
+    cases x steps per second for the tuned batched schedule and for one
+    launch per case and step (same kernel, no graph), and their ratio."""
+    from paper_2103_01444_gb300.lbm import Batch, Domain
+    cases = workloads.sweep_cases(args.sweep_cases)
+    doms = [Domain.from_case(c, precision=args.precision, stream=stream.cuda_stream)
+            for c in cases]
+    cells = sum(c["nx"] * c["ny"] for c in cases)
+    b = Batch(doms)
+    sched, var, _ = b.tune(5)
+    K = args.sweep_steps
+    b.step(16)
+    t_best = b.time_steps(K) / 1e3
+    b.set_schedule("per-case", variant=var)
+    b.step(4)
+    t_naive = b.time_steps(K) / 1e3
+    b.set_schedule("persistent" if sched == 0 else "graph", variant=var)
+    b.step(4)
+    t_other = b.time_steps(K) / 1e3
+    n = len(cases)
+    out = {"unit": "cases*steps/s", "cases": n, "cells": cells, "steps": K,
+           "value": n * K / t_best, "schedule": ["graph", "persistent"][sched],
+           "variant": var, "mlups": cells * K / t_best / 1e6,
+           "per_case_launches": n * K / t_naive,
+           "other_schedule": n * K / t_other,
+           "speedup_vs_per_case": t_naive / t_best}
+    b.close()
+    for d in doms:
+        d.close()
+    return out
 
 
 def d_esize(precision):

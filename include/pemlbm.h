@@ -205,6 +205,68 @@ lbm_status lbm_set_variant(lbm_domain *d, int32_t variant);
  * (24 populations read and written once, plus the 1-byte node mask). */
 lbm_status lbm_bytes_per_cell(lbm_domain *d, double *bytes);
 
+/* Discrete adjoint of the coupled step (gradients for design studies of
+ * the GDL, Sec. 5: porosity, permeability and effective O2 diffusivity).
+ * Starting from the domain's current state s^0, held fixed, the domain is
+ * advanced nsteps steps (in private buffers: the domain's own state is left
+ * unchanged) and the objective is evaluated at step N = nsteps:
+ *   objective 0: mean current density over the catalyst of step N (A/cm^2),
+ *                the value lbm_current_density reports after N steps;
+ *   objective 1: the largest temperature of the bottom row in the fields
+ *                of step N (K; ties go to the smallest x).
+ * Its gradient with respect to the per-cell phi, K and D_O2 of
+ * lbm_set_fields (lattice units; K of clear cells gets 0) and to the lattice
+ * inlet velocity u_in_avg is computed by the transposed step, applied from
+ * step N back to step 1, with the forward states recomputed from
+ * checkpoints every `segment` steps (<= 0: ceil(sqrt(nsteps))).  Memory:
+ * about (nsteps/segment + segment) population states.  The gradient of the
+ * Fickian interface mode treats each scalar's b (that of its largest
+ * diffusivity) as fixed.  J and the gradients go to host memory: dphi, dK,
+ * dD_O2 are [ny][nx] doubles (NULL to skip), du_in one double.  EINVAL for
+ * objective outside {0, 1} or nsteps outside [2, 2^30]; ENOMEM if the
+ * checkpoints do not fit. */
+lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t segment,
+                    double *J, double *dphi, double *dK, double *dD_O2, double *du_in);
+
+/* One transposed step at the current state s: given lam_next (host
+ * [24][ny][nx], the adjoint of the state after one step), writes lam_prev =
+ * (d step / d s)^T lam_next and the parameter gradients of
+ * <lam_next, step(s)> (host, as in lbm_grad; NULL to skip). */
+lbm_status lbm_vjp(lbm_domain *d, const double *lam_next, double *lam_prev, double *dphi,
+                   double *dK, double *dD_O2, double *du_in);
+
+/* Batched stepping (operating-point sweeps over cases of uneven size).
+ * lbm_create_batch groups ncases domains, each already set up and reset
+ * (ESTATE otherwise) and all of one precision (EINVAL otherwise); the batch
+ * borrows them (they must outlive it) and works on their own buffers, so
+ * fields, current density and checkpoints of each case stay available
+ * through the per-domain calls.  The batch runs on the first domain's
+ * stream, ordered after and before the other domains' streams by events.
+ * Schedules (lbm_batch_set_schedule):
+ *   0  one launch per step covering every case's tiles (launch shape
+ *      `variant` of lbm_set_variant), long runs replayed from a CUDA graph;
+ *   1  one persistent cooperative launch for all steps: co-resident blocks
+ *      loop over the tiles and meet at a grid barrier between steps; each
+ *      barrier wait gives up after spin_limit polls (<= 0 keeps the current
+ *      limit, 2^24 by default) and the call returns ETIMEOUT, leaving the
+ *      case states undefined (reset or load them);
+ *   2  one launch per case and step, no graph (the unbatched reference).
+ * All schedules give bit-identical states.  lbm_batch_tune, called between
+ * lbm_reset and the first step of every case, times schedule 0 with every
+ * launch shape and schedule 1 over trial_steps repetitions of the first
+ * step, keeps the fastest and leaves the states as reset left them. */
+typedef struct lbm_batch lbm_batch; /* opaque */
+lbm_status lbm_create_batch(lbm_domain *const *domains, int32_t ncases, lbm_batch **out);
+lbm_status lbm_destroy_batch(lbm_batch *b);
+lbm_status lbm_batch_set_schedule(lbm_batch *b, int32_t schedule, int32_t variant,
+                                  int64_t spin_limit);
+lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, int32_t *schedule, int32_t *variant,
+                          double *best_ms);
+/* Advances every case by nsteps (0 <= nsteps <= 2^30). */
+lbm_status lbm_batch_step(lbm_batch *b, int64_t nsteps);
+/* lbm_batch_step bracketed by CUDA events on the batch stream; elapsed ms. */
+lbm_status lbm_batch_time_steps(lbm_batch *b, int64_t nsteps, double *elapsed_ms);
+
 /* The steady-state residual of lbm_residual, computed without allocating.
  * This entry point has no counterpart in the paper.  It serves callers that
  * cannot call cudaMalloc when they need the residual: code under CUDA stream

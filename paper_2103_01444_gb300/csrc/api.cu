@@ -705,6 +705,553 @@ lbm_status lbm_bytes_per_cell(lbm_domain *d, double *bytes) {
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// Discrete adjoint (gradients of the objectives w.r.t. phi, K, D_O2 and the
+// inlet velocity).
+namespace {
+
+struct DevBuf {
+  void *p = nullptr;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  lbm_status alloc(size_t bytes) {
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(LBM_ENOMEM, "device allocation of %.1f MB for the adjoint failed", bytes / 1e6);
+    }
+    return LBM_OK;
+  }
+};
+
+// Reverse workspace of one domain.
+struct AdjWork {
+  DevBuf lam[2], M, O, V, gphi, gK, gD, gU;
+  lbm_status alloc(const lbm_domain *d) {
+    const size_t r = fp64(d) ? 8 : 4, planes = 24 * (size_t)d->plane;
+    lbm_status s;
+    for (auto *b : {&lam[0], &lam[1], &M, &O})
+      if ((s = b->alloc(planes * r)) != LBM_OK) return s;
+    if ((s = V.alloc(20 * (size_t)d->ny * r)) != LBM_OK) return s;
+    for (auto *b : {&gphi, &gK, &gD})
+      if ((s = b->alloc(sizeof(double) * d->plane)) != LBM_OK) return s;
+    if ((s = gU.alloc(sizeof(double))) != LBM_OK) return s;
+    return LBM_OK;
+  }
+  lbm_status zero_grads(const lbm_domain *d) {
+    for (auto *b : {&gphi, &gK, &gD}) CK(cudaMemsetAsync(b->p, 0, sizeof(double) * d->plane, d->stream));
+    CK(cudaMemsetAsync(gU.p, 0, sizeof(double), d->stream));
+    return LBM_OK;
+  }
+  AdjPtrs ptrs(int cur) {
+    return AdjPtrs{lam[cur].p, M.p, O.p, V.p, (double *)gphi.p, (double *)gK.p, (double *)gD.p,
+                   (double *)gU.p, lam[cur ^ 1].p};
+  }
+};
+
+// One reverse step: lambda^n (w.lam[cur]) at state src = s^{n-1} ->
+// lambda^{n-1} (w.lam[cur ^ 1]), gradients accumulated.
+void reverse_step(lbm_domain *d, AdjWork &w, int cur, const void *src, long long seed_cell) {
+  const KArgs a = make_args(d);
+  const int fick = d->prm.interface_mode == 1;
+  const AdjPtrs b = w.ptrs(cur);
+  dispatch(d->desc.precision, [&](auto *tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    launch_adj_local<S>(src, geom(d), d->raw, a, fick, b, seed_cell, d->stream);
+    launch_adj_gather<S>(geom(d), a, b, d->stream);
+  });
+}
+
+lbm_status copy_grads_out(lbm_domain *d, AdjWork &w, double *dphi, double *dK, double *dD,
+                          double *du) {
+  const size_t row = sizeof(double) * d->nx, pitch = sizeof(double) * d->nxp;
+  if (dphi) CK(cudaMemcpy2DAsync(dphi, row, w.gphi.p, pitch, row, d->ny, cudaMemcpyDeviceToHost, d->stream));
+  if (dK) CK(cudaMemcpy2DAsync(dK, row, w.gK.p, pitch, row, d->ny, cudaMemcpyDeviceToHost, d->stream));
+  if (dD) CK(cudaMemcpy2DAsync(dD, row, w.gD.p, pitch, row, d->ny, cudaMemcpyDeviceToHost, d->stream));
+  if (du) CK(cudaMemcpyAsync(du, w.gU.p, sizeof(double), cudaMemcpyDeviceToHost, d->stream));
+  CK(cudaStreamSynchronize(d->stream));
+  return LBM_OK;
+}
+
+// Full-value planes [24][ny][nx] (host) <-> deviation-free device planes of
+// type R [24][plane]: adjoints of deviations equal adjoints of full values.
+lbm_status lam_upload(lbm_domain *d, const double *host, void *dev) {
+  const size_t n = (size_t)d->nx * d->ny;
+  std::vector<unsigned char> tmp(24 * (size_t)d->plane * (fp64(d) ? 8 : 4), 0);
+  for (int q = 0; q < 24; ++q)
+    for (int y = 0; y < d->ny; ++y)
+      for (int x = 0; x < d->nx; ++x) {
+        const double v = host[q * n + (size_t)y * d->nx + x];
+        const size_t o = (size_t)q * d->plane + (size_t)y * d->nxp + x;
+        if (fp64(d)) ((double *)tmp.data())[o] = v;
+        else ((float *)tmp.data())[o] = (float)v;
+      }
+  CK(cudaMemcpyAsync(dev, tmp.data(), tmp.size(), cudaMemcpyHostToDevice, d->stream));
+  CK(cudaStreamSynchronize(d->stream));
+  return LBM_OK;
+}
+lbm_status lam_download(lbm_domain *d, const void *dev, double *host) {
+  const size_t n = (size_t)d->nx * d->ny;
+  std::vector<unsigned char> tmp(24 * (size_t)d->plane * (fp64(d) ? 8 : 4));
+  CK(cudaMemcpyAsync(tmp.data(), dev, tmp.size(), cudaMemcpyDeviceToHost, d->stream));
+  CK(cudaStreamSynchronize(d->stream));
+  for (int q = 0; q < 24; ++q)
+    for (int y = 0; y < d->ny; ++y)
+      for (int x = 0; x < d->nx; ++x) {
+        const size_t o = (size_t)q * d->plane + (size_t)y * d->nxp + x;
+        host[q * n + (size_t)y * d->nx + x] =
+            fp64(d) ? ((const double *)tmp.data())[o] : (double)((const float *)tmp.data())[o];
+      }
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_vjp(lbm_domain *d, const double *lam_next, double *lam_prev, double *dphi,
+                   double *dK, double *dD_O2, double *du_in) {
+  lbm_status s = check_ready(d);
+  if (s != LBM_OK) return s;
+  if (!lam_next || !lam_prev) return fail(LBM_EINVAL, "null argument");
+  AdjWork w;
+  if ((s = w.alloc(d)) != LBM_OK) return s;
+  if ((s = w.zero_grads(d)) != LBM_OK) return s;
+  if ((s = lam_upload(d, lam_next, w.lam[0].p)) != LBM_OK) return s;
+  reverse_step(d, w, 0, d->pop[d->cur], -1);
+  CK(cudaGetLastError());
+  if ((s = lam_download(d, w.lam[1].p, lam_prev)) != LBM_OK) return s;
+  return copy_grads_out(d, w, dphi, dK, dD_O2, du_in);
+}
+
+lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t segment,
+                    double *J, double *dphi, double *dK, double *dD_O2, double *du_in) {
+  lbm_status s = check_ready(d);
+  if (s != LBM_OK) return s;
+  if (objective != 0 && objective != 1) return fail(LBM_EINVAL, "objective must be 0 or 1");
+  if (nsteps < 2 || nsteps > (1LL << 30)) return fail(LBM_EINVAL, "nsteps outside [2, 2^30]");
+  const int64_t N = nsteps;
+  const int seg = segment > 0 ? segment : (int)std::ceil(std::sqrt((double)N));
+  const int64_t nck = (N + seg - 1) / seg;     // checkpoints of s^0, s^seg, ... (< N)
+  const size_t stride = 24 * (size_t)d->plane + d->nxp + 64;   // guard as in the domain
+  const size_t sbytes = stride * d->esize;
+  DevBuf ck, sg;
+  if ((s = ck.alloc(sbytes * nck)) != LBM_OK) return s;
+  if ((s = sg.alloc(sbytes * (seg + 1))) != LBM_OK) return s;
+  AdjWork w;
+  if ((s = w.alloc(d)) != LBM_OK) return s;
+  if ((s = w.zero_grads(d)) != LBM_OK) return s;
+  CK(cudaMemsetAsync(sg.p, 0, sbytes * (seg + 1), d->stream));
+  auto CKP = [&](int64_t k) { return (void *)((char *)ck.p + k * sbytes); };
+  auto SEG = [&](int64_t j) { return (void *)((char *)sg.p + j * sbytes); };
+  const KArgs a = make_args(d);
+  const DevGeom g = geom(d);
+  auto fwd = [&](const void *src, void *dst) {
+    dispatch(d->desc.precision, [&](auto *tag) {
+      using S = std::remove_pointer_t<decltype(tag)>;
+      launch_step<S>(src, dst, g, a, d->variant, d->stream);
+    });
+  };
+  // forward s^0 .. s^{N-1}, checkpoints every seg states
+  CK(cudaMemcpyAsync(CKP(0), d->pop[d->cur], sbytes, cudaMemcpyDeviceToDevice, d->stream));
+  CK(cudaMemcpyAsync(SEG(0), d->pop[d->cur], sbytes, cudaMemcpyDeviceToDevice, d->stream));
+  for (int64_t n = 1; n <= N - 1; ++n) {
+    fwd(SEG((n - 1) & 1), SEG(n & 1));
+    if (n % seg == 0) CK(cudaMemcpyAsync(CKP(n / seg), SEG(n & 1), sbytes, cudaMemcpyDeviceToDevice, d->stream));
+  }
+  CK(cudaGetLastError());
+  // reverse, last segment first
+  int cur = 0;
+  long long seed_cell = -1;
+  for (int64_t k = nck - 1; k >= 0; --k) {
+    const int64_t first = k * seg, last = std::min<int64_t>(first + seg - 1, N - 1);
+    CK(cudaMemcpyAsync(SEG(0), CKP(k), sbytes, cudaMemcpyDeviceToDevice, d->stream));
+    for (int64_t n = first + 1; n <= last; ++n) fwd(SEG(n - 1 - first), SEG(n - first));
+    CK(cudaGetLastError());
+    if (k == nck - 1) {
+      // objective at step N from s^{N-1}, and its seed lambda^{N-1}
+      const void *sN1 = SEG(N - 1 - first);
+      const lbm_params &p = d->prm;
+      const double i_scale = 4.0 * p.F * p.c_tot * p.dx_cm / p.dt_s;
+      if (objective == 0) {
+        dispatch(d->desc.precision, [&](auto *tag) {
+          using S = std::remove_pointer_t<decltype(tag)>;
+          launch_catalyst<S>(sN1, g, a, i_scale, nullptr, d->colsum, d->dsmall, d->stream);
+          launch_adj_seed_current<S>(sN1, g, a, d->prm.interface_mode == 1, i_scale / d->nx,
+                                     w.ptrs(1), d->stream);   // writes lam[0]
+        });
+        CK(cudaMemcpyAsync(d->hsmall, d->dsmall, sizeof(double), cudaMemcpyDeviceToHost, d->stream));
+        CK(cudaStreamSynchronize(d->stream));
+        if (J) *J = d->hsmall[0] * i_scale / d->nx;
+      } else {
+        if ((s = ensure_scratch(d)) != LBM_OK) return s;
+        dispatch(d->desc.precision, [&](auto *tag) {
+          using S = std::remove_pointer_t<decltype(tag)>;
+          launch_fields<S>(sN1, g, a, d->scratch, d->stream);
+        });
+        std::vector<double> Trow(d->nx);
+        const size_t n = (size_t)d->nx * d->ny;
+        CK(cudaMemcpyAsync(Trow.data(), d->scratch + 3 * n, sizeof(double) * d->nx,
+                           cudaMemcpyDeviceToHost, d->stream));
+        CK(cudaStreamSynchronize(d->stream));
+        int xs = 0;
+        for (int x = 1; x < d->nx; ++x)
+          if (Trow[x] > Trow[xs]) xs = x;       // ties: the smallest x
+        if (J) *J = Trow[xs];
+        seed_cell = xs;                          // row 0
+        // lambda^{N-1}: the seed pulled through the reverse of the pull
+        CK(cudaMemsetAsync(w.lam[0].p, 0, 24 * (size_t)d->plane * (fp64(d) ? 8 : 4), d->stream));
+        reverse_step(d, w, 0, sN1, seed_cell);   // lam[1] = lambda^{N-1}
+        cur = 1;
+      }
+    }
+    const int64_t ntop = (k == nck - 1) ? N - 1 : last + 1;
+    for (int64_t n = ntop; n >= first + 1; --n) {
+      reverse_step(d, w, cur, SEG(n - 1 - first), -1);
+      cur ^= 1;
+    }
+    CK(cudaGetLastError());
+  }
+  return copy_grads_out(d, w, dphi, dK, dD_O2, du_in);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched stepping of many domains (operating-point sweeps).
+struct lbm_batch {
+  std::vector<lbm_domain *> doms;
+  int precision = LBM_FP32;
+  cudaStream_t stream = nullptr;
+  BatchCase *dcases = nullptr;      // device case table
+  BatchCase *hcases = nullptr;      // pinned host staging of the table
+  int *dtile = nullptr;             // device tile prefix sums [ncases + 1]
+  int tile_bx = 0, tile_by = 0;     // tile shape of the current prefix sums
+  int total_tiles = 0;
+  int schedule = 0;                 // 0 per-step launches, 1 persistent, 2 launch per case
+  int variant = 6;
+  long long spin_limit = 1LL << 24; // polls of the grid barrier before giving up
+  unsigned *dbar = nullptr;         // barrier counter and generation
+  int *dstatus = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  std::vector<cudaEvent_t> ev;      // one per domain, for stream ordering
+  cudaEvent_t ev_batch = nullptr, ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+constexpr int kBatchGraphSteps = 64;
+
+void drop_batch_graph(lbm_batch *b) {
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+}
+
+// Tile prefix sums of all cases for a bx x by tile shape.
+lbm_status batch_tiles(lbm_batch *b, int bx, int by) {
+  if (b->tile_bx == bx && b->tile_by == by) return LBM_OK;
+  const int n = (int)b->doms.size();
+  std::vector<int> start(n + 1, 0);
+  for (int c = 0; c < n; ++c) {
+    const lbm_domain *d = b->doms[c];
+    const long long t = (long long)((d->nx + bx - 1) / bx) * ((d->ny + by - 1) / by);
+    if (start[c] + t > (1LL << 30)) return fail(LBM_EINVAL, "batch too large");
+    start[c + 1] = start[c] + (int)t;
+  }
+  CK(cudaStreamSynchronize(b->stream));
+  CK(cudaMemcpy(b->dtile, start.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
+  b->tile_bx = bx;
+  b->tile_by = by;
+  b->total_tiles = start[n];
+  drop_batch_graph(b);
+  return LBM_OK;
+}
+
+// Uploads the case table (arguments, buffers, current parity of each case).
+lbm_status batch_table(lbm_batch *b, int bx) {
+  CK(cudaStreamSynchronize(b->stream));   // the staging buffer is reused
+  for (size_t c = 0; c < b->doms.size(); ++c) {
+    lbm_domain *d = b->doms[c];
+    BatchCase &bc = b->hcases[c];
+    bc.a = make_args(d);
+    bc.pop[0] = d->pop[0];
+    bc.pop[1] = d->pop[1];
+    bc.mask = d->mask;
+    bc.mid = d->mid;
+    bc.pal = d->pal;
+    bc.cur0 = d->cur;
+    bc.tiles_x = (d->nx + bx - 1) / bx;
+  }
+  CK(cudaMemcpyAsync(b->dcases, b->hcases, sizeof(BatchCase) * b->doms.size(),
+                     cudaMemcpyHostToDevice, b->stream));
+  return LBM_OK;
+}
+
+// Orders the batch stream after (before) the work of every domain's stream.
+lbm_status batch_join_in(lbm_batch *b) {
+  for (size_t c = 0; c < b->doms.size(); ++c) {
+    CK(cudaEventRecord(b->ev[c], b->doms[c]->stream));
+    CK(cudaStreamWaitEvent(b->stream, b->ev[c], 0));
+  }
+  return LBM_OK;
+}
+lbm_status batch_join_out(lbm_batch *b) {
+  CK(cudaEventRecord(b->ev_batch, b->stream));
+  for (lbm_domain *d : b->doms) CK(cudaStreamWaitEvent(d->stream, b->ev_batch, 0));
+  return LBM_OK;
+}
+
+void batch_launch_steps(lbm_batch *b, int64_t n, int parity0) {
+  for (int64_t k = 0; k < n; ++k)
+    dispatch(b->precision, [&](auto *tag) {
+      using S = std::remove_pointer_t<decltype(tag)>;
+      launch_batch_step<S>(b->dcases, b->dtile, (int)b->doms.size(), b->total_tiles, b->variant,
+                           (int)((parity0 + k) & 1), b->stream);
+    });
+}
+
+lbm_status batch_run(lbm_batch *b, int64_t nsteps, bool fixed_parity) {
+  const int n = (int)b->doms.size();
+  if (b->schedule == 2) {              // one launch per case and step, no graph
+    for (int64_t k = 0; k < nsteps; ++k)
+      for (lbm_domain *d : b->doms) {
+        const KArgs a = make_args(d);
+        const int src = fixed_parity ? d->cur : (int)(d->cur ^ (k & 1));
+        dispatch(b->precision, [&](auto *tag) {
+          using S = std::remove_pointer_t<decltype(tag)>;
+          launch_step<S>(d->pop[src], d->pop[src ^ 1], geom(d), a, d->variant, b->stream);
+        });
+      }
+    CK(cudaGetLastError());
+    return LBM_OK;
+  }
+  if (b->schedule == 1) {              // persistent cooperative launch
+    lbm_status s = batch_tiles(b, kPersistBX, kPersistBY);
+    if (s != LBM_OK) return s;
+    if ((s = batch_table(b, kPersistBX)) != LBM_OK) return s;
+    CK(cudaMemsetAsync(b->dbar, 0, 2 * sizeof(unsigned), b->stream));
+    CK(cudaMemsetAsync(b->dstatus, 0, sizeof(int), b->stream));
+    int steps_arg = (int)nsteps;
+    if (fixed_parity) {
+      // trials: the same step again and again from each case's current state
+      for (int64_t k = 0; k < nsteps; ++k) {
+        cudaError_t e = cudaSuccess;
+        dispatch(b->precision, [&](auto *tag) {
+          using S = std::remove_pointer_t<decltype(tag)>;
+          e = launch_batch_persistent<S>(b->dcases, b->dtile, n, b->total_tiles, 1, b->dbar,
+                                         b->dstatus, b->spin_limit, b->stream);
+        });
+        if (e != cudaSuccess) return fail(LBM_ECUDA, "persistent launch: %s", cudaGetErrorString(e));
+        CK(cudaMemsetAsync(b->dbar, 0, 2 * sizeof(unsigned), b->stream));
+      }
+    } else {
+      cudaError_t e = cudaSuccess;
+      dispatch(b->precision, [&](auto *tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        e = launch_batch_persistent<S>(b->dcases, b->dtile, n, b->total_tiles, steps_arg, b->dbar,
+                                       b->dstatus, b->spin_limit, b->stream);
+      });
+      if (e != cudaSuccess) return fail(LBM_ECUDA, "persistent launch: %s", cudaGetErrorString(e));
+    }
+    int status = 0;
+    CK(cudaMemcpyAsync(&status, b->dstatus, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    if (status) {
+      for (lbm_domain *d : b->doms) d->have_state = false;
+      return fail(LBM_ETIMEOUT, "grid barrier gave up after %lld polls; states are undefined, "
+                  "reset or load them", b->spin_limit);
+    }
+    return LBM_OK;
+  }
+  // schedule 0: one launch per step over all tiles, replayed from a graph
+  const StepShape sh = kStepShapes[b->variant];
+  lbm_status s = batch_tiles(b, sh.bx, sh.by);
+  if (s != LBM_OK) return s;
+  if ((s = batch_table(b, sh.bx)) != LBM_OK) return s;
+  if (fixed_parity) {
+    for (int64_t k = 0; k < nsteps; ++k) batch_launch_steps(b, 1, 0);
+    CK(cudaGetLastError());
+    return LBM_OK;
+  }
+  int64_t left = nsteps;
+  while (left >= 2 * kBatchGraphSteps) {
+    if (!b->graph) {
+      cudaGraph_t gr = nullptr;
+      CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+      batch_launch_steps(b, kBatchGraphSteps, 0);
+      cudaError_t e = cudaStreamEndCapture(b->stream, &gr);
+      if (e != cudaSuccess) return fail(LBM_ECUDA, "batch graph capture: %s", cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&b->graph, gr, 0);
+      cudaGraphDestroy(gr);
+      if (e != cudaSuccess) return fail(LBM_ECUDA, "batch graph instantiate: %s", cudaGetErrorString(e));
+    }
+    CK(cudaGraphLaunch(b->graph, b->stream));   // even count: parity returns to 0
+    left -= kBatchGraphSteps;
+  }
+  batch_launch_steps(b, left, 0);
+  CK(cudaGetLastError());
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_create_batch(lbm_domain *const *domains, int32_t ncases, lbm_batch **out) {
+  if (!domains || !out || ncases < 1) return fail(LBM_EINVAL, "need at least one domain");
+  *out = nullptr;
+  for (int c = 0; c < ncases; ++c) {
+    lbm_status s = check_ready(domains[c]);
+    if (s != LBM_OK) return s;
+    if (domains[c]->desc.precision != domains[0]->desc.precision)
+      return fail(LBM_EINVAL, "batched domains must share one precision");
+    for (int k = 0; k < c; ++k)
+      if (domains[k] == domains[c]) return fail(LBM_EINVAL, "domain %d appears twice", c);
+  }
+  lbm_batch *b = new lbm_batch();
+  b->doms.assign(domains, domains + ncases);
+  b->precision = domains[0]->desc.precision;
+  b->stream = domains[0]->stream;
+  b->ev.resize(ncases, nullptr);
+  auto cleanup = [&](lbm_status s) { lbm_destroy_batch(b); return s; };
+  if (cudaMalloc(&b->dcases, sizeof(BatchCase) * ncases) != cudaSuccess ||
+      cudaMallocHost(&b->hcases, sizeof(BatchCase) * ncases) != cudaSuccess ||
+      cudaMalloc(&b->dtile, sizeof(int) * (ncases + 1)) != cudaSuccess ||
+      cudaMalloc(&b->dbar, 2 * sizeof(unsigned)) != cudaSuccess ||
+      cudaMalloc(&b->dstatus, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return cleanup(fail(LBM_ENOMEM, "batch tables"));
+  }
+  for (auto &e : b->ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      return cleanup(fail(LBM_ECUDA, "cudaEventCreate failed"));
+  if (cudaEventCreateWithFlags(&b->ev_batch, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess)
+    return cleanup(fail(LBM_ECUDA, "cudaEventCreate failed"));
+  *out = b;
+  return LBM_OK;
+}
+
+lbm_status lbm_destroy_batch(lbm_batch *b) {
+  if (!b) return LBM_OK;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  drop_batch_graph(b);
+  for (void *p : {(void *)b->dcases, (void *)b->dtile, (void *)b->dbar, (void *)b->dstatus})
+    if (p) cudaFree(p);
+  if (b->hcases) cudaFreeHost(b->hcases);
+  for (auto e : b->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto e : {b->ev_batch, b->ev0, b->ev1})
+    if (e) cudaEventDestroy(e);
+  delete b;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_set_schedule(lbm_batch *b, int32_t schedule, int32_t variant,
+                                  int64_t spin_limit) {
+  if (!b) return fail(LBM_EINVAL, "null batch");
+  if (schedule < 0 || schedule > 2) return fail(LBM_EINVAL, "schedule must be 0, 1 or 2");
+  if (variant < 0 || variant >= kStepVariants) return fail(LBM_EINVAL, "variant %d outside [0, %d)", variant, kStepVariants);
+  b->schedule = schedule;
+  if (b->variant != variant) drop_batch_graph(b);
+  b->variant = variant;
+  if (spin_limit > 0) b->spin_limit = spin_limit;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch *b, int64_t nsteps) {
+  if (!b) return fail(LBM_EINVAL, "null batch");
+  if (nsteps < 0 || nsteps > (1LL << 30)) return fail(LBM_EINVAL, "nsteps outside [0, 2^30]");
+  for (lbm_domain *d : b->doms) {
+    lbm_status s = check_ready(d);
+    if (s != LBM_OK) return s;
+  }
+  if (nsteps == 0) return LBM_OK;
+  lbm_status s = batch_join_in(b);
+  if (s != LBM_OK) return s;
+  if ((s = batch_run(b, nsteps, false)) != LBM_OK) return s;
+  for (lbm_domain *d : b->doms) {
+    d->cur ^= (int)(nsteps & 1);
+    d->steps += nsteps;
+  }
+  return batch_join_out(b);
+}
+
+lbm_status lbm_batch_time_steps(lbm_batch *b, int64_t nsteps, double *elapsed_ms) {
+  if (!b || !elapsed_ms) return fail(LBM_EINVAL, "null argument");
+  lbm_status s = batch_join_in(b);
+  if (s != LBM_OK) return s;
+  CK(cudaEventRecord(b->ev0, b->stream));
+  if ((s = lbm_batch_step(b, nsteps)) != LBM_OK) return s;
+  CK(cudaEventRecord(b->ev1, b->stream));
+  CK(cudaEventSynchronize(b->ev1));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+  *elapsed_ms = ms;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, int32_t *schedule, int32_t *variant,
+                          double *best_ms) {
+  if (!b || trial_steps < 1) return fail(LBM_EINVAL, "bad argument");
+  for (lbm_domain *d : b->doms) {
+    lbm_status s = check_ready(d);
+    if (s != LBM_OK) return s;
+    if (d->steps != 0) return fail(LBM_ESTATE, "lbm_batch_tune runs between lbm_reset and the first step");
+  }
+  lbm_status s = batch_join_in(b);
+  if (s != LBM_OK) return s;
+  const int keep_sched = b->schedule, keep_var = b->variant;
+  double best = 1e300;
+  int best_sched = 0, best_var = 0;
+  auto trial = [&](int sched, int var) -> lbm_status {
+    b->schedule = sched;
+    if (b->variant != var) drop_batch_graph(b);
+    b->variant = var;
+    lbm_status st = batch_run(b, 1, true);   // warm-up (tables, occupancy)
+    if (st != LBM_OK) return st;
+    CK(cudaEventRecord(b->ev0, b->stream));
+    if ((st = batch_run(b, trial_steps, true)) != LBM_OK) return st;
+    CK(cudaEventRecord(b->ev1, b->stream));
+    CK(cudaEventSynchronize(b->ev1));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+    if (ms / trial_steps < best) {
+      best = ms / trial_steps;
+      best_sched = sched;
+      best_var = var;
+    }
+    return LBM_OK;
+  };
+  for (int v = 0; v < kStepVariants && s == LBM_OK; ++v) s = trial(0, v);
+  if (s == LBM_OK) s = trial(1, 6);
+  // the trials wrote each case's next state into its other buffer: restore
+  for (lbm_domain *d : b->doms) {
+    const KArgs a = make_args(d);
+    dispatch(b->precision, [&](auto *tag) {
+      using S = std::remove_pointer_t<decltype(tag)>;
+      launch_init<S>(d->pop[d->cur ^ 1], geom(d), a, b->stream);
+    });
+  }
+  CK(cudaStreamSynchronize(b->stream));
+  if (s != LBM_OK) {
+    b->schedule = keep_sched;
+    b->variant = keep_var;
+    return s;
+  }
+  b->schedule = best_sched;
+  if (b->variant != best_var) drop_batch_graph(b);
+  b->variant = best_var;
+  if (schedule) *schedule = best_sched;
+  if (variant) *variant = best_var;
+  if (best_ms) *best_ms = best;
+  return batch_join_out(b);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
 // Residual without allocation.
 //
 // Some callers cannot call cudaMalloc when they need the steady-state

@@ -40,6 +40,24 @@ __device__ __forceinline__ double ld_r(const double *p) { return __ldg(p); }
 __device__ __forceinline__ float ld_r(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
 __device__ __forceinline__ float ld_r(const __half *p) { return __half2float(*p); }
 
+// Loads that bypass L1 (L2 only).  Within one launch L1 is not coherent
+// across SMs, so a kernel that reads, across a grid barrier, what other SMs
+// wrote must use these.
+__device__ __forceinline__ float ld_cg(const float *p) { return __ldcg(p); }
+__device__ __forceinline__ double ld_cg(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ float ld_cg(const __nv_bfloat16 *p) {
+  const unsigned short b = __ldcg(reinterpret_cast<const unsigned short *>(p));
+  return __bfloat162float(__ushort_as_bfloat16(b));
+}
+__device__ __forceinline__ float ld_cg(const __half *p) {
+  const unsigned short b = __ldcg(reinterpret_cast<const unsigned short *>(p));
+  return __half2float(__ushort_as_half(b));
+}
+template <bool CG, typename S> __device__ __forceinline__ auto ldp(const S *p) {
+  if constexpr (CG) return ld_cg(p);
+  else return ld_r(p);
+}
+
 __device__ __forceinline__ void st_r(float *p, float v) { *p = v; }
 __device__ __forceinline__ void st_r(double *p, double v) { *p = v; }
 __device__ __forceinline__ void st_r(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
@@ -81,6 +99,17 @@ struct KArgs {
   double hpo;               // temperature per unit O2 consumed (Eq. 15, 16)
 };
 
+// One case of a batched step (device table entry).
+struct BatchCase {
+  KArgs a;
+  const void *pop[2];       // the case's two population buffers
+  const uint8_t *mask;
+  const uint16_t *mid;
+  const void *pal;
+  int cur0;                 // buffer holding the state when the batched run starts
+  int tiles_x;              // tiles along x
+};
+
 // Velocity sets, Eq. 2 and Eq. 9 orders (folded by the compiler once the
 // loops over links are unrolled).
 #define EX9_TAB {0, 1, 0, -1, 0, 1, -1, -1, 1}
@@ -95,12 +124,13 @@ template <typename R> __device__ __forceinline__ R lam9(int i) {
   return i == 0 ? R(-5.0 / 3.0) : (i < 5 ? R(1.0 / 3.0) : R(1.0 / 12.0));
 }
 
-template <typename S> struct Pops {
+// Population planes of one buffer; CG selects L2-only loads.
+template <typename S, bool CG = false> struct Pops {
   const S *__restrict__ p;
   long long plane;
   int nxp;
   __device__ __forceinline__ auto at(int q, int x, int y) const {
-    return ld_r(p + (long long)q * plane + (long long)y * nxp + x);
+    return ldp<CG>(p + (long long)q * plane + (long long)y * nxp + x);
   }
 };
 
@@ -119,8 +149,8 @@ template <typename R> __device__ __forceinline__ R inlet_u(const KArgs &a, R yh)
 
 // Flow link i into cell (x, y) whose source may lie outside the fluid;
 // `v` is the interior pull already loaded for this link.
-template <typename S, typename R>
-__device__ R pull_flow_edge(const Pops<S> &src, const KArgs &a, const uint8_t *__restrict__ mask,
+template <typename S, typename R, bool CG = false>
+__device__ R pull_flow_edge(const Pops<S, CG> &src, const KArgs &a, const uint8_t *__restrict__ mask,
                             const uint16_t *__restrict__ mid, const MatCoef<R> *__restrict__ pal,
                             int i, int x, int y, uint8_t m, R v) {
   const int EX[9] = EX9_TAB, EY[9] = EY9_TAB, OP[9] = OP9_TAB;
@@ -156,8 +186,8 @@ __device__ R pull_flow_edge(const Pops<S> &src, const KArgs &a, const uint8_t *_
 
 // Scalar link i of scalar s into cell (x, y); the bottom wall returns the
 // insulated value and the reaction is applied afterwards.
-template <typename S, typename R>
-__device__ R pull_scalar_edge(const Pops<S> &src, const KArgs &a, const uint8_t *__restrict__ mask,
+template <typename S, typename R, bool CG = false>
+__device__ R pull_scalar_edge(const Pops<S, CG> &src, const KArgs &a, const uint8_t *__restrict__ mask,
                               const MatCoef<R> &mc, int s, int i, int x, int y, uint8_t m, R v) {
   const int EX[5] = {0, 1, 0, -1, 0}, EY[5] = {0, 0, 1, 0, -1}, OP[5] = {0, 3, 4, 1, 2};
   const int q = 9 + 5 * s;
@@ -209,8 +239,8 @@ __device__ __forceinline__ R d2q5_sum(R d0, R d1, R d2, R d3, R d4) {
   return d0 + ((d1 + d3) + (d2 + d4));
 }
 
-template <typename S, typename R>
-__device__ __forceinline__ R own_sum(const Pops<S> &src, int s, int x, int y) {
+template <typename S, typename R, bool CG = false>
+__device__ __forceinline__ R own_sum(const Pops<S, CG> &src, int s, int x, int y) {
   const int q = 9 + 5 * s;
   return d2q5_sum<R>(R(src.at(q, x, y)), R(src.at(q + 1, x, y)), R(src.at(q + 2, x, y)),
                      R(src.at(q + 3, x, y)), R(src.at(q + 4, x, y)));
@@ -219,10 +249,10 @@ __device__ __forceinline__ R own_sum(const Pops<S> &src, int s, int x, int y) {
 // Surface reaction of the thin film at a bottom cell (Sec. 4): the implicit
 // Tafel link.  Returns the O2 consumed J (lattice units) and modifies the
 // three upward links.  theta_n = T^n - T_in from the cell's own state.
-template <typename S, typename R>
-__device__ __forceinline__ R surface_reaction(const Pops<S> &src, const KArgs &a,
+template <typename S, typename R, bool CG = false>
+__device__ __forceinline__ R surface_reaction(const Pops<S, CG> &src, const KArgs &a,
                                               const MatCoef<R> &mc, int x, Cell<R> &c) {
-  R theta = own_sum<S, R>(src, 0, x, 0) + R(a.Cref[0] - a.T_in);
+  R theta = own_sum<S, R, CG>(src, 0, x, 0) + R(a.Cref[0] - a.T_in);
   R k = rate<R>(a, R(a.kA_surf), theta);
   R kappa = k / (R(2) * mc.w1[1]);
   R gdown = c.g[1][2] + R(a.wr1[1]) * R(a.Cref[1]);   // full g*_4 of O2 (bounced)
@@ -234,44 +264,44 @@ __device__ __forceinline__ R surface_reaction(const Pops<S> &src, const KArgs &a
 }
 
 // Volumetric catalyst sink of a catalyst cell (backward Euler in C).
-template <typename S, typename R>
-__device__ __forceinline__ R volume_sink(const Pops<S> &src, const KArgs &a, int x, int y) {
-  R theta = own_sum<S, R>(src, 0, x, y) + R(a.Cref[0] - a.T_in);
-  R C = own_sum<S, R>(src, 1, x, y) + R(a.Cref[1]);
+template <typename S, typename R, bool CG = false>
+__device__ __forceinline__ R volume_sink(const Pops<S, CG> &src, const KArgs &a, int x, int y) {
+  R theta = own_sum<S, R, CG>(src, 0, x, y) + R(a.Cref[0] - a.T_in);
+  R C = own_sum<S, R, CG>(src, 1, x, y) + R(a.Cref[1]);
   R k = rate<R>(a, R(a.kA_vol), theta);
   return -k * C / (R(1) + k);
 }
 
 // The 24 interior pulls of cell (x, y), issued without looking at the mask.
-template <typename S, typename R>
-__device__ __forceinline__ void load_interior(const Pops<S> &src, const KArgs &a, int x, int y,
+template <typename S, typename R, bool CG = false>
+__device__ __forceinline__ void load_interior(const Pops<S, CG> &src, const KArgs &a, int x, int y,
                                               Cell<R> &c) {
   const long long base = (long long)y * a.nxp + x, P = a.plane, W = a.nxp;
   const S *p = src.p + base;
-  c.f[0] = ld_r(p);
-  c.f[1] = ld_r(p + 1 * P - 1);
-  c.f[2] = ld_r(p + 2 * P - W);
-  c.f[3] = ld_r(p + 3 * P + 1);
-  c.f[4] = ld_r(p + 4 * P + W);
-  c.f[5] = ld_r(p + 5 * P - W - 1);
-  c.f[6] = ld_r(p + 6 * P - W + 1);
-  c.f[7] = ld_r(p + 7 * P + W + 1);
-  c.f[8] = ld_r(p + 8 * P + W - 1);
+  c.f[0] = ldp<CG>(p);
+  c.f[1] = ldp<CG>(p + 1 * P - 1);
+  c.f[2] = ldp<CG>(p + 2 * P - W);
+  c.f[3] = ldp<CG>(p + 3 * P + 1);
+  c.f[4] = ldp<CG>(p + 4 * P + W);
+  c.f[5] = ldp<CG>(p + 5 * P - W - 1);
+  c.f[6] = ldp<CG>(p + 6 * P - W + 1);
+  c.f[7] = ldp<CG>(p + 7 * P + W + 1);
+  c.f[8] = ldp<CG>(p + 8 * P + W - 1);
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
     const S *q = p + (9 + 5 * s) * P;
-    c.g[s][0] = ld_r(q);
-    c.g[s][1] = ld_r(q + 1 * P - 1);
-    c.g[s][2] = ld_r(q + 2 * P - W);
-    c.g[s][3] = ld_r(q + 3 * P + 1);
-    c.g[s][4] = ld_r(q + 4 * P + W);
+    c.g[s][0] = ldp<CG>(q);
+    c.g[s][1] = ldp<CG>(q + 1 * P - 1);
+    c.g[s][2] = ldp<CG>(q + 2 * P - W);
+    c.g[s][3] = ldp<CG>(q + 3 * P + 1);
+    c.g[s][4] = ldp<CG>(q + 4 * P + W);
   }
 }
 
 // Replaces the pulls of links that cross a wall, the inlet, the outlet, a
 // periodic seam or a solid grain (cells with any edge bit only).
-template <typename S, typename R>
-__device__ __forceinline__ void fix_edges(const Pops<S> &src, const KArgs &a,
+template <typename S, typename R, bool CG = false>
+__device__ __forceinline__ void fix_edges(const Pops<S, CG> &src, const KArgs &a,
                                           const uint8_t *__restrict__ mask,
                                           const uint16_t *__restrict__ mid,
                                           const MatCoef<R> *__restrict__ pal,
@@ -279,24 +309,24 @@ __device__ __forceinline__ void fix_edges(const Pops<S> &src, const KArgs &a,
                                           Cell<R> &c) {
 #pragma unroll
   for (int i = 1; i < 9; ++i)
-    c.f[i] = pull_flow_edge<S, R>(src, a, mask, mid, pal, i, x, y, m, c.f[i]);
+    c.f[i] = pull_flow_edge<S, R, CG>(src, a, mask, mid, pal, i, x, y, m, c.f[i]);
 #pragma unroll
   for (int s = 0; s < 3; ++s)
 #pragma unroll
     for (int i = 1; i < 5; ++i)
-      c.g[s][i] = pull_scalar_edge<S, R>(src, a, mask, mc, s, i, x, y, m, c.g[s][i]);
+      c.g[s][i] = pull_scalar_edge<S, R, CG>(src, a, mask, mc, s, i, x, y, m, c.g[s][i]);
 }
 
 // Pull all 24 populations of a non-solid cell (x, y).
-template <typename S, typename R>
-__device__ __forceinline__ void pull_cell(const Pops<S> &src, const KArgs &a,
+template <typename S, typename R, bool CG = false>
+__device__ __forceinline__ void pull_cell(const Pops<S, CG> &src, const KArgs &a,
                                           const uint8_t *__restrict__ mask,
                                           const uint16_t *__restrict__ mid,
                                           const MatCoef<R> *__restrict__ pal,
                                           const MatCoef<R> &mc, int x, int y, uint8_t m,
                                           Cell<R> &c) {
-  load_interior<S, R>(src, a, x, y, c);
-  if (m & M_EDGE) fix_edges<S, R>(src, a, mask, mid, pal, mc, x, y, m, c);
+  load_interior<S, R, CG>(src, a, x, y, c);
+  if (m & M_EDGE) fix_edges<S, R, CG>(src, a, mask, mid, pal, mc, x, y, m, c);
 }
 
 // Macroscopic values of a post-stream cell (Eq. 8, 11).

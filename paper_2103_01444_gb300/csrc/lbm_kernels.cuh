@@ -3,34 +3,35 @@
 // R = Real<S>::type (FP64 for double storage, FP32 otherwise); reductions
 // accumulate in FP64.
 #pragma once
+#include "lbm_adjoint.cuh"
 #include "lbm_core.cuh"
 #include "lbm_launch.h"
 
 namespace pemlbm {
 
 // ------------------------------------------------------------- step (K1)
-template <typename S, int BX, int BY, int MINB>
-__global__ void __launch_bounds__(BX * BY, MINB)
-k_step(const S *__restrict__ src_p, S *__restrict__ dst, const uint8_t *__restrict__ mask,
-       const uint16_t *__restrict__ mid, const MatCoef<typename Real<S>::type> *__restrict__ pal,
-       KArgs a) {
+// One coupled update of cell (x, y): src -> dst.  Shared by the single-
+// domain step and the batched steps.
+template <typename S, bool CG = false>
+__device__ __forceinline__ void cell_update(const S *__restrict__ src_p, S *__restrict__ dst,
+                                            const uint8_t *__restrict__ mask,
+                                            const uint16_t *__restrict__ mid,
+                                            const MatCoef<typename Real<S>::type> *__restrict__ pal,
+                                            const KArgs &a, int x, int y) {
   using R = typename Real<S>::type;
-  const int x = blockIdx.x * BX + (threadIdx.x % BX);
-  const int y = blockIdx.y * BY + (threadIdx.x / BX);
-  if (x >= a.nx || y >= a.ny) return;
   const long long c = (long long)y * a.nxp + x;
-  const Pops<S> src{src_p, a.plane, a.nxp};
+  const Pops<S, CG> src{src_p, a.plane, a.nxp};
   const uint8_t m = mask[c];
   Cell<R> cell;
-  load_interior<S, R>(src, a, x, y, cell);
+  load_interior<S, R, CG>(src, a, x, y, cell);
   // solid cells run the same arithmetic on their (unused) values and only
   // skip the stores, so no branch stands between the mask and the loads
   const bool live = (m & REG_MASK) != REG_SOLID;
   const MatCoef<R> mc = pal[mid[c]];
-  if (m & M_EDGE) fix_edges<S, R>(src, a, mask, mid, pal, mc, x, y, m, cell);
-  if (a.mode == 0 && (m & M_YLO)) surface_reaction<S, R>(src, a, mc, x, cell);
+  if (m & M_EDGE) fix_edges<S, R, CG>(src, a, mask, mid, pal, mc, x, y, m, cell);
+  if (a.mode == 0 && (m & M_YLO)) surface_reaction<S, R, CG>(src, a, mc, x, cell);
   R S_vol = 0;
-  if (a.mode == 1 && (m & REG_MASK) == REG_CATALYST) S_vol = volume_sink<S, R>(src, a, x, y);
+  if (a.mode == 1 && (m & REG_MASK) == REG_CATALYST) S_vol = volume_sink<S, R, CG>(src, a, x, y);
   const Macro<R> u = macros<R>(a, mc, cell);
   R o[9];
   collide_flow<R>(a, mc, u, cell.f, o);
@@ -48,6 +49,117 @@ k_step(const S *__restrict__ src_p, S *__restrict__ dst, const uint8_t *__restri
 #pragma unroll
       for (int i = 0; i < 5; ++i) st_r(out + (long long)(9 + 5 * s + i) * a.plane, g[i]);
     }
+  }
+}
+
+template <typename S, int BX, int BY, int MINB>
+__global__ void __launch_bounds__(BX * BY, MINB)
+k_step(const S *__restrict__ src_p, S *__restrict__ dst, const uint8_t *__restrict__ mask,
+       const uint16_t *__restrict__ mid, const MatCoef<typename Real<S>::type> *__restrict__ pal,
+       KArgs a) {
+  const int x = blockIdx.x * BX + (threadIdx.x % BX);
+  const int y = blockIdx.y * BY + (threadIdx.x / BX);
+  if (x >= a.nx || y >= a.ny) return;
+  cell_update<S>(src_p, dst, mask, mid, pal, a, x, y);
+}
+
+// ---------------------------------------------------- batched steps (K6)
+// Many cases of uneven size advance together.  The tiles of all cases (BX x
+// BY cells each) are numbered case after case; tile_start[c] is the first
+// tile of case c.  A block finds its case by binary search and stages that
+// case's arguments in shared memory.
+__device__ __forceinline__ int batch_case_of(const int *__restrict__ tile_start, int ncases, int t) {
+  int lo = 0, hi = ncases - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(tile_start + mid) <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void stage_args(const BatchCase *__restrict__ cases, int c, KArgs *sa) {
+  const int *srcw = reinterpret_cast<const int *>(&cases[c].a);
+  int *dstw = reinterpret_cast<int *>(sa);
+  for (int k = threadIdx.x; k < (int)(sizeof(KArgs) / sizeof(int)); k += blockDim.x)
+    dstw[k] = __ldg(srcw + k);
+}
+
+template <typename S, int BX, int BY, bool CG>
+__device__ __forceinline__ void batch_tile(const BatchCase *__restrict__ cases,
+                                           const int *__restrict__ tile_start, int ncases, int t,
+                                           int parity, KArgs *sa, int *sc) {
+  using R = typename Real<S>::type;
+  if (threadIdx.x == 0) *sc = batch_case_of(tile_start, ncases, t);
+  __syncthreads();
+  const int c = *sc;
+  stage_args(cases, c, sa);
+  __syncthreads();
+  const BatchCase &bc = cases[c];
+  const int tile = t - __ldg(tile_start + c);
+  const int tx = tile % bc.tiles_x, ty = tile / bc.tiles_x;
+  const int x = tx * BX + (threadIdx.x % BX), y = ty * BY + (threadIdx.x / BX);
+  const int cur = bc.cur0 ^ parity;
+  if (x < sa->nx && y < sa->ny)
+    cell_update<S, CG>((const S *)bc.pop[cur], (S *)bc.pop[cur ^ 1], bc.mask, bc.mid,
+                       (const MatCoef<R> *)bc.pal, *sa, x, y);
+  __syncthreads();   // the staged arguments are reused by the next tile
+}
+
+// One launch per step: one block per tile.
+template <typename S, int BX, int BY, int MINB>
+__global__ void __launch_bounds__(BX * BY, MINB)
+k_batch_step(const BatchCase *__restrict__ cases, const int *__restrict__ tile_start, int ncases,
+             int parity) {
+  __shared__ KArgs sa;
+  __shared__ int sc;
+  batch_tile<S, BX, BY, false>(cases, tile_start, ncases, blockIdx.x, parity, &sa, &sc);
+}
+
+// Grid-wide barrier of a cooperative launch.  Every wait is bounded: after
+// spin_limit polls the block raises *status and returns false, and so does
+// every block that later finds *status raised.
+__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned *gen, unsigned nblocks,
+                                             int *status, long long spin_limit) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *vgen = gen;
+    const unsigned g = *vgen;
+    __threadfence();
+    if (atomicAdd(count, 1u) == nblocks - 1) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*vgen == g) {
+        if (++spins > spin_limit) {
+          atomicExch(status, 1);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *((volatile int *)status) == 0;
+}
+
+// Persistent: nsteps steps in one cooperative launch of co-resident blocks,
+// each looping over tiles, a grid barrier between steps.  Population loads
+// bypass L1 (other SMs wrote them in the previous step).
+template <typename S, int BX, int BY, int MINB>
+__global__ void __launch_bounds__(BX * BY, MINB)
+k_batch_persistent(const BatchCase *__restrict__ cases, const int *__restrict__ tile_start,
+                   int ncases, int total_tiles, int nsteps, unsigned *bar, int *status,
+                   long long spin_limit) {
+  __shared__ KArgs sa;
+  __shared__ int sc;
+  for (int step = 0; step < nsteps; ++step) {
+    for (int t = blockIdx.x; t < total_tiles; t += gridDim.x)
+      batch_tile<S, BX, BY, true>(cases, tile_start, ncases, t, step & 1, &sa, &sc);
+    if (!grid_barrier(bar, bar + 1, gridDim.x, status, spin_limit)) return;
   }
 }
 
@@ -304,6 +416,82 @@ void launch_step(const void *src, void *dst, const DevGeom &g, const KArgs &a, i
   }
 }
 
+template <typename S, int V>
+void launch_batch_v(const BatchCase *cases, const int *tile_start, int ncases, int total_tiles,
+                    int parity, cudaStream_t st) {
+  constexpr StepShape sh = kStepShapes[V];
+  k_batch_step<S, sh.bx, sh.by, sh.minb><<<total_tiles, sh.bx * sh.by, 0, st>>>(
+      cases, tile_start, ncases, parity);
+}
+
+template <typename S>
+void launch_batch_step(const BatchCase *cases, const int *tile_start, int ncases, int total_tiles,
+                       int variant, int parity, cudaStream_t st) {
+  switch (variant) {
+    case 1: launch_batch_v<S, 1>(cases, tile_start, ncases, total_tiles, parity, st); break;
+    case 2: launch_batch_v<S, 2>(cases, tile_start, ncases, total_tiles, parity, st); break;
+    case 3: launch_batch_v<S, 3>(cases, tile_start, ncases, total_tiles, parity, st); break;
+    case 4: launch_batch_v<S, 4>(cases, tile_start, ncases, total_tiles, parity, st); break;
+    case 5: launch_batch_v<S, 5>(cases, tile_start, ncases, total_tiles, parity, st); break;
+    case 6: launch_batch_v<S, 6>(cases, tile_start, ncases, total_tiles, parity, st); break;
+    case 7: launch_batch_v<S, 7>(cases, tile_start, ncases, total_tiles, parity, st); break;
+    default: launch_batch_v<S, 0>(cases, tile_start, ncases, total_tiles, parity, st); break;
+  }
+}
+
+
+template <typename S>
+cudaError_t launch_batch_persistent(const BatchCase *cases, const int *tile_start, int ncases,
+                                    int total_tiles, int nsteps, unsigned *bar, int *status,
+                                    long long spin_limit, cudaStream_t st) {
+  auto kern = k_batch_persistent<S, kPersistBX, kPersistBY, kPersistMinB>;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPersistBX * kPersistBY, 0);
+  if (e != cudaSuccess) return e;
+  int grid = sms * per_sm;
+  if (grid > total_tiles) grid = total_tiles;
+  if (grid < 1) return cudaErrorInvalidConfiguration;
+  void *args[] = {(void *)&cases, (void *)&tile_start, (void *)&ncases, (void *)&total_tiles,
+                  (void *)&nsteps, (void *)&bar, (void *)&status, (void *)&spin_limit};
+  return cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(kPersistBX * kPersistBY),
+                                     args, 0, st);
+}
+
+template <typename R> AdjBufs<R> adj_bufs(const AdjPtrs &b) {
+  return AdjBufs<R>{(const R *)b.lam, (R *)b.M, (R *)b.O, (R *)b.V, b.gphi, b.gK, b.gD, b.gU,
+                    (R *)b.lam_out};
+}
+
+template <typename S>
+void launch_adj_local(const void *src, const DevGeom &g, const MatRaw *raw, const KArgs &a,
+                      int fickian, const AdjPtrs &b, long long seed_cell, cudaStream_t st) {
+  using R = typename Real<S>::type;
+  dim3 grid((a.nx + 127) / 128, a.ny);
+  k_adj_local<S><<<grid, 128, 0, st>>>((const S *)src, g.mask, g.mid, (const MatCoef<R> *)g.pal,
+                                       raw, a, fickian, adj_bufs<R>(b), seed_cell);
+}
+
+template <typename S>
+void launch_adj_gather(const DevGeom &g, const KArgs &a, const AdjPtrs &b, cudaStream_t st) {
+  using R = typename Real<S>::type;
+  dim3 grid((a.nx + 127) / 128, a.ny);
+  k_adj_gather<R><<<grid, 128, 0, st>>>(g.mask, g.mid, (const MatCoef<R> *)g.pal, a,
+                                        adj_bufs<R>(b));
+}
+
+template <typename S>
+void launch_adj_seed_current(const void *src, const DevGeom &g, const KArgs &a, int fickian,
+                             double weight, const AdjPtrs &b, cudaStream_t st) {
+  using R = typename Real<S>::type;
+  dim3 grid((a.nx + 127) / 128, a.ny);
+  k_adj_seed_current<S><<<grid, 128, 0, st>>>((const S *)src, g.mask, g.mid,
+                                              (const MatCoef<R> *)g.pal, a, fickian, weight,
+                                              adj_bufs<R>(b));
+}
+
 template <typename S>
 void launch_fields(const void *src, const DevGeom &g, const KArgs &a, double *out, cudaStream_t st) {
   dim3 grid((a.nx + 127) / 128, a.ny);
@@ -362,6 +550,16 @@ void launch_set_state(void *pop, const DevGeom &g, const KArgs &a, const double 
   template void launch_get_state<S>(const void *, const DevGeom &, const KArgs &, double *,     \
                                     cudaStream_t);                                              \
   template void launch_set_state<S>(void *, const DevGeom &, const KArgs &, const double *,     \
-                                    cudaStream_t);
+                                    cudaStream_t);                                              \
+  template void launch_batch_step<S>(const BatchCase *, const int *, int, int, int, int,        \
+                                     cudaStream_t);                                             \
+  template cudaError_t launch_batch_persistent<S>(const BatchCase *, const int *, int, int, int, \
+                                                  unsigned *, int *, long long, cudaStream_t);  \
+  template void launch_adj_local<S>(const void *, const DevGeom &, const MatRaw *, const KArgs &, \
+                                    int, const AdjPtrs &, long long, cudaStream_t);             \
+  template void launch_adj_gather<S>(const DevGeom &, const KArgs &, const AdjPtrs &,            \
+                                     cudaStream_t);                                             \
+  template void launch_adj_seed_current<S>(const void *, const DevGeom &, const KArgs &, int,    \
+                                           double, const AdjPtrs &, cudaStream_t);
 
 }  // namespace pemlbm

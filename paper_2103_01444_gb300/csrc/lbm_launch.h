@@ -19,8 +19,14 @@ constexpr StepShape kStepShapes[kStepVariants] = {
     {128, 2, 1}, {128, 2, 3}, {128, 2, 4}, {64, 4, 4},
     {256, 1, 4}, {32, 8, 4}, {128, 1, 8}, {64, 2, 8}};
 constexpr int kReduceThreads = 512;
+// Persistent batched step: 128 x 1 cells per block, 8 blocks per SM asked of
+// the register allocator; the grid is the number of co-resident blocks.
+constexpr int kPersistBX = 128, kPersistBY = 1, kPersistMinB = 8;
 constexpr int kResidualBX = 128, kResidualBY = 2;      // residual blocks
 constexpr int kCatalystBX = 32, kCatalystBY = 8;       // catalyst reduction blocks
+
+// One case of a batched step: its arguments, buffers and geometry.
+struct BatchCase;
 
 // Device-resident geometry shared by all kernels of a domain.
 struct DevGeom {
@@ -40,6 +46,20 @@ inline int residual_blocks(int nx, int ny) {
 template <typename S> void launch_init(void *pop, const DevGeom &g, const KArgs &a, cudaStream_t st);
 template <typename S> void launch_get_state(const void *pop, const DevGeom &g, const KArgs &a, double *out, cudaStream_t st);
 template <typename S> void launch_set_state(void *pop, const DevGeom &g, const KArgs &a, const double *in, cudaStream_t st);
+
+template <typename S> void launch_batch_step(const BatchCase *cases, const int *tile_start, int ncases, int total_tiles, int variant, int parity, cudaStream_t st);
+template <typename S> cudaError_t launch_batch_persistent(const BatchCase *cases, const int *tile_start, int ncases, int total_tiles, int nsteps, unsigned *bar, int *status, long long spin_limit, cudaStream_t st);
+
+// Buffers of one reverse step (types follow the domain's arithmetic).
+struct AdjPtrs {
+  const void *lam;
+  void *M, *O, *V;
+  double *gphi, *gK, *gD, *gU;
+  void *lam_out;
+};
+template <typename S> void launch_adj_local(const void *src, const DevGeom &g, const MatRaw *raw, const KArgs &a, int fickian, const AdjPtrs &b, long long seed_cell, cudaStream_t st);
+template <typename S> void launch_adj_gather(const DevGeom &g, const KArgs &a, const AdjPtrs &b, cudaStream_t st);
+template <typename S> void launch_adj_seed_current(const void *src, const DevGeom &g, const KArgs &a, int fickian, double weight, const AdjPtrs &b, cudaStream_t st);
 
 // Node mask from the geometry (solid may be NULL).
 void launch_build_mask(uint8_t *mask, const uint8_t *solid, int nx, int ny, int nxp, int ny_cl,

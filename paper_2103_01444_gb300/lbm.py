@@ -24,7 +24,9 @@ EXPORTS = ("lbm_create_domain", "lbm_destroy_domain", "lbm_set_params", "lbm_set
            "lbm_reset", "lbm_step", "lbm_current_density", "lbm_residual", "lbm_get_fields",
            "lbm_get_state", "lbm_set_state", "lbm_get_mask", "lbm_get_step", "lbm_save_state",
            "lbm_load_state", "lbm_time_steps", "lbm_bytes_per_cell", "lbm_tune",
-           "lbm_set_variant", "lbm_residual_noalloc", "lbm_last_error")
+           "lbm_set_variant", "lbm_residual_noalloc", "lbm_create_batch", "lbm_destroy_batch",
+           "lbm_batch_set_schedule", "lbm_batch_tune", "lbm_batch_step", "lbm_batch_time_steps",
+           "lbm_grad", "lbm_vjp", "lbm_last_error")
 
 
 class LbmError(RuntimeError):
@@ -85,6 +87,14 @@ def load_library(path: str = LIB_PATH):
         "lbm_tune": [P, C.c_int32, C.POINTER(C.c_int32), d],
         "lbm_set_variant": [P, C.c_int32],
         "lbm_residual_noalloc": [P, C.c_void_p, d],
+        "lbm_create_batch": [C.POINTER(P), C.c_int32, C.POINTER(P)],
+        "lbm_destroy_batch": [P],
+        "lbm_batch_set_schedule": [P, C.c_int32, C.c_int32, C.c_int64],
+        "lbm_batch_tune": [P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), d],
+        "lbm_batch_step": [P, C.c_int64],
+        "lbm_batch_time_steps": [P, C.c_int64, d],
+        "lbm_grad": [P, C.c_int32, C.c_int64, C.c_int32, d, d, d, d, d],
+        "lbm_vjp": [P, d, d, d, d, d, d],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -204,6 +214,28 @@ class Domain:
         _check(self.L.lbm_residual_noalloc(self.h, C.c_void_p(snapshot.data_ptr()), C.byref(r)))
         return r.value
 
+    def grad(self, objective: int = 0, nsteps: int = 100, segment: int = 0):
+        """Objective after nsteps from the current state and its gradient:
+        (J, {"phi", "K", "D_O2": [ny][nx] arrays, "u_in": float})."""
+        J, du = C.c_double(), C.c_double()
+        g = {k: np.zeros((self.ny, self.nx)) for k in ("phi", "K", "D_O2")}
+        _check(self.L.lbm_grad(self.h, int(objective), int(nsteps), int(segment), C.byref(J),
+                               _dp(g["phi"]), _dp(g["K"]), _dp(g["D_O2"]), C.byref(du)))
+        g["u_in"] = du.value
+        return J.value, g
+
+    def vjp(self, lam_next):
+        """One transposed step at the current state: (lam_prev, gradients)."""
+        lam = np.ascontiguousarray(lam_next, np.float64)
+        assert lam.shape == (24, self.ny, self.nx)
+        out = np.zeros_like(lam)
+        du = C.c_double()
+        g = {k: np.zeros((self.ny, self.nx)) for k in ("phi", "K", "D_O2")}
+        _check(self.L.lbm_vjp(self.h, _dp(lam), _dp(out), _dp(g["phi"]), _dp(g["K"]),
+                              _dp(g["D_O2"]), C.byref(du)))
+        g["u_in"] = du.value
+        return out, g
+
     def fields(self, out=None):
         """dict of [ny][nx] float64 arrays ux, uy, p, T, C_O2, C_H2O; with a
         CUDA tensor ``out`` of shape (6, ny, nx) float64 they are written there
@@ -255,3 +287,82 @@ class Domain:
         b = C.c_double()
         _check(self.L.lbm_bytes_per_cell(self.h, C.byref(b)))
         return b.value
+
+
+class Batch:
+    """Many domains stepped together (lbm_create_batch); the domains stay
+    usable through their own methods."""
+
+    SCHEDULES = {"graph": 0, "persistent": 1, "per-case": 2}
+
+    def __init__(self, domains):
+        self.L = load_library()
+        self.domains = list(domains)
+        arr = (C.c_void_p * len(self.domains))(*[d.h for d in self.domains])
+        h = C.c_void_p()
+        _check(self.L.lbm_create_batch(arr, len(self.domains), C.byref(h)))
+        self.h = h
+
+    def set_schedule(self, schedule, variant: int = 6, spin_limit: int = 0):
+        sch = self.SCHEDULES.get(schedule, schedule)
+        _check(self.L.lbm_batch_set_schedule(self.h, int(sch), int(variant), int(spin_limit)))
+
+    def tune(self, trial_steps: int = 10):
+        sch, var, ms = C.c_int32(), C.c_int32(), C.c_double()
+        _check(self.L.lbm_batch_tune(self.h, int(trial_steps), C.byref(sch), C.byref(var),
+                                     C.byref(ms)))
+        return sch.value, var.value, ms.value
+
+    def step(self, n: int = 1):
+        _check(self.L.lbm_batch_step(self.h, int(n)))
+        return self
+
+    def time_steps(self, n: int) -> float:
+        ms = C.c_double()
+        _check(self.L.lbm_batch_time_steps(self.h, int(n), C.byref(ms)))
+        return ms.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.lbm_destroy_batch(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cathode_objective():
+    """torch.autograd.Function over the lattice material and inlet velocity:
+    CathodeObjective.apply(phi, K, D_O2, u_in, domain, fields, params,
+    objective, nsteps, segment) sets the domain's material (phi, K, D_O2 from
+    the tensors, alpha_T, D_H2O, rho_cp_ratio from `fields`) and u_in_avg,
+    resets it, and returns the objective after nsteps; backward returns the
+    adjoint gradients computed by lbm_grad."""
+    import torch
+
+    class CathodeObjective(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, phi, K, D_O2, u_in, domain, fields, params, objective, nsteps, segment):
+            p = dict(params)
+            p["u_in_avg"] = float(u_in)
+            domain.set_params(p)
+            domain.set_fields(phi.detach().cpu().double().numpy(), K.detach().cpu().double().numpy(),
+                              fields["alpha_T"], D_O2.detach().cpu().double().numpy(),
+                              fields["D_H2O"], fields.get("rho_cp_ratio"))
+            domain.reset()
+            J, g = domain.grad(objective, nsteps, segment)
+            dev = phi.device
+            ctx.save_for_backward(torch.from_numpy(g["phi"]).to(dev), torch.from_numpy(g["K"]).to(dev),
+                                  torch.from_numpy(g["D_O2"]).to(dev),
+                                  torch.tensor(g["u_in"], dtype=torch.float64, device=dev))
+            return torch.tensor(J, dtype=torch.float64, device=dev)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            gphi, gK, gD, gU = ctx.saved_tensors
+            return gJ * gphi, gJ * gK, gJ * gD, gJ * gU, None, None, None, None, None, None
+
+    return CathodeObjective

@@ -1,0 +1,97 @@
+"""Batched stepping of uneven cases (operating-point sweeps): every schedule
+must give the same states as stepping each case on its own."""
+import numpy as np
+import pytest
+
+from paper_2103_01444_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def cases():
+    out = []
+    for k, (nx, ny, mode, V) in enumerate([(96, 32, 1, 0.35), (160, 24, 0, 0.6),
+                                           (64, 40, 1, 0.8), (130, 48, 0, 0.45),
+                                           (200, 16, 1, 0.5)]):
+        c = workloads.small_cathode(nx=nx, ny=ny, reaction_mode=mode, V_op=V, seed=k)
+        out.append(c)
+    return out
+
+
+def domains(precision="fp32", interface_mode=0):
+    from paper_2103_01444_gb300.build import build
+    from paper_2103_01444_gb300.lbm import Domain
+    build()
+    return [Domain.from_case(c, precision=precision, interface_mode=interface_mode)
+            for c in cases()]
+
+
+@pytest.mark.parametrize("schedule", ["graph", "persistent", "per-case"])
+def test_batched_states_equal_individual_steps(schedule):
+    from paper_2103_01444_gb300.lbm import Batch
+    ref = domains()
+    for d in ref:
+        d.step(150)
+    ds = domains()
+    b = Batch(ds)
+    b.set_schedule(schedule, variant=6)
+    b.step(150)          # 150 >= 128: the graph schedule replays its graph
+    b.step(1)            # odd counts flip each case's buffer
+    for d in ref:
+        d.step(1)
+    for d, r in zip(ds, ref):
+        assert d.steps == r.steps == 151
+        np.testing.assert_array_equal(d.state(), r.state())
+        assert d.current_density()[0] == r.current_density()[0]
+
+
+def test_batch_tune_keeps_states_and_picks_a_schedule():
+    from paper_2103_01444_gb300.lbm import Batch
+    ds = domains()
+    ref = domains()
+    b = Batch(ds)
+    sch, var, ms = b.tune(3)
+    assert sch in (0, 1) and 0 <= var < 8 and ms > 0
+    for d, r in zip(ds, ref):
+        np.testing.assert_array_equal(d.state(), r.state())
+    b.step(20)
+    for r in ref:
+        r.step(20)
+    for d, r in zip(ds, ref):
+        np.testing.assert_array_equal(d.state(), r.state())
+
+
+def test_grid_barrier_gives_up_and_the_context_survives():
+    """A barrier allowed a single poll gives up: the call returns ETIMEOUT
+    (no hang, no fault), the states are marked undefined, and after a reset
+    the same batch steps normally."""
+    from paper_2103_01444_gb300.lbm import Batch, LbmError
+    ds = domains()
+    b = Batch(ds)
+    b.set_schedule("persistent", spin_limit=1)
+    with pytest.raises(LbmError, match="ETIMEOUT"):
+        b.step(40)
+    with pytest.raises(LbmError, match="ESTATE"):
+        ds[0].step(1)
+    for d in ds:
+        d.reset()
+    b.set_schedule("persistent", spin_limit=1 << 24)
+    b.step(10)
+    ref = domains()
+    for r in ref:
+        r.step(10)
+    for d, r in zip(ds, ref):
+        np.testing.assert_array_equal(d.state(), r.state())
+
+
+def test_batch_rejects_mixed_precision_and_unready_domains():
+    from paper_2103_01444_gb300.lbm import Batch, Domain, LbmError
+    ds = domains()
+    other = domains("fp64")[0]
+    with pytest.raises(LbmError, match="EINVAL"):
+        Batch([ds[0], other])
+    with pytest.raises(LbmError, match="EINVAL"):
+        Batch([ds[0], ds[0]])
+    fresh = Domain(32, 16, ny_gdl=8)
+    with pytest.raises(LbmError, match="ESTATE"):
+        Batch([ds[0], fresh])
