@@ -1,0 +1,596 @@
+// Discrete adjoint of the coupled step (reverse mode, hand-written).
+//
+// The step maps the post-collision state s^{n-1} to s^n cell by cell:
+// s^n(x) = C_x(P_x(s^{n-1}), theta_x), where P_x pulls the 24 populations
+// (plain links from neighbours, boundary links from the cell itself, the
+// outlet's virtual cells, the inlet velocity) and C_x relaxes them (Eq. 1,
+// 8, 10) with the catalyst terms (Eq. 12-17).  The transpose is applied in
+// two kernels per step:
+//   k_adj_local (one thread per cell x): recomputes the forward update of x
+//     from s^{n-1}, back-propagates lambda^n(x) through C_x, and splits the
+//     result over the pull: the adjoint of each plain link goes to M(x, q),
+//     the adjoint of values x took from its own state goes to O(x, q), the
+//     outlet's uses of the cells above and below go to the outlet buffers,
+//     and the parameter adjoints of x accumulate in FP64.
+//   k_adj_gather (one thread per cell y): lambda^{n-1}(y, q) = M(y + e_q, q)
+//     when that neighbour is fluid (every plain link has exactly one
+//     consumer), plus O(y, q), plus the outlet contributions.
+// Storage is the domain's storage type S; arithmetic is R.
+#pragma once
+#include "lbm_core.cuh"
+
+namespace pemlbm {
+
+// Per-step adjoint workspace (device pointers).
+template <typename R> struct AdjBufs {
+  const R *lam;      // lambda^n, [24][plane] (deviation coordinates = full coordinates)
+  R *M;              // pull adjoints [24][plane]
+  R *O;              // own-use adjoints [24][plane]
+  R *V;              // outlet column: [2][10][ny] (down: from y+1 to y, up: from y-1 to y)
+  double *gphi, *gK, *gD;   // per-cell parameter gradients [plane]
+  double *gU;               // d objective / d u_in_avg
+  R *lam_out;        // lambda^{n-1} [24][plane]
+};
+
+// Adjoint of the D2Q5 collision of scalar s (collide_scalar).  Given the
+// output adjoints lo[5], accumulates into ld[5] (pulled values), lux, luy,
+// and the adjoints of the source, b, w1 and q1.
+template <typename R>
+__device__ __forceinline__ void collide_scalar_rev(const KArgs &a, const MatCoef<R> &mc, int s,
+                                                   R ux, R uy, R Cdev, const R d[5], R srcv,
+                                                   const R lo[5], R ld[5], R &lux, R &luy,
+                                                   R &lsrc, R &lb, R &lw1, R &lq1) {
+  const R Q1 = mc.q1[s], Q3 = R(a.Q3), b = mc.b[s], w1 = mc.w1[s], w0 = R(1) - R(4) * w1;
+  const R C = Cdev + R(a.Cref[s]);
+  const R n1 = d[1] - d[3], n2 = d[2] - d[4];
+  const R e13 = d[1] + d[3], e24 = d[2] + d[4];
+  const R n3 = R(-4) * d[0] + (e13 + e24);
+  // outputs: o0 = 0.2 (n0 - n3') + w0 src; o1,3 = ev +- 0.25 n4' ... (see forward)
+  const R lex = lo[1] + lo[3], ley = lo[2] + lo[4];
+  const R ln1p = R(0.5) * (lo[1] - lo[3]), ln2p = R(0.5) * (lo[2] - lo[4]);
+  const R lev = lex + ley, ln4p = R(0.25) * (lex - ley);
+  R ln0 = R(0.2) * lev + R(0.2) * lo[0];
+  const R ln3p = R(0.05) * lev - R(0.2) * lo[0];
+  lw1 += srcv * lev - R(4) * srcv * lo[0];
+  lsrc += w1 * lev + w0 * lo[0];
+  const R ln4 = (R(1) - Q3) * ln4p;
+  const R ln3 = (R(1) - Q3) * ln3p;
+  lb += Q3 * C * ln3p;
+  R lC = Q3 * b * ln3p;
+  const R ln1 = (R(1) - Q1) * ln1p, ln2 = (R(1) - Q1) * ln2p;
+  lux += Q1 * C * ln1p;
+  luy += Q1 * C * ln2p;
+  lC += Q1 * ux * ln1p + Q1 * uy * ln2p;
+  lq1 += (ux * C - n1) * ln1p + (uy * C - n2) * ln2p;
+  const R lCdev = lC + ln0;
+  const R le13 = ln3 + ln4, le24 = ln3 - ln4;
+  ld[0] += R(-4) * ln3 + lCdev;
+  ld[1] += ln1 + le13 + lCdev;
+  ld[3] += -ln1 + le13 + lCdev;
+  ld[2] += ln2 + le24 + lCdev;
+  ld[4] += -ln2 + le24 + lCdev;
+  (void)n3;
+}
+
+// Adjoint of collide_flow + the flow part of macros (Eq. 1, 3-8).  Given the
+// output adjoints lo[9] and the adjoints lux, luy of the velocity coming
+// from the scalar collisions, accumulates ld[9] and the adjoints of phi
+// (direct), darcy, forch, l0, l1 and 1/phi.
+template <typename R>
+__device__ __forceinline__ void flow_rev(const KArgs &a, const MatCoef<R> &mc, const R d[9],
+                                         const R lo[9], R lux_in, R luy_in, R ld[9], R &lphi,
+                                         R &ldarcy, R &lforch, R &ll0, R &ll1, R &lip) {
+  const R sn = R(a.s_nu), sq = R(a.s_q), g = R(a.body_g), ip = mc.inv_phi;
+  // ---- forward recomputation of the macroscopic values (macros)
+  const R vx = d[1] - d[3] + d[5] - d[6] - d[7] + d[8] + R(0.5) * mc.phi * g;
+  const R vy = d[2] - d[4] + d[5] + d[6] - d[7] - d[8];
+  const R vn = sqrt(vx * vx + vy * vy);
+  const R rr = sqrt(mc.l0 * mc.l0 + mc.l1 * vn);
+  const R den = mc.l0 + rr;
+  const R ux = vx / den, uy = vy / den;
+  const R s18 = ((d[1] + d[3]) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8]));
+  const R u2 = ux * ux + uy * uy, un = sqrt(u2);
+  const R P = R(0.6) * s18 - R(0.4) * u2 * ip;
+  const R Fx = -mc.darcy * ux - mc.forch * un * ux + mc.phi * g;
+  const R Fy = -mc.darcy * uy - mc.forch * un * uy;
+  const R uF = ux * Fx + uy * Fy;
+  const R hn = R(1) - R(0.5) * sn, hq = R(1) - R(0.5) * sq;
+  // ---- back through f* = M^T diag(1/n) m*
+  R la[9];
+  la[0] = lo[0] + lo[1] + lo[2] + lo[3] + lo[4] + lo[5] + lo[6] + lo[7] + lo[8];
+  la[1] = R(-4) * lo[0] - (lo[1] + lo[2] + lo[3] + lo[4]) + R(2) * (lo[5] + lo[6] + lo[7] + lo[8]);
+  la[2] = R(4) * lo[0] - R(2) * (lo[1] + lo[2] + lo[3] + lo[4]) + (lo[5] + lo[6] + lo[7] + lo[8]);
+  la[3] = lo[1] - lo[3] + lo[5] - lo[6] - lo[7] + lo[8];
+  la[4] = R(-2) * (lo[1] - lo[3]) + lo[5] - lo[6] - lo[7] + lo[8];
+  la[5] = lo[2] - lo[4] + lo[5] + lo[6] - lo[7] - lo[8];
+  la[6] = R(-2) * (lo[2] - lo[4]) + lo[5] + lo[6] - lo[7] - lo[8];
+  la[7] = lo[1] - lo[2] + lo[3] - lo[4];
+  la[8] = lo[5] - lo[6] + lo[7] - lo[8];
+  const R lm0p = la[0] * R(1.0 / 9), lm1p = la[1] * R(1.0 / 36), lm2p = la[2] * R(1.0 / 36);
+  const R lm3p = la[3] * R(1.0 / 6), lm4p = la[4] * R(1.0 / 12), lm5p = la[5] * R(1.0 / 6);
+  const R lm6p = la[6] * R(1.0 / 12), lm7p = la[7] * R(0.25), lm8p = la[8] * R(0.25);
+  // ---- back through m* = m - S (m - m_eq) + (1 - S/2) G
+  R lm[9];
+  lm[0] = (R(1) - sn) * lm0p;
+  lm[1] = (R(1) - sn) * lm1p;
+  lm[2] = (R(1) - sn) * lm2p;
+  lm[3] = lm3p;
+  lm[4] = (R(1) - sq) * lm4p;
+  lm[5] = lm5p;
+  lm[6] = (R(1) - sq) * lm6p;
+  lm[7] = (R(1) - sn) * lm7p;
+  lm[8] = (R(1) - sn) * lm8p;
+  R lP = R(6) * sn * lm1p - R(9) * sn * lm2p;
+  R lu2 = R(3) * sn * ip * lm1p - R(3) * sn * ip * lm2p;
+  R luF = R(6) * hn * ip * lm1p - R(6) * hn * ip * lm2p;
+  lip += R(3) * sn * u2 * lm1p + R(6) * hn * uF * lm1p - R(3) * sn * u2 * lm2p -
+         R(6) * hn * uF * lm2p;
+  R lFx = lm3p - hq * lm4p, lFy = lm5p - hq * lm6p;
+  R lux = lux_in - sq * lm4p, luy = luy_in - sq * lm6p;
+  // m7: E = (ux^2 - uy^2) ip, H = 2 (ux Fx - uy Fy) ip
+  lux += sn * R(2) * ux * ip * lm7p + hn * R(2) * Fx * ip * lm7p;
+  luy += -sn * R(2) * uy * ip * lm7p - hn * R(2) * Fy * ip * lm7p;
+  lFx += hn * R(2) * ux * ip * lm7p;
+  lFy += -hn * R(2) * uy * ip * lm7p;
+  lip += sn * (ux * ux - uy * uy) * lm7p + hn * R(2) * (ux * Fx - uy * Fy) * lm7p;
+  // m8: E = ux uy ip, H = (ux Fy + uy Fx) ip
+  lux += sn * uy * ip * lm8p + hn * Fy * ip * lm8p;
+  luy += sn * ux * ip * lm8p + hn * Fx * ip * lm8p;
+  lFy += hn * ux * ip * lm8p;
+  lFx += hn * uy * ip * lm8p;
+  lip += sn * ux * uy * lm8p + hn * (ux * Fy + uy * Fx) * lm8p;
+  // uF = ux Fx + uy Fy
+  lux += Fx * luF;
+  luy += Fy * luF;
+  lFx += ux * luF;
+  lFy += uy * luF;
+  // u2 in the energy equilibria
+  lux += R(2) * ux * lu2;
+  luy += R(2) * uy * lu2;
+  // F = -darcy u - forch |u| u + phi g x
+  const R lFu = ux * lFx + uy * lFy;
+  lux += (-mc.darcy - mc.forch * un) * lFx;
+  luy += (-mc.darcy - mc.forch * un) * lFy;
+  const R lun = -mc.forch * lFu;
+  ldarcy += -lFu;
+  lforch += -un * lFu;
+  lphi += g * lFx;
+  if (un > R(0)) {
+    lux += ux / un * lun;
+    luy += uy / un * lun;
+  }
+  // P = 0.6 s18 - 0.4 |u|^2 ip
+  const R ls18 = R(0.6) * lP;
+  lux += R(-0.8) * ux * ip * lP;
+  luy += R(-0.8) * uy * ip * lP;
+  lip += R(-0.4) * u2 * lP;
+  // u = v / (l0 + sqrt(l0^2 + l1 |v|))
+  const R lden = -(ux * lux + uy * luy) / den;
+  R lvx = lux / den, lvy = luy / den;
+  if (vn > R(0)) {
+    const R dr = mc.l1 / (R(2) * rr) * lden;   // d den / d vn = l1 / (2 rr)
+    lvx += dr * vx / vn;
+    lvy += dr * vy / vn;
+  }
+  ll0 += lden * (R(1) + mc.l0 / rr);
+  ll1 += lden * vn / (R(2) * rr);
+  lphi += R(0.5) * g * lvx;
+  // moments and velocity back to the pulled populations
+  const int EX[9] = EX9_TAB, EY[9] = EY9_TAB;
+  const R M1[9] = {-4, -1, -1, -1, -1, 2, 2, 2, 2};
+  const R M2[9] = {4, -2, -2, -2, -2, 1, 1, 1, 1};
+  const R M4[9] = {0, -2, 0, 2, 0, 1, -1, -1, 1};
+  const R M6[9] = {0, 0, -2, 0, 2, 1, 1, -1, -1};
+  const R M7[9] = {0, 1, -1, 1, -1, 0, 0, 0, 0};
+  const R M8[9] = {0, 0, 0, 0, 0, 1, -1, 1, -1};
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    ld[i] += lm[0] + M1[i] * lm[1] + M2[i] * lm[2] + R(EX[i]) * (lm[3] + lvx) + M4[i] * lm[4] +
+             R(EY[i]) * (lm[5] + lvy) + M6[i] * lm[6] + M7[i] * lm[7] + M8[i] * lm[8] +
+             (i > 0 ? ls18 : R(0));
+  }
+}
+
+// d k / d theta of the rate k = A exp(e_in - c1 theta / (T T_in)): -c1 k / T^2.
+template <typename R> __device__ __forceinline__ R drate_dtheta(const KArgs &a, R k, R theta) {
+  const R T = R(a.T_in) + theta;
+  return -R(a.k_c1) * k / (T * T);
+}
+
+// Adds lam_theta to the five own T populations and lam_C to the own O2 ones.
+template <typename R>
+__device__ __forceinline__ void own_sums_rev(R *__restrict__ O, long long c, long long P,
+                                             R lam_theta, R lam_C) {
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    O[(9 + k) * P + c] += lam_theta;
+    O[(14 + k) * P + c] += lam_C;
+  }
+}
+
+// Parameter chain of one cell: adjoints of the derived coefficients to the
+// caller's fields phi, K and D_O2 (Eq. 7, 8, 10).
+template <typename R>
+__device__ __forceinline__ void param_rev(const KArgs &a, const MatCoef<R> &mc, const MatRaw &raw,
+                                          int fickian, R lphi, R ldarcy, R lforch, R ll0, R ll1,
+                                          R lip, R lbO2, R lw1O2, R lq1O2, double &gphi,
+                                          double &gK, double &gD) {
+  ldarcy += R(0.25) * ll0;
+  lforch += R(0.5) * ll1;
+  double dphi = (double)lphi - (double)lip * (double)mc.inv_phi * (double)mc.inv_phi;
+  double dK = 0.0;
+  if (!isinf(raw.K)) {
+    dphi += (double)ldarcy * (double)mc.darcy / raw.phi - 0.5 * (double)lforch * (double)mc.forch / raw.phi;
+    dK = -(double)ldarcy * (double)mc.darcy / raw.K - 0.5 * (double)lforch * (double)mc.forch / raw.K;
+  }
+  const double sqrt3 = 1.7320508075688772;
+  double dD;
+  if (fickian) {
+    const double q1 = (double)mc.q1[1], b0 = (double)mc.b[1];
+    dD = (double)lq1O2 * (-q1 * q1 * 10.0 / (4.0 + b0));
+  } else {
+    dD = (double)lbO2 * 20.0 * sqrt3 + (double)lw1O2 * sqrt3;
+  }
+  gphi += dphi;
+  gK += dK;
+  gD += dD;
+}
+
+}  // namespace pemlbm
+
+namespace pemlbm {
+
+// Inlet parabola derivative: d u_in(yh) / d u_in_avg.
+template <typename R> __device__ __forceinline__ R dinlet_du(const KArgs &a, R yh) {
+  R s = (yh - R(a.y_ch0) + R(0.5)) / R(a.h_ch);
+  return (s <= R(0) || s >= R(1)) ? R(0) : R(6) * s * (R(1) - s);
+}
+
+// Reverse of the pull of one flow link i at cell (x, y).  lam is the adjoint
+// of the pulled value; the result goes to Mloc (plain link), Oacc (own
+// populations), the outlet's virtual-cell adjoints or the inlet velocity.
+template <typename S, typename R>
+__device__ __forceinline__ void pull_flow_rev(const Pops<S> &src, const KArgs &a,
+                                              const uint8_t *__restrict__ mask,
+                                              const uint16_t *__restrict__ mid,
+                                              const MatCoef<R> *__restrict__ pal, int i, int x,
+                                              int y, uint8_t m, R lam, R *Mloc, R *Oacc,
+                                              R *Vdn, R *Vup, R &lip_own, R &lU) {
+  const int EX[9] = EX9_TAB, EY[9] = EY9_TAB, OP[9] = OP9_TAB;
+  if (i == 0 || !(m & M_EDGE)) {
+    Mloc[i] = lam;
+    return;
+  }
+  int sx = x - EX[i], sy = y - EY[i];
+  if (sy < 0 || sy >= a.ny) {
+    Oacc[OP[i]] += lam;
+    return;
+  }
+  if (sx < 0 || sx >= a.nx) {
+    if (a.periodic) {
+      sx = sx < 0 ? sx + a.nx : sx - a.nx;
+    } else if (sx < 0) {
+      Oacc[OP[i]] += lam;
+      if (m & M_INLET) lU += lam * R(6) * w9<R>(i) * R(EX[i]) * dinlet_du<R>(a, R(y) - R(0.5) * R(EY[i]));
+      return;
+    } else {
+      const int vx = a.nx - 1;
+      R d[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) d[k] = R(src.at(k, vx, sy));
+      const R jx = d[1] - d[3] + d[5] - d[6] - d[7] + d[8];
+      const R jy = d[2] - d[4] + d[5] + d[6] - d[7] - d[8];
+      const R ipv = pal[mid[(long long)sy * a.nxp + vx]].inv_phi;
+      const R ldP = lam9<R>(i) * lam;
+      R lv[10];
+#pragma unroll
+      for (int k = 0; k < 9; ++k)
+        lv[k] = ldP * ((k > 0 ? R(-0.6) : R(0)) + R(0.8) * ipv * (jx * R(EX[k]) + jy * R(EY[k])));
+      lv[i] += lam;
+      lv[9] = ldP * R(0.4) * (jx * jx + jy * jy);   // adjoint of the virtual cell's 1/phi
+      R *dst = sy == y ? nullptr : (sy < y ? Vdn : Vup);
+      if (!dst) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Oacc[k] += lv[k];
+        lip_own += lv[9];
+      } else {
+#pragma unroll
+        for (int k = 0; k < 10; ++k) dst[k] += lv[k];
+      }
+      return;
+    }
+    if ((m & M_NEAR_SOLID) && (mask[(long long)sy * a.nxp + sx] & REG_MASK) == REG_SOLID) {
+      Oacc[OP[i]] += lam;
+      return;
+    }
+    Mloc[i] = lam;   // periodic wrap: a plain link
+    return;
+  }
+  if ((m & M_NEAR_SOLID) && (mask[(long long)sy * a.nxp + sx] & REG_MASK) == REG_SOLID) {
+    Oacc[OP[i]] += lam;
+    return;
+  }
+  Mloc[i] = lam;
+}
+
+// Reverse of the pull of link i of scalar s.
+template <typename R>
+__device__ __forceinline__ void pull_scalar_rev(const KArgs &a, const uint8_t *__restrict__ mask,
+                                                const MatCoef<R> &mc, int s, int i, int x, int y,
+                                                uint8_t m, R lam, R *Mloc, R *Oacc, R &lw1) {
+  const int EX[5] = {0, 1, 0, -1, 0}, EY[5] = {0, 0, 1, 0, -1}, OP[5] = {0, 3, 4, 1, 2};
+  const int q = 9 + 5 * s;
+  if (i == 0 || !(m & M_EDGE)) {
+    Mloc[q + i] = lam;
+    return;
+  }
+  int sx = x - EX[i], sy = y - EY[i];
+  if (sy < 0) {
+    Oacc[q + OP[i]] += lam;
+    return;
+  }
+  if (sy >= a.ny) {
+    if (a.top_dirichlet) {
+      Oacc[q + OP[i]] -= lam;
+      lw1 += R(2) * R(a.Ctop[s]) * lam;
+    } else {
+      Oacc[q + OP[i]] += lam;
+    }
+    return;
+  }
+  if (sx < 0 || sx >= a.nx) {
+    if (a.periodic) {
+      sx = sx < 0 ? sx + a.nx : sx - a.nx;
+    } else if (sx < 0) {
+      if (m & M_INLET) {
+        Oacc[q + OP[i]] -= lam;
+        lw1 += R(2) * R(a.Cin[s]) * lam;
+      } else {
+        Oacc[q + OP[i]] += lam;
+      }
+      return;
+    } else {
+      Oacc[q + i] += lam;   // fully developed: the cell's own population of link i
+      return;
+    }
+  }
+  if ((m & M_NEAR_SOLID) && (mask[(long long)sy * a.nxp + sx] & REG_MASK) == REG_SOLID) {
+    Oacc[q + OP[i]] += lam;
+    return;
+  }
+  Mloc[q + i] = lam;
+}
+
+// Local adjoint of one step (see the file comment).  seed_cell >= 0 turns
+// the kernel into the seed of the "CL temperature" objective: the adjoint of
+// the pulled temperature populations of that cell is 1 (others 0) and the
+// collision is not traversed.
+template <typename S>
+__global__ void __launch_bounds__(128)
+k_adj_local(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
+            const uint16_t *__restrict__ mid,
+            const MatCoef<typename Real<S>::type> *__restrict__ pal,
+            const MatRaw *__restrict__ raw, KArgs a, int fickian,
+            AdjBufs<typename Real<S>::type> B, long long seed_cell) {
+  using R = typename Real<S>::type;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  R lU = 0;
+  if (x < a.nx && y < a.ny) {
+    const long long c = (long long)y * a.nxp + x, P = a.plane;
+    const uint8_t m = mask[c];
+    R Mloc[24], Oacc[24];
+#pragma unroll
+    for (int q = 0; q < 24; ++q) Mloc[q] = Oacc[q] = R(0);
+    R Vdn[10], Vup[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) Vdn[k] = Vup[k] = R(0);
+    const bool outlet = !a.periodic && x == a.nx - 1;
+    if ((m & REG_MASK) != REG_SOLID) {
+      const Pops<S> src{src_p, a.plane, a.nxp};
+      const MatCoef<R> mc = pal[mid[c]];
+      Cell<R> cell;
+      pull_cell<S, R>(src, a, mask, mid, pal, mc, x, y, m, cell);
+      // forward reaction terms (kept for the reverse)
+      const bool surf = a.mode == 0 && (m & M_YLO);
+      const bool vol = a.mode == 1 && (m & REG_MASK) == REG_CATALYST;
+      R theta = 0, k = 0, kappa = 0, gd = 0, Jv = 0, Cv = 0;
+      if (surf || vol) theta = own_sum<S, R>(src, 0, x, y) + R(a.Cref[0] - a.T_in);
+      if (surf) {
+        k = rate<R>(a, R(a.kA_surf), theta);
+        kappa = k / (R(2) * mc.w1[1]);
+        gd = cell.g[1][2] + R(a.wr1[1]) * R(a.Cref[1]);
+        Jv = gd * (R(2) * kappa) / (R(1) + kappa);
+        cell.g[1][2] -= Jv;
+        cell.g[0][2] += R(a.hpo) * mc.inv_sigma * Jv;
+        cell.g[2][2] += R(2) * Jv;
+      }
+      R S_vol = 0;
+      if (vol) {
+        Cv = own_sum<S, R>(src, 1, x, y) + R(a.Cref[1]);
+        k = rate<R>(a, R(a.kA_vol), theta);
+        S_vol = -k * Cv / (R(1) + k);
+      }
+      // ---- reverse of the collisions
+      R lcf[9], lcg[3][5];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) lcf[i] = R(0);
+#pragma unroll
+      for (int s = 0; s < 3; ++s)
+#pragma unroll
+        for (int i = 0; i < 5; ++i) lcg[s][i] = R(0);
+      R lphi = 0, ldarcy = 0, lforch = 0, ll0 = 0, ll1 = 0, lip = 0;
+      R lb[3] = {0, 0, 0}, lw1[3] = {0, 0, 0}, lq1[3] = {0, 0, 0}, lsrc[3] = {0, 0, 0};
+      if (seed_cell < 0) {
+        const Macro<R> u = macros<R>(a, mc, cell);
+        const R srcv[3] = {-S_vol * R(a.hpo) * mc.inv_sigma, S_vol, R(-2) * S_vol};
+        R lux = 0, luy = 0;
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+          R lo[5];
+#pragma unroll
+          for (int i = 0; i < 5; ++i) lo[i] = B.lam[(9 + 5 * s + i) * P + c];
+          collide_scalar_rev<R>(a, mc, s, u.ux, u.uy, u.C[s], cell.g[s], srcv[s], lo, lcg[s], lux,
+                                luy, lsrc[s], lb[s], lw1[s], lq1[s]);
+        }
+        R lo[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) lo[i] = B.lam[i * P + c];
+        flow_rev<R>(a, mc, cell.f, lo, lux, luy, lcf, lphi, ldarcy, lforch, ll0, ll1, lip);
+        // volumetric sources: (-S h / sigma, S, -2 S)
+        if (vol) {
+          const R lS = -R(a.hpo) * mc.inv_sigma * lsrc[0] + lsrc[1] - R(2) * lsrc[2];
+          const R lC = lS * (-k / (R(1) + k));
+          const R lk = lS * (-Cv / ((R(1) + k) * (R(1) + k)));
+          const R lth = lk * drate_dtheta<R>(a, k, theta);
+#pragma unroll
+          for (int q = 0; q < 5; ++q) {
+            Oacc[9 + q] += lth;
+            Oacc[14 + q] += lC;
+          }
+        }
+      } else if (c == seed_cell) {
+#pragma unroll
+        for (int i = 0; i < 5; ++i) lcg[0][i] = R(1);
+      }
+      // ---- reverse of the surface reaction (post -> pre link values)
+      if (surf) {
+        const R lJ = -lcg[1][2] + R(a.hpo) * mc.inv_sigma * lcg[0][2] + R(2) * lcg[2][2];
+        const R lgd = lJ * R(2) * kappa / (R(1) + kappa);
+        const R lkap = lJ * R(2) * gd / ((R(1) + kappa) * (R(1) + kappa));
+        const R lk = lkap / (R(2) * mc.w1[1]);
+        lw1[1] += -lkap * k / (R(2) * mc.w1[1] * mc.w1[1]);
+        const R lth = lk * drate_dtheta<R>(a, k, theta);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) Oacc[9 + q] += lth;
+        lcg[1][2] += lgd;
+      }
+      // ---- reverse of the pull
+#pragma unroll
+      for (int i = 0; i < 9; ++i)
+        pull_flow_rev<S, R>(src, a, mask, mid, pal, i, x, y, m, lcf[i], Mloc, Oacc, Vdn, Vup, lip, lU);
+#pragma unroll
+      for (int s = 0; s < 3; ++s)
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+          pull_scalar_rev<R>(a, mask, mc, s, i, x, y, m, lcg[s][i], Mloc, Oacc, lw1[s]);
+      // ---- parameters of this cell
+      param_rev<R>(a, mc, raw[mid[c]], fickian, lphi, ldarcy, lforch, ll0, ll1, lip, lb[1], lw1[1],
+                   lq1[1], B.gphi[c], B.gK[c], B.gD[c]);
+    }
+#pragma unroll
+    for (int q = 0; q < 24; ++q) {
+      B.M[q * P + c] = Mloc[q];
+      B.O[q * P + c] = Oacc[q];
+    }
+    if (outlet) {
+#pragma unroll
+      for (int k = 0; k < 10; ++k) {
+        B.V[(0 * 10 + k) * a.ny + y] = Vdn[k];
+        B.V[(1 * 10 + k) * a.ny + y] = Vup[k];
+      }
+    }
+  }
+  // inlet velocity: warp sum, one FP64 atomic per warp that has inlet cells
+  R t = lU;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+  if ((threadIdx.x & 31) == 0 && t != R(0)) atomicAdd(B.gU, (double)t);
+}
+
+// lambda^{n-1}(y, q) = M(y + e_q, q) [fluid consumer] + O(y, q) + outlet terms.
+template <typename R>
+__global__ void __launch_bounds__(128)
+k_adj_gather(const uint8_t *__restrict__ mask, const uint16_t *__restrict__ mid,
+             const MatCoef<R> *__restrict__ pal, KArgs a, AdjBufs<R> B) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= a.nx || y >= a.ny) return;
+  const long long c = (long long)y * a.nxp + x, P = a.plane;
+  const bool solid = (mask[c] & REG_MASK) == REG_SOLID;
+  const int EX9[9] = EX9_TAB, EY9[9] = EY9_TAB;
+  const int EX5[5] = {0, 1, 0, -1, 0}, EY5[5] = {0, 0, 1, 0, -1};
+  const bool outlet = !a.periodic && x == a.nx - 1;
+  R vsum_ip = 0;
+#pragma unroll
+  for (int q = 0; q < 24; ++q) {
+    R l = 0;
+    if (!solid) {
+      const int ex = q < 9 ? EX9[q] : EX5[(q - 9) % 5];
+      const int ey = q < 9 ? EY9[q] : EY5[(q - 9) % 5];
+      int cx = x + ex, cy = y + ey;
+      if (cy >= 0 && cy < a.ny) {
+        if (a.periodic) cx = cx < 0 ? cx + a.nx : (cx >= a.nx ? cx - a.nx : cx);
+        if (cx >= 0 && cx < a.nx) {
+          const long long cc = (long long)cy * a.nxp + cx;
+          if ((mask[cc] & REG_MASK) != REG_SOLID) l += B.M[q * P + cc];
+        }
+      }
+      l += B.O[q * P + c];
+      if (outlet && q < 9) {
+        if (y + 1 < a.ny) l += B.V[(0 * 10 + q) * a.ny + (y + 1)];
+        if (y - 1 >= 0) l += B.V[(1 * 10 + q) * a.ny + (y - 1)];
+      }
+    }
+    B.lam_out[q * P + c] = l;
+  }
+  if (outlet && !solid) {
+    if (y + 1 < a.ny) vsum_ip += B.V[(0 * 10 + 9) * a.ny + (y + 1)];
+    if (y - 1 >= 0) vsum_ip += B.V[(1 * 10 + 9) * a.ny + (y - 1)];
+    const double ip = (double)pal[mid[c]].inv_phi;
+    B.gphi[c] += -(double)vsum_ip * ip * ip;
+  }
+}
+
+// Seed of the "mean current density" objective: lambda^{N-1} = d i_avg /
+// d s^{N-1} (own populations of the catalyst cells) and the objective's
+// direct parameter dependence.  weight = i_scale / nx.
+template <typename S>
+__global__ void __launch_bounds__(128)
+k_adj_seed_current(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
+                   const uint16_t *__restrict__ mid,
+                   const MatCoef<typename Real<S>::type> *__restrict__ pal, KArgs a, int fickian,
+                   double weight, AdjBufs<typename Real<S>::type> B) {
+  using R = typename Real<S>::type;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= a.nx || y >= a.ny) return;
+  const long long c = (long long)y * a.nxp + x, P = a.plane;
+  const uint8_t m = mask[c];
+  R l[24];
+#pragma unroll
+  for (int q = 0; q < 24; ++q) l[q] = R(0);
+  if ((m & REG_MASK) != REG_SOLID) {
+    const Pops<S> src{src_p, a.plane, a.nxp};
+    const MatCoef<R> mc = pal[mid[c]];
+    const R w = R(weight);
+    if (a.mode == 0 && (m & M_YLO)) {
+      const R theta = own_sum<S, R>(src, 0, x, y) + R(a.Cref[0] - a.T_in);
+      const R k = rate<R>(a, R(a.kA_surf), theta);
+      const R kappa = k / (R(2) * mc.w1[1]);
+      const R gd = R(src.at(9 + 5 + 4, x, y)) + R(a.wr1[1]) * R(a.Cref[1]);
+      const R lkap = w * R(2) * gd / ((R(1) + kappa) * (R(1) + kappa));
+      const R lth = lkap / (R(2) * mc.w1[1]) * drate_dtheta<R>(a, k, theta);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) l[9 + q] += lth;
+      l[18] += w * R(2) * kappa / (R(1) + kappa);
+      if (!fickian) {
+        const R lw1 = -lkap * k / (R(2) * mc.w1[1] * mc.w1[1]);
+        B.gD[c] += (double)lw1 * 1.7320508075688772;
+      }
+    } else if (a.mode == 1 && (m & REG_MASK) == REG_CATALYST) {
+      const R theta = own_sum<S, R>(src, 0, x, y) + R(a.Cref[0] - a.T_in);
+      const R Cv = own_sum<S, R>(src, 1, x, y) + R(a.Cref[1]);
+      const R k = rate<R>(a, R(a.kA_vol), theta);
+      const R lS = -w;   // i_avg = sum(-S) weight
+      const R lC = lS * (-k / (R(1) + k));
+      const R lth = lS * (-Cv / ((R(1) + k) * (R(1) + k))) * drate_dtheta<R>(a, k, theta);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        l[9 + q] += lth;
+        l[14 + q] += lC;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 24; ++q) B.lam_out[q * P + c] = l[q];
+}
+
+}  // namespace pemlbm
