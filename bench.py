@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the batched operating-point sweep measurement")
     ap.add_argument("--sweep-cases", type=int, default=64)
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-steps", type=int, default=20000)
     ap.add_argument("--sweep-steps", type=int, default=256)
     ap.add_argument("--workload", default="blocks", choices=["blocks", "grains"],
                     help="blocks: 4096x1024 GDL blocks + volumetric catalyst; grains: "
@@ -332,6 +334,8 @@ def run_ours(args):
         line["e2e"] = e2e
     if not args.no_sweep and args.workload == "blocks":
         line["sweep"] = sweep(args, stream)
+    if not args.no_adjoint and args.workload == "blocks":
+        line["adjoint"] = adjoint_ratio(args, stream)
     if world == 1 and not args.no_cpu_baseline:
         v, cores, sample = cpu_baseline(case)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -371,6 +375,29 @@ def sweep(args, stream):
     for d in doms:
         d.close()
     return out
+
+
+def adjoint_ratio(args, stream):
+    """The adjoint on the 1024 x 256 cathode: gradient of the mean current
+    density after N steps w.r.t. per-cell phi, K, D_O2 and u_in, checkpoint
+    segments of ceil(sqrt N), timed against N forward steps."""
+    import torch
+    from paper_2103_01444_gb300.lbm import Domain
+    case = workloads.cathode_blocks(nx=1024, ny=256, seed=4)
+    d = Domain.from_case(case, precision=args.precision, stream=stream.cuda_stream)
+    d.tune(10)
+    N = args.adjoint_steps
+    d.step(20)
+    torch.cuda.synchronize()
+    t_fwd = d.time_steps(N) / 1e3
+    t0 = time.perf_counter()
+    J, g = d.grad(0, N)
+    t_adj = time.perf_counter() - t0
+    assert np.isfinite(J) and all(np.isfinite(g[k]).all() for k in ("phi", "K", "D_O2"))
+    d.close()
+    return {"unit": "adjoint/forward time", "value": t_adj / t_fwd, "steps": N,
+            "segment": int(np.ceil(np.sqrt(N))), "forward_s": t_fwd, "adjoint_s": t_adj,
+            "workload": "cathode-1024x256-blocks", "objective": "mean current density"}
 
 
 def d_esize(precision):

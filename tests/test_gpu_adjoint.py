@@ -1,0 +1,190 @@
+"""Discrete adjoint of the coupled step.
+
+1. One transposed step against finite differences of the FP64 GPU step
+   (dot-product test) in state and parameter directions.
+2. Gradients of the objectives (mean current density, hottest catalyst-row
+   temperature) after N steps against FP64 central finite differences of the
+   independent oracle, within 1e-3 relative.
+"""
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from oracle.params import lattice_problem
+from paper_2103_01444_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2103_01444_gb300.build import build
+    build()
+
+
+def case_of(name):
+    if name == "film":
+        return workloads.small_cathode(nx=40, ny=14, reaction_mode=0, V_op=0.45, seed=21)
+    if name == "vol":
+        return workloads.small_cathode(nx=36, ny=20, reaction_mode=1, V_op=0.4, seed=22)
+    if name == "grains":
+        return workloads.small_cathode(nx=44, ny=16, reaction_mode=0, V_op=0.45, grains=True,
+                                       seed=23)
+    raise KeyError(name)
+
+
+def gpu(case, precision="fp64", mode=0):
+    from paper_2103_01444_gb300.lbm import Domain
+    return Domain.from_case(case, precision=precision, interface_mode=mode)
+
+
+@pytest.mark.parametrize("name", ["film", "vol", "grains"])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_one_step_transpose_dot_product(name, mode):
+    """<lam, (step(s + e v) - step(s - e v)) / 2e> = <step^T lam, v>, and the
+    same for the parameters phi, K, D_O2 and u_in (FP64 storage)."""
+    from paper_2103_01444_gb300.units import cathode_params
+    case = case_of(name)
+    d = gpu(case, mode=mode)
+    d.step(25)
+    s0 = d.state()
+    live = (d.mask() & 3) != 3
+    rng = np.random.default_rng(5)
+    lam = rng.standard_normal(s0.shape) * live
+    lam_prev, g = d.vjp(lam)
+
+    def step_from(state, fields=None, params=None):
+        if params is not None:
+            d.set_params(params)
+        if fields is not None:
+            d.set_fields(**fields)
+        d.set_state(state)
+        d.step(1)
+        out = d.state()
+        return out
+
+    v = rng.standard_normal(s0.shape) * live * 1e-3
+    eps = 1e-4
+    fd = np.sum(lam * (step_from(s0 + eps * v) - step_from(s0 - eps * v))) / (2 * eps)
+    ad = np.sum(lam_prev * v)
+    assert abs(fd - ad) <= 1e-7 * (abs(fd) + np.abs(lam_prev * v).sum()), (fd, ad)
+
+    params, fields, _ = cathode_params(case, interface_mode=mode)
+    gdl = np.zeros((case["ny"], case["nx"]), bool)
+    gdl[case["ny_cl"]:case["ny_cl"] + case["ny_gdl"]] = True
+    gdl &= live
+    for key, gkey in (("phi", "phi"), ("K", "K"), ("D_O2", "D_O2")):
+        base = fields[key]
+        vv = np.where(gdl, rng.standard_normal(base.shape) * np.where(gdl, base, 0.0), 0.0)
+        h = 1e-5
+        fp = dict(fields, **{key: base + h * vv})
+        fm = dict(fields, **{key: base - h * vv})
+        # difference the states first: the temperature populations are large
+        diff = step_from(s0, fields=fp) - step_from(s0, fields=fm)
+        fdp = np.sum(lam * diff) / (2 * h)
+        adp = np.sum(g[gkey] * vv)
+        assert abs(fdp - adp) <= 1e-4 * max(abs(fdp), abs(adp), 1e-12), (key, fdp, adp)
+    d.set_fields(**fields)
+    h = 1e-6 * params["u_in_avg"]
+    diff = (step_from(s0, params=dict(params, u_in_avg=params["u_in_avg"] + h)) -
+            step_from(s0, params=dict(params, u_in_avg=params["u_in_avg"] - h)))
+    fdu = np.sum(lam * diff) / (2 * h)
+    assert abs(fdu - g["u_in"]) <= 1e-4 * max(abs(fdu), 1e-12), (fdu, g["u_in"])
+
+
+def oracle_objective(case, mode, objective, N, material=None, u_in=None, x_star=None):
+    params, mat0, solid = lattice_problem(case, interface_mode=mode)
+    base = Oracle(params, mat0, solid)          # the initial state is held fixed
+    p = dict(params)
+    if u_in is not None:
+        p["u_in_avg"] = u_in
+    o = Oracle(p, material if material is not None else mat0, solid)
+    o.f[...] = base.f
+    o.g[...] = base.g
+    o.step(N)
+    if objective == 0:
+        return o.current_density()[0], None
+    T = o.fields()["T"][0]
+    xs = int(np.argmax(T)) if x_star is None else x_star
+    return T[xs], xs
+
+
+@pytest.mark.parametrize("name,mode,objective", [("film", 0, 0), ("film", 1, 1), ("vol", 0, 0),
+                                                 ("vol", 1, 0), ("grains", 0, 1)])
+def test_gradient_matches_oracle_finite_differences(name, mode, objective):
+    """Gradients of the objective after 40 steps (checkpoint segments of 7)
+    w.r.t. phi, K, D_O2 (random directions over the GDL and on single cells)
+    and u_in against FP64 central differences of the oracle: 1e-3 relative."""
+    case = case_of(name)
+    N = 40
+    d = gpu(case, mode=mode)
+    J, g = d.grad(objective, N, segment=7)
+    J0, xs = oracle_objective(case, mode, objective, N)
+    assert J == pytest.approx(J0, rel=1e-9)
+    params, mat0, _ = lattice_problem(case, interface_mode=mode)
+    live = (d.mask() & 3) != 3
+    gdl = np.zeros((case["ny"], case["nx"]), bool)
+    gdl[case["ny_cl"]:case["ny_cl"] + case["ny_gdl"]] = True
+    gdl &= live
+    rng = np.random.default_rng(9)
+    cells = np.argwhere(gdl)
+    picks = cells[rng.choice(len(cells), 3, replace=False)]
+    for key in ("phi", "K", "D_O2"):
+        base = mat0[key]
+        dirs = [np.where(gdl, rng.standard_normal(base.shape) * np.where(gdl, base, 0.0), 0.0)]
+        for (yy, xx) in picks:
+            e = np.zeros(base.shape)
+            e[yy, xx] = base[yy, xx]
+            dirs.append(e)
+        for vv in dirs:
+            h = 1e-5
+            Jp, _ = oracle_objective(case, mode, objective, N, dict(mat0, **{key: base + h * vv}),
+                                     x_star=xs)
+            Jm, _ = oracle_objective(case, mode, objective, N, dict(mat0, **{key: base - h * vv}),
+                                     x_star=xs)
+            fd = (Jp - Jm) / (2 * h)
+            ad = float(np.sum(g[key] * vv))
+            scale = max(abs(fd), abs(ad), 1e-5 * abs(J0))
+            assert abs(fd - ad) <= 1e-3 * scale, (key, fd, ad)
+    hu = 1e-6 * params["u_in_avg"]
+    Jp, _ = oracle_objective(case, mode, objective, N, u_in=params["u_in_avg"] + hu, x_star=xs)
+    Jm, _ = oracle_objective(case, mode, objective, N, u_in=params["u_in_avg"] - hu, x_star=xs)
+    fdu = (Jp - Jm) / (2 * hu)
+    assert abs(fdu - g["u_in"]) <= 1e-3 * max(abs(fdu), 1e-5 * abs(J0) / params["u_in_avg"]), \
+        (fdu, g["u_in"])
+
+
+def test_fp32_adjoint_close_to_fp64():
+    case = case_of("vol")
+    J64, g64 = gpu(case, "fp64").grad(0, 60)
+    J32, g32 = gpu(case, "fp32").grad(0, 60)
+    assert J32 == pytest.approx(J64, rel=1e-4)
+    for k in ("phi", "K", "D_O2"):
+        err = np.linalg.norm(g32[k] - g64[k]) / np.linalg.norm(g64[k])
+        assert err < 1e-3, (k, err)
+    assert g32["u_in"] == pytest.approx(g64["u_in"], rel=1e-3)
+
+
+def test_grad_leaves_state_and_autograd_function():
+    import torch
+    from paper_2103_01444_gb300.lbm import cathode_objective
+    from paper_2103_01444_gb300.units import cathode_params
+    case = case_of("film")
+    d = gpu(case)
+    d.step(10)
+    s = d.state()
+    d.grad(0, 20)
+    np.testing.assert_array_equal(d.state(), s)
+    params, fields, _ = cathode_params(case)
+    phi = torch.tensor(fields["phi"], dtype=torch.float64, requires_grad=True)
+    K = torch.tensor(fields["K"], dtype=torch.float64, requires_grad=True)
+    D = torch.tensor(fields["D_O2"], dtype=torch.float64, requires_grad=True)
+    u = torch.tensor(params["u_in_avg"], dtype=torch.float64, requires_grad=True)
+    f = cathode_objective()
+    J = f.apply(phi, K, D, u, d, fields, params, 0, 20, 0)
+    (2.0 * J).backward()
+    d2 = gpu(case)
+    _, g = d2.grad(0, 20)
+    np.testing.assert_allclose(phi.grad.numpy(), 2 * g["phi"], rtol=1e-12)
+    np.testing.assert_allclose(D.grad.numpy(), 2 * g["D_O2"], rtol=1e-12)
+    assert u.grad.item() == pytest.approx(2 * g["u_in"], rel=1e-12)
