@@ -137,6 +137,7 @@ KArgs make_args(const lbm_domain *d) {
   a.k_ein = c0 + c1 / p.T_in;
   a.k_c1 = c1;
   a.T_in = p.T_in;
+  a.theta0 = d->Cref[0] - p.T_in;
   // Eq. 15 with Eq. 16: eta + T dU0/dT = V - U0_0, so the heat per O2
   // consumed does not depend on T.
   a.hpo = four_F_c * (p.V_op - p.U0_0) / p.rho_cp_f;
@@ -851,12 +852,39 @@ lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t se
       launch_step<S>(src, dst, g, a, d->variant, d->stream);
     });
   };
-  // forward s^0 .. s^{N-1}, checkpoints every seg states
+  // Work of a full segment is replayed from CUDA graphs: the same buffers
+  // and launches for every segment (only the checkpoint copied differs).
+  struct Graph {
+    cudaGraphExec_t g = nullptr;
+    ~Graph() {
+      if (g) cudaGraphExecDestroy(g);
+    }
+  };
+  auto capture = [&](Graph &gr, auto &&body) -> lbm_status {
+    if (gr.g) return LBM_OK;
+    cudaGraph_t raw_g = nullptr;
+    CK(cudaStreamBeginCapture(d->stream, cudaStreamCaptureModeThreadLocal));
+    body();
+    cudaError_t e = cudaStreamEndCapture(d->stream, &raw_g);
+    if (e != cudaSuccess) return fail(LBM_ECUDA, "adjoint graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&gr.g, raw_g, 0);
+    cudaGraphDestroy(raw_g);
+    if (e != cudaSuccess) return fail(LBM_ECUDA, "adjoint graph instantiate: %s", cudaGetErrorString(e));
+    return LBM_OK;
+  };
+  Graph g_fwd, g_rec, g_rev[2];
+  // forward s^0 .. s^{N-1}: segment k starts from SEG(0) = s^{k seg}
   CK(cudaMemcpyAsync(CKP(0), d->pop[d->cur], sbytes, cudaMemcpyDeviceToDevice, d->stream));
   CK(cudaMemcpyAsync(SEG(0), d->pop[d->cur], sbytes, cudaMemcpyDeviceToDevice, d->stream));
-  for (int64_t n = 1; n <= N - 1; ++n) {
-    fwd(SEG((n - 1) & 1), SEG(n & 1));
-    if (n % seg == 0) CK(cudaMemcpyAsync(CKP(n / seg), SEG(n & 1), sbytes, cudaMemcpyDeviceToDevice, d->stream));
+  for (int64_t k = 0; k + 1 < nck; ++k) {
+    // seg steps SEG(0) -> ... -> SEG(seg & 1), then back into SEG(0)
+    auto body = [&] {
+      for (int j = 1; j <= seg; ++j) fwd(SEG((j - 1) & 1), SEG(j & 1));
+      if (seg & 1) cudaMemcpyAsync(SEG(0), SEG(1), sbytes, cudaMemcpyDeviceToDevice, d->stream);
+    };
+    if ((s = capture(g_fwd, body)) != LBM_OK) return s;
+    CK(cudaGraphLaunch(g_fwd.g, d->stream));
+    CK(cudaMemcpyAsync(CKP(k + 1), SEG(0), sbytes, cudaMemcpyDeviceToDevice, d->stream));
   }
   CK(cudaGetLastError());
   // reverse, last segment first
@@ -864,8 +892,17 @@ lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t se
   long long seed_cell = -1;
   for (int64_t k = nck - 1; k >= 0; --k) {
     const int64_t first = k * seg, last = std::min<int64_t>(first + seg - 1, N - 1);
+    const bool full = last - first + 1 == seg && k != nck - 1;
     CK(cudaMemcpyAsync(SEG(0), CKP(k), sbytes, cudaMemcpyDeviceToDevice, d->stream));
-    for (int64_t n = first + 1; n <= last; ++n) fwd(SEG(n - 1 - first), SEG(n - first));
+    if (full) {
+      auto body = [&] {
+        for (int j = 1; j < seg; ++j) fwd(SEG(j - 1), SEG(j));
+      };
+      if ((s = capture(g_rec, body)) != LBM_OK) return s;
+      CK(cudaGraphLaunch(g_rec.g, d->stream));
+    } else {
+      for (int64_t n = first + 1; n <= last; ++n) fwd(SEG(n - 1 - first), SEG(n - first));
+    }
     CK(cudaGetLastError());
     if (k == nck - 1) {
       // objective at step N from s^{N-1}, and its seed lambda^{N-1}
@@ -905,9 +942,23 @@ lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t se
       }
     }
     const int64_t ntop = (k == nck - 1) ? N - 1 : last + 1;
-    for (int64_t n = ntop; n >= first + 1; --n) {
-      reverse_step(d, w, cur, SEG(n - 1 - first), -1);
-      cur ^= 1;
+    if (full) {
+      const int c0 = cur;
+      auto body = [&] {
+        int cc = c0;
+        for (int64_t n = ntop; n >= first + 1; --n) {
+          reverse_step(d, w, cc, SEG(n - 1 - first), -1);
+          cc ^= 1;
+        }
+      };
+      if ((s = capture(g_rev[c0], body)) != LBM_OK) return s;
+      CK(cudaGraphLaunch(g_rev[c0].g, d->stream));
+      cur ^= (int)(seg & 1);
+    } else {
+      for (int64_t n = ntop; n >= first + 1; --n) {
+        reverse_step(d, w, cur, SEG(n - 1 - first), -1);
+        cur ^= 1;
+      }
     }
     CK(cudaGetLastError());
   }
@@ -971,9 +1022,10 @@ lbm_status batch_tiles(lbm_batch *b, int bx, int by) {
 // Uploads the case table (arguments, buffers, current parity of each case).
 lbm_status batch_table(lbm_batch *b, int bx) {
   CK(cudaStreamSynchronize(b->stream));   // the staging buffer is reused
+  std::vector<BatchCase> table(b->doms.size());
   for (size_t c = 0; c < b->doms.size(); ++c) {
     lbm_domain *d = b->doms[c];
-    BatchCase &bc = b->hcases[c];
+    BatchCase &bc = table[c];
     bc.a = make_args(d);
     bc.pop[0] = d->pop[0];
     bc.pop[1] = d->pop[1];
@@ -983,8 +1035,11 @@ lbm_status batch_table(lbm_batch *b, int bx) {
     bc.cur0 = d->cur;
     bc.tiles_x = (d->nx + bx - 1) / bx;
   }
-  CK(cudaMemcpyAsync(b->dcases, b->hcases, sizeof(BatchCase) * b->doms.size(),
-                     cudaMemcpyHostToDevice, b->stream));
+  dispatch(b->precision, [&](auto *tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    batch_upload<S>(table.data(), (int)table.size(), b->hcases, b->dcases, b->stream);
+  });
+  CK(cudaGetLastError());
   return LBM_OK;
 }
 
@@ -1027,7 +1082,7 @@ lbm_status batch_run(lbm_batch *b, int64_t nsteps, bool fixed_parity) {
     return LBM_OK;
   }
   if (b->schedule == 1) {              // persistent cooperative launch
-    lbm_status s = batch_tiles(b, kPersistBX, kPersistBY);
+    lbm_status s = batch_tiles(b, kPersistBX, kPersistBY * kBatchRows);
     if (s != LBM_OK) return s;
     if ((s = batch_table(b, kPersistBX)) != LBM_OK) return s;
     CK(cudaMemsetAsync(b->dbar, 0, 2 * sizeof(unsigned), b->stream));
@@ -1066,7 +1121,7 @@ lbm_status batch_run(lbm_batch *b, int64_t nsteps, bool fixed_parity) {
   }
   // schedule 0: one launch per step over all tiles, replayed from a graph
   const StepShape sh = kStepShapes[b->variant];
-  lbm_status s = batch_tiles(b, sh.bx, sh.by);
+  lbm_status s = batch_tiles(b, sh.bx, sh.by * kBatchRows);
   if (s != LBM_OK) return s;
   if ((s = batch_table(b, sh.bx)) != LBM_OK) return s;
   if (fixed_parity) {

@@ -36,7 +36,7 @@ template <typename R> struct AdjBufs {
 // output adjoints lo[5], accumulates into ld[5] (pulled values), lux, luy,
 // and the adjoints of the source, b, w1 and q1.
 template <typename R>
-__device__ __forceinline__ void collide_scalar_rev(const KArgs &a, const MatCoef<R> &mc, int s,
+__device__ __forceinline__ void collide_scalar_rev(const KArgsT<R> &a, const MatCoef<R> &mc, int s,
                                                    R ux, R uy, R Cdev, const R d[5], R srcv,
                                                    const R lo[5], R ld[5], R &lux, R &luy,
                                                    R &lsrc, R &lb, R &lw1, R &lq1) {
@@ -77,7 +77,7 @@ __device__ __forceinline__ void collide_scalar_rev(const KArgs &a, const MatCoef
 // from the scalar collisions, accumulates ld[9] and the adjoints of phi
 // (direct), darcy, forch, l0, l1 and 1/phi.
 template <typename R>
-__device__ __forceinline__ void flow_rev(const KArgs &a, const MatCoef<R> &mc, const R d[9],
+__device__ __forceinline__ void flow_rev(const KArgsT<R> &a, const MatCoef<R> &mc, const R d[9],
                                          const R lo[9], R lux_in, R luy_in, R ld[9], R &lphi,
                                          R &ldarcy, R &lforch, R &ll0, R &ll1, R &lip) {
   const R sn = R(a.s_nu), sq = R(a.s_q), g = R(a.body_g), ip = mc.inv_phi;
@@ -192,7 +192,7 @@ __device__ __forceinline__ void flow_rev(const KArgs &a, const MatCoef<R> &mc, c
 }
 
 // d k / d theta of the rate k = A exp(e_in - c1 theta / (T T_in)): -c1 k / T^2.
-template <typename R> __device__ __forceinline__ R drate_dtheta(const KArgs &a, R k, R theta) {
+template <typename R> __device__ __forceinline__ R drate_dtheta(const KArgsT<R> &a, R k, R theta) {
   const R T = R(a.T_in) + theta;
   return -R(a.k_c1) * k / (T * T);
 }
@@ -209,31 +209,34 @@ __device__ __forceinline__ void own_sums_rev(R *__restrict__ O, long long c, lon
 }
 
 // Parameter chain of one cell: adjoints of the derived coefficients to the
-// caller's fields phi, K and D_O2 (Eq. 7, 8, 10).
+// caller's fields phi, K and D_O2 (Eq. 7, 8, 10), in the arithmetic type;
+// only the accumulation into the per-cell gradients is FP64.
 template <typename R>
-__device__ __forceinline__ void param_rev(const KArgs &a, const MatCoef<R> &mc, const MatRaw &raw,
-                                          int fickian, R lphi, R ldarcy, R lforch, R ll0, R ll1,
-                                          R lip, R lbO2, R lw1O2, R lq1O2, double &gphi,
-                                          double &gK, double &gD) {
+__device__ __forceinline__ void param_rev(const KArgsT<R> &a, const MatCoef<R> &mc, int fickian,
+                                          R lphi, R ldarcy, R lforch, R ll0, R ll1, R lip,
+                                          R lbO2, R lw1O2, R lq1O2, double *gphi, double *gK,
+                                          double *gD) {
   ldarcy += R(0.25) * ll0;
   lforch += R(0.5) * ll1;
-  double dphi = (double)lphi - (double)lip * (double)mc.inv_phi * (double)mc.inv_phi;
-  double dK = 0.0;
-  if (!isinf(raw.K)) {
-    dphi += (double)ldarcy * (double)mc.darcy / raw.phi - 0.5 * (double)lforch * (double)mc.forch / raw.phi;
-    dK = -(double)ldarcy * (double)mc.darcy / raw.K - 0.5 * (double)lforch * (double)mc.forch / raw.K;
-  }
-  const double sqrt3 = 1.7320508075688772;
-  double dD;
+  const R ip = mc.inv_phi;
+  // darcy = phi nu / K, forch = 0.143 phi^-1/2 K^-1/2
+  const R ddf = ldarcy * mc.darcy + R(0.5) * lforch * mc.forch;
+  const R dphi = lphi - lip * ip * ip + (ldarcy * mc.darcy - R(0.5) * lforch * mc.forch) * ip;
+  const R sqrt3 = R(1.7320508075688772);
+  R dD;
   if (fickian) {
-    const double q1 = (double)mc.q1[1], b0 = (double)mc.b[1];
-    dD = (double)lq1O2 * (-q1 * q1 * 10.0 / (4.0 + b0));
+    const R q1 = mc.q1[1];
+    dD = lq1O2 * (-q1 * q1 * R(10) / (R(4) + mc.b[1]));
   } else {
-    dD = (double)lbO2 * 20.0 * sqrt3 + (double)lw1O2 * sqrt3;
+    dD = lbO2 * R(20) * sqrt3 + lw1O2 * sqrt3;
   }
-  gphi += dphi;
-  gK += dK;
-  gD += dD;
+  *gphi += (double)dphi;
+  if (mc.darcy > R(0)) {
+    const R nu = (R(1) / R(a.s_nu) - R(0.5)) / R(3);
+    const R inv_K = mc.darcy * ip / nu;
+    *gK += (double)(-ddf * inv_K);
+  }
+  *gD += (double)dD;
 }
 
 }  // namespace pemlbm
@@ -241,7 +244,7 @@ __device__ __forceinline__ void param_rev(const KArgs &a, const MatCoef<R> &mc, 
 namespace pemlbm {
 
 // Inlet parabola derivative: d u_in(yh) / d u_in_avg.
-template <typename R> __device__ __forceinline__ R dinlet_du(const KArgs &a, R yh) {
+template <typename R> __device__ __forceinline__ R dinlet_du(const KArgsT<R> &a, R yh) {
   R s = (yh - R(a.y_ch0) + R(0.5)) / R(a.h_ch);
   return (s <= R(0) || s >= R(1)) ? R(0) : R(6) * s * (R(1) - s);
 }
@@ -250,7 +253,7 @@ template <typename R> __device__ __forceinline__ R dinlet_du(const KArgs &a, R y
 // of the pulled value; the result goes to Mloc (plain link), Oacc (own
 // populations), the outlet's virtual-cell adjoints or the inlet velocity.
 template <typename S, typename R>
-__device__ __forceinline__ void pull_flow_rev(const Pops<S> &src, const KArgs &a,
+__device__ __forceinline__ void pull_flow_rev(const Pops<S> &src, const KArgsT<R> &a,
                                               const uint8_t *__restrict__ mask,
                                               const uint16_t *__restrict__ mid,
                                               const MatCoef<R> *__restrict__ pal, int i, int x,
@@ -315,7 +318,7 @@ __device__ __forceinline__ void pull_flow_rev(const Pops<S> &src, const KArgs &a
 
 // Reverse of the pull of link i of scalar s.
 template <typename R>
-__device__ __forceinline__ void pull_scalar_rev(const KArgs &a, const uint8_t *__restrict__ mask,
+__device__ __forceinline__ void pull_scalar_rev(const KArgsT<R> &a, const uint8_t *__restrict__ mask,
                                                 const MatCoef<R> &mc, int s, int i, int x, int y,
                                                 uint8_t m, R lam, R *Mloc, R *Oacc, R &lw1) {
   const int EX[5] = {0, 1, 0, -1, 0}, EY[5] = {0, 0, 1, 0, -1}, OP[5] = {0, 3, 4, 1, 2};
@@ -370,7 +373,7 @@ __global__ void __launch_bounds__(128)
 k_adj_local(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
             const uint16_t *__restrict__ mid,
             const MatCoef<typename Real<S>::type> *__restrict__ pal,
-            const MatRaw *__restrict__ raw, KArgs a, int fickian,
+            const MatRaw *__restrict__ raw, KArgsT<typename Real<S>::type> a, int fickian,
             AdjBufs<typename Real<S>::type> B, long long seed_cell) {
   using R = typename Real<S>::type;
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
@@ -394,7 +397,7 @@ k_adj_local(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
       const bool surf = a.mode == 0 && (m & M_YLO);
       const bool vol = a.mode == 1 && (m & REG_MASK) == REG_CATALYST;
       R theta = 0, k = 0, kappa = 0, gd = 0, Jv = 0, Cv = 0;
-      if (surf || vol) theta = own_sum<S, R>(src, 0, x, y) + R(a.Cref[0] - a.T_in);
+      if (surf || vol) theta = own_sum<S, R>(src, 0, x, y) + a.theta0;
       if (surf) {
         k = rate<R>(a, R(a.kA_surf), theta);
         kappa = k / (R(2) * mc.w1[1]);
@@ -474,13 +477,16 @@ k_adj_local(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
         for (int i = 0; i < 5; ++i)
           pull_scalar_rev<R>(a, mask, mc, s, i, x, y, m, lcg[s][i], Mloc, Oacc, lw1[s]);
       // ---- parameters of this cell
-      param_rev<R>(a, mc, raw[mid[c]], fickian, lphi, ldarcy, lforch, ll0, ll1, lip, lb[1], lw1[1],
-                   lq1[1], B.gphi[c], B.gK[c], B.gD[c]);
+      param_rev<R>(a, mc, fickian, lphi, ldarcy, lforch, ll0, ll1, lip, lb[1], lw1[1], lq1[1],
+                   B.gphi + c, B.gK + c, B.gD + c);
     }
+    // O is written (and later read) only by cells that use their own state
+    const bool own = (m & M_EDGE) || (a.mode == 1 && (m & REG_MASK) == REG_CATALYST);
 #pragma unroll
-    for (int q = 0; q < 24; ++q) {
-      B.M[q * P + c] = Mloc[q];
-      B.O[q * P + c] = Oacc[q];
+    for (int q = 0; q < 24; ++q) B.M[q * P + c] = Mloc[q];
+    if (own) {
+#pragma unroll
+      for (int q = 0; q < 24; ++q) B.O[q * P + c] = Oacc[q];
     }
     if (outlet) {
 #pragma unroll
@@ -501,15 +507,28 @@ k_adj_local(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
 template <typename R>
 __global__ void __launch_bounds__(128)
 k_adj_gather(const uint8_t *__restrict__ mask, const uint16_t *__restrict__ mid,
-             const MatCoef<R> *__restrict__ pal, KArgs a, AdjBufs<R> B) {
+             const MatCoef<R> *__restrict__ pal, KArgsT<R> a, AdjBufs<R> B) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   if (x >= a.nx || y >= a.ny) return;
   const long long c = (long long)y * a.nxp + x, P = a.plane;
-  const bool solid = (mask[c] & REG_MASK) == REG_SOLID;
+  const uint8_t my = mask[c];
+  const bool solid = (my & REG_MASK) == REG_SOLID;
+  const bool own = (my & M_EDGE) || (a.mode == 1 && (my & REG_MASK) == REG_CATALYST);
   const int EX9[9] = EX9_TAB, EY9[9] = EY9_TAB;
   const int EX5[5] = {0, 1, 0, -1, 0}, EY5[5] = {0, 0, 1, 0, -1};
   const bool outlet = !a.periodic && x == a.nx - 1;
   R vsum_ip = 0;
+  if (!solid && !own) {
+    // interior cell: every consumer y + e_q exists and is fluid
+    const long long W = a.nxp;
+#pragma unroll
+    for (int q = 0; q < 24; ++q) {
+      const int ex = q < 9 ? EX9[q] : EX5[(q - 9) % 5];
+      const int ey = q < 9 ? EY9[q] : EY5[(q - 9) % 5];
+      B.lam_out[q * P + c] = B.M[q * P + c + ey * W + ex];
+    }
+    return;
+  }
 #pragma unroll
   for (int q = 0; q < 24; ++q) {
     R l = 0;
@@ -524,7 +543,7 @@ k_adj_gather(const uint8_t *__restrict__ mask, const uint16_t *__restrict__ mid,
           if ((mask[cc] & REG_MASK) != REG_SOLID) l += B.M[q * P + cc];
         }
       }
-      l += B.O[q * P + c];
+      if (own) l += B.O[q * P + c];
       if (outlet && q < 9) {
         if (y + 1 < a.ny) l += B.V[(0 * 10 + q) * a.ny + (y + 1)];
         if (y - 1 >= 0) l += B.V[(1 * 10 + q) * a.ny + (y - 1)];
@@ -547,7 +566,8 @@ template <typename S>
 __global__ void __launch_bounds__(128)
 k_adj_seed_current(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
                    const uint16_t *__restrict__ mid,
-                   const MatCoef<typename Real<S>::type> *__restrict__ pal, KArgs a, int fickian,
+                   const MatCoef<typename Real<S>::type> *__restrict__ pal,
+                   KArgsT<typename Real<S>::type> a, int fickian,
                    double weight, AdjBufs<typename Real<S>::type> B) {
   using R = typename Real<S>::type;
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
@@ -562,7 +582,7 @@ k_adj_seed_current(const S *__restrict__ src_p, const uint8_t *__restrict__ mask
     const MatCoef<R> mc = pal[mid[c]];
     const R w = R(weight);
     if (a.mode == 0 && (m & M_YLO)) {
-      const R theta = own_sum<S, R>(src, 0, x, y) + R(a.Cref[0] - a.T_in);
+      const R theta = own_sum<S, R>(src, 0, x, y) + a.theta0;
       const R k = rate<R>(a, R(a.kA_surf), theta);
       const R kappa = k / (R(2) * mc.w1[1]);
       const R gd = R(src.at(9 + 5 + 4, x, y)) + R(a.wr1[1]) * R(a.Cref[1]);
@@ -573,10 +593,10 @@ k_adj_seed_current(const S *__restrict__ src_p, const uint8_t *__restrict__ mask
       l[18] += w * R(2) * kappa / (R(1) + kappa);
       if (!fickian) {
         const R lw1 = -lkap * k / (R(2) * mc.w1[1] * mc.w1[1]);
-        B.gD[c] += (double)lw1 * 1.7320508075688772;
+        B.gD[c] += (double)(lw1 * R(1.7320508075688772));
       }
     } else if (a.mode == 1 && (m & REG_MASK) == REG_CATALYST) {
-      const R theta = own_sum<S, R>(src, 0, x, y) + R(a.Cref[0] - a.T_in);
+      const R theta = own_sum<S, R>(src, 0, x, y) + a.theta0;
       const R Cv = own_sum<S, R>(src, 1, x, y) + R(a.Cref[1]);
       const R k = rate<R>(a, R(a.kA_vol), theta);
       const R lS = -w;   // i_avg = sum(-S) weight

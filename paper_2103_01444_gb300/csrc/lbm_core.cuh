@@ -81,27 +81,46 @@ struct MatRaw { double phi, K, alpha[3], sigma; };
 // How each scalar's diffusivity enters Eq. 10 (see lbm_params.interface_mode).
 struct ScalarMode { int fickian; double alpha_max[3]; };
 
-// Launch-invariant arguments (passed by value: constant bank).
-struct KArgs {
+// Launch-invariant arguments (passed by value: constant bank).  The host
+// fills them in FP64 (KArgs) and narrows them to the kernels' arithmetic
+// type once per launch, so no kernel converts per cell.
+template <typename F> struct KArgsT {
   int nx, ny, nxp, periodic;
   long long plane;          // elements per population plane
   int mode;                 // 0 thin film, 1 volumetric catalyst rows
   int ny_cl, y_ch0;         // catalyst rows; first channel row
   int top_dirichlet;
-  double s_nu, s_q;         // 1/tau and the q-moment rate of Sec. 2.1
-  double body_g;            // body force per unit mass along x
-  double u_in_avg, h_ch;    // inlet parabola
-  double Q3;                // Eq. 10 rate of the energy moments
-  double Cref[3], wr0[3], wr1[3], bref[3];  // deviation references
-  double Cin[3], Ctop[3];
+  F s_nu, s_q;              // 1/tau and the q-moment rate of Sec. 2.1
+  F body_g;                 // body force per unit mass along x
+  F u_in_avg, h_ch;         // inlet parabola
+  F Q3;                     // Eq. 10 rate of the energy moments
+  F Cref[3], wr0[3], wr1[3], bref[3];  // deviation references
+  F Cin[3], Ctop[3];
   // kinetics: k(T) = A exp(e_in - c1 (T - T_in)/(T T_in)), Eq. 13, 14, 16, 17
-  double kA_surf, kA_vol, k_ein, k_c1, T_in;
-  double hpo;               // temperature per unit O2 consumed (Eq. 15, 16)
+  F kA_surf, kA_vol, k_ein, k_c1, T_in;
+  F theta0;                 // Cref_T - T_in
+  F hpo;                    // temperature per unit O2 consumed (Eq. 15, 16)
 };
+using KArgs = KArgsT<double>;
+
+template <typename F> __host__ __device__ inline KArgsT<F> narrow_args(const KArgs &a) {
+  KArgsT<F> r;
+  r.nx = a.nx; r.ny = a.ny; r.nxp = a.nxp; r.periodic = a.periodic; r.plane = a.plane;
+  r.mode = a.mode; r.ny_cl = a.ny_cl; r.y_ch0 = a.y_ch0; r.top_dirichlet = a.top_dirichlet;
+  r.s_nu = F(a.s_nu); r.s_q = F(a.s_q); r.body_g = F(a.body_g); r.u_in_avg = F(a.u_in_avg);
+  r.h_ch = F(a.h_ch); r.Q3 = F(a.Q3);
+  for (int s = 0; s < 3; ++s) {
+    r.Cref[s] = F(a.Cref[s]); r.wr0[s] = F(a.wr0[s]); r.wr1[s] = F(a.wr1[s]);
+    r.bref[s] = F(a.bref[s]); r.Cin[s] = F(a.Cin[s]); r.Ctop[s] = F(a.Ctop[s]);
+  }
+  r.kA_surf = F(a.kA_surf); r.kA_vol = F(a.kA_vol); r.k_ein = F(a.k_ein); r.k_c1 = F(a.k_c1);
+  r.T_in = F(a.T_in); r.theta0 = F(a.theta0); r.hpo = F(a.hpo);
+  return r;
+}
 
 // One case of a batched step (device table entry).
-struct BatchCase {
-  KArgs a;
+template <typename F> struct BatchCaseT {
+  KArgsT<F> a;
   const void *pop[2];       // the case's two population buffers
   const uint8_t *mask;
   const uint16_t *mid;
@@ -109,6 +128,7 @@ struct BatchCase {
   int cur0;                 // buffer holding the state when the batched run starts
   int tiles_x;              // tiles along x
 };
+using BatchCase = BatchCaseT<double>;
 
 // Velocity sets, Eq. 2 and Eq. 9 orders (folded by the compiler once the
 // loops over links are unrolled).
@@ -135,7 +155,7 @@ template <typename S, bool CG = false> struct Pops {
 };
 
 // Inlet parabola at height yh (cell centres at integer y).
-template <typename R> __device__ __forceinline__ R inlet_u(const KArgs &a, R yh) {
+template <typename R> __device__ __forceinline__ R inlet_u(const KArgsT<R> &a, R yh) {
   R s = (yh - R(a.y_ch0) + R(0.5)) / R(a.h_ch);
   return (s <= R(0) || s >= R(1)) ? R(0) : R(6) * R(a.u_in_avg) * s * (R(1) - s);
 }
@@ -150,7 +170,7 @@ template <typename R> __device__ __forceinline__ R inlet_u(const KArgs &a, R yh)
 // Flow link i into cell (x, y) whose source may lie outside the fluid;
 // `v` is the interior pull already loaded for this link.
 template <typename S, typename R, bool CG = false>
-__device__ R pull_flow_edge(const Pops<S, CG> &src, const KArgs &a, const uint8_t *__restrict__ mask,
+__device__ R pull_flow_edge(const Pops<S, CG> &src, const KArgsT<R> &a, const uint8_t *__restrict__ mask,
                             const uint16_t *__restrict__ mid, const MatCoef<R> *__restrict__ pal,
                             int i, int x, int y, uint8_t m, R v) {
   const int EX[9] = EX9_TAB, EY[9] = EY9_TAB, OP[9] = OP9_TAB;
@@ -187,7 +207,7 @@ __device__ R pull_flow_edge(const Pops<S, CG> &src, const KArgs &a, const uint8_
 // Scalar link i of scalar s into cell (x, y); the bottom wall returns the
 // insulated value and the reaction is applied afterwards.
 template <typename S, typename R, bool CG = false>
-__device__ R pull_scalar_edge(const Pops<S, CG> &src, const KArgs &a, const uint8_t *__restrict__ mask,
+__device__ R pull_scalar_edge(const Pops<S, CG> &src, const KArgsT<R> &a, const uint8_t *__restrict__ mask,
                               const MatCoef<R> &mc, int s, int i, int x, int y, uint8_t m, R v) {
   const int EX[5] = {0, 1, 0, -1, 0}, EY[5] = {0, 0, 1, 0, -1}, OP[5] = {0, 3, 4, 1, 2};
   const int q = 9 + 5 * s;
@@ -226,7 +246,7 @@ template <typename R> struct Cell {
 
 // Rate constant of the catalyst at temperature deviation theta = T - T_in:
 // A exp(e_in - c1 theta / (T T_in)) with T = T_in + theta.
-template <typename R> __device__ __forceinline__ R rate(const KArgs &a, R A, R theta) {
+template <typename R> __device__ __forceinline__ R rate(const KArgsT<R> &a, R A, R theta) {
   R T = R(a.T_in) + theta;
   return A * exp(R(a.k_ein) - R(a.k_c1) * theta / (T * R(a.T_in)));
 }
@@ -250,9 +270,9 @@ __device__ __forceinline__ R own_sum(const Pops<S, CG> &src, int s, int x, int y
 // Tafel link.  Returns the O2 consumed J (lattice units) and modifies the
 // three upward links.  theta_n = T^n - T_in from the cell's own state.
 template <typename S, typename R, bool CG = false>
-__device__ __forceinline__ R surface_reaction(const Pops<S, CG> &src, const KArgs &a,
+__device__ __forceinline__ R surface_reaction(const Pops<S, CG> &src, const KArgsT<R> &a,
                                               const MatCoef<R> &mc, int x, Cell<R> &c) {
-  R theta = own_sum<S, R, CG>(src, 0, x, 0) + R(a.Cref[0] - a.T_in);
+  R theta = own_sum<S, R, CG>(src, 0, x, 0) + a.theta0;
   R k = rate<R>(a, R(a.kA_surf), theta);
   R kappa = k / (R(2) * mc.w1[1]);
   R gdown = c.g[1][2] + R(a.wr1[1]) * R(a.Cref[1]);   // full g*_4 of O2 (bounced)
@@ -265,8 +285,8 @@ __device__ __forceinline__ R surface_reaction(const Pops<S, CG> &src, const KArg
 
 // Volumetric catalyst sink of a catalyst cell (backward Euler in C).
 template <typename S, typename R, bool CG = false>
-__device__ __forceinline__ R volume_sink(const Pops<S, CG> &src, const KArgs &a, int x, int y) {
-  R theta = own_sum<S, R, CG>(src, 0, x, y) + R(a.Cref[0] - a.T_in);
+__device__ __forceinline__ R volume_sink(const Pops<S, CG> &src, const KArgsT<R> &a, int x, int y) {
+  R theta = own_sum<S, R, CG>(src, 0, x, y) + a.theta0;
   R C = own_sum<S, R, CG>(src, 1, x, y) + R(a.Cref[1]);
   R k = rate<R>(a, R(a.kA_vol), theta);
   return -k * C / (R(1) + k);
@@ -274,7 +294,7 @@ __device__ __forceinline__ R volume_sink(const Pops<S, CG> &src, const KArgs &a,
 
 // The 24 interior pulls of cell (x, y), issued without looking at the mask.
 template <typename S, typename R, bool CG = false>
-__device__ __forceinline__ void load_interior(const Pops<S, CG> &src, const KArgs &a, int x, int y,
+__device__ __forceinline__ void load_interior(const Pops<S, CG> &src, const KArgsT<R> &a, int x, int y,
                                               Cell<R> &c) {
   const long long base = (long long)y * a.nxp + x, P = a.plane, W = a.nxp;
   const S *p = src.p + base;
@@ -301,7 +321,7 @@ __device__ __forceinline__ void load_interior(const Pops<S, CG> &src, const KArg
 // Replaces the pulls of links that cross a wall, the inlet, the outlet, a
 // periodic seam or a solid grain (cells with any edge bit only).
 template <typename S, typename R, bool CG = false>
-__device__ __forceinline__ void fix_edges(const Pops<S, CG> &src, const KArgs &a,
+__device__ __forceinline__ void fix_edges(const Pops<S, CG> &src, const KArgsT<R> &a,
                                           const uint8_t *__restrict__ mask,
                                           const uint16_t *__restrict__ mid,
                                           const MatCoef<R> *__restrict__ pal,
@@ -319,7 +339,7 @@ __device__ __forceinline__ void fix_edges(const Pops<S, CG> &src, const KArgs &a
 
 // Pull all 24 populations of a non-solid cell (x, y).
 template <typename S, typename R, bool CG = false>
-__device__ __forceinline__ void pull_cell(const Pops<S, CG> &src, const KArgs &a,
+__device__ __forceinline__ void pull_cell(const Pops<S, CG> &src, const KArgsT<R> &a,
                                           const uint8_t *__restrict__ mask,
                                           const uint16_t *__restrict__ mid,
                                           const MatCoef<R> *__restrict__ pal,
@@ -336,7 +356,7 @@ template <typename R> struct Macro {
 };
 
 template <typename R>
-__device__ __forceinline__ Macro<R> macros(const KArgs &a, const MatCoef<R> &mc, const Cell<R> &c) {
+__device__ __forceinline__ Macro<R> macros(const KArgsT<R> &a, const MatCoef<R> &mc, const Cell<R> &c) {
   Macro<R> r;
   const R *d = c.f;
   R vx = d[1] - d[3] + d[5] - d[6] - d[7] + d[8] + R(0.5) * mc.phi * R(a.body_g);
@@ -355,7 +375,7 @@ __device__ __forceinline__ Macro<R> macros(const KArgs &a, const MatCoef<R> &mc,
 
 // D2Q9 MRT collision with the porous force, in deviation moments (Eq. 1, 3-7).
 template <typename R>
-__device__ __forceinline__ void collide_flow(const KArgs &a, const MatCoef<R> &mc, const Macro<R> &u,
+__device__ __forceinline__ void collide_flow(const KArgsT<R> &a, const MatCoef<R> &mc, const Macro<R> &u,
                                              const R d[9], R o[9]) {
   const R sn = R(a.s_nu), sq = R(a.s_q);
   R ux = u.ux, uy = u.uy, u2 = ux * ux + uy * uy, un = sqrt(u2), ip = mc.inv_phi;
@@ -402,7 +422,7 @@ __device__ __forceinline__ void collide_flow(const KArgs &a, const MatCoef<R> &m
 // D2Q5 MRT collision of scalar s in deviation moments (Eq. 10), plus a
 // volumetric source src added with the cell's equilibrium weights.
 template <typename R>
-__device__ __forceinline__ void collide_scalar(const KArgs &a, const MatCoef<R> &mc, int s,
+__device__ __forceinline__ void collide_scalar(const KArgsT<R> &a, const MatCoef<R> &mc, int s,
                                                R ux, R uy, R Cdev, const R d[5], R srcv, R o[5]) {
   const R Q1 = mc.q1[s], Q3 = R(a.Q3);
   R C = Cdev + R(a.Cref[s]);

@@ -17,7 +17,8 @@ __device__ __forceinline__ void cell_update(const S *__restrict__ src_p, S *__re
                                             const uint8_t *__restrict__ mask,
                                             const uint16_t *__restrict__ mid,
                                             const MatCoef<typename Real<S>::type> *__restrict__ pal,
-                                            const KArgs &a, int x, int y) {
+                                            const KArgsT<typename Real<S>::type> &a, int x,
+                                            int y) {
   using R = typename Real<S>::type;
   const long long c = (long long)y * a.nxp + x;
   const Pops<S, CG> src{src_p, a.plane, a.nxp};
@@ -56,7 +57,7 @@ template <typename S, int BX, int BY, int MINB>
 __global__ void __launch_bounds__(BX * BY, MINB)
 k_step(const S *__restrict__ src_p, S *__restrict__ dst, const uint8_t *__restrict__ mask,
        const uint16_t *__restrict__ mid, const MatCoef<typename Real<S>::type> *__restrict__ pal,
-       KArgs a) {
+       KArgsT<typename Real<S>::type> a) {
   const int x = blockIdx.x * BX + (threadIdx.x % BX);
   const int y = blockIdx.y * BY + (threadIdx.x / BX);
   if (x >= a.nx || y >= a.ny) return;
@@ -78,40 +79,47 @@ __device__ __forceinline__ int batch_case_of(const int *__restrict__ tile_start,
   return lo;
 }
 
-__device__ __forceinline__ void stage_args(const BatchCase *__restrict__ cases, int c, KArgs *sa) {
+template <typename R>
+__device__ __forceinline__ void stage_args(const BatchCaseT<R> *__restrict__ cases, int c,
+                                           KArgsT<R> *sa) {
   const int *srcw = reinterpret_cast<const int *>(&cases[c].a);
   int *dstw = reinterpret_cast<int *>(sa);
-  for (int k = threadIdx.x; k < (int)(sizeof(KArgs) / sizeof(int)); k += blockDim.x)
+  for (int k = threadIdx.x; k < (int)(sizeof(KArgsT<R>) / sizeof(int)); k += blockDim.x)
     dstw[k] = __ldg(srcw + k);
 }
 
 template <typename S, int BX, int BY, bool CG>
-__device__ __forceinline__ void batch_tile(const BatchCase *__restrict__ cases,
+__device__ __forceinline__ void batch_tile(const BatchCaseT<typename Real<S>::type> *__restrict__ cases,
                                            const int *__restrict__ tile_start, int ncases, int t,
-                                           int parity, KArgs *sa, int *sc) {
+                                           int parity, KArgsT<typename Real<S>::type> *sa,
+                                           int *sc) {
   using R = typename Real<S>::type;
   if (threadIdx.x == 0) *sc = batch_case_of(tile_start, ncases, t);
   __syncthreads();
   const int c = *sc;
   stage_args(cases, c, sa);
   __syncthreads();
-  const BatchCase &bc = cases[c];
+  const BatchCaseT<R> &bc = cases[c];
   const int tile = t - __ldg(tile_start + c);
   const int tx = tile % bc.tiles_x, ty = tile / bc.tiles_x;
-  const int x = tx * BX + (threadIdx.x % BX), y = ty * BY + (threadIdx.x / BX);
+  const int x = tx * BX + (threadIdx.x % BX);
   const int cur = bc.cur0 ^ parity;
-  if (x < sa->nx && y < sa->ny)
-    cell_update<S, CG>((const S *)bc.pop[cur], (S *)bc.pop[cur ^ 1], bc.mask, bc.mid,
-                       (const MatCoef<R> *)bc.pal, *sa, x, y);
+  const S *src = (const S *)bc.pop[cur];
+  S *dst = (S *)bc.pop[cur ^ 1];
+  for (int r = 0; r < kBatchRows; ++r) {
+    const int y = (ty * kBatchRows + r) * BY + (threadIdx.x / BX);
+    if (x < sa->nx && y < sa->ny)
+      cell_update<S, CG>(src, dst, bc.mask, bc.mid, (const MatCoef<R> *)bc.pal, *sa, x, y);
+  }
   __syncthreads();   // the staged arguments are reused by the next tile
 }
 
 // One launch per step: one block per tile.
 template <typename S, int BX, int BY, int MINB>
 __global__ void __launch_bounds__(BX * BY, MINB)
-k_batch_step(const BatchCase *__restrict__ cases, const int *__restrict__ tile_start, int ncases,
-             int parity) {
-  __shared__ KArgs sa;
+k_batch_step(const BatchCaseT<typename Real<S>::type> *__restrict__ cases,
+             const int *__restrict__ tile_start, int ncases, int parity) {
+  __shared__ KArgsT<typename Real<S>::type> sa;
   __shared__ int sc;
   batch_tile<S, BX, BY, false>(cases, tile_start, ncases, blockIdx.x, parity, &sa, &sc);
 }
@@ -151,10 +159,10 @@ __device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned *gen, uns
 // bypass L1 (other SMs wrote them in the previous step).
 template <typename S, int BX, int BY, int MINB>
 __global__ void __launch_bounds__(BX * BY, MINB)
-k_batch_persistent(const BatchCase *__restrict__ cases, const int *__restrict__ tile_start,
-                   int ncases, int total_tiles, int nsteps, unsigned *bar, int *status,
-                   long long spin_limit) {
-  __shared__ KArgs sa;
+k_batch_persistent(const BatchCaseT<typename Real<S>::type> *__restrict__ cases,
+                   const int *__restrict__ tile_start, int ncases, int total_tiles, int nsteps,
+                   unsigned *bar, int *status, long long spin_limit) {
+  __shared__ KArgsT<typename Real<S>::type> sa;
   __shared__ int sc;
   for (int step = 0; step < nsteps; ++step) {
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x)
@@ -168,8 +176,8 @@ k_batch_persistent(const BatchCase *__restrict__ cases, const int *__restrict__ 
 template <typename S>
 __global__ void k_fields(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
                          const uint16_t *__restrict__ mid,
-                         const MatCoef<typename Real<S>::type> *__restrict__ pal, KArgs a,
-                         double *__restrict__ out) {
+                         const MatCoef<typename Real<S>::type> *__restrict__ pal,
+                         KArgsT<typename Real<S>::type> a, double *__restrict__ out) {
   using R = typename Real<S>::type;
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   if (x >= a.nx || y >= a.ny) return;
@@ -225,7 +233,8 @@ template <typename S>
 __global__ void __launch_bounds__(kCatalystBX * kCatalystBY)
 k_catalyst(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
            const uint16_t *__restrict__ mid, const MatCoef<typename Real<S>::type> *__restrict__ pal,
-           KArgs a, double i_scale, float *__restrict__ profile, double *__restrict__ colsum) {
+           KArgsT<typename Real<S>::type> a, double i_scale, float *__restrict__ profile,
+           double *__restrict__ colsum) {
   using R = typename Real<S>::type;
   __shared__ double sm[kCatalystBY][kCatalystBX];
   const Pops<S> src{src_p, a.plane, a.nxp};
@@ -270,7 +279,8 @@ __global__ void k_sum_columns(const double *__restrict__ colsum, int nx, double 
 // overwritten.  Non-finite values raise *bad.
 template <typename S>
 __global__ void __launch_bounds__(kResidualBX * kResidualBY)
-k_residual(const S *__restrict__ src_p, const uint8_t *__restrict__ mask, KArgs a,
+k_residual(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
+           KArgsT<typename Real<S>::type> a,
            typename Real<S>::type *__restrict__ snap, double *__restrict__ partial,
            int *__restrict__ bad) {
   using R = typename Real<S>::type;
@@ -289,7 +299,7 @@ k_residual(const S *__restrict__ src_p, const uint8_t *__restrict__ mask, KArgs 
     R X[5];
     X[0] = d[1] - d[3] + d[5] - d[6] - d[7] + d[8];
     X[1] = d[2] - d[4] + d[5] + d[6] - d[7] - d[8];
-    X[2] = own_sum<S, R>(src, 0, x, y) + R(a.Cref[0] - a.T_in);
+    X[2] = own_sum<S, R>(src, 0, x, y) + a.theta0;
     X[3] = own_sum<S, R>(src, 1, x, y) + R(a.Cref[1]);
     X[4] = own_sum<S, R>(src, 2, x, y) + R(a.Cref[2]);
     bool ok = true;
@@ -330,7 +340,8 @@ __global__ void k_sum_partials(const double *__restrict__ partial, int nblocks,
 template <typename S>
 __global__ void k_init(S *__restrict__ pop, const uint8_t *__restrict__ mask,
                        const uint16_t *__restrict__ mid,
-                       const MatCoef<typename Real<S>::type> *__restrict__ pal, KArgs a) {
+                       const MatCoef<typename Real<S>::type> *__restrict__ pal,
+                       KArgsT<typename Real<S>::type> a) {
   using R = typename Real<S>::type;
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   if (x >= a.nxp || y >= a.ny) return;
@@ -351,8 +362,8 @@ __global__ void k_init(S *__restrict__ pop, const uint8_t *__restrict__ mask,
 
 // ------------------------------------------- full-value state in/out
 template <typename S>
-__global__ void k_get_state(const S *__restrict__ pop, const uint8_t *__restrict__ mask, KArgs a,
-                            double *__restrict__ out) {
+__global__ void k_get_state(const S *__restrict__ pop, const uint8_t *__restrict__ mask,
+                            KArgsT<typename Real<S>::type> a, double *__restrict__ out) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   if (x >= a.nx || y >= a.ny) return;
   const long long c = (long long)y * a.nxp + x, n = (long long)a.nx * a.ny,
@@ -364,15 +375,15 @@ __global__ void k_get_state(const S *__restrict__ pop, const uint8_t *__restrict
     if (q < 9) ref = W9[q];
     else {
       const int s = (q - 9) / 5, i = (q - 9) % 5;
-      ref = (i == 0 ? a.wr0[s] : a.wr1[s]) * a.Cref[s];
+      ref = (double)(i == 0 ? a.wr0[s] : a.wr1[s]) * (double)a.Cref[s];
     }
     out[q * n + o] = solid ? 0.0 : (double)ld_r(pop + q * a.plane + c) + ref;
   }
 }
 
 template <typename S>
-__global__ void k_set_state(S *__restrict__ pop, const uint8_t *__restrict__ mask, KArgs a,
-                            const double *__restrict__ in) {
+__global__ void k_set_state(S *__restrict__ pop, const uint8_t *__restrict__ mask,
+                            KArgsT<typename Real<S>::type> a, const double *__restrict__ in) {
   using R = typename Real<S>::type;
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   if (x >= a.nx || y >= a.ny) return;
@@ -385,7 +396,7 @@ __global__ void k_set_state(S *__restrict__ pop, const uint8_t *__restrict__ mas
     if (q < 9) ref = W9[q];
     else {
       const int s = (q - 9) / 5, i = (q - 9) % 5;
-      ref = (i == 0 ? a.wr0[s] : a.wr1[s]) * a.Cref[s];
+      ref = (double)(i == 0 ? a.wr0[s] : a.wr1[s]) * (double)a.Cref[s];
     }
     st_r(pop + q * a.plane + c, solid ? R(0) : R(in[q * n + o] - ref));
   }
@@ -398,7 +409,7 @@ void launch_step_v(const void *src, void *dst, const DevGeom &g, const KArgs &a,
   dim3 grid((a.nx + sh.bx - 1) / sh.bx, (a.ny + sh.by - 1) / sh.by);
   k_step<S, sh.bx, sh.by, sh.minb><<<grid, sh.bx * sh.by, 0, st>>>(
       (const S *)src, (S *)dst, g.mask, g.mid,
-      (const MatCoef<typename Real<S>::type> *)g.pal, a);
+      (const MatCoef<typename Real<S>::type> *)g.pal, narrow_args<typename Real<S>::type>(a));
 }
 
 template <typename S>
@@ -421,7 +432,7 @@ void launch_batch_v(const BatchCase *cases, const int *tile_start, int ncases, i
                     int parity, cudaStream_t st) {
   constexpr StepShape sh = kStepShapes[V];
   k_batch_step<S, sh.bx, sh.by, sh.minb><<<total_tiles, sh.bx * sh.by, 0, st>>>(
-      cases, tile_start, ncases, parity);
+      (const BatchCaseT<typename Real<S>::type> *)cases, tile_start, ncases, parity);
 }
 
 template <typename S>
@@ -454,7 +465,8 @@ cudaError_t launch_batch_persistent(const BatchCase *cases, const int *tile_star
   int grid = sms * per_sm;
   if (grid > total_tiles) grid = total_tiles;
   if (grid < 1) return cudaErrorInvalidConfiguration;
-  void *args[] = {(void *)&cases, (void *)&tile_start, (void *)&ncases, (void *)&total_tiles,
+  const BatchCaseT<typename Real<S>::type> *rc = (const BatchCaseT<typename Real<S>::type> *)cases;
+  void *args[] = {(void *)&rc, (void *)&tile_start, (void *)&ncases, (void *)&total_tiles,
                   (void *)&nsteps, (void *)&bar, (void *)&status, (void *)&spin_limit};
   return cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(kPersistBX * kPersistBY),
                                      args, 0, st);
@@ -471,15 +483,15 @@ void launch_adj_local(const void *src, const DevGeom &g, const MatRaw *raw, cons
   using R = typename Real<S>::type;
   dim3 grid((a.nx + 127) / 128, a.ny);
   k_adj_local<S><<<grid, 128, 0, st>>>((const S *)src, g.mask, g.mid, (const MatCoef<R> *)g.pal,
-                                       raw, a, fickian, adj_bufs<R>(b), seed_cell);
+                                       raw, narrow_args<R>(a), fickian, adj_bufs<R>(b), seed_cell);
 }
 
 template <typename S>
 void launch_adj_gather(const DevGeom &g, const KArgs &a, const AdjPtrs &b, cudaStream_t st) {
   using R = typename Real<S>::type;
   dim3 grid((a.nx + 127) / 128, a.ny);
-  k_adj_gather<R><<<grid, 128, 0, st>>>(g.mask, g.mid, (const MatCoef<R> *)g.pal, a,
-                                        adj_bufs<R>(b));
+  k_adj_gather<R><<<grid, 128, 0, st>>>(g.mask, g.mid, (const MatCoef<R> *)g.pal,
+                                        narrow_args<R>(a), adj_bufs<R>(b));
 }
 
 template <typename S>
@@ -488,15 +500,35 @@ void launch_adj_seed_current(const void *src, const DevGeom &g, const KArgs &a, 
   using R = typename Real<S>::type;
   dim3 grid((a.nx + 127) / 128, a.ny);
   k_adj_seed_current<S><<<grid, 128, 0, st>>>((const S *)src, g.mask, g.mid,
-                                              (const MatCoef<R> *)g.pal, a, fickian, weight,
-                                              adj_bufs<R>(b));
+                                              (const MatCoef<R> *)g.pal, narrow_args<R>(a),
+                                              fickian, weight, adj_bufs<R>(b));
+}
+
+// Narrows a host table of batched cases into `staging` (pinned) and copies
+// it to the device table.
+template <typename S>
+void batch_upload(const BatchCase *host, int n, void *staging, void *dev, cudaStream_t st) {
+  using R = typename Real<S>::type;
+  BatchCaseT<R> *out = (BatchCaseT<R> *)staging;
+  for (int c = 0; c < n; ++c) {
+    out[c].a = narrow_args<R>(host[c].a);
+    out[c].pop[0] = host[c].pop[0];
+    out[c].pop[1] = host[c].pop[1];
+    out[c].mask = host[c].mask;
+    out[c].mid = host[c].mid;
+    out[c].pal = host[c].pal;
+    out[c].cur0 = host[c].cur0;
+    out[c].tiles_x = host[c].tiles_x;
+  }
+  cudaMemcpyAsync(dev, staging, sizeof(BatchCaseT<R>) * n, cudaMemcpyHostToDevice, st);
 }
 
 template <typename S>
 void launch_fields(const void *src, const DevGeom &g, const KArgs &a, double *out, cudaStream_t st) {
   dim3 grid((a.nx + 127) / 128, a.ny);
   k_fields<S><<<grid, 128, 0, st>>>((const S *)src, g.mask, g.mid,
-                                    (const MatCoef<typename Real<S>::type> *)g.pal, a, out);
+                                    (const MatCoef<typename Real<S>::type> *)g.pal,
+                                    narrow_args<typename Real<S>::type>(a), out);
 }
 
 template <typename S>
@@ -504,8 +536,8 @@ void launch_catalyst(const void *src, const DevGeom &g, const KArgs &a, double i
                      float *profile, double *colsum, double *out, cudaStream_t st) {
   const int nb = (a.nx + kCatalystBX - 1) / kCatalystBX;
   k_catalyst<S><<<nb, kCatalystBX * kCatalystBY, 0, st>>>(
-      (const S *)src, g.mask, g.mid, (const MatCoef<typename Real<S>::type> *)g.pal, a, i_scale,
-      profile, colsum);
+      (const S *)src, g.mask, g.mid, (const MatCoef<typename Real<S>::type> *)g.pal,
+      narrow_args<typename Real<S>::type>(a), i_scale, profile, colsum);
   k_sum_columns<<<1, kReduceThreads, 0, st>>>(colsum, a.nx, out);
 }
 
@@ -514,7 +546,8 @@ void launch_residual(const void *src, const DevGeom &g, const KArgs &a, void *sn
                      double *partial, int *bad, double *out, cudaStream_t st) {
   dim3 grid((a.nx + kResidualBX - 1) / kResidualBX, (a.ny + kResidualBY - 1) / kResidualBY);
   k_residual<S><<<grid, kResidualBX * kResidualBY, 0, st>>>(
-      (const S *)src, g.mask, a, (typename Real<S>::type *)snap, partial, bad);
+      (const S *)src, g.mask, narrow_args<typename Real<S>::type>(a),
+      (typename Real<S>::type *)snap, partial, bad);
   k_sum_partials<<<1, kReduceThreads, 0, st>>>(partial, grid.x * grid.y, out);
 }
 
@@ -522,19 +555,22 @@ template <typename S>
 void launch_init(void *pop, const DevGeom &g, const KArgs &a, cudaStream_t st) {
   dim3 grid((a.nxp + 127) / 128, a.ny);
   k_init<S><<<grid, 128, 0, st>>>((S *)pop, g.mask, g.mid,
-                                  (const MatCoef<typename Real<S>::type> *)g.pal, a);
+                                  (const MatCoef<typename Real<S>::type> *)g.pal,
+                                  narrow_args<typename Real<S>::type>(a));
 }
 
 template <typename S>
 void launch_get_state(const void *pop, const DevGeom &g, const KArgs &a, double *out, cudaStream_t st) {
   dim3 grid((a.nx + 127) / 128, a.ny);
-  k_get_state<S><<<grid, 128, 0, st>>>((const S *)pop, g.mask, a, out);
+  k_get_state<S><<<grid, 128, 0, st>>>((const S *)pop, g.mask,
+                                        narrow_args<typename Real<S>::type>(a), out);
 }
 
 template <typename S>
 void launch_set_state(void *pop, const DevGeom &g, const KArgs &a, const double *in, cudaStream_t st) {
   dim3 grid((a.nx + 127) / 128, a.ny);
-  k_set_state<S><<<grid, 128, 0, st>>>((S *)pop, g.mask, a, in);
+  k_set_state<S><<<grid, 128, 0, st>>>((S *)pop, g.mask, narrow_args<typename Real<S>::type>(a),
+                                        in);
 }
 
 #define PEMLBM_INSTANTIATE(S)                                                                   \
@@ -555,6 +591,7 @@ void launch_set_state(void *pop, const DevGeom &g, const KArgs &a, const double 
                                      cudaStream_t);                                             \
   template cudaError_t launch_batch_persistent<S>(const BatchCase *, const int *, int, int, int, \
                                                   unsigned *, int *, long long, cudaStream_t);  \
+  template void batch_upload<S>(const BatchCase *, int, void *, void *, cudaStream_t);         \
   template void launch_adj_local<S>(const void *, const DevGeom &, const MatRaw *, const KArgs &, \
                                     int, const AdjPtrs &, long long, cudaStream_t);             \
   template void launch_adj_gather<S>(const DevGeom &, const KArgs &, const AdjPtrs &,            \

@@ -6,7 +6,8 @@
 
 namespace pemlbm {
 
-struct KArgs;
+template <typename F> struct KArgsT;
+using KArgs = KArgsT<double>;
 struct MatRaw;
 struct ScalarMode;
 
@@ -22,11 +23,16 @@ constexpr int kReduceThreads = 512;
 // Persistent batched step: 128 x 1 cells per block, 8 blocks per SM asked of
 // the register allocator; the grid is the number of co-resident blocks.
 constexpr int kPersistBX = 128, kPersistBY = 1, kPersistMinB = 8;
+// A batched tile is BX x (BY * kBatchRows) cells: each thread updates
+// kBatchRows cells, so the case lookup and argument staging are amortised.
+constexpr int kBatchRows = 8;
 constexpr int kResidualBX = 128, kResidualBY = 2;      // residual blocks
 constexpr int kCatalystBX = 32, kCatalystBY = 8;       // catalyst reduction blocks
 
 // One case of a batched step: its arguments, buffers and geometry.
-struct BatchCase;
+template <typename F> struct BatchCaseT;
+using BatchCase = BatchCaseT<double>;
+template <typename F> struct KArgsT;
 
 // Device-resident geometry shared by all kernels of a domain.
 struct DevGeom {
@@ -47,6 +53,7 @@ template <typename S> void launch_init(void *pop, const DevGeom &g, const KArgs 
 template <typename S> void launch_get_state(const void *pop, const DevGeom &g, const KArgs &a, double *out, cudaStream_t st);
 template <typename S> void launch_set_state(void *pop, const DevGeom &g, const KArgs &a, const double *in, cudaStream_t st);
 
+template <typename S> void batch_upload(const BatchCase *host, int n, void *staging, void *dev, cudaStream_t st);
 template <typename S> void launch_batch_step(const BatchCase *cases, const int *tile_start, int ncases, int total_tiles, int variant, int parity, cudaStream_t st);
 template <typename S> cudaError_t launch_batch_persistent(const BatchCase *cases, const int *tile_start, int ncases, int total_tiles, int nsteps, unsigned *bar, int *status, long long spin_limit, cudaStream_t st);
 
