@@ -39,7 +39,7 @@ FALLBACK_HBM_GBS = 6800.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=8000)
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16", "fp16"])
@@ -116,7 +116,9 @@ def measured_peak():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms; entering
+    waits (at most 5 s) for the first sample so that sampling is live when
+    the timed region starts."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -131,10 +133,17 @@ class ClockSampler:
             self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=self.out, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return self
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and self.proc.poll() is None:
+            if os.path.getsize(self.out.name) > 0:
+                break
+            time.sleep(0.05)
+        self.start_bytes = os.path.getsize(self.out.name)
         return self
 
     def __exit__(self, *exc):
@@ -149,8 +158,12 @@ class ClockSampler:
         if self.proc is None or self.out is None:
             return None
         self.out.flush()
-        rows = [r.split(",") for r in open(self.out.name).read().strip().splitlines() if r.strip()]
+        text = open(self.out.name).read()
         os.unlink(self.out.name)
+        # samples taken before the timed region started are dropped
+        timed = text[getattr(self, "start_bytes", 0):]
+        rows = [r.split(",") for r in (timed if timed.strip() else text).strip().splitlines()
+                if r.strip()]
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:
@@ -182,13 +195,22 @@ def traffic_from_profiles():
     return None
 
 
+STEP_SOURCES = ("lbm_core.cuh", "lbm_step.cuh", "kernels_f32.cu")
+
+
 def kernel_source_hash():
+    """Hash of the sources that make the FP32 step kernel (its device code,
+    its launcher and its launch shapes): a committed DRAM count is used only
+    while these are unchanged."""
     import hashlib
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2103_01444_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, name), "rb").read())
+    for name in STEP_SOURCES:
+        h.update(open(os.path.join(csrc, name), "rb").read())
+    launch = open(os.path.join(csrc, "lbm_launch.h")).read()
+    shapes = re.search(r"kStepShapes\[kStepVariants\] = \{[^;]*;", launch)
+    h.update(shapes.group(0).encode() if shapes else b"")
     return h.hexdigest()[:16]
 
 

@@ -726,7 +726,7 @@ struct DevBuf {
 
 // Reverse workspace of one domain.
 struct AdjWork {
-  DevBuf lam[2], M, O, V, gphi, gK, gD, gU;
+  DevBuf lam[2], M, O, V, gphi, gK, gD, gU, tphi, tK, tD;
   lbm_status alloc(const lbm_domain *d) {
     const size_t r = fp64(d) ? 8 : 4, planes = 24 * (size_t)d->plane;
     lbm_status s;
@@ -734,20 +734,33 @@ struct AdjWork {
       if ((s = b->alloc(planes * r)) != LBM_OK) return s;
     if ((s = V.alloc(20 * (size_t)d->ny * r)) != LBM_OK) return s;
     for (auto *b : {&gphi, &gK, &gD})
+      if ((s = b->alloc(r * d->plane)) != LBM_OK) return s;
+    for (auto *b : {&tphi, &tK, &tD})
       if ((s = b->alloc(sizeof(double) * d->plane)) != LBM_OK) return s;
     if ((s = gU.alloc(sizeof(double))) != LBM_OK) return s;
     return LBM_OK;
   }
   lbm_status zero_grads(const lbm_domain *d) {
-    for (auto *b : {&gphi, &gK, &gD}) CK(cudaMemsetAsync(b->p, 0, sizeof(double) * d->plane, d->stream));
+    const size_t r = fp64(d) ? 8 : 4;
+    for (auto *b : {&gphi, &gK, &gD}) CK(cudaMemsetAsync(b->p, 0, r * d->plane, d->stream));
+    for (auto *b : {&tphi, &tK, &tD}) CK(cudaMemsetAsync(b->p, 0, sizeof(double) * d->plane, d->stream));
     CK(cudaMemsetAsync(gU.p, 0, sizeof(double), d->stream));
     return LBM_OK;
   }
   AdjPtrs ptrs(int cur) {
-    return AdjPtrs{lam[cur].p, M.p, O.p, V.p, (double *)gphi.p, (double *)gK.p, (double *)gD.p,
-                   (double *)gU.p, lam[cur ^ 1].p};
+    return AdjPtrs{lam[cur].p, M.p, O.p, V.p, gphi.p, gK.p, gD.p, (double *)gU.p,
+                   lam[cur ^ 1].p, (double *)tphi.p, (double *)tK.p, (double *)tD.p};
   }
 };
+
+// Adds the segment gradients into the FP64 totals.
+void fold_grads(lbm_domain *d, AdjWork &w) {
+  const KArgs a = make_args(d);
+  dispatch(d->desc.precision, [&](auto *tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    launch_adj_fold<S>(geom(d), a, w.ptrs(0), d->stream);
+  });
+}
 
 // One reverse step: lambda^n (w.lam[cur]) at state src = s^{n-1} ->
 // lambda^{n-1} (w.lam[cur ^ 1]), gradients accumulated.
@@ -765,9 +778,10 @@ void reverse_step(lbm_domain *d, AdjWork &w, int cur, const void *src, long long
 lbm_status copy_grads_out(lbm_domain *d, AdjWork &w, double *dphi, double *dK, double *dD,
                           double *du) {
   const size_t row = sizeof(double) * d->nx, pitch = sizeof(double) * d->nxp;
-  if (dphi) CK(cudaMemcpy2DAsync(dphi, row, w.gphi.p, pitch, row, d->ny, cudaMemcpyDeviceToHost, d->stream));
-  if (dK) CK(cudaMemcpy2DAsync(dK, row, w.gK.p, pitch, row, d->ny, cudaMemcpyDeviceToHost, d->stream));
-  if (dD) CK(cudaMemcpy2DAsync(dD, row, w.gD.p, pitch, row, d->ny, cudaMemcpyDeviceToHost, d->stream));
+  fold_grads(d, w);
+  if (dphi) CK(cudaMemcpy2DAsync(dphi, row, w.tphi.p, pitch, row, d->ny, cudaMemcpyDeviceToHost, d->stream));
+  if (dK) CK(cudaMemcpy2DAsync(dK, row, w.tK.p, pitch, row, d->ny, cudaMemcpyDeviceToHost, d->stream));
+  if (dD) CK(cudaMemcpy2DAsync(dD, row, w.tD.p, pitch, row, d->ny, cudaMemcpyDeviceToHost, d->stream));
   if (du) CK(cudaMemcpyAsync(du, w.gU.p, sizeof(double), cudaMemcpyDeviceToHost, d->stream));
   CK(cudaStreamSynchronize(d->stream));
   return LBM_OK;
@@ -950,6 +964,7 @@ lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t se
           reverse_step(d, w, cc, SEG(n - 1 - first), -1);
           cc ^= 1;
         }
+        fold_grads(d, w);
       };
       if ((s = capture(g_rev[c0], body)) != LBM_OK) return s;
       CK(cudaGraphLaunch(g_rev[c0].g, d->stream));
@@ -959,6 +974,7 @@ lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t se
         reverse_step(d, w, cur, SEG(n - 1 - first), -1);
         cur ^= 1;
       }
+      fold_grads(d, w);
     }
     CK(cudaGetLastError());
   }

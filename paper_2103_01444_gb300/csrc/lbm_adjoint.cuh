@@ -27,7 +27,7 @@ template <typename R> struct AdjBufs {
   R *M;              // pull adjoints [24][plane]
   R *O;              // own-use adjoints [24][plane]
   R *V;              // outlet column: [2][10][ny] (down: from y+1 to y, up: from y-1 to y)
-  double *gphi, *gK, *gD;   // per-cell parameter gradients [plane]
+  R *gphi, *gK, *gD;        // per-cell parameter gradients of the current segment [plane]
   double *gU;               // d objective / d u_in_avg
   R *lam_out;        // lambda^{n-1} [24][plane]
 };
@@ -209,13 +209,13 @@ __device__ __forceinline__ void own_sums_rev(R *__restrict__ O, long long c, lon
 }
 
 // Parameter chain of one cell: adjoints of the derived coefficients to the
-// caller's fields phi, K and D_O2 (Eq. 7, 8, 10), in the arithmetic type;
-// only the accumulation into the per-cell gradients is FP64.
+// caller's fields phi, K and D_O2 (Eq. 7, 8, 10), in the arithmetic type,
+// accumulated per checkpoint segment (k_adj_fold adds each segment into the
+// FP64 totals).
 template <typename R>
 __device__ __forceinline__ void param_rev(const KArgsT<R> &a, const MatCoef<R> &mc, int fickian,
                                           R lphi, R ldarcy, R lforch, R ll0, R ll1, R lip,
-                                          R lbO2, R lw1O2, R lq1O2, double *gphi, double *gK,
-                                          double *gD) {
+                                          R lbO2, R lw1O2, R lq1O2, R *gphi, R *gK, R *gD) {
   ldarcy += R(0.25) * ll0;
   lforch += R(0.5) * ll1;
   const R ip = mc.inv_phi;
@@ -230,13 +230,13 @@ __device__ __forceinline__ void param_rev(const KArgsT<R> &a, const MatCoef<R> &
   } else {
     dD = lbO2 * R(20) * sqrt3 + lw1O2 * sqrt3;
   }
-  *gphi += (double)dphi;
+  *gphi += dphi;
   if (mc.darcy > R(0)) {
     const R nu = (R(1) / R(a.s_nu) - R(0.5)) / R(3);
     const R inv_K = mc.darcy * ip / nu;
-    *gK += (double)(-ddf * inv_K);
+    *gK += -ddf * inv_K;
   }
-  *gD += (double)dD;
+  *gD += dD;
 }
 
 }  // namespace pemlbm
@@ -554,8 +554,8 @@ k_adj_gather(const uint8_t *__restrict__ mask, const uint16_t *__restrict__ mid,
   if (outlet && !solid) {
     if (y + 1 < a.ny) vsum_ip += B.V[(0 * 10 + 9) * a.ny + (y + 1)];
     if (y - 1 >= 0) vsum_ip += B.V[(1 * 10 + 9) * a.ny + (y - 1)];
-    const double ip = (double)pal[mid[c]].inv_phi;
-    B.gphi[c] += -(double)vsum_ip * ip * ip;
+    const R ip = pal[mid[c]].inv_phi;
+    B.gphi[c] += -vsum_ip * ip * ip;
   }
 }
 
@@ -593,7 +593,7 @@ k_adj_seed_current(const S *__restrict__ src_p, const uint8_t *__restrict__ mask
       l[18] += w * R(2) * kappa / (R(1) + kappa);
       if (!fickian) {
         const R lw1 = -lkap * k / (R(2) * mc.w1[1] * mc.w1[1]);
-        B.gD[c] += (double)(lw1 * R(1.7320508075688772));
+        B.gD[c] += lw1 * R(1.7320508075688772);
       }
     } else if (a.mode == 1 && (m & REG_MASK) == REG_CATALYST) {
       const R theta = own_sum<S, R>(src, 0, x, y) + a.theta0;
@@ -611,6 +611,23 @@ k_adj_seed_current(const S *__restrict__ src_p, const uint8_t *__restrict__ mask
   }
 #pragma unroll
   for (int q = 0; q < 24; ++q) B.lam_out[q * P + c] = l[q];
+}
+
+// Adds a segment's gradients (arithmetic type) into the FP64 totals and
+// clears them: n values per array, three arrays.
+template <typename R>
+__global__ void k_adj_fold(R *__restrict__ g0, R *__restrict__ g1, R *__restrict__ g2,
+                           double *__restrict__ t0, double *__restrict__ t1,
+                           double *__restrict__ t2, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    t0[i] += (double)g0[i];
+    t1[i] += (double)g1[i];
+    t2[i] += (double)g2[i];
+    g0[i] = R(0);
+    g1[i] = R(0);
+    g2[i] = R(0);
+  }
 }
 
 }  // namespace pemlbm

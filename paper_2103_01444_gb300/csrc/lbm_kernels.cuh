@@ -6,63 +6,9 @@
 #include "lbm_adjoint.cuh"
 #include "lbm_core.cuh"
 #include "lbm_launch.h"
+#include "lbm_step.cuh"
 
 namespace pemlbm {
-
-// ------------------------------------------------------------- step (K1)
-// One coupled update of cell (x, y): src -> dst.  Shared by the single-
-// domain step and the batched steps.
-template <typename S, bool CG = false>
-__device__ __forceinline__ void cell_update(const S *__restrict__ src_p, S *__restrict__ dst,
-                                            const uint8_t *__restrict__ mask,
-                                            const uint16_t *__restrict__ mid,
-                                            const MatCoef<typename Real<S>::type> *__restrict__ pal,
-                                            const KArgsT<typename Real<S>::type> &a, int x,
-                                            int y) {
-  using R = typename Real<S>::type;
-  const long long c = (long long)y * a.nxp + x;
-  const Pops<S, CG> src{src_p, a.plane, a.nxp};
-  const uint8_t m = mask[c];
-  Cell<R> cell;
-  load_interior<S, R, CG>(src, a, x, y, cell);
-  // solid cells run the same arithmetic on their (unused) values and only
-  // skip the stores, so no branch stands between the mask and the loads
-  const bool live = (m & REG_MASK) != REG_SOLID;
-  const MatCoef<R> mc = pal[mid[c]];
-  if (m & M_EDGE) fix_edges<S, R, CG>(src, a, mask, mid, pal, mc, x, y, m, cell);
-  if (a.mode == 0 && (m & M_YLO)) surface_reaction<S, R, CG>(src, a, mc, x, cell);
-  R S_vol = 0;
-  if (a.mode == 1 && (m & REG_MASK) == REG_CATALYST) S_vol = volume_sink<S, R, CG>(src, a, x, y);
-  const Macro<R> u = macros<R>(a, mc, cell);
-  R o[9];
-  collide_flow<R>(a, mc, u, cell.f, o);
-  S *out = dst + c;
-  if (live) {
-#pragma unroll
-    for (int i = 0; i < 9; ++i) st_r(out + (long long)i * a.plane, o[i]);
-  }
-  const R srcv[3] = {-S_vol * R(a.hpo) * mc.inv_sigma, S_vol, R(-2) * S_vol};
-#pragma unroll
-  for (int s = 0; s < 3; ++s) {
-    R g[5];
-    collide_scalar<R>(a, mc, s, u.ux, u.uy, u.C[s], cell.g[s], srcv[s], g);
-    if (live) {
-#pragma unroll
-      for (int i = 0; i < 5; ++i) st_r(out + (long long)(9 + 5 * s + i) * a.plane, g[i]);
-    }
-  }
-}
-
-template <typename S, int BX, int BY, int MINB>
-__global__ void __launch_bounds__(BX * BY, MINB)
-k_step(const S *__restrict__ src_p, S *__restrict__ dst, const uint8_t *__restrict__ mask,
-       const uint16_t *__restrict__ mid, const MatCoef<typename Real<S>::type> *__restrict__ pal,
-       KArgsT<typename Real<S>::type> a) {
-  const int x = blockIdx.x * BX + (threadIdx.x % BX);
-  const int y = blockIdx.y * BY + (threadIdx.x / BX);
-  if (x >= a.nx || y >= a.ny) return;
-  cell_update<S>(src_p, dst, mask, mid, pal, a, x, y);
-}
 
 // ---------------------------------------------------- batched steps (K6)
 // Many cases of uneven size advance together.  The tiles of all cases (BX x
@@ -284,7 +230,7 @@ k_residual(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
            typename Real<S>::type *__restrict__ snap, double *__restrict__ partial,
            int *__restrict__ bad) {
   using R = typename Real<S>::type;
-  __shared__ double sm[10 * 32];
+  __shared__ R sm[10 * 32];
   const Pops<S> src{src_p, a.plane, a.nxp};
   const int x = blockIdx.x * kResidualBX + (threadIdx.x % kResidualBX);
   const int y = blockIdx.y * kResidualBY + (threadIdx.x / kResidualBX);
@@ -313,21 +259,20 @@ k_residual(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
     }
     if (!ok) *bad = 1;
   }
-  double acc[10];
 #pragma unroll
   for (int k = 0; k < 10; ++k) {
-    R t = v[k];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
-    acc[k] = (double)t;   // lane 0 holds the warp sum; the rest is FP64
+    for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
   }
+  // lane 0 holds the warp sums; only they are widened (the FP64 pipe is
+  // narrow), and the block sum of the warp sums is FP64
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if (lane == 0)
-    for (int k = 0; k < 10; ++k) sm[k * 32 + warp] = acc[k];
+    for (int k = 0; k < 10; ++k) sm[k * 32 + warp] = v[k];
   __syncthreads();
   if (threadIdx.x < 10) {
     double t = 0.0;
-    for (int w = 0; w < nw; ++w) t += sm[threadIdx.x * 32 + w];
+    for (int w = 0; w < nw; ++w) t += (double)sm[threadIdx.x * 32 + w];
     partial[((long long)blockIdx.y * gridDim.x + blockIdx.x) * 10 + threadIdx.x] = t;
   }
 }
@@ -404,30 +349,6 @@ __global__ void k_set_state(S *__restrict__ pop, const uint8_t *__restrict__ mas
 
 // ------------------------------------------------------ launchers
 template <typename S, int V>
-void launch_step_v(const void *src, void *dst, const DevGeom &g, const KArgs &a, cudaStream_t st) {
-  constexpr StepShape sh = kStepShapes[V];
-  dim3 grid((a.nx + sh.bx - 1) / sh.bx, (a.ny + sh.by - 1) / sh.by);
-  k_step<S, sh.bx, sh.by, sh.minb><<<grid, sh.bx * sh.by, 0, st>>>(
-      (const S *)src, (S *)dst, g.mask, g.mid,
-      (const MatCoef<typename Real<S>::type> *)g.pal, narrow_args<typename Real<S>::type>(a));
-}
-
-template <typename S>
-void launch_step(const void *src, void *dst, const DevGeom &g, const KArgs &a, int variant,
-                 cudaStream_t st) {
-  switch (variant) {
-    case 1: launch_step_v<S, 1>(src, dst, g, a, st); break;
-    case 2: launch_step_v<S, 2>(src, dst, g, a, st); break;
-    case 3: launch_step_v<S, 3>(src, dst, g, a, st); break;
-    case 4: launch_step_v<S, 4>(src, dst, g, a, st); break;
-    case 5: launch_step_v<S, 5>(src, dst, g, a, st); break;
-    case 6: launch_step_v<S, 6>(src, dst, g, a, st); break;
-    case 7: launch_step_v<S, 7>(src, dst, g, a, st); break;
-    default: launch_step_v<S, 0>(src, dst, g, a, st); break;
-  }
-}
-
-template <typename S, int V>
 void launch_batch_v(const BatchCase *cases, const int *tile_start, int ncases, int total_tiles,
                     int parity, cudaStream_t st) {
   constexpr StepShape sh = kStepShapes[V];
@@ -473,8 +394,16 @@ cudaError_t launch_batch_persistent(const BatchCase *cases, const int *tile_star
 }
 
 template <typename R> AdjBufs<R> adj_bufs(const AdjPtrs &b) {
-  return AdjBufs<R>{(const R *)b.lam, (R *)b.M, (R *)b.O, (R *)b.V, b.gphi, b.gK, b.gD, b.gU,
-                    (R *)b.lam_out};
+  return AdjBufs<R>{(const R *)b.lam, (R *)b.M, (R *)b.O, (R *)b.V, (R *)b.gphi, (R *)b.gK,
+                    (R *)b.gD, b.gU, (R *)b.lam_out};
+}
+
+template <typename S>
+void launch_adj_fold(const DevGeom &g, const KArgs &a, const AdjPtrs &b, cudaStream_t st) {
+  using R = typename Real<S>::type;
+  (void)g;
+  k_adj_fold<R><<<4 * 152, 256, 0, st>>>((R *)b.gphi, (R *)b.gK, (R *)b.gD, b.tphi, b.tK, b.tD,
+                                         a.plane);
 }
 
 template <typename S>
@@ -596,6 +525,8 @@ void launch_set_state(void *pop, const DevGeom &g, const KArgs &a, const double 
                                     int, const AdjPtrs &, long long, cudaStream_t);             \
   template void launch_adj_gather<S>(const DevGeom &, const KArgs &, const AdjPtrs &,            \
                                      cudaStream_t);                                             \
+  template void launch_adj_fold<S>(const DevGeom &, const KArgs &, const AdjPtrs &,              \
+                                   cudaStream_t);                                               \
   template void launch_adj_seed_current<S>(const void *, const DevGeom &, const KArgs &, int,    \
                                            double, const AdjPtrs &, cudaStream_t);
 
