@@ -726,18 +726,47 @@ struct DevBuf {
 
 // Reverse workspace of one domain.
 struct AdjWork {
-  DevBuf lam[2], M, O, V, gphi, gK, gD, gU, tphi, tK, tD;
-  lbm_status alloc(const lbm_domain *d) {
+  DevBuf lam[2], O, V, gphi, gK, gD, gU, tphi, tK, tD, cells;
+  int n_edge = 0, n_own = 0;
+  lbm_status alloc(lbm_domain *d) {
     const size_t r = fp64(d) ? 8 : 4, planes = 24 * (size_t)d->plane;
     lbm_status s;
-    for (auto *b : {&lam[0], &lam[1], &M, &O})
+    for (auto *b : {&lam[0], &lam[1], &O})
       if ((s = b->alloc(planes * r)) != LBM_OK) return s;
+    // lambda^{n-1} of solid cells is zeroed by every step; the rest of both
+    // buffers starts at zero so that no stale value is ever read
+    for (auto *b : {&lam[0], &lam[1]}) CK(cudaMemsetAsync(b->p, 0, planes * r, d->stream));
     if ((s = V.alloc(20 * (size_t)d->ny * r)) != LBM_OK) return s;
     for (auto *b : {&gphi, &gK, &gD})
       if ((s = b->alloc(r * d->plane)) != LBM_OK) return s;
     for (auto *b : {&tphi, &tK, &tD})
       if ((s = b->alloc(sizeof(double) * d->plane)) != LBM_OK) return s;
     if ((s = gU.alloc(sizeof(double))) != LBM_OK) return s;
+    // cell lists: fluid cells with edge bits, then fluid catalyst cells of
+    // the volumetric mode without them (both use their own state)
+    std::vector<uint8_t> m((size_t)d->plane);
+    CK(cudaMemcpyAsync(m.data(), d->mask, m.size(), cudaMemcpyDeviceToHost, d->stream));
+    CK(cudaStreamSynchronize(d->stream));
+    std::vector<long long> list;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int y = 0; y < d->ny; ++y)
+        for (int x = 0; x < d->nx; ++x) {
+          const long long c = (long long)y * d->nxp + x;
+          const uint8_t b = m[c];
+          if ((b & REG_MASK) == REG_SOLID) continue;
+          const bool edge = (b & M_EDGE) != 0;
+          const bool vol = d->desc.reaction_mode == 1 && (b & REG_MASK) == REG_CATALYST;
+          if (pass == 0 ? edge : (vol && !edge)) list.push_back(c);
+        }
+      if (pass == 0) n_edge = (int)list.size();
+    }
+    n_own = (int)list.size();
+    if (n_own > 0) {
+      if ((s = cells.alloc(sizeof(long long) * list.size())) != LBM_OK) return s;
+      CK(cudaMemcpyAsync(cells.p, list.data(), sizeof(long long) * list.size(),
+                         cudaMemcpyHostToDevice, d->stream));
+      CK(cudaStreamSynchronize(d->stream));
+    }
     return LBM_OK;
   }
   lbm_status zero_grads(const lbm_domain *d) {
@@ -748,8 +777,9 @@ struct AdjWork {
     return LBM_OK;
   }
   AdjPtrs ptrs(int cur) {
-    return AdjPtrs{lam[cur].p, M.p, O.p, V.p, gphi.p, gK.p, gD.p, (double *)gU.p,
-                   lam[cur ^ 1].p, (double *)tphi.p, (double *)tK.p, (double *)tD.p};
+    return AdjPtrs{lam[cur].p, O.p, V.p, gphi.p, gK.p, gD.p, (double *)gU.p,
+                   lam[cur ^ 1].p, (double *)tphi.p, (double *)tK.p, (double *)tD.p,
+                   (const long long *)cells.p, n_edge, n_own};
   }
 };
 
@@ -770,8 +800,7 @@ void reverse_step(lbm_domain *d, AdjWork &w, int cur, const void *src, long long
   const AdjPtrs b = w.ptrs(cur);
   dispatch(d->desc.precision, [&](auto *tag) {
     using S = std::remove_pointer_t<decltype(tag)>;
-    launch_adj_local<S>(src, geom(d), d->raw, a, fick, b, seed_cell, d->stream);
-    launch_adj_gather<S>(geom(d), a, b, d->stream);
+    launch_adj_step<S>(src, geom(d), a, fick, b, seed_cell, d->stream);
   });
 }
 

@@ -4,17 +4,22 @@
 // s^n(x) = C_x(P_x(s^{n-1}), theta_x), where P_x pulls the 24 populations
 // (plain links from neighbours, boundary links from the cell itself, the
 // outlet's virtual cells, the inlet velocity) and C_x relaxes them (Eq. 1,
-// 8, 10) with the catalyst terms (Eq. 12-17).  The transpose is applied in
-// two kernels per step:
-//   k_adj_local (one thread per cell x): recomputes the forward update of x
-//     from s^{n-1}, back-propagates lambda^n(x) through C_x, and splits the
-//     result over the pull: the adjoint of each plain link goes to M(x, q),
-//     the adjoint of values x took from its own state goes to O(x, q), the
-//     outlet's uses of the cells above and below go to the outlet buffers,
-//     and the parameter adjoints of x accumulate in FP64.
-//   k_adj_gather (one thread per cell y): lambda^{n-1}(y, q) = M(y + e_q, q)
-//     when that neighbour is fluid (every plain link has exactly one
-//     consumer), plus O(y, q), plus the outlet contributions.
+// 8, 10) with the catalyst terms (Eq. 12-17).  Every plain link (y, q) of
+// s^{n-1} has exactly one consumer, the fluid cell y + e_q, so the transpose
+// of the pull is a push: the consumer writes the adjoint of what it pulled
+// straight into lambda^{n-1}(y, q).  Three kernels per step:
+//   k_adj_interior (one thread per cell; cells without edge bits): recomputes
+//     the forward update of x from s^{n-1}, back-propagates lambda^n(x)
+//     through C_x, pushes the 24 link adjoints to the source cells and
+//     accumulates the parameter adjoints of x.  Catalyst cells of the
+//     volumetric mode also read their own state; that adjoint goes to O(x).
+//     Solid cells zero their own lambda^{n-1}.
+//   k_adj_edge (one thread per listed edge cell): the same for cells with
+//     boundary links; the adjoint of values taken from the cell's own state
+//     goes to O(x, q), the outlet's uses of the cells above and below to V.
+//   k_adj_fix (one thread per listed own-use cell y): lambda^{n-1}(y, q) =
+//     (pushed value if y + e_q is a fluid consumer, else 0) + O(y, q) + the
+//     outlet terms.
 // Storage is the domain's storage type S; arithmetic is R.
 #pragma once
 #include "lbm_core.cuh"
@@ -24,8 +29,7 @@ namespace pemlbm {
 // Per-step adjoint workspace (device pointers).
 template <typename R> struct AdjBufs {
   const R *lam;      // lambda^n, [24][plane] (deviation coordinates = full coordinates)
-  R *M;              // pull adjoints [24][plane]
-  R *O;              // own-use adjoints [24][plane]
+  R *O;              // own-use adjoints [24][plane] (own-use cells only)
   R *V;              // outlet column: [2][10][ny] (down: from y+1 to y, up: from y-1 to y)
   R *gphi, *gK, *gD;        // per-cell parameter gradients of the current segment [plane]
   double *gU;               // d objective / d u_in_avg
@@ -197,17 +201,6 @@ template <typename R> __device__ __forceinline__ R drate_dtheta(const KArgsT<R> 
   return -R(a.k_c1) * k / (T * T);
 }
 
-// Adds lam_theta to the five own T populations and lam_C to the own O2 ones.
-template <typename R>
-__device__ __forceinline__ void own_sums_rev(R *__restrict__ O, long long c, long long P,
-                                             R lam_theta, R lam_C) {
-#pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    O[(9 + k) * P + c] += lam_theta;
-    O[(14 + k) * P + c] += lam_C;
-  }
-}
-
 // Parameter chain of one cell: adjoints of the derived coefficients to the
 // caller's fields phi, K and D_O2 (Eq. 7, 8, 10), in the arithmetic type,
 // accumulated per checkpoint segment (k_adj_fold adds each segment into the
@@ -249,21 +242,18 @@ template <typename R> __device__ __forceinline__ R dinlet_du(const KArgsT<R> &a,
   return (s <= R(0) || s >= R(1)) ? R(0) : R(6) * s * (R(1) - s);
 }
 
-// Reverse of the pull of one flow link i at cell (x, y).  lam is the adjoint
-// of the pulled value; the result goes to Mloc (plain link), Oacc (own
-// populations), the outlet's virtual-cell adjoints or the inlet velocity.
+// Reverse of the pull of one flow link i at edge cell (x, y).  lam is the
+// adjoint of the pulled value; it is pushed to lambda^{n-1} of the source
+// (plain link, `out`), or goes to Oacc (own populations), the outlet's
+// virtual-cell adjoints or the inlet velocity.
 template <typename S, typename R>
 __device__ __forceinline__ void pull_flow_rev(const Pops<S> &src, const KArgsT<R> &a,
                                               const uint8_t *__restrict__ mask,
                                               const uint16_t *__restrict__ mid,
                                               const MatCoef<R> *__restrict__ pal, int i, int x,
-                                              int y, uint8_t m, R lam, R *Mloc, R *Oacc,
-                                              R *Vdn, R *Vup, R &lip_own, R &lU) {
+                                              int y, uint8_t m, R lam, R *__restrict__ out,
+                                              R *Oacc, R *Vdn, R *Vup, R &lip_own, R &lU) {
   const int EX[9] = EX9_TAB, EY[9] = EY9_TAB, OP[9] = OP9_TAB;
-  if (i == 0 || !(m & M_EDGE)) {
-    Mloc[i] = lam;
-    return;
-  }
   int sx = x - EX[i], sy = y - EY[i];
   if (sy < 0 || sy >= a.ny) {
     Oacc[OP[i]] += lam;
@@ -302,31 +292,24 @@ __device__ __forceinline__ void pull_flow_rev(const Pops<S> &src, const KArgsT<R
       }
       return;
     }
-    if ((m & M_NEAR_SOLID) && (mask[(long long)sy * a.nxp + sx] & REG_MASK) == REG_SOLID) {
-      Oacc[OP[i]] += lam;
-      return;
-    }
-    Mloc[i] = lam;   // periodic wrap: a plain link
-    return;
   }
-  if ((m & M_NEAR_SOLID) && (mask[(long long)sy * a.nxp + sx] & REG_MASK) == REG_SOLID) {
+  // plain link (possibly across the periodic seam) unless the source is solid
+  const long long sc = (long long)sy * a.nxp + sx;
+  if ((m & M_NEAR_SOLID) && (mask[sc] & REG_MASK) == REG_SOLID) {
     Oacc[OP[i]] += lam;
     return;
   }
-  Mloc[i] = lam;
+  out[(long long)i * a.plane + sc] = lam;
 }
 
-// Reverse of the pull of link i of scalar s.
+// Reverse of the pull of link i of scalar s at edge cell (x, y).
 template <typename R>
 __device__ __forceinline__ void pull_scalar_rev(const KArgsT<R> &a, const uint8_t *__restrict__ mask,
                                                 const MatCoef<R> &mc, int s, int i, int x, int y,
-                                                uint8_t m, R lam, R *Mloc, R *Oacc, R &lw1) {
+                                                uint8_t m, R lam, R *__restrict__ out, R *Oacc,
+                                                R &lw1) {
   const int EX[5] = {0, 1, 0, -1, 0}, EY[5] = {0, 0, 1, 0, -1}, OP[5] = {0, 3, 4, 1, 2};
   const int q = 9 + 5 * s;
-  if (i == 0 || !(m & M_EDGE)) {
-    Mloc[q + i] = lam;
-    return;
-  }
   int sx = x - EX[i], sy = y - EY[i];
   if (sy < 0) {
     Oacc[q + OP[i]] += lam;
@@ -357,201 +340,238 @@ __device__ __forceinline__ void pull_scalar_rev(const KArgsT<R> &a, const uint8_
       return;
     }
   }
-  if ((m & M_NEAR_SOLID) && (mask[(long long)sy * a.nxp + sx] & REG_MASK) == REG_SOLID) {
+  const long long sc = (long long)sy * a.nxp + sx;
+  if ((m & M_NEAR_SOLID) && (mask[sc] & REG_MASK) == REG_SOLID) {
     Oacc[q + OP[i]] += lam;
     return;
   }
-  Mloc[q + i] = lam;
+  out[(long long)(q + i) * a.plane + sc] = lam;
 }
 
-// Local adjoint of one step (see the file comment).  seed_cell >= 0 turns
-// the kernel into the seed of the "CL temperature" objective: the adjoint of
-// the pulled temperature populations of that cell is 1 (others 0) and the
-// collision is not traversed.
-template <typename S>
-__global__ void __launch_bounds__(128)
-k_adj_local(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
-            const uint16_t *__restrict__ mid,
-            const MatCoef<typename Real<S>::type> *__restrict__ pal,
-            const MatRaw *__restrict__ raw, KArgsT<typename Real<S>::type> a, int fickian,
-            AdjBufs<typename Real<S>::type> B, long long seed_cell) {
+// Reverse of one fluid cell's update (see the file comment).  EDGE selects
+// the edge-cell form: boundary pulls, the surface reaction, own-use and
+// outlet adjoints, the inlet velocity and the seed of the "CL temperature"
+// objective (seed_cell >= 0: the adjoint of the pulled temperature
+// populations of that cell is 1 on top of a zero lambda^n).
+template <typename S, bool EDGE>
+__device__ __forceinline__ void adj_cell(const S *__restrict__ src_p,
+                                         const uint8_t *__restrict__ mask,
+                                         const uint16_t *__restrict__ mid,
+                                         const MatCoef<typename Real<S>::type> *__restrict__ pal,
+                                         const KArgsT<typename Real<S>::type> &a, int fickian,
+                                         const AdjBufs<typename Real<S>::type> &B, int x, int y,
+                                         long long c, uint8_t m, long long seed_cell,
+                                         typename Real<S>::type &lU) {
   using R = typename Real<S>::type;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-  R lU = 0;
-  if (x < a.nx && y < a.ny) {
-    const long long c = (long long)y * a.nxp + x, P = a.plane;
-    const uint8_t m = mask[c];
-    R Mloc[24], Oacc[24];
+  const long long P = a.plane, W = a.nxp;
+  const Pops<S> src{src_p, a.plane, a.nxp};
+  const MatCoef<R> mc = pal[mid[c]];
+  Cell<R> cell;
+  if constexpr (EDGE) pull_cell<S, R>(src, a, mask, mid, pal, mc, x, y, m, cell);
+  else load_interior<S, R>(src, a, x, y, cell);
+  // forward reaction terms (kept for the reverse)
+  const bool surf = EDGE && a.mode == 0 && (m & M_YLO);
+  const bool vol = a.mode == 1 && (m & REG_MASK) == REG_CATALYST;
+  R theta = 0, k = 0, kappa = 0, gd = 0, Cv = 0;
+  if (surf || vol) theta = own_sum<S, R>(src, 0, x, y) + a.theta0;
+  if (surf) {
+    k = rate<R>(a, R(a.kA_surf), theta);
+    kappa = k / (R(2) * mc.w1[1]);
+    gd = cell.g[1][2] + R(a.wr1[1]) * R(a.Cref[1]);
+    const R Jv = gd * (R(2) * kappa) / (R(1) + kappa);
+    cell.g[1][2] -= Jv;
+    cell.g[0][2] += R(a.hpo) * mc.inv_sigma * Jv;
+    cell.g[2][2] += R(2) * Jv;
+  }
+  R S_vol = 0;
+  if (vol) {
+    Cv = own_sum<S, R>(src, 1, x, y) + R(a.Cref[1]);
+    k = rate<R>(a, R(a.kA_vol), theta);
+    S_vol = -k * Cv / (R(1) + k);
+  }
+  // ---- reverse of the collisions
+  R lcf[9], lcg[3][5];
 #pragma unroll
-    for (int q = 0; q < 24; ++q) Mloc[q] = Oacc[q] = R(0);
-    R Vdn[10], Vup[10];
+  for (int i = 0; i < 9; ++i) lcf[i] = R(0);
+  R lphi = 0, ldarcy = 0, lforch = 0, ll0 = 0, ll1 = 0, lip = 0;
+  R lb[3] = {0, 0, 0}, lw1[3] = {0, 0, 0}, lq1[3] = {0, 0, 0}, lsrc[3] = {0, 0, 0};
+  R lth_own = 0, lC_own = 0;   // own-use adjoints of the reaction (theta, C_O2)
+  {
+    const Macro<R> u = macros<R>(a, mc, cell);
+    const R srcv[3] = {-S_vol * R(a.hpo) * mc.inv_sigma, S_vol, R(-2) * S_vol};
+    R lux = 0, luy = 0;
 #pragma unroll
-    for (int k = 0; k < 10; ++k) Vdn[k] = Vup[k] = R(0);
-    const bool outlet = !a.periodic && x == a.nx - 1;
-    if ((m & REG_MASK) != REG_SOLID) {
-      const Pops<S> src{src_p, a.plane, a.nxp};
-      const MatCoef<R> mc = pal[mid[c]];
-      Cell<R> cell;
-      pull_cell<S, R>(src, a, mask, mid, pal, mc, x, y, m, cell);
-      // forward reaction terms (kept for the reverse)
-      const bool surf = a.mode == 0 && (m & M_YLO);
-      const bool vol = a.mode == 1 && (m & REG_MASK) == REG_CATALYST;
-      R theta = 0, k = 0, kappa = 0, gd = 0, Jv = 0, Cv = 0;
-      if (surf || vol) theta = own_sum<S, R>(src, 0, x, y) + a.theta0;
-      if (surf) {
-        k = rate<R>(a, R(a.kA_surf), theta);
-        kappa = k / (R(2) * mc.w1[1]);
-        gd = cell.g[1][2] + R(a.wr1[1]) * R(a.Cref[1]);
-        Jv = gd * (R(2) * kappa) / (R(1) + kappa);
-        cell.g[1][2] -= Jv;
-        cell.g[0][2] += R(a.hpo) * mc.inv_sigma * Jv;
-        cell.g[2][2] += R(2) * Jv;
+    for (int s = 0; s < 3; ++s) {
+      R lo[5];
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        lo[i] = B.lam[(9 + 5 * s + i) * P + c];
+        lcg[s][i] = R(0);
       }
-      R S_vol = 0;
-      if (vol) {
-        Cv = own_sum<S, R>(src, 1, x, y) + R(a.Cref[1]);
-        k = rate<R>(a, R(a.kA_vol), theta);
-        S_vol = -k * Cv / (R(1) + k);
-      }
-      // ---- reverse of the collisions
-      R lcf[9], lcg[3][5];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) lcf[i] = R(0);
-#pragma unroll
-      for (int s = 0; s < 3; ++s)
-#pragma unroll
-        for (int i = 0; i < 5; ++i) lcg[s][i] = R(0);
-      R lphi = 0, ldarcy = 0, lforch = 0, ll0 = 0, ll1 = 0, lip = 0;
-      R lb[3] = {0, 0, 0}, lw1[3] = {0, 0, 0}, lq1[3] = {0, 0, 0}, lsrc[3] = {0, 0, 0};
-      if (seed_cell < 0) {
-        const Macro<R> u = macros<R>(a, mc, cell);
-        const R srcv[3] = {-S_vol * R(a.hpo) * mc.inv_sigma, S_vol, R(-2) * S_vol};
-        R lux = 0, luy = 0;
-#pragma unroll
-        for (int s = 0; s < 3; ++s) {
-          R lo[5];
-#pragma unroll
-          for (int i = 0; i < 5; ++i) lo[i] = B.lam[(9 + 5 * s + i) * P + c];
-          collide_scalar_rev<R>(a, mc, s, u.ux, u.uy, u.C[s], cell.g[s], srcv[s], lo, lcg[s], lux,
-                                luy, lsrc[s], lb[s], lw1[s], lq1[s]);
-        }
-        R lo[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) lo[i] = B.lam[i * P + c];
-        flow_rev<R>(a, mc, cell.f, lo, lux, luy, lcf, lphi, ldarcy, lforch, ll0, ll1, lip);
-        // volumetric sources: (-S h / sigma, S, -2 S)
-        if (vol) {
-          const R lS = -R(a.hpo) * mc.inv_sigma * lsrc[0] + lsrc[1] - R(2) * lsrc[2];
-          const R lC = lS * (-k / (R(1) + k));
-          const R lk = lS * (-Cv / ((R(1) + k) * (R(1) + k)));
-          const R lth = lk * drate_dtheta<R>(a, k, theta);
-#pragma unroll
-          for (int q = 0; q < 5; ++q) {
-            Oacc[9 + q] += lth;
-            Oacc[14 + q] += lC;
-          }
-        }
-      } else if (c == seed_cell) {
-#pragma unroll
-        for (int i = 0; i < 5; ++i) lcg[0][i] = R(1);
-      }
-      // ---- reverse of the surface reaction (post -> pre link values)
-      if (surf) {
-        const R lJ = -lcg[1][2] + R(a.hpo) * mc.inv_sigma * lcg[0][2] + R(2) * lcg[2][2];
-        const R lgd = lJ * R(2) * kappa / (R(1) + kappa);
-        const R lkap = lJ * R(2) * gd / ((R(1) + kappa) * (R(1) + kappa));
-        const R lk = lkap / (R(2) * mc.w1[1]);
-        lw1[1] += -lkap * k / (R(2) * mc.w1[1] * mc.w1[1]);
-        const R lth = lk * drate_dtheta<R>(a, k, theta);
-#pragma unroll
-        for (int q = 0; q < 5; ++q) Oacc[9 + q] += lth;
-        lcg[1][2] += lgd;
-      }
-      // ---- reverse of the pull
-#pragma unroll
-      for (int i = 0; i < 9; ++i)
-        pull_flow_rev<S, R>(src, a, mask, mid, pal, i, x, y, m, lcf[i], Mloc, Oacc, Vdn, Vup, lip, lU);
-#pragma unroll
-      for (int s = 0; s < 3; ++s)
+      collide_scalar_rev<R>(a, mc, s, u.ux, u.uy, u.C[s], cell.g[s], srcv[s], lo, lcg[s], lux,
+                            luy, lsrc[s], lb[s], lw1[s], lq1[s]);
+      if constexpr (!EDGE) {
+        // interior: every link is plain; push as soon as the scalar is done
+        const int EX5[5] = {0, 1, 0, -1, 0}, EY5[5] = {0, 0, 1, 0, -1};
 #pragma unroll
         for (int i = 0; i < 5; ++i)
-          pull_scalar_rev<R>(a, mask, mc, s, i, x, y, m, lcg[s][i], Mloc, Oacc, lw1[s]);
-      // ---- parameters of this cell
-      param_rev<R>(a, mc, fickian, lphi, ldarcy, lforch, ll0, ll1, lip, lb[1], lw1[1], lq1[1],
-                   B.gphi + c, B.gK + c, B.gD + c);
+          B.lam_out[(9 + 5 * s + i) * P + c - EY5[i] * W - EX5[i]] = lcg[s][i];
+      }
     }
-    // O is written (and later read) only by cells that use their own state
-    const bool own = (m & M_EDGE) || (a.mode == 1 && (m & REG_MASK) == REG_CATALYST);
+    R lo[9];
 #pragma unroll
-    for (int q = 0; q < 24; ++q) B.M[q * P + c] = Mloc[q];
-    if (own) {
+    for (int i = 0; i < 9; ++i) lo[i] = B.lam[i * P + c];
+    flow_rev<R>(a, mc, cell.f, lo, lux, luy, lcf, lphi, ldarcy, lforch, ll0, ll1, lip);
+  }
+  // volumetric sources: (-S h / sigma, S, -2 S)
+  if (vol) {
+    const R lS = -R(a.hpo) * mc.inv_sigma * lsrc[0] + lsrc[1] - R(2) * lsrc[2];
+    lC_own = lS * (-k / (R(1) + k));
+    const R lk = lS * (-Cv / ((R(1) + k) * (R(1) + k)));
+    lth_own = lk * drate_dtheta<R>(a, k, theta);
+  }
+  if constexpr (!EDGE) {
+    const int EX[9] = EX9_TAB, EY[9] = EY9_TAB;
 #pragma unroll
-      for (int q = 0; q < 24; ++q) B.O[q * P + c] = Oacc[q];
+    for (int i = 0; i < 9; ++i) B.lam_out[i * P + c - EY[i] * W - EX[i]] = lcf[i];
+    if (vol) {
+#pragma unroll
+      for (int q = 0; q < 24; ++q)
+        B.O[q * P + c] = q >= 9 && q < 14 ? lth_own : (q >= 14 && q < 19 ? lC_own : R(0));
     }
-    if (outlet) {
+  } else {
+    R Oacc[24];
 #pragma unroll
-      for (int k = 0; k < 10; ++k) {
-        B.V[(0 * 10 + k) * a.ny + y] = Vdn[k];
-        B.V[(1 * 10 + k) * a.ny + y] = Vup[k];
+    for (int q = 0; q < 24; ++q) Oacc[q] = q >= 9 && q < 14 ? lth_own : (q >= 14 && q < 19 ? lC_own : R(0));
+    R Vdn[10], Vup[10];
+#pragma unroll
+    for (int kk = 0; kk < 10; ++kk) Vdn[kk] = Vup[kk] = R(0);
+    if (c == seed_cell) {
+#pragma unroll
+      for (int i = 0; i < 5; ++i) lcg[0][i] += R(1);
+    }
+    // ---- reverse of the surface reaction (post -> pre link values)
+    if (surf) {
+      const R lJ = -lcg[1][2] + R(a.hpo) * mc.inv_sigma * lcg[0][2] + R(2) * lcg[2][2];
+      const R lgd = lJ * R(2) * kappa / (R(1) + kappa);
+      const R lkap = lJ * R(2) * gd / ((R(1) + kappa) * (R(1) + kappa));
+      const R lk = lkap / (R(2) * mc.w1[1]);
+      lw1[1] += -lkap * k / (R(2) * mc.w1[1] * mc.w1[1]);
+      const R lth = lk * drate_dtheta<R>(a, k, theta);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) Oacc[9 + q] += lth;
+      lcg[1][2] += lgd;
+    }
+    // ---- reverse of the pull
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+      pull_flow_rev<S, R>(src, a, mask, mid, pal, i, x, y, m, lcf[i], B.lam_out, Oacc, Vdn, Vup,
+                          lip, lU);
+#pragma unroll
+    for (int s = 0; s < 3; ++s)
+#pragma unroll
+      for (int i = 0; i < 5; ++i)
+        pull_scalar_rev<R>(a, mask, mc, s, i, x, y, m, lcg[s][i], B.lam_out, Oacc, lw1[s]);
+#pragma unroll
+    for (int q = 0; q < 24; ++q) B.O[q * P + c] = Oacc[q];
+    if (!a.periodic && x == a.nx - 1) {
+#pragma unroll
+      for (int kk = 0; kk < 10; ++kk) {
+        B.V[(0 * 10 + kk) * a.ny + y] = Vdn[kk];
+        B.V[(1 * 10 + kk) * a.ny + y] = Vup[kk];
       }
     }
   }
-  // inlet velocity: warp sum, one FP64 atomic per warp that has inlet cells
-  R t = lU;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
-  if ((threadIdx.x & 31) == 0 && t != R(0)) atomicAdd(B.gU, (double)t);
+  // ---- parameters of this cell
+  param_rev<R>(a, mc, fickian, lphi, ldarcy, lforch, ll0, ll1, lip, lb[1], lw1[1], lq1[1],
+               B.gphi + c, B.gK + c, B.gD + c);
 }
 
-// lambda^{n-1}(y, q) = M(y + e_q, q) [fluid consumer] + O(y, q) + outlet terms.
-template <typename R>
+// Cells without edge bits, one thread per cell (grid over the lattice);
+// solid cells zero their own lambda^{n-1} (nothing is ever pushed there).
+template <typename S>
 __global__ void __launch_bounds__(128)
-k_adj_gather(const uint8_t *__restrict__ mask, const uint16_t *__restrict__ mid,
-             const MatCoef<R> *__restrict__ pal, KArgsT<R> a, AdjBufs<R> B) {
+k_adj_interior(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
+               const uint16_t *__restrict__ mid,
+               const MatCoef<typename Real<S>::type> *__restrict__ pal,
+               KArgsT<typename Real<S>::type> a, int fickian,
+               AdjBufs<typename Real<S>::type> B) {
+  using R = typename Real<S>::type;
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   if (x >= a.nx || y >= a.ny) return;
-  const long long c = (long long)y * a.nxp + x, P = a.plane;
-  const uint8_t my = mask[c];
-  const bool solid = (my & REG_MASK) == REG_SOLID;
-  const bool own = (my & M_EDGE) || (a.mode == 1 && (my & REG_MASK) == REG_CATALYST);
+  const long long c = (long long)y * a.nxp + x;
+  const uint8_t m = mask[c];
+  if ((m & REG_MASK) == REG_SOLID) {
+#pragma unroll
+    for (int q = 0; q < 24; ++q) B.lam_out[q * a.plane + c] = R(0);
+    return;
+  }
+  if (m & M_EDGE) return;
+  R lU = 0;
+  adj_cell<S, false>(src_p, mask, mid, pal, a, fickian, B, x, y, c, m, -1, lU);
+}
+
+// Fluid cells with edge bits, one thread per entry of `cells` (linear cell
+// indices y * nxp + x).
+template <typename S>
+__global__ void __launch_bounds__(128)
+k_adj_edge(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
+           const uint16_t *__restrict__ mid,
+           const MatCoef<typename Real<S>::type> *__restrict__ pal,
+           KArgsT<typename Real<S>::type> a, int fickian, AdjBufs<typename Real<S>::type> B,
+           const long long *__restrict__ cells, int ncells, long long seed_cell) {
+  using R = typename Real<S>::type;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  R lU = 0;
+  if (t < ncells) {
+    const long long c = cells[t];
+    const int y = (int)(c / a.nxp), x = (int)(c - (long long)y * a.nxp);
+    adj_cell<S, true>(src_p, mask, mid, pal, a, fickian, B, x, y, c, mask[c], seed_cell, lU);
+  }
+  // inlet velocity: warp sum, one FP64 atomic per warp that has inlet cells
+  R s = lU;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0 && s != R(0)) atomicAdd(B.gU, (double)s);
+}
+
+// Own-use cells (edge cells, then catalyst cells of the volumetric mode),
+// one thread per entry of `cells`: lambda^{n-1}(y, q) = pushed value (if
+// y + e_q is a fluid consumer) + O(y, q) + the outlet's uses of y.
+template <typename R>
+__global__ void __launch_bounds__(128)
+k_adj_fix(const uint8_t *__restrict__ mask, const uint16_t *__restrict__ mid,
+          const MatCoef<R> *__restrict__ pal, KArgsT<R> a, AdjBufs<R> B,
+          const long long *__restrict__ cells, int ncells) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ncells) return;
+  const long long c = cells[t], P = a.plane;
+  const int y = (int)(c / a.nxp), x = (int)(c - (long long)y * a.nxp);
   const int EX9[9] = EX9_TAB, EY9[9] = EY9_TAB;
   const int EX5[5] = {0, 1, 0, -1, 0}, EY5[5] = {0, 0, 1, 0, -1};
   const bool outlet = !a.periodic && x == a.nx - 1;
-  R vsum_ip = 0;
-  if (!solid && !own) {
-    // interior cell: every consumer y + e_q exists and is fluid
-    const long long W = a.nxp;
-#pragma unroll
-    for (int q = 0; q < 24; ++q) {
-      const int ex = q < 9 ? EX9[q] : EX5[(q - 9) % 5];
-      const int ey = q < 9 ? EY9[q] : EY5[(q - 9) % 5];
-      B.lam_out[q * P + c] = B.M[q * P + c + ey * W + ex];
-    }
-    return;
-  }
 #pragma unroll
   for (int q = 0; q < 24; ++q) {
-    R l = 0;
-    if (!solid) {
-      const int ex = q < 9 ? EX9[q] : EX5[(q - 9) % 5];
-      const int ey = q < 9 ? EY9[q] : EY5[(q - 9) % 5];
-      int cx = x + ex, cy = y + ey;
-      if (cy >= 0 && cy < a.ny) {
-        if (a.periodic) cx = cx < 0 ? cx + a.nx : (cx >= a.nx ? cx - a.nx : cx);
-        if (cx >= 0 && cx < a.nx) {
-          const long long cc = (long long)cy * a.nxp + cx;
-          if ((mask[cc] & REG_MASK) != REG_SOLID) l += B.M[q * P + cc];
-        }
-      }
-      if (own) l += B.O[q * P + c];
-      if (outlet && q < 9) {
-        if (y + 1 < a.ny) l += B.V[(0 * 10 + q) * a.ny + (y + 1)];
-        if (y - 1 >= 0) l += B.V[(1 * 10 + q) * a.ny + (y - 1)];
-      }
+    const int ex = q < 9 ? EX9[q] : EX5[(q - 9) % 5];
+    const int ey = q < 9 ? EY9[q] : EY5[(q - 9) % 5];
+    int cx = x + ex;
+    const int cy = y + ey;
+    bool pushed = false;
+    if (cy >= 0 && cy < a.ny) {
+      if (a.periodic) cx = cx < 0 ? cx + a.nx : (cx >= a.nx ? cx - a.nx : cx);
+      if (cx >= 0 && cx < a.nx)
+        pushed = (mask[(long long)cy * a.nxp + cx] & REG_MASK) != REG_SOLID;
+    }
+    R l = pushed ? B.lam_out[q * P + c] : R(0);
+    l += B.O[q * P + c];
+    if (outlet && q < 9) {
+      if (y + 1 < a.ny) l += B.V[(0 * 10 + q) * a.ny + (y + 1)];
+      if (y - 1 >= 0) l += B.V[(1 * 10 + q) * a.ny + (y - 1)];
     }
     B.lam_out[q * P + c] = l;
   }
-  if (outlet && !solid) {
+  if (outlet) {
+    R vsum_ip = 0;
     if (y + 1 < a.ny) vsum_ip += B.V[(0 * 10 + 9) * a.ny + (y + 1)];
     if (y - 1 >= 0) vsum_ip += B.V[(1 * 10 + 9) * a.ny + (y - 1)];
     const R ip = pal[mid[c]].inv_phi;

@@ -394,7 +394,7 @@ cudaError_t launch_batch_persistent(const BatchCase *cases, const int *tile_star
 }
 
 template <typename R> AdjBufs<R> adj_bufs(const AdjPtrs &b) {
-  return AdjBufs<R>{(const R *)b.lam, (R *)b.M, (R *)b.O, (R *)b.V, (R *)b.gphi, (R *)b.gK,
+  return AdjBufs<R>{(const R *)b.lam, (R *)b.O, (R *)b.V, (R *)b.gphi, (R *)b.gK,
                     (R *)b.gD, b.gU, (R *)b.lam_out};
 }
 
@@ -406,21 +406,24 @@ void launch_adj_fold(const DevGeom &g, const KArgs &a, const AdjPtrs &b, cudaStr
                                          a.plane);
 }
 
+// One reverse step: interior cells, then edge cells (both push into
+// lambda^{n-1}), then the own-use fix-up.
 template <typename S>
-void launch_adj_local(const void *src, const DevGeom &g, const MatRaw *raw, const KArgs &a,
-                      int fickian, const AdjPtrs &b, long long seed_cell, cudaStream_t st) {
+void launch_adj_step(const void *src, const DevGeom &g, const KArgs &a, int fickian,
+                     const AdjPtrs &b, long long seed_cell, cudaStream_t st) {
   using R = typename Real<S>::type;
-  dim3 grid((a.nx + 127) / 128, a.ny);
-  k_adj_local<S><<<grid, 128, 0, st>>>((const S *)src, g.mask, g.mid, (const MatCoef<R> *)g.pal,
-                                       raw, narrow_args<R>(a), fickian, adj_bufs<R>(b), seed_cell);
-}
-
-template <typename S>
-void launch_adj_gather(const DevGeom &g, const KArgs &a, const AdjPtrs &b, cudaStream_t st) {
-  using R = typename Real<S>::type;
-  dim3 grid((a.nx + 127) / 128, a.ny);
-  k_adj_gather<R><<<grid, 128, 0, st>>>(g.mask, g.mid, (const MatCoef<R> *)g.pal,
-                                        narrow_args<R>(a), adj_bufs<R>(b));
+  const KArgsT<R> an = narrow_args<R>(a);
+  const AdjBufs<R> B = adj_bufs<R>(b);
+  const MatCoef<R> *pal = (const MatCoef<R> *)g.pal;
+  k_adj_interior<S><<<dim3((a.nx + 127) / 128, a.ny), 128, 0, st>>>((const S *)src, g.mask, g.mid,
+                                                                    pal, an, fickian, B);
+  if (b.n_edge > 0)
+    k_adj_edge<S><<<(b.n_edge + 127) / 128, 128, 0, st>>>((const S *)src, g.mask, g.mid, pal, an,
+                                                          fickian, B, b.cells, b.n_edge,
+                                                          seed_cell);
+  if (b.n_own > 0)
+    k_adj_fix<R><<<(b.n_own + 127) / 128, 128, 0, st>>>(g.mask, g.mid, pal, an, B, b.cells,
+                                                        b.n_own);
 }
 
 template <typename S>
@@ -521,10 +524,8 @@ void launch_set_state(void *pop, const DevGeom &g, const KArgs &a, const double 
   template cudaError_t launch_batch_persistent<S>(const BatchCase *, const int *, int, int, int, \
                                                   unsigned *, int *, long long, cudaStream_t);  \
   template void batch_upload<S>(const BatchCase *, int, void *, void *, cudaStream_t);         \
-  template void launch_adj_local<S>(const void *, const DevGeom &, const MatRaw *, const KArgs &, \
-                                    int, const AdjPtrs &, long long, cudaStream_t);             \
-  template void launch_adj_gather<S>(const DevGeom &, const KArgs &, const AdjPtrs &,            \
-                                     cudaStream_t);                                             \
+  template void launch_adj_step<S>(const void *, const DevGeom &, const KArgs &, int,              \
+                                   const AdjPtrs &, long long, cudaStream_t);                      \
   template void launch_adj_fold<S>(const DevGeom &, const KArgs &, const AdjPtrs &,              \
                                    cudaStream_t);                                               \
   template void launch_adj_seed_current<S>(const void *, const DevGeom &, const KArgs &, int,    \

@@ -60,14 +60,15 @@ template <typename S> cudaError_t launch_batch_persistent(const BatchCase *cases
 // Buffers of one reverse step (types follow the domain's arithmetic).
 struct AdjPtrs {
   const void *lam;
-  void *M, *O, *V;
+  void *O, *V;
   void *gphi, *gK, *gD;      // segment gradients (arithmetic type)
   double *gU;
   void *lam_out;
   double *tphi, *tK, *tD;    // FP64 totals
+  const long long *cells;    // fluid edge cells, then volumetric catalyst cells
+  int n_edge, n_own;         // edge cells; all own-use cells
 };
-template <typename S> void launch_adj_local(const void *src, const DevGeom &g, const MatRaw *raw, const KArgs &a, int fickian, const AdjPtrs &b, long long seed_cell, cudaStream_t st);
-template <typename S> void launch_adj_gather(const DevGeom &g, const KArgs &a, const AdjPtrs &b, cudaStream_t st);
+template <typename S> void launch_adj_step(const void *src, const DevGeom &g, const KArgs &a, int fickian, const AdjPtrs &b, long long seed_cell, cudaStream_t st);
 template <typename S> void launch_adj_fold(const DevGeom &g, const KArgs &a, const AdjPtrs &b, cudaStream_t st);
 template <typename S> void launch_adj_seed_current(const void *src, const DevGeom &g, const KArgs &a, int fickian, double weight, const AdjPtrs &b, cudaStream_t st);
 
