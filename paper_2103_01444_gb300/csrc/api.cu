@@ -728,9 +728,22 @@ struct DevBuf {
 struct AdjWork {
   DevBuf lam[2], O, V, gphi, gK, gD, gU, tphi, tK, tD, cells;
   int n_edge = 0, n_own = 0;
+  cudaStream_t side = nullptr;                  // edge-cell branch of each step
+  cudaEvent_t fork = nullptr, join = nullptr;
+  ~AdjWork() {
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    if (side) cudaStreamDestroy(side);
+  }
   lbm_status alloc(lbm_domain *d) {
     const size_t r = fp64(d) ? 8 : 4, planes = 24 * (size_t)d->plane;
     lbm_status s;
+    if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(LBM_ECUDA, "stream or event creation for the adjoint failed");
+    }
     for (auto *b : {&lam[0], &lam[1], &O})
       if ((s = b->alloc(planes * r)) != LBM_OK) return s;
     // lambda^{n-1} of solid cells is zeroed by every step; the rest of both
@@ -800,7 +813,7 @@ void reverse_step(lbm_domain *d, AdjWork &w, int cur, const void *src, long long
   const AdjPtrs b = w.ptrs(cur);
   dispatch(d->desc.precision, [&](auto *tag) {
     using S = std::remove_pointer_t<decltype(tag)>;
-    launch_adj_step<S>(src, geom(d), a, fick, b, seed_cell, d->stream);
+    launch_adj_step<S>(src, geom(d), a, fick, b, seed_cell, d->stream, w.side, w.fork, w.join);
   });
 }
 

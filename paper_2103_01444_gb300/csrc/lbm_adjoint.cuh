@@ -536,41 +536,39 @@ k_adj_edge(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
 }
 
 // Own-use cells (edge cells, then catalyst cells of the volumetric mode),
-// one thread per entry of `cells`: lambda^{n-1}(y, q) = pushed value (if
+// one thread per (link q, entry of `cells`), q-major so that neighbouring
+// threads touch neighbouring cells: lambda^{n-1}(y, q) = pushed value (if
 // y + e_q is a fluid consumer) + O(y, q) + the outlet's uses of y.
 template <typename R>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(256)
 k_adj_fix(const uint8_t *__restrict__ mask, const uint16_t *__restrict__ mid,
           const MatCoef<R> *__restrict__ pal, KArgsT<R> a, AdjBufs<R> B,
           const long long *__restrict__ cells, int ncells) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= ncells) return;
-  const long long c = cells[t], P = a.plane;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 24LL * ncells) return;
+  const int q = (int)(t / ncells);
+  const long long c = cells[t - (long long)q * ncells], P = a.plane;
   const int y = (int)(c / a.nxp), x = (int)(c - (long long)y * a.nxp);
   const int EX9[9] = EX9_TAB, EY9[9] = EY9_TAB;
   const int EX5[5] = {0, 1, 0, -1, 0}, EY5[5] = {0, 0, 1, 0, -1};
   const bool outlet = !a.periodic && x == a.nx - 1;
-#pragma unroll
-  for (int q = 0; q < 24; ++q) {
-    const int ex = q < 9 ? EX9[q] : EX5[(q - 9) % 5];
-    const int ey = q < 9 ? EY9[q] : EY5[(q - 9) % 5];
-    int cx = x + ex;
-    const int cy = y + ey;
-    bool pushed = false;
-    if (cy >= 0 && cy < a.ny) {
-      if (a.periodic) cx = cx < 0 ? cx + a.nx : (cx >= a.nx ? cx - a.nx : cx);
-      if (cx >= 0 && cx < a.nx)
-        pushed = (mask[(long long)cy * a.nxp + cx] & REG_MASK) != REG_SOLID;
-    }
-    R l = pushed ? B.lam_out[q * P + c] : R(0);
-    l += B.O[q * P + c];
-    if (outlet && q < 9) {
-      if (y + 1 < a.ny) l += B.V[(0 * 10 + q) * a.ny + (y + 1)];
-      if (y - 1 >= 0) l += B.V[(1 * 10 + q) * a.ny + (y - 1)];
-    }
-    B.lam_out[q * P + c] = l;
+  const int ex = q < 9 ? EX9[q] : EX5[(q - 9) % 5];
+  const int ey = q < 9 ? EY9[q] : EY5[(q - 9) % 5];
+  int cx = x + ex;
+  const int cy = y + ey;
+  bool pushed = false;
+  if (cy >= 0 && cy < a.ny) {
+    if (a.periodic) cx = cx < 0 ? cx + a.nx : (cx >= a.nx ? cx - a.nx : cx);
+    if (cx >= 0 && cx < a.nx) pushed = (mask[(long long)cy * a.nxp + cx] & REG_MASK) != REG_SOLID;
   }
-  if (outlet) {
+  R l = pushed ? B.lam_out[q * P + c] : R(0);
+  l += B.O[q * P + c];
+  if (outlet && q < 9) {
+    if (y + 1 < a.ny) l += B.V[(0 * 10 + q) * a.ny + (y + 1)];
+    if (y - 1 >= 0) l += B.V[(1 * 10 + q) * a.ny + (y - 1)];
+  }
+  B.lam_out[q * P + c] = l;
+  if (outlet && q == 0) {
     R vsum_ip = 0;
     if (y + 1 < a.ny) vsum_ip += B.V[(0 * 10 + 9) * a.ny + (y + 1)];
     if (y - 1 >= 0) vsum_ip += B.V[(1 * 10 + 9) * a.ny + (y - 1)];

@@ -406,24 +406,35 @@ void launch_adj_fold(const DevGeom &g, const KArgs &a, const AdjPtrs &b, cudaStr
                                          a.plane);
 }
 
-// One reverse step: interior cells, then edge cells (both push into
-// lambda^{n-1}), then the own-use fix-up.
+// One reverse step.  The edge cells (a short list whose threads each run a
+// long boundary path) go first on the side stream, concurrently with the
+// interior cells on `st`; both push into lambda^{n-1}; the own-use fix-up
+// follows once both are done.  The fork and join are events, so the step
+// can be captured into a graph (two parallel branches).
 template <typename S>
 void launch_adj_step(const void *src, const DevGeom &g, const KArgs &a, int fickian,
-                     const AdjPtrs &b, long long seed_cell, cudaStream_t st) {
+                     const AdjPtrs &b, long long seed_cell, cudaStream_t st, cudaStream_t side,
+                     cudaEvent_t fork, cudaEvent_t join) {
   using R = typename Real<S>::type;
   const KArgsT<R> an = narrow_args<R>(a);
   const AdjBufs<R> B = adj_bufs<R>(b);
   const MatCoef<R> *pal = (const MatCoef<R> *)g.pal;
+  if (b.n_edge > 0) {
+    cudaEventRecord(fork, st);
+    cudaStreamWaitEvent(side, fork, 0);
+    k_adj_edge<S><<<(b.n_edge + 31) / 32, 32, 0, side>>>((const S *)src, g.mask, g.mid, pal, an,
+                                                         fickian, B, b.cells, b.n_edge,
+                                                         seed_cell);
+    cudaEventRecord(join, side);
+  }
   k_adj_interior<S><<<dim3((a.nx + 127) / 128, a.ny), 128, 0, st>>>((const S *)src, g.mask, g.mid,
                                                                     pal, an, fickian, B);
-  if (b.n_edge > 0)
-    k_adj_edge<S><<<(b.n_edge + 127) / 128, 128, 0, st>>>((const S *)src, g.mask, g.mid, pal, an,
-                                                          fickian, B, b.cells, b.n_edge,
-                                                          seed_cell);
-  if (b.n_own > 0)
-    k_adj_fix<R><<<(b.n_own + 127) / 128, 128, 0, st>>>(g.mask, g.mid, pal, an, B, b.cells,
-                                                        b.n_own);
+  if (b.n_edge > 0) cudaStreamWaitEvent(st, join, 0);
+  if (b.n_own > 0) {
+    const long long n = 24LL * b.n_own;
+    k_adj_fix<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g.mask, g.mid, pal, an, B, b.cells,
+                                                               b.n_own);
+  }
 }
 
 template <typename S>
@@ -525,7 +536,8 @@ void launch_set_state(void *pop, const DevGeom &g, const KArgs &a, const double 
                                                   unsigned *, int *, long long, cudaStream_t);  \
   template void batch_upload<S>(const BatchCase *, int, void *, void *, cudaStream_t);         \
   template void launch_adj_step<S>(const void *, const DevGeom &, const KArgs &, int,              \
-                                   const AdjPtrs &, long long, cudaStream_t);                      \
+                                   const AdjPtrs &, long long, cudaStream_t, cudaStream_t,         \
+                                   cudaEvent_t, cudaEvent_t);                                      \
   template void launch_adj_fold<S>(const DevGeom &, const KArgs &, const AdjPtrs &,              \
                                    cudaStream_t);                                               \
   template void launch_adj_seed_current<S>(const void *, const DevGeom &, const KArgs &, int,    \

@@ -68,7 +68,7 @@ struct AdjPtrs {
   const long long *cells;    // fluid edge cells, then volumetric catalyst cells
   int n_edge, n_own;         // edge cells; all own-use cells
 };
-template <typename S> void launch_adj_step(const void *src, const DevGeom &g, const KArgs &a, int fickian, const AdjPtrs &b, long long seed_cell, cudaStream_t st);
+template <typename S> void launch_adj_step(const void *src, const DevGeom &g, const KArgs &a, int fickian, const AdjPtrs &b, long long seed_cell, cudaStream_t st, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join);
 template <typename S> void launch_adj_fold(const DevGeom &g, const KArgs &a, const AdjPtrs &b, cudaStream_t st);
 template <typename S> void launch_adj_seed_current(const void *src, const DevGeom &g, const KArgs &a, int fickian, double weight, const AdjPtrs &b, cudaStream_t st);
 
