@@ -4,6 +4,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -726,7 +727,7 @@ struct DevBuf {
 
 // Reverse workspace of one domain.
 struct AdjWork {
-  DevBuf lam[2], O, V, gphi, gK, gD, gU, tphi, tK, tD, cells;
+  DevBuf lam[2], O[2], V[2], gphi, gK, gD, gU, tphi, tK, tD, cells, pushed;
   int n_edge = 0, n_own = 0;
   cudaStream_t side = nullptr;                  // edge-cell branch of each step
   cudaEvent_t fork = nullptr, join = nullptr;
@@ -744,12 +745,15 @@ struct AdjWork {
       cudaGetLastError();
       return fail(LBM_ECUDA, "stream or event creation for the adjoint failed");
     }
-    for (auto *b : {&lam[0], &lam[1], &O})
+    for (auto *b : {&lam[0], &lam[1], &O[0], &O[1]})
       if ((s = b->alloc(planes * r)) != LBM_OK) return s;
-    // lambda^{n-1} of solid cells is zeroed by every step; the rest of both
-    // buffers starts at zero so that no stale value is ever read
-    for (auto *b : {&lam[0], &lam[1]}) CK(cudaMemsetAsync(b->p, 0, planes * r, d->stream));
-    if ((s = V.alloc(20 * (size_t)d->ny * r)) != LBM_OK) return s;
+    for (auto *b : {&V[0], &V[1]})
+      if ((s = b->alloc(20 * (size_t)d->ny * r)) != LBM_OK) return s;
+    // everything starts at zero: lambda^{n-1} of solid cells is zeroed by
+    // every step, and the own-use parts of the first lambda are zero
+    for (auto *b : {&lam[0], &lam[1], &O[0], &O[1]})
+      CK(cudaMemsetAsync(b->p, 0, planes * r, d->stream));
+    for (auto *b : {&V[0], &V[1]}) CK(cudaMemsetAsync(b->p, 0, 20 * (size_t)d->ny * r, d->stream));
     for (auto *b : {&gphi, &gK, &gD})
       if ((s = b->alloc(r * d->plane)) != LBM_OK) return s;
     for (auto *b : {&tphi, &tK, &tD})
@@ -771,15 +775,45 @@ struct AdjWork {
           const bool vol = d->desc.reaction_mode == 1 && (b & REG_MASK) == REG_CATALYST;
           if (pass == 0 ? edge : (vol && !edge)) list.push_back(c);
         }
-      if (pass == 0) n_edge = (int)list.size();
+      if (pass == 0) {
+        // edge cells grouped by node type, so that the threads of a warp take
+        // the same boundary path (row-major order would mix inlet and outlet
+        // cells in one warp and serialise both paths)
+        std::stable_sort(list.begin(), list.end(),
+                         [&](long long p1, long long p2) { return m[p1] < m[p2]; });
+        n_edge = (int)list.size();
+      }
     }
     n_own = (int)list.size();
+    // per edge cell, the links q whose consumer y + e_q is a fluid cell
+    // (periodic seam included): only those are pushed by a consumer
+    std::vector<uint32_t> bits(n_edge);
+    for (int t = 0; t < n_edge; ++t) {
+      const int y = (int)(list[t] / d->nxp), x = (int)(list[t] - (long long)y * d->nxp);
+      uint32_t b = 0;
+      for (int q = 0; q < 24; ++q) {
+        const int l = q < 9 ? q : (q - 9) % 5;
+        const int ex[9] = EX9_TAB, ey[9] = EY9_TAB;
+        int cx = x + ex[l];
+        const int cy = y + ey[l];
+        if (cy < 0 || cy >= d->ny) continue;
+        if (d->desc.periodic_x) cx = cx < 0 ? cx + d->nx : (cx >= d->nx ? cx - d->nx : cx);
+        if (cx < 0 || cx >= d->nx) continue;
+        if ((m[(size_t)cy * d->nxp + cx] & REG_MASK) != REG_SOLID) b |= 1u << q;
+      }
+      bits[t] = b;
+    }
     if (n_own > 0) {
       if ((s = cells.alloc(sizeof(long long) * list.size())) != LBM_OK) return s;
       CK(cudaMemcpyAsync(cells.p, list.data(), sizeof(long long) * list.size(),
                          cudaMemcpyHostToDevice, d->stream));
-      CK(cudaStreamSynchronize(d->stream));
     }
+    if (n_edge > 0) {
+      if ((s = pushed.alloc(sizeof(uint32_t) * bits.size())) != LBM_OK) return s;
+      CK(cudaMemcpyAsync(pushed.p, bits.data(), sizeof(uint32_t) * bits.size(),
+                         cudaMemcpyHostToDevice, d->stream));
+    }
+    CK(cudaStreamSynchronize(d->stream));
     return LBM_OK;
   }
   lbm_status zero_grads(const lbm_domain *d) {
@@ -789,10 +823,20 @@ struct AdjWork {
     CK(cudaMemsetAsync(gU.p, 0, sizeof(double), d->stream));
     return LBM_OK;
   }
+  // A step reading lambda = lam[cur] (own-use parts in O[cur], V[cur])
+  // writes lam[cur ^ 1], O[cur ^ 1], V[cur ^ 1].
   AdjPtrs ptrs(int cur) {
-    return AdjPtrs{lam[cur].p, O.p, V.p, gphi.p, gK.p, gD.p, (double *)gU.p,
-                   lam[cur ^ 1].p, (double *)tphi.p, (double *)tK.p, (double *)tD.p,
-                   (const long long *)cells.p, n_edge, n_own};
+    return AdjPtrs{lam[cur].p, O[cur ^ 1].p, V[cur ^ 1].p, O[cur].p, V[cur].p,
+                   gphi.p, gK.p, gD.p, (double *)gU.p, lam[cur ^ 1].p,
+                   (double *)tphi.p, (double *)tK.p, (double *)tD.p,
+                   (const long long *)cells.p, (const uint32_t *)pushed.p, n_edge, n_own};
+  }
+  // Completion of lam[cur] in place (its own-use parts are O[cur], V[cur]).
+  AdjPtrs finish_ptrs(int cur) {
+    AdjPtrs b = ptrs(cur ^ 1);
+    b.lam = nullptr;
+    b.O_in = b.V_in = nullptr;
+    return b;   // lam_out = lam[cur], O = O[cur], V = V[cur]
   }
 };
 
@@ -807,13 +851,26 @@ void fold_grads(lbm_domain *d, AdjWork &w) {
 
 // One reverse step: lambda^n (w.lam[cur]) at state src = s^{n-1} ->
 // lambda^{n-1} (w.lam[cur ^ 1]), gradients accumulated.
-void reverse_step(lbm_domain *d, AdjWork &w, int cur, const void *src, long long seed_cell) {
+// lam_complete: lambda^n = w.lam[cur] holds every link in full (uploaded or
+// seeded) rather than the pushed part of a previous reverse step.
+void reverse_step(lbm_domain *d, AdjWork &w, int cur, const void *src, long long seed_cell,
+                  bool lam_complete = false) {
   const KArgs a = make_args(d);
   const int fick = d->prm.interface_mode == 1;
   const AdjPtrs b = w.ptrs(cur);
   dispatch(d->desc.precision, [&](auto *tag) {
     using S = std::remove_pointer_t<decltype(tag)>;
-    launch_adj_step<S>(src, geom(d), a, fick, b, seed_cell, d->stream, w.side, w.fork, w.join);
+    launch_adj_step<S>(src, geom(d), a, fick, b, seed_cell, lam_complete ? 1 : 0, d->stream,
+                       w.side, w.fork, w.join);
+  });
+}
+
+// Completes lambda = lam[cur] after the last reverse step.
+void finish_lambda(lbm_domain *d, AdjWork &w, int cur) {
+  const KArgs a = make_args(d);
+  dispatch(d->desc.precision, [&](auto *tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    launch_adj_finish<S>(geom(d), a, w.finish_ptrs(cur), d->stream);
   });
 }
 
@@ -874,7 +931,8 @@ lbm_status lbm_vjp(lbm_domain *d, const double *lam_next, double *lam_prev, doub
   if ((s = w.alloc(d)) != LBM_OK) return s;
   if ((s = w.zero_grads(d)) != LBM_OK) return s;
   if ((s = lam_upload(d, lam_next, w.lam[0].p)) != LBM_OK) return s;
-  reverse_step(d, w, 0, d->pop[d->cur], -1);
+  reverse_step(d, w, 0, d->pop[d->cur], -1, true);
+  finish_lambda(d, w, 1);
   CK(cudaGetLastError());
   if ((s = lam_download(d, w.lam[1].p, lam_prev)) != LBM_OK) return s;
   return copy_grads_out(d, w, dphi, dK, dD_O2, du_in);
@@ -946,9 +1004,10 @@ lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t se
   // reverse, last segment first
   int cur = 0;
   long long seed_cell = -1;
+  bool fresh = true;   // lam[cur] is the seed, held in full (see reverse_step)
   for (int64_t k = nck - 1; k >= 0; --k) {
     const int64_t first = k * seg, last = std::min<int64_t>(first + seg - 1, N - 1);
-    const bool full = last - first + 1 == seg && k != nck - 1;
+    bool full = last - first + 1 == seg && k != nck - 1;
     CK(cudaMemcpyAsync(SEG(0), CKP(k), sbytes, cudaMemcpyDeviceToDevice, d->stream));
     if (full) {
       auto body = [&] {
@@ -993,11 +1052,13 @@ lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t se
         seed_cell = xs;                          // row 0
         // lambda^{N-1}: the seed pulled through the reverse of the pull
         CK(cudaMemsetAsync(w.lam[0].p, 0, 24 * (size_t)d->plane * (fp64(d) ? 8 : 4), d->stream));
-        reverse_step(d, w, 0, sN1, seed_cell);   // lam[1] = lambda^{N-1}
+        reverse_step(d, w, 0, sN1, seed_cell, true);   // lam[1] = lambda^{N-1}
         cur = 1;
+        fresh = false;
       }
     }
     const int64_t ntop = (k == nck - 1) ? N - 1 : last + 1;
+    if (fresh) full = false;   // the captured segment expects a pushed lambda
     if (full) {
       const int c0 = cur;
       auto body = [&] {
@@ -1013,13 +1074,15 @@ lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t se
       cur ^= (int)(seg & 1);
     } else {
       for (int64_t n = ntop; n >= first + 1; --n) {
-        reverse_step(d, w, cur, SEG(n - 1 - first), -1);
+        reverse_step(d, w, cur, SEG(n - 1 - first), -1, fresh);
+        fresh = false;
         cur ^= 1;
       }
       fold_grads(d, w);
     }
     CK(cudaGetLastError());
   }
+  finish_lambda(d, w, cur);   // adds the last step's outlet term to gphi
   return copy_grads_out(d, w, dphi, dK, dD_O2, du_in);
 }
 

@@ -7,7 +7,8 @@
 // 8, 10) with the catalyst terms (Eq. 12-17).  Every plain link (y, q) of
 // s^{n-1} has exactly one consumer, the fluid cell y + e_q, so the transpose
 // of the pull is a push: the consumer writes the adjoint of what it pulled
-// straight into lambda^{n-1}(y, q).  Three kernels per step:
+// straight into lambda^{n-1}(y, q).  Two kernels per step, run
+// concurrently (they write disjoint links):
 //   k_adj_interior (one thread per cell; cells without edge bits): recomputes
 //     the forward update of x from s^{n-1}, back-propagates lambda^n(x)
 //     through C_x, pushes the 24 link adjoints to the source cells and
@@ -17,23 +18,62 @@
 //   k_adj_edge (one thread per listed edge cell): the same for cells with
 //     boundary links; the adjoint of values taken from the cell's own state
 //     goes to O(x, q), the outlet's uses of the cells above and below to V.
-//   k_adj_fix (one thread per listed own-use cell y): lambda^{n-1}(y, q) =
-//     (pushed value if y + e_q is a fluid consumer, else 0) + O(y, q) + the
-//     outlet terms.
+// At a cell that uses its own state, lambda^{n-1}(y, q) is therefore split:
+// the pushed value (only if y + e_q is a fluid consumer) + O(y, q) + the
+// outlet terms.  The next reverse step adds the parts when it reads lambda
+// (O and V are double-buffered for that); k_adj_fix adds them in place once,
+// after the last step, for a caller that reads lambda itself.
 // Storage is the domain's storage type S; arithmetic is R.
 #pragma once
 #include "lbm_core.cuh"
 
 namespace pemlbm {
 
+// The link tables of the core packed into single constants (2 bits per link for the
+// direction + 1, 4 bits for the opposite link), so that a link index known
+// only at run time costs a shift and a mask instead of a local-memory
+// table.  The D2Q5 links of Eq. 9 are the first five D2Q9 links.
+namespace dirbits {
+constexpr int ex[9] = EX9_TAB, ey[9] = EY9_TAB, op[9] = OP9_TAB;
+constexpr unsigned long long pack(const int (&t)[9], int bits, int bias) {
+  unsigned long long r = 0;
+  for (int i = 0; i < 9; ++i) r |= (unsigned long long)(t[i] + bias) << (bits * i);
+  return r;
+}
+constexpr unsigned kEX = (unsigned)pack(ex, 2, 1), kEY = (unsigned)pack(ey, 2, 1);
+constexpr unsigned long long kOP = pack(op, 4, 0);
+}  // namespace dirbits
+__host__ __device__ __forceinline__ constexpr int ex9(int i) {
+  return (int)((dirbits::kEX >> (2 * i)) & 3u) - 1;
+}
+__host__ __device__ __forceinline__ constexpr int ey9(int i) {
+  return (int)((dirbits::kEY >> (2 * i)) & 3u) - 1;
+}
+__host__ __device__ __forceinline__ constexpr int op9(int i) {
+  return (int)((dirbits::kOP >> (4 * i)) & 15ull);
+}
+// Direction of population plane q (0..8 flow, 9..23 three D2Q5 scalars).
+__host__ __device__ __forceinline__ constexpr int plane_link(int q) {
+  return q < 9 ? q : (q - 9) % 5;
+}
+static_assert(ex9(5) == 1 && ey9(5) == 1 && ex9(7) == -1 && ey9(8) == -1 && op9(5) == 7 &&
+                  op9(8) == 6 && op9(3) == 1,
+              "packed link tables");
+
+
 // Per-step adjoint workspace (device pointers).
 template <typename R> struct AdjBufs {
-  const R *lam;      // lambda^n, [24][plane] (deviation coordinates = full coordinates)
-  R *O;              // own-use adjoints [24][plane] (own-use cells only)
-  R *V;              // outlet column: [2][10][ny] (down: from y+1 to y, up: from y-1 to y)
+  const R *lam;      // lambda^n, [24][plane] (deviation coordinates = full coordinates);
+                     // at own-use cells only the pushed links are valid, the
+                     // rest of lambda^n is O_in / V_in
+  R *O;              // own-use adjoints of this step [24][plane] (own-use cells only)
+  R *V;              // outlet column of this step: [2][10][ny] (down: from y+1 to y, up: from y-1 to y)
+  const R *O_in;     // the same two left by the previous reverse step
+  const R *V_in;
   R *gphi, *gK, *gD;        // per-cell parameter gradients of the current segment [plane]
   double *gU;               // d objective / d u_in_avg
-  R *lam_out;        // lambda^{n-1} [24][plane]
+  R *lam_out;        // lambda^{n-1} [24][plane] (pushed links)
+  const uint32_t *pushed;   // per edge cell: bit q set if link q has a fluid consumer
 };
 
 // Adjoint of the D2Q5 collision of scalar s (collide_scalar).  Given the
@@ -242,29 +282,34 @@ template <typename R> __device__ __forceinline__ R dinlet_du(const KArgsT<R> &a,
   return (s <= R(0) || s >= R(1)) ? R(0) : R(6) * s * (R(1) - s);
 }
 
+// Accumulation into the per-cell sums of the edge kernel, where each lane
+// of a warp reverses one link of the same cell (shared memory).
+template <typename R> __device__ __forceinline__ void acc_shared(R *p, R v) { atomicAdd(p, v); }
+
 // Reverse of the pull of one flow link i at edge cell (x, y).  lam is the
 // adjoint of the pulled value; it is pushed to lambda^{n-1} of the source
 // (plain link, `out`), or goes to Oacc (own populations), the outlet's
-// virtual-cell adjoints or the inlet velocity.
+// virtual-cell adjoints or the inlet velocity.  Oacc, Vdn, Vup and lip_own
+// are shared by the lanes of the cell; lU is the lane's own.
 template <typename S, typename R>
 __device__ __forceinline__ void pull_flow_rev(const Pops<S> &src, const KArgsT<R> &a,
                                               const uint8_t *__restrict__ mask,
                                               const uint16_t *__restrict__ mid,
                                               const MatCoef<R> *__restrict__ pal, int i, int x,
                                               int y, uint8_t m, R lam, R *__restrict__ out,
-                                              R *Oacc, R *Vdn, R *Vup, R &lip_own, R &lU) {
-  const int EX[9] = EX9_TAB, EY[9] = EY9_TAB, OP[9] = OP9_TAB;
-  int sx = x - EX[i], sy = y - EY[i];
+                                              R *Oacc, R *Vdn, R *Vup, R *lip_own, R &lU) {
+  const int opi = op9(i);
+  int sx = x - ex9(i), sy = y - ey9(i);
   if (sy < 0 || sy >= a.ny) {
-    Oacc[OP[i]] += lam;
+    acc_shared(&Oacc[opi], lam);
     return;
   }
   if (sx < 0 || sx >= a.nx) {
     if (a.periodic) {
       sx = sx < 0 ? sx + a.nx : sx - a.nx;
     } else if (sx < 0) {
-      Oacc[OP[i]] += lam;
-      if (m & M_INLET) lU += lam * R(6) * w9<R>(i) * R(EX[i]) * dinlet_du<R>(a, R(y) - R(0.5) * R(EY[i]));
+      acc_shared(&Oacc[opi], lam);
+      if (m & M_INLET) lU += lam * R(6) * w9<R>(i) * R(ex9(i)) * dinlet_du<R>(a, R(y) - R(0.5) * R(ey9(i)));
       return;
     } else {
       const int vx = a.nx - 1;
@@ -278,17 +323,17 @@ __device__ __forceinline__ void pull_flow_rev(const Pops<S> &src, const KArgsT<R
       R lv[10];
 #pragma unroll
       for (int k = 0; k < 9; ++k)
-        lv[k] = ldP * ((k > 0 ? R(-0.6) : R(0)) + R(0.8) * ipv * (jx * R(EX[k]) + jy * R(EY[k])));
+        lv[k] = ldP * ((k > 0 ? R(-0.6) : R(0)) + R(0.8) * ipv * (jx * R(ex9(k)) + jy * R(ey9(k))));
       lv[i] += lam;
       lv[9] = ldP * R(0.4) * (jx * jx + jy * jy);   // adjoint of the virtual cell's 1/phi
       R *dst = sy == y ? nullptr : (sy < y ? Vdn : Vup);
       if (!dst) {
 #pragma unroll
-        for (int k = 0; k < 9; ++k) Oacc[k] += lv[k];
-        lip_own += lv[9];
+        for (int k = 0; k < 9; ++k) acc_shared(&Oacc[k], lv[k]);
+        acc_shared(lip_own, lv[9]);
       } else {
 #pragma unroll
-        for (int k = 0; k < 10; ++k) dst[k] += lv[k];
+        for (int k = 0; k < 10; ++k) acc_shared(&dst[k], lv[k]);
       }
       return;
     }
@@ -296,31 +341,31 @@ __device__ __forceinline__ void pull_flow_rev(const Pops<S> &src, const KArgsT<R
   // plain link (possibly across the periodic seam) unless the source is solid
   const long long sc = (long long)sy * a.nxp + sx;
   if ((m & M_NEAR_SOLID) && (mask[sc] & REG_MASK) == REG_SOLID) {
-    Oacc[OP[i]] += lam;
+    acc_shared(&Oacc[opi], lam);
     return;
   }
   out[(long long)i * a.plane + sc] = lam;
 }
 
-// Reverse of the pull of link i of scalar s at edge cell (x, y).
+// Reverse of the pull of link i of scalar s at edge cell (x, y); Oacc and
+// lw1 are shared by the lanes of the cell.
 template <typename R>
 __device__ __forceinline__ void pull_scalar_rev(const KArgsT<R> &a, const uint8_t *__restrict__ mask,
                                                 const MatCoef<R> &mc, int s, int i, int x, int y,
                                                 uint8_t m, R lam, R *__restrict__ out, R *Oacc,
-                                                R &lw1) {
-  const int EX[5] = {0, 1, 0, -1, 0}, EY[5] = {0, 0, 1, 0, -1}, OP[5] = {0, 3, 4, 1, 2};
-  const int q = 9 + 5 * s;
-  int sx = x - EX[i], sy = y - EY[i];
+                                                R *lw1) {
+  const int q = 9 + 5 * s, opi = op9(i);
+  int sx = x - ex9(i), sy = y - ey9(i);
   if (sy < 0) {
-    Oacc[q + OP[i]] += lam;
+    acc_shared(&Oacc[q + opi], lam);
     return;
   }
   if (sy >= a.ny) {
     if (a.top_dirichlet) {
-      Oacc[q + OP[i]] -= lam;
-      lw1 += R(2) * R(a.Ctop[s]) * lam;
+      acc_shared(&Oacc[q + opi], -lam);
+      acc_shared(lw1, R(2) * R(a.Ctop[s]) * lam);
     } else {
-      Oacc[q + OP[i]] += lam;
+      acc_shared(&Oacc[q + opi], lam);
     }
     return;
   }
@@ -329,73 +374,67 @@ __device__ __forceinline__ void pull_scalar_rev(const KArgsT<R> &a, const uint8_
       sx = sx < 0 ? sx + a.nx : sx - a.nx;
     } else if (sx < 0) {
       if (m & M_INLET) {
-        Oacc[q + OP[i]] -= lam;
-        lw1 += R(2) * R(a.Cin[s]) * lam;
+        acc_shared(&Oacc[q + opi], -lam);
+        acc_shared(lw1, R(2) * R(a.Cin[s]) * lam);
       } else {
-        Oacc[q + OP[i]] += lam;
+        acc_shared(&Oacc[q + opi], lam);
       }
       return;
     } else {
-      Oacc[q + i] += lam;   // fully developed: the cell's own population of link i
+      acc_shared(&Oacc[q + i], lam);   // fully developed: the cell's own population of link i
       return;
     }
   }
   const long long sc = (long long)sy * a.nxp + sx;
   if ((m & M_NEAR_SOLID) && (mask[sc] & REG_MASK) == REG_SOLID) {
-    Oacc[q + OP[i]] += lam;
+    acc_shared(&Oacc[q + opi], lam);
     return;
   }
   out[(long long)(q + i) * a.plane + sc] = lam;
 }
 
-// Reverse of one fluid cell's update (see the file comment).  EDGE selects
-// the edge-cell form: boundary pulls, the surface reaction, own-use and
-// outlet adjoints, the inlet velocity and the seed of the "CL temperature"
-// objective (seed_cell >= 0: the adjoint of the pulled temperature
-// populations of that cell is 1 on top of a zero lambda^n).
-template <typename S, bool EDGE>
-__device__ __forceinline__ void adj_cell(const S *__restrict__ src_p,
-                                         const uint8_t *__restrict__ mask,
-                                         const uint16_t *__restrict__ mid,
-                                         const MatCoef<typename Real<S>::type> *__restrict__ pal,
-                                         const KArgsT<typename Real<S>::type> &a, int fickian,
-                                         const AdjBufs<typename Real<S>::type> &B, int x, int y,
-                                         long long c, uint8_t m, long long seed_cell,
-                                         typename Real<S>::type &lU) {
+// Reverse of the update of one fluid interior cell (no edge bits; see the
+// file comment).  Catalyst cells of the volumetric mode also read their
+// own state (the sink) and leave that adjoint in O.
+template <typename S>
+__device__ __forceinline__ void adj_interior_cell(
+    const S *__restrict__ src_p, const uint16_t *__restrict__ mid,
+    const MatCoef<typename Real<S>::type> *__restrict__ pal,
+    const KArgsT<typename Real<S>::type> &a, int fickian,
+    const AdjBufs<typename Real<S>::type> &B, int x, int y, long long c, uint8_t m) {
   using R = typename Real<S>::type;
   const long long P = a.plane, W = a.nxp;
   const Pops<S> src{src_p, a.plane, a.nxp};
   const MatCoef<R> mc = pal[mid[c]];
+  // this cell's segment gradients, read before any store of the thread so
+  // that their latency overlaps the population loads (no other thread of
+  // the launch touches them)
+  R gacc[3] = {B.gphi[c], B.gK[c], B.gD[c]};
   Cell<R> cell;
-  if constexpr (EDGE) pull_cell<S, R>(src, a, mask, mid, pal, mc, x, y, m, cell);
-  else load_interior<S, R>(src, a, x, y, cell);
-  // forward reaction terms (kept for the reverse)
-  const bool surf = EDGE && a.mode == 0 && (m & M_YLO);
+  load_interior<S, R>(src, a, x, y, cell);
   const bool vol = a.mode == 1 && (m & REG_MASK) == REG_CATALYST;
-  R theta = 0, k = 0, kappa = 0, gd = 0, Cv = 0;
-  if (surf || vol) theta = own_sum<S, R>(src, 0, x, y) + a.theta0;
-  if (surf) {
-    k = rate<R>(a, R(a.kA_surf), theta);
-    kappa = k / (R(2) * mc.w1[1]);
-    gd = cell.g[1][2] + R(a.wr1[1]) * R(a.Cref[1]);
-    const R Jv = gd * (R(2) * kappa) / (R(1) + kappa);
-    cell.g[1][2] -= Jv;
-    cell.g[0][2] += R(a.hpo) * mc.inv_sigma * Jv;
-    cell.g[2][2] += R(2) * Jv;
-  }
-  R S_vol = 0;
+  // lambda^n of link q: every link of an interior cell is pushed; a
+  // catalyst cell adds the own-use adjoint the previous step left in O_in
+  auto lam_at = [&](int q) -> R {
+    R v = ld_r(B.lam + q * P + c);
+    if (vol && q >= 9 && q < 19) v += ld_r(B.O_in + q * P + c);
+    return v;
+  };
+  // forward reaction terms (kept for the reverse)
+  R theta = 0, k = 0, Cv = 0, S_vol = 0;
   if (vol) {
+    theta = own_sum<S, R>(src, 0, x, y) + a.theta0;
     Cv = own_sum<S, R>(src, 1, x, y) + R(a.Cref[1]);
     k = rate<R>(a, R(a.kA_vol), theta);
     S_vol = -k * Cv / (R(1) + k);
   }
-  // ---- reverse of the collisions
-  R lcf[9], lcg[3][5];
+  // ---- reverse of the collisions; every link is plain, so each link's
+  // adjoint is pushed to its source as soon as it is known
+  R lcf[9], lcg[5];
 #pragma unroll
   for (int i = 0; i < 9; ++i) lcf[i] = R(0);
   R lphi = 0, ldarcy = 0, lforch = 0, ll0 = 0, ll1 = 0, lip = 0;
   R lb[3] = {0, 0, 0}, lw1[3] = {0, 0, 0}, lq1[3] = {0, 0, 0}, lsrc[3] = {0, 0, 0};
-  R lth_own = 0, lC_own = 0;   // own-use adjoints of the reaction (theta, C_O2)
   {
     const Macro<R> u = macros<R>(a, mc, cell);
     const R srcv[3] = {-S_vol * R(a.hpo) * mc.inv_sigma, S_vol, R(-2) * S_vol};
@@ -405,92 +444,43 @@ __device__ __forceinline__ void adj_cell(const S *__restrict__ src_p,
       R lo[5];
 #pragma unroll
       for (int i = 0; i < 5; ++i) {
-        lo[i] = B.lam[(9 + 5 * s + i) * P + c];
-        lcg[s][i] = R(0);
+        lo[i] = lam_at(9 + 5 * s + i);
+        lcg[i] = R(0);
       }
-      collide_scalar_rev<R>(a, mc, s, u.ux, u.uy, u.C[s], cell.g[s], srcv[s], lo, lcg[s], lux,
-                            luy, lsrc[s], lb[s], lw1[s], lq1[s]);
-      if constexpr (!EDGE) {
-        // interior: every link is plain; push as soon as the scalar is done
-        const int EX5[5] = {0, 1, 0, -1, 0}, EY5[5] = {0, 0, 1, 0, -1};
+      collide_scalar_rev<R>(a, mc, s, u.ux, u.uy, u.C[s], cell.g[s], srcv[s], lo, lcg, lux, luy,
+                            lsrc[s], lb[s], lw1[s], lq1[s]);
 #pragma unroll
-        for (int i = 0; i < 5; ++i)
-          B.lam_out[(9 + 5 * s + i) * P + c - EY5[i] * W - EX5[i]] = lcg[s][i];
-      }
+      for (int i = 0; i < 5; ++i)
+        B.lam_out[(9 + 5 * s + i) * P + c - ey9(i) * W - ex9(i)] = lcg[i];
     }
     R lo[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) lo[i] = B.lam[i * P + c];
+    for (int i = 0; i < 9; ++i) lo[i] = lam_at(i);
     flow_rev<R>(a, mc, cell.f, lo, lux, luy, lcf, lphi, ldarcy, lforch, ll0, ll1, lip);
   }
-  // volumetric sources: (-S h / sigma, S, -2 S)
+#pragma unroll
+  for (int i = 0; i < 9; ++i) B.lam_out[i * P + c - ey9(i) * W - ex9(i)] = lcf[i];
+  // volumetric sources (-S h / sigma, S, -2 S): own-use adjoints of theta, C_O2
   if (vol) {
     const R lS = -R(a.hpo) * mc.inv_sigma * lsrc[0] + lsrc[1] - R(2) * lsrc[2];
-    lC_own = lS * (-k / (R(1) + k));
-    const R lk = lS * (-Cv / ((R(1) + k) * (R(1) + k)));
-    lth_own = lk * drate_dtheta<R>(a, k, theta);
-  }
-  if constexpr (!EDGE) {
-    const int EX[9] = EX9_TAB, EY[9] = EY9_TAB;
+    const R lC_own = lS * (-k / (R(1) + k));
+    const R lth_own = lS * (-Cv / ((R(1) + k) * (R(1) + k))) * drate_dtheta<R>(a, k, theta);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) B.lam_out[i * P + c - EY[i] * W - EX[i]] = lcf[i];
-    if (vol) {
-#pragma unroll
-      for (int q = 0; q < 24; ++q)
-        B.O[q * P + c] = q >= 9 && q < 14 ? lth_own : (q >= 14 && q < 19 ? lC_own : R(0));
-    }
-  } else {
-    R Oacc[24];
-#pragma unroll
-    for (int q = 0; q < 24; ++q) Oacc[q] = q >= 9 && q < 14 ? lth_own : (q >= 14 && q < 19 ? lC_own : R(0));
-    R Vdn[10], Vup[10];
-#pragma unroll
-    for (int kk = 0; kk < 10; ++kk) Vdn[kk] = Vup[kk] = R(0);
-    if (c == seed_cell) {
-#pragma unroll
-      for (int i = 0; i < 5; ++i) lcg[0][i] += R(1);
-    }
-    // ---- reverse of the surface reaction (post -> pre link values)
-    if (surf) {
-      const R lJ = -lcg[1][2] + R(a.hpo) * mc.inv_sigma * lcg[0][2] + R(2) * lcg[2][2];
-      const R lgd = lJ * R(2) * kappa / (R(1) + kappa);
-      const R lkap = lJ * R(2) * gd / ((R(1) + kappa) * (R(1) + kappa));
-      const R lk = lkap / (R(2) * mc.w1[1]);
-      lw1[1] += -lkap * k / (R(2) * mc.w1[1] * mc.w1[1]);
-      const R lth = lk * drate_dtheta<R>(a, k, theta);
-#pragma unroll
-      for (int q = 0; q < 5; ++q) Oacc[9 + q] += lth;
-      lcg[1][2] += lgd;
-    }
-    // ---- reverse of the pull
-#pragma unroll
-    for (int i = 0; i < 9; ++i)
-      pull_flow_rev<S, R>(src, a, mask, mid, pal, i, x, y, m, lcf[i], B.lam_out, Oacc, Vdn, Vup,
-                          lip, lU);
-#pragma unroll
-    for (int s = 0; s < 3; ++s)
-#pragma unroll
-      for (int i = 0; i < 5; ++i)
-        pull_scalar_rev<R>(a, mask, mc, s, i, x, y, m, lcg[s][i], B.lam_out, Oacc, lw1[s]);
-#pragma unroll
-    for (int q = 0; q < 24; ++q) B.O[q * P + c] = Oacc[q];
-    if (!a.periodic && x == a.nx - 1) {
-#pragma unroll
-      for (int kk = 0; kk < 10; ++kk) {
-        B.V[(0 * 10 + kk) * a.ny + y] = Vdn[kk];
-        B.V[(1 * 10 + kk) * a.ny + y] = Vup[kk];
-      }
-    }
+    for (int q = 0; q < 24; ++q)
+      B.O[q * P + c] = q >= 9 && q < 14 ? lth_own : (q >= 14 && q < 19 ? lC_own : R(0));
   }
   // ---- parameters of this cell
   param_rev<R>(a, mc, fickian, lphi, ldarcy, lforch, ll0, ll1, lip, lb[1], lw1[1], lq1[1],
-               B.gphi + c, B.gK + c, B.gD + c);
+               &gacc[0], &gacc[1], &gacc[2]);
+  B.gphi[c] = gacc[0];
+  B.gK[c] = gacc[1];
+  B.gD[c] = gacc[2];
 }
 
 // Cells without edge bits, one thread per cell (grid over the lattice);
 // solid cells zero their own lambda^{n-1} (nothing is ever pushed there).
 template <typename S>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 8)
 k_adj_interior(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
                const uint16_t *__restrict__ mid,
                const MatCoef<typename Real<S>::type> *__restrict__ pal,
@@ -507,38 +497,207 @@ k_adj_interior(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
     return;
   }
   if (m & M_EDGE) return;
-  R lU = 0;
-  adj_cell<S, false>(src_p, mask, mid, pal, a, fickian, B, x, y, c, m, -1, lU);
+  adj_interior_cell<S>(src_p, mid, pal, a, fickian, B, x, y, c, m);
 }
 
-// Fluid cells with edge bits, one thread per entry of `cells` (linear cell
-// indices y * nxp + x).
+// Fluid cells with edge bits, one warp per entry of `cells` (linear cell
+// indices y * nxp + x), four cells per block.  An edge cell's boundary
+// pulls and their reverses are independent per link, so lane q < 24 takes
+// link q (in parallel instead of one long serial chain per cell); lane 0
+// runs the cell's collision reverse in between.  lam_complete: lambda^n
+// holds every link in full (the seed, or the caller's), O_in and V_in are
+// zero.  seed_cell >= 0: the "CL temperature" seed on a zero lambda^n.
+constexpr int kEdgeWarps = 4;
 template <typename S>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(32 * kEdgeWarps)
 k_adj_edge(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
            const uint16_t *__restrict__ mid,
            const MatCoef<typename Real<S>::type> *__restrict__ pal,
            KArgsT<typename Real<S>::type> a, int fickian, AdjBufs<typename Real<S>::type> B,
-           const long long *__restrict__ cells, int ncells, long long seed_cell) {
+           const long long *__restrict__ cells, int ncells, long long seed_cell,
+           int lam_complete) {
   using R = typename Real<S>::type;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  R lU = 0;
-  if (t < ncells) {
-    const long long c = cells[t];
-    const int y = (int)(c / a.nxp), x = (int)(c - (long long)y * a.nxp);
-    adj_cell<S, true>(src_p, mask, mid, pal, a, fickian, B, x, y, c, mask[c], seed_cell, lU);
+  struct Shared {
+    R pulled[24];   // post-stream values of the cell
+    R lin[24];      // lambda^n of the cell
+    R lpull[24];    // adjoints of the pulled values
+    R O[24];        // own-use adjoints
+    R V[20];        // outlet: 10 down (to y - 1's use), 10 up
+    R lip, lw1[3];
+  };
+  __shared__ Shared sh_all[kEdgeWarps];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * kEdgeWarps + w;
+  if (t >= ncells) return;   // whole warps leave
+  Shared &sh = sh_all[w];
+  const long long c = cells[t], P = a.plane, W = a.nxp;
+  const int y = (int)(c / a.nxp), x = (int)(c - (long long)y * a.nxp);
+  const uint8_t m = mask[c];
+  const Pops<S> src{src_p, a.plane, a.nxp};
+  const MatCoef<R> mc = pal[mid[c]];
+  const bool outlet = !a.periodic && x == a.nx - 1;
+  // ---- phase 1 (lane q): pull link q, read lambda^n of link q
+  if (lane < 24) {
+    const int q = lane, l = plane_link(q);
+    R v = R(ldp<false>(src_p + q * P + c - ey9(l) * W - ex9(l)));   // interior pull
+    if (l != 0) {
+      if (q < 9) v = pull_flow_edge<S, R>(src, a, mask, mid, pal, q, x, y, m, v);
+      else v = pull_scalar_edge<S, R>(src, a, mask, mc, (q - 9) / 5, l, x, y, m, v);
+    }
+    sh.pulled[q] = v;
+    const uint32_t pbits = lam_complete ? 0xffffffffu : B.pushed[t];
+    R lv = ((pbits >> q) & 1u) ? ld_r(B.lam + q * P + c) : R(0);
+    lv += ld_r(B.O_in + q * P + c);
+    if (outlet && q < 9) {
+      if (y + 1 < a.ny) lv += ld_r(B.V_in + (0 * 10 + q) * a.ny + (y + 1));
+      if (y - 1 >= 0) lv += ld_r(B.V_in + (1 * 10 + q) * a.ny + (y - 1));
+    }
+    sh.lin[q] = lv;
+    sh.O[q] = R(0);
   }
-  // inlet velocity: warp sum, one FP64 atomic per warp that has inlet cells
-  R s = lU;
+  if (lane < 20) sh.V[lane] = R(0);
+  if (lane == 0) sh.lip = sh.lw1[0] = sh.lw1[1] = sh.lw1[2] = R(0);
+  __syncwarp();
+  // ---- phase 2 (lane 0): reaction and collision reverse of the cell
+  R lphi = 0, ldarcy = 0, lforch = 0, ll0 = 0, ll1 = 0, lip = 0;
+  R lb1 = 0, lq1_1 = 0, lw1[3] = {0, 0, 0};
+  R gacc[3] = {0, 0, 0};
+  if (lane == 0) {
+    gacc[0] = B.gphi[c];
+    gacc[1] = B.gK[c];
+    gacc[2] = B.gD[c];
+    Cell<R> cell;
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-  if ((threadIdx.x & 31) == 0 && s != R(0)) atomicAdd(B.gU, (double)s);
+    for (int i = 0; i < 9; ++i) cell.f[i] = sh.pulled[i];
+#pragma unroll
+    for (int s = 0; s < 3; ++s)
+#pragma unroll
+      for (int i = 0; i < 5; ++i) cell.g[s][i] = sh.pulled[9 + 5 * s + i];
+    const bool surf = a.mode == 0 && (m & M_YLO);
+    const bool vol = a.mode == 1 && (m & REG_MASK) == REG_CATALYST;
+    R theta = 0, k = 0, kappa = 0, gd = 0, Cv = 0, S_vol = 0;
+    if (surf || vol) theta = own_sum<S, R>(src, 0, x, y) + a.theta0;
+    if (surf) {
+      k = rate<R>(a, R(a.kA_surf), theta);
+      kappa = k / (R(2) * mc.w1[1]);
+      gd = cell.g[1][2] + R(a.wr1[1]) * R(a.Cref[1]);
+      const R Jv = gd * (R(2) * kappa) / (R(1) + kappa);
+      cell.g[1][2] -= Jv;
+      cell.g[0][2] += R(a.hpo) * mc.inv_sigma * Jv;
+      cell.g[2][2] += R(2) * Jv;
+    }
+    if (vol) {
+      Cv = own_sum<S, R>(src, 1, x, y) + R(a.Cref[1]);
+      k = rate<R>(a, R(a.kA_vol), theta);
+      S_vol = -k * Cv / (R(1) + k);
+    }
+    R lcf[9], lcg[3][5];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) lcf[i] = R(0);
+    R lb[3] = {0, 0, 0}, lq1[3] = {0, 0, 0}, lsrc[3] = {0, 0, 0};
+    {
+      const Macro<R> u = macros<R>(a, mc, cell);
+      const R srcv[3] = {-S_vol * R(a.hpo) * mc.inv_sigma, S_vol, R(-2) * S_vol};
+      R lux = 0, luy = 0;
+#pragma unroll
+      for (int s = 0; s < 3; ++s) {
+        R lo[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+          lo[i] = sh.lin[9 + 5 * s + i];
+          lcg[s][i] = R(0);
+        }
+        collide_scalar_rev<R>(a, mc, s, u.ux, u.uy, u.C[s], cell.g[s], srcv[s], lo, lcg[s], lux,
+                              luy, lsrc[s], lb[s], lw1[s], lq1[s]);
+      }
+      R lo[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) lo[i] = sh.lin[i];
+      flow_rev<R>(a, mc, cell.f, lo, lux, luy, lcf, lphi, ldarcy, lforch, ll0, ll1, lip);
+    }
+    if (vol) {   // volumetric sources (-S h / sigma, S, -2 S)
+      const R lS = -R(a.hpo) * mc.inv_sigma * lsrc[0] + lsrc[1] - R(2) * lsrc[2];
+      const R lC_own = lS * (-k / (R(1) + k));
+      const R lth_own = lS * (-Cv / ((R(1) + k) * (R(1) + k))) * drate_dtheta<R>(a, k, theta);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        sh.O[9 + q] += lth_own;
+        sh.O[14 + q] += lC_own;
+      }
+    }
+    if (c == seed_cell) {
+#pragma unroll
+      for (int i = 0; i < 5; ++i) lcg[0][i] += R(1);
+    }
+    if (surf) {   // reverse of the surface reaction (post -> pre link values)
+      const R lJ = -lcg[1][2] + R(a.hpo) * mc.inv_sigma * lcg[0][2] + R(2) * lcg[2][2];
+      const R lgd = lJ * R(2) * kappa / (R(1) + kappa);
+      const R lkap = lJ * R(2) * gd / ((R(1) + kappa) * (R(1) + kappa));
+      const R lk = lkap / (R(2) * mc.w1[1]);
+      lw1[1] += -lkap * k / (R(2) * mc.w1[1] * mc.w1[1]);
+      const R lth = lk * drate_dtheta<R>(a, k, theta);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) sh.O[9 + q] += lth;
+      lcg[1][2] += lgd;
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) sh.lpull[i] = lcf[i];
+#pragma unroll
+    for (int s = 0; s < 3; ++s)
+#pragma unroll
+      for (int i = 0; i < 5; ++i) sh.lpull[9 + 5 * s + i] = lcg[s][i];
+    lb1 = lb[1];
+    lq1_1 = lq1[1];
+  }
+  __syncwarp();
+  // ---- phase 3 (lane q): reverse of the pull of link q
+  R lU = 0;
+  if (lane < 24) {
+    const int q = lane;
+    if (q < 9) {
+      pull_flow_rev<S, R>(src, a, mask, mid, pal, q, x, y, m, sh.lpull[q], B.lam_out, sh.O,
+                          sh.V, sh.V + 10, &sh.lip, lU);
+    } else {
+      const int s = (q - 9) / 5;
+      pull_scalar_rev<R>(a, mask, mc, s, q - 9 - 5 * s, x, y, m, sh.lpull[q], B.lam_out, sh.O,
+                         &sh.lw1[s]);
+    }
+  }
+  __syncwarp();
+  // ---- phase 4: own-use and outlet adjoints out; parameters (lane 0)
+  if (lane < 24) B.O[lane * P + c] = sh.O[lane];
+  if (outlet && lane < 10) {
+    B.V[(0 * 10 + lane) * a.ny + y] = sh.V[lane];
+    B.V[(1 * 10 + lane) * a.ny + y] = sh.V[10 + lane];
+  }
+  if (lane == 0) {
+    lip += sh.lip;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) lw1[s] += sh.lw1[s];
+    if (outlet) {   // the outlet's use of this cell's 1/phi in the previous step
+      R vsum_ip = 0;
+      if (y + 1 < a.ny) vsum_ip += ld_r(B.V_in + (0 * 10 + 9) * a.ny + (y + 1));
+      if (y - 1 >= 0) vsum_ip += ld_r(B.V_in + (1 * 10 + 9) * a.ny + (y - 1));
+      gacc[0] += -vsum_ip * mc.inv_phi * mc.inv_phi;
+    }
+    param_rev<R>(a, mc, fickian, lphi, ldarcy, lforch, ll0, ll1, lip, lb1, lw1[1], lq1_1,
+                 &gacc[0], &gacc[1], &gacc[2]);
+    B.gphi[c] = gacc[0];
+    B.gK[c] = gacc[1];
+    B.gD[c] = gacc[2];
+  }
+  // inlet velocity: warp sum, one FP64 atomic per warp that has inlet links
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) lU += __shfl_down_sync(0xffffffffu, lU, off);
+  if (lane == 0 && lU != R(0)) atomicAdd(B.gU, (double)lU);
 }
 
-// Own-use cells (edge cells, then catalyst cells of the volumetric mode),
-// one thread per (link q, entry of `cells`), q-major so that neighbouring
-// threads touch neighbouring cells: lambda^{n-1}(y, q) = pushed value (if
-// y + e_q is a fluid consumer) + O(y, q) + the outlet's uses of y.
+// Completes lambda in place after the last reverse step, at the own-use
+// cells (edge cells, then catalyst cells of the volumetric mode), one thread
+// per (link q, entry of `cells`), q-major so that neighbouring threads touch
+// neighbouring cells: lambda(y, q) = pushed value (if y + e_q is a fluid
+// consumer) + O(y, q) + the outlet's uses of y (B.lam_out, B.O, B.V: the
+// buffers of that step); the outlet's 1/phi term goes to gphi.
 template <typename R>
 __global__ void __launch_bounds__(256)
 k_adj_fix(const uint8_t *__restrict__ mask, const uint16_t *__restrict__ mid,
@@ -549,11 +708,8 @@ k_adj_fix(const uint8_t *__restrict__ mask, const uint16_t *__restrict__ mid,
   const int q = (int)(t / ncells);
   const long long c = cells[t - (long long)q * ncells], P = a.plane;
   const int y = (int)(c / a.nxp), x = (int)(c - (long long)y * a.nxp);
-  const int EX9[9] = EX9_TAB, EY9[9] = EY9_TAB;
-  const int EX5[5] = {0, 1, 0, -1, 0}, EY5[5] = {0, 0, 1, 0, -1};
   const bool outlet = !a.periodic && x == a.nx - 1;
-  const int ex = q < 9 ? EX9[q] : EX5[(q - 9) % 5];
-  const int ey = q < 9 ? EY9[q] : EY5[(q - 9) % 5];
+  const int ex = ex9(plane_link(q)), ey = ey9(plane_link(q));
   int cx = x + ex;
   const int cy = y + ey;
   bool pushed = false;

@@ -394,8 +394,8 @@ cudaError_t launch_batch_persistent(const BatchCase *cases, const int *tile_star
 }
 
 template <typename R> AdjBufs<R> adj_bufs(const AdjPtrs &b) {
-  return AdjBufs<R>{(const R *)b.lam, (R *)b.O, (R *)b.V, (R *)b.gphi, (R *)b.gK,
-                    (R *)b.gD, b.gU, (R *)b.lam_out};
+  return AdjBufs<R>{(const R *)b.lam, (R *)b.O, (R *)b.V, (const R *)b.O_in, (const R *)b.V_in,
+                    (R *)b.gphi, (R *)b.gK, (R *)b.gD, b.gU, (R *)b.lam_out, b.pushed};
 }
 
 template <typename S>
@@ -408,13 +408,13 @@ void launch_adj_fold(const DevGeom &g, const KArgs &a, const AdjPtrs &b, cudaStr
 
 // One reverse step.  The edge cells (a short list whose threads each run a
 // long boundary path) go first on the side stream, concurrently with the
-// interior cells on `st`; both push into lambda^{n-1}; the own-use fix-up
-// follows once both are done.  The fork and join are events, so the step
-// can be captured into a graph (two parallel branches).
+// interior cells on `st`; both push into lambda^{n-1}.  The fork and join
+// are events, so the step can be captured into a graph (two parallel
+// branches).
 template <typename S>
 void launch_adj_step(const void *src, const DevGeom &g, const KArgs &a, int fickian,
-                     const AdjPtrs &b, long long seed_cell, cudaStream_t st, cudaStream_t side,
-                     cudaEvent_t fork, cudaEvent_t join) {
+                     const AdjPtrs &b, long long seed_cell, int lam_complete, cudaStream_t st,
+                     cudaStream_t side, cudaEvent_t fork, cudaEvent_t join) {
   using R = typename Real<S>::type;
   const KArgsT<R> an = narrow_args<R>(a);
   const AdjBufs<R> B = adj_bufs<R>(b);
@@ -422,19 +422,26 @@ void launch_adj_step(const void *src, const DevGeom &g, const KArgs &a, int fick
   if (b.n_edge > 0) {
     cudaEventRecord(fork, st);
     cudaStreamWaitEvent(side, fork, 0);
-    k_adj_edge<S><<<(b.n_edge + 31) / 32, 32, 0, side>>>((const S *)src, g.mask, g.mid, pal, an,
-                                                         fickian, B, b.cells, b.n_edge,
-                                                         seed_cell);
+    k_adj_edge<S><<<(b.n_edge + kEdgeWarps - 1) / kEdgeWarps, 32 * kEdgeWarps, 0, side>>>(
+        (const S *)src, g.mask, g.mid, pal, an, fickian, B, b.cells, b.n_edge, seed_cell,
+        lam_complete);
     cudaEventRecord(join, side);
   }
   k_adj_interior<S><<<dim3((a.nx + 127) / 128, a.ny), 128, 0, st>>>((const S *)src, g.mask, g.mid,
                                                                     pal, an, fickian, B);
   if (b.n_edge > 0) cudaStreamWaitEvent(st, join, 0);
-  if (b.n_own > 0) {
-    const long long n = 24LL * b.n_own;
-    k_adj_fix<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g.mask, g.mid, pal, an, B, b.cells,
-                                                               b.n_own);
-  }
+}
+
+// Completes lambda in place at the own-use cells after the last step
+// (b.lam_out, b.O and b.V are that step's buffers).
+template <typename S>
+void launch_adj_finish(const DevGeom &g, const KArgs &a, const AdjPtrs &b, cudaStream_t st) {
+  using R = typename Real<S>::type;
+  if (b.n_own <= 0) return;
+  const long long n = 24LL * b.n_own;
+  k_adj_fix<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+      g.mask, g.mid, (const MatCoef<R> *)g.pal, narrow_args<R>(a), adj_bufs<R>(b), b.cells,
+      b.n_own);
 }
 
 template <typename S>
@@ -536,8 +543,10 @@ void launch_set_state(void *pop, const DevGeom &g, const KArgs &a, const double 
                                                   unsigned *, int *, long long, cudaStream_t);  \
   template void batch_upload<S>(const BatchCase *, int, void *, void *, cudaStream_t);         \
   template void launch_adj_step<S>(const void *, const DevGeom &, const KArgs &, int,              \
-                                   const AdjPtrs &, long long, cudaStream_t, cudaStream_t,         \
+                                   const AdjPtrs &, long long, int, cudaStream_t, cudaStream_t,    \
                                    cudaEvent_t, cudaEvent_t);                                      \
+  template void launch_adj_finish<S>(const DevGeom &, const KArgs &, const AdjPtrs &,            \
+                                     cudaStream_t);                                              \
   template void launch_adj_fold<S>(const DevGeom &, const KArgs &, const AdjPtrs &,              \
                                    cudaStream_t);                                               \
   template void launch_adj_seed_current<S>(const void *, const DevGeom &, const KArgs &, int,    \

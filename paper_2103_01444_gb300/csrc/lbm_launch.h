@@ -60,15 +60,18 @@ template <typename S> cudaError_t launch_batch_persistent(const BatchCase *cases
 // Buffers of one reverse step (types follow the domain's arithmetic).
 struct AdjPtrs {
   const void *lam;
-  void *O, *V;
+  void *O, *V;               // own-use / outlet adjoints written by this step
+  const void *O_in, *V_in;   // those of the previous step
   void *gphi, *gK, *gD;      // segment gradients (arithmetic type)
   double *gU;
   void *lam_out;
   double *tphi, *tK, *tD;    // FP64 totals
   const long long *cells;    // fluid edge cells, then volumetric catalyst cells
+  const uint32_t *pushed;    // per edge cell: links that have a fluid consumer
   int n_edge, n_own;         // edge cells; all own-use cells
 };
-template <typename S> void launch_adj_step(const void *src, const DevGeom &g, const KArgs &a, int fickian, const AdjPtrs &b, long long seed_cell, cudaStream_t st, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join);
+template <typename S> void launch_adj_step(const void *src, const DevGeom &g, const KArgs &a, int fickian, const AdjPtrs &b, long long seed_cell, int lam_complete, cudaStream_t st, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join);
+template <typename S> void launch_adj_finish(const DevGeom &g, const KArgs &a, const AdjPtrs &b, cudaStream_t st);
 template <typename S> void launch_adj_fold(const DevGeom &g, const KArgs &a, const AdjPtrs &b, cudaStream_t st);
 template <typename S> void launch_adj_seed_current(const void *src, const DevGeom &g, const KArgs &a, int fickian, double weight, const AdjPtrs &b, cudaStream_t st);
 
