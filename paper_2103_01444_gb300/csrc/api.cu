@@ -949,25 +949,58 @@ lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t se
   const int64_t nck = (N + seg - 1) / seg;     // checkpoints of s^0, s^seg, ... (< N)
   const size_t stride = 24 * (size_t)d->plane + d->nxp + 64;   // guard as in the domain
   const size_t sbytes = stride * d->esize;
-  DevBuf ck, sg;
+  DevBuf ck, sgb[2];
   if ((s = ck.alloc(sbytes * nck)) != LBM_OK) return s;
-  if ((s = sg.alloc(sbytes * (seg + 1))) != LBM_OK) return s;
+  if ((s = sgb[0].alloc(sbytes * (seg + 1))) != LBM_OK) return s;
+  // A second segment buffer lets segment k - 1 be recomputed (on a stream
+  // of its own) while segment k is reversed; without room for it the two
+  // alternate on one buffer.
+  bool overlap = false;
+  if (nck > 1) {
+    if (cudaMalloc(&sgb[1].p, sbytes * (seg + 1)) == cudaSuccess) overlap = true;
+    else cudaGetLastError();
+  }
+  struct Sync {   // recompute stream and its two buffer events
+    cudaStream_t rs = nullptr;
+    cudaEvent_t ready[2] = {nullptr, nullptr}, freed[2] = {nullptr, nullptr};
+    ~Sync() {
+      for (cudaEvent_t e : {ready[0], ready[1], freed[0], freed[1]})
+        if (e) cudaEventDestroy(e);
+      if (rs) cudaStreamDestroy(rs);
+    }
+  } sync;
+  if (overlap) {
+    if (cudaStreamCreateWithFlags(&sync.rs, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(LBM_ECUDA, "cudaStreamCreate failed");
+    }
+    for (cudaEvent_t *e : {&sync.ready[0], &sync.ready[1], &sync.freed[0], &sync.freed[1]})
+      if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LBM_ECUDA, "cudaEventCreate failed");
+      }
+  }
+  cudaStream_t rstream = overlap ? sync.rs : d->stream;
   AdjWork w;
   if ((s = w.alloc(d)) != LBM_OK) return s;
   if ((s = w.zero_grads(d)) != LBM_OK) return s;
-  CK(cudaMemsetAsync(sg.p, 0, sbytes * (seg + 1), d->stream));
+  for (int b = 0; b < (overlap ? 2 : 1); ++b)
+    CK(cudaMemsetAsync(sgb[b].p, 0, sbytes * (seg + 1), d->stream));
   auto CKP = [&](int64_t k) { return (void *)((char *)ck.p + k * sbytes); };
-  auto SEG = [&](int64_t j) { return (void *)((char *)sg.p + j * sbytes); };
+  auto SEGB = [&](int b, int64_t j) {
+    return (void *)((char *)sgb[overlap ? b : 0].p + j * sbytes);
+  };
   const KArgs a = make_args(d);
   const DevGeom g = geom(d);
-  auto fwd = [&](const void *src, void *dst) {
+  auto fwd = [&](const void *src, void *dst, cudaStream_t st) {
     dispatch(d->desc.precision, [&](auto *tag) {
       using S = std::remove_pointer_t<decltype(tag)>;
-      launch_step<S>(src, dst, g, a, d->variant, d->stream);
+      launch_step<S>(src, dst, g, a, d->variant, st);
     });
   };
   // Work of a full segment is replayed from CUDA graphs: the same buffers
   // and launches for every segment (only the checkpoint copied differs).
+  // Graphs are captured on the domain's stream and may be launched on any.
   struct Graph {
     cudaGraphExec_t g = nullptr;
     ~Graph() {
@@ -986,42 +1019,66 @@ lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t se
     if (e != cudaSuccess) return fail(LBM_ECUDA, "adjoint graph instantiate: %s", cudaGetErrorString(e));
     return LBM_OK;
   };
-  Graph g_fwd, g_rec, g_rev[2];
-  // forward s^0 .. s^{N-1}: segment k starts from SEG(0) = s^{k seg}
+  Graph g_fwd, g_rec[2], g_rev[2][2];
+  // forward s^0 .. s^{N-1}: segment k starts from SEGB(0, 0) = s^{k seg}
   CK(cudaMemcpyAsync(CKP(0), d->pop[d->cur], sbytes, cudaMemcpyDeviceToDevice, d->stream));
-  CK(cudaMemcpyAsync(SEG(0), d->pop[d->cur], sbytes, cudaMemcpyDeviceToDevice, d->stream));
+  CK(cudaMemcpyAsync(SEGB(0, 0), d->pop[d->cur], sbytes, cudaMemcpyDeviceToDevice, d->stream));
   for (int64_t k = 0; k + 1 < nck; ++k) {
-    // seg steps SEG(0) -> ... -> SEG(seg & 1), then back into SEG(0)
+    // seg steps SEGB(0, 0) -> ... -> SEGB(0, seg & 1), then back into SEGB(0, 0)
     auto body = [&] {
-      for (int j = 1; j <= seg; ++j) fwd(SEG((j - 1) & 1), SEG(j & 1));
-      if (seg & 1) cudaMemcpyAsync(SEG(0), SEG(1), sbytes, cudaMemcpyDeviceToDevice, d->stream);
+      for (int j = 1; j <= seg; ++j) fwd(SEGB(0, (j - 1) & 1), SEGB(0, j & 1), d->stream);
+      if (seg & 1)
+        cudaMemcpyAsync(SEGB(0, 0), SEGB(0, 1), sbytes, cudaMemcpyDeviceToDevice, d->stream);
     };
     if ((s = capture(g_fwd, body)) != LBM_OK) return s;
     CK(cudaGraphLaunch(g_fwd.g, d->stream));
-    CK(cudaMemcpyAsync(CKP(k + 1), SEG(0), sbytes, cudaMemcpyDeviceToDevice, d->stream));
+    CK(cudaMemcpyAsync(CKP(k + 1), SEGB(0, 0), sbytes, cudaMemcpyDeviceToDevice, d->stream));
   }
   CK(cudaGetLastError());
+  // Segment k lives in buffer k & 1.  Its recompute (on rstream) waits until
+  // the reverse of segment k + 2, the last user of that buffer, has ended;
+  // its reverse (on the domain's stream) waits until the recompute is done.
+  if (overlap)
+    for (int b = 0; b < 2; ++b) CK(cudaEventRecord(sync.freed[b], d->stream));
+  auto span = [&](int64_t k, int64_t &first, int64_t &last) {
+    first = k * seg;
+    last = std::min<int64_t>(first + seg - 1, N - 1);
+    return last - first + 1 == seg && k != nck - 1;   // a full segment
+  };
+  auto recompute = [&](int64_t k) -> lbm_status {
+    const int b = (int)(k & 1);
+    int64_t first, last;
+    const bool full = span(k, first, last);
+    if (overlap) CK(cudaStreamWaitEvent(rstream, sync.freed[b], 0));
+    CK(cudaMemcpyAsync(SEGB(b, 0), CKP(k), sbytes, cudaMemcpyDeviceToDevice, rstream));
+    if (full) {
+      auto body = [&] {
+        for (int j = 1; j < seg; ++j) fwd(SEGB(b, j - 1), SEGB(b, j), d->stream);
+      };
+      if ((s = capture(g_rec[b], body)) != LBM_OK) return s;
+      CK(cudaGraphLaunch(g_rec[b].g, rstream));
+    } else {
+      for (int64_t n = first + 1; n <= last; ++n)
+        fwd(SEGB(b, n - 1 - first), SEGB(b, n - first), rstream);
+    }
+    if (overlap) CK(cudaEventRecord(sync.ready[b], rstream));
+    CK(cudaGetLastError());
+    return LBM_OK;
+  };
   // reverse, last segment first
   int cur = 0;
   long long seed_cell = -1;
   bool fresh = true;   // lam[cur] is the seed, held in full (see reverse_step)
+  if ((s = recompute(nck - 1)) != LBM_OK) return s;
   for (int64_t k = nck - 1; k >= 0; --k) {
-    const int64_t first = k * seg, last = std::min<int64_t>(first + seg - 1, N - 1);
-    bool full = last - first + 1 == seg && k != nck - 1;
-    CK(cudaMemcpyAsync(SEG(0), CKP(k), sbytes, cudaMemcpyDeviceToDevice, d->stream));
-    if (full) {
-      auto body = [&] {
-        for (int j = 1; j < seg; ++j) fwd(SEG(j - 1), SEG(j));
-      };
-      if ((s = capture(g_rec, body)) != LBM_OK) return s;
-      CK(cudaGraphLaunch(g_rec.g, d->stream));
-    } else {
-      for (int64_t n = first + 1; n <= last; ++n) fwd(SEG(n - 1 - first), SEG(n - first));
-    }
-    CK(cudaGetLastError());
+    if (k >= 1 && (s = recompute(k - 1)) != LBM_OK) return s;
+    const int b = (int)(k & 1);
+    int64_t first, last;
+    bool full = span(k, first, last);
+    if (overlap) CK(cudaStreamWaitEvent(d->stream, sync.ready[b], 0));
     if (k == nck - 1) {
       // objective at step N from s^{N-1}, and its seed lambda^{N-1}
-      const void *sN1 = SEG(N - 1 - first);
+      const void *sN1 = SEGB(b, N - 1 - first);
       const lbm_params &p = d->prm;
       const double i_scale = 4.0 * p.F * p.c_tot * p.dx_cm / p.dt_s;
       if (objective == 0) {
@@ -1064,22 +1121,23 @@ lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t se
       auto body = [&] {
         int cc = c0;
         for (int64_t n = ntop; n >= first + 1; --n) {
-          reverse_step(d, w, cc, SEG(n - 1 - first), -1);
+          reverse_step(d, w, cc, SEGB(b, n - 1 - first), -1);
           cc ^= 1;
         }
         fold_grads(d, w);
       };
-      if ((s = capture(g_rev[c0], body)) != LBM_OK) return s;
-      CK(cudaGraphLaunch(g_rev[c0].g, d->stream));
+      if ((s = capture(g_rev[c0][b], body)) != LBM_OK) return s;
+      CK(cudaGraphLaunch(g_rev[c0][b].g, d->stream));
       cur ^= (int)(seg & 1);
     } else {
       for (int64_t n = ntop; n >= first + 1; --n) {
-        reverse_step(d, w, cur, SEG(n - 1 - first), -1, fresh);
+        reverse_step(d, w, cur, SEGB(b, n - 1 - first), -1, fresh);
         fresh = false;
         cur ^= 1;
       }
       fold_grads(d, w);
     }
+    if (overlap) CK(cudaEventRecord(sync.freed[b], d->stream));
     CK(cudaGetLastError());
   }
   finish_lambda(d, w, cur);   // adds the last step's outlet term to gphi
