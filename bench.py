@@ -365,13 +365,10 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
-def sweep(args, stream):
-    """The operating-point sweep: ncases cathodes of uneven size (512..2048
-    x 128..512, V, T, Re, K drawn from a seed) advanced together.  Reports
-    cases x steps per second for the tuned batched schedule and for one
+def sweep_run(cases, args, stream):
+    """Cases x steps per second for the tuned batched schedule, for one
     launch per case and step (same kernel, no graph), and their ratio."""
     from paper_2103_01444_gb300.lbm import Batch, Domain
-    cases = workloads.sweep_cases(args.sweep_cases)
     doms = [Domain.from_case(c, precision=args.precision, stream=stream.cuda_stream)
             for c in cases]
     cells = sum(c["nx"] * c["ny"] for c in cases)
@@ -396,6 +393,19 @@ def sweep(args, stream):
     b.close()
     for d in doms:
         d.close()
+    return out
+
+
+def sweep(args, stream):
+    """The operating-point sweep: ncases cathodes of uneven size (512..2048
+    x 128..512, V, T, Re, K drawn from a seed) advanced together, and the
+    same sweep over 256 small cathodes (128..512 x 32..128), where one launch
+    per case leaves most of the GPU idle."""
+    out = sweep_run(workloads.sweep_cases(args.sweep_cases), args, stream)
+    small = workloads.sweep_cases(256, seed=2103, nx_range=(128, 512), ny_range=(32, 128),
+                                  re_range=(5.0, 20.0))
+    out["small_cases"] = sweep_run(small, args, stream)
+    out["small_cases"]["workload"] = "256 cathodes 128..512 x 32..128, Re 5..20"
     return out
 
 

@@ -248,15 +248,21 @@ k_residual(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
     X[2] = own_sum<S, R>(src, 0, x, y) + a.theta0;
     X[3] = own_sum<S, R>(src, 1, x, y) + R(a.Cref[1]);
     X[4] = own_sum<S, R>(src, 2, x, y) + R(a.Cref[2]);
+    // all five snapshot values are read before any is overwritten, so the
+    // loads overlap instead of waiting on each other's stores
+    R prev[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) prev[k] = snap[k * n + o];
     bool ok = true;
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
       ok = ok && isfinite(X[k]);
-      const R dv = X[k] - snap[k * n + o];
+      const R dv = X[k] - prev[k];
       v[k] = dv * dv;
       v[5 + k] = X[k] * X[k];
-      snap[k * n + o] = X[k];
     }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) snap[k * n + o] = X[k];
     if (!ok) *bad = 1;
   }
 #pragma unroll

@@ -105,11 +105,13 @@ def cathode_grains(nx: int = 8192, ny: int = 2048, seed: int = 7, solid_fraction
 
 
 def sweep_cases(n: int = 64, seed: int = 1444, nx_range=(512, 2048), ny_range=(128, 512),
-                steps: int = 20000) -> list:
+                steps: int = 20000, re_range=(10.0, 100.0)) -> list:
     """Operating-point sweep: cell voltage U[0.3, 0.9] V, temperature
-    U[333, 363] K, Re log-uniform [10, 100], GDL permeability one of
-    1e-12/1e-11/1e-10 m^2, grid sizes U{nx_range} x U{ny_range} rounded down
-    to multiples of 32, 40/55/5 % split, volumetric catalyst."""
+    U[333, 363] K, Re log-uniform over re_range (default [10, 100]), GDL
+    permeability one of 1e-12/1e-11/1e-10 m^2, grid sizes U{nx_range} x
+    U{ny_range} rounded down to multiples of 32, 40/55/5 % split, volumetric
+    catalyst.  Small channels need a smaller Re to keep the inlet Mach
+    number low."""
     rng = np.random.default_rng(seed)
     out = []
     for k in range(n):
@@ -117,7 +119,7 @@ def sweep_cases(n: int = 64, seed: int = 1444, nx_range=(512, 2048), ny_range=(1
         ny = int(rng.integers(ny_range[0], ny_range[1] + 1)) // 32 * 32
         V = float(rng.uniform(0.3, 0.9))
         T = float(rng.uniform(333.0, 363.0))
-        Re = float(10.0 ** rng.uniform(1.0, 2.0))
+        Re = float(10.0 ** rng.uniform(np.log10(re_range[0]), np.log10(re_range[1])))
         Kg = float(rng.choice([1e-12, 1e-11, 1e-10])) * 1e4
         ny_cl, ny_gdl = split_rows(ny)
         phi, K = _layered(nx, ny, ny_cl, ny_gdl, 0.6, Kg, phi_cl=0.4, K_cl_cm2=1e-8)

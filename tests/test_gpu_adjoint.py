@@ -1,7 +1,8 @@
 """Discrete adjoint of the coupled step.
 
-1. One transposed step against finite differences of the FP64 GPU step
-   (dot-product test) in state and parameter directions.
+1. One transposed step against finite differences of the FP64 GPU step and
+   of the independent FP64 oracle's step (dot-product test) in state and
+   parameter directions.
 2. Gradients of the objectives (mean current density, hottest catalyst-row
    temperature) after N steps against FP64 central finite differences of the
    independent oracle, within 1e-3 relative.
@@ -69,6 +70,19 @@ def test_one_step_transpose_dot_product(name, mode):
     ad = np.sum(lam_prev * v)
     assert abs(fd - ad) <= 1e-7 * (abs(fd) + np.abs(lam_prev * v).sum()), (fd, ad)
 
+    # the same directional derivative from the independent FP64 oracle's step
+    o_params, o_mat, o_solid = lattice_problem(case, interface_mode=mode)
+
+    def oracle_step_from(state, material=None):
+        o = Oracle(o_params, material if material is not None else o_mat, o_solid)
+        o.f[...] = state[:9]
+        o.g[...] = state[9:].reshape(3, 5, *state.shape[1:])
+        o.step(1)
+        return np.concatenate([o.f, o.g.reshape(15, *state.shape[1:])]) * live
+
+    fdo = np.sum(lam * (oracle_step_from(s0 + eps * v) - oracle_step_from(s0 - eps * v))) / (2 * eps)
+    assert abs(fdo - ad) <= 1e-7 * (abs(fdo) + np.abs(lam_prev * v).sum()), (fdo, ad)
+
     params, fields, _ = cathode_params(case, interface_mode=mode)
     gdl = np.zeros((case["ny"], case["nx"]), bool)
     gdl[case["ny_cl"]:case["ny_cl"] + case["ny_gdl"]] = True
@@ -84,6 +98,11 @@ def test_one_step_transpose_dot_product(name, mode):
         fdp = np.sum(lam * diff) / (2 * h)
         adp = np.sum(g[gkey] * vv)
         assert abs(fdp - adp) <= 1e-4 * max(abs(fdp), abs(adp), 1e-12), (key, fdp, adp)
+        base_o = o_mat[key]
+        diff_o = (oracle_step_from(s0, dict(o_mat, **{key: base_o + h * vv})) -
+                  oracle_step_from(s0, dict(o_mat, **{key: base_o - h * vv})))
+        fdo = np.sum(lam * diff_o) / (2 * h)
+        assert abs(fdo - adp) <= 1e-4 * max(abs(fdo), abs(adp), 1e-12), (key, fdo, adp)
     d.set_fields(**fields)
     h = 1e-6 * params["u_in_avg"]
     diff = (step_from(s0, params=dict(params, u_in_avg=params["u_in_avg"] + h)) -
