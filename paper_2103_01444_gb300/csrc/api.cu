@@ -67,7 +67,7 @@ struct lbm_domain {
   void *pop[2] = {nullptr, nullptr};
   int cur = 0;                 // buffer holding the latest state
   int64_t steps = 0;
-  uint8_t *mask = nullptr;
+  uint8_t *mask = nullptr;    // [2][ny][nxp]: node bits, then solid-neighbour bits
   uint16_t *mid = nullptr;
   void *pal = nullptr;
   MatRaw *raw = nullptr;
@@ -292,7 +292,7 @@ lbm_status lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
   const size_t coef = fp64(d) ? sizeof(MatCoef<double>) : sizeof(MatCoef<float>);
   const size_t rsize = fp64(d) ? 8 : 4;
   if (cudaMalloc(&d->pop[0], pop_bytes) != cudaSuccess || cudaMalloc(&d->pop[1], pop_bytes) != cudaSuccess ||
-      cudaMalloc(&d->mask, cells) != cudaSuccess || cudaMalloc(&d->mid, cells * 2) != cudaSuccess ||
+      cudaMalloc(&d->mask, 2 * cells) != cudaSuccess || cudaMalloc(&d->mid, cells * 2) != cudaSuccess ||
       cudaMalloc(&d->pal, coef * kMaxPalette) != cudaSuccess ||
       cudaMalloc(&d->raw, sizeof(MatRaw) * kMaxPalette) != cudaSuccess ||
       cudaMalloc(&d->snap, rsize * 5 * (size_t)D.nx * D.ny) != cudaSuccess ||

@@ -4,14 +4,17 @@
 namespace pemlbm {
 
 // Node mask (Sec. 4 geometry): region by rows, boundary bits by position,
-// explicit solids, and a flag for cells with a solid D2Q9 neighbour.
+// explicit solids, and a flag for cells with a solid D2Q9 neighbour; a
+// second plane of the same size says which neighbours are solid.
 __global__ void k_build_mask(uint8_t *__restrict__ mask, const uint8_t *__restrict__ solid, int nx,
                              int ny, int nxp, int ny_cl, int ny_gdl, int mode, int periodic) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   if (x >= nxp || y >= ny) return;
   const long long c = (long long)y * nxp + x;
+  const long long plane = (long long)nxp * ny;
   if (x >= nx) {
     mask[c] = REG_SOLID;   // padding: never updated, never a pull source
+    mask[plane + c] = 0;
     return;
   }
   auto is_solid = [&](int xx, int yy) { return solid && solid[(long long)yy * nx + xx]; };
@@ -26,18 +29,23 @@ __global__ void k_build_mask(uint8_t *__restrict__ mask, const uint8_t *__restri
   if (y == ny - 1) m |= M_YHI;
   if (y == 0) m |= M_YLO;
   if (reg == REG_CLEAR && x == 0 && !periodic) m |= M_INLET;
+  // second plane: bit i - 1 set when the source x - e_i of flow link i
+  // (i = 1..8, Eq. 2 order) is a solid cell inside the lattice
+  uint8_t nb = 0;
   if (reg != REG_SOLID && solid) {
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx) {
-        if (!dx && !dy) continue;
-        int sx = x + dx, sy = y + dy;
-        if (sy < 0 || sy >= ny) continue;
-        if (periodic) sx = (sx + nx) % nx;
-        if (sx < 0 || sx >= nx) continue;
-        if (is_solid(sx, sy)) m |= M_NEAR_SOLID;
-      }
+    const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1}, ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    for (int i = 1; i < 9; ++i) {
+      int sx = x - ex[i];
+      const int sy = y - ey[i];
+      if (sy < 0 || sy >= ny) continue;
+      if (periodic) sx = (sx + nx) % nx;
+      if (sx < 0 || sx >= nx) continue;
+      if (is_solid(sx, sy)) nb |= (uint8_t)(1u << (i - 1));
+    }
+    if (nb) m |= M_NEAR_SOLID;
   }
   mask[c] = m;
+  mask[plane + c] = nb;
 }
 
 void launch_build_mask(uint8_t *mask, const uint8_t *solid, int nx, int ny, int nxp, int ny_cl,

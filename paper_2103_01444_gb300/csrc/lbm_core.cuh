@@ -337,6 +337,24 @@ __device__ __forceinline__ void fix_edges(const Pops<S, CG> &src, const KArgsT<R
       c.g[s][i] = pull_scalar_edge<S, R, CG>(src, a, mask, mc, s, i, x, y, m, c.g[s][i]);
 }
 
+// Cells whose only edge bit is M_NEAR_SOLID: a link whose source is a solid
+// grain takes the cell's own population of the opposite link (bounce-back,
+// as pull_flow_edge and pull_scalar_edge do); nb holds the solid sources
+// (bit i - 1 for link i of Eq. 2; the D2Q5 links are the first four).
+template <typename S, typename R, bool CG = false>
+__device__ __forceinline__ void bounce_solid(const Pops<S, CG> &src, int x, int y, uint32_t nb,
+                                             Cell<R> &c) {
+  const int OP[9] = OP9_TAB;
+#pragma unroll
+  for (int i = 1; i < 9; ++i)
+    if (nb & (1u << (i - 1))) c.f[i] = R(src.at(OP[i], x, y));
+#pragma unroll
+  for (int s = 0; s < 3; ++s)
+#pragma unroll
+    for (int i = 1; i < 5; ++i)
+      if (nb & (1u << (i - 1))) c.g[s][i] = R(src.at(9 + 5 * s + OP[i], x, y));
+}
+
 // Pull all 24 populations of a non-solid cell (x, y).
 template <typename S, typename R, bool CG = false>
 __device__ __forceinline__ void pull_cell(const Pops<S, CG> &src, const KArgsT<R> &a,

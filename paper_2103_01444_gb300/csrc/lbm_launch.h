@@ -36,7 +36,7 @@ template <typename F> struct KArgsT;
 
 // Device-resident geometry shared by all kernels of a domain.
 struct DevGeom {
-  const uint8_t *mask;   // [ny][nxp] node bits
+  const uint8_t *mask;   // [ny][nxp] node bits, then [ny][nxp] solid-neighbour bits
   const uint16_t *mid;   // [ny][nxp] palette index
   const void *pal;       // MatCoef<R>[npal]
 };

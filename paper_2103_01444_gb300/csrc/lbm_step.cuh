@@ -28,7 +28,11 @@ __device__ __forceinline__ void cell_update(const S *__restrict__ src_p, S *__re
   // skip the stores, so no branch stands between the mask and the loads
   const bool live = (m & REG_MASK) != REG_SOLID;
   const MatCoef<R> mc = pal[mid[c]];
-  if (m & M_EDGE) fix_edges<S, R, CG>(src, a, mask, mid, pal, mc, x, y, m, cell);
+  if (m & M_EDGE) {
+    // next to grains but away from the lattice's edges: bounce-back only
+    if ((m & M_EDGE) == M_NEAR_SOLID) bounce_solid<S, R, CG>(src, x, y, mask[a.plane + c], cell);
+    else fix_edges<S, R, CG>(src, a, mask, mid, pal, mc, x, y, m, cell);
+  }
   if (a.mode == 0 && (m & M_YLO)) surface_reaction<S, R, CG>(src, a, mc, x, cell);
   R S_vol = 0;
   if (a.mode == 1 && (m & REG_MASK) == REG_CATALYST) S_vol = volume_sink<S, R, CG>(src, a, x, y);
