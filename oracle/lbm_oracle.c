@@ -28,6 +28,9 @@
  *     velocity taken where the link crosses the inlet plane) over the
  *     channel rows; GDL/CL rows at the inlet are walls.  Scalars:
  *     anti-bounce-back Dirichlet at the inlet channel rows.
+ *   - Pressure inlet (inlet_mode 1, the drive of Sec. 4): the channel rows
+ *     pull from a virtual column -1 that repeats column 0 with its
+ *     equilibrium pressure part moved to phi p = rho0/3 + dp_in.
  *   - Outlet: fully developed (the virtual column nx repeats column nx-1);
  *     for the flow, the virtual cell's equilibrium pressure part is moved to
  *     the specified outlet pressure phi p = rho0/3 (Sec. 5), which anchors
@@ -153,7 +156,7 @@ typedef struct {
   int32_t top_dirichlet;    /* scalars at the top wall: 0 insulated, 1 Dirichlet */
   int32_t interface_mode;   /* 0: per-cell b, fixed Q (Eq. 10 as printed);
                                1: Fickian: one b per scalar, per-cell flux rate */
-  int32_t reserved;
+  int32_t inlet_mode;       /* 0: parabolic velocity inlet; 1: pressure inlet (Sec. 4) */
   double nu;                /* kinematic viscosity; 3 nu = tau - 1/2 (Eq. 8) */
   double u_in_avg;          /* mean inlet velocity over the channel rows */
   double body_force_x;      /* uniform body force per unit mass (tests only) */
@@ -165,6 +168,7 @@ typedef struct {
   double dU0dT, U0_0;       /* Eq. 16 */
   double x_ref;             /* reference O2 mole fraction (C_O2,ref) */
   double dx_cm, dt_s, delta_cl_cm, c_tot, rho_cp_f;
+  double dp_in;             /* pressure inlet: phi p there is rho0/3 + dp_in */
 } orc_params;
 
 /* Per-cell material, lattice units. K = +inf marks clear fluid.  sigma is
@@ -490,7 +494,21 @@ static void stream(const orc_params *P, const orc_material *mat, const uint8_t *
         } else {
           if (P->periodic_x) sx = (sx + nx) % nx;
           if (sx < 0) {
-            if (m & B_INLET) {                                /* moving-wall inlet */
+            if ((m & B_INLET) && P->inlet_mode == 1) {
+              /* pressure inlet: the virtual column -1 repeats column 0 (fully
+               * developed), with its equilibrium pressure part moved to
+               * phi p = rho0/3 + dp_in; the outlet stays at rho0/3, so the
+               * pressure difference drives the flow (Sec. 4).  A source row
+               * outside the channel is the GDL's end wall. */
+              size_t cv = IDX(0, sy);
+              if (mask[cv] & B_INLET) {
+                val = fs[i * n + cv] +
+                      pressure_weight(i) * (1.0 / 3.0 + P->dp_in - post_pressure(mat->phi[cv], fs, n, cv));
+                diag[D_IN + 0] += val - fs[io * n + c];
+              } else {
+                val = fs[io * n + c];
+              }
+            } else if (m & B_INLET) {                         /* moving-wall inlet */
               /* link crosses the inlet plane at height y - e_iy/2 */
               double uin = inlet_u(P, y - 0.5 * EY9[i]);
               val = fs[io * n + c] + 6.0 * W9[i] * 1.0 * (EX9[i] * uin);

@@ -39,7 +39,7 @@ class Params(C.Structure):
         ("nx", C.c_int32), ("ny", C.c_int32), ("ny_cl", C.c_int32), ("ny_gdl", C.c_int32),
         ("reaction_mode", C.c_int32), ("periodic_x", C.c_int32),
         ("forchheimer", C.c_int32), ("top_dirichlet", C.c_int32),
-        ("interface_mode", C.c_int32), ("reserved", C.c_int32),
+        ("interface_mode", C.c_int32), ("inlet_mode", C.c_int32),
         ("nu", C.c_double), ("u_in_avg", C.c_double), ("body_force_x", C.c_double),
         ("V_op", C.c_double), ("T_in", C.c_double), ("C_O2_in", C.c_double),
         ("C_H2O_in", C.c_double),
@@ -48,7 +48,7 @@ class Params(C.Structure):
         ("alpha_c", C.c_double), ("F", C.c_double), ("R", C.c_double),
         ("dU0dT", C.c_double), ("U0_0", C.c_double), ("x_ref", C.c_double),
         ("dx_cm", C.c_double), ("dt_s", C.c_double), ("delta_cl_cm", C.c_double),
-        ("c_tot", C.c_double), ("rho_cp_f", C.c_double),
+        ("c_tot", C.c_double), ("rho_cp_f", C.c_double), ("dp_in", C.c_double),
     ]
 
 

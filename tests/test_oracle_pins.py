@@ -264,6 +264,39 @@ def test_poiseuille_exact():
     assert np.abs(u - ex).max() / ex.max() < 1e-8
 
 
+def test_pressure_driven_poiseuille_exact():
+    """The paper's drive (Sec. 4): no body force, inlet pressure phi p =
+    1/3 + dp at the virtual column -1, 1/3 at the virtual column nx.  The
+    pressure falls linearly over nx + 1 spacings, G = dp/(nx + 1), and the
+    steady profile is G/(2 nu) y (H - y) in every column, with no transverse
+    velocity."""
+    nx, ny, dp, nu = 10, 12, 2e-5, 0.05
+    p = base_params(nx, ny, nu=nu, periodic_x=0, inlet_mode=1, dp_in=dp)
+    o = Oracle(p, uniform_material(nx, ny))
+    o.step(30000)
+    f = o.fields()
+    y = np.arange(ny) + 0.5
+    ex = dp / (nx + 1) / (2 * nu) * y * (ny - y)
+    for x in (0, nx // 2, nx - 1):
+        assert np.abs(f["ux"][:, x] - ex).max() / ex.max() < 1e-8, x
+    # transverse velocity at round-off of the populations (~1e-12 absolute)
+    assert np.abs(f["uy"]).max() < 1e-7 * ex.max()
+    # the pressure falls linearly between the two virtual columns
+    pc = f["p"][ny // 2]
+    assert np.allclose(np.diff(pc), -dp / (nx + 1), rtol=1e-6, atol=0)
+    # mass balance: what enters through the inlet links equals the column
+    # flux and leaves through the outlet
+    d = f["diag"]
+    flux = f["ux"][:, nx // 2].sum()
+    assert d[DIAG["in_mass"]] == pytest.approx(flux, rel=1e-9)
+    assert d[DIAG["out_mass"]] == pytest.approx(-flux, rel=1e-9)
+    # the same with the inlet disabled (velocity mode, zero velocity): no flow
+    o0 = Oracle(base_params(nx, ny, nu=nu, periodic_x=0, inlet_mode=0, dp_in=dp),
+                uniform_material(nx, ny))
+    o0.step(2000)
+    assert np.abs(o0.fields()["ux"]).max() < 1e-14
+
+
 def brinkman_error(H, phi=0.5):
     g, nu = 1e-6, 0.05
     K = phi * H * H / 16.0
