@@ -58,6 +58,15 @@ def parse():
                          "8192x2048 pore-scale grains + thin film")
     ap.add_argument("--interface", type=int, default=0, choices=[0, 1],
                     help="0: Eq. 10 as printed (per-cell b); 1: Fickian interfaces")
+    ap.add_argument("--inlet", default="velocity", choices=["velocity", "pressure"],
+                    help="drive of the flow: parabolic inlet velocity at Re, or the pressure "
+                         "difference of Sec. 4 (--dp-in, lattice units)")
+    ap.add_argument("--dp-in", type=float, default=2e-3)
+    ap.add_argument("--to-residual", type=float, default=0.0, metavar="TOL",
+                    help="instead of the throughput bench: step the workload from reset until "
+                         "the residual (checked every 100 steps) is below TOL, or until "
+                         "--max-seconds of stepping; one JSON line with steps and wall time")
+    ap.add_argument("--max-seconds", type=float, default=240.0)
     return ap.parse_args()
 
 
@@ -98,8 +107,12 @@ def workload(args):
     if args.workload == "grains":
         nx = args.nx if args.nx != NX else 8192
         ny = args.ny if args.ny != NY else 2048
-        return workloads.cathode_grains(nx=nx, ny=ny)
-    return workloads.cathode_blocks(nx=args.nx, ny=args.ny)
+        case = workloads.cathode_grains(nx=nx, ny=ny)
+    else:
+        case = workloads.cathode_blocks(nx=args.nx, ny=args.ny)
+    if getattr(args, "inlet", "velocity") == "pressure":
+        case = dict(case, inlet="pressure", dp_in=args.dp_in)
+    return case
 
 
 def measured_peak():
@@ -343,7 +356,9 @@ def run_ours(args):
                    "interface_mode": args.interface,
                    "step_variant": variant,
                    "V_op": case["V_op"],
-                   "Re": case["Re"], "T_in": case["T_in"]},
+                   "inlet": (f"pressure, dp_in {case['dp_in']:g}" if case.get("inlet") == "pressure"
+                             else f"velocity, Re {case['Re']:g}"),
+                   "T_in": case["T_in"]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic_from_profiles(),
                      "peak_source": peak_kind, "bytes_per_cell": bpc,
@@ -468,9 +483,59 @@ def end_to_end(case, precision, K, stream, interface_mode=0):
             "includes": "material upload, reset, per-step current-density read, final fields read"}
 
 
+def run_to_residual(args):
+    """The separate run of the production cathode to residual < TOL: steps
+    and wall time from reset, the residual r = max over (u_x, u_y, T - T_in,
+    C_O2, C_H2O) of ||X^n - X^{n-100}|| / ||X^n|| checked every 100 steps
+    (FP64 accumulation), and its trace.  Stops at TOL or after max-seconds
+    of stepping and says which."""
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (there is no CPU fallback)")
+    from paper_2103_01444_gb300.build import build
+    from paper_2103_01444_gb300.lbm import Domain, LbmError
+    build()
+    case = workload(args)
+    d = Domain.from_case(case, precision=args.precision, interface_mode=args.interface)
+    d.tune(10)
+    d.reset()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps, r, trace = 0, float("inf"), []
+    d.residual()                       # snapshot of the reset state
+    while True:
+        d.step(100)
+        steps += 100
+        try:
+            r = d.residual()
+        except LbmError as e:          # diverged: report it
+            r = float("nan")
+            trace.append([steps, str(e)])
+            break
+        if steps % 10000 == 0 or r < args.to_residual:
+            trace.append([steps, r])
+        if r < args.to_residual or time.perf_counter() - t0 > args.max_seconds:
+            break
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    i_avg, heat, _ = d.current_density(profile=False)
+    cells = case["nx"] * case["ny"]
+    print(json.dumps({
+        "metric": "steps to residual", "tol": args.to_residual,
+        "reached": bool(r < args.to_residual), "steps": steps, "wall_s": wall,
+        "final_residual": r, "mlups_incl_checks": cells * steps / wall / 1e6,
+        "i_avg_A_cm2": i_avg, "heat_W_cm2": heat,
+        "config": {"workload": f"cathode-{case['nx']}x{case['ny']}-{args.workload}",
+                   "storage": args.precision, "check_every": 100},
+        "trace": trace}))
+    d.close()
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.to_residual > 0:
+        run_to_residual(a)
     else:
         run_ours(a)

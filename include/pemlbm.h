@@ -92,7 +92,15 @@ typedef struct {
                                   1: Fickian, one b per scalar (that of its largest
                                   diffusivity) and each cell's diffusivity set through
                                   the flux-moment rate (C and -alpha grad C continuous) */
-  int32_t reserved;            /* must be 0 */
+  int32_t inlet_mode;          /* drive of the flow: 0 parabolic inlet velocity u_in_avg over
+                                  the channel rows (Ladd moving wall); 1 the pressure
+                                  difference of Sec. 4: the channel rows pull from a virtual
+                                  column -1 that repeats column 0 with its equilibrium
+                                  pressure moved to phi p = 1/3 + dp_in, against 1/3 at the
+                                  outlet (u_in_avg is then unused).  lbm_grad and lbm_vjp
+                                  need inlet_mode 0 (EINVAL otherwise). */
+  double dp_in;                /* inlet pressure excess of inlet_mode 1, lattice units,
+                                  |dp_in| < 0.01 */
 } lbm_params;
 
 typedef struct lbm_domain lbm_domain; /* opaque */
@@ -108,7 +116,8 @@ lbm_status lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out);
 lbm_status lbm_destroy_domain(lbm_domain *d);
 
 /* Copies the operating point (Sec. 4-5).  EINVAL unless nu > 0,
- * sqrt(3) * 1.5 * u_in_avg < 0.3, T_in > 0, dx_cm > 0, dt_s > 0. */
+ * sqrt(3) * 1.5 * u_in_avg < 0.3 (inlet_mode 0), |dp_in| < 0.01 (inlet_mode
+ * 1), T_in > 0, dx_cm > 0, dt_s > 0. */
 lbm_status lbm_set_params(lbm_domain *d, const lbm_params *p);
 
 /* Per-cell material, host arrays [ny][nx] of doubles, lattice units:
@@ -223,15 +232,17 @@ lbm_status lbm_bytes_per_cell(lbm_domain *d, double *bytes);
  * Fickian interface mode treats each scalar's b (that of its largest
  * diffusivity) as fixed.  J and the gradients go to host memory: dphi, dK,
  * dD_O2 are [ny][nx] doubles (NULL to skip), du_in one double.  EINVAL for
- * objective outside {0, 1} or nsteps outside [2, 2^30]; ENOMEM if the
- * checkpoints do not fit. */
+ * objective outside {0, 1}, nsteps outside [2, 2^30] or the pressure inlet
+ * (inlet_mode 1, whose boundary links have no transpose here); ENOMEM if
+ * the checkpoints do not fit. */
 lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t segment,
                     double *J, double *dphi, double *dK, double *dD_O2, double *du_in);
 
 /* One transposed step at the current state s: given lam_next (host
  * [24][ny][nx], the adjoint of the state after one step), writes lam_prev =
  * (d step / d s)^T lam_next and the parameter gradients of
- * <lam_next, step(s)> (host, as in lbm_grad; NULL to skip). */
+ * <lam_next, step(s)> (host, as in lbm_grad; NULL to skip).  EINVAL for
+ * the pressure inlet (inlet_mode 1). */
 lbm_status lbm_vjp(lbm_domain *d, const double *lam_next, double *lam_prev, double *dphi,
                    double *dK, double *dD_O2, double *du_in);
 

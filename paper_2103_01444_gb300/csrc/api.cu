@@ -112,7 +112,9 @@ KArgs make_args(const lbm_domain *d) {
   a.s_nu = 1.0 / tau;
   a.s_q = 8.0 * (2.0 - 1.0 / tau) / (8.0 - 1.0 / tau);
   a.body_g = p.body_force_x;
-  a.u_in_avg = p.u_in_avg;
+  a.u_in_avg = p.inlet_mode == 0 ? p.u_in_avg : 0.0;
+  a.inlet_pressure = p.inlet_mode == 1;
+  a.dp_in = p.inlet_mode == 1 ? p.dp_in : 0.0;
   a.h_ch = d->ny - a.y_ch0;
   a.Q3 = 6.0 / (3.0 + 2.0 * std::sqrt(3.0));
   const double Cin[3] = {p.T_in, p.C_O2_in, p.C_H2O_in};
@@ -342,13 +344,15 @@ lbm_status lbm_destroy_domain(lbm_domain *d) {
 lbm_status lbm_set_params(lbm_domain *d, const lbm_params *p) {
   if (!d || !p) return fail(LBM_EINVAL, "null argument");
   if (!(p->nu > 0)) return fail(LBM_EINVAL, "nu must be > 0");
-  if (!(std::sqrt(3.0) * 1.5 * std::fabs(p->u_in_avg) < 0.3))
+  if (p->inlet_mode != 0 && p->inlet_mode != 1) return fail(LBM_EINVAL, "inlet_mode must be 0 or 1");
+  if (p->inlet_mode == 0 && !(std::sqrt(3.0) * 1.5 * std::fabs(p->u_in_avg) < 0.3))
     return fail(LBM_EINVAL, "inlet Mach number too high (u_in_avg = %g)", p->u_in_avg);
+  if (p->inlet_mode == 1 && !(std::fabs(p->dp_in) < 0.01))
+    return fail(LBM_EINVAL, "inlet pressure excess |dp_in| = %g not below 0.01", p->dp_in);
   if (!(p->T_in > 0) || !(p->dx_cm > 0) || !(p->dt_s > 0) || !(p->c_tot > 0) || !(p->rho_cp_f > 0) ||
       !(p->x_ref > 0) || !(p->R > 0) || !(p->F > 0) || !(p->T_ref_kin > 0) || !(p->aj0_ref >= 0))
     return fail(LBM_EINVAL, "non-positive physical constant");
   if (p->interface_mode != 0 && p->interface_mode != 1) return fail(LBM_EINVAL, "interface_mode must be 0 or 1");
-  if (p->reserved != 0) return fail(LBM_EINVAL, "reserved must be 0");
   const bool reprep = d->have_fields && (p->nu != d->prm.nu || p->forchheimer != d->prm.forchheimer ||
                                          p->interface_mode != d->prm.interface_mode);
   d->prm = *p;
@@ -927,6 +931,7 @@ lbm_status lbm_vjp(lbm_domain *d, const double *lam_next, double *lam_prev, doub
   lbm_status s = check_ready(d);
   if (s != LBM_OK) return s;
   if (!lam_next || !lam_prev) return fail(LBM_EINVAL, "null argument");
+  if (d->prm.inlet_mode != 0) return fail(LBM_EINVAL, "the adjoint needs the velocity inlet (inlet_mode 0)");
   AdjWork w;
   if ((s = w.alloc(d)) != LBM_OK) return s;
   if ((s = w.zero_grads(d)) != LBM_OK) return s;
@@ -943,6 +948,7 @@ lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t se
   lbm_status s = check_ready(d);
   if (s != LBM_OK) return s;
   if (objective != 0 && objective != 1) return fail(LBM_EINVAL, "objective must be 0 or 1");
+  if (d->prm.inlet_mode != 0) return fail(LBM_EINVAL, "the adjoint needs the velocity inlet (inlet_mode 0)");
   if (nsteps < 2 || nsteps > (1LL << 30)) return fail(LBM_EINVAL, "nsteps outside [2, 2^30]");
   const int64_t N = nsteps;
   const int seg = segment > 0 ? segment : (int)std::ceil(std::sqrt((double)N));

@@ -93,6 +93,8 @@ template <typename F> struct KArgsT {
   F s_nu, s_q;              // 1/tau and the q-moment rate of Sec. 2.1
   F body_g;                 // body force per unit mass along x
   F u_in_avg, h_ch;         // inlet parabola
+  int inlet_pressure;       // 1: pressure inlet (virtual column -1 at phi p = 1/3 + dp_in)
+  F dp_in;
   F Q3;                     // Eq. 10 rate of the energy moments
   F Cref[3], wr0[3], wr1[3], bref[3];  // deviation references
   F Cin[3], Ctop[3];
@@ -109,6 +111,7 @@ template <typename F> __host__ __device__ inline KArgsT<F> narrow_args(const KAr
   r.mode = a.mode; r.ny_cl = a.ny_cl; r.y_ch0 = a.y_ch0; r.top_dirichlet = a.top_dirichlet;
   r.s_nu = F(a.s_nu); r.s_q = F(a.s_q); r.body_g = F(a.body_g); r.u_in_avg = F(a.u_in_avg);
   r.h_ch = F(a.h_ch); r.Q3 = F(a.Q3);
+  r.inlet_pressure = a.inlet_pressure; r.dp_in = F(a.dp_in);
   for (int s = 0; s < 3; ++s) {
     r.Cref[s] = F(a.Cref[s]); r.wr0[s] = F(a.wr0[s]); r.wr1[s] = F(a.wr1[s]);
     r.bref[s] = F(a.bref[s]); r.Cin[s] = F(a.Cin[s]); r.Ctop[s] = F(a.Ctop[s]);
@@ -180,6 +183,21 @@ __device__ R pull_flow_edge(const Pops<S, CG> &src, const KArgsT<R> &a, const ui
     if (a.periodic) {
       sx = sx < 0 ? sx + a.nx : sx - a.nx;
     } else if (sx < 0) {                                              // inlet
+      if (a.inlet_pressure && (m & M_INLET)) {
+        // pressure inlet: the virtual column -1 repeats column 0 with its
+        // equilibrium pressure part moved to phi p = 1/3 + dp_in; a source
+        // row outside the channel is the GDL's end wall
+        if (!(mask[(long long)sy * a.nxp] & M_INLET)) return R(src.at(OP[i], x, y));
+        R d[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) d[k] = R(src.at(k, 0, sy));
+        R jx = d[1] - d[3] + d[5] - d[6] - d[7] + d[8];
+        R jy = d[2] - d[4] + d[5] + d[6] - d[7] - d[8];
+        R s18 = ((d[1] + d[3]) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8]));
+        R inv_phi = pal[mid[(long long)sy * a.nxp]].inv_phi;
+        R dP = R(a.dp_in) + (R(-0.6) * s18 + R(0.4) * (jx * jx + jy * jy) * inv_phi);
+        return d[i] + lam9<R>(i) * dP;
+      }
       R w = R(src.at(OP[i], x, y));
       if (m & M_INLET) w += R(6) * w9<R>(i) * R(EX[i]) * inlet_u<R>(a, R(y) - R(0.5) * R(EY[i]));
       return w;

@@ -74,7 +74,11 @@ def cathode_params(case: dict, forchheimer: int = 1, interface_mode: int = 0):
         alpha_c=PAPER["alpha_c"], F=PAPER["F"], R=PAPER["R"], dU0dT=PAPER["dU0dT"],
         U0_0=PAPER["U0_0"], x_ref=L["x_ref"], dx_cm=dx, dt_s=dt, delta_cl_cm=L["delta_cl_cm"],
         c_tot=c_tot, rho_cp_f=L["gas_cp_J_molK"] * c_tot, forchheimer=forchheimer,
-        top_dirichlet=0, interface_mode=interface_mode, reserved=0,
+        top_dirichlet=0, interface_mode=interface_mode,
+        # the drive: inlet velocity at Re (default) or the pressure difference
+        # of Sec. 4 (case["inlet"] == "pressure", excess dp_in in lattice units)
+        inlet_mode=1 if case.get("inlet") == "pressure" else 0,
+        dp_in=float(case.get("dp_in", 0.0)),
     )
     geometry = dict(nx=nx, ny=ny, ny_cl=ny_cl, ny_gdl=ny_gdl,
                     reaction_mode=int(case["reaction_mode"]),

@@ -109,6 +109,44 @@ def test_fp64_state_matches_oracle(name, steps, mode):
     np.testing.assert_allclose(prof_g, prof_o, rtol=1e-6)
 
 
+@pytest.mark.parametrize("name", ["film-64x16", "vol-77x20", "grains-70x24"])
+def test_fp64_pressure_inlet_matches_oracle(name):
+    """The pressure-driven inlet of Sec. 4 (virtual column -1 at phi p =
+    1/3 + dp_in): every population agrees with the oracle to round-off, and
+    FP32 storage stays within 1e-5 on the flow."""
+    case = dict(CASES[name](), inlet="pressure", dp_in=1e-3, V_op=0.4)
+    o = oracle_of(case)
+    o.step(300)
+    live = (o.mask & 3) != 3
+    ref = oracle_state(o)
+    d = gpu_domain(case, "fp64")
+    d.step(300)
+    st = d.state()
+    for q in range(24):
+        scale = np.abs(ref[q][live]).max()
+        np.testing.assert_allclose(st[q][live], ref[q][live], rtol=0, atol=1e-11 * scale,
+                                   err_msg=f"population plane {q}")
+    fo = o.fields()
+    assert np.abs(fo["ux"][live]).max() > 1e-4          # the pressure drives a flow
+    i_g, _, _ = d.current_density()
+    assert i_g == pytest.approx(o.current_density()[0], rel=1e-11)
+    d32 = gpu_domain(case, "fp32")
+    d32.step(300)
+    f32 = d32.fields()
+    u32 = np.stack([f32["ux"], f32["uy"]])
+    uo = np.stack([fo["ux"], fo["uy"]])
+    assert rel_l2(u32, uo, np.stack([live, live])) < 1e-5
+
+
+def test_adjoint_refuses_the_pressure_inlet():
+    from paper_2103_01444_gb300.lbm import LbmError
+    case = dict(CASES["film-64x16"](), inlet="pressure", dp_in=1e-3)
+    d = gpu_domain(case, "fp64")
+    d.step(2)
+    with pytest.raises(LbmError, match="EINVAL.*velocity inlet"):
+        d.grad(0, 4)
+
+
 @pytest.fixture(scope="module")
 def cathode_200x40_oracles():
     case = workloads.cathode_200x40()
