@@ -45,6 +45,10 @@
  *     Water gets +2J (Eq. 12); temperature gets the heat of Eq. 15.
  *   - Volumetric catalyst rows: backward-Euler sink S = -k_v C/(1 + k_v),
  *     added after collision as w_i(b) S.
+ *   - Butler-Volmer (alpha_a > 0): an anodic branch aj0(T) exp(alpha_a F
+ *     eta/(RT)) at unit reactant activity is subtracted from the O2 flux,
+ *     J = k C_w - k_a; the implicit link becomes g_up = (g_down* (1 - kappa)
+ *     + k_a)/(1 + kappa), the sink S = (k_va - k_v C)/(1 + k_v).
  *   - k(T), C and T in the reaction terms use the cell's previous
  *     post-collision sums (C^n = sum g*(x)).
  *   - Eq. 10 with a per-cell b and fixed Q (the default) diffuses alpha C,
@@ -169,6 +173,8 @@ typedef struct {
   double x_ref;             /* reference O2 mole fraction (C_O2,ref) */
   double dx_cm, dt_s, delta_cl_cm, c_tot, rho_cp_f;
   double dp_in;             /* pressure inlet: phi p there is rho0/3 + dp_in */
+  double alpha_a;           /* anodic transfer coefficient of the Butler-Volmer
+                               branch; 0 = Tafel kinetics, Eq. 13 as printed */
 } orc_params;
 
 /* Per-cell material, lattice units. K = +inf marks clear fluid.  sigma is
@@ -239,6 +245,14 @@ double orc_tafel_j(const orc_params *P, double x, double T) {
   return -orc_aj0(P, T) * (x / P->x_ref) *
          exp(-P->alpha_c * P->F / (P->R * T) * orc_eta(P, T));
 }
+/* Anodic branch of Butler-Volmer kinetics, the reverse of Eq. 12 (water
+ * oxidation), taken at unit reactant activity: aj0(T) exp(alpha_a F eta/(RT))
+ * in A/cm^3; zero when alpha_a = 0 (Tafel, Eq. 13 alone).  The full current
+ * is j = orc_tafel_j + orc_anodic_j. */
+double orc_anodic_j(const orc_params *P, double T) {
+  if (P->alpha_a == 0.0) return 0.0;
+  return orc_aj0(P, T) * exp(P->alpha_a * P->F / (P->R * T) * orc_eta(P, T));
+}
 /* Eq. 15: heat per unit volume (W/cm^3) released by current j at T. */
 double orc_heat_Q(const orc_params *P, double j, double T) {
   return -j * (orc_eta(P, T) + T * P->dU0dT);
@@ -255,6 +269,14 @@ static double k_surface(const orc_params *P, double T) {
 static double k_volume(const orc_params *P, double T) {
   double j1 = -orc_tafel_j(P, P->x_ref, T) / P->x_ref;
   return j1 / (4.0 * P->F * P->c_tot) * P->dt_s;
+}
+/* The anodic branch as O2 mole fraction produced per step: through one
+ * wall link of the thin film, and per cell of the volumetric catalyst. */
+static double k_surface_anodic(const orc_params *P, double T) {
+  return orc_anodic_j(P, T) * P->delta_cl_cm / (4.0 * P->F * P->c_tot) * P->dt_s / P->dx_cm;
+}
+static double k_volume_anodic(const orc_params *P, double T) {
+  return orc_anodic_j(P, T) / (4.0 * P->F * P->c_tot) * P->dt_s;
 }
 /* Temperature rise (K) per unit of O2 mole fraction consumed, Eq. 15 with
  * j = -4 F c_tot (consumed flux). */
@@ -542,11 +564,11 @@ static void stream(const orc_params *P, const orc_material *mat, const uint8_t *
       }
 
       /* ---- reaction rate at this cell (uses T^n and C^n) */
-      double kS = 0, kV = 0;
+      double kS = 0, kV = 0, kSa = 0, kVa = 0;
       int surface = (P->reaction_mode == 0) && (m & B_YLO);
       int volume = (P->reaction_mode == 1) && ((m & 3) == REG_CATALYST);
-      if (surface) kS = k_surface(P, Cn[0]);
-      if (volume) kV = k_volume(P, Cn[0]);
+      if (surface) { kS = k_surface(P, Cn[0]); kSa = k_surface_anodic(P, Cn[0]); }
+      if (volume) { kV = k_volume(P, Cn[0]); kVa = k_volume_anodic(P, Cn[0]); }
       double hpo = (surface || volume) ? heat_per_O2(P, Cn[0]) : 0.0;   /* gas K per O2 */
       double sig = mat->sigma ? mat->sigma[c] : 1.0;
 
@@ -562,8 +584,10 @@ static void stream(const orc_params *P, const orc_material *mat, const uint8_t *
           if (sy < 0) {
             if (surface) {
               if (s == 1) {
+                /* net O2 flux J = kS C_w - kSa with the wall value
+                 * C_w = (own_out + val)/(2 w1) and J = own_out - val */
                 double kappa = kS / (2.0 * w1);
-                val = own_out * (1.0 - kappa) / (1.0 + kappa);
+                val = (own_out * (1.0 - kappa) + kSa) / (1.0 + kappa);
                 Jsurf = own_out - val;
               } else {
                 val = own_out; /* completed after O2 below */
@@ -615,7 +639,8 @@ static void stream(const orc_params *P, const orc_material *mat, const uint8_t *
         if (qx) qx[x] += hpo * Jsurf;
       }
       if (volume) {
-        double S = -kV * Cn[1] / (1.0 + kV);
+        /* backward Euler for dC/dt = kVa - kV C */
+        double S = (kVa - kV * Cn[1]) / (1.0 + kV);
         src[0 * n + c] = -S * hpo / sig;
         src[1 * n + c] = S;
         src[2 * n + c] = -2.0 * S;
@@ -808,6 +833,8 @@ void orc_d2q5_eq(double C, double ux, double uy, double b, double *geq) {
 double orc_k_surface(const orc_params *P, double T) { return k_surface(P, T); }
 double orc_k_volume(const orc_params *P, double T) { return k_volume(P, T); }
 double orc_heat_per_O2(const orc_params *P, double T) { return heat_per_O2(P, T); }
+double orc_k_surface_anodic(const orc_params *P, double T) { return k_surface_anodic(P, T); }
+double orc_k_volume_anodic(const orc_params *P, double T) { return k_volume_anodic(P, T); }
 void orc_porous(const orc_params *P, double phi, double K, double *out5) {
   porous_coef c = porous(P, phi, K);
   out5[0] = c.phi; out5[1] = c.darcy; out5[2] = c.forch; out5[3] = c.l0; out5[4] = c.l1;

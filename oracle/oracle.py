@@ -49,6 +49,7 @@ class Params(C.Structure):
         ("dU0dT", C.c_double), ("U0_0", C.c_double), ("x_ref", C.c_double),
         ("dx_cm", C.c_double), ("dt_s", C.c_double), ("delta_cl_cm", C.c_double),
         ("c_tot", C.c_double), ("rho_cp_f", C.c_double), ("dp_in", C.c_double),
+        ("alpha_a", C.c_double),
     ]
 
 
@@ -81,7 +82,8 @@ def lib():
             L.orc_velocity.argtypes = [C.c_double] * 4 + [_d, _d]
             L.orc_porous.argtypes = [_P(Params), C.c_double, C.c_double, _d]
             for name in ("orc_U0", "orc_eta", "orc_aj0", "orc_k_surface", "orc_k_volume",
-                         "orc_heat_per_O2"):
+                         "orc_heat_per_O2", "orc_k_surface_anodic", "orc_k_volume_anodic",
+                         "orc_anodic_j"):
                 getattr(L, name).argtypes = [_P(Params), C.c_double]
                 getattr(L, name).restype = C.c_double
             L.orc_tafel_j.argtypes = [_P(Params), C.c_double, C.c_double]

@@ -98,6 +98,9 @@ def lattice_problem(case: dict, forchheimer: int = 1, interface_mode: int = 0):
         # the inlet, 1/3 at the outlet, dp_in in lattice units
         inlet_mode=1 if case.get("inlet") == "pressure" else 0,
         dp_in=float(case.get("dp_in", 0.0)),
+        # kinetics: Tafel (Eq. 13) unless the case gives an anodic transfer
+        # coefficient for the Butler-Volmer branch
+        alpha_a=float(case.get("alpha_a", 0.0)),
     )
     return params, material, case.get("solid")
 
@@ -110,7 +113,7 @@ def base_params(nx, ny, **kw):
              C_H2O_top=0.0, aj0_ref=0.0, T_ref_kin=T_REF_KIN, E_act=E_ACT, alpha_c=ALPHA_C,
              F=FARADAY, R=R_GAS, dU0dT=DU0_DT, U0_0=U0_0, x_ref=X_REF, dx_cm=1e-3,
              dt_s=1e-6, delta_cl_cm=DELTA_CL_CM, c_tot=C_TOT, rho_cp_f=RHO_CP_F,
-             inlet_mode=0, dp_in=0.0)
+             inlet_mode=0, dp_in=0.0, alpha_a=0.0)
     p.update(kw)
     return p
 

@@ -415,16 +415,83 @@ def test_volumetric_reaction_cosh_profile(oracle_lib):
     assert 3.5 < e16 / e32 < 4.5
 
 
+def bv_box(mode, oracle_lib, k_target, nx=4, ny=8, alpha_a=0.5):
+    """Closed periodic box at rest, insulated walls, no heat (rho_cp_f huge)
+    and no Arrhenius factor: the temperature stays at T_in, eta = -0.02 V.
+    The time step is scaled so that the cathodic lattice rate is k_target."""
+    p = base_params(nx, ny, reaction_mode=mode, ny_cl=ny if mode else 0, V_op=0.98,
+                    U0_0=1.0, dU0dT=0.0, E_act=0.0, aj0_ref=1e-4, alpha_a=alpha_a,
+                    rho_cp_f=1e30)
+    rate = oracle_lib.orc_k_volume if mode else oracle_lib.orc_k_surface
+    k0 = rate(ctypes.byref(Oracle(p, uniform_material(nx, ny)).P), p["T_in"])
+    p["dt_s"] *= k_target / k0
+    return p
+
+
+def nernst_equilibrium(p):
+    """O2 mole fraction at which the Butler-Volmer current is zero:
+    (C/C_ref) exp(-alpha_c F eta/RT) = exp(alpha_a F eta/RT)."""
+    eta = p["V_op"] - (p["dU0dT"] * p["T_in"] + p["U0_0"])
+    return p["x_ref"] * math.exp((p["alpha_a"] + p["alpha_c"]) * p["F"] * eta /
+                                 (p["R"] * p["T_in"]))
+
+
+def test_butler_volmer_volumetric_relaxation_exact(oracle_lib):
+    """Butler-Volmer kinetics in a uniform catalyst box: each cell's sink is
+    the backward Euler step of dC/dt = k_a - k_v C, so C_n = C* + (C_0 - C*)
+    (1 + k_v)^-n exactly, and C* = k_a/k_v is the mole fraction at which the
+    current of the two branches cancels."""
+    p = bv_box(1, oracle_lib, 0.05)
+    o = Oracle(p, uniform_material(4, 8, D_O2=0.05))
+    kv = oracle_lib.orc_k_volume(ctypes.byref(o.P), p["T_in"])   # T stays T_in
+    ka = oracle_lib.orc_k_volume_anodic(ctypes.byref(o.P), p["T_in"])
+    Cs = nernst_equilibrium(p)
+    assert ka / kv == pytest.approx(Cs, rel=1e-13)
+    assert 0.01 < kv < 1 and 0.02 < Cs < 0.2
+    C0 = p["C_O2_in"]
+    o2 = Oracle(p, uniform_material(4, 8, D_O2=0.05))
+    done = 0
+    for n in (1, 7, 40):
+        o2.step(n - done)
+        done = n
+        C = o2.g[1].sum(axis=0)        # after n sink steps (post-collision state)
+        np.testing.assert_allclose(C, Cs + (C0 - Cs) * (1 + kv) ** -n, rtol=1e-13)
+    # two H2O per O2 (Eq. 12) in both directions of the reaction
+    np.testing.assert_allclose(o2.g[2].sum(axis=0), p["C_H2O_in"] + 2 * (C0 - C), atol=1e-14)
+
+
+def test_butler_volmer_thin_film_equilibrium(oracle_lib):
+    """Butler-Volmer at the reacting bottom wall of a closed box: the O2
+    field relaxes to the uniform mole fraction at which the net wall current
+    is zero."""
+    p = bv_box(0, oracle_lib, 0.01)
+    o = Oracle(p, uniform_material(4, 8, D_O2=0.05))
+    o.step(40000)
+    np.testing.assert_allclose(o.fields()["C_O2"], nernst_equilibrium(p), rtol=1e-10)
+
+
+def test_butler_volmer_off_is_tafel():
+    """alpha_a = 0 removes the anodic branch: Eq. 13 as printed."""
+    case = workloads.small_cathode(nx=30, ny=12, reaction_mode=0, V_op=0.45)
+    p, m, s = lattice_problem(case)
+    a = Oracle(p, m, s).step(50)
+    b = Oracle(dict(p, alpha_a=0.0), m, s).step(50)
+    np.testing.assert_array_equal(a.g, b.g)
+    c = Oracle(dict(p, alpha_a=0.5), m, s).step(50)
+    assert np.abs(c.g - a.g).max() > 0
+
+
 # --------------------------------------------------------------- balances
 
+@pytest.mark.parametrize("alpha_a", [0.0, 0.5])
 @pytest.mark.parametrize("mode", [0, 1])
-def test_closed_box_stoichiometric_and_energy_invariants(mode, oracle_lib):
+def test_closed_box_stoichiometric_and_energy_invariants(mode, alpha_a, oracle_lib):
     """Periodic x, insulated walls, reaction on: every O2 consumed makes two
     H2O (Eq. 12) and releases Eq. 15's heat, so sum(C_H2O + 2 C_O2) and
     sum(T + h C_O2) stay constant, and so does the flow mass."""
     nx, ny = 12, 10
     p = base_params(nx, ny, reaction_mode=mode, ny_cl=3 if mode else 0, V_op=0.5,
-                    aj0_ref=1e-4, dt_s=2e-5, dx_cm=2e-3, body_force_x=1e-5)
+                    aj0_ref=1e-4, dt_s=2e-5, dx_cm=2e-3, body_force_x=1e-5, alpha_a=alpha_a)
     o = Oracle(p, uniform_material(nx, ny, phi=0.6, K=1.0, D_O2=0.03, D_H2O=0.04,
                                    alpha_T=0.02))
     h = oracle_lib.orc_heat_per_O2(ctypes.byref(o.P), 343.0)
