@@ -101,6 +101,10 @@ typedef struct {
                                   need inlet_mode 0 (EINVAL otherwise). */
   double dp_in;                /* inlet pressure excess of inlet_mode 1, lattice units,
                                   |dp_in| < 0.01 */
+  double alpha_a;              /* kinetics: 0 Tafel, Eq. 13 as printed; > 0 (at most 4)
+                                  Butler-Volmer, with the anodic branch
+                                  aj0(T) exp(alpha_a F eta/(R T)) at unit reactant
+                                  activity subtracted from the O2 consumption */
 } lbm_params;
 
 typedef struct lbm_domain lbm_domain; /* opaque */
@@ -117,7 +121,7 @@ lbm_status lbm_destroy_domain(lbm_domain *d);
 
 /* Copies the operating point (Sec. 4-5).  EINVAL unless nu > 0,
  * sqrt(3) * 1.5 * u_in_avg < 0.3 (inlet_mode 0), |dp_in| < 0.01 (inlet_mode
- * 1), T_in > 0, dx_cm > 0, dt_s > 0. */
+ * 1), 0 <= alpha_a <= 4, T_in > 0, dx_cm > 0, dt_s > 0. */
 lbm_status lbm_set_params(lbm_domain *d, const lbm_params *p);
 
 /* Per-cell material, host arrays [ny][nx] of doubles, lattice units:

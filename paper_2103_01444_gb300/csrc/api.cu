@@ -139,6 +139,19 @@ KArgs make_args(const lbm_domain *d) {
   const double c1 = -p.E_act + p.alpha_c * p.F * (p.U0_0 - p.V_op) / p.R;
   a.k_ein = c0 + c1 / p.T_in;
   a.k_c1 = c1;
+  // Butler-Volmer anodic branch (zero in the Tafel case): the O2 produced
+  // per step, k_a(T) = A x_ref exp(e_in_a - c1_a (T - T_in)/(T T_in)) with
+  //   c0_a = E/T_ref - alpha_a F dU0dT / R,  c1_a = -E + alpha_a F (V - U0_0)/R.
+  if (p.alpha_a > 0.0) {
+    const double c0a = p.E_act / p.T_ref_kin - p.alpha_a * p.F * p.dU0dT / p.R;
+    const double c1a = -p.E_act + p.alpha_a * p.F * (p.V_op - p.U0_0) / p.R;
+    a.kA_surf_a = a.kA_surf * p.x_ref;
+    a.kA_vol_a = a.kA_vol * p.x_ref;
+    a.k_ein_a = c0a + c1a / p.T_in;
+    a.k_c1_a = c1a;
+  } else {
+    a.kA_surf_a = a.kA_vol_a = a.k_ein_a = a.k_c1_a = 0.0;
+  }
   a.T_in = p.T_in;
   a.theta0 = d->Cref[0] - p.T_in;
   // Eq. 15 with Eq. 16: eta + T dU0/dT = V - U0_0, so the heat per O2
@@ -347,6 +360,8 @@ lbm_status lbm_set_params(lbm_domain *d, const lbm_params *p) {
   if (p->inlet_mode != 0 && p->inlet_mode != 1) return fail(LBM_EINVAL, "inlet_mode must be 0 or 1");
   if (p->inlet_mode == 0 && !(std::sqrt(3.0) * 1.5 * std::fabs(p->u_in_avg) < 0.3))
     return fail(LBM_EINVAL, "inlet Mach number too high (u_in_avg = %g)", p->u_in_avg);
+  if (!(p->alpha_a >= 0.0 && p->alpha_a <= 4.0))
+    return fail(LBM_EINVAL, "anodic transfer coefficient alpha_a = %g outside [0, 4]", p->alpha_a);
   if (p->inlet_mode == 1 && !(std::fabs(p->dp_in) < 0.01))
     return fail(LBM_EINVAL, "inlet pressure excess |dp_in| = %g not below 0.01", p->dp_in);
   if (!(p->T_in > 0) || !(p->dx_cm > 0) || !(p->dt_s > 0) || !(p->c_tot > 0) || !(p->rho_cp_f > 0) ||

@@ -240,6 +240,12 @@ template <typename R> __device__ __forceinline__ R drate_dtheta(const KArgsT<R> 
   const R T = R(a.T_in) + theta;
   return -R(a.k_c1) * k / (T * T);
 }
+// The same for the Butler-Volmer anodic rate k_a (constant c1_a; 0 when k_a = 0).
+template <typename R>
+__device__ __forceinline__ R drate_anodic_dtheta(const KArgsT<R> &a, R ka, R theta) {
+  const R T = R(a.T_in) + theta;
+  return -R(a.k_c1_a) * ka / (T * T);
+}
 
 // Parameter chain of one cell: adjoints of the derived coefficients to the
 // caller's fields phi, K and D_O2 (Eq. 7, 8, 10), in the arithmetic type,
@@ -421,12 +427,13 @@ __device__ __forceinline__ void adj_interior_cell(
     return v;
   };
   // forward reaction terms (kept for the reverse)
-  R theta = 0, k = 0, Cv = 0, S_vol = 0;
+  R theta = 0, k = 0, ka = 0, Cv = 0, S_vol = 0;
   if (vol) {
     theta = own_sum<S, R>(src, 0, x, y) + a.theta0;
     Cv = own_sum<S, R>(src, 1, x, y) + R(a.Cref[1]);
     k = rate<R>(a, R(a.kA_vol), theta);
-    S_vol = -k * Cv / (R(1) + k);
+    ka = rate_anodic<R>(a, R(a.kA_vol_a), theta);
+    S_vol = (ka - k * Cv) / (R(1) + k);
   }
   // ---- reverse of the collisions; every link is plain, so each link's
   // adjoint is pushed to its source as soon as it is known
@@ -463,8 +470,10 @@ __device__ __forceinline__ void adj_interior_cell(
   // volumetric sources (-S h / sigma, S, -2 S): own-use adjoints of theta, C_O2
   if (vol) {
     const R lS = -R(a.hpo) * mc.inv_sigma * lsrc[0] + lsrc[1] - R(2) * lsrc[2];
+    // S = (k_a - k C)/(1 + k): dS/dC, dS/dk and dS/dk_a, with k and k_a of theta
     const R lC_own = lS * (-k / (R(1) + k));
-    const R lth_own = lS * (-Cv / ((R(1) + k) * (R(1) + k))) * drate_dtheta<R>(a, k, theta);
+    const R lth_own = lS * (-(Cv + ka) / ((R(1) + k) * (R(1) + k))) * drate_dtheta<R>(a, k, theta) +
+                      lS / (R(1) + k) * drate_anodic_dtheta<R>(a, ka, theta);
 #pragma unroll
     for (int q = 0; q < 24; ++q)
       B.O[q * P + c] = q >= 9 && q < 14 ? lth_own : (q >= 14 && q < 19 ? lC_own : R(0));
@@ -575,13 +584,14 @@ k_adj_edge(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
       for (int i = 0; i < 5; ++i) cell.g[s][i] = sh.pulled[9 + 5 * s + i];
     const bool surf = a.mode == 0 && (m & M_YLO);
     const bool vol = a.mode == 1 && (m & REG_MASK) == REG_CATALYST;
-    R theta = 0, k = 0, kappa = 0, gd = 0, Cv = 0, S_vol = 0;
+    R theta = 0, k = 0, ka = 0, kappa = 0, gd = 0, Cv = 0, S_vol = 0;
     if (surf || vol) theta = own_sum<S, R>(src, 0, x, y) + a.theta0;
     if (surf) {
       k = rate<R>(a, R(a.kA_surf), theta);
+      ka = rate_anodic<R>(a, R(a.kA_surf_a), theta);
       kappa = k / (R(2) * mc.w1[1]);
       gd = cell.g[1][2] + R(a.wr1[1]) * R(a.Cref[1]);
-      const R Jv = gd * (R(2) * kappa) / (R(1) + kappa);
+      const R Jv = (gd * (R(2) * kappa) - ka) / (R(1) + kappa);
       cell.g[1][2] -= Jv;
       cell.g[0][2] += R(a.hpo) * mc.inv_sigma * Jv;
       cell.g[2][2] += R(2) * Jv;
@@ -589,7 +599,8 @@ k_adj_edge(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
     if (vol) {
       Cv = own_sum<S, R>(src, 1, x, y) + R(a.Cref[1]);
       k = rate<R>(a, R(a.kA_vol), theta);
-      S_vol = -k * Cv / (R(1) + k);
+      ka = rate_anodic<R>(a, R(a.kA_vol_a), theta);
+      S_vol = (ka - k * Cv) / (R(1) + k);
     }
     R lcf[9], lcg[3][5];
 #pragma unroll
@@ -618,7 +629,9 @@ k_adj_edge(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
     if (vol) {   // volumetric sources (-S h / sigma, S, -2 S)
       const R lS = -R(a.hpo) * mc.inv_sigma * lsrc[0] + lsrc[1] - R(2) * lsrc[2];
       const R lC_own = lS * (-k / (R(1) + k));
-      const R lth_own = lS * (-Cv / ((R(1) + k) * (R(1) + k))) * drate_dtheta<R>(a, k, theta);
+      const R lth_own =
+          lS * (-(Cv + ka) / ((R(1) + k) * (R(1) + k))) * drate_dtheta<R>(a, k, theta) +
+          lS / (R(1) + k) * drate_anodic_dtheta<R>(a, ka, theta);
 #pragma unroll
       for (int q = 0; q < 5; ++q) {
         sh.O[9 + q] += lth_own;
@@ -631,11 +644,13 @@ k_adj_edge(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
     }
     if (surf) {   // reverse of the surface reaction (post -> pre link values)
       const R lJ = -lcg[1][2] + R(a.hpo) * mc.inv_sigma * lcg[0][2] + R(2) * lcg[2][2];
+      // J = (2 kappa g_d - k_a)/(1 + kappa)
       const R lgd = lJ * R(2) * kappa / (R(1) + kappa);
-      const R lkap = lJ * R(2) * gd / ((R(1) + kappa) * (R(1) + kappa));
+      const R lkap = lJ * (R(2) * gd + ka) / ((R(1) + kappa) * (R(1) + kappa));
       const R lk = lkap / (R(2) * mc.w1[1]);
       lw1[1] += -lkap * k / (R(2) * mc.w1[1] * mc.w1[1]);
-      const R lth = lk * drate_dtheta<R>(a, k, theta);
+      const R lth = lk * drate_dtheta<R>(a, k, theta) +
+                    (-lJ / (R(1) + kappa)) * drate_anodic_dtheta<R>(a, ka, theta);
 #pragma unroll
       for (int q = 0; q < 5; ++q) sh.O[9 + q] += lth;
       lcg[1][2] += lgd;
@@ -758,10 +773,12 @@ k_adj_seed_current(const S *__restrict__ src_p, const uint8_t *__restrict__ mask
     if (a.mode == 0 && (m & M_YLO)) {
       const R theta = own_sum<S, R>(src, 0, x, y) + a.theta0;
       const R k = rate<R>(a, R(a.kA_surf), theta);
+      const R ka = rate_anodic<R>(a, R(a.kA_surf_a), theta);
       const R kappa = k / (R(2) * mc.w1[1]);
       const R gd = R(src.at(9 + 5 + 4, x, y)) + R(a.wr1[1]) * R(a.Cref[1]);
-      const R lkap = w * R(2) * gd / ((R(1) + kappa) * (R(1) + kappa));
-      const R lth = lkap / (R(2) * mc.w1[1]) * drate_dtheta<R>(a, k, theta);
+      const R lkap = w * (R(2) * gd + ka) / ((R(1) + kappa) * (R(1) + kappa));
+      const R lth = lkap / (R(2) * mc.w1[1]) * drate_dtheta<R>(a, k, theta) +
+                    (-w / (R(1) + kappa)) * drate_anodic_dtheta<R>(a, ka, theta);
 #pragma unroll
       for (int q = 0; q < 5; ++q) l[9 + q] += lth;
       l[18] += w * R(2) * kappa / (R(1) + kappa);
@@ -773,9 +790,11 @@ k_adj_seed_current(const S *__restrict__ src_p, const uint8_t *__restrict__ mask
       const R theta = own_sum<S, R>(src, 0, x, y) + a.theta0;
       const R Cv = own_sum<S, R>(src, 1, x, y) + R(a.Cref[1]);
       const R k = rate<R>(a, R(a.kA_vol), theta);
+      const R ka = rate_anodic<R>(a, R(a.kA_vol_a), theta);
       const R lS = -w;   // i_avg = sum(-S) weight
       const R lC = lS * (-k / (R(1) + k));
-      const R lth = lS * (-Cv / ((R(1) + k) * (R(1) + k))) * drate_dtheta<R>(a, k, theta);
+      const R lth = lS * (-(Cv + ka) / ((R(1) + k) * (R(1) + k))) * drate_dtheta<R>(a, k, theta) +
+                    lS / (R(1) + k) * drate_anodic_dtheta<R>(a, ka, theta);
 #pragma unroll
       for (int q = 0; q < 5; ++q) {
         l[9 + q] += lth;

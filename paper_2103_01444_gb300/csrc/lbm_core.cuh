@@ -100,6 +100,8 @@ template <typename F> struct KArgsT {
   F Cin[3], Ctop[3];
   // kinetics: k(T) = A exp(e_in - c1 (T - T_in)/(T T_in)), Eq. 13, 14, 16, 17
   F kA_surf, kA_vol, k_ein, k_c1, T_in;
+  // Butler-Volmer anodic branch, same form (all zero for Tafel kinetics)
+  F kA_surf_a, kA_vol_a, k_ein_a, k_c1_a;
   F theta0;                 // Cref_T - T_in
   F hpo;                    // temperature per unit O2 consumed (Eq. 15, 16)
 };
@@ -118,6 +120,8 @@ template <typename F> __host__ __device__ inline KArgsT<F> narrow_args(const KAr
   }
   r.kA_surf = F(a.kA_surf); r.kA_vol = F(a.kA_vol); r.k_ein = F(a.k_ein); r.k_c1 = F(a.k_c1);
   r.T_in = F(a.T_in); r.theta0 = F(a.theta0); r.hpo = F(a.hpo);
+  r.kA_surf_a = F(a.kA_surf_a); r.kA_vol_a = F(a.kA_vol_a);
+  r.k_ein_a = F(a.k_ein_a); r.k_c1_a = F(a.k_c1_a);
   return r;
 }
 
@@ -268,6 +272,13 @@ template <typename R> __device__ __forceinline__ R rate(const KArgsT<R> &a, R A,
   R T = R(a.T_in) + theta;
   return A * exp(R(a.k_ein) - R(a.k_c1) * theta / (T * R(a.T_in)));
 }
+// Butler-Volmer anodic branch: O2 produced per step (link or cell); 0 for
+// Tafel kinetics (A = 0), without evaluating the exponential.
+template <typename R> __device__ __forceinline__ R rate_anodic(const KArgsT<R> &a, R A, R theta) {
+  if (A == R(0)) return R(0);
+  R T = R(a.T_in) + theta;
+  return A * exp(R(a.k_ein_a) - R(a.k_c1_a) * theta / (T * R(a.T_in)));
+}
 
 // Sum of the cell's own post-collision deviations of scalar s.
 // Opposite links are summed first: their large advective parts cancel
@@ -294,7 +305,9 @@ __device__ __forceinline__ R surface_reaction(const Pops<S, CG> &src, const KArg
   R k = rate<R>(a, R(a.kA_surf), theta);
   R kappa = k / (R(2) * mc.w1[1]);
   R gdown = c.g[1][2] + R(a.wr1[1]) * R(a.Cref[1]);   // full g*_4 of O2 (bounced)
-  R J = gdown * (R(2) * kappa) / (R(1) + kappa);
+  // J = k C_w - k_a with C_w = (g_down + g_up)/(2 w1), solved for g_up
+  R ka = rate_anodic<R>(a, R(a.kA_surf_a), theta);
+  R J = (gdown * (R(2) * kappa) - ka) / (R(1) + kappa);
   c.g[1][2] -= J;
   c.g[0][2] += R(a.hpo) * mc.inv_sigma * J;
   c.g[2][2] += R(2) * J;
@@ -307,7 +320,8 @@ __device__ __forceinline__ R volume_sink(const Pops<S, CG> &src, const KArgsT<R>
   R theta = own_sum<S, R, CG>(src, 0, x, y) + a.theta0;
   R C = own_sum<S, R, CG>(src, 1, x, y) + R(a.Cref[1]);
   R k = rate<R>(a, R(a.kA_vol), theta);
-  return -k * C / (R(1) + k);
+  R ka = rate_anodic<R>(a, R(a.kA_vol_a), theta);
+  return (ka - k * C) / (R(1) + k);   // backward Euler of dC/dt = k_a - k C
 }
 
 // The 24 interior pulls of cell (x, y), issued without looking at the mask.

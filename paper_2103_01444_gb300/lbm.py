@@ -51,7 +51,8 @@ _PARAM_DOUBLES = ("nu", "u_in_avg", "body_force_x", "V_op", "T_in", "C_O2_in", "
 class lbm_params(C.Structure):
     _fields_ = [(k, C.c_double) for k in _PARAM_DOUBLES] + [
         ("forchheimer", C.c_int32), ("top_dirichlet", C.c_int32),
-        ("interface_mode", C.c_int32), ("inlet_mode", C.c_int32), ("dp_in", C.c_double)]
+        ("interface_mode", C.c_int32), ("inlet_mode", C.c_int32), ("dp_in", C.c_double),
+        ("alpha_a", C.c_double)]
 
 
 _lib = None

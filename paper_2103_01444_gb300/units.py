@@ -79,6 +79,9 @@ def cathode_params(case: dict, forchheimer: int = 1, interface_mode: int = 0):
         # of Sec. 4 (case["inlet"] == "pressure", excess dp_in in lattice units)
         inlet_mode=1 if case.get("inlet") == "pressure" else 0,
         dp_in=float(case.get("dp_in", 0.0)),
+        # kinetics: Tafel (Eq. 13) unless an anodic transfer coefficient is
+        # given for the Butler-Volmer branch
+        alpha_a=float(case.get("alpha_a", 0.0)),
     )
     geometry = dict(nx=nx, ny=ny, ny_cl=ny_cl, ny_gdl=ny_gdl,
                     reaction_mode=int(case["reaction_mode"]),

@@ -45,7 +45,7 @@ def test_param_structs_match_header():
     p = src[src.index("} lbm_domain_desc;"):src.index("} lbm_params;")]
     doubles = re.findall(r"double ([\w, ]+);", p)
     names = [n.strip() for grp in doubles for n in grp.split(",")]
-    assert names == list(lbm._PARAM_DOUBLES) + ["dp_in"]
+    assert names == list(lbm._PARAM_DOUBLES) + ["dp_in", "alpha_a"]
     assert ctypes.sizeof(lbm.lbm_params) == 8 * len(names) + 16
     assert lbm.lbm_params.dp_in.offset == 8 * len(lbm._PARAM_DOUBLES) + 16
     assert ctypes.sizeof(lbm.lbm_domain_desc) == 8 * 4 + 16
@@ -55,7 +55,7 @@ def test_param_structs_match_header():
                                   workloads.small_cathode(nx=40, ny=20, reaction_mode=1),
                                   workloads.cathode_blocks(nx=256, ny=128),
                                   dict(workloads.cathode_200x40(), inlet="pressure",
-                                       dp_in=2e-4)])
+                                       dp_in=2e-4, alpha_a=0.5)])
 def test_product_and_oracle_unit_mappings_agree(case):
     """The product's unit helper and the oracle's independent mapping turn
     the same physical workload into the same lattice problem."""

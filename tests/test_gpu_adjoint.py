@@ -31,6 +31,18 @@ def case_of(name):
     if name == "grains":
         return workloads.small_cathode(nx=44, ny=16, reaction_mode=0, V_op=0.45, grains=True,
                                        seed=23)
+    if name == "film-bv":      # Butler-Volmer near open circuit
+        return dict(workloads.small_cathode(nx=40, ny=14, reaction_mode=0, V_op=1.05, seed=21),
+                    alpha_a=0.5)
+    if name == "vol-bv":
+        return dict(workloads.small_cathode(nx=36, ny=20, reaction_mode=1, V_op=1.05, seed=22),
+                    alpha_a=0.5)
+    if name == "film-bv1":     # Butler-Volmer, anodic branch about 1 % of the flux
+        return dict(workloads.small_cathode(nx=40, ny=14, reaction_mode=0, V_op=1.0, seed=21),
+                    alpha_a=0.5)
+    if name == "vol-bv1":
+        return dict(workloads.small_cathode(nx=36, ny=20, reaction_mode=1, V_op=1.0, seed=22),
+                    alpha_a=0.5)
     raise KeyError(name)
 
 
@@ -39,7 +51,7 @@ def gpu(case, precision="fp64", mode=0):
     return Domain.from_case(case, precision=precision, interface_mode=mode)
 
 
-@pytest.mark.parametrize("name", ["film", "vol", "grains"])
+@pytest.mark.parametrize("name", ["film", "vol", "grains", "film-bv", "vol-bv"])
 @pytest.mark.parametrize("mode", [0, 1])
 def test_one_step_transpose_dot_product(name, mode):
     """<lam, (step(s + e v) - step(s - e v)) / 2e> = <step^T lam, v>, and the
@@ -129,7 +141,9 @@ def oracle_objective(case, mode, objective, N, material=None, u_in=None, x_star=
 
 
 @pytest.mark.parametrize("name,mode,objective", [("film", 0, 0), ("film", 1, 1), ("vol", 0, 0),
-                                                 ("vol", 1, 0), ("grains", 0, 1)])
+                                                 ("vol", 1, 0), ("grains", 0, 1),
+                                                 ("film-bv1", 0, 0), ("vol-bv1", 1, 0),
+                                                 ("film-bv1", 0, 1)])
 def test_gradient_matches_oracle_finite_differences(name, mode, objective):
     """Gradients of the objective after 40 steps (checkpoint segments of 7)
     w.r.t. phi, K, D_O2 (random directions over the GDL and on single cells)
@@ -156,16 +170,21 @@ def test_gradient_matches_oracle_finite_differences(name, mode, objective):
             e[yy, xx] = base[yy, xx]
             dirs.append(e)
         for vv in dirs:
-            h = 1e-5
+            # near open circuit the current is small (~1e-6 A/cm2) and the
+            # oracle's central difference is in round-off below h = 3e-4; at
+            # h = 1e-3 it is converged to about 3e-4 in every direction
+            h = 1e-3 if "bv" in name else 1e-5
             Jp, _ = oracle_objective(case, mode, objective, N, dict(mat0, **{key: base + h * vv}),
                                      x_star=xs)
             Jm, _ = oracle_objective(case, mode, objective, N, dict(mat0, **{key: base - h * vv}),
                                      x_star=xs)
             fd = (Jp - Jm) / (2 * h)
             ad = float(np.sum(g[key] * vv))
-            scale = max(abs(fd), abs(ad), 1e-5 * abs(J0))
+            # directions whose effect is below the finite difference's noise
+            # (about 1e-4 of J0 per unit h near open circuit) count as zero
+            scale = max(abs(fd), abs(ad), (1e-3 if "bv" in name else 1e-5) * abs(J0))
             assert abs(fd - ad) <= 1e-3 * scale, (key, fd, ad)
-    hu = 1e-6 * params["u_in_avg"]
+    hu = (1e-5 if "bv" in name else 1e-6) * params["u_in_avg"]
     Jp, _ = oracle_objective(case, mode, objective, N, u_in=params["u_in_avg"] + hu, x_star=xs)
     Jm, _ = oracle_objective(case, mode, objective, N, u_in=params["u_in_avg"] - hu, x_star=xs)
     fdu = (Jp - Jm) / (2 * hu)
