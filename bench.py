@@ -468,18 +468,25 @@ def end_to_end(case, precision, K, stream, interface_mode=0):
     t0 = time.perf_counter()
     d.set_fields(**pinned)
     d.reset()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
     for _ in range(K):
         d.step(1)
         d.current_density(profile=False)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
     out = d.fields()
     torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
+    t3 = time.perf_counter()
+    dt = t3 - t0
     assert np.isfinite(out["T"]).all()
     h2d = 5 * 8 * cells + 2 * cells   # material arrays + palette indices
     d2h = K * 2 * 8 + 6 * 8 * cells
     d.close()
     return {"seconds": dt, "unit": UNIT,
             "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
+            "breakdown_s": {"upload_and_reset": t1 - t0, "steps_with_reads": t2 - t1,
+                            "fields_read": t3 - t2},
             "includes": "material upload, reset, per-step current-density read, final fields read"}
 
 

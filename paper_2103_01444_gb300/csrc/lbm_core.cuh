@@ -186,35 +186,29 @@ __device__ R pull_flow_edge(const Pops<S, CG> &src, const KArgsT<R> &a, const ui
   if (sx < 0 || sx >= a.nx) {
     if (a.periodic) {
       sx = sx < 0 ? sx + a.nx : sx - a.nx;
-    } else if (sx < 0) {                                              // inlet
-      if (a.inlet_pressure && (m & M_INLET)) {
-        // pressure inlet: the virtual column -1 repeats column 0 with its
-        // equilibrium pressure part moved to phi p = 1/3 + dp_in; a source
-        // row outside the channel is the GDL's end wall
-        if (!(mask[(long long)sy * a.nxp] & M_INLET)) return R(src.at(OP[i], x, y));
-        R d[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) d[k] = R(src.at(k, 0, sy));
-        R jx = d[1] - d[3] + d[5] - d[6] - d[7] + d[8];
-        R jy = d[2] - d[4] + d[5] + d[6] - d[7] - d[8];
-        R s18 = ((d[1] + d[3]) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8]));
-        R inv_phi = pal[mid[(long long)sy * a.nxp]].inv_phi;
-        R dP = R(a.dp_in) + (R(-0.6) * s18 + R(0.4) * (jx * jx + jy * jy) * inv_phi);
-        return d[i] + lam9<R>(i) * dP;
+    } else {
+      const bool in = sx < 0;
+      if (in && !(a.inlet_pressure && (m & M_INLET))) {             // velocity inlet / wall
+        R w = R(src.at(OP[i], x, y));
+        if (m & M_INLET) w += R(6) * w9<R>(i) * R(EX[i]) * inlet_u<R>(a, R(y) - R(0.5) * R(EY[i]));
+        return w;
       }
-      R w = R(src.at(OP[i], x, y));
-      if (m & M_INLET) w += R(6) * w9<R>(i) * R(EX[i]) * inlet_u<R>(a, R(y) - R(0.5) * R(EY[i]));
-      return w;
-    } else {                                                          // outlet
-      const int vx = a.nx - 1;
+      // outlet, or the pressure inlet: a virtual column (nx, or -1) repeats
+      // the lattice's last (or first) column at the source row, with its
+      // equilibrium pressure part moved to phi p = 1/3 (+ dp_in at the
+      // inlet); at the inlet a source row outside the channel is the GDL's
+      // end wall
+      const int vx = in ? 0 : a.nx - 1;
+      const long long vc = (long long)sy * a.nxp + vx;
+      if (in && !(mask[vc] & M_INLET)) return R(src.at(OP[i], x, y));
       R d[9];
 #pragma unroll
       for (int k = 0; k < 9; ++k) d[k] = R(src.at(k, vx, sy));
       R jx = d[1] - d[3] + d[5] - d[6] - d[7] + d[8];
       R jy = d[2] - d[4] + d[5] + d[6] - d[7] - d[8];
       R s18 = ((d[1] + d[3]) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8]));
-      R inv_phi = pal[mid[(long long)sy * a.nxp + vx]].inv_phi;
-      R dP = R(-0.6) * s18 + R(0.4) * (jx * jx + jy * jy) * inv_phi;  // 1/3 - phi p*
+      R inv_phi = pal[mid[vc]].inv_phi;
+      R dP = (in ? R(a.dp_in) : R(0)) + (R(-0.6) * s18 + R(0.4) * (jx * jx + jy * jy) * inv_phi);
       return d[i] + lam9<R>(i) * dP;
     }
     if ((m & M_NEAR_SOLID) && (mask[(long long)sy * a.nxp + sx] & REG_MASK) == REG_SOLID)
