@@ -67,6 +67,12 @@ def parse():
                          "the residual (checked every 100 steps) is below TOL, or until "
                          "--max-seconds of stepping; one JSON line with steps and wall time")
     ap.add_argument("--max-seconds", type=float, default=240.0)
+    ap.add_argument("--rounding", default="nearest", choices=["nearest", "stochastic"],
+                    help="16-bit storage: round to nearest even, or stochastic rounding")
+    ap.add_argument("--precision-errors", type=int, default=0, metavar="NSTEPS",
+                    help="instead of the throughput bench: run the workload NSTEPS steps with "
+                         "FP32, BF16 and FP16 storage and report per-field relative L2 errors "
+                         "of the 16-bit runs against the FP32 run (default workload: grains)")
     return ap.parse_args()
 
 
@@ -310,7 +316,7 @@ def run_ours(args):
     cells = case["nx"] * case["ny"]
     stream = torch.cuda.Stream(device=dev)
     d = Domain.from_case(case, precision=args.precision, stream=stream.cuda_stream,
-                         interface_mode=args.interface)
+                         interface_mode=args.interface, rounding=args.rounding)
     variant, tune_ms = d.tune(20)       # launch shape of the step kernel
     W, K = max(args.warmup, 3), max(args.steps, 1)
     d.step(W)
@@ -348,7 +354,9 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
         "data": "synthetic",
         "config": {"workload": case["name"], "nx": case["nx"], "ny": case["ny"],
-                   "storage": args.precision, "parallelism": f"replicas{world}",
+                   "storage": args.precision + ("" if args.rounding == "nearest"
+                                                else ", stochastic rounding"),
+                   "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (two population buffers of "
                          f"{24 * cells * d_esize(args.precision) / 1e6:.0f} MB)",
                    "reaction": ("volumetric catalyst rows" if case["reaction_mode"] == 1
@@ -538,11 +546,66 @@ def run_to_residual(args):
     d.close()
 
 
+def run_precision_errors(args):
+    """Reduced-precision storage at full size: the workload stepped NSTEPS
+    times from reset with FP32, BF16 and FP16 populations (FP32 arithmetic
+    in all), the 16-bit ones with round-to-nearest and with stochastic
+    rounding; per-field relative L2 errors of the 16-bit runs against the
+    FP32 run over the fluid cells, and the current density of each.
+    The FP64 oracle is far too slow for this size; the comparison against
+    it is made on small grain cathodes by the tests."""
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (there is no CPU fallback)")
+    from paper_2103_01444_gb300.build import build
+    from paper_2103_01444_gb300.lbm import Domain
+    build()
+    case = workload(args)
+    N = args.precision_errors
+    out, ref, live = {}, None, None
+    runs = [("fp32", "nearest")] + [(p, r) for p in ("bf16", "fp16")
+                                    for r in ("nearest", "stochastic")]
+    for prec, rounding in runs:
+        d = Domain.from_case(case, precision=prec, interface_mode=args.interface,
+                             rounding=rounding)
+        d.tune(5)
+        d.reset()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d.step(N)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        f = d.fields()
+        i_avg = d.current_density(profile=False)[0]
+        if live is None:
+            live = (d.mask() & 3) != 3
+        fields = {"u": np.stack([f["ux"], f["uy"]]), "T-T_in": f["T"] - case["T_in"],
+                  "C_O2": f["C_O2"], "C_H2O": f["C_H2O"]}
+        row = {"i_avg_A_cm2": i_avg, "glups": case["nx"] * case["ny"] * N / wall / 1e9}
+        if ref is None:
+            ref = (fields, i_avg)
+        else:
+            for k, v in fields.items():
+                m = np.broadcast_to(live, v.shape)
+                row[k] = float(np.linalg.norm((v - ref[0][k])[m]) / np.linalg.norm(ref[0][k][m]))
+            row["i_avg"] = abs(i_avg - ref[1]) / abs(ref[1])
+        out[prec if prec == "fp32" else f"{prec}-{rounding}"] = row
+        d.close()
+    print(json.dumps({"metric": "per-field relative L2 error of 16-bit storage vs FP32",
+                      "steps": N, "config": {"workload": case["name"], "nx": case["nx"],
+                                             "ny": case["ny"], "interface_mode": args.interface},
+                      "results": out}))
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
     elif a.to_residual > 0:
         run_to_residual(a)
+    elif a.precision_errors > 0:
+        if a.workload == "blocks" and a.nx == NX and a.ny == NY:
+            a.workload = "grains"
+        run_precision_errors(a)
     else:
         run_ours(a)

@@ -59,7 +59,14 @@ typedef struct {
                               negligible-thickness layer); 1: volumetric catalyst rows */
   int32_t periodic_x;      /* 1: x is periodic (closed-form tests); 0: inlet/outlet */
   int32_t precision;       /* lbm_precision */
-  int32_t reserved;        /* must be 0 */
+  int32_t rounding;        /* how a step stores 16-bit populations (LBM_BF16, LBM_FP16):
+                              0 round to nearest even; 1 stochastic rounding, unbiased,
+                              with random bits from a counter-based hash of the cell, the
+                              link and a device step counter (reset by lbm_reset), so runs
+                              from reset are reproducible.  Small per-step increments of a
+                              large deviation (slow heating, water production) survive
+                              in expectation instead of being rounded away.  Must be 0 for
+                              FP32/FP64; lbm_grad, lbm_vjp and batches need 0. */
   const uint8_t *solid;    /* optional host [ny][nx] pore-scale solid cells (1 = solid);
                               NULL = none.  Solids may not touch column 0 or the last
                               two columns. */
@@ -112,7 +119,8 @@ typedef struct lbm_domain lbm_domain; /* opaque */
 /* Allocates a domain (two population buffers, node mask, material palette,
  * reduction scratch) and builds the node mask on the device.  The state is
  * undefined until lbm_set_params, lbm_set_fields and lbm_reset are called.
- * EINVAL: bad sizes, reserved != 0, solids on the inlet/outlet columns.
+ * EINVAL: bad sizes, rounding outside {0, 1} or 1 with FP32/FP64 storage,
+ * solids on the inlet/outlet columns.
  * ENOMEM: device allocation failed. */
 lbm_status lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out);
 

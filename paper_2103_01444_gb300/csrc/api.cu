@@ -81,6 +81,7 @@ struct lbm_domain {
   double tuned_ms[kStepVariants] = {};
   double *dsmall = nullptr;    // device results (16 doubles)
   int *dbad = nullptr;
+  unsigned *dseed = nullptr;   // step counter seeding stochastic 16-bit rounding
   double *hsmall = nullptr;    // pinned host mirror
   double *scratch = nullptr;   // [24][ny][nx] doubles, lazily allocated
   float *dprofile = nullptr;   // [nx]
@@ -111,6 +112,8 @@ KArgs make_args(const lbm_domain *d) {
   const double tau = 3.0 * p.nu + 0.5;
   a.s_nu = 1.0 / tau;
   a.s_q = 8.0 * (2.0 - 1.0 / tau) / (8.0 - 1.0 / tau);
+  a.stochastic = d->desc.rounding == 1;
+  a.seed_ctr = d->dseed;
   a.body_g = p.body_force_x;
   a.u_in_avg = p.inlet_mode == 0 ? p.u_in_avg : 0.0;
   a.inlet_pressure = p.inlet_mode == 1;
@@ -188,6 +191,7 @@ lbm_status launch_steps(lbm_domain *d, int64_t n) {
       using S = std::remove_pointer_t<decltype(tag)>;
       launch_step<S>(d->pop[d->cur], d->pop[d->cur ^ 1], g, a, d->variant, d->stream);
     });
+    if (a.stochastic) launch_seed_advance(d->dseed, d->stream);
     d->cur ^= 1;
   }
   CK(cudaGetLastError());
@@ -271,7 +275,9 @@ lbm_status lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
   const lbm_domain_desc &D = *desc;
   if (D.nx < 4 || D.ny < 3) return fail(LBM_EINVAL, "lattice must be at least 4 x 3 (got %d x %d)", D.nx, D.ny);
   if ((long long)D.nx * D.ny > (1LL << 31)) return fail(LBM_EINVAL, "lattice too large");
-  if (D.reserved != 0) return fail(LBM_EINVAL, "reserved must be 0");
+  if (D.rounding != 0 && D.rounding != 1) return fail(LBM_EINVAL, "rounding must be 0 or 1");
+  if (D.rounding == 1 && D.precision != LBM_BF16 && D.precision != LBM_FP16)
+    return fail(LBM_EINVAL, "stochastic rounding applies to BF16/FP16 storage only");
   if (D.precision < LBM_FP64 || D.precision > LBM_FP16) return fail(LBM_EINVAL, "bad precision %d", D.precision);
   if (D.reaction_mode != 0 && D.reaction_mode != 1) return fail(LBM_EINVAL, "reaction_mode must be 0 or 1");
   if (D.reaction_mode == 0 && D.ny_cl != 0) return fail(LBM_EINVAL, "thin-film mode takes ny_cl = 0");
@@ -314,6 +320,7 @@ lbm_status lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
       cudaMalloc(&d->partial, sizeof(double) * 10 * residual_blocks(D.nx, D.ny)) != cudaSuccess ||
       cudaMalloc(&d->colsum, sizeof(double) * 2 * D.nx) != cudaSuccess ||
       cudaMalloc(&d->dsmall, sizeof(double) * 16) != cudaSuccess || cudaMalloc(&d->dbad, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&d->dseed, 256) != cudaSuccess ||
       cudaMalloc(&d->dprofile, sizeof(float) * D.nx) != cudaSuccess ||
       cudaMallocHost(&d->hsmall, sizeof(double) * 16) != cudaSuccess) {
     cudaGetLastError();
@@ -343,7 +350,7 @@ lbm_status lbm_destroy_domain(lbm_domain *d) {
   if (d->stream) cudaStreamSynchronize(d->stream);
   drop_graphs(d);
   for (void *p : {d->pop[0], d->pop[1], (void *)d->mask, (void *)d->mid, d->pal, (void *)d->raw,
-                  d->snap, (void *)d->partial, (void *)d->colsum, (void *)d->dsmall, (void *)d->dbad,
+                  d->snap, (void *)d->partial, (void *)d->colsum, (void *)d->dsmall, (void *)d->dbad, (void *)d->dseed,
                   (void *)d->scratch, (void *)d->dprofile})
     if (p) cudaFree(p);
   if (d->hsmall) cudaFreeHost(d->hsmall);
@@ -457,6 +464,7 @@ lbm_status lbm_reset(lbm_domain *d) {
     launch_init<S>(d->pop[0], g, a, d->stream);
     launch_init<S>(d->pop[1], g, a, d->stream);
   });
+  CK(cudaMemsetAsync(d->dseed, 0, sizeof(unsigned), d->stream));
   CK(cudaGetLastError());
   d->cur = 0;
   d->steps = 0;
@@ -947,6 +955,7 @@ lbm_status lbm_vjp(lbm_domain *d, const double *lam_next, double *lam_prev, doub
   if (s != LBM_OK) return s;
   if (!lam_next || !lam_prev) return fail(LBM_EINVAL, "null argument");
   if (d->prm.inlet_mode != 0) return fail(LBM_EINVAL, "the adjoint needs the velocity inlet (inlet_mode 0)");
+  if (d->desc.rounding != 0) return fail(LBM_EINVAL, "the adjoint needs round-to-nearest storage");
   AdjWork w;
   if ((s = w.alloc(d)) != LBM_OK) return s;
   if ((s = w.zero_grads(d)) != LBM_OK) return s;
@@ -964,6 +973,7 @@ lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t se
   if (s != LBM_OK) return s;
   if (objective != 0 && objective != 1) return fail(LBM_EINVAL, "objective must be 0 or 1");
   if (d->prm.inlet_mode != 0) return fail(LBM_EINVAL, "the adjoint needs the velocity inlet (inlet_mode 0)");
+  if (d->desc.rounding != 0) return fail(LBM_EINVAL, "the adjoint needs round-to-nearest storage");
   if (nsteps < 2 || nsteps > (1LL << 30)) return fail(LBM_EINVAL, "nsteps outside [2, 2^30]");
   const int64_t N = nsteps;
   const int seg = segment > 0 ? segment : (int)std::ceil(std::sqrt((double)N));
@@ -1361,6 +1371,8 @@ lbm_status lbm_create_batch(lbm_domain *const *domains, int32_t ncases, lbm_batc
     if (s != LBM_OK) return s;
     if (domains[c]->desc.precision != domains[0]->desc.precision)
       return fail(LBM_EINVAL, "batched domains must share one precision");
+    if (domains[c]->desc.rounding != 0)
+      return fail(LBM_EINVAL, "batched domains need round-to-nearest storage");
     for (int k = 0; k < c; ++k)
       if (domains[k] == domains[c]) return fail(LBM_EINVAL, "domain %d appears twice", c);
   }

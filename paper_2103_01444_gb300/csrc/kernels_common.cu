@@ -48,6 +48,10 @@ __global__ void k_build_mask(uint8_t *__restrict__ mask, const uint8_t *__restri
   mask[plane + c] = nb;
 }
 
+__global__ void k_seed_advance(unsigned *ctr) { *ctr += 1u; }
+
+void launch_seed_advance(unsigned *ctr, cudaStream_t st) { k_seed_advance<<<1, 1, 0, st>>>(ctr); }
+
 void launch_build_mask(uint8_t *mask, const uint8_t *solid, int nx, int ny, int nxp, int ny_cl,
                        int ny_gdl, int mode, int periodic, cudaStream_t st) {
   dim3 grid((nxp + 127) / 128, ny);

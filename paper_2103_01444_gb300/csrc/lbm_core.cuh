@@ -58,6 +58,45 @@ template <bool CG, typename S> __device__ __forceinline__ auto ldp(const S *p) {
   else return ld_r(p);
 }
 
+// Stochastic rounding of a step's 16-bit stores: unbiased, E[stored] = v,
+// so increments far below half an ulp of a stored value still accumulate.
+// r holds uniform random bits.  BF16 keeps the top 16 bits of the FP32
+// pattern: adding 16 random bits below them and truncating rounds the
+// magnitude up with probability equal to the dropped fraction.  FP16 picks
+// between the neighbours toward and away from zero with that probability.
+__device__ __forceinline__ void st_sr(__nv_bfloat16 *p, float v, unsigned r) {
+  const unsigned b = __float_as_uint(v) + (r & 0xffffu);
+  *reinterpret_cast<unsigned short *>(p) = (unsigned short)(b >> 16);
+}
+__device__ __forceinline__ void st_sr(__half *p, float v, unsigned r) {
+  const __half lo = __float2half_rz(v);
+  const float lof = __half2float(lo), d = v - lof;   // exact (Sterbenz, or lof = 0)
+  if (d == 0.0f) {
+    *p = lo;
+    return;
+  }
+  const __half hi = v > 0.0f ? __float2half_ru(v) : __float2half_rd(v);
+  const float span = __half2float(hi) - lof;
+  const float u = (float)(r >> 8) * (1.0f / 16777216.0f);   // [0, 1)
+  *p = (v > 0.0f ? (u * span < d) : (u * span > d)) ? hi : lo;
+}
+// Random bits for cell c of a step: a 32-bit integer hash of (c, seed), and
+// a xorshift stream from it for the cell's 24 stores.
+__device__ __forceinline__ unsigned hash32(unsigned x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+__device__ __forceinline__ unsigned xorshift32(unsigned &s) {
+  s ^= s << 13;
+  s ^= s >> 17;
+  s ^= s << 5;
+  return s;
+}
+
 __device__ __forceinline__ void st_r(float *p, float v) { *p = v; }
 __device__ __forceinline__ void st_r(double *p, double v) { *p = v; }
 __device__ __forceinline__ void st_r(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
@@ -103,6 +142,8 @@ template <typename F> struct KArgsT {
   // Butler-Volmer anodic branch, same form (all zero for Tafel kinetics)
   F kA_surf_a, kA_vol_a, k_ein_a, k_c1_a;
   F theta0;                 // Cref_T - T_in
+  int stochastic;           // 16-bit step stores: 1 stochastic rounding, 0 nearest even
+  const unsigned *seed_ctr; // device step counter seeding the stochastic rounding
   F hpo;                    // temperature per unit O2 consumed (Eq. 15, 16)
 };
 using KArgs = KArgsT<double>;
@@ -120,6 +161,7 @@ template <typename F> __host__ __device__ inline KArgsT<F> narrow_args(const KAr
   }
   r.kA_surf = F(a.kA_surf); r.kA_vol = F(a.kA_vol); r.k_ein = F(a.k_ein); r.k_c1 = F(a.k_c1);
   r.T_in = F(a.T_in); r.theta0 = F(a.theta0); r.hpo = F(a.hpo);
+  r.stochastic = a.stochastic; r.seed_ctr = a.seed_ctr;
   r.kA_surf_a = F(a.kA_surf_a); r.kA_vol_a = F(a.kA_vol_a);
   r.k_ein_a = F(a.k_ein_a); r.k_c1_a = F(a.k_c1_a);
   return r;

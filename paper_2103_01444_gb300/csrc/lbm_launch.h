@@ -75,6 +75,9 @@ template <typename S> void launch_adj_finish(const DevGeom &g, const KArgs &a, c
 template <typename S> void launch_adj_fold(const DevGeom &g, const KArgs &a, const AdjPtrs &b, cudaStream_t st);
 template <typename S> void launch_adj_seed_current(const void *src, const DevGeom &g, const KArgs &a, int fickian, double weight, const AdjPtrs &b, cudaStream_t st);
 
+// Advances the step counter that seeds stochastic 16-bit rounding.
+void launch_seed_advance(unsigned *ctr, cudaStream_t st);
+
 // Node mask from the geometry (solid may be NULL).
 void launch_build_mask(uint8_t *mask, const uint8_t *solid, int nx, int ny, int nxp, int ny_cl,
                        int ny_gdl, int mode, int periodic, cudaStream_t st);

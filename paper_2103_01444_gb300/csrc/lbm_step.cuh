@@ -11,7 +11,7 @@ namespace pemlbm {
 // ------------------------------------------------------------- step (K1)
 // One coupled update of cell (x, y): src -> dst.  Shared by the single-
 // domain step and the batched steps.
-template <typename S, bool CG = false>
+template <typename S, bool CG = false, bool SR = false>
 __device__ __forceinline__ void cell_update(const S *__restrict__ src_p, S *__restrict__ dst,
                                             const uint8_t *__restrict__ mask,
                                             const uint16_t *__restrict__ mid,
@@ -39,10 +39,19 @@ __device__ __forceinline__ void cell_update(const S *__restrict__ src_p, S *__re
   const Macro<R> u = macros<R>(a, mc, cell);
   R o[9];
   collide_flow<R>(a, mc, u, cell.f, o);
+  // 16-bit storage with stochastic rounding: a random stream per cell and
+  // step (hash of the cell and the device step counter)
+  unsigned rs = 0;
+  if constexpr (SR)
+    rs = hash32((unsigned)c * 0x9e3779b9u ^ hash32(__ldg(a.seed_ctr) + 0x632be5abu)) | 1u;
+  auto store = [&](S *p, R v) {
+    if constexpr (SR) st_sr(p, v, xorshift32(rs));
+    else st_r(p, v);
+  };
   S *out = dst + c;
   if (live) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) st_r(out + (long long)i * a.plane, o[i]);
+    for (int i = 0; i < 9; ++i) store(out + (long long)i * a.plane, o[i]);
   }
   const R srcv[3] = {-S_vol * R(a.hpo) * mc.inv_sigma, S_vol, R(-2) * S_vol};
 #pragma unroll
@@ -51,12 +60,14 @@ __device__ __forceinline__ void cell_update(const S *__restrict__ src_p, S *__re
     collide_scalar<R>(a, mc, s, u.ux, u.uy, u.C[s], cell.g[s], srcv[s], g);
     if (live) {
 #pragma unroll
-      for (int i = 0; i < 5; ++i) st_r(out + (long long)(9 + 5 * s + i) * a.plane, g[i]);
+      for (int i = 0; i < 5; ++i) store(out + (long long)(9 + 5 * s + i) * a.plane, g[i]);
     }
   }
 }
 
-template <typename S, int BX, int BY, int MINB>
+// SR: 16-bit stores with stochastic rounding (a separate instantiation, so
+// the round-to-nearest kernel carries none of its code).
+template <typename S, int BX, int BY, int MINB, bool SR = false>
 __global__ void __launch_bounds__(BX * BY, MINB)
 k_step(const S *__restrict__ src_p, S *__restrict__ dst, const uint8_t *__restrict__ mask,
        const uint16_t *__restrict__ mid, const MatCoef<typename Real<S>::type> *__restrict__ pal,
@@ -64,7 +75,7 @@ k_step(const S *__restrict__ src_p, S *__restrict__ dst, const uint8_t *__restri
   const int x = blockIdx.x * BX + (threadIdx.x % BX);
   const int y = blockIdx.y * BY + (threadIdx.x / BX);
   if (x >= a.nx || y >= a.ny) return;
-  cell_update<S>(src_p, dst, mask, mid, pal, a, x, y);
+  cell_update<S, false, SR>(src_p, dst, mask, mid, pal, a, x, y);
 }
 
 // ------------------------------------------------------ launcher
@@ -72,9 +83,16 @@ template <typename S, int V>
 void launch_step_v(const void *src, void *dst, const DevGeom &g, const KArgs &a, cudaStream_t st) {
   constexpr StepShape sh = kStepShapes[V];
   dim3 grid((a.nx + sh.bx - 1) / sh.bx, (a.ny + sh.by - 1) / sh.by);
+  using R = typename Real<S>::type;
+  if constexpr (sizeof(S) == 2) {
+    if (a.stochastic) {
+      k_step<S, sh.bx, sh.by, sh.minb, true><<<grid, sh.bx * sh.by, 0, st>>>(
+          (const S *)src, (S *)dst, g.mask, g.mid, (const MatCoef<R> *)g.pal, narrow_args<R>(a));
+      return;
+    }
+  }
   k_step<S, sh.bx, sh.by, sh.minb><<<grid, sh.bx * sh.by, 0, st>>>(
-      (const S *)src, (S *)dst, g.mask, g.mid,
-      (const MatCoef<typename Real<S>::type> *)g.pal, narrow_args<typename Real<S>::type>(a));
+      (const S *)src, (S *)dst, g.mask, g.mid, (const MatCoef<R> *)g.pal, narrow_args<R>(a));
 }
 
 template <typename S>

@@ -38,7 +38,7 @@ class LbmError(RuntimeError):
 class lbm_domain_desc(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("ny_cl", C.c_int32),
                 ("ny_gdl", C.c_int32), ("reaction_mode", C.c_int32), ("periodic_x", C.c_int32),
-                ("precision", C.c_int32), ("reserved", C.c_int32),
+                ("precision", C.c_int32), ("rounding", C.c_int32),
                 ("solid", C.POINTER(C.c_uint8)), ("cuda_stream", C.c_void_p)]
 
 
@@ -120,7 +120,8 @@ class Domain:
     """One cathode lattice on the GPU (wraps an lbm_domain handle)."""
 
     def __init__(self, nx, ny, ny_cl=0, ny_gdl=0, reaction_mode=0, periodic_x=0,
-                 precision="fp32", solid=None, stream=None):
+                 precision="fp32", solid=None, stream=None, rounding="nearest"):
+        """rounding: "nearest" or "stochastic" (16-bit storage only)."""
         self.L = load_library()
         self.nx, self.ny = int(nx), int(ny)
         self._solid = None if solid is None else np.ascontiguousarray(solid, np.uint8)
@@ -128,7 +129,7 @@ class Domain:
             nx=self.nx, ny=self.ny, ny_cl=int(ny_cl), ny_gdl=int(ny_gdl),
             reaction_mode=int(reaction_mode), periodic_x=int(periodic_x),
             precision=PRECISION[precision] if isinstance(precision, str) else int(precision),
-            reserved=0,
+            rounding={"nearest": 0, "stochastic": 1}[rounding],
             solid=None if self._solid is None else self._solid.ctypes.data_as(C.POINTER(C.c_uint8)),
             cuda_stream=None if stream is None else C.c_void_p(int(stream)))
         h = C.c_void_p()
@@ -138,10 +139,10 @@ class Domain:
 
     @classmethod
     def from_case(cls, case: dict, precision="fp32", forchheimer: int = 1, stream=None,
-                  reset: bool = True, interface_mode: int = 0):
+                  reset: bool = True, interface_mode: int = 0, rounding="nearest"):
         from .units import cathode_params
         params, fields, geo = cathode_params(case, forchheimer, interface_mode)
-        d = cls(precision=precision, stream=stream, **geo)
+        d = cls(precision=precision, stream=stream, rounding=rounding, **geo)
         d.set_params(params)
         d.set_fields(**fields)
         if reset:
