@@ -174,6 +174,21 @@ lbm_status lbm_current_density(lbm_domain *d, double *i_avg_A_cm2, double *heat_
  * values. */
 lbm_status lbm_residual(lbm_domain *d, double *res);
 
+/* Balances of the last step (per-step reductions of Sec. 4's boundary
+ * conditions and Eq. 12-15), lattice units, summed over the lattice, FP64:
+ *   out[0] O2 consumed by the reaction (mole fraction per step),
+ *   out[1] its heat, h J summed (temperature x mole fraction per step),
+ *   out[2..5] net inflow through the inlet column of mass, T, O2, H2O,
+ *   out[6..9] net inflow through the outlet column (negative = outflow).
+ * With them, the change of each scalar total over the step is exact
+ * (the D2Q5 collisions conserve C): O2 in + out - J, H2O in + out + 2 J;
+ * the mass flows are those through the boundary links (the collision also
+ * relaxes the flow's mass moment, Sec. 2.1).  Recomputed from the
+ * state before the last step by the step's own boundary pulls (zeros for
+ * a periodic lattice).  out: host, 10 doubles.  ESTATE before the first
+ * step. */
+lbm_status lbm_balances(lbm_domain *d, double *out);
+
 /* Macroscopic fields of the last step (the values its collision used):
  * out = [6][ny][nx] doubles: u_x, u_y, p (Eq. 8), T, C_O2, C_H2O (Eq. 11);
  * zeros in solid cells.  on_device = 1: out is a device pointer written on

@@ -529,6 +529,25 @@ lbm_status lbm_current_density(lbm_domain *d, double *i_avg, double *heat, float
   return LBM_OK;
 }
 
+lbm_status lbm_balances(lbm_domain *d, double *out) {
+  lbm_status s = check_ready(d);
+  if (s != LBM_OK) return s;
+  if (!out) return fail(LBM_EINVAL, "null argument");
+  if (d->steps < 1) return fail(LBM_ESTATE, "no step taken yet");
+  const KArgs a = make_args(d);
+  dispatch(d->desc.precision, [&](auto *tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    launch_catalyst<S>(d->pop[d->cur ^ 1], geom(d), a, 1.0, nullptr, d->colsum, d->dsmall,
+                       d->stream);
+    launch_balances<S>(d->pop[d->cur ^ 1], geom(d), a, d->dsmall + 2, d->stream);
+  });
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(d->hsmall, d->dsmall, 10 * sizeof(double), cudaMemcpyDeviceToHost, d->stream));
+  CK(cudaStreamSynchronize(d->stream));
+  std::memcpy(out, d->hsmall, 10 * sizeof(double));
+  return LBM_OK;
+}
+
 lbm_status lbm_residual(lbm_domain *d, double *res) {
   if (!d || !res) return fail(LBM_EINVAL, "null argument");
   if (!d->have_state) return fail(LBM_ESTATE, "call lbm_reset first");

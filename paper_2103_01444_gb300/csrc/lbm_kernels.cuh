@@ -168,6 +168,81 @@ __device__ __forceinline__ void block_sum(double (&v)[N], double *smem /* N * 32
   }
 }
 
+// ------------------------------------- inlet / outlet balances (K3b)
+// Net inflow of mass and of the three scalars through the inlet column and
+// through the outlet column during the last step, recomputed from the state
+// before it (src) with the step's own boundary pulls.  Each incoming
+// boundary link counts its pulled value, each population that leaves the
+// lattice through the column counts negatively; opposite links carry equal
+// weights, so the deviation references cancel.  One block; rows in a fixed
+// order per thread, then a fixed-order block sum (deterministic).
+// out: in_mass, in_T, in_O2, in_H2O, out_mass, out_T, out_O2, out_H2O.
+template <typename S>
+__global__ void __launch_bounds__(kReduceThreads)
+k_balances(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
+           const uint16_t *__restrict__ mid, const MatCoef<typename Real<S>::type> *__restrict__ pal,
+           KArgsT<typename Real<S>::type> a, double *__restrict__ out) {
+  using R = typename Real<S>::type;
+  __shared__ double sm[8 * 32];
+  const Pops<S> src{src_p, a.plane, a.nxp};
+  const int EX[9] = EX9_TAB, EY[9] = EY9_TAB, OP[9] = OP9_TAB;
+  double acc[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) acc[k] = 0.0;
+  if (!a.periodic) {
+    for (int y = threadIdx.x; y < a.ny; y += blockDim.x) {
+      for (int side = 0; side < 2; ++side) {
+        const int x = side ? a.nx - 1 : 0;
+        const long long c = (long long)y * a.nxp + x;
+        const uint8_t m = mask[c];
+        if ((m & REG_MASK) == REG_SOLID) continue;
+        const MatCoef<R> mc = pal[mid[c]];
+        const int dir = side ? -1 : 1;             // e_x of the links entering through this side
+        double *o = acc + 4 * side;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+          const int sy = y - EY[i];
+          if (EX[i] == dir) {                       // enters through the column
+            if (sy < 0 || sy >= a.ny) continue;     // a wall link
+            const R v = pull_flow_edge<S, R>(src, a, mask, mid, pal, i, x, y, m, R(0));
+            // inlet: the pulled value replaces the bounced one (the moving-wall
+            // or virtual-column excess); outlet: the whole pulled value
+            o[0] += side ? (double)v : (double)v - (double)R(src.at(OP[i], x, y));
+          } else if (side && EX[i] == -dir) {       // leaves through the outlet
+            const int ty = y + EY[i];
+            if (ty >= 0 && ty < a.ny) o[0] -= (double)R(src.at(i, x, y));
+          }
+        }
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+          const int q = 9 + 5 * s;
+          const int lin = side ? 3 : 1;              // D2Q5 link entering through the column
+          const R v = pull_scalar_edge<S, R>(src, a, mask, mc, s, lin, x, y, m, R(0));
+          if (side) {
+            o[1 + s] += (double)v - (double)R(src.at(q + 1, x, y));   // in via 3, out via 1
+          } else if (m & M_INLET) {
+            o[1 + s] += (double)v - (double)R(src.at(q + 3, x, y));   // Dirichlet excess
+          }
+        }
+      }
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], off);
+  }
+  if (lane == 0)
+    for (int k = 0; k < 8; ++k) sm[k * 32 + warp] = acc[k];
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += sm[threadIdx.x * 32 + w];
+    out[threadIdx.x] = t;
+  }
+}
+
 // --------------------------------------------- catalyst reduction (K3)
 // Recomputes the reaction applied in the last step from the state before it
 // (src).  Blocks of kCatalystBX columns x kCatalystBY row-threads: each
@@ -488,6 +563,14 @@ void launch_fields(const void *src, const DevGeom &g, const KArgs &a, double *ou
 }
 
 template <typename S>
+void launch_balances(const void *src, const DevGeom &g, const KArgs &a, double *out,
+                     cudaStream_t st) {
+  using R = typename Real<S>::type;
+  k_balances<S><<<1, kReduceThreads, 0, st>>>((const S *)src, g.mask, g.mid,
+                                              (const MatCoef<R> *)g.pal, narrow_args<R>(a), out);
+}
+
+template <typename S>
 void launch_catalyst(const void *src, const DevGeom &g, const KArgs &a, double i_scale,
                      float *profile, double *colsum, double *out, cudaStream_t st) {
   const int nb = (a.nx + kCatalystBX - 1) / kCatalystBX;
@@ -534,6 +617,8 @@ void launch_set_state(void *pop, const DevGeom &g, const KArgs &a, const double 
                                cudaStream_t);                                                   \
   template void launch_fields<S>(const void *, const DevGeom &, const KArgs &, double *,        \
                                  cudaStream_t);                                                 \
+  template void launch_balances<S>(const void *, const DevGeom &, const KArgs &, double *,      \
+                                   cudaStream_t);                                                \
   template void launch_catalyst<S>(const void *, const DevGeom &, const KArgs &, double,        \
                                    float *, double *, double *, cudaStream_t);                  \
   template void launch_residual<S>(const void *, const DevGeom &, const KArgs &, void *,        \

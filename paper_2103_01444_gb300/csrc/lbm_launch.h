@@ -43,6 +43,7 @@ struct DevGeom {
 
 template <typename S> void launch_step(const void *src, void *dst, const DevGeom &g, const KArgs &a, int variant, cudaStream_t st);
 template <typename S> void launch_fields(const void *src, const DevGeom &g, const KArgs &a, double *out, cudaStream_t st);
+template <typename S> void launch_balances(const void *src, const DevGeom &g, const KArgs &a, double *out, cudaStream_t st);
 template <typename S> void launch_catalyst(const void *src, const DevGeom &g, const KArgs &a, double i_scale, float *profile, double *colsum, double *out, cudaStream_t st);
 template <typename S> void launch_residual(const void *src, const DevGeom &g, const KArgs &a, void *snap, double *partial, int *bad, double *out, cudaStream_t st);
 // Blocks of the residual kernel (= rows of its partial-sum buffer).

@@ -24,7 +24,7 @@ EXPORTS = ("lbm_create_domain", "lbm_destroy_domain", "lbm_set_params", "lbm_set
            "lbm_reset", "lbm_step", "lbm_current_density", "lbm_residual", "lbm_get_fields",
            "lbm_get_state", "lbm_set_state", "lbm_get_mask", "lbm_get_step", "lbm_save_state",
            "lbm_load_state", "lbm_time_steps", "lbm_bytes_per_cell", "lbm_tune",
-           "lbm_set_variant", "lbm_residual_noalloc", "lbm_create_batch", "lbm_destroy_batch",
+           "lbm_set_variant", "lbm_residual_noalloc", "lbm_balances", "lbm_create_batch", "lbm_destroy_batch",
            "lbm_batch_set_schedule", "lbm_batch_tune", "lbm_batch_step", "lbm_batch_time_steps",
            "lbm_grad", "lbm_vjp", "lbm_last_error")
 
@@ -76,6 +76,7 @@ def load_library(path: str = LIB_PATH):
         "lbm_step": [P, C.c_int64],
         "lbm_current_density": [P, d, d, C.POINTER(C.c_float)],
         "lbm_residual": [P, d],
+        "lbm_balances": [P, d],
         "lbm_get_fields": [P, C.c_void_p, C.c_int32],
         "lbm_get_state": [P, d],
         "lbm_set_state": [P, d],
@@ -202,6 +203,16 @@ class Domain:
             self.h, C.byref(i_avg), C.byref(heat),
             None if prof is None else prof.ctypes.data_as(C.POINTER(C.c_float))))
         return i_avg.value, heat.value, prof
+
+    BALANCE_KEYS = ("J", "heat", "in_mass", "in_T", "in_O2", "in_H2O",
+                    "out_mass", "out_T", "out_O2", "out_H2O")
+
+    def balances(self) -> dict:
+        """Balances of the last step (lattice units): O2 consumed, its heat,
+        and the net inflows through the inlet and outlet columns."""
+        out = np.zeros(10)
+        _check(self.L.lbm_balances(self.h, _dp(out)))
+        return dict(zip(self.BALANCE_KEYS, out.tolist()))
 
     def residual(self) -> float:
         r = C.c_double()

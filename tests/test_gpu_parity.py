@@ -173,6 +173,40 @@ def test_fp64_butler_volmer_matches_oracle(name, mode):
     assert t.current_density()[0] > 1.005 * i_g
 
 
+@pytest.mark.parametrize("name,inlet", [("film-64x16", "velocity"), ("vol-77x20", "velocity"),
+                                        ("grains-70x24", "pressure"), ("vol-77x20", "pressure")])
+def test_balances_match_oracle_and_close_the_budgets(name, inlet):
+    """lbm_balances: the O2 consumed, its heat and the inlet/outlet inflows
+    of the last step equal the oracle's diagnostics of the same step, and
+    they close the GPU's own O2 and H2O budgets over that step exactly."""
+    from oracle.oracle import DIAG
+    case = CASES[name]()
+    if inlet == "pressure":
+        case = dict(case, inlet="pressure", dp_in=1e-3)
+    o = oracle_of(case)
+    o.step(200)
+    d = gpu_domain(case, "fp64")
+    d.step(199)
+    s0 = d.state()
+    d.step(1)
+    s1 = d.state()
+    b = d.balances()
+    dg = o.diag
+    assert b["J"] == pytest.approx(dg[DIAG["J"]], rel=1e-10)
+    assert b["heat"] == pytest.approx(o.qx.sum(), rel=1e-10)
+    for k in ("in_mass", "in_T", "in_O2", "in_H2O", "out_mass", "out_T", "out_O2", "out_H2O"):
+        assert b[k] == pytest.approx(dg[DIAG[k]], rel=1e-9, abs=1e-13 * abs(dg[DIAG["in_T"]])), k
+    assert b["J"] > 0 and b["in_mass"] != 0
+    # the scalar collisions conserve C (Q0 = 0), so the O2 and H2O totals
+    # change by exactly the boundary flows and the reaction (the flow's
+    # mass moment relaxes at s0 = 1/tau, so sum f has no such budget)
+    tot = lambda s: (s[14:19].sum(), s[19:24].sum())  # noqa
+    O0, W0 = tot(s0)
+    O1, W1 = tot(s1)
+    assert O1 - O0 == pytest.approx(b["in_O2"] + b["out_O2"] - b["J"], abs=1e-12 * O0)
+    assert W1 - W0 == pytest.approx(b["in_H2O"] + b["out_H2O"] + 2 * b["J"], abs=1e-12 * O0)
+
+
 def test_adjoint_refuses_the_pressure_inlet():
     from paper_2103_01444_gb300.lbm import LbmError
     case = dict(CASES["film-64x16"](), inlet="pressure", dp_in=1e-3)
