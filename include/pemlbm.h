@@ -104,8 +104,8 @@ typedef struct {
                                   difference of Sec. 4: the channel rows pull from a virtual
                                   column -1 that repeats column 0 with its equilibrium
                                   pressure moved to phi p = 1/3 + dp_in, against 1/3 at the
-                                  outlet (u_in_avg is then unused).  lbm_grad and lbm_vjp
-                                  need inlet_mode 0 (EINVAL otherwise). */
+                                  outlet (u_in_avg is then unused; the du_in of lbm_grad
+                                  and lbm_vjp is then the derivative by dp_in). */
   double dp_in;                /* inlet pressure excess of inlet_mode 1, lattice units,
                                   |dp_in| < 0.01 */
   double alpha_a;              /* kinetics: 0 Tafel, Eq. 13 as printed; > 0 (at most 4)
@@ -251,17 +251,18 @@ lbm_status lbm_bytes_per_cell(lbm_domain *d, double *bytes);
  *   objective 1: the largest temperature of the bottom row in the fields
  *                of step N (K; ties go to the smallest x).
  * Its gradient with respect to the per-cell phi, K and D_O2 of
- * lbm_set_fields (lattice units; K of clear cells gets 0) and to the lattice
- * inlet velocity u_in_avg is computed by the transposed step, applied from
+ * lbm_set_fields (lattice units; K of clear cells gets 0) and to the inlet
+ * drive (the lattice inlet velocity u_in_avg, or dp_in with inlet_mode 1)
+ * is computed by the transposed step, applied from
  * step N back to step 1, with the forward states recomputed from
  * checkpoints every `segment` steps (<= 0: ceil(sqrt(nsteps))).  Memory:
  * about (nsteps/segment + segment) population states.  The gradient of the
  * Fickian interface mode treats each scalar's b (that of its largest
  * diffusivity) as fixed.  J and the gradients go to host memory: dphi, dK,
  * dD_O2 are [ny][nx] doubles (NULL to skip), du_in one double.  EINVAL for
- * objective outside {0, 1}, nsteps outside [2, 2^30] or the pressure inlet
- * (inlet_mode 1, whose boundary links have no transpose here); ENOMEM if
- * the checkpoints do not fit. */
+ * objective outside {0, 1}, nsteps outside [2, 2^30] or stochastic
+ * rounding (lbm_domain_desc.rounding 1); ENOMEM if the checkpoints do not
+ * fit. */
 lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t segment,
                     double *J, double *dphi, double *dK, double *dD_O2, double *du_in);
 
@@ -269,7 +270,7 @@ lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t se
  * [24][ny][nx], the adjoint of the state after one step), writes lam_prev =
  * (d step / d s)^T lam_next and the parameter gradients of
  * <lam_next, step(s)> (host, as in lbm_grad; NULL to skip).  EINVAL for
- * the pressure inlet (inlet_mode 1). */
+ * stochastic rounding (lbm_domain_desc.rounding 1). */
 lbm_status lbm_vjp(lbm_domain *d, const double *lam_next, double *lam_prev, double *dphi,
                    double *dK, double *dD_O2, double *du_in);
 

@@ -793,13 +793,13 @@ struct AdjWork {
     }
     for (auto *b : {&lam[0], &lam[1], &O[0], &O[1]})
       if ((s = b->alloc(planes * r)) != LBM_OK) return s;
-    for (auto *b : {&V[0], &V[1]})
-      if ((s = b->alloc(20 * (size_t)d->ny * r)) != LBM_OK) return s;
+    for (auto *b : {&V[0], &V[1]})   // [outlet, inlet][down, up][10][ny]
+      if ((s = b->alloc(40 * (size_t)d->ny * r)) != LBM_OK) return s;
     // everything starts at zero: lambda^{n-1} of solid cells is zeroed by
     // every step, and the own-use parts of the first lambda are zero
     for (auto *b : {&lam[0], &lam[1], &O[0], &O[1]})
       CK(cudaMemsetAsync(b->p, 0, planes * r, d->stream));
-    for (auto *b : {&V[0], &V[1]}) CK(cudaMemsetAsync(b->p, 0, 20 * (size_t)d->ny * r, d->stream));
+    for (auto *b : {&V[0], &V[1]}) CK(cudaMemsetAsync(b->p, 0, 40 * (size_t)d->ny * r, d->stream));
     for (auto *b : {&gphi, &gK, &gD})
       if ((s = b->alloc(r * d->plane)) != LBM_OK) return s;
     for (auto *b : {&tphi, &tK, &tD})
@@ -973,7 +973,6 @@ lbm_status lbm_vjp(lbm_domain *d, const double *lam_next, double *lam_prev, doub
   lbm_status s = check_ready(d);
   if (s != LBM_OK) return s;
   if (!lam_next || !lam_prev) return fail(LBM_EINVAL, "null argument");
-  if (d->prm.inlet_mode != 0) return fail(LBM_EINVAL, "the adjoint needs the velocity inlet (inlet_mode 0)");
   if (d->desc.rounding != 0) return fail(LBM_EINVAL, "the adjoint needs round-to-nearest storage");
   AdjWork w;
   if ((s = w.alloc(d)) != LBM_OK) return s;
@@ -991,7 +990,6 @@ lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t se
   lbm_status s = check_ready(d);
   if (s != LBM_OK) return s;
   if (objective != 0 && objective != 1) return fail(LBM_EINVAL, "objective must be 0 or 1");
-  if (d->prm.inlet_mode != 0) return fail(LBM_EINVAL, "the adjoint needs the velocity inlet (inlet_mode 0)");
   if (d->desc.rounding != 0) return fail(LBM_EINVAL, "the adjoint needs round-to-nearest storage");
   if (nsteps < 2 || nsteps > (1LL << 30)) return fail(LBM_EINVAL, "nsteps outside [2, 2^30]");
   const int64_t N = nsteps;

@@ -3,7 +3,8 @@
 // The step maps the post-collision state s^{n-1} to s^n cell by cell:
 // s^n(x) = C_x(P_x(s^{n-1}), theta_x), where P_x pulls the 24 populations
 // (plain links from neighbours, boundary links from the cell itself, the
-// outlet's virtual cells, the inlet velocity) and C_x relaxes them (Eq. 1,
+// virtual cells of the outlet and of the pressure inlet, the inlet velocity)
+// and C_x relaxes them (Eq. 1,
 // 8, 10) with the catalyst terms (Eq. 12-17).  Every plain link (y, q) of
 // s^{n-1} has exactly one consumer, the fluid cell y + e_q, so the transpose
 // of the pull is a push: the consumer writes the adjoint of what it pulled
@@ -15,12 +16,13 @@
 //     accumulates the parameter adjoints of x.  Catalyst cells of the
 //     volumetric mode also read their own state; that adjoint goes to O(x).
 //     Solid cells zero their own lambda^{n-1}.
-//   k_adj_edge (one thread per listed edge cell): the same for cells with
+//   k_adj_edge (one warp per listed edge cell): the same for cells with
 //     boundary links; the adjoint of values taken from the cell's own state
-//     goes to O(x, q), the outlet's uses of the cells above and below to V.
+//     goes to O(x, q), a virtual column's uses of the cells above and below
+//     to V.
 // At a cell that uses its own state, lambda^{n-1}(y, q) is therefore split:
 // the pushed value (only if y + e_q is a fluid consumer) + O(y, q) + the
-// outlet terms.  The next reverse step adds the parts when it reads lambda
+// virtual-column terms.  The next reverse step adds the parts when it reads lambda
 // (O and V are double-buffered for that); k_adj_fix adds them in place once,
 // after the last step, for a caller that reads lambda itself.
 // Storage is the domain's storage type S; arithmetic is R.
@@ -67,11 +69,12 @@ template <typename R> struct AdjBufs {
                      // at own-use cells only the pushed links are valid, the
                      // rest of lambda^n is O_in / V_in
   R *O;              // own-use adjoints of this step [24][plane] (own-use cells only)
-  R *V;              // outlet column of this step: [2][10][ny] (down: from y+1 to y, up: from y-1 to y)
+  R *V;              // virtual columns of this step: [side][2][10][ny], side 0 the outlet,
+                     // 1 the pressure inlet (down: from y+1 to y, up: from y-1 to y)
   const R *O_in;     // the same two left by the previous reverse step
   const R *V_in;
   R *gphi, *gK, *gD;        // per-cell parameter gradients of the current segment [plane]
-  double *gU;               // d objective / d u_in_avg
+  double *gU;               // d objective / d u_in_avg (velocity inlet) or d dp_in (pressure)
   R *lam_out;        // lambda^{n-1} [24][plane] (pushed links)
   const uint32_t *pushed;   // per edge cell: bit q set if link q has a fluid consumer
 };
@@ -292,10 +295,23 @@ template <typename R> __device__ __forceinline__ R dinlet_du(const KArgsT<R> &a,
 // of a warp reverses one link of the same cell (shared memory).
 template <typename R> __device__ __forceinline__ void acc_shared(R *p, R v) { atomicAdd(p, v); }
 
+// Columns whose cells feed a virtual column of the previous step: the outlet
+// (x = nx - 1) and, with the pressure inlet, x = 0.  Their cross-row
+// adjoints live in B.V as [side][down, up][10][ny], side 0 the outlet and 1
+// the inlet (vcol_side gives the offset of the side in units of ny).
+template <typename R>
+__device__ __forceinline__ bool has_vcol(const KArgsT<R> &a, int x) {
+  return !a.periodic && (x == a.nx - 1 || (x == 0 && a.inlet_pressure));
+}
+template <typename R>
+__device__ __forceinline__ int vcol_side(const KArgsT<R> &a, int x) {
+  return x == a.nx - 1 ? 0 : 20;
+}
+
 // Reverse of the pull of one flow link i at edge cell (x, y).  lam is the
 // adjoint of the pulled value; it is pushed to lambda^{n-1} of the source
-// (plain link, `out`), or goes to Oacc (own populations), the outlet's
-// virtual-cell adjoints or the inlet velocity.  Oacc, Vdn, Vup and lip_own
+// (plain link, `out`), or goes to Oacc (own populations), the virtual
+// cells' adjoints (outlet, pressure inlet) or the inlet drive.  Oacc, Vdn, Vup and lip_own
 // are shared by the lanes of the cell; lU is the lane's own.
 template <typename S, typename R>
 __device__ __forceinline__ void pull_flow_rev(const Pops<S> &src, const KArgsT<R> &a,
@@ -313,19 +329,30 @@ __device__ __forceinline__ void pull_flow_rev(const Pops<S> &src, const KArgsT<R
   if (sx < 0 || sx >= a.nx) {
     if (a.periodic) {
       sx = sx < 0 ? sx + a.nx : sx - a.nx;
-    } else if (sx < 0) {
-      acc_shared(&Oacc[opi], lam);
-      if (m & M_INLET) lU += lam * R(6) * w9<R>(i) * R(ex9(i)) * dinlet_du<R>(a, R(y) - R(0.5) * R(ey9(i)));
-      return;
     } else {
-      const int vx = a.nx - 1;
+      const bool in = sx < 0;
+      if (in && !(a.inlet_pressure && (m & M_INLET))) {   // velocity inlet, or a wall
+        acc_shared(&Oacc[opi], lam);
+        if (m & M_INLET)
+          lU += lam * R(6) * w9<R>(i) * R(ex9(i)) * dinlet_du<R>(a, R(y) - R(0.5) * R(ey9(i)));
+        return;
+      }
+      // outlet, or the pressure inlet: the virtual column repeats column vx
+      // at the source row with its pressure moved (by dp_in at the inlet)
+      const int vx = in ? 0 : a.nx - 1;
+      const long long vc = (long long)sy * a.nxp + vx;
+      if (in && !(mask[vc] & M_INLET)) {               // the GDL's end wall
+        acc_shared(&Oacc[opi], lam);
+        return;
+      }
       R d[9];
 #pragma unroll
       for (int k = 0; k < 9; ++k) d[k] = R(src.at(k, vx, sy));
       const R jx = d[1] - d[3] + d[5] - d[6] - d[7] + d[8];
       const R jy = d[2] - d[4] + d[5] + d[6] - d[7] - d[8];
-      const R ipv = pal[mid[(long long)sy * a.nxp + vx]].inv_phi;
+      const R ipv = pal[mid[vc]].inv_phi;
       const R ldP = lam9<R>(i) * lam;
+      if (in) lU += ldP;                               // d value / d dp_in
       R lv[10];
 #pragma unroll
       for (int k = 0; k < 9; ++k)
@@ -531,7 +558,7 @@ k_adj_edge(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
     R lin[24];      // lambda^n of the cell
     R lpull[24];    // adjoints of the pulled values
     R O[24];        // own-use adjoints
-    R V[20];        // outlet: 10 down (to y - 1's use), 10 up
+    R V[20];        // virtual column: 10 down (to y - 1's use), 10 up
     R lip, lw1[3];
   };
   __shared__ Shared sh_all[kEdgeWarps];
@@ -544,7 +571,8 @@ k_adj_edge(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
   const uint8_t m = mask[c];
   const Pops<S> src{src_p, a.plane, a.nxp};
   const MatCoef<R> mc = pal[mid[c]];
-  const bool outlet = !a.periodic && x == a.nx - 1;
+  const bool vcol = has_vcol(a, x);
+  const int vs = vcol_side(a, x);
   // ---- phase 1 (lane q): pull link q, read lambda^n of link q
   if (lane < 24) {
     const int q = lane, l = plane_link(q);
@@ -557,9 +585,9 @@ k_adj_edge(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
     const uint32_t pbits = lam_complete ? 0xffffffffu : B.pushed[t];
     R lv = ((pbits >> q) & 1u) ? ld_r(B.lam + q * P + c) : R(0);
     lv += ld_r(B.O_in + q * P + c);
-    if (outlet && q < 9) {
-      if (y + 1 < a.ny) lv += ld_r(B.V_in + (0 * 10 + q) * a.ny + (y + 1));
-      if (y - 1 >= 0) lv += ld_r(B.V_in + (1 * 10 + q) * a.ny + (y - 1));
+    if (vcol && q < 9) {
+      if (y + 1 < a.ny) lv += ld_r(B.V_in + (vs + 0 * 10 + q) * a.ny + (y + 1));
+      if (y - 1 >= 0) lv += ld_r(B.V_in + (vs + 1 * 10 + q) * a.ny + (y - 1));
     }
     sh.lin[q] = lv;
     sh.O[q] = R(0);
@@ -679,20 +707,20 @@ k_adj_edge(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
     }
   }
   __syncwarp();
-  // ---- phase 4: own-use and outlet adjoints out; parameters (lane 0)
+  // ---- phase 4: own-use and virtual-column adjoints out; parameters (lane 0)
   if (lane < 24) B.O[lane * P + c] = sh.O[lane];
-  if (outlet && lane < 10) {
-    B.V[(0 * 10 + lane) * a.ny + y] = sh.V[lane];
-    B.V[(1 * 10 + lane) * a.ny + y] = sh.V[10 + lane];
+  if (vcol && lane < 10) {
+    B.V[(vs + 0 * 10 + lane) * a.ny + y] = sh.V[lane];
+    B.V[(vs + 1 * 10 + lane) * a.ny + y] = sh.V[10 + lane];
   }
   if (lane == 0) {
     lip += sh.lip;
 #pragma unroll
     for (int s = 0; s < 3; ++s) lw1[s] += sh.lw1[s];
-    if (outlet) {   // the outlet's use of this cell's 1/phi in the previous step
+    if (vcol) {   // the virtual column's use of this cell's 1/phi in the previous step
       R vsum_ip = 0;
-      if (y + 1 < a.ny) vsum_ip += ld_r(B.V_in + (0 * 10 + 9) * a.ny + (y + 1));
-      if (y - 1 >= 0) vsum_ip += ld_r(B.V_in + (1 * 10 + 9) * a.ny + (y - 1));
+      if (y + 1 < a.ny) vsum_ip += ld_r(B.V_in + (vs + 0 * 10 + 9) * a.ny + (y + 1));
+      if (y - 1 >= 0) vsum_ip += ld_r(B.V_in + (vs + 1 * 10 + 9) * a.ny + (y - 1));
       gacc[0] += -vsum_ip * mc.inv_phi * mc.inv_phi;
     }
     param_rev<R>(a, mc, fickian, lphi, ldarcy, lforch, ll0, ll1, lip, lb1, lw1[1], lq1_1,
@@ -701,7 +729,7 @@ k_adj_edge(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
     B.gK[c] = gacc[1];
     B.gD[c] = gacc[2];
   }
-  // inlet velocity: warp sum, one FP64 atomic per warp that has inlet links
+  // inlet drive (velocity, or dp_in): warp sum, one FP64 atomic per warp that has inlet links
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) lU += __shfl_down_sync(0xffffffffu, lU, off);
   if (lane == 0 && lU != R(0)) atomicAdd(B.gU, (double)lU);
@@ -711,8 +739,8 @@ k_adj_edge(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
 // cells (edge cells, then catalyst cells of the volumetric mode), one thread
 // per (link q, entry of `cells`), q-major so that neighbouring threads touch
 // neighbouring cells: lambda(y, q) = pushed value (if y + e_q is a fluid
-// consumer) + O(y, q) + the outlet's uses of y (B.lam_out, B.O, B.V: the
-// buffers of that step); the outlet's 1/phi term goes to gphi.
+// consumer) + O(y, q) + the virtual columns' uses of y (B.lam_out, B.O, B.V:
+// the buffers of that step); their 1/phi terms go to gphi.
 template <typename R>
 __global__ void __launch_bounds__(256)
 k_adj_fix(const uint8_t *__restrict__ mask, const uint16_t *__restrict__ mid,
@@ -723,7 +751,8 @@ k_adj_fix(const uint8_t *__restrict__ mask, const uint16_t *__restrict__ mid,
   const int q = (int)(t / ncells);
   const long long c = cells[t - (long long)q * ncells], P = a.plane;
   const int y = (int)(c / a.nxp), x = (int)(c - (long long)y * a.nxp);
-  const bool outlet = !a.periodic && x == a.nx - 1;
+  const bool vcol = has_vcol(a, x);
+  const int vs = vcol_side(a, x);
   const int ex = ex9(plane_link(q)), ey = ey9(plane_link(q));
   int cx = x + ex;
   const int cy = y + ey;
@@ -734,15 +763,15 @@ k_adj_fix(const uint8_t *__restrict__ mask, const uint16_t *__restrict__ mid,
   }
   R l = pushed ? B.lam_out[q * P + c] : R(0);
   l += B.O[q * P + c];
-  if (outlet && q < 9) {
-    if (y + 1 < a.ny) l += B.V[(0 * 10 + q) * a.ny + (y + 1)];
-    if (y - 1 >= 0) l += B.V[(1 * 10 + q) * a.ny + (y - 1)];
+  if (vcol && q < 9) {
+    if (y + 1 < a.ny) l += B.V[(vs + 0 * 10 + q) * a.ny + (y + 1)];
+    if (y - 1 >= 0) l += B.V[(vs + 1 * 10 + q) * a.ny + (y - 1)];
   }
   B.lam_out[q * P + c] = l;
-  if (outlet && q == 0) {
+  if (vcol && q == 0) {
     R vsum_ip = 0;
-    if (y + 1 < a.ny) vsum_ip += B.V[(0 * 10 + 9) * a.ny + (y + 1)];
-    if (y - 1 >= 0) vsum_ip += B.V[(1 * 10 + 9) * a.ny + (y - 1)];
+    if (y + 1 < a.ny) vsum_ip += B.V[(vs + 0 * 10 + 9) * a.ny + (y + 1)];
+    if (y - 1 >= 0) vsum_ip += B.V[(vs + 1 * 10 + 9) * a.ny + (y - 1)];
     const R ip = pal[mid[c]].inv_phi;
     B.gphi[c] += -vsum_ip * ip * ip;
   }

@@ -229,7 +229,9 @@ class Domain:
 
     def grad(self, objective: int = 0, nsteps: int = 100, segment: int = 0):
         """Objective after nsteps from the current state and its gradient:
-        (J, {"phi", "K", "D_O2": [ny][nx] arrays, "u_in": float})."""
+        (J, {"phi", "K", "D_O2": [ny][nx] arrays, "u_in": float}); "u_in" is
+        the derivative by the inlet drive, u_in_avg (inlet_mode 0) or dp_in
+        (inlet_mode 1)."""
         J, du = C.c_double(), C.c_double()
         g = {k: np.zeros((self.ny, self.nx)) for k in ("phi", "K", "D_O2")}
         _check(self.L.lbm_grad(self.h, int(objective), int(nsteps), int(segment), C.byref(J),
@@ -348,11 +350,11 @@ class Batch:
 
 
 def cathode_objective():
-    """torch.autograd.Function over the lattice material and inlet velocity:
+    """torch.autograd.Function over the lattice material and inlet drive:
     CathodeObjective.apply(phi, K, D_O2, u_in, domain, fields, params,
     objective, nsteps, segment) sets the domain's material (phi, K, D_O2 from
-    the tensors, alpha_T, D_H2O, rho_cp_ratio from `fields`) and u_in_avg,
-    resets it, and returns the objective after nsteps; backward returns the
+    the tensors, alpha_T, D_H2O, rho_cp_ratio from `fields`) and the drive
+    (u_in_avg, or dp_in when params["inlet_mode"] is 1) to u_in, resets it, and returns the objective after nsteps; backward returns the
     adjoint gradients computed by lbm_grad."""
     import torch
 
@@ -360,7 +362,7 @@ def cathode_objective():
         @staticmethod
         def forward(ctx, phi, K, D_O2, u_in, domain, fields, params, objective, nsteps, segment):
             p = dict(params)
-            p["u_in_avg"] = float(u_in)
+            p["dp_in" if p.get("inlet_mode", 0) == 1 else "u_in_avg"] = float(u_in)
             domain.set_params(p)
             domain.set_fields(phi.detach().cpu().double().numpy(), K.detach().cpu().double().numpy(),
                               fields["alpha_T"], D_O2.detach().cpu().double().numpy(),

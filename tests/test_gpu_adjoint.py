@@ -43,7 +43,14 @@ def case_of(name):
     if name == "vol-bv1":
         return dict(workloads.small_cathode(nx=36, ny=20, reaction_mode=1, V_op=1.0, seed=22),
                     alpha_a=0.5)
+    if name.endswith("-p"):    # the pressure-driven inlet of Sec. 4
+        return dict(case_of(name[:-2]), inlet="pressure", dp_in=1e-3)
     raise KeyError(name)
+
+
+def drive_key(case):
+    """The inlet drive that du_in differentiates by."""
+    return "dp_in" if case.get("inlet") == "pressure" else "u_in_avg"
 
 
 def gpu(case, precision="fp64", mode=0):
@@ -51,11 +58,13 @@ def gpu(case, precision="fp64", mode=0):
     return Domain.from_case(case, precision=precision, interface_mode=mode)
 
 
-@pytest.mark.parametrize("name", ["film", "vol", "grains", "film-bv", "vol-bv"])
+@pytest.mark.parametrize("name", ["film", "vol", "grains", "film-bv", "vol-bv", "film-p",
+                                  "grains-p"])
 @pytest.mark.parametrize("mode", [0, 1])
 def test_one_step_transpose_dot_product(name, mode):
     """<lam, (step(s + e v) - step(s - e v)) / 2e> = <step^T lam, v>, and the
-    same for the parameters phi, K, D_O2 and u_in (FP64 storage)."""
+    same for the parameters phi, K, D_O2 and the inlet drive (u_in_avg, or
+    dp_in with the pressure inlet) (FP64 storage)."""
     from paper_2103_01444_gb300.units import cathode_params
     case = case_of(name)
     d = gpu(case, mode=mode)
@@ -116,19 +125,20 @@ def test_one_step_transpose_dot_product(name, mode):
         fdo = np.sum(lam * diff_o) / (2 * h)
         assert abs(fdo - adp) <= 1e-4 * max(abs(fdo), abs(adp), 1e-12), (key, fdo, adp)
     d.set_fields(**fields)
-    h = 1e-6 * params["u_in_avg"]
-    diff = (step_from(s0, params=dict(params, u_in_avg=params["u_in_avg"] + h)) -
-            step_from(s0, params=dict(params, u_in_avg=params["u_in_avg"] - h)))
+    key = drive_key(case)
+    h = 1e-6 * params[key]
+    diff = (step_from(s0, params=dict(params, **{key: params[key] + h})) -
+            step_from(s0, params=dict(params, **{key: params[key] - h})))
     fdu = np.sum(lam * diff) / (2 * h)
     assert abs(fdu - g["u_in"]) <= 1e-4 * max(abs(fdu), 1e-12), (fdu, g["u_in"])
 
 
-def oracle_objective(case, mode, objective, N, material=None, u_in=None, x_star=None):
+def oracle_objective(case, mode, objective, N, material=None, drive=None, x_star=None):
     params, mat0, solid = lattice_problem(case, interface_mode=mode)
     base = Oracle(params, mat0, solid)          # the initial state is held fixed
     p = dict(params)
-    if u_in is not None:
-        p["u_in_avg"] = u_in
+    if drive is not None:
+        p[drive_key(case)] = drive
     o = Oracle(p, material if material is not None else mat0, solid)
     o.f[...] = base.f
     o.g[...] = base.g
@@ -143,11 +153,13 @@ def oracle_objective(case, mode, objective, N, material=None, u_in=None, x_star=
 @pytest.mark.parametrize("name,mode,objective", [("film", 0, 0), ("film", 1, 1), ("vol", 0, 0),
                                                  ("vol", 1, 0), ("grains", 0, 1),
                                                  ("film-bv1", 0, 0), ("vol-bv1", 1, 0),
-                                                 ("film-bv1", 0, 1)])
+                                                 ("film-bv1", 0, 1), ("film-p", 0, 0),
+                                                 ("grains-p", 1, 1), ("vol-p", 0, 0)])
 def test_gradient_matches_oracle_finite_differences(name, mode, objective):
     """Gradients of the objective after 40 steps (checkpoint segments of 7)
     w.r.t. phi, K, D_O2 (random directions over the GDL and on single cells)
-    and u_in against FP64 central differences of the oracle: 1e-3 relative."""
+    and the inlet drive against FP64 central differences of the oracle: 1e-3
+    relative."""
     case = case_of(name)
     N = 40
     d = gpu(case, mode=mode)
@@ -184,12 +196,12 @@ def test_gradient_matches_oracle_finite_differences(name, mode, objective):
             # (about 1e-4 of J0 per unit h near open circuit) count as zero
             scale = max(abs(fd), abs(ad), (1e-3 if "bv" in name else 1e-5) * abs(J0))
             assert abs(fd - ad) <= 1e-3 * scale, (key, fd, ad)
-    hu = (1e-5 if "bv" in name else 1e-6) * params["u_in_avg"]
-    Jp, _ = oracle_objective(case, mode, objective, N, u_in=params["u_in_avg"] + hu, x_star=xs)
-    Jm, _ = oracle_objective(case, mode, objective, N, u_in=params["u_in_avg"] - hu, x_star=xs)
+    u0 = params[drive_key(case)]
+    hu = (1e-5 if "bv" in name else 1e-6) * u0
+    Jp, _ = oracle_objective(case, mode, objective, N, drive=u0 + hu, x_star=xs)
+    Jm, _ = oracle_objective(case, mode, objective, N, drive=u0 - hu, x_star=xs)
     fdu = (Jp - Jm) / (2 * hu)
-    assert abs(fdu - g["u_in"]) <= 1e-3 * max(abs(fdu), 1e-5 * abs(J0) / params["u_in_avg"]), \
-        (fdu, g["u_in"])
+    assert abs(fdu - g["u_in"]) <= 1e-3 * max(abs(fdu), 1e-5 * abs(J0) / u0), (fdu, g["u_in"])
 
 
 def test_fp32_adjoint_close_to_fp64():

@@ -207,15 +207,6 @@ def test_balances_match_oracle_and_close_the_budgets(name, inlet):
     assert W1 - W0 == pytest.approx(b["in_H2O"] + b["out_H2O"] + 2 * b["J"], abs=1e-12 * O0)
 
 
-def test_adjoint_refuses_the_pressure_inlet():
-    from paper_2103_01444_gb300.lbm import LbmError
-    case = dict(CASES["film-64x16"](), inlet="pressure", dp_in=1e-3)
-    d = gpu_domain(case, "fp64")
-    d.step(2)
-    with pytest.raises(LbmError, match="EINVAL.*velocity inlet"):
-        d.grad(0, 4)
-
-
 @pytest.fixture(scope="module")
 def cathode_200x40_oracles():
     case = workloads.cathode_200x40()
