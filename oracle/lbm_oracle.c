@@ -161,6 +161,10 @@ typedef struct {
   int32_t interface_mode;   /* 0: per-cell b, fixed Q (Eq. 10 as printed);
                                1: Fickian: one b per scalar, per-cell flux rate */
   int32_t inlet_mode;       /* 0: parabolic velocity inlet; 1: pressure inlet (Sec. 4) */
+  int32_t closed_x;         /* 1: no-slip walls at both x ends (the cavities of Sec. 3) */
+  int32_t wall_dirichlet;   /* bit 3k+s: scalar s held at C_wall[3k+s] on wall k
+                               (0 the x = 0 end outside inlet rows, 1 the x = nx-1 end,
+                               2 the bottom); otherwise insulated */
   double nu;                /* kinematic viscosity; 3 nu = tau - 1/2 (Eq. 8) */
   double u_in_avg;          /* mean inlet velocity over the channel rows */
   double body_force_x;      /* uniform body force per unit mass (tests only) */
@@ -175,6 +179,10 @@ typedef struct {
   double dp_in;             /* pressure inlet: phi p there is rho0/3 + dp_in */
   double alpha_a;           /* anodic transfer coefficient of the Butler-Volmer
                                branch; 0 = Tafel kinetics, Eq. 13 as printed */
+  double buoy_gx, buoy_gy;  /* Boussinesq buoyancy of the natural-convection cases
+                               (Sec. 3): force per unit mass (buoy_gx, buoy_gy)(T - T_buoy) */
+  double T_buoy;
+  double C_wall[9];         /* wall values of wall_dirichlet, [wall][scalar] */
 } orc_params;
 
 /* Per-cell material, lattice units. K = +inf marks clear fluid.  sigma is
@@ -213,7 +221,7 @@ void orc_build_mask(const orc_params *P, const uint8_t *solid, uint8_t *mask) {
       if (x == nx - 1) m |= B_XHI;
       if (y == ny - 1) m |= B_YHI;
       if (y == 0) m |= B_YLO;
-      if (reg == REG_CLEAR && x == 0 && !P->periodic_x) m |= B_INLET;
+      if (reg == REG_CLEAR && x == 0 && !P->periodic_x && !P->closed_x) m |= B_INLET;
       mask[IDX(x, y)] = m;
     }
   for (int y = 0; y < ny; ++y)
@@ -417,6 +425,20 @@ static double inlet_u(const orc_params *P, double y) {
   return 6.0 * P->u_in_avg * s * (1.0 - s);
 }
 
+/* Whether scalar s is held at a fixed value on wall k (0 the x = 0 end,
+ * 1 the x = nx-1 end, 2 the bottom). */
+static int wall_fixed(const orc_params *P, int k, int s) {
+  return (P->wall_dirichlet >> (3 * k + s)) & 1;
+}
+
+/* Body force per unit mass at temperature T: the uniform force along x of
+ * the closed-form tests plus the Boussinesq buoyancy of Sec. 3's
+ * natural-convection cases, gamma (T - T_buoy). */
+static void body_force(const orc_params *P, double T, double *Gx, double *Gy) {
+  *Gx = P->body_force_x + P->buoy_gx * (T - P->T_buoy);
+  *Gy = P->buoy_gy * (T - P->T_buoy);
+}
+
 /* --------------------------------------------------------------- state */
 
 /* Initial state: f = w rho0 (rest), g = D2Q5 equilibrium of the inlet values
@@ -538,6 +560,9 @@ static void stream(const orc_params *P, const orc_material *mat, const uint8_t *
             } else {
               val = fs[io * n + c];
             }
+          } else if (sx >= nx && P->closed_x) {
+            val = fs[io * n + c];                              /* end wall */
+            diag[D_OUT + 0] += val;
           } else if (sx >= nx) {
             /* outlet: the virtual column nx repeats column nx-1 (fully
              * developed flow), with its equilibrium pressure part moved to
@@ -582,7 +607,10 @@ static void stream(const orc_params *P, const orc_material *mat, const uint8_t *
           double own_out = gq[io * n + c];
           double val;
           if (sy < 0) {
-            if (surface) {
+            if (wall_fixed(P, 2, s)) {
+              /* fixed bottom value (anti-bounce-back at the halfway wall) */
+              val = -own_out + 2.0 * w1 * P->C_wall[6 + s];
+            } else if (surface) {
               if (s == 1) {
                 /* net O2 flux J = kS C_w - kSa with the wall value
                  * C_w = (own_out + val)/(2 w1) and J = own_out - val */
@@ -604,9 +632,15 @@ static void stream(const orc_params *P, const orc_material *mat, const uint8_t *
               if (m & B_INLET) {
                 val = -own_out + 2.0 * w1 * Cin[s];
                 diag[D_IN + 1 + s] += val - own_out;
+              } else if (wall_fixed(P, 0, s)) {
+                val = -own_out + 2.0 * w1 * P->C_wall[s];
+                diag[D_IN + 1 + s] += val - own_out;
               } else {
                 val = own_out;
               }
+            } else if (sx >= nx && P->closed_x) {
+              val = wall_fixed(P, 1, s) ? -own_out + 2.0 * w1 * P->C_wall[3 + s] : own_out;
+              diag[D_OUT + 1 + s] += val;
             } else if (sx >= nx) {
               int x2 = nx - 2, tx = x2 - EX5[i], ty = y - EY5[i];
               size_t c2 = IDX(x2, y);
@@ -666,7 +700,13 @@ static cell_macro macros_at(const orc_params *P, const orc_material *mat, size_t
     vy += EY9[i] * f[i * n + c] / rho0;
     if (i >= 1) s18 += f[i * n + c];
   }
-  vx += 0.5 * pc.phi * P->body_force_x;
+  /* the force enters Eq. 8's auxiliary velocity with half a time step; the
+   * buoyancy takes the cell's temperature after streaming */
+  double T = 0, Gx, Gy;
+  for (int i = 0; i < 5; ++i) T += g[(0 * 5 + i) * n + c];
+  body_force(P, T, &Gx, &Gy);
+  vx += 0.5 * pc.phi * Gx;
+  vy += 0.5 * pc.phi * Gy;
   orc_velocity(pc.l0, pc.l1, vx, vy, &r.ux, &r.uy);
   /* velocity carried by the scalars: the flow's, or an imposed one (tests) */
   r.usx = mat->u_imposed ? mat->u_imposed[c] : r.ux;
@@ -711,10 +751,11 @@ void orc_step(const orc_params *P, const orc_material *mat, const uint8_t *mask,
       }
       cell_macro mc = macros_at(P, mat, n, c, f, g);
       porous_coef pc = porous(P, mat->phi[c], mat->K[c]);
-      /* Eq. 7 force (plus the optional uniform body force) */
-      double un = sqrt(mc.ux * mc.ux + mc.uy * mc.uy);
-      double Fx = -pc.darcy * mc.ux - pc.forch * un * mc.ux + pc.phi * P->body_force_x;
-      double Fy = -pc.darcy * mc.uy - pc.forch * un * mc.uy;
+      /* Eq. 7 force plus phi times the body force (uniform and buoyant) */
+      double un = sqrt(mc.ux * mc.ux + mc.uy * mc.uy), Gx, Gy;
+      body_force(P, mc.C[0], &Gx, &Gy);
+      double Fx = -pc.darcy * mc.ux - pc.forch * un * mc.ux + pc.phi * Gx;
+      double Fy = -pc.darcy * mc.uy - pc.forch * un * mc.uy + pc.phi * Gy;
       /* Eq. 1 in moment space */
       double m[9], meq[9], G[9], ms[9];
       for (int k = 0; k < 9; ++k) {

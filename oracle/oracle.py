@@ -40,6 +40,7 @@ class Params(C.Structure):
         ("reaction_mode", C.c_int32), ("periodic_x", C.c_int32),
         ("forchheimer", C.c_int32), ("top_dirichlet", C.c_int32),
         ("interface_mode", C.c_int32), ("inlet_mode", C.c_int32),
+        ("closed_x", C.c_int32), ("wall_dirichlet", C.c_int32),
         ("nu", C.c_double), ("u_in_avg", C.c_double), ("body_force_x", C.c_double),
         ("V_op", C.c_double), ("T_in", C.c_double), ("C_O2_in", C.c_double),
         ("C_H2O_in", C.c_double),
@@ -49,7 +50,8 @@ class Params(C.Structure):
         ("dU0dT", C.c_double), ("U0_0", C.c_double), ("x_ref", C.c_double),
         ("dx_cm", C.c_double), ("dt_s", C.c_double), ("delta_cl_cm", C.c_double),
         ("c_tot", C.c_double), ("rho_cp_f", C.c_double), ("dp_in", C.c_double),
-        ("alpha_a", C.c_double),
+        ("alpha_a", C.c_double), ("buoy_gx", C.c_double), ("buoy_gy", C.c_double),
+        ("T_buoy", C.c_double), ("C_wall", C.c_double * 9),
     ]
 
 
@@ -115,7 +117,10 @@ class Oracle:
 
     def __init__(self, params: dict, material: dict, solid=None):
         self.L = lib()
-        self.P = Params(**params)
+        p = dict(params)
+        if "C_wall" in p:   # [wall][scalar] values, flattened
+            p["C_wall"] = (C.c_double * 9)(*np.asarray(p["C_wall"], np.float64).ravel())
+        self.P = Params(**p)
         nx, ny = self.P.nx, self.P.ny
         self.nx, self.ny = nx, ny
         self._mat_arrays = {}

@@ -65,7 +65,10 @@ def heat_capacity_ratio(phi, rc=RHOCP_RATIO):
 
 
 def lattice_problem(case: dict, forchheimer: int = 1, interface_mode: int = 0):
-    """Physical workload dict -> (params dict, material dict, solid)."""
+    """Physical workload dict -> (params dict, material dict, solid); the
+    validation cases of Sec. 3 (case["kind"]) go to validation_problem."""
+    if case.get("kind"):
+        return validation_problem(case, forchheimer, interface_mode)
     nx, ny = case["nx"], case["ny"]
     ny_cl, ny_gdl = case["ny_cl"], case["ny_gdl"]
     dx = case["h_gdl_cm"] / ny_gdl
@@ -113,7 +116,8 @@ def base_params(nx, ny, **kw):
              C_H2O_top=0.0, aj0_ref=0.0, T_ref_kin=T_REF_KIN, E_act=E_ACT, alpha_c=ALPHA_C,
              F=FARADAY, R=R_GAS, dU0dT=DU0_DT, U0_0=U0_0, x_ref=X_REF, dx_cm=1e-3,
              dt_s=1e-6, delta_cl_cm=DELTA_CL_CM, c_tot=C_TOT, rho_cp_f=RHO_CP_F,
-             inlet_mode=0, dp_in=0.0, alpha_a=0.0)
+             inlet_mode=0, dp_in=0.0, alpha_a=0.0, closed_x=0, wall_dirichlet=0, buoy_gx=0.0,
+             buoy_gy=0.0, T_buoy=343.0, C_wall=[0.0] * 9)
     p.update(kw)
     return p
 
@@ -122,3 +126,61 @@ def uniform_material(nx, ny, phi=1.0, K=math.inf, alpha_T=0.05, D_O2=0.05, D_H2O
     full = lambda v: np.full((ny, nx), float(v))  # noqa: E731
     return dict(phi=full(phi), K=full(K), alpha_T=full(alpha_T), D_O2=full(D_O2),
                 D_H2O=full(D_H2O))
+
+
+# Readings for the validation cases (Sec. 3 gives only their dimensionless
+# groups): the buoyant velocity scale alpha sqrt(Ra Pr)/L is 0.05 in lattice
+# units, alpha at most 0.1; sigma = 1.
+BUOYANT_VELOCITY = 0.05
+ALPHA_CAP = 0.1
+
+
+def validation_problem(case: dict, forchheimer: int = 1, interface_mode: int = 0):
+    """Cavity (natural convection, clear or porous) and Kang's surface
+    reaction -> (params, material, solid).
+
+    Cavity of side L = n cells (walls halfway outside the end cells):
+    Ra = g beta dT L^3 / (nu alpha) and Pr = nu / alpha fix
+    gamma = g beta = Ra nu alpha / (dT L^3); Da = K / L^2 in the porous
+    cavity.  Left wall T_hot, right wall T_cold, bottom T_hot when heated,
+    the rest insulated; gravity along -y, so the buoyancy per unit mass is
+    +gamma (T - T_mean) along y.
+
+    Kang: fluid at rest, C0 on the left wall, first-order consumption
+    k C_w on the bottom wall with Da = k ny / D.  The kinetics are made
+    linear and heat-free: no activation energy, alpha_c = 0, V = U0, and
+    unit scales so that the film's lattice rate is aj0_ref."""
+    nx, ny = case["nx"], case["ny"]
+    p = base_params(nx, ny, periodic_x=0, closed_x=1, reaction_mode=0,
+                    forchheimer=forchheimer, interface_mode=interface_mode,
+                    E_act=0.0, alpha_c=0.0, dU0dT=0.0, U0_0=0.0, V_op=0.0, T_ref_kin=343.0,
+                    x_ref=1.0, F=0.25, c_tot=1.0, delta_cl_cm=1.0, dx_cm=1.0, dt_s=1.0,
+                    rho_cp_f=1.0)
+    ones = np.ones((ny, nx))
+    if case["kind"] == "cavity":
+        L = float(nx)
+        hot, cold = case["T_hot"], case["T_cold"]
+        mean = 0.5 * (hot + cold)
+        Ra, Pr = case["Ra"], case["Pr"]
+        alpha = min(ALPHA_CAP, BUOYANT_VELOCITY * L / math.sqrt(Ra * Pr))
+        nu = Pr * alpha
+        p.update(nu=nu, T_in=mean, T_top=mean, buoy_gx=0.0, buoy_gy=Ra * nu * alpha / ((hot - cold) * L ** 3),
+                 T_buoy=mean, C_O2_in=0.21, C_H2O_in=0.0,
+                 wall_dirichlet=1 | (1 << 3) | ((1 << 6) if case["heated_bottom"] else 0),
+                 C_wall=[hot, 0.21, 0.0, cold, 0.21, 0.0, hot, 0.21, 0.0])
+        if case.get("Da") is not None:
+            p["ny_gdl"] = ny
+            mat = dict(phi=case["phi"] * ones, K=case["Da"] * L * L * ones)
+        else:
+            mat = dict(phi=ones, K=np.full((ny, nx), np.inf))
+        mat.update(alpha_T=alpha * ones, D_O2=alpha * ones, D_H2O=alpha * ones, sigma=ones)
+        return p, mat, None
+    if case["kind"] == "kang":
+        D = case["D"]
+        p.update(nu=0.1, T_in=343.0, C_O2_in=case["C0"], C_O2_top=case["C0"], C_H2O_in=0.0,
+                 aj0_ref=case["Da"] * D / ny, wall_dirichlet=0b111,
+                 C_wall=[343.0, case["C0"], 0.0] + [0.0] * 6)
+        mat = dict(phi=ones, K=np.full((ny, nx), np.inf), alpha_T=D * ones, D_O2=D * ones,
+                   D_H2O=D * ones, sigma=ones)
+        return p, mat, None
+    raise ValueError(case["kind"])

@@ -17,6 +17,8 @@ A workload is a plain dict:
   solid                 : (ny, nx) uint8 pore-scale solid cells, or None
   V_op, T_in, Re        : operating point (V, K, channel Reynolds number)
   C_O2_in, C_H2O_in     : inlet mole fractions
+The validation cases at the end carry kind="cavity" or kind="kang" and
+their dimensionless groups instead.
 """
 from __future__ import annotations
 
@@ -157,3 +159,32 @@ def small_cathode(nx: int = 64, ny: int = 16, reaction_mode: int = 0, seed: int 
                 ny_gdl=ny_gdl, reaction_mode=reaction_mode, periodic_x=0, h_gdl_cm=H_GDL_CM,
                 phi=phi, K_cm2=K, solid=solid, V_op=V_op, T_in=343.0, Re=Re, C_O2_in=0.21,
                 C_H2O_in=0.0)
+
+
+# ------------------------------------------------- validation workloads
+# The validation cases of Sec. 3, described by their dimensionless groups
+# (the paper plots them for ranges of these numbers; no lattice sizes are
+# given).  Both the product and the oracle map them to lattice parameters
+# with their own code.
+
+def natural_convection_cavity(n: int = 64, Ra: float = 1e4, Pr: float = 0.71,
+                              heated_bottom: bool = False, Da: float | None = None,
+                              phi: float = 1.0, T_hot: float = 348.0,
+                              T_cold: float = 338.0) -> dict:
+    """Square cavity of n x n cells with no-slip walls all round: the left
+    wall hot, the right wall cold, the top insulated; the bottom hot with
+    heated_bottom (the clear-media case of Sec. 3), else insulated (the
+    porous-media case, with Darcy number Da = K / L^2 and porosity phi over
+    the whole cavity).  Gravity points down."""
+    return dict(kind="cavity", nx=n, ny=n, Ra=float(Ra), Pr=float(Pr),
+                heated_bottom=bool(heated_bottom), Da=None if Da is None else float(Da),
+                phi=float(phi), T_hot=float(T_hot), T_cold=float(T_cold))
+
+
+def kang_surface_reaction(nx: int = 96, ny: int = 48, Da: float = 1.0, D: float = 0.1,
+                          C0: float = 0.2) -> dict:
+    """Diffusion with a first-order surface reaction in a rectangle (the
+    third case of Sec. 3): fluid at rest, the reactant held at C0 on the left
+    wall, consumed on the bottom wall at the rate k C with Damkohler number
+    Da = k ny / D, the other walls closed.  D is the lattice diffusivity."""
+    return dict(kind="kang", nx=nx, ny=ny, Da=float(Da), D=float(D), C0=float(C0))

@@ -552,3 +552,148 @@ def test_clear_channel_inlet_outlet():
     u = fl["ux"][:, nx // 2]
     np.testing.assert_allclose(u / u.sum(), par / par.sum(), atol=2e-3)
     assert np.abs(fl["uy"][:, nx // 2]).max() < 1e-6
+
+
+# ------------------------------------------- validation set-ups (Sec. 3)
+def test_fixed_walls_conduction_exact():
+    """Closed box at rest, T held at the halfway x walls, top and bottom
+    insulated: the steady profile is linear between the wall values, and
+    the heat through each wall is alpha dT ny / nx (the discrete flux of a
+    linear profile is exact).  The same with the bottom and top held
+    (bottom wall bit, top_dirichlet): linear in y.  A fixed O2 value on the
+    left wall with the rest closed fills the box with that value."""
+    nx, ny, a = 12, 5, 0.1
+    p = base_params(nx, ny, periodic_x=0, closed_x=1, wall_dirichlet=1 | (1 << 1) | (1 << 3),
+                    C_wall=[350.0, 0.3, 0.0, 340.0, 0.0, 0.0, 0.0, 0.0, 0.0], T_in=345.0)
+    o = Oracle(p, uniform_material(nx, ny, alpha_T=a, D_O2=a))
+    o.step(20000)
+    f = o.fields()
+    x = np.arange(nx) + 0.5
+    assert np.abs(f["T"] - (350.0 - 10.0 * x / nx)).max() < 1e-9
+    assert np.abs(f["C_O2"] - 0.3).max() < 1e-12
+    assert np.abs(f["ux"]).max() == 0.0 and np.abs(f["uy"]).max() == 0.0
+    d = f["diag"]
+    assert d[DIAG["in_T"]] == pytest.approx(a * 10.0 * ny / nx, rel=1e-10)
+    assert d[DIAG["out_T"]] == pytest.approx(-a * 10.0 * ny / nx, rel=1e-10)
+    assert d[DIAG["in_mass"]] == 0.0 and abs(d[DIAG["out_mass"]]) < 1e-15
+    # vertical: bottom held by the wall bit, top by top_dirichlet
+    nx, ny = 4, 10
+    p = base_params(nx, ny, periodic_x=1, wall_dirichlet=1 << 6, C_wall=[0.0] * 6 + [330.0, 0, 0],
+                    top_dirichlet=1, T_top=350.0, T_in=345.0)
+    o = Oracle(p, uniform_material(nx, ny, alpha_T=a))
+    o.step(20000)
+    y = np.arange(ny) + 0.5
+    assert np.abs(o.fields()["T"][:, 0] - (330.0 + 20.0 * y / ny)).max() < 1e-9
+
+
+def buoyant_slot(H, phi=1.0, K=math.inf):
+    """Periodic slot with the bottom at Tb and the top at Tt, gravity along
+    x: T is linear in y and the flow obeys nu u'' - (phi nu / K) u +
+    phi gamma (T - T_buoy) = 0 with no-slip halfway walls."""
+    Tb, Tt, Tr, gam, nu, a = 350.0, 340.0, 343.0, 1e-5, 0.1, 0.1
+    p = base_params(4, H, periodic_x=1, wall_dirichlet=1 << 6, C_wall=[0.0] * 6 + [Tb, 0.21, 0],
+                    top_dirichlet=1, T_top=Tt, T_in=345.0, nu=nu, buoy_gx=gam, T_buoy=Tr,
+                    forchheimer=0)
+    o = Oracle(p, uniform_material(4, H, phi=phi, K=K, alpha_T=a))
+    o.step(40 * H * H)
+    f = o.fields()
+    s = np.arange(H) + 0.5
+    G = lambda s: gam * (Tb + (Tt - Tb) * s / H - Tr)  # noqa: E731
+    if math.isinf(K):
+        eta = s / H
+        A, B = G(0.0), gam * (Tt - Tb)
+        u = H * H / nu * (A * eta * (1 - eta) / 2 + B * eta * (1 - eta ** 2) / 6)
+    else:
+        r = math.sqrt(phi / K)
+        c1 = -(K / nu) * G(0.0)
+        c2 = (-(K / nu) * G(float(H)) - c1 * math.cosh(r * H)) / math.sinh(r * H)
+        u = (K / nu) * G(s) + c1 * np.cosh(r * s) + c2 * np.sinh(r * s)
+    T_err = np.abs(f["T"][:, 0] - (Tb + (Tt - Tb) * s / H)).max() / (Tb - Tt)
+    return np.abs(f["ux"][:, 0] - u).max() / np.abs(u).max(), T_err, np.abs(f["uy"]).max()
+
+
+def test_buoyant_slot_closed_forms():
+    """Boussinesq buoyancy along a periodic slot between held walls: the
+    clear slot has the cubic profile (H^2/nu)[A eta(1-eta)/2 +
+    B eta(1-eta^2)/6] (A = gamma (Tb - T_buoy), B = gamma (Tt - Tb)); the
+    porous slot (Darcy drag, no Forchheimer) the Brinkman solution
+    (K/nu) G(y) + c1 cosh(ry) + c2 sinh(ry), r = sqrt(phi/K), converging at
+    second order."""
+    eu, eT, uy = buoyant_slot(8)
+    assert eu < 1e-4 and eT < 5e-5 and uy < 1e-6
+    e8, _, _ = buoyant_slot(8, phi=0.6, K=0.6 * 8 * 8 / 16)
+    e16, eT16, _ = buoyant_slot(16, phi=0.6, K=0.6 * 16 * 16 / 16)
+    assert e16 < 2e-3 and eT16 < 1e-4
+    assert 3.0 < e8 / e16 < 4.5
+
+
+def test_cavity_point_symmetry_and_heat_balance():
+    """Differentially heated cavity (left +1/2, right -1/2, top and bottom
+    insulated, buoyancy gamma T along y): the set-up is invariant under the
+    half turn about the centre with T -> -T and u -> -u, and so is every
+    discrete step, so the state stays symmetric to round-off.  At the steady
+    state the heat entering through the hot wall leaves through the cold one,
+    and convection raises it above conduction (Nu > 1)."""
+    n, nu, a, Ra = 12, 0.071, 0.1, 1e4
+    gam = Ra * nu * a / n ** 3
+    p = base_params(n, n, periodic_x=0, closed_x=1, reaction_mode=1,
+                    wall_dirichlet=1 | (1 << 3), C_wall=[0.5, 0.21, 0, -0.5, 0.21, 0, 0, 0, 0],
+                    T_in=0.0, nu=nu, buoy_gy=gam, T_buoy=0.0)
+    o = Oracle(p, uniform_material(n, n, alpha_T=a))
+    o.step(1500)
+    f = o.fields()
+    umax = np.abs(f["uy"]).max()
+    assert umax > 1e-3
+    assert np.abs(f["T"] + f["T"][::-1, ::-1]).max() < 1e-13
+    assert np.abs(f["ux"] + f["ux"][::-1, ::-1]).max() < 1e-13 * umax * 1e3
+    assert np.abs(f["uy"] + f["uy"][::-1, ::-1]).max() < 1e-13 * umax * 1e3
+    o.step(20000)
+    d = o.diag
+    assert d[DIAG["in_T"]] == pytest.approx(-d[DIAG["out_T"]], rel=1e-9)
+    Nu = d[DIAG["in_T"]] / (a * 1.0 * n / n)
+    assert 1.2 < Nu < 4.0
+    # no buoyancy: pure conduction, Nu = 1 exactly
+    o0 = Oracle(dict(p, buoy_gy=0.0), uniform_material(n, n, alpha_T=a))
+    o0.step(20000)
+    assert o0.diag[DIAG["in_T"]] / (a * n / n) == pytest.approx(1.0, rel=1e-10)
+
+
+def kang_series(nx, ny, k, D, C0, terms=80):
+    """C(x, y) = C0 sum_n A_n cos(l_n (Ly - y)) cosh(l_n (Lx - x)) /
+    cosh(l_n Lx): D dC/dy = k C at the bottom (l tan(l Ly) = k/D), dC/dy = 0
+    at the top, C = C0 at x = 0, dC/dx = 0 at x = Lx; A_n by orthogonality.
+    Coordinates from the halfway walls (cell centres at +1/2)."""
+    from scipy.optimize import brentq
+    Lx, Ly = float(nx), float(ny)
+    lam = np.array([brentq(lambda v: v * math.tan(v * Ly) - k / D,
+                           j * math.pi / Ly + 1e-12, (j + 0.5) * math.pi / Ly - 1e-12)
+                    for j in range(terms)])
+    A = (np.sin(lam * Ly) / lam) / (Ly / 2 + np.sin(2 * lam * Ly) / (4 * lam))
+    X, Y = np.meshgrid(np.arange(nx) + 0.5, np.arange(ny) + 0.5)
+    return C0 * sum(A[j] * np.cos(lam[j] * (Ly - Y)) * np.cosh(lam[j] * (Lx - X)) /
+                    np.cosh(lam[j] * Lx) for j in range(terms))
+
+
+@pytest.mark.parametrize("Da", [0.5, 4.0])
+def test_kang_surface_reaction_series(Da):
+    """Diffusion with first-order consumption on the bottom wall, the
+    reactant held on the left wall (the surface-reaction case of Sec. 3):
+    the steady field matches the separable series solution, within 1.5e-3
+    of C0 away from the corner where the held wall meets the reactive one
+    (the series and the lattice both resolve that corner coarsely)."""
+    from paper_2103_01444_gb300 import workloads
+    case = workloads.kang_surface_reaction(nx=24, ny=12, Da=Da, D=0.1, C0=0.2)
+    p, mat, solid = lattice_problem(case)
+    o = Oracle(p, mat, solid)
+    o.step(20000)
+    C = o.fields()["C_O2"]
+    k = Da * 0.1 / 12
+    err = np.abs(C - kang_series(24, 12, k, 0.1, 0.2)) / 0.2
+    away = np.ones_like(err, bool)
+    away[:2, :2] = False
+    assert err[away].max() < 1.5e-3, err[away].max()
+    assert err.max() < 2e-2
+    # at the steady state the consumption equals what enters through the
+    # held wall
+    d = o.diag
+    assert d[DIAG["J"]] == pytest.approx(d[DIAG["in_O2"]], rel=1e-5)
