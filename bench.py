@@ -53,9 +53,13 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--adjoint-steps", type=int, default=20000)
     ap.add_argument("--sweep-steps", type=int, default=256)
-    ap.add_argument("--workload", default="blocks", choices=["blocks", "grains"],
+    ap.add_argument("--workload", default="blocks",
+                    choices=["blocks", "grains", "cavity", "porous-cavity", "kang"],
                     help="blocks: 4096x1024 GDL blocks + volumetric catalyst; grains: "
-                         "8192x2048 pore-scale grains + thin film")
+                         "8192x2048 pore-scale grains + thin film; cavity, porous-cavity, "
+                         "kang: the validation set-ups of Sec. 3 (2048x2048 cavities at "
+                         "Ra 1e6, clear with a heated bottom or porous with Da 1e-2; "
+                         "a 4096x1024 surface-reaction box), their own line")
     ap.add_argument("--interface", type=int, default=0, choices=[0, 1],
                     help="0: Eq. 10 as printed (per-cell b); 1: Fickian interfaces")
     ap.add_argument("--inlet", default="velocity", choices=["velocity", "pressure"],
@@ -597,10 +601,84 @@ def run_precision_errors(args):
                       "results": out}))
 
 
+def validation_case(args):
+    if args.workload == "cavity":
+        n = args.nx if args.nx != NX else 2048
+        return workloads.natural_convection_cavity(n, Ra=1e6, heated_bottom=True)
+    if args.workload == "porous-cavity":
+        n = args.nx if args.nx != NX else 2048
+        return workloads.natural_convection_cavity(n, Ra=1e6, Da=1e-2, phi=0.6)
+    return workloads.kang_surface_reaction(nx=args.nx, ny=args.ny, Da=1.0)
+
+
+def run_validation(args):
+    """MLUPS of the step on a validation set-up of Sec. 3 (the extended
+    step instantiation: closed ends, fixed wall values, buoyancy), with the
+    wall balances of the state it reaches."""
+    import torch
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2103_01444_gb300.build import build
+    build()
+    from paper_2103_01444_gb300.lbm import Domain
+    case = validation_case(args)
+    cells = case["nx"] * case["ny"]
+    stream = torch.cuda.Stream(device=dev)
+    d = Domain.from_case(case, precision=args.precision, stream=stream.cuda_stream)
+    W, K = max(args.warmup, 3), max(args.steps, 1)
+    d.step(W)
+    torch.cuda.synchronize()
+    barrier(pg, dev)
+    with ClockSampler(local) as clk:
+        ms = d.time_steps(K)
+    torch.cuda.synchronize()
+    ms_max = max_over_ranks(ms, pg, dev)
+    b = d.balances()
+    if rank != 0:
+        return
+    ms_step = ms_max / K
+    bpc = d.bytes_per_cell()
+    achieved = bpc * cells / (ms_step * 1e-3) / 1e9
+    peak, peak_kind = measured_peak()
+    state = {k: b[k] for k in ("in_T", "out_T", "J", "in_O2")}
+    if case["kind"] == "cavity":
+        alpha = d.params["nu"] / case["Pr"]
+        dT = case["T_hot"] - case["T_cold"]
+        # wall-averaged Nusselt numbers of the state reached (not steady)
+        state["Nu_left"] = b["in_T"] / (alpha * dT)
+        state["Nu_right"] = -b["out_T"] / (alpha * dT)
+    line = {
+        "metric": METRIC, "value": world * cells * K / (ms_max * 1e-3) / 1e6, "unit": UNIT,
+        "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}-{case['nx']}x{case['ny']}",
+                   "nx": case["nx"], "ny": case["ny"], "storage": args.precision,
+                   "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (two population buffers of "
+                         f"{24 * cells * d_esize(args.precision) / 1e6:.0f} MB)",
+                   **{k: case[k] for k in ("Ra", "Pr", "Da", "phi", "heated_bottom", "D")
+                      if k in case}},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                     "bytes_per_cell": bpc,
+                     "kernel": "k_step, extended instantiation (128 x 2 threads per block)"},
+        "gpu_launches": K, "clocks": clk.summary(), "state_check": state,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        v, cores, sample = cpu_baseline(case)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": sample}
+    print(json.dumps(line), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload in ("cavity", "porous-cavity", "kang"):
+        run_validation(a)
     elif a.to_residual > 0:
         run_to_residual(a)
     elif a.precision_errors > 0:

@@ -58,6 +58,10 @@ typedef struct {
   int32_t reaction_mode;   /* 0: thin catalyst film on the bottom wall (the paper's
                               negligible-thickness layer); 1: volumetric catalyst rows */
   int32_t periodic_x;      /* 1: x is periodic (closed-form tests); 0: inlet/outlet */
+  int32_t closed_x;        /* 1: both x ends are no-slip walls (the cavities of Sec. 3):
+                              no inlet, no outlet; the scalars there are insulated
+                              unless lbm_params.wall_dirichlet fixes them.  Excludes
+                              periodic_x; lbm_grad and lbm_vjp need 0. */
   int32_t precision;       /* lbm_precision */
   int32_t rounding;        /* how a step stores 16-bit populations (LBM_BF16, LBM_FP16):
                               0 round to nearest even; 1 stochastic rounding, unbiased,
@@ -66,7 +70,8 @@ typedef struct {
                               from reset are reproducible.  Small per-step increments of a
                               large deviation (slow heating, water production) survive
                               in expectation instead of being rounded away.  Must be 0 for
-                              FP32/FP64; lbm_grad, lbm_vjp and batches need 0. */
+                              FP32/FP64; lbm_grad, lbm_vjp, batches, closed_x,
+                              buoyancy and fixed wall values need 0. */
   const uint8_t *solid;    /* optional host [ny][nx] pore-scale solid cells (1 = solid);
                               NULL = none.  Solids may not touch column 0 or the last
                               two columns. */
@@ -112,6 +117,22 @@ typedef struct {
                                   Butler-Volmer, with the anodic branch
                                   aj0(T) exp(alpha_a F eta/(R T)) at unit reactant
                                   activity subtracted from the O2 consumption */
+  double buoy_gx, buoy_gy;     /* Boussinesq buoyancy (the natural-convection cases of
+                                  Sec. 3): body force per unit mass
+                                  (buoy_gx, buoy_gy) (T - T_buoy), lattice units per K,
+                                  with T the cell's temperature after streaming.  Like the
+                                  uniform body force it enters Eq. 8's velocity and, times
+                                  phi, the force F of Eq. 7 (the generalised porous model
+                                  Eq. 7-8 come from).  lbm_grad and lbm_vjp need 0. */
+  double T_buoy;               /* K, reference temperature of the buoyancy */
+  int32_t wall_dirichlet;      /* bit 3 k + s: scalar s (0 T, 1 O2, 2 H2O) is held at
+                                  C_wall[k][s] on wall k (0 the x = 0 end outside the inlet
+                                  rows, 1 the x = nx - 1 end, closed_x only, 2 the bottom)
+                                  instead of insulated.  With the thin film (reaction_mode
+                                  0) the bottom's O2 and H2O bits must be 0; the film's
+                                  heat adds to a fixed bottom temperature.  lbm_grad and
+                                  lbm_vjp need 0. */
+  double C_wall[3][3];         /* wall values of wall_dirichlet: K and mole fractions */
 } lbm_params;
 
 typedef struct lbm_domain lbm_domain; /* opaque */
@@ -120,7 +141,8 @@ typedef struct lbm_domain lbm_domain; /* opaque */
  * reduction scratch) and builds the node mask on the device.  The state is
  * undefined until lbm_set_params, lbm_set_fields and lbm_reset are called.
  * EINVAL: bad sizes, rounding outside {0, 1} or 1 with FP32/FP64 storage,
- * solids on the inlet/outlet columns.
+ * solids on the inlet/outlet columns (or on the end walls' columns with
+ * closed_x), closed_x outside {0, 1} or together with periodic_x.
  * ENOMEM: device allocation failed. */
 lbm_status lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out);
 
@@ -129,7 +151,9 @@ lbm_status lbm_destroy_domain(lbm_domain *d);
 
 /* Copies the operating point (Sec. 4-5).  EINVAL unless nu > 0,
  * sqrt(3) * 1.5 * u_in_avg < 0.3 (inlet_mode 0), |dp_in| < 0.01 (inlet_mode
- * 1), 0 <= alpha_a <= 4, T_in > 0, dx_cm > 0, dt_s > 0. */
+ * 1), 0 <= alpha_a <= 4, T_in > 0, dx_cm > 0, dt_s > 0, wall_dirichlet
+ * within bits 0..8 (the right wall's only with closed_x, the bottom's O2
+ * and H2O bits 0 with the thin film), finite buoyancy. */
 lbm_status lbm_set_params(lbm_domain *d, const lbm_params *p);
 
 /* Per-cell material, host arrays [ny][nx] of doubles, lattice units:
@@ -183,10 +207,12 @@ lbm_status lbm_residual(lbm_domain *d, double *res);
  * With them, the change of each scalar total over the step is exact
  * (the D2Q5 collisions conserve C): O2 in + out - J, H2O in + out + 2 J;
  * the mass flows are those through the boundary links (the collision also
- * relaxes the flow's mass moment, Sec. 2.1).  Recomputed from the
- * state before the last step by the step's own boundary pulls (zeros for
- * a periodic lattice).  out: host, 10 doubles.  ESTATE before the first
- * step. */
+ * relaxes the flow's mass moment, Sec. 2.1).  With closed_x, out[2..5]
+ * and out[6..9] are the flows through the walls at x = 0 and x = nx - 1
+ * (non-zero only for scalars held at fixed wall values); a fixed bottom
+ * value's flow is not listed.  Recomputed from the state before the last
+ * step by the step's own boundary pulls (zeros for a periodic lattice).
+ * out: host, 10 doubles.  ESTATE before the first step. */
 lbm_status lbm_balances(lbm_domain *d, double *out);
 
 /* Macroscopic fields of the last step (the values its collision used):
@@ -260,23 +286,25 @@ lbm_status lbm_bytes_per_cell(lbm_domain *d, double *bytes);
  * Fickian interface mode treats each scalar's b (that of its largest
  * diffusivity) as fixed.  J and the gradients go to host memory: dphi, dK,
  * dD_O2 are [ny][nx] doubles (NULL to skip), du_in one double.  EINVAL for
- * objective outside {0, 1}, nsteps outside [2, 2^30] or stochastic
- * rounding (lbm_domain_desc.rounding 1); ENOMEM if the checkpoints do not
- * fit. */
+ * objective outside {0, 1}, nsteps outside [2, 2^30], stochastic rounding
+ * (lbm_domain_desc.rounding 1), closed_x, buoyancy or fixed wall values
+ * (the natural-convection and validation set-ups); ENOMEM if the
+ * checkpoints do not fit. */
 lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t segment,
                     double *J, double *dphi, double *dK, double *dD_O2, double *du_in);
 
 /* One transposed step at the current state s: given lam_next (host
  * [24][ny][nx], the adjoint of the state after one step), writes lam_prev =
  * (d step / d s)^T lam_next and the parameter gradients of
- * <lam_next, step(s)> (host, as in lbm_grad; NULL to skip).  EINVAL for
- * stochastic rounding (lbm_domain_desc.rounding 1). */
+ * <lam_next, step(s)> (host, as in lbm_grad; NULL to skip).  EINVAL as
+ * lbm_grad for the rounding and the set-ups it does not cover. */
 lbm_status lbm_vjp(lbm_domain *d, const double *lam_next, double *lam_prev, double *dphi,
                    double *dK, double *dD_O2, double *du_in);
 
 /* Batched stepping (operating-point sweeps over cases of uneven size).
  * lbm_create_batch groups ncases domains, each already set up and reset
- * (ESTATE otherwise) and all of one precision (EINVAL otherwise); the batch
+ * (ESTATE otherwise), all of one precision and each a cathode set-up
+ * without closed_x, buoyancy or fixed wall values (EINVAL otherwise); the batch
  * borrows them (they must outlive it) and works on their own buffers, so
  * fields, current density and checkpoints of each case stay available
  * through the per-domain calls.  The batch runs on the first domain's

@@ -115,6 +115,13 @@ KArgs make_args(const lbm_domain *d) {
   a.stochastic = d->desc.rounding == 1;
   a.seed_ctr = d->dseed;
   a.body_g = p.body_force_x;
+  a.gam_x = p.buoy_gx;
+  a.gam_y = p.buoy_gy;
+  a.buoy_off = d->Cref[0] - p.T_buoy;
+  a.closed_x = d->desc.closed_x;
+  a.wall_dir = p.wall_dirichlet;
+  for (int k = 0; k < 3; ++k)
+    for (int s = 0; s < 3; ++s) a.Cwall[k][s] = p.C_wall[k][s];
   a.u_in_avg = p.inlet_mode == 0 ? p.u_in_avg : 0.0;
   a.inlet_pressure = p.inlet_mode == 1;
   a.dp_in = p.inlet_mode == 1 ? p.dp_in : 0.0;
@@ -282,12 +289,16 @@ lbm_status lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
   if (D.reaction_mode != 0 && D.reaction_mode != 1) return fail(LBM_EINVAL, "reaction_mode must be 0 or 1");
   if (D.reaction_mode == 0 && D.ny_cl != 0) return fail(LBM_EINVAL, "thin-film mode takes ny_cl = 0");
   if (D.reaction_mode == 1 && D.ny_cl < 1) return fail(LBM_EINVAL, "volumetric mode needs ny_cl >= 1");
-  if (D.ny_cl < 0 || D.ny_gdl < 0 || D.ny_cl + D.ny_gdl > D.ny - (D.periodic_x ? 0 : 1))
+  if (D.periodic_x != 0 && D.periodic_x != 1) return fail(LBM_EINVAL, "periodic_x must be 0 or 1");
+  if (D.closed_x != 0 && D.closed_x != 1) return fail(LBM_EINVAL, "closed_x must be 0 or 1");
+  if (D.closed_x && D.periodic_x) return fail(LBM_EINVAL, "closed_x excludes periodic_x");
+  if (D.ny_cl < 0 || D.ny_gdl < 0 ||
+      D.ny_cl + D.ny_gdl > D.ny - ((D.periodic_x || D.closed_x) ? 0 : 1))
     return fail(LBM_EINVAL, "row split leaves no channel rows");
   if (D.solid && !D.periodic_x) {
     for (int y = 0; y < D.ny; ++y)
       for (int x : {0, D.nx - 2, D.nx - 1})
-        if (D.solid[(size_t)y * D.nx + x]) return fail(LBM_EINVAL, "solid cell on inlet/outlet column x=%d", x);
+        if (D.solid[(size_t)y * D.nx + x]) return fail(LBM_EINVAL, "solid cell on an end column x=%d", x);
   }
   lbm_domain *d = new lbm_domain();
   d->desc = D;
@@ -337,7 +348,7 @@ lbm_status lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
   cudaMemsetAsync(d->pop[0], 0, pop_bytes, d->stream);
   cudaMemsetAsync(d->pop[1], 0, pop_bytes, d->stream);
   launch_build_mask(d->mask, dsolid, D.nx, D.ny, d->nxp, D.ny_cl, D.ny_gdl, D.reaction_mode,
-                    D.periodic_x, d->stream);
+                    D.periodic_x, D.closed_x, d->stream);
   cudaError_t e = cudaStreamSynchronize(d->stream);
   if (dsolid) cudaFree(dsolid);
   if (e != cudaSuccess) return cleanup(fail(LBM_ECUDA, "mask build: %s", cudaGetErrorString(e)));
@@ -375,6 +386,17 @@ lbm_status lbm_set_params(lbm_domain *d, const lbm_params *p) {
       !(p->x_ref > 0) || !(p->R > 0) || !(p->F > 0) || !(p->T_ref_kin > 0) || !(p->aj0_ref >= 0))
     return fail(LBM_EINVAL, "non-positive physical constant");
   if (p->interface_mode != 0 && p->interface_mode != 1) return fail(LBM_EINVAL, "interface_mode must be 0 or 1");
+  if (p->wall_dirichlet & ~0x1ff) return fail(LBM_EINVAL, "wall_dirichlet has bits beyond 8");
+  if ((p->wall_dirichlet & 0x38) && !d->desc.closed_x)
+    return fail(LBM_EINVAL, "fixed values on the x = nx - 1 wall need closed_x");
+  if ((p->wall_dirichlet & 0x180) && d->desc.reaction_mode == 0)
+    return fail(LBM_EINVAL, "the thin film owns the bottom's O2 and H2O links");
+  if (!std::isfinite(p->buoy_gx) || !std::isfinite(p->buoy_gy) || !std::isfinite(p->T_buoy))
+    return fail(LBM_EINVAL, "buoyancy must be finite");
+  if (d->desc.rounding == 1 && (d->desc.closed_x || p->wall_dirichlet || p->buoy_gx != 0.0 ||
+                                p->buoy_gy != 0.0))
+    return fail(LBM_EINVAL, "stochastic rounding is not combined with closed_x, buoyancy or "
+                "fixed wall values");
   const bool reprep = d->have_fields && (p->nu != d->prm.nu || p->forchheimer != d->prm.forchheimer ||
                                          p->interface_mode != d->prm.interface_mode);
   d->prm = *p;
@@ -949,6 +971,15 @@ lbm_status lam_upload(lbm_domain *d, const double *host, void *dev) {
   CK(cudaStreamSynchronize(d->stream));
   return LBM_OK;
 }
+// The adjoint differentiates the cathode's boundaries and forces; the
+// closed ends, buoyancy and fixed wall values of the validation set-ups
+// have no transpose here.
+lbm_status adjoint_covers(const lbm_domain *d) {
+  const lbm_params &p = d->prm;
+  if (d->desc.closed_x || p.buoy_gx != 0.0 || p.buoy_gy != 0.0 || p.wall_dirichlet != 0)
+    return fail(LBM_EINVAL, "the adjoint does not cover closed_x, buoyancy or fixed wall values");
+  return LBM_OK;
+}
 lbm_status lam_download(lbm_domain *d, const void *dev, double *host) {
   const size_t n = (size_t)d->nx * d->ny;
   std::vector<unsigned char> tmp(24 * (size_t)d->plane * (fp64(d) ? 8 : 4));
@@ -974,6 +1005,7 @@ lbm_status lbm_vjp(lbm_domain *d, const double *lam_next, double *lam_prev, doub
   if (s != LBM_OK) return s;
   if (!lam_next || !lam_prev) return fail(LBM_EINVAL, "null argument");
   if (d->desc.rounding != 0) return fail(LBM_EINVAL, "the adjoint needs round-to-nearest storage");
+  if ((s = adjoint_covers(d)) != LBM_OK) return s;
   AdjWork w;
   if ((s = w.alloc(d)) != LBM_OK) return s;
   if ((s = w.zero_grads(d)) != LBM_OK) return s;
@@ -991,6 +1023,7 @@ lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t se
   if (s != LBM_OK) return s;
   if (objective != 0 && objective != 1) return fail(LBM_EINVAL, "objective must be 0 or 1");
   if (d->desc.rounding != 0) return fail(LBM_EINVAL, "the adjoint needs round-to-nearest storage");
+  if ((s = adjoint_covers(d)) != LBM_OK) return s;
   if (nsteps < 2 || nsteps > (1LL << 30)) return fail(LBM_EINVAL, "nsteps outside [2, 2^30]");
   const int64_t N = nsteps;
   const int seg = segment > 0 ? segment : (int)std::ceil(std::sqrt((double)N));
@@ -1390,6 +1423,9 @@ lbm_status lbm_create_batch(lbm_domain *const *domains, int32_t ncases, lbm_batc
       return fail(LBM_EINVAL, "batched domains must share one precision");
     if (domains[c]->desc.rounding != 0)
       return fail(LBM_EINVAL, "batched domains need round-to-nearest storage");
+    if (needs_extended(make_args(domains[c])))
+      return fail(LBM_EINVAL, "batched domains step the cathode set-up (no closed_x, buoyancy "
+                  "or fixed wall values)");
     for (int k = 0; k < c; ++k)
       if (domains[k] == domains[c]) return fail(LBM_EINVAL, "domain %d appears twice", c);
   }

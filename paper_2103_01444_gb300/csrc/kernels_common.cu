@@ -7,7 +7,8 @@ namespace pemlbm {
 // explicit solids, and a flag for cells with a solid D2Q9 neighbour; a
 // second plane of the same size says which neighbours are solid.
 __global__ void k_build_mask(uint8_t *__restrict__ mask, const uint8_t *__restrict__ solid, int nx,
-                             int ny, int nxp, int ny_cl, int ny_gdl, int mode, int periodic) {
+                             int ny, int nxp, int ny_cl, int ny_gdl, int mode, int periodic,
+                             int closed) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   if (x >= nxp || y >= ny) return;
   const long long c = (long long)y * nxp + x;
@@ -28,7 +29,7 @@ __global__ void k_build_mask(uint8_t *__restrict__ mask, const uint8_t *__restri
   if (x == nx - 1) m |= M_XHI;
   if (y == ny - 1) m |= M_YHI;
   if (y == 0) m |= M_YLO;
-  if (reg == REG_CLEAR && x == 0 && !periodic) m |= M_INLET;
+  if (reg == REG_CLEAR && x == 0 && !periodic && !closed) m |= M_INLET;
   // second plane: bit i - 1 set when the source x - e_i of flow link i
   // (i = 1..8, Eq. 2 order) is a solid cell inside the lattice
   uint8_t nb = 0;
@@ -53,9 +54,10 @@ __global__ void k_seed_advance(unsigned *ctr) { *ctr += 1u; }
 void launch_seed_advance(unsigned *ctr, cudaStream_t st) { k_seed_advance<<<1, 1, 0, st>>>(ctr); }
 
 void launch_build_mask(uint8_t *mask, const uint8_t *solid, int nx, int ny, int nxp, int ny_cl,
-                       int ny_gdl, int mode, int periodic, cudaStream_t st) {
+                       int ny_gdl, int mode, int periodic, int closed, cudaStream_t st) {
   dim3 grid((nxp + 127) / 128, ny);
-  k_build_mask<<<grid, 128, 0, st>>>(mask, solid, nx, ny, nxp, ny_cl, ny_gdl, mode, periodic);
+  k_build_mask<<<grid, 128, 0, st>>>(mask, solid, nx, ny, nxp, ny_cl, ny_gdl, mode, periodic,
+                                     closed);
 }
 
 // Per-material coefficients: Darcy and Forchheimer terms of Eq. 7, the l0,

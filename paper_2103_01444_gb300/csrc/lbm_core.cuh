@@ -145,8 +145,19 @@ template <typename F> struct KArgsT {
   int stochastic;           // 16-bit step stores: 1 stochastic rounding, 0 nearest even
   const unsigned *seed_ctr; // device step counter seeding the stochastic rounding
   F hpo;                    // temperature per unit O2 consumed (Eq. 15, 16)
+  // Boussinesq buoyancy: force per unit mass (gam_x, gam_y) (T - T_buoy),
+  // with T - T_buoy = C_T + buoy_off (C_T the deviation sum of the T lattice)
+  F gam_x, gam_y, buoy_off;
+  int closed_x;             // 1: both x ends are no-slip walls
+  int wall_dir;             // bit 3 k + s: scalar s fixed to Cwall[k][s] on wall k
+  F Cwall[3][3];            // k: 0 the x = 0 end, 1 the x = nx - 1 end, 2 the bottom
 };
 using KArgs = KArgsT<double>;
+
+// Whether a set-up uses what only the X instantiations of the step carry.
+template <typename F> __host__ __device__ inline bool needs_extended(const KArgsT<F> &a) {
+  return a.closed_x || a.wall_dir || a.gam_x != F(0) || a.gam_y != F(0);
+}
 
 template <typename F> __host__ __device__ inline KArgsT<F> narrow_args(const KArgs &a) {
   KArgsT<F> r;
@@ -155,6 +166,10 @@ template <typename F> __host__ __device__ inline KArgsT<F> narrow_args(const KAr
   r.s_nu = F(a.s_nu); r.s_q = F(a.s_q); r.body_g = F(a.body_g); r.u_in_avg = F(a.u_in_avg);
   r.h_ch = F(a.h_ch); r.Q3 = F(a.Q3);
   r.inlet_pressure = a.inlet_pressure; r.dp_in = F(a.dp_in);
+  r.gam_x = F(a.gam_x); r.gam_y = F(a.gam_y); r.buoy_off = F(a.buoy_off);
+  r.closed_x = a.closed_x; r.wall_dir = a.wall_dir;
+  for (int k = 0; k < 3; ++k)
+    for (int s = 0; s < 3; ++s) r.Cwall[k][s] = F(a.Cwall[k][s]);
   for (int s = 0; s < 3; ++s) {
     r.Cref[s] = F(a.Cref[s]); r.wr0[s] = F(a.wr0[s]); r.wr1[s] = F(a.wr1[s]);
     r.bref[s] = F(a.bref[s]); r.Cin[s] = F(a.Cin[s]); r.Ctop[s] = F(a.Ctop[s]);
@@ -217,8 +232,10 @@ template <typename R> __device__ __forceinline__ R inlet_u(const KArgsT<R> &a, R
 // arrives keeps one DRAM latency off the critical path.
 
 // Flow link i into cell (x, y) whose source may lie outside the fluid;
-// `v` is the interior pull already loaded for this link.
-template <typename S, typename R, bool CG = false>
+// `v` is the interior pull already loaded for this link.  X: the extended
+// set-ups (closed x ends, fixed wall values, buoyancy) are compiled in; the
+// cathode's own step kernels are built without them.
+template <typename S, typename R, bool CG = false, bool X = false>
 __device__ R pull_flow_edge(const Pops<S, CG> &src, const KArgsT<R> &a, const uint8_t *__restrict__ mask,
                             const uint16_t *__restrict__ mid, const MatCoef<R> *__restrict__ pal,
                             int i, int x, int y, uint8_t m, R v) {
@@ -230,6 +247,8 @@ __device__ R pull_flow_edge(const Pops<S, CG> &src, const KArgsT<R> &a, const ui
       sx = sx < 0 ? sx + a.nx : sx - a.nx;
     } else {
       const bool in = sx < 0;
+      if constexpr (X)
+        if (!in && a.closed_x) return R(src.at(OP[i], x, y));       // closed end: wall
       if (in && !(a.inlet_pressure && (m & M_INLET))) {             // velocity inlet / wall
         R w = R(src.at(OP[i], x, y));
         if (m & M_INLET) w += R(6) * w9<R>(i) * R(EX[i]) * inlet_u<R>(a, R(y) - R(0.5) * R(EY[i]));
@@ -262,15 +281,28 @@ __device__ R pull_flow_edge(const Pops<S, CG> &src, const KArgsT<R> &a, const ui
   return v;
 }
 
+// Anti-bounce-back of a wall link of scalar s held at value Cw (the
+// halfway wall's value, in deviation coordinates) given the bounced
+// population w.
+template <typename R>
+__device__ __forceinline__ R wall_value(const KArgsT<R> &a, const MatCoef<R> &mc, int s, R w, R Cw) {
+  return -w + R(2) * mc.w1[s] * Cw - R(2) * R(a.wr1[s]) * R(a.Cref[s]);
+}
+
 // Scalar link i of scalar s into cell (x, y); the bottom wall returns the
-// insulated value and the reaction is applied afterwards.
-template <typename S, typename R, bool CG = false>
+// insulated (or, with X, fixed) value and the reaction is applied afterwards.
+template <typename S, typename R, bool CG = false, bool X = false>
 __device__ R pull_scalar_edge(const Pops<S, CG> &src, const KArgsT<R> &a, const uint8_t *__restrict__ mask,
                               const MatCoef<R> &mc, int s, int i, int x, int y, uint8_t m, R v) {
   const int EX[5] = {0, 1, 0, -1, 0}, EY[5] = {0, 0, 1, 0, -1}, OP[5] = {0, 3, 4, 1, 2};
   const int q = 9 + 5 * s;
   int sx = x - EX[i], sy = y - EY[i];
-  if (sy < 0) return R(src.at(q + OP[i], x, y));
+  if (sy < 0) {
+    R w = R(src.at(q + OP[i], x, y));
+    if constexpr (X)
+      if ((a.wall_dir >> (6 + s)) & 1) w = wall_value<R>(a, mc, s, w, R(a.Cwall[2][s]));
+    return w;
+  }
   if (sy >= a.ny) {
     R w = R(src.at(q + OP[i], x, y));
     if (a.top_dirichlet)
@@ -282,7 +314,15 @@ __device__ R pull_scalar_edge(const Pops<S, CG> &src, const KArgsT<R> &a, const 
       sx = sx < 0 ? sx + a.nx : sx - a.nx;
     } else if (sx < 0) {
       R w = R(src.at(q + OP[i], x, y));
-      if (m & M_INLET) w = -w + R(2) * mc.w1[s] * R(a.Cin[s]) - R(2) * R(a.wr1[s]) * R(a.Cref[s]);
+      if (m & M_INLET) {
+        w = wall_value<R>(a, mc, s, w, R(a.Cin[s]));
+      } else if constexpr (X) {
+        if ((a.wall_dir >> s) & 1) w = wall_value<R>(a, mc, s, w, R(a.Cwall[0][s]));
+      }
+      return w;
+    } else if (X && a.closed_x) {
+      R w = R(src.at(q + OP[i], x, y));
+      if ((a.wall_dir >> (3 + s)) & 1) w = wall_value<R>(a, mc, s, w, R(a.Cwall[1][s]));
       return w;
     } else {
       return R(src.at(q + i, a.nx - 1, y));                           // fully developed
@@ -388,7 +428,7 @@ __device__ __forceinline__ void load_interior(const Pops<S, CG> &src, const KArg
 
 // Replaces the pulls of links that cross a wall, the inlet, the outlet, a
 // periodic seam or a solid grain (cells with any edge bit only).
-template <typename S, typename R, bool CG = false>
+template <typename S, typename R, bool CG = false, bool X = false>
 __device__ __forceinline__ void fix_edges(const Pops<S, CG> &src, const KArgsT<R> &a,
                                           const uint8_t *__restrict__ mask,
                                           const uint16_t *__restrict__ mid,
@@ -397,12 +437,12 @@ __device__ __forceinline__ void fix_edges(const Pops<S, CG> &src, const KArgsT<R
                                           Cell<R> &c) {
 #pragma unroll
   for (int i = 1; i < 9; ++i)
-    c.f[i] = pull_flow_edge<S, R, CG>(src, a, mask, mid, pal, i, x, y, m, c.f[i]);
+    c.f[i] = pull_flow_edge<S, R, CG, X>(src, a, mask, mid, pal, i, x, y, m, c.f[i]);
 #pragma unroll
   for (int s = 0; s < 3; ++s)
 #pragma unroll
     for (int i = 1; i < 5; ++i)
-      c.g[s][i] = pull_scalar_edge<S, R, CG>(src, a, mask, mc, s, i, x, y, m, c.g[s][i]);
+      c.g[s][i] = pull_scalar_edge<S, R, CG, X>(src, a, mask, mc, s, i, x, y, m, c.g[s][i]);
 }
 
 // Cells whose only edge bit is M_NEAR_SOLID: a link whose source is a solid
@@ -424,7 +464,7 @@ __device__ __forceinline__ void bounce_solid(const Pops<S, CG> &src, int x, int 
 }
 
 // Pull all 24 populations of a non-solid cell (x, y).
-template <typename S, typename R, bool CG = false>
+template <typename S, typename R, bool CG = false, bool X = false>
 __device__ __forceinline__ void pull_cell(const Pops<S, CG> &src, const KArgsT<R> &a,
                                           const uint8_t *__restrict__ mask,
                                           const uint16_t *__restrict__ mid,
@@ -432,7 +472,7 @@ __device__ __forceinline__ void pull_cell(const Pops<S, CG> &src, const KArgsT<R
                                           const MatCoef<R> &mc, int x, int y, uint8_t m,
                                           Cell<R> &c) {
   load_interior<S, R, CG>(src, a, x, y, c);
-  if (m & M_EDGE) fix_edges<S, R, CG>(src, a, mask, mid, pal, mc, x, y, m, c);
+  if (m & M_EDGE) fix_edges<S, R, CG, X>(src, a, mask, mid, pal, mc, x, y, m, c);
 }
 
 // Macroscopic values of a post-stream cell (Eq. 8, 11).
@@ -441,12 +481,28 @@ template <typename R> struct Macro {
   R C[3];           // deviation sums (value - Cref)
 };
 
-template <typename R>
+// Body force per unit mass at a cell whose T deviation sum is CT: the
+// uniform force along x, plus the Boussinesq buoyancy with X.
+template <typename R, bool X>
+__device__ __forceinline__ void body_force(const KArgsT<R> &a, R CT, R &Gx, R &Gy) {
+  Gx = R(a.body_g);
+  Gy = R(0);
+  if constexpr (X) {
+    const R tb = CT + R(a.buoy_off);   // T - T_buoy
+    Gx += R(a.gam_x) * tb;
+    Gy = R(a.gam_y) * tb;
+  }
+}
+
+template <typename R, bool X = false>
 __device__ __forceinline__ Macro<R> macros(const KArgsT<R> &a, const MatCoef<R> &mc, const Cell<R> &c) {
   Macro<R> r;
   const R *d = c.f;
-  R vx = d[1] - d[3] + d[5] - d[6] - d[7] + d[8] + R(0.5) * mc.phi * R(a.body_g);
+  R Gx, Gy;
+  body_force<R, X>(a, d2q5_sum<R>(c.g[0][0], c.g[0][1], c.g[0][2], c.g[0][3], c.g[0][4]), Gx, Gy);
+  R vx = d[1] - d[3] + d[5] - d[6] - d[7] + d[8] + R(0.5) * mc.phi * Gx;
   R vy = d[2] - d[4] + d[5] + d[6] - d[7] - d[8];
+  if constexpr (X) vy += R(0.5) * mc.phi * Gy;
   R vn = sqrt(vx * vx + vy * vy);
   R den = mc.l0 + sqrt(mc.l0 * mc.l0 + mc.l1 * vn);
   r.ux = vx / den;
@@ -460,13 +516,16 @@ __device__ __forceinline__ Macro<R> macros(const KArgsT<R> &a, const MatCoef<R> 
 }
 
 // D2Q9 MRT collision with the porous force, in deviation moments (Eq. 1, 3-7).
-template <typename R>
+template <typename R, bool X = false>
 __device__ __forceinline__ void collide_flow(const KArgsT<R> &a, const MatCoef<R> &mc, const Macro<R> &u,
                                              const R d[9], R o[9]) {
   const R sn = R(a.s_nu), sq = R(a.s_q);
   R ux = u.ux, uy = u.uy, u2 = ux * ux + uy * uy, un = sqrt(u2), ip = mc.inv_phi;
-  R Fx = -mc.darcy * ux - mc.forch * un * ux + mc.phi * R(a.body_g);
+  R Gx, Gy;
+  body_force<R, X>(a, u.C[0], Gx, Gy);
+  R Fx = -mc.darcy * ux - mc.forch * un * ux + mc.phi * Gx;
   R Fy = -mc.darcy * uy - mc.forch * un * uy;
+  if constexpr (X) Fy += mc.phi * Gy;
   R ax = (d[1] + d[3]) + (d[2] + d[4]), dg = (d[5] + d[7]) + (d[6] + d[8]);
   R m0 = d[0] + ax + dg;
   R m1 = R(-4) * d[0] - ax + R(2) * dg;

@@ -137,9 +137,9 @@ __global__ void k_fields(const S *__restrict__ src_p, const uint8_t *__restrict_
   const Pops<S> src{src_p, a.plane, a.nxp};
   const MatCoef<R> mc = pal[mid[c]];
   Cell<R> cell;
-  pull_cell<S, R>(src, a, mask, mid, pal, mc, x, y, m, cell);
+  pull_cell<S, R, false, true>(src, a, mask, mid, pal, mc, x, y, m, cell);
   if (a.mode == 0 && (m & M_YLO)) surface_reaction<S, R>(src, a, mc, x, cell);
-  const Macro<R> u = macros<R>(a, mc, cell);
+  const Macro<R> u = macros<R, true>(a, mc, cell);
   out[0 * n + o] = (double)u.ux;
   out[1 * n + o] = (double)u.uy;
   out[2 * n + o] = ((double)u.Pdev + 1.0 / 3.0) / (double)mc.phi;
@@ -204,7 +204,7 @@ k_balances(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
           const int sy = y - EY[i];
           if (EX[i] == dir) {                       // enters through the column
             if (sy < 0 || sy >= a.ny) continue;     // a wall link
-            const R v = pull_flow_edge<S, R>(src, a, mask, mid, pal, i, x, y, m, R(0));
+            const R v = pull_flow_edge<S, R, false, true>(src, a, mask, mid, pal, i, x, y, m, R(0));
             // inlet: the pulled value replaces the bounced one (the moving-wall
             // or virtual-column excess); outlet: the whole pulled value
             o[0] += side ? (double)v : (double)v - (double)R(src.at(OP[i], x, y));
@@ -217,10 +217,10 @@ k_balances(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
         for (int s = 0; s < 3; ++s) {
           const int q = 9 + 5 * s;
           const int lin = side ? 3 : 1;              // D2Q5 link entering through the column
-          const R v = pull_scalar_edge<S, R>(src, a, mask, mc, s, lin, x, y, m, R(0));
+          const R v = pull_scalar_edge<S, R, false, true>(src, a, mask, mc, s, lin, x, y, m, R(0));
           if (side) {
             o[1 + s] += (double)v - (double)R(src.at(q + 1, x, y));   // in via 3, out via 1
-          } else if (m & M_INLET) {
+          } else if ((m & M_INLET) || ((a.wall_dir >> s) & 1)) {
             o[1 + s] += (double)v - (double)R(src.at(q + 3, x, y));   // Dirichlet excess
           }
         }

@@ -81,7 +81,7 @@ void launch_seed_advance(unsigned *ctr, cudaStream_t st);
 
 // Node mask from the geometry (solid may be NULL).
 void launch_build_mask(uint8_t *mask, const uint8_t *solid, int nx, int ny, int nxp, int ny_cl,
-                       int ny_gdl, int mode, int periodic, cudaStream_t st);
+                       int ny_gdl, int mode, int periodic, int closed, cudaStream_t st);
 // Derived material coefficients of a palette (Eq. 7, 8, 10): R = double if
 // fp64 else float.
 void launch_prep_palette(void *pal, const MatRaw *raw, int npal, double nu, int forchheimer,

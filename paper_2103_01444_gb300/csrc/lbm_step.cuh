@@ -10,8 +10,9 @@ namespace pemlbm {
 
 // ------------------------------------------------------------- step (K1)
 // One coupled update of cell (x, y): src -> dst.  Shared by the single-
-// domain step and the batched steps.
-template <typename S, bool CG = false, bool SR = false>
+// domain step and the batched steps.  X: closed ends, fixed wall values and
+// buoyancy compiled in (see pull_flow_edge).
+template <typename S, bool CG = false, bool SR = false, bool X = false>
 __device__ __forceinline__ void cell_update(const S *__restrict__ src_p, S *__restrict__ dst,
                                             const uint8_t *__restrict__ mask,
                                             const uint16_t *__restrict__ mid,
@@ -31,14 +32,14 @@ __device__ __forceinline__ void cell_update(const S *__restrict__ src_p, S *__re
   if (m & M_EDGE) {
     // next to grains but away from the lattice's edges: bounce-back only
     if ((m & M_EDGE) == M_NEAR_SOLID) bounce_solid<S, R, CG>(src, x, y, mask[a.plane + c], cell);
-    else fix_edges<S, R, CG>(src, a, mask, mid, pal, mc, x, y, m, cell);
+    else fix_edges<S, R, CG, X>(src, a, mask, mid, pal, mc, x, y, m, cell);
   }
   if (a.mode == 0 && (m & M_YLO)) surface_reaction<S, R, CG>(src, a, mc, x, cell);
   R S_vol = 0;
   if (a.mode == 1 && (m & REG_MASK) == REG_CATALYST) S_vol = volume_sink<S, R, CG>(src, a, x, y);
-  const Macro<R> u = macros<R>(a, mc, cell);
+  const Macro<R> u = macros<R, X>(a, mc, cell);
   R o[9];
-  collide_flow<R>(a, mc, u, cell.f, o);
+  collide_flow<R, X>(a, mc, u, cell.f, o);
   // 16-bit storage with stochastic rounding: a random stream per cell and
   // step (hash of the cell and the device step counter)
   unsigned rs = 0;
@@ -66,8 +67,8 @@ __device__ __forceinline__ void cell_update(const S *__restrict__ src_p, S *__re
 }
 
 // SR: 16-bit stores with stochastic rounding (a separate instantiation, so
-// the round-to-nearest kernel carries none of its code).
-template <typename S, int BX, int BY, int MINB, bool SR = false>
+// the round-to-nearest kernel carries none of its code); X as cell_update.
+template <typename S, int BX, int BY, int MINB, bool SR = false, bool X = false>
 __global__ void __launch_bounds__(BX * BY, MINB)
 k_step(const S *__restrict__ src_p, S *__restrict__ dst, const uint8_t *__restrict__ mask,
        const uint16_t *__restrict__ mid, const MatCoef<typename Real<S>::type> *__restrict__ pal,
@@ -75,7 +76,7 @@ k_step(const S *__restrict__ src_p, S *__restrict__ dst, const uint8_t *__restri
   const int x = blockIdx.x * BX + (threadIdx.x % BX);
   const int y = blockIdx.y * BY + (threadIdx.x / BX);
   if (x >= a.nx || y >= a.ny) return;
-  cell_update<S, false, SR>(src_p, dst, mask, mid, pal, a, x, y);
+  cell_update<S, false, SR, X>(src_p, dst, mask, mid, pal, a, x, y);
 }
 
 // ------------------------------------------------------ launcher
@@ -84,6 +85,13 @@ void launch_step_v(const void *src, void *dst, const DevGeom &g, const KArgs &a,
   constexpr StepShape sh = kStepShapes[V];
   dim3 grid((a.nx + sh.bx - 1) / sh.bx, (a.ny + sh.by - 1) / sh.by);
   using R = typename Real<S>::type;
+  if (needs_extended(a)) {   // one shape (the first: no register cap) for every variant
+    constexpr StepShape s0 = kStepShapes[0];
+    dim3 g0((a.nx + s0.bx - 1) / s0.bx, (a.ny + s0.by - 1) / s0.by);
+    k_step<S, s0.bx, s0.by, s0.minb, false, true><<<g0, s0.bx * s0.by, 0, st>>>(
+        (const S *)src, (S *)dst, g.mask, g.mid, (const MatCoef<R> *)g.pal, narrow_args<R>(a));
+    return;
+  }
   if constexpr (sizeof(S) == 2) {
     if (a.stochastic) {
       k_step<S, sh.bx, sh.by, sh.minb, true><<<grid, sh.bx * sh.by, 0, st>>>(

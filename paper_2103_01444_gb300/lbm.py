@@ -38,7 +38,7 @@ class LbmError(RuntimeError):
 class lbm_domain_desc(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("ny_cl", C.c_int32),
                 ("ny_gdl", C.c_int32), ("reaction_mode", C.c_int32), ("periodic_x", C.c_int32),
-                ("precision", C.c_int32), ("rounding", C.c_int32),
+                ("closed_x", C.c_int32), ("precision", C.c_int32), ("rounding", C.c_int32),
                 ("solid", C.POINTER(C.c_uint8)), ("cuda_stream", C.c_void_p)]
 
 
@@ -52,7 +52,8 @@ class lbm_params(C.Structure):
     _fields_ = [(k, C.c_double) for k in _PARAM_DOUBLES] + [
         ("forchheimer", C.c_int32), ("top_dirichlet", C.c_int32),
         ("interface_mode", C.c_int32), ("inlet_mode", C.c_int32), ("dp_in", C.c_double),
-        ("alpha_a", C.c_double)]
+        ("alpha_a", C.c_double), ("buoy_gx", C.c_double), ("buoy_gy", C.c_double),
+        ("T_buoy", C.c_double), ("wall_dirichlet", C.c_int32), ("C_wall", (C.c_double * 3) * 3)]
 
 
 _lib = None
@@ -121,14 +122,14 @@ class Domain:
     """One cathode lattice on the GPU (wraps an lbm_domain handle)."""
 
     def __init__(self, nx, ny, ny_cl=0, ny_gdl=0, reaction_mode=0, periodic_x=0,
-                 precision="fp32", solid=None, stream=None, rounding="nearest"):
+                 precision="fp32", solid=None, stream=None, rounding="nearest", closed_x=0):
         """rounding: "nearest" or "stochastic" (16-bit storage only)."""
         self.L = load_library()
         self.nx, self.ny = int(nx), int(ny)
         self._solid = None if solid is None else np.ascontiguousarray(solid, np.uint8)
         desc = lbm_domain_desc(
             nx=self.nx, ny=self.ny, ny_cl=int(ny_cl), ny_gdl=int(ny_gdl),
-            reaction_mode=int(reaction_mode), periodic_x=int(periodic_x),
+            reaction_mode=int(reaction_mode), periodic_x=int(periodic_x), closed_x=int(closed_x),
             precision=PRECISION[precision] if isinstance(precision, str) else int(precision),
             rounding={"nearest": 0, "stochastic": 1}[rounding],
             solid=None if self._solid is None else self._solid.ctypes.data_as(C.POINTER(C.c_uint8)),
@@ -164,7 +165,11 @@ class Domain:
     # -- set-up
     def set_params(self, params: dict):
         self.params = dict(params)
-        _check(self.L.lbm_set_params(self.h, C.byref(lbm_params(**params))))
+        p = dict(params)
+        if "C_wall" in p:   # [wall][scalar] values
+            w = np.asarray(p["C_wall"], np.float64).reshape(3, 3)
+            p["C_wall"] = ((C.c_double * 3) * 3)(*[(C.c_double * 3)(*row) for row in w])
+        _check(self.L.lbm_set_params(self.h, C.byref(lbm_params(**p))))
 
     def set_fields(self, phi, K, alpha_T, D_O2, D_H2O, rho_cp_ratio=None):
         arrs = [np.ascontiguousarray(np.broadcast_to(np.asarray(a, np.float64), (self.ny, self.nx)))

@@ -47,7 +47,10 @@ def effective_thermal_diffusivity(phi, alpha_gas):
 
 def cathode_params(case: dict, forchheimer: int = 1, interface_mode: int = 0):
     """Returns (params dict matching lbm_params, fields dict of [ny][nx]
-    float64 arrays phi, K, alpha_T, D_O2, D_H2O, geometry dict)."""
+    float64 arrays phi, K, alpha_T, D_O2, D_H2O, geometry dict).  The
+    validation cases (case["kind"]) go to validation_params."""
+    if case.get("kind"):
+        return validation_params(case, forchheimer, interface_mode)
     nx, ny = int(case["nx"]), int(case["ny"])
     ny_cl, ny_gdl = int(case["ny_cl"]), int(case["ny_gdl"])
     L = LATTICE
@@ -87,3 +90,72 @@ def cathode_params(case: dict, forchheimer: int = 1, interface_mode: int = 0):
                     reaction_mode=int(case["reaction_mode"]),
                     periodic_x=int(case.get("periodic_x", 0)), solid=case.get("solid"))
     return params, fields, geometry
+
+
+# Lattice scales of the validation cases (Sec. 3): the buoyant velocity
+# scale alpha sqrt(Ra Pr) / L is held at 0.05 (Mach number about 0.09), with
+# the diffusivity capped at 0.1; the heat capacity ratio is 1.
+CAVITY_U = 0.05
+CAVITY_ALPHA_MAX = 0.1
+
+
+def _lattice_base(nx, ny, forchheimer, interface_mode, **kw):
+    """lbm_params for a case given in lattice units: no drive, no reaction
+    heat (V_op = U0_0), temperature-independent kinetics (E_act = alpha_c =
+    0) whose lattice rate constant is aj0_ref (x_ref = 4 F c_tot = delta =
+    dx = dt = 1)."""
+    p = dict(nu=0.1, u_in_avg=0.0, body_force_x=0.0, V_op=0.0, T_in=343.0, C_O2_in=0.21,
+             C_H2O_in=0.0, T_top=343.0, C_O2_top=0.21, C_H2O_top=0.0, aj0_ref=0.0,
+             T_ref_kin=343.0, E_act=0.0, alpha_c=0.0, F=0.25, R=PAPER["R"], dU0dT=0.0, U0_0=0.0,
+             x_ref=1.0, dx_cm=1.0, dt_s=1.0, delta_cl_cm=1.0, c_tot=1.0, rho_cp_f=1.0,
+             forchheimer=forchheimer, top_dirichlet=0, interface_mode=interface_mode,
+             inlet_mode=0, dp_in=0.0, alpha_a=0.0, buoy_gx=0.0, buoy_gy=0.0, T_buoy=343.0,
+             wall_dirichlet=0, C_wall=[[0.0] * 3 for _ in range(3)])
+    p.update(kw)
+    return p
+
+
+def validation_params(case: dict, forchheimer: int = 1, interface_mode: int = 0):
+    """The validation cases of Sec. 3 -> (params, fields, geometry), as
+    cathode_params.
+      cavity: L = n cells between the halfway walls, dT = T_hot - T_cold,
+        alpha = min(0.1, 0.05 L / sqrt(Ra Pr)), nu = Pr alpha, and the
+        buoyancy gamma = Ra nu alpha / (dT L^3) (Ra = g beta dT L^3/(nu
+        alpha)); the porous cavity has K = Da L^2 and porosity phi
+        everywhere; the walls hold T_hot (left, and the bottom if heated)
+        and T_cold (right); T_buoy and the initial T are the mean.
+      kang: k = Da D / ny on the bottom film, C0 held on the left wall."""
+    nx, ny = int(case["nx"]), int(case["ny"])
+    full = lambda v: np.full((ny, nx), float(v))  # noqa: E731
+    if case["kind"] == "cavity":
+        L = float(nx)
+        dT = case["T_hot"] - case["T_cold"]
+        Tm = 0.5 * (case["T_hot"] + case["T_cold"])
+        alpha = min(CAVITY_ALPHA_MAX, CAVITY_U * L / np.sqrt(case["Ra"] * case["Pr"]))
+        nu = case["Pr"] * alpha
+        porous = case.get("Da") is not None
+        fields = dict(phi=full(case["phi"] if porous else 1.0),
+                      K=full(case["Da"] * L * L if porous else np.inf),
+                      alpha_T=full(alpha), D_O2=full(alpha), D_H2O=full(alpha),
+                      rho_cp_ratio=full(1.0))
+        bits = (1 << 0) | (1 << 3) | ((1 << 6) if case["heated_bottom"] else 0)
+        wall = [[case["T_hot"], 0.21, 0.0], [case["T_cold"], 0.21, 0.0],
+                [case["T_hot"], 0.21, 0.0]]
+        params = _lattice_base(nx, ny, forchheimer, interface_mode, nu=nu, T_in=Tm, T_top=Tm,
+                               buoy_gy=case["Ra"] * nu * alpha / (dT * L ** 3), T_buoy=Tm,
+                               wall_dirichlet=bits, C_wall=wall)
+        geometry = dict(nx=nx, ny=ny, ny_cl=0, ny_gdl=ny if porous else 0, reaction_mode=0,
+                        periodic_x=0, closed_x=1, solid=None)
+        return params, fields, geometry
+    if case["kind"] == "kang":
+        D = case["D"]
+        fields = dict(phi=full(1.0), K=full(np.inf), alpha_T=full(D), D_O2=full(D),
+                      D_H2O=full(D), rho_cp_ratio=full(1.0))
+        params = _lattice_base(nx, ny, forchheimer, interface_mode, C_O2_in=case["C0"],
+                               C_O2_top=case["C0"], aj0_ref=case["Da"] * D / ny,
+                               wall_dirichlet=0b111, C_wall=[[343.0, case["C0"], 0.0],
+                                                             [0.0] * 3, [0.0] * 3])
+        geometry = dict(nx=nx, ny=ny, ny_cl=0, ny_gdl=0, reaction_mode=0, periodic_x=0,
+                        closed_x=1, solid=None)
+        return params, fields, geometry
+    raise ValueError(f"unknown case kind {case['kind']!r}")

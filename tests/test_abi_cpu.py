@@ -40,22 +40,47 @@ def test_binding_loads_without_gpu(libpath):
     assert L.lbm_last_error() is not None
 
 
-def test_param_structs_match_header():
+def test_param_structs_match_header(tmp_path):
+    """The ctypes mirrors have the header's field names, offsets and sizes
+    (a C program compiled against the header prints them)."""
     src = open(HEADER).read()
     p = src[src.index("} lbm_domain_desc;"):src.index("} lbm_params;")]
-    doubles = re.findall(r"double ([\w, ]+);", p)
+    doubles = re.findall(r"double ([\w, ]+)(?:\[\d+\])*;", p)
     names = [n.strip() for grp in doubles for n in grp.split(",")]
-    assert names == list(lbm._PARAM_DOUBLES) + ["dp_in", "alpha_a"]
-    assert ctypes.sizeof(lbm.lbm_params) == 8 * len(names) + 16
-    assert lbm.lbm_params.dp_in.offset == 8 * len(lbm._PARAM_DOUBLES) + 16
-    assert ctypes.sizeof(lbm.lbm_domain_desc) == 8 * 4 + 16
+    assert names == list(lbm._PARAM_DOUBLES) + ["dp_in", "alpha_a", "buoy_gx", "buoy_gy",
+                                                 "T_buoy", "C_wall"]
+    fields = {"lbm_params": [f[0] for f in lbm.lbm_params._fields_],
+              "lbm_domain_desc": [f[0] for f in lbm.lbm_domain_desc._fields_]}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pemlbm.h"', "int main(void) {"]
+    for st, fl in fields.items():
+        lines.append(f'printf("{st} size %zu\\n", sizeof({st}));')
+        for f in fl:
+            lines.append(f'printf("{st} {f} %zu\\n", offsetof({st}, {f}));')
+    lines.append("return 0; }")
+    c = tmp_path / "abi.c"
+    c.write_text("\n".join(lines))
+    exe = tmp_path / "abi"
+    import subprocess
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(c), "-o",
+                           str(exe)])
+    out = subprocess.check_output([str(exe)], text=True).split("\n")
+    for line in filter(None, out):
+        st, f, v = line.split()
+        cls = getattr(lbm, st)
+        got = ctypes.sizeof(cls) if f == "size" else getattr(cls, f).offset
+        assert got == int(v), (st, f, got, v)
 
 
 @pytest.mark.parametrize("case", [workloads.cathode_200x40(),
                                   workloads.small_cathode(nx=40, ny=20, reaction_mode=1),
                                   workloads.cathode_blocks(nx=256, ny=128),
                                   dict(workloads.cathode_200x40(), inlet="pressure",
-                                       dp_in=2e-4, alpha_a=0.5)])
+                                       dp_in=2e-4, alpha_a=0.5),
+                                  workloads.natural_convection_cavity(32, Ra=1e5,
+                                                                      heated_bottom=True),
+                                  workloads.natural_convection_cavity(24, Ra=1e4, Da=1e-2,
+                                                                      phi=0.6),
+                                  workloads.kang_surface_reaction(30, 10, Da=2.0)])
 def test_product_and_oracle_unit_mappings_agree(case):
     """The product's unit helper and the oracle's independent mapping turn
     the same physical workload into the same lattice problem."""
@@ -63,7 +88,8 @@ def test_product_and_oracle_unit_mappings_agree(case):
     p2, m2, _ = lattice_problem(case)
     for k, v in p1.items():
         if k in p2:
-            assert v == pytest.approx(p2[k], rel=1e-13), k
+            np.testing.assert_allclose(np.ravel(v), np.ravel(p2[k]), rtol=1e-13, err_msg=k)
+    assert g1.get("closed_x", 0) == p2.get("closed_x", 0)
     for k in ("phi", "K", "alpha_T", "D_O2", "D_H2O"):
         np.testing.assert_allclose(f1[k], m2[k], rtol=1e-13)
     np.testing.assert_allclose(f1["rho_cp_ratio"], m2["sigma"], rtol=1e-13)
