@@ -626,6 +626,7 @@ def run_validation(args):
     cells = case["nx"] * case["ny"]
     stream = torch.cuda.Stream(device=dev)
     d = Domain.from_case(case, precision=args.precision, stream=stream.cuda_stream)
+    variant, _ = d.tune(20)
     W, K = max(args.warmup, 3), max(args.steps, 1)
     d.step(W)
     torch.cuda.synchronize()
@@ -655,7 +656,7 @@ def run_validation(args):
         "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
         "config": {"workload": f"{args.workload}-{case['nx']}x{case['ny']}",
                    "nx": case["nx"], "ny": case["ny"], "storage": args.precision,
-                   "parallelism": f"replicas{world}",
+                   "parallelism": f"replicas{world}", "step_variant": variant,
                    "l2": "inputs larger than L2 (two population buffers of "
                          f"{24 * cells * d_esize(args.precision) / 1e6:.0f} MB)",
                    **{k: case[k] for k in ("Ra", "Pr", "Da", "phi", "heated_bottom", "D")
@@ -663,7 +664,8 @@ def run_validation(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
                      "bytes_per_cell": bpc,
-                     "kernel": "k_step, extended instantiation (128 x 2 threads per block)"},
+                     "kernel": "k_step, extended instantiation (" +
+                               ("128 x 2" if variant <= 2 else "64 x 2") + " threads per block)"},
         "gpu_launches": K, "clocks": clk.summary(), "state_check": state,
     }
     if world == 1 and not args.no_cpu_baseline:

@@ -282,11 +282,14 @@ __device__ R pull_flow_edge(const Pops<S, CG> &src, const KArgsT<R> &a, const ui
 }
 
 // Anti-bounce-back of a wall link of scalar s held at value Cw (the
-// halfway wall's value, in deviation coordinates) given the bounced
-// population w.
+// halfway wall's value) given the bounced deviation w: in full values
+// g_in = -g_out + 2 w1 Cw, i.e. in deviations -w + 2 w1 Cw - 2 wr1 Cref,
+// evaluated as 2 w1 (Cw - Cref) + 2 (w1 - wr1) Cref so that a wall at the
+// reference value adds no rounding of the two large products.
 template <typename R>
 __device__ __forceinline__ R wall_value(const KArgsT<R> &a, const MatCoef<R> &mc, int s, R w, R Cw) {
-  return -w + R(2) * mc.w1[s] * Cw - R(2) * R(a.wr1[s]) * R(a.Cref[s]);
+  const R w1 = mc.w1[s], Cref = R(a.Cref[s]);
+  return -w + R(2) * w1 * (Cw - Cref) + R(2) * (w1 - R(a.wr1[s])) * Cref;
 }
 
 // Scalar link i of scalar s into cell (x, y); the bottom wall returns the
@@ -306,7 +309,7 @@ __device__ R pull_scalar_edge(const Pops<S, CG> &src, const KArgsT<R> &a, const 
   if (sy >= a.ny) {
     R w = R(src.at(q + OP[i], x, y));
     if (a.top_dirichlet)
-      w = -w + R(2) * mc.w1[s] * R(a.Ctop[s]) - R(2) * R(a.wr1[s]) * R(a.Cref[s]);
+      w = wall_value<R>(a, mc, s, w, R(a.Ctop[s]));
     return w;
   }
   if (sx < 0 || sx >= a.nx) {

@@ -85,10 +85,12 @@ void launch_step_v(const void *src, void *dst, const DevGeom &g, const KArgs &a,
   constexpr StepShape sh = kStepShapes[V];
   dim3 grid((a.nx + sh.bx - 1) / sh.bx, (a.ny + sh.by - 1) / sh.by);
   using R = typename Real<S>::type;
-  if (needs_extended(a)) {   // one shape (the first: no register cap) for every variant
-    constexpr StepShape s0 = kStepShapes[0];
-    dim3 g0((a.nx + s0.bx - 1) / s0.bx, (a.ny + s0.by - 1) / s0.by);
-    k_step<S, s0.bx, s0.by, s0.minb, false, true><<<g0, s0.bx * s0.by, 0, st>>>(
+  if (needs_extended(a)) {
+    // two shapes of the extended step: 128 x 2 at 80 registers (variants
+    // 0-2) and 64 x 2 at 64 registers (the rest); the tuner picks one
+    constexpr StepShape sx = kStepShapes[V <= 2 ? 1 : 7];
+    dim3 gx((a.nx + sx.bx - 1) / sx.bx, (a.ny + sx.by - 1) / sx.by);
+    k_step<S, sx.bx, sx.by, sx.minb, false, true><<<gx, sx.bx * sx.by, 0, st>>>(
         (const S *)src, (S *)dst, g.mask, g.mid, (const MatCoef<R> *)g.pal, narrow_args<R>(a));
     return;
   }
