@@ -465,9 +465,10 @@ def d_esize(precision):
 
 def end_to_end(case, precision, K, stream, interface_mode=0):
     """The user's job through the public API with host buffers: upload the
-    material from pinned host memory, reset, then K steps each followed by a
-    device->host read of the current density, and a final read of the
-    fields.  MLUPS over the wall-clock of the whole job."""
+    material from pinned host memory, reset, then K observed steps (each
+    step's current density and heat copied to pinned host arrays as it
+    completes, lbm_step_observe), and a final read of the fields.  MLUPS
+    over the wall-clock of the whole job."""
     import torch
     from paper_2103_01444_gb300.units import cathode_params
     from paper_2103_01444_gb300.lbm import Domain
@@ -482,11 +483,12 @@ def end_to_end(case, precision, K, stream, interface_mode=0):
     d.reset()
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    for _ in range(K):
-        d.step(1)
-        d.current_density(profile=False)
+    i_avg = torch.zeros(K, dtype=torch.float64).pin_memory().numpy()
+    heat = torch.zeros(K, dtype=torch.float64).pin_memory().numpy()
+    d.step_observe(K, i_avg, heat)      # every step's reaction copied to the host
     torch.cuda.synchronize()
     t2 = time.perf_counter()
+    assert np.isfinite(i_avg).all() and i_avg[-1] > 0
     out = d.fields()
     torch.cuda.synchronize()
     t3 = time.perf_counter()
@@ -499,7 +501,8 @@ def end_to_end(case, precision, K, stream, interface_mode=0):
             "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
             "breakdown_s": {"upload_and_reset": t1 - t0, "steps_with_reads": t2 - t1,
                             "fields_read": t3 - t2},
-            "includes": "material upload, reset, per-step current-density read, final fields read"}
+            "includes": "material upload, reset, per-step current-density and heat copy to the "
+                        "host (lbm_step_observe), final fields read"}
 
 
 def run_to_residual(args):

@@ -191,6 +191,18 @@ lbm_status lbm_step(lbm_domain *d, int64_t nsteps);
 lbm_status lbm_current_density(lbm_domain *d, double *i_avg_A_cm2, double *heat_W_cm2,
                                float *profile_nx);
 
+/* Observed stepping: advances nsteps steps like lbm_step and reports the
+ * reaction of every step, i_avg[k] and heat[k] (host arrays of nsteps
+ * doubles, A/cm^2 and W/cm^2 as lbm_current_density; either may be NULL,
+ * not both).  Each step's FP64 sums are copied to the host as soon as that
+ * step's reduction ends, without stopping the stream: chunks of 64 steps
+ * are replayed from CUDA graphs while the host converts the previous
+ * chunk.  Synchronises the stream before returning.  EINVAL for nsteps < 0
+ * or two NULL arrays; ENOMEM if the observation slots cannot be
+ * allocated. */
+lbm_status lbm_step_observe(lbm_domain *d, int64_t nsteps, double *i_avg_A_cm2,
+                            double *heat_W_cm2);
+
 /* Steady-state residual: r = max over X in {j_x, j_y, T - T_in, C_O2, C_H2O}
  * (moments of the post-collision state) of ||X - X_prev|| / ||X||, where
  * X_prev is the snapshot taken by the previous call (or by lbm_reset); the

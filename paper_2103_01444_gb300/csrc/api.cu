@@ -91,6 +91,12 @@ struct lbm_domain {
   double bref_next[3] = {0, 0, 0};   // reference b the next reset will use
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // observed stepping: per-step (J, heat) sums in device slots [2][64][2],
+  // copied every step into pinned host slots of the same shape; one graph
+  // per (starting buffer, slot half)
+  double *dobs = nullptr, *hobs = nullptr;
+  cudaGraphExec_t obs_graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  cudaEvent_t obs_done[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -188,6 +194,12 @@ void drop_graphs(lbm_domain *d) {
       cudaGraphExecDestroy(g);
       g = nullptr;
     }
+  for (auto &row : d->obs_graph)
+    for (auto &g : row)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
 }
 
 lbm_status launch_steps(lbm_domain *d, int64_t n) {
@@ -216,6 +228,46 @@ lbm_status ensure_graph(lbm_domain *d) {
   if (s != LBM_OK) return s;
   if (e != cudaSuccess) return fail(LBM_ECUDA, "graph capture: %s", cudaGetErrorString(e));
   e = cudaGraphInstantiate(&d->graph[start], gr, 0);
+  cudaGraphDestroy(gr);
+  if (e != cudaSuccess) return fail(LBM_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+// Observed steps: n steps (n <= kGraphSteps), each followed by the
+// catalyst reduction of that step into device slot half `half` and an
+// asynchronous copy of its (J, heat) sums to the pinned host slots.
+lbm_status launch_observed(lbm_domain *d, int64_t n, int half) {
+  const KArgs a = make_args(d);
+  const lbm_params &p = d->prm;
+  const double i_scale = 4.0 * p.F * p.c_tot * p.dx_cm / p.dt_s;
+  for (int64_t k = 0; k < n; ++k) {
+    lbm_status s = launch_steps(d, 1);
+    if (s != LBM_OK) return s;
+    const size_t slot = ((size_t)half * kGraphSteps + (size_t)k) * 2;
+    dispatch(d->desc.precision, [&](auto *tag) {
+      using S = std::remove_pointer_t<decltype(tag)>;
+      launch_catalyst<S>(d->pop[d->cur ^ 1], geom(d), a, i_scale, nullptr, d->colsum,
+                         d->dobs + slot, d->stream);
+    });
+    CK(cudaMemcpyAsync(d->hobs + slot, d->dobs + slot, 2 * sizeof(double),
+                       cudaMemcpyDeviceToHost, d->stream));
+  }
+  CK(cudaGetLastError());
+  return LBM_OK;
+}
+
+lbm_status ensure_obs_graph(lbm_domain *d, int half) {
+  cudaGraphExec_t &ge = d->obs_graph[d->cur][half];
+  if (ge) return LBM_OK;
+  const int start = d->cur;
+  cudaGraph_t gr = nullptr;
+  CK(cudaStreamBeginCapture(d->stream, cudaStreamCaptureModeThreadLocal));
+  lbm_status s = launch_observed(d, kGraphSteps, half);
+  cudaError_t e = cudaStreamEndCapture(d->stream, &gr);
+  d->cur = start;
+  if (s != LBM_OK) return s;
+  if (e != cudaSuccess) return fail(LBM_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&ge, gr, 0);
   cudaGraphDestroy(gr);
   if (e != cudaSuccess) return fail(LBM_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
   return LBM_OK;
@@ -362,9 +414,12 @@ lbm_status lbm_destroy_domain(lbm_domain *d) {
   drop_graphs(d);
   for (void *p : {d->pop[0], d->pop[1], (void *)d->mask, (void *)d->mid, d->pal, (void *)d->raw,
                   d->snap, (void *)d->partial, (void *)d->colsum, (void *)d->dsmall, (void *)d->dbad, (void *)d->dseed,
-                  (void *)d->scratch, (void *)d->dprofile})
+                  (void *)d->scratch, (void *)d->dprofile, (void *)d->dobs})
     if (p) cudaFree(p);
   if (d->hsmall) cudaFreeHost(d->hsmall);
+  if (d->hobs) cudaFreeHost(d->hobs);
+  for (auto e : d->obs_done)
+    if (e) cudaEventDestroy(e);
   if (d->ev0) cudaEventDestroy(d->ev0);
   if (d->ev1) cudaEventDestroy(d->ev1);
   if (d->own_stream && d->stream) cudaStreamDestroy(d->stream);
@@ -548,6 +603,56 @@ lbm_status lbm_current_density(lbm_domain *d, double *i_avg, double *heat, float
   CK(cudaStreamSynchronize(d->stream));
   if (i_avg) *i_avg = d->hsmall[0] * i_scale / d->nx;
   if (heat) *heat = d->hsmall[1] * q_scale / d->nx;
+  return LBM_OK;
+}
+
+lbm_status lbm_step_observe(lbm_domain *d, int64_t nsteps, double *i_avg, double *heat) {
+  lbm_status s = check_ready(d);
+  if (s != LBM_OK) return s;
+  if (nsteps < 0) return fail(LBM_EINVAL, "nsteps < 0");
+  if (nsteps > 0 && !i_avg && !heat) return fail(LBM_EINVAL, "nothing to observe (use lbm_step)");
+  if (!d->dobs) {
+    const size_t bytes = 2 * kGraphSteps * 2 * sizeof(double);
+    if (cudaMalloc(&d->dobs, bytes) != cudaSuccess || cudaMallocHost(&d->hobs, bytes) != cudaSuccess ||
+        cudaEventCreateWithFlags(&d->obs_done[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&d->obs_done[1], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(LBM_ENOMEM, "observation slots");
+    }
+  }
+  const lbm_params &p = d->prm;
+  const double i_scale = 4.0 * p.F * p.c_tot * p.dx_cm / p.dt_s;
+  const double q_scale = p.rho_cp_f * p.dx_cm / p.dt_s;
+  // chunks of up to kGraphSteps steps alternate between the two slot halves:
+  // while chunk c runs, the host reads chunk c - 1's slots
+  auto collect = [&](int half, int64_t first, int64_t n) -> lbm_status {
+    CK(cudaEventSynchronize(d->obs_done[half]));
+    for (int64_t k = 0; k < n; ++k) {
+      const double *v = d->hobs + ((size_t)half * kGraphSteps + (size_t)k) * 2;
+      if (i_avg) i_avg[first + k] = v[0] * i_scale / d->nx;
+      if (heat) heat[first + k] = v[1] * q_scale / d->nx;
+    }
+    return LBM_OK;
+  };
+  int64_t done = 0, prev_first = -1, prev_n = 0;
+  int half = 0;
+  while (done < nsteps) {
+    const int64_t n = std::min<int64_t>(kGraphSteps, nsteps - done);
+    if (n == kGraphSteps) {
+      if ((s = ensure_obs_graph(d, half)) != LBM_OK) return s;
+      CK(cudaGraphLaunch(d->obs_graph[d->cur][half], d->stream));   // even: cur unchanged
+    } else if ((s = launch_observed(d, n, half)) != LBM_OK) {
+      return s;
+    }
+    CK(cudaEventRecord(d->obs_done[half], d->stream));
+    if (prev_n > 0 && (s = collect(half ^ 1, prev_first, prev_n)) != LBM_OK) return s;
+    prev_first = done;
+    prev_n = n;
+    done += n;
+    d->steps += n;
+    half ^= 1;
+  }
+  if (prev_n > 0 && (s = collect(half ^ 1, prev_first, prev_n)) != LBM_OK) return s;
   return LBM_OK;
 }
 

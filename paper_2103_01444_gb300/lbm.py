@@ -24,7 +24,8 @@ EXPORTS = ("lbm_create_domain", "lbm_destroy_domain", "lbm_set_params", "lbm_set
            "lbm_reset", "lbm_step", "lbm_current_density", "lbm_residual", "lbm_get_fields",
            "lbm_get_state", "lbm_set_state", "lbm_get_mask", "lbm_get_step", "lbm_save_state",
            "lbm_load_state", "lbm_time_steps", "lbm_bytes_per_cell", "lbm_tune",
-           "lbm_set_variant", "lbm_residual_noalloc", "lbm_balances", "lbm_create_batch", "lbm_destroy_batch",
+           "lbm_set_variant", "lbm_residual_noalloc", "lbm_balances", "lbm_step_observe",
+           "lbm_create_batch", "lbm_destroy_batch",
            "lbm_batch_set_schedule", "lbm_batch_tune", "lbm_batch_step", "lbm_batch_time_steps",
            "lbm_grad", "lbm_vjp", "lbm_last_error")
 
@@ -78,6 +79,7 @@ def load_library(path: str = LIB_PATH):
         "lbm_current_density": [P, d, d, C.POINTER(C.c_float)],
         "lbm_residual": [P, d],
         "lbm_balances": [P, d],
+        "lbm_step_observe": [P, C.c_int64, d, d],
         "lbm_get_fields": [P, C.c_void_p, C.c_int32],
         "lbm_get_state": [P, d],
         "lbm_set_state": [P, d],
@@ -208,6 +210,17 @@ class Domain:
             self.h, C.byref(i_avg), C.byref(heat),
             None if prof is None else prof.ctypes.data_as(C.POINTER(C.c_float))))
         return i_avg.value, heat.value, prof
+
+    def step_observe(self, nsteps: int, i_avg=None, heat=None):
+        """nsteps steps with the reaction of every step: (i_avg, heat)
+        arrays (A/cm^2, W/cm^2).  Output arrays may be passed in (float64,
+        e.g. pinned)."""
+        i_avg = np.zeros(nsteps) if i_avg is None else i_avg
+        heat = np.zeros(nsteps) if heat is None else heat
+        assert i_avg.dtype == np.float64 and heat.dtype == np.float64
+        assert i_avg.size >= nsteps and heat.size >= nsteps
+        _check(self.L.lbm_step_observe(self.h, int(nsteps), _dp(i_avg), _dp(heat)))
+        return i_avg, heat
 
     BALANCE_KEYS = ("J", "heat", "in_mass", "in_T", "in_O2", "in_H2O",
                     "out_mass", "out_T", "out_O2", "out_H2O")

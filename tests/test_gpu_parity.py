@@ -445,3 +445,34 @@ def test_tune_leaves_the_reset_state():
     from paper_2103_01444_gb300.lbm import LbmError
     with pytest.raises(LbmError, match="ESTATE"):
         a.tune(2)
+
+
+def test_step_observe_reports_every_step():
+    """lbm_step_observe: the per-step current density and heat equal those
+    of stepping one step at a time and reading lbm_current_density, bit for
+    bit, over graph-replayed chunks and ragged remainders from both buffer
+    parities; the state is that of plain stepping; FP64 values match the
+    oracle's per-step reaction."""
+    case = dict(CASES["film-64x16"](), V_op=0.4)
+    a, b = gpu_domain(case, "fp64"), gpu_domain(case, "fp64")
+    ia, ha = [], []
+    for n in (131, 130):
+        i1, h1 = a.step_observe(n)
+        ia += list(i1)
+        ha += list(h1)
+    ib, hb = [], []
+    for _ in range(261):
+        b.step(1)
+        i, h, _ = b.current_density(profile=False)
+        ib.append(i)
+        hb.append(h)
+    assert ia == ib and ha == hb
+    np.testing.assert_array_equal(a.state(), b.state())
+    o = oracle_of(case)
+    for k in range(40):
+        o.step(1)
+        i_o, h_o, _ = o.current_density()
+        assert ia[k] == pytest.approx(i_o, rel=1e-11)
+        assert ha[k] == pytest.approx(h_o, rel=1e-11)
+    assert a.L.lbm_step_observe(a.h, 5, None, None) == 1     # EINVAL: nothing to observe
+    assert a.L.lbm_step_observe(a.h, -1, None, None) == 1
