@@ -271,7 +271,8 @@ lbm_status lbm_time_steps(lbm_domain *d, int64_t nsteps, double *elapsed_ms);
  * left it), keeps the fastest and returns its index and time per step (ms).
  * ESTATE after the first step.  lbm_set_variant selects one explicitly
  * (0 <= variant < 8; EINVAL otherwise).  All shapes give bit-identical
- * results. */
+ * results.  Untuned, FP32 domains use variant 7 (64 x 2 cells, 8 blocks
+ * per SM) and the others variant 0. */
 lbm_status lbm_tune(lbm_domain *d, int32_t trial_steps, int32_t *variant, double *best_ms);
 lbm_status lbm_set_variant(lbm_domain *d, int32_t variant);
 

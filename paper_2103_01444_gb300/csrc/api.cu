@@ -77,7 +77,7 @@ struct lbm_domain {
   void *snap = nullptr;        // residual snapshot [5][ny][nx], storage precision
   double *partial = nullptr;   // residual block partials [blocks][10]
   double *colsum = nullptr;    // catalyst column sums [2][nx]
-  int variant = 0;             // launch shape of the step kernel
+  int variant = 0;             // launch shape of the step kernel (lbm_tune picks one)
   double tuned_ms[kStepVariants] = {};
   double *dsmall = nullptr;    // device results (16 doubles)
   int *dbad = nullptr;
@@ -97,6 +97,8 @@ struct lbm_domain {
   double *dobs = nullptr, *hobs = nullptr;
   cudaGraphExec_t obs_graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   cudaEvent_t obs_done[2] = {nullptr, nullptr};
+  cudaStream_t obs_side = nullptr;             // the reductions, beside the steps
+  cudaEvent_t obs_fork = nullptr, obs_join = nullptr;
 };
 
 namespace {
@@ -233,25 +235,32 @@ lbm_status ensure_graph(lbm_domain *d) {
   return LBM_OK;
 }
 
-// Observed steps: n steps (n <= kGraphSteps), each followed by the
-// catalyst reduction of that step into device slot half `half` and an
-// asynchronous copy of its (J, heat) sums to the pinned host slots.
+// Observed steps: n steps (n <= kGraphSteps).  The reaction of a step is a
+// function of the state it starts from, so its catalyst reduction (into
+// device slot half `half`) and the asynchronous copy of its (J, heat) sums
+// to the pinned host slots run on the side stream concurrently with the
+// step itself; the next step, which overwrites that state, waits for them.
 lbm_status launch_observed(lbm_domain *d, int64_t n, int half) {
   const KArgs a = make_args(d);
   const lbm_params &p = d->prm;
   const double i_scale = 4.0 * p.F * p.c_tot * p.dx_cm / p.dt_s;
   for (int64_t k = 0; k < n; ++k) {
-    lbm_status s = launch_steps(d, 1);
-    if (s != LBM_OK) return s;
+    if (k > 0) CK(cudaStreamWaitEvent(d->stream, d->obs_join, 0));
+    CK(cudaEventRecord(d->obs_fork, d->stream));
+    CK(cudaStreamWaitEvent(d->obs_side, d->obs_fork, 0));
     const size_t slot = ((size_t)half * kGraphSteps + (size_t)k) * 2;
     dispatch(d->desc.precision, [&](auto *tag) {
       using S = std::remove_pointer_t<decltype(tag)>;
-      launch_catalyst<S>(d->pop[d->cur ^ 1], geom(d), a, i_scale, nullptr, d->colsum,
-                         d->dobs + slot, d->stream);
+      launch_catalyst<S>(d->pop[d->cur], geom(d), a, i_scale, nullptr, d->colsum,
+                         d->dobs + slot, d->obs_side);
     });
     CK(cudaMemcpyAsync(d->hobs + slot, d->dobs + slot, 2 * sizeof(double),
-                       cudaMemcpyDeviceToHost, d->stream));
+                       cudaMemcpyDeviceToHost, d->obs_side));
+    CK(cudaEventRecord(d->obs_join, d->obs_side));
+    lbm_status s = launch_steps(d, 1);
+    if (s != LBM_OK) return s;
   }
+  if (n > 0) CK(cudaStreamWaitEvent(d->stream, d->obs_join, 0));
   CK(cudaGetLastError());
   return LBM_OK;
 }
@@ -267,7 +276,7 @@ lbm_status ensure_obs_graph(lbm_domain *d, int half) {
   d->cur = start;
   if (s != LBM_OK) return s;
   if (e != cudaSuccess) return fail(LBM_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-  e = cudaGraphInstantiate(&ge, gr, 0);
+  e = cudaGraphInstantiateWithFlags(&ge, gr, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(gr);
   if (e != cudaSuccess) return fail(LBM_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
   return LBM_OK;
@@ -361,6 +370,9 @@ lbm_status lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
   d->nxp = (D.nx + align - 1) / align * align;
   d->plane = (long long)d->nxp * D.ny;
   d->esize = elem_size(D.precision);
+  // untuned default: 64 x 2 cells at 8 blocks per SM for FP32 storage (the
+  // tuner's usual choice at large sizes), the uncapped 128 x 2 otherwise
+  d->variant = D.precision == LBM_FP32 ? 7 : 0;
   auto cleanup = [&](lbm_status s) { lbm_destroy_domain(d); return s; };
   if (D.cuda_stream) {
     d->stream = (cudaStream_t)D.cuda_stream;
@@ -418,8 +430,9 @@ lbm_status lbm_destroy_domain(lbm_domain *d) {
     if (p) cudaFree(p);
   if (d->hsmall) cudaFreeHost(d->hsmall);
   if (d->hobs) cudaFreeHost(d->hobs);
-  for (auto e : d->obs_done)
+  for (auto e : {d->obs_done[0], d->obs_done[1], d->obs_fork, d->obs_join})
     if (e) cudaEventDestroy(e);
+  if (d->obs_side) cudaStreamDestroy(d->obs_side);
   if (d->ev0) cudaEventDestroy(d->ev0);
   if (d->ev1) cudaEventDestroy(d->ev1);
   if (d->own_stream && d->stream) cudaStreamDestroy(d->stream);
@@ -612,8 +625,16 @@ lbm_status lbm_step_observe(lbm_domain *d, int64_t nsteps, double *i_avg, double
   if (nsteps < 0) return fail(LBM_EINVAL, "nsteps < 0");
   if (nsteps > 0 && !i_avg && !heat) return fail(LBM_EINVAL, "nothing to observe (use lbm_step)");
   if (!d->dobs) {
+    // the reductions run at the highest priority, so that their few blocks
+    // are dispatched while the step's blocks are still being issued
+    // instead of after them
+    int lo_prio = 0, hi_prio = 0;
     const size_t bytes = 2 * kGraphSteps * 2 * sizeof(double);
     if (cudaMalloc(&d->dobs, bytes) != cudaSuccess || cudaMallocHost(&d->hobs, bytes) != cudaSuccess ||
+        cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&d->obs_side, cudaStreamNonBlocking, hi_prio) != cudaSuccess ||
+        cudaEventCreateWithFlags(&d->obs_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&d->obs_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&d->obs_done[0], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&d->obs_done[1], cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
