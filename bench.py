@@ -404,18 +404,22 @@ def sweep_run(cases, args, stream):
     K = args.sweep_steps
     b.step(16)
     t_best = b.time_steps(K) / 1e3
+    names = ["graph", "persistent", "per-case", "concurrent"]
     b.set_schedule("per-case", variant=var)
     b.step(4)
     t_naive = b.time_steps(K) / 1e3
-    b.set_schedule("persistent" if sched == 0 else "graph", variant=var)
-    b.step(4)
-    t_other = b.time_steps(K) / 1e3
     n = len(cases)
+    others = {}
+    for other in ("graph", "persistent", "concurrent"):
+        if other != names[sched]:
+            b.set_schedule(other, variant=var if other != "persistent" else 6)
+            b.step(4)
+            others[other] = n * K / (b.time_steps(K) / 1e3)
     out = {"unit": "cases*steps/s", "cases": n, "cells": cells, "steps": K,
-           "value": n * K / t_best, "schedule": ["graph", "persistent"][sched],
+           "value": n * K / t_best, "schedule": names[sched],
            "variant": var, "mlups": cells * K / t_best / 1e6,
            "per_case_launches": n * K / t_naive,
-           "other_schedule": n * K / t_other,
+           "other_schedules": others,
            "speedup_vs_per_case": t_naive / t_best}
     b.close()
     for d in doms:

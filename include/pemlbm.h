@@ -330,11 +330,15 @@ lbm_status lbm_vjp(lbm_domain *d, const double *lam_next, double *lam_prev, doub
  *      barrier wait gives up after spin_limit polls (<= 0 keeps the current
  *      limit, 2^24 by default) and the call returns ETIMEOUT, leaving the
  *      case states undefined (reset or load them);
- *   2  one launch per case and step, no graph (the unbatched reference).
+ *   2  one launch per case and step, no graph (the unbatched reference);
+ *   3  one stream per case, each case's steps a chain of single-domain
+ *      launches (shape `variant`), the chains running concurrently; long
+ *      runs replayed from one graph, captured again when a case was stepped
+ *      on its own or its arguments changed.
  * All schedules give bit-identical states.  lbm_batch_tune, called between
- * lbm_reset and the first step of every case, times schedule 0 with every
- * launch shape and schedule 1 over trial_steps repetitions of the first
- * step, keeps the fastest and leaves the states as reset left them. */
+ * lbm_reset and the first step of every case, times schedules 0 and 3 with
+ * every launch shape and schedule 1 over trial_steps repetitions of the
+ * first step, keeps the fastest and leaves the states as reset left them. */
 typedef struct lbm_batch lbm_batch; /* opaque */
 lbm_status lbm_create_batch(lbm_domain *const *domains, int32_t ncases, lbm_batch **out);
 lbm_status lbm_destroy_batch(lbm_batch *b);

@@ -1372,6 +1372,15 @@ struct lbm_batch {
   cudaGraphExec_t graph = nullptr;
   std::vector<cudaEvent_t> ev;      // one per domain, for stream ordering
   cudaEvent_t ev_batch = nullptr, ev0 = nullptr, ev1 = nullptr;
+  // schedule 3: one stream ("lane") per case, each case's steps a chain of
+  // single-domain launches; the chains run concurrently, replayed from one
+  // graph captured for the cases' current buffers (conc_cur)
+  std::vector<cudaStream_t> lanes;
+  std::vector<cudaEvent_t> lane_done;
+  cudaEvent_t ev_fork = nullptr;
+  cudaGraphExec_t conc_graph = nullptr;
+  std::vector<int> conc_cur;
+  std::vector<KArgs> conc_args;     // the arguments the graph's launches carry
 };
 
 namespace {
@@ -1383,6 +1392,48 @@ void drop_batch_graph(lbm_batch *b) {
     cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
   }
+  if (b->conc_graph) {
+    cudaGraphExecDestroy(b->conc_graph);
+    b->conc_graph = nullptr;
+  }
+}
+
+// Schedule 3: n steps of every case, each case on its own lane stream,
+// forked from and joined back into the batch stream.  fixed_parity: every
+// step starts from the case's current state (tuner trials).
+lbm_status batch_lanes(lbm_batch *b, int64_t n, bool fixed_parity) {
+  const int nc = (int)b->doms.size();
+  if ((int)b->lanes.size() != nc) {
+    b->lanes.assign(nc, nullptr);
+    b->lane_done.assign(nc, nullptr);
+    for (int c = 0; c < nc; ++c)
+      if (cudaStreamCreateWithFlags(&b->lanes[c], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&b->lane_done[c], cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LBM_ECUDA, "lane streams for the concurrent schedule");
+      }
+    if (cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(LBM_ECUDA, "cudaEventCreate failed");
+    }
+  }
+  CK(cudaEventRecord(b->ev_fork, b->stream));
+  for (int c = 0; c < nc; ++c) {
+    lbm_domain *d = b->doms[c];
+    const KArgs a = make_args(d);
+    CK(cudaStreamWaitEvent(b->lanes[c], b->ev_fork, 0));
+    for (int64_t k = 0; k < n; ++k) {
+      const int src = fixed_parity ? d->cur : (int)(d->cur ^ (k & 1));
+      dispatch(b->precision, [&](auto *tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        launch_step<S>(d->pop[src], d->pop[src ^ 1], geom(d), a, b->variant, b->lanes[c]);
+      });
+    }
+    CK(cudaEventRecord(b->lane_done[c], b->lanes[c]));
+    CK(cudaStreamWaitEvent(b->stream, b->lane_done[c], 0));
+  }
+  CK(cudaGetLastError());
+  return LBM_OK;
 }
 
 // Tile prefix sums of all cases for a bx x by tile shape.
@@ -1454,6 +1505,40 @@ void batch_launch_steps(lbm_batch *b, int64_t n, int parity0) {
 
 lbm_status batch_run(lbm_batch *b, int64_t nsteps, bool fixed_parity) {
   const int n = (int)b->doms.size();
+  if (b->schedule == 3) {              // concurrent chains of single-domain launches
+    if (fixed_parity) return batch_lanes(b, nsteps, true);
+    std::vector<int> cur(n);
+    std::vector<KArgs> args(n);
+    for (int c = 0; c < n; ++c) {
+      cur[c] = b->doms[c]->cur;
+      args[c] = make_args(b->doms[c]);
+    }
+    // the graph bakes in each case's buffers and arguments: recapture when
+    // a case was stepped alone or its parameters changed
+    if (b->conc_graph &&
+        (cur != b->conc_cur ||
+         std::memcmp(args.data(), b->conc_args.data(), sizeof(KArgs) * n) != 0))
+      drop_batch_graph(b);
+    int64_t left = nsteps;
+    while (left >= 2 * kBatchGraphSteps) {
+      if (!b->conc_graph) {
+        cudaGraph_t gr = nullptr;
+        CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        lbm_status s = batch_lanes(b, kBatchGraphSteps, false);
+        cudaError_t e = cudaStreamEndCapture(b->stream, &gr);
+        if (s != LBM_OK) return s;
+        if (e != cudaSuccess) return fail(LBM_ECUDA, "lane graph capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&b->conc_graph, gr, 0);
+        cudaGraphDestroy(gr);
+        if (e != cudaSuccess) return fail(LBM_ECUDA, "lane graph instantiate: %s", cudaGetErrorString(e));
+        b->conc_cur = cur;
+        b->conc_args = args;
+      }
+      CK(cudaGraphLaunch(b->conc_graph, b->stream));   // even count: parities return
+      left -= kBatchGraphSteps;
+    }
+    return left > 0 ? batch_lanes(b, left, false) : LBM_OK;
+  }
   if (b->schedule == 2) {              // one launch per case and step, no graph
     for (int64_t k = 0; k < nsteps; ++k)
       for (lbm_domain *d : b->doms) {
@@ -1588,8 +1673,12 @@ lbm_status lbm_destroy_batch(lbm_batch *b) {
   if (b->hcases) cudaFreeHost(b->hcases);
   for (auto e : b->ev)
     if (e) cudaEventDestroy(e);
-  for (auto e : {b->ev_batch, b->ev0, b->ev1})
+  for (auto e : {b->ev_batch, b->ev0, b->ev1, b->ev_fork})
     if (e) cudaEventDestroy(e);
+  for (auto e : b->lane_done)
+    if (e) cudaEventDestroy(e);
+  for (auto st : b->lanes)
+    if (st) cudaStreamDestroy(st);
   delete b;
   return LBM_OK;
 }
@@ -1597,7 +1686,7 @@ lbm_status lbm_destroy_batch(lbm_batch *b) {
 lbm_status lbm_batch_set_schedule(lbm_batch *b, int32_t schedule, int32_t variant,
                                   int64_t spin_limit) {
   if (!b) return fail(LBM_EINVAL, "null batch");
-  if (schedule < 0 || schedule > 2) return fail(LBM_EINVAL, "schedule must be 0, 1 or 2");
+  if (schedule < 0 || schedule > 3) return fail(LBM_EINVAL, "schedule must be 0, 1, 2 or 3");
   if (variant < 0 || variant >= kStepVariants) return fail(LBM_EINVAL, "variant %d outside [0, %d)", variant, kStepVariants);
   b->schedule = schedule;
   if (b->variant != variant) drop_batch_graph(b);
@@ -1672,6 +1761,7 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, int32_t *schedule, 
   };
   for (int v = 0; v < kStepVariants && s == LBM_OK; ++v) s = trial(0, v);
   if (s == LBM_OK) s = trial(1, 6);
+  for (int v = 0; v < kStepVariants && s == LBM_OK; ++v) s = trial(3, v);
   // the trials wrote each case's next state into its other buffer: restore
   for (lbm_domain *d : b->doms) {
     const KArgs a = make_args(d);

@@ -326,7 +326,7 @@ class Batch:
     """Many domains stepped together (lbm_create_batch); the domains stay
     usable through their own methods."""
 
-    SCHEDULES = {"graph": 0, "persistent": 1, "per-case": 2}
+    SCHEDULES = {"graph": 0, "persistent": 1, "per-case": 2, "concurrent": 3}
 
     def __init__(self, domains):
         self.L = load_library()
