@@ -543,9 +543,12 @@ k_adj_interior(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
 // runs the cell's collision reverse in between.  lam_complete: lambda^n
 // holds every link in full (the seed, or the caller's), O_in and V_in are
 // zero.  seed_cell >= 0: the "CL temperature" seed on a zero lambda^n.
-constexpr int kEdgeWarps = 4;
+constexpr int kEdgeWarps = 4, kEdgeMinBlocks = 1;
+// Launch order of a reverse step: the edge kernel before (true) or after
+// the interior kernel; the first one's blocks are dispatched first.
+constexpr bool kAdjEdgeFirst = true;
 template <typename S>
-__global__ void __launch_bounds__(32 * kEdgeWarps)
+__global__ void __launch_bounds__(32 * kEdgeWarps, kEdgeMinBlocks)
 k_adj_edge(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
            const uint16_t *__restrict__ mid,
            const MatCoef<typename Real<S>::type> *__restrict__ pal,

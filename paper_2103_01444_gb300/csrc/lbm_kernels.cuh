@@ -500,16 +500,19 @@ void launch_adj_step(const void *src, const DevGeom &g, const KArgs &a, int fick
   const KArgsT<R> an = narrow_args<R>(a);
   const AdjBufs<R> B = adj_bufs<R>(b);
   const MatCoef<R> *pal = (const MatCoef<R> *)g.pal;
-  if (b.n_edge > 0) {
-    cudaEventRecord(fork, st);
+  auto edge = [&] {
+    if (b.n_edge <= 0) return;
     cudaStreamWaitEvent(side, fork, 0);
     k_adj_edge<S><<<(b.n_edge + kEdgeWarps - 1) / kEdgeWarps, 32 * kEdgeWarps, 0, side>>>(
         (const S *)src, g.mask, g.mid, pal, an, fickian, B, b.cells, b.n_edge, seed_cell,
         lam_complete);
     cudaEventRecord(join, side);
-  }
+  };
+  if (b.n_edge > 0) cudaEventRecord(fork, st);
+  if (kAdjEdgeFirst) edge();
   k_adj_interior<S><<<dim3((a.nx + 127) / 128, a.ny), 128, 0, st>>>((const S *)src, g.mask, g.mid,
                                                                     pal, an, fickian, B);
+  if (!kAdjEdgeFirst) edge();
   if (b.n_edge > 0) cudaStreamWaitEvent(st, join, 0);
 }
 
