@@ -257,6 +257,52 @@ def cpu_baseline(case, seconds_target=15.0):
     return cells * n / dt / 1e6, cores, f"{n} oracle steps of the {case['nx']}x{case['ny']} lattice after 1 warm-up step"
 
 
+_SINGLE_CORE = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+from oracle import Oracle
+from oracle.params import lattice_problem
+from paper_2103_01444_gb300 import workloads
+out = {{}}
+for name, case, n in (("cathode-1024x256-blocks", workloads.cathode_blocks(1024, 256), 6),
+                      ("cathode-200x40 (the 5000-step FP64 case)", workloads.cathode_200x40(), 400)):
+    o = Oracle(*lattice_problem(case))
+    o.step(1)
+    t = time.perf_counter()
+    o.step(n)
+    out[name] = [case["nx"] * case["ny"] * n / (time.perf_counter() - t) / 1e6, n]
+print(json.dumps(out))
+"""
+
+
+def cpu_baseline_extra():
+    """The oracle on one host core (OMP_NUM_THREADS=1, a child process) and
+    on all cores for the small FP64 case: bounded samples, MLUPS."""
+    import subprocess
+    out = {}
+    try:
+        env = dict(os.environ, OMP_NUM_THREADS="1")
+        r = subprocess.run([sys.executable, "-c", _SINGLE_CORE.format(root=ROOT)], env=env,
+                           capture_output=True, text=True, timeout=120)
+        for name, (v, n) in json.loads(r.stdout.strip().splitlines()[-1]).items():
+            out[f"single_core {name}"] = {"value": v, "unit": UNIT, "cores": 1,
+                                          "sample": f"{n} oracle steps after 1 warm-up step"}
+    except Exception as e:   # the extra figures never fail the run
+        out["single_core"] = {"error": str(e)[:200]}
+    from oracle import Oracle
+    from oracle.params import lattice_problem
+    case = workloads.cathode_200x40()
+    o = Oracle(*lattice_problem(case))
+    o.step(1)
+    t = time.perf_counter()
+    o.step(1000)
+    cores = int(os.environ.get("OMP_NUM_THREADS", len(os.sched_getaffinity(0))))
+    out["all_cores cathode-200x40"] = {"value": 200 * 40 * 1000 / (time.perf_counter() - t) / 1e6,
+                                       "unit": UNIT, "cores": cores,
+                                       "sample": "1000 oracle steps after 1 warm-up step"}
+    return out
+
+
 def reference_sample(args, budget_s=90.0):
     """Largest lattice of the same recipe (halving nx and ny from the bench
     size) whose W + K oracle steps fit the time budget."""
@@ -388,7 +434,7 @@ def run_ours(args):
     if world == 1 and not args.no_cpu_baseline:
         v, cores, sample = cpu_baseline(case)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": sample}
+                                "sample": sample, "other_samples": cpu_baseline_extra()}
     print(json.dumps(line), flush=True)
 
 
