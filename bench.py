@@ -506,6 +506,9 @@ def adjoint_ratio(args, stream):
     d.close()
     return {"unit": "adjoint/forward time", "value": t_adj / t_fwd, "steps": N,
             "segment": int(np.ceil(np.sqrt(N))), "forward_s": t_fwd, "adjoint_s": t_adj,
+            # lbm_grad runs the forward sweep itself (the N steps that give J, with a
+            # checkpoint copy every segment); what it adds to it is the reverse sweep
+            "reverse_sweep_over_forward": (t_adj - t_fwd) / t_fwd,
             "workload": "cathode-1024x256-blocks", "objective": "mean current density"}
 
 
