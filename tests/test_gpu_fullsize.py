@@ -59,3 +59,46 @@ def test_sampled_columns_one_step(precision, mode, tol):
         worst = max(worst, err)
         assert err < tol, (xc, err)
     print(f"worst scaled one-step difference over {len(cols)} columns: {worst:.3e}")
+
+
+@pytest.mark.parametrize("kind", ["cavity", "kang"])
+def test_validation_setups_sampled_columns_one_step(kind):
+    """The same column check for the validation set-ups at the benchmark's
+    sizes and tuned launch shape (the extended step instantiation): a
+    2048 x 2048 cavity at Ra 1e6 with a heated bottom, and the 4096 x 1024
+    surface-reaction box.  The window's own x ends are walls; only columns
+    whose neighbours lie inside the window, or that sit on the lattice's
+    real walls, are compared."""
+    from paper_2103_01444_gb300.build import build
+    from paper_2103_01444_gb300.lbm import Domain
+    build()
+    if kind == "cavity":
+        case = workloads.natural_convection_cavity(2048, Ra=1e6, heated_bottom=True)
+    else:
+        case = workloads.kang_surface_reaction(nx=4096, ny=1024, Da=1.0)
+    nx, ny = case["nx"], case["ny"]
+    d = Domain.from_case(case, precision="fp32")
+    d.tune(5)
+    d.step(300)
+    s0 = d.state()
+    d.step(1)
+    s1 = d.state()
+    params, material, _ = lattice_problem(case)
+    rng = np.random.default_rng(12)
+    cols = sorted(set([0, 1, 63, 64, nx // 2, nx - 2, nx - 1] + list(rng.integers(0, nx, 16))))
+    scale = np.abs(s1).reshape(24, -1).max(axis=1)
+    worst = 0.0
+    for xc in cols:
+        x0 = min(max(xc - 1, 0), nx - 3)
+        k = xc - x0
+        win = {key: (v[:, x0:x0 + 3] if isinstance(v, np.ndarray) and v.ndim == 2 else v)
+               for key, v in material.items()}
+        o = Oracle(dict(params, nx=3), win, None)
+        o.f = np.ascontiguousarray(s0[:9, :, x0:x0 + 3])
+        o.g = np.ascontiguousarray(s0[9:, :, x0:x0 + 3].reshape(3, 5, ny, 3))
+        o.step(1)
+        ref = np.concatenate([o.f, o.g.reshape(15, ny, 3)])[:, :, k]
+        err = (np.abs(s1[:, :, xc] - ref).max(axis=1) / scale).max()
+        worst = max(worst, err)
+        assert err < 3e-6, (xc, err)
+    print(f"{kind}: worst scaled one-step difference over {len(cols)} columns: {worst:.3e}")
