@@ -87,6 +87,7 @@ def test_validation_setups_sampled_columns_one_step(kind):
     rng = np.random.default_rng(12)
     cols = sorted(set([0, 1, 63, 64, nx // 2, nx - 2, nx - 1] + list(rng.integers(0, nx, 16))))
     scale = np.abs(s1).reshape(24, -1).max(axis=1)
+    scale = np.where(scale > 0, scale, 1.0)   # the cavity's H2O planes are exactly zero
     worst = 0.0
     for xc in cols:
         x0 = min(max(xc - 1, 0), nx - 3)
