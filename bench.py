@@ -71,6 +71,10 @@ def parse():
                          "the residual (checked every 100 steps) is below TOL, or until "
                          "--max-seconds of stepping; one JSON line with steps and wall time")
     ap.add_argument("--max-seconds", type=float, default=240.0)
+    ap.add_argument("--cavity-study", action="store_true",
+                    help="steady differentially heated cavities (Sec. 3) at Ra 1e3..1e5 on "
+                         "three grids: wall Nusselt numbers, their agreement and grid "
+                         "convergence; its own line")
     ap.add_argument("--rounding", default="nearest", choices=["nearest", "stochastic"],
                     help="16-bit storage: round to nearest even, or stochastic rounding")
     ap.add_argument("--precision-errors", type=int, default=0, metavar="NSTEPS",
@@ -558,6 +562,57 @@ def end_to_end(case, precision, K, stream, interface_mode=0):
                         "host (lbm_step_observe), final fields read"}
 
 
+def run_cavity_study(args):
+    """The clear cavity of Sec. 3 with the left wall hot, the right wall cold
+    and the top and bottom insulated, run to a steady state (residual below
+    1e-7, checked every 1000 steps, at most 40 diffusion times L^2/alpha) on
+    grids of 32, 64 and 128 cells for Ra 1e3 and 1e4 and of 64, 128 and 256
+    cells for Ra 1e5: the mean Nusselt numbers of the hot and the cold wall
+    (equal at a steady state), the largest velocities in units of alpha / L,
+    and the observed order of convergence of Nu between the grids."""
+    import torch
+    from paper_2103_01444_gb300.build import build
+    from paper_2103_01444_gb300.lbm import Domain, LbmError
+    build()
+    out = []
+    for Ra, grids in ((1e3, (32, 64, 128)), (1e4, (32, 64, 128)), (1e5, (64, 128, 256))):
+        row = {"Ra": Ra, "grids": []}
+        for n in grids:
+            case = workloads.natural_convection_cavity(n, Ra=Ra)
+            d = Domain.from_case(case, precision=args.precision)
+            alpha = d.params["nu"] / case["Pr"]
+            dT = case["T_hot"] - case["T_cold"]
+            cap = int(40 * n * n / alpha)
+            t0 = time.perf_counter()
+            d.residual()
+            steps, r = 0, float("inf")
+            try:
+                while steps < cap and r >= 1e-7:
+                    d.step(1000)
+                    steps += 1000
+                    r = d.residual()
+            except LbmError as e:       # diverged: reported, not fatal
+                row["grids"].append({"n": n, "steps": steps, "error": str(e)})
+                d.close()
+                continue
+            b = d.balances()
+            f = d.fields()
+            torch.cuda.synchronize()
+            row["grids"].append({
+                "n": n, "steps": steps, "residual": r, "wall_s": time.perf_counter() - t0,
+                "Nu_hot": b["in_T"] / (alpha * dT), "Nu_cold": -b["out_T"] / (alpha * dT),
+                "u_max": float(np.abs(f["ux"]).max()) * n / alpha,
+                "v_max": float(np.abs(f["uy"]).max()) * n / alpha})
+            d.close()
+        nu = [g.get("Nu_hot", float("nan")) for g in row["grids"]]
+        if np.all(np.isfinite(nu)) and abs(nu[2] - nu[1]) > 0 and abs(nu[1] - nu[0]) > 0:
+            row["observed_order"] = float(np.log2(abs(nu[1] - nu[0]) / abs(nu[2] - nu[1])))
+            row["Nu_extrapolated"] = nu[2] + (nu[2] - nu[1]) / (2 ** row["observed_order"] - 1)
+        out.append(row)
+    print(json.dumps({"metric": "steady cavity Nusselt numbers", "storage": args.precision,
+                      "Pr": 0.71, "results": out}), flush=True)
+
+
 def run_to_residual(args):
     """The separate run of the production cathode to residual < TOL: steps
     and wall time from reset, the residual r = max over (u_x, u_y, T - T_in,
@@ -737,6 +792,8 @@ if __name__ == "__main__":
         run_reference(a)
     elif a.workload in ("cavity", "porous-cavity", "kang"):
         run_validation(a)
+    elif a.cavity_study:
+        run_cavity_study(a)
     elif a.to_residual > 0:
         run_to_residual(a)
     elif a.precision_errors > 0:
