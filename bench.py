@@ -564,8 +564,10 @@ def end_to_end(case, precision, K, stream, interface_mode=0):
 
 def run_cavity_study(args):
     """The clear cavity of Sec. 3 with the left wall hot, the right wall cold
-    and the top and bottom insulated, run to a steady state (residual below
-    1e-7, checked every 1000 steps, at most 40 diffusion times L^2/alpha) on
+    and the top and bottom insulated, run to a steady state in FP64 storage
+    (residual below 1e-10, checked every 1000 steps, at most 40 diffusion
+    times L^2/alpha; FP32 storage drifts away from the steady state over
+    millions of steps in the closed cavity) on
     grids of 32, 64 and 128 cells for Ra 1e3 and 1e4 and of 64, 128 and 256
     cells for Ra 1e5: the mean Nusselt numbers of the hot and the cold wall
     (equal at a steady state), the largest velocities in units of alpha / L,
@@ -579,7 +581,7 @@ def run_cavity_study(args):
         row = {"Ra": Ra, "grids": []}
         for n in grids:
             case = workloads.natural_convection_cavity(n, Ra=Ra)
-            d = Domain.from_case(case, precision=args.precision)
+            d = Domain.from_case(case, precision="fp64")
             alpha = d.params["nu"] / case["Pr"]
             dT = case["T_hot"] - case["T_cold"]
             cap = int(40 * n * n / alpha)
@@ -587,7 +589,7 @@ def run_cavity_study(args):
             d.residual()
             steps, r = 0, float("inf")
             try:
-                while steps < cap and r >= 1e-7:
+                while steps < cap and r >= 1e-10:
                     d.step(1000)
                     steps += 1000
                     r = d.residual()
@@ -609,7 +611,7 @@ def run_cavity_study(args):
             row["observed_order"] = float(np.log2(abs(nu[1] - nu[0]) / abs(nu[2] - nu[1])))
             row["Nu_extrapolated"] = nu[2] + (nu[2] - nu[1]) / (2 ** row["observed_order"] - 1)
         out.append(row)
-    print(json.dumps({"metric": "steady cavity Nusselt numbers", "storage": args.precision,
+    print(json.dumps({"metric": "steady cavity Nusselt numbers", "storage": "fp64",
                       "Pr": 0.71, "results": out}), flush=True)
 
 
