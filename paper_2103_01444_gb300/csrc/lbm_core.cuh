@@ -60,25 +60,23 @@ template <bool CG, typename S> __device__ __forceinline__ auto ldp(const S *p) {
 
 // Stochastic rounding of a step's 16-bit stores: unbiased, E[stored] = v,
 // so increments far below half an ulp of a stored value still accumulate.
-// r holds uniform random bits.  BF16 keeps the top 16 bits of the FP32
-// pattern: adding 16 random bits below them and truncating rounds the
-// magnitude up with probability equal to the dropped fraction.  FP16 picks
-// between the neighbours toward and away from zero with that probability.
-__device__ __forceinline__ void st_sr(__nv_bfloat16 *p, float v, unsigned r) {
-  const unsigned b = __float_as_uint(v) + (r & 0xffffu);
+// r16 holds 16 uniform random bits.  Both formats add a uniform fraction of
+// the 16-bit spacing to the magnitude and round toward zero, which rounds
+// the magnitude up with probability equal to the dropped fraction.  BF16
+// keeps the top 16 bits of the FP32 pattern, so the fraction is added to
+// the 16 bits below them.  FP16's spacing at |v| is 2^(E - 10) for an FP32
+// exponent E of a normal FP16 value and 2^-24 below 2^-14; the FP32 sum
+// v + sign(v) u spacing rounds at 2^-13 of that spacing or finer, a bias
+// below 1e-4 of one rounding step.
+__device__ __forceinline__ void st_sr(__nv_bfloat16 *p, float v, unsigned r16) {
+  const unsigned b = __float_as_uint(v) + r16;
   *reinterpret_cast<unsigned short *>(p) = (unsigned short)(b >> 16);
 }
-__device__ __forceinline__ void st_sr(__half *p, float v, unsigned r) {
-  const __half lo = __float2half_rz(v);
-  const float lof = __half2float(lo), d = v - lof;   // exact (Sterbenz, or lof = 0)
-  if (d == 0.0f) {
-    *p = lo;
-    return;
-  }
-  const __half hi = v > 0.0f ? __float2half_ru(v) : __float2half_rd(v);
-  const float span = __half2float(hi) - lof;
-  const float u = (float)(r >> 8) * (1.0f / 16777216.0f);   // [0, 1)
-  *p = (v > 0.0f ? (u * span < d) : (u * span > d)) ? hi : lo;
+__device__ __forceinline__ void st_sr(__half *p, float v, unsigned r16) {
+  const unsigned e = __float_as_uint(v) & 0x7f800000u;
+  const float spacing = __uint_as_float(max(e, 113u << 23) - (10u << 23));
+  const float a = fmaf(copysignf(spacing, v), (float)r16 * (1.0f / 65536.0f), v);
+  *p = __float2half_rz(a);
 }
 // Random bits for cell c of a step: a 32-bit integer hash of (c, seed), and
 // a xorshift stream from it for the cell's 24 stores.

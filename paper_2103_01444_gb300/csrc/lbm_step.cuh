@@ -42,12 +42,25 @@ __device__ __forceinline__ void cell_update(const S *__restrict__ src_p, S *__re
   collide_flow<R, X>(a, mc, u, cell.f, o);
   // 16-bit storage with stochastic rounding: a random stream per cell and
   // step (hash of the cell and the device step counter)
-  unsigned rs = 0;
+  // (16 bits per store: each xorshift draw serves two stores)
+  unsigned rs = 0, rbits = 0;
+  bool rhalf = false;
   if constexpr (SR)
     rs = hash32((unsigned)c * 0x9e3779b9u ^ hash32(__ldg(a.seed_ctr) + 0x632be5abu)) | 1u;
   auto store = [&](S *p, R v) {
-    if constexpr (SR) st_sr(p, v, xorshift32(rs));
-    else st_r(p, v);
+    if constexpr (SR) {
+      unsigned r16;
+      if (rhalf) {
+        r16 = rbits >> 16;
+      } else {
+        rbits = xorshift32(rs);
+        r16 = rbits & 0xffffu;
+      }
+      rhalf = !rhalf;
+      st_sr(p, v, r16);
+    } else {
+      st_r(p, v);
+    }
   };
   S *out = dst + c;
   if (live) {

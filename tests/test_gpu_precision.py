@@ -164,3 +164,60 @@ def test_stochastic_rounding_keeps_the_slow_fields():
     for prec in ("bf16", "fp16"):
         for k in ("T", "C_H2O"):
             assert errs[prec, "stochastic"][k] < errs[prec, "nearest"][k] / 3, (prec, k)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_stochastic_rounding_picks_a_neighbour_without_bias(precision):
+    """One stochastically rounded 16-bit step from a given state stores, for
+    every population, one of the two 16-bit neighbours of the FP32 step of
+    that state (the one toward zero, or the next one away from it), and over
+    64 repetitions with fresh random bits the stored values average to the
+    FP32 values: the mean offset is zero within the sampling error."""
+    from paper_2103_01444_gb300.lbm import Domain
+    case = workloads.small_cathode(nx=70, ny=24, reaction_mode=0, grains=True, seed=9)
+    d16 = Domain.from_case(case, precision=precision, rounding="stochastic")
+    d16.step(40)
+    blob16 = d16.save_state()
+    b16, cur16 = _buffers(d16, blob16, np.uint16)
+    d32 = _domain(case, "fp32")
+    blob32 = bytearray(d32.save_state())
+    if precision == "bf16":
+        as32 = (b16.astype(np.uint32) << 16).view(np.float32)
+    else:
+        as32 = b16.view(np.float16).astype(np.float32)
+    blob32[:HEADER] = bytes(blob32[:8]) + blob16[8:16] + bytes(blob32[16:20]) + blob16[20:HEADER]
+    blob32[HEADER:] = np.ascontiguousarray(as32).tobytes()
+    d32.load_state(bytes(blob32))
+    d32.step(1)
+    n32, c32 = _buffers(d32, d32.save_state(), np.float32)
+    f = np.ascontiguousarray(n32[c32][:, :, :d16.nx]).astype(np.float64)
+    fluid = np.broadcast_to(((d16.mask() & 3) != 3)[None], f.shape)
+    # the two neighbours of f in the 16-bit format, toward and away from zero
+    if precision == "bf16":
+        bits = np.ascontiguousarray(n32[c32][:, :, :d16.nx]).view(np.uint32) >> 16
+        lo = (bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+        hi = ((bits.astype(np.uint32) + 1) << 16).view(np.float32).astype(np.float64)
+    else:
+        rn = f.astype(np.float16)
+        lo16 = np.where(np.abs(rn.astype(np.float64)) > np.abs(f),
+                        np.nextafter(rn, np.float16(0)), rn)
+        hi16 = np.nextafter(lo16, np.copysign(np.float16(np.inf), f).astype(np.float16))
+        lo, hi = lo16.astype(np.float64), hi16.astype(np.float64)
+    exact = lo == f
+    total = np.zeros_like(f)
+    K = 64
+    for _ in range(K):
+        d16.load_state(blob16)
+        d16.step(1)
+        n16, c16 = _buffers(d16, d16.save_state(), np.uint16)
+        g = n16[c16][:, :, :d16.nx]
+        got = ((g.astype(np.uint32) << 16).view(np.float32) if precision == "bf16"
+               else g.view(np.float16)).astype(np.float64)
+        ok = (got == lo) | ((got == hi) & ~exact)
+        assert ok[fluid].all(), int((~ok & fluid).sum())
+        total += got
+    spacing = np.where(exact, 1.0, np.abs(hi - lo))
+    frac = ((total / K - f) / spacing)[fluid & ~exact]   # mean offset in spacings
+    # each draw's offset has variance p(1 - p) <= 1/4; the mean of n K draws
+    # is within 6 sigma of zero
+    assert abs(frac.mean()) < 6 * 0.5 / np.sqrt(K * frac.size), frac.mean()
