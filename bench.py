@@ -208,10 +208,10 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def traffic_from_profiles():
+def traffic_from_profiles(name="k_step_cathode-4096x1024-fp32.json"):
     """DRAM bytes per launch of the step kernel from the committed ncu
-    summary of this workload, if one exists for the current kernel."""
-    path = os.path.join(ROOT, "profiles", "k_step_cathode-4096x1024-fp32.json")
+    summary of a workload, if one exists for the current kernel."""
+    path = os.path.join(ROOT, "profiles", name)
     if os.path.exists(path):
         try:
             j = json.load(open(path))
@@ -775,7 +775,11 @@ def run_validation(args):
                    **{k: case[k] for k in ("Ra", "Pr", "Da", "phi", "heated_bottom", "D")
                       if k in case}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                     "frac": achieved / peak,
+                     "traffic": (traffic_from_profiles("k_step_cavity-2048x2048-fp32.json")
+                                 if args.workload == "cavity" and args.precision == "fp32"
+                                 and case["nx"] == 2048 else None),
+                     "peak_source": peak_kind,
                      "bytes_per_cell": bpc,
                      "kernel": "k_step, extended instantiation (" +
                                ("128 x 2" if variant <= 2 else "64 x 2") + " threads per block)"},
