@@ -637,6 +637,17 @@ lbm_status lbm_step_observe(lbm_domain *d, int64_t nsteps, double *i_avg, double
         cudaEventCreateWithFlags(&d->obs_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&d->obs_done[0], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&d->obs_done[1], cudaEventDisableTiming) != cudaSuccess) {
+      // release what was made, so that a later call starts over
+      if (d->dobs) cudaFree(d->dobs);
+      if (d->hobs) cudaFreeHost(d->hobs);
+      if (d->obs_side) cudaStreamDestroy(d->obs_side);
+      for (cudaEvent_t *e : {&d->obs_fork, &d->obs_join, &d->obs_done[0], &d->obs_done[1]})
+        if (*e) {
+          cudaEventDestroy(*e);
+          *e = nullptr;
+        }
+      d->dobs = d->hobs = nullptr;
+      d->obs_side = nullptr;
       cudaGetLastError();
       return fail(LBM_ENOMEM, "observation slots");
     }
@@ -1404,17 +1415,27 @@ void drop_batch_graph(lbm_batch *b) {
 lbm_status batch_lanes(lbm_batch *b, int64_t n, bool fixed_parity) {
   const int nc = (int)b->doms.size();
   if ((int)b->lanes.size() != nc) {
+    // all or nothing: a partial set is released, so a later call starts over
+    auto release = [&] {
+      for (auto st : b->lanes)
+        if (st) cudaStreamDestroy(st);
+      for (auto e : b->lane_done)
+        if (e) cudaEventDestroy(e);
+      if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+      b->lanes.clear();
+      b->lane_done.clear();
+      b->ev_fork = nullptr;
+      cudaGetLastError();
+    };
     b->lanes.assign(nc, nullptr);
     b->lane_done.assign(nc, nullptr);
-    for (int c = 0; c < nc; ++c)
-      if (cudaStreamCreateWithFlags(&b->lanes[c], cudaStreamNonBlocking) != cudaSuccess ||
-          cudaEventCreateWithFlags(&b->lane_done[c], cudaEventDisableTiming) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(LBM_ECUDA, "lane streams for the concurrent schedule");
-      }
-    if (cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(LBM_ECUDA, "cudaEventCreate failed");
+    bool ok = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int c = 0; c < nc && ok; ++c)
+      ok = cudaStreamCreateWithFlags(&b->lanes[c], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&b->lane_done[c], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      release();
+      return fail(LBM_ECUDA, "lane streams for the concurrent schedule");
     }
   }
   CK(cudaEventRecord(b->ev_fork, b->stream));
