@@ -55,6 +55,11 @@
  *     so alpha C, not C, is continuous across the GDL/channel interface; an
  *     optional Fickian interface mode keeps one b per scalar and sets each
  *     cell's diffusivity through the flux-moment rate instead.
+ *   - The validation cases of Sec. 3: closed x ends (no-slip walls), scalars
+ *     held at fixed values on walls by anti-bounce-back at the halfway wall,
+ *     and the Boussinesq buoyancy gamma (T - T_buoy) added like the uniform
+ *     body force (half a step in Eq. 8's velocity, times phi in the force),
+ *     with T the cell's post-stream sum.
  *
  * Storage: f[q][y][x] (9 planes), g[s][q][y][x] (3 scalars x 5 planes),
  * s = 0 temperature, 1 O2 mole fraction, 2 H2O mole fraction.  Full values,
