@@ -4,12 +4,16 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <optional>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -41,6 +45,48 @@ lbm_status fail(lbm_status s, const char *fmt, ...) {
       return fail(LBM_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
                   __LINE__);                                                          \
   } while (0)
+
+// Host-side NVTX ranges around the library's calls and phases, for
+// timelines (header-only NVTX: no cost without an attached tool).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
+// Host-side fault injection for tests of the ENOMEM paths: with
+// PEMLBM_FAIL_ALLOC=n in the environment, the n-th allocation the library
+// makes after the variable last changed fails as if memory were exhausted.
+// Nothing reaches the device.
+bool inject_alloc_failure() {
+  static std::mutex mu;
+  static std::string last;
+  static long count = 0;
+  const char *e = std::getenv("PEMLBM_FAIL_ALLOC");
+  const std::string cur = e ? e : "";
+  std::lock_guard<std::mutex> lock(mu);
+  if (cur != last) {
+    last = cur;
+    count = 0;
+  }
+  if (cur.empty()) return false;
+  return ++count == std::atol(cur.c_str());
+}
+template <typename T> cudaError_t dmalloc(T **p, size_t bytes) {
+  if (inject_alloc_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc((void **)p, bytes);
+}
+template <typename T> cudaError_t hmalloc(T **p, size_t bytes) {
+  if (inject_alloc_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocHost((void **)p, bytes);
+}
 
 constexpr int kGraphSteps = 64;   // even: a replay returns to the same buffer
 constexpr int kMaxPalette = 65535;
@@ -283,7 +329,10 @@ lbm_status ensure_obs_graph(lbm_domain *d, int half) {
 }
 
 lbm_status ensure_scratch(lbm_domain *d) {
-  if (!d->scratch) CK(cudaMalloc(&d->scratch, sizeof(double) * 24 * (size_t)d->nx * d->ny));
+  if (!d->scratch && dmalloc(&d->scratch, sizeof(double) * 24 * (size_t)d->nx * d->ny) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(LBM_ENOMEM, "read-out scratch of %.1f MB", 192.0 * d->nx * d->ny / 1e6);
+  }
   return LBM_OK;
 }
 
@@ -387,17 +436,17 @@ lbm_status lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
   const size_t cells = (size_t)d->plane;
   const size_t coef = fp64(d) ? sizeof(MatCoef<double>) : sizeof(MatCoef<float>);
   const size_t rsize = fp64(d) ? 8 : 4;
-  if (cudaMalloc(&d->pop[0], pop_bytes) != cudaSuccess || cudaMalloc(&d->pop[1], pop_bytes) != cudaSuccess ||
-      cudaMalloc(&d->mask, 2 * cells) != cudaSuccess || cudaMalloc(&d->mid, cells * 2) != cudaSuccess ||
-      cudaMalloc(&d->pal, coef * kMaxPalette) != cudaSuccess ||
-      cudaMalloc(&d->raw, sizeof(MatRaw) * kMaxPalette) != cudaSuccess ||
-      cudaMalloc(&d->snap, rsize * 5 * (size_t)D.nx * D.ny) != cudaSuccess ||
-      cudaMalloc(&d->partial, sizeof(double) * 10 * residual_blocks(D.nx, D.ny)) != cudaSuccess ||
-      cudaMalloc(&d->colsum, sizeof(double) * 2 * D.nx) != cudaSuccess ||
-      cudaMalloc(&d->dsmall, sizeof(double) * 16) != cudaSuccess || cudaMalloc(&d->dbad, sizeof(int)) != cudaSuccess ||
-      cudaMalloc(&d->dseed, 256) != cudaSuccess ||
-      cudaMalloc(&d->dprofile, sizeof(float) * D.nx) != cudaSuccess ||
-      cudaMallocHost(&d->hsmall, sizeof(double) * 16) != cudaSuccess) {
+  if (dmalloc(&d->pop[0], pop_bytes) != cudaSuccess || dmalloc(&d->pop[1], pop_bytes) != cudaSuccess ||
+      dmalloc(&d->mask, 2 * cells) != cudaSuccess || dmalloc(&d->mid, cells * 2) != cudaSuccess ||
+      dmalloc(&d->pal, coef * kMaxPalette) != cudaSuccess ||
+      dmalloc(&d->raw, sizeof(MatRaw) * kMaxPalette) != cudaSuccess ||
+      dmalloc(&d->snap, rsize * 5 * (size_t)D.nx * D.ny) != cudaSuccess ||
+      dmalloc(&d->partial, sizeof(double) * 10 * residual_blocks(D.nx, D.ny)) != cudaSuccess ||
+      dmalloc(&d->colsum, sizeof(double) * 2 * D.nx) != cudaSuccess ||
+      dmalloc(&d->dsmall, sizeof(double) * 16) != cudaSuccess || dmalloc(&d->dbad, sizeof(int)) != cudaSuccess ||
+      dmalloc(&d->dseed, 256) != cudaSuccess ||
+      dmalloc(&d->dprofile, sizeof(float) * D.nx) != cudaSuccess ||
+      hmalloc(&d->hsmall, sizeof(double) * 16) != cudaSuccess) {
     cudaGetLastError();
     return cleanup(fail(LBM_ENOMEM, "device allocation of %.1f MB failed", 2.0 * pop_bytes / 1e6));
   }
@@ -405,7 +454,7 @@ lbm_status lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
     return cleanup(fail(LBM_ECUDA, "cudaEventCreate failed"));
   uint8_t *dsolid = nullptr;
   if (D.solid) {
-    if (cudaMalloc(&dsolid, (size_t)D.nx * D.ny) != cudaSuccess) return cleanup(fail(LBM_ENOMEM, "solid mask"));
+    if (dmalloc(&dsolid, (size_t)D.nx * D.ny) != cudaSuccess) return cleanup(fail(LBM_ENOMEM, "solid mask"));
     cudaMemcpyAsync(dsolid, D.solid, (size_t)D.nx * D.ny, cudaMemcpyHostToDevice, d->stream);
   }
   cudaMemsetAsync(d->mid, 0, cells * 2, d->stream);
@@ -476,6 +525,7 @@ lbm_status lbm_set_params(lbm_domain *d, const lbm_params *p) {
 
 lbm_status lbm_set_fields(lbm_domain *d, const double *phi, const double *K, const double *alpha_T,
                           const double *D_O2, const double *D_H2O, const double *rho_cp_ratio) {
+  NvtxRange nvtx_("pemlbm.set_fields");
   if (!d || !phi || !K || !alpha_T || !D_O2 || !D_H2O) return fail(LBM_EINVAL, "null argument");
   if (!d->have_params) return fail(LBM_ESTATE, "call lbm_set_params before lbm_set_fields");
   const int nx = d->nx, ny = d->ny;
@@ -541,6 +591,7 @@ lbm_status lbm_set_fields(lbm_domain *d, const double *phi, const double *K, con
 }
 
 lbm_status lbm_reset(lbm_domain *d) {
+  NvtxRange nvtx_("pemlbm.reset");
   if (!d) return fail(LBM_EINVAL, "null domain");
   if (!d->have_params || !d->have_fields) return fail(LBM_ESTATE, "call lbm_set_params and lbm_set_fields first");
   d->Cref[0] = d->prm.T_in;
@@ -569,6 +620,7 @@ lbm_status lbm_reset(lbm_domain *d) {
 }
 
 lbm_status lbm_step(lbm_domain *d, int64_t nsteps) {
+  NvtxRange nvtx_("pemlbm.step");
   lbm_status s = check_ready(d);
   if (s != LBM_OK) return s;
   if (nsteps < 0) return fail(LBM_EINVAL, "nsteps < 0");
@@ -598,6 +650,7 @@ lbm_status lbm_time_steps(lbm_domain *d, int64_t nsteps, double *elapsed_ms) {
 }
 
 lbm_status lbm_current_density(lbm_domain *d, double *i_avg, double *heat, float *profile) {
+  NvtxRange nvtx_("pemlbm.current_density");
   lbm_status s = check_ready(d);
   if (s != LBM_OK) return s;
   if (d->steps < 1) return fail(LBM_ESTATE, "no step taken yet");
@@ -620,6 +673,7 @@ lbm_status lbm_current_density(lbm_domain *d, double *i_avg, double *heat, float
 }
 
 lbm_status lbm_step_observe(lbm_domain *d, int64_t nsteps, double *i_avg, double *heat) {
+  NvtxRange nvtx_("pemlbm.step_observe");
   lbm_status s = check_ready(d);
   if (s != LBM_OK) return s;
   if (nsteps < 0) return fail(LBM_EINVAL, "nsteps < 0");
@@ -630,7 +684,7 @@ lbm_status lbm_step_observe(lbm_domain *d, int64_t nsteps, double *i_avg, double
     // instead of after them
     int lo_prio = 0, hi_prio = 0;
     const size_t bytes = 2 * kGraphSteps * 2 * sizeof(double);
-    if (cudaMalloc(&d->dobs, bytes) != cudaSuccess || cudaMallocHost(&d->hobs, bytes) != cudaSuccess ||
+    if (dmalloc(&d->dobs, bytes) != cudaSuccess || hmalloc(&d->hobs, bytes) != cudaSuccess ||
         cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio) != cudaSuccess ||
         cudaStreamCreateWithPriority(&d->obs_side, cudaStreamNonBlocking, hi_prio) != cudaSuccess ||
         cudaEventCreateWithFlags(&d->obs_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -689,6 +743,7 @@ lbm_status lbm_step_observe(lbm_domain *d, int64_t nsteps, double *i_avg, double
 }
 
 lbm_status lbm_balances(lbm_domain *d, double *out) {
+  NvtxRange nvtx_("pemlbm.balances");
   lbm_status s = check_ready(d);
   if (s != LBM_OK) return s;
   if (!out) return fail(LBM_EINVAL, "null argument");
@@ -708,6 +763,7 @@ lbm_status lbm_balances(lbm_domain *d, double *out) {
 }
 
 lbm_status lbm_residual(lbm_domain *d, double *res) {
+  NvtxRange nvtx_("pemlbm.residual");
   if (!d || !res) return fail(LBM_EINVAL, "null argument");
   if (!d->have_state) return fail(LBM_ESTATE, "call lbm_reset first");
   const KArgs a = make_args(d);
@@ -735,6 +791,7 @@ lbm_status lbm_residual(lbm_domain *d, double *res) {
 }
 
 lbm_status lbm_get_fields(lbm_domain *d, double *out, int32_t on_device) {
+  NvtxRange nvtx_("pemlbm.get_fields");
   lbm_status s = check_ready(d);
   if (s != LBM_OK) return s;
   if (!out) return fail(LBM_EINVAL, "null argument");
@@ -810,6 +867,7 @@ struct StateHeader {
 };
 
 lbm_status lbm_save_state(lbm_domain *d, void *buf, size_t *bytes) {
+  NvtxRange nvtx_("pemlbm.save_state");
   lbm_status s = check_ready(d);
   if (s != LBM_OK) return s;
   if (!bytes) return fail(LBM_EINVAL, "null argument");
@@ -834,6 +892,7 @@ lbm_status lbm_save_state(lbm_domain *d, void *buf, size_t *bytes) {
 }
 
 lbm_status lbm_load_state(lbm_domain *d, const void *buf, size_t bytes) {
+  NvtxRange nvtx_("pemlbm.load_state");
   if (!d || !buf) return fail(LBM_EINVAL, "null argument");
   if (!d->have_params || !d->have_fields) return fail(LBM_ESTATE, "call lbm_set_params and lbm_set_fields first");
   const size_t pop_bytes = 24 * (size_t)d->plane * d->esize;
@@ -863,6 +922,7 @@ lbm_status lbm_set_variant(lbm_domain *d, int32_t variant) {
 }
 
 lbm_status lbm_tune(lbm_domain *d, int32_t trial_steps, int32_t *variant, double *best_ms) {
+  NvtxRange nvtx_("pemlbm.tune");
   lbm_status s = check_ready(d);
   if (s != LBM_OK) return s;
   if (d->steps != 0) return fail(LBM_ESTATE, "lbm_tune runs between lbm_reset and the first step");
@@ -922,7 +982,7 @@ struct DevBuf {
     if (p) cudaFree(p);
   }
   lbm_status alloc(size_t bytes) {
-    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    if (dmalloc(&p, bytes) != cudaSuccess) {
       cudaGetLastError();
       return fail(LBM_ENOMEM, "device allocation of %.1f MB for the adjoint failed", bytes / 1e6);
     }
@@ -1138,6 +1198,7 @@ extern "C" {
 
 lbm_status lbm_vjp(lbm_domain *d, const double *lam_next, double *lam_prev, double *dphi,
                    double *dK, double *dD_O2, double *du_in) {
+  NvtxRange nvtx_("pemlbm.vjp");
   lbm_status s = check_ready(d);
   if (s != LBM_OK) return s;
   if (!lam_next || !lam_prev) return fail(LBM_EINVAL, "null argument");
@@ -1156,6 +1217,7 @@ lbm_status lbm_vjp(lbm_domain *d, const double *lam_next, double *lam_prev, doub
 
 lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t segment,
                     double *J, double *dphi, double *dK, double *dD_O2, double *du_in) {
+  NvtxRange nvtx_("pemlbm.grad");
   lbm_status s = check_ready(d);
   if (s != LBM_OK) return s;
   if (objective != 0 && objective != 1) return fail(LBM_EINVAL, "objective must be 0 or 1");
@@ -1175,7 +1237,7 @@ lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t se
   // alternate on one buffer.
   bool overlap = false;
   if (nck > 1) {
-    if (cudaMalloc(&sgb[1].p, sbytes * (seg + 1)) == cudaSuccess) overlap = true;
+    if (dmalloc(&sgb[1].p, sbytes * (seg + 1)) == cudaSuccess) overlap = true;
     else cudaGetLastError();
   }
   struct Sync {   // recompute stream and its two buffer events
@@ -1239,6 +1301,8 @@ lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t se
   };
   Graph g_fwd, g_rec[2], g_rev[2][2];
   // forward s^0 .. s^{N-1}: segment k starts from SEGB(0, 0) = s^{k seg}
+  std::optional<NvtxRange> nvtx_fwd;
+  nvtx_fwd.emplace("pemlbm.grad.forward");
   CK(cudaMemcpyAsync(CKP(0), d->pop[d->cur], sbytes, cudaMemcpyDeviceToDevice, d->stream));
   CK(cudaMemcpyAsync(SEGB(0, 0), d->pop[d->cur], sbytes, cudaMemcpyDeviceToDevice, d->stream));
   for (int64_t k = 0; k + 1 < nck; ++k) {
@@ -1283,7 +1347,9 @@ lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t se
     CK(cudaGetLastError());
     return LBM_OK;
   };
+  nvtx_fwd.reset();
   // reverse, last segment first
+  NvtxRange nvtx_rev("pemlbm.grad.reverse");
   int cur = 0;
   long long seed_cell = -1;
   bool fresh = true;   // lam[cur] is the seed, held in full (see reverse_step)
@@ -1667,11 +1733,11 @@ lbm_status lbm_create_batch(lbm_domain *const *domains, int32_t ncases, lbm_batc
   b->stream = domains[0]->stream;
   b->ev.resize(ncases, nullptr);
   auto cleanup = [&](lbm_status s) { lbm_destroy_batch(b); return s; };
-  if (cudaMalloc(&b->dcases, sizeof(BatchCase) * ncases) != cudaSuccess ||
-      cudaMallocHost(&b->hcases, sizeof(BatchCase) * ncases) != cudaSuccess ||
-      cudaMalloc(&b->dtile, sizeof(int) * (ncases + 1)) != cudaSuccess ||
-      cudaMalloc(&b->dbar, 2 * sizeof(unsigned)) != cudaSuccess ||
-      cudaMalloc(&b->dstatus, sizeof(int)) != cudaSuccess) {
+  if (dmalloc(&b->dcases, sizeof(BatchCase) * ncases) != cudaSuccess ||
+      hmalloc(&b->hcases, sizeof(BatchCase) * ncases) != cudaSuccess ||
+      dmalloc(&b->dtile, sizeof(int) * (ncases + 1)) != cudaSuccess ||
+      dmalloc(&b->dbar, 2 * sizeof(unsigned)) != cudaSuccess ||
+      dmalloc(&b->dstatus, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     return cleanup(fail(LBM_ENOMEM, "batch tables"));
   }
@@ -1717,6 +1783,7 @@ lbm_status lbm_batch_set_schedule(lbm_batch *b, int32_t schedule, int32_t varian
 }
 
 lbm_status lbm_batch_step(lbm_batch *b, int64_t nsteps) {
+  NvtxRange nvtx_("pemlbm.batch_step");
   if (!b) return fail(LBM_EINVAL, "null batch");
   if (nsteps < 0 || nsteps > (1LL << 30)) return fail(LBM_EINVAL, "nsteps outside [0, 2^30]");
   for (lbm_domain *d : b->doms) {
@@ -1750,6 +1817,7 @@ lbm_status lbm_batch_time_steps(lbm_batch *b, int64_t nsteps, double *elapsed_ms
 
 lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, int32_t *schedule, int32_t *variant,
                           double *best_ms) {
+  NvtxRange nvtx_("pemlbm.batch_tune");
   if (!b || trial_steps < 1) return fail(LBM_EINVAL, "bad argument");
   for (lbm_domain *d : b->doms) {
     lbm_status s = check_ready(d);
