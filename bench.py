@@ -571,16 +571,20 @@ def run_cavity_study(args):
     grids of 32, 64 and 128 cells for Ra 1e3 and of 64, 128 and 256 cells
     for Ra 1e4 and 1e5: the mean Nusselt numbers of the hot and the cold wall
     (equal at a steady state), the largest velocities in units of alpha / L,
-    and the observed order of convergence of Nu between the grids."""
+    and the observed order of convergence of Nu between the grids; then the
+    porous cavity (porosity 0.6, Darcy number 1e-2) at Ra 1e4 and 1e5."""
     import torch
     from paper_2103_01444_gb300.build import build
     from paper_2103_01444_gb300.lbm import Domain, LbmError
     build()
     out = []
-    for Ra, grids in ((1e3, (32, 64, 128)), (1e4, (64, 128, 256)), (1e5, (64, 128, 256))):
-        row = {"Ra": Ra, "grids": []}
+    runs = [(1e3, None, (32, 64, 128)), (1e4, None, (64, 128, 256)), (1e5, None, (64, 128, 256)),
+            (1e4, 1e-2, (32, 64, 128)), (1e5, 1e-2, (64, 128, 256))]
+    for Ra, Da, grids in runs:
+        row = {"Ra": Ra, "Da": Da, "phi": 0.6 if Da else 1.0, "grids": []}
         for n in grids:
-            case = workloads.natural_convection_cavity(n, Ra=Ra)
+            case = (workloads.natural_convection_cavity(n, Ra=Ra) if Da is None else
+                    workloads.natural_convection_cavity(n, Ra=Ra, Da=Da, phi=0.6))
             d = Domain.from_case(case, precision="fp64")
             alpha = d.params["nu"] / case["Pr"]
             dT = case["T_hot"] - case["T_cold"]
