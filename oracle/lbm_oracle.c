@@ -18,6 +18,8 @@
  *                                                             (Eq. 1, 3-7)
  *             n = N g;  n* = n - Q (n - n_eq);  g* = N^-1 n*  (Eq. 10)
  *             + volumetric catalyst sink when the catalyst layer has rows.
+ *   outputs : current density and heat of the reaction links (Eq. 13, 15)
+ *             and the steady-state residual of the moments (orc_residual).
  *
  * Readings taken where the paper is silent or garbled (each listed in the
  * design notes):
@@ -853,6 +855,37 @@ void orc_state_moments(const orc_params *P, const uint8_t *mask, const double *f
     out[1 * n + c] = jy;
     for (int s = 0; s < 3; ++s) out[(2 + s) * n + c] = C[s];
   }
+}
+
+/* Steady-state residual (the paper reports steady states and states no
+ * convergence test; reading): the moments X of the post-collision state,
+ * X in {sum e_x f*, sum e_y f*, T - T_in, C_O2, C_H2O} (solid cells 0), are
+ * compared with the moments of the previous call, held in snapshot
+ * [5][ny][nx]; r = max over the five of ||X - X_prev||_2 / ||X||_2, with
+ * 0/0 read as 0 and x/0 (x > 0) as +inf.  The snapshot is then replaced by
+ * the current moments.  Sums in FP64, cell by cell in row-major order. */
+double orc_residual(const orc_params *P, const uint8_t *mask, const double *fs,
+                    const double *gs, double *snapshot) {
+  int nx = P->nx, ny = P->ny;
+  size_t n = (size_t)nx * ny;
+  double *X = malloc(sizeof(double) * 5 * n);
+  orc_state_moments(P, mask, fs, gs, X);
+  for (size_t c = 0; c < n; ++c)
+    if ((mask[c] & 3) != REG_SOLID) X[2 * n + c] -= P->T_in;
+  double r = 0.0;
+  for (int k = 0; k < 5; ++k) {
+    double num = 0.0, den = 0.0;
+    for (size_t c = 0; c < n; ++c) {
+      double d = X[k * n + c] - snapshot[k * n + c];
+      num += d * d;
+      den += X[k * n + c] * X[k * n + c];
+    }
+    double rk = den > 0 ? sqrt(num / den) : (num > 0 ? INFINITY : 0.0);
+    if (rk > r || isnan(rk)) r = rk;
+  }
+  memcpy(snapshot, X, sizeof(double) * 5 * n);
+  free(X);
+  return r;
 }
 
 /* ----------------------------------------- exposed pieces for the pins */

@@ -75,6 +75,8 @@ def lib():
             L.orc_step.argtypes = [_P(Params), _P(Material), _u8, _d, _d, _d, _d, _d, _d, _d]
             L.orc_fields.argtypes = [_P(Params), _P(Material), _u8, _d, _d, _d, _d, _d, _d]
             L.orc_state_moments.argtypes = [_P(Params), _u8, _d, _d, _d]
+            L.orc_residual.argtypes = [_P(Params), _u8, _d, _d, _d]
+            L.orc_residual.restype = C.c_double
             L.orc_matrices.argtypes = [_d, _d, _d, _d]
             L.orc_flow_meq.argtypes = [C.c_double] * 4 + [_d]
             L.orc_flow_G.argtypes = [C.c_double] * 5 + [_d]
@@ -146,6 +148,9 @@ class Oracle:
                         _ptr(self.f), _ptr(self.g))
         self.f_prev, self.g_prev = self.f.copy(), self.g.copy()
         self.steps = 0
+        # residual snapshot: the moments of the initial state
+        self.snapshot = np.zeros((5, ny, nx))
+        self.residual()
         self.diag = np.zeros(10)
         self.Jx = np.zeros(nx)
         self.qx = np.zeros(nx)
@@ -181,6 +186,14 @@ class Oracle:
         self.L.orc_state_moments(C.byref(self.P), _ptr(self.mask, C.c_uint8), _ptr(self.f),
                                  _ptr(self.g), _ptr(out))
         return out
+
+    def residual(self):
+        """Steady-state residual of the current post-collision state against
+        the moments of the previous call (or of the initial state): max over
+        (sum e_x f, sum e_y f, T - T_in, C_O2, C_H2O) of ||X - X_prev|| / ||X||.
+        Replaces the snapshot."""
+        return float(self.L.orc_residual(C.byref(self.P), _ptr(self.mask, C.c_uint8),
+                                         _ptr(self.f), _ptr(self.g), _ptr(self.snapshot)))
 
     # -- reported quantities (Sec. 5 performance outputs)
     def current_density(self):

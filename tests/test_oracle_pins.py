@@ -697,3 +697,174 @@ def test_kang_surface_reaction_series(Da):
     # held wall
     d = o.diag
     assert d[DIAG["J"]] == pytest.approx(d[DIAG["in_O2"]], rel=1e-5)
+
+
+# --------------------------------------------- physical units (Eq. 13-17)
+# The reaction terms are the only place where the oracle leaves lattice
+# units.  These pins evaluate Eq. 13-17 by hand from the printed constants
+# (tests/golden/paper_values.txt) and check the oracle's lattice rates, its
+# heat per unit O2 and its current and heat outputs against Fick's and
+# Fourier's laws in physical units, so that a lost factor 4 (electrons per
+# O2), a misplaced catalyst thickness or a wrong dx/dt scale fails.
+
+def hand_kinetics(V, T):
+    """Eq. 13, 14, 16, 17 evaluated from the printed constants: the
+    volumetric current magnitude per unit O2 mole fraction (A/cm^3)."""
+    gv = golden()
+    aj0 = gv["aj0_ref_A_cm3"] * math.exp(-gv["E_act_K"] * (1 / T - 1 / gv["T_ref_kin_K"]))
+    U0 = gv["U0_slope_V_K"] * T + gv["U0_intercept_V"]
+    eta = V - U0
+    return aj0 * math.exp(-gv["alpha_c"] * gv["F_C_mol"] * eta / (gv["R_J_molK"] * T)) / 0.21
+
+
+def physical_scales(dx_cm, D_lat=0.05):
+    """Lattice time step that maps the lattice O2 diffusivity onto the
+    printed D_O2, and the total gas concentration C_O2,ref / 0.21."""
+    gv = golden()
+    dt = D_lat * dx_cm ** 2 / gv["D_O2_cm2_s"]
+    c_tot = gv["C_O2_ref_mol_cm3"] / 0.21
+    return dt, c_tot
+
+
+def test_lattice_rate_constants_hand_evaluated(oracle_lib):
+    """At 0.6 V and 343 K: the film's lattice rate is the Tafel current of a
+    catalyst of thickness delta per unit mole fraction, divided by the charge
+    4 F c_tot per unit mole fraction and volume (Eq. 12: four electrons per
+    O2), times dt/dx; the volumetric rate is the same without delta/dx; the
+    heat per unit O2 consumed is 4 F c_tot (V - 0.2329)/(rho c_p)_f (Eq. 15
+    with Eq. 16, whose T dU0/dT terms cancel)."""
+    gv = golden()
+    F = gv["F_C_mol"]
+    dx = 0.05
+    dt, c_tot = physical_scales(dx)
+    rho_cp = 29.3 * c_tot
+    delta = 10e-4
+    p = base_params(4, 4, V_op=0.6, aj0_ref=gv["aj0_ref_A_cm3"], dx_cm=dx, dt_s=dt,
+                    c_tot=c_tot, rho_cp_f=rho_cp, delta_cl_cm=delta)
+    P = ctypes.byref(Oracle(p, uniform_material(4, 4)).P)
+    j1 = hand_kinetics(0.6, 343.0)
+    assert j1 * 0.21 == pytest.approx(404.79, rel=2e-4)      # A/cm^3 at C = C_ref
+    k_s = j1 * delta / (4 * F * c_tot) * dt / dx
+    k_v = j1 / (4 * F * c_tot) * dt
+    h = 4 * F * c_tot * (0.6 - gv["U0_intercept_V"]) / rho_cp
+    assert oracle_lib.orc_k_surface(P, 343.0) == pytest.approx(k_s, rel=1e-13)
+    assert oracle_lib.orc_k_volume(P, 343.0) == pytest.approx(k_v, rel=1e-13)
+    assert oracle_lib.orc_heat_per_O2(P, 343.0) == pytest.approx(h, rel=1e-13)
+    # the same numbers written out (dx = 0.05 cm, dt = 2.3948e-3 s)
+    assert k_s == pytest.approx(2.82086e-3, rel=1e-5)
+    assert k_v == pytest.approx(0.141043, rel=1e-5)
+    assert h == pytest.approx(4835.55, rel=1e-5)
+    # the heat per unit O2 does not depend on T (Eq. 15-16)
+    assert oracle_lib.orc_heat_per_O2(P, 360.0) == pytest.approx(h, rel=1e-13)
+
+
+def steady_column(reaction_mode, H=16, ny_cl=0, dx=0.05, sigma=50.0, alpha_T=0.1, steps=60000):
+    """A column at rest (periodic x), held at C_O2 = 0.21 and T = 343 K on the
+    halfway top wall, the catalyst at the bottom (film or rows), run to its
+    steady state.  Physical scales from the printed constants."""
+    gv = golden()
+    dt, c_tot = physical_scales(dx)
+    p = base_params(4, H, reaction_mode=reaction_mode, ny_cl=ny_cl, top_dirichlet=1,
+                    C_O2_top=0.21, T_top=343.0, V_op=0.6, aj0_ref=gv["aj0_ref_A_cm3"],
+                    dx_cm=dx, dt_s=dt, c_tot=c_tot, rho_cp_f=29.3 * c_tot)
+    m = uniform_material(4, H, alpha_T=alpha_T, D_O2=0.05, D_H2O=0.05)
+    m["sigma"] = np.full((H, 4), sigma)
+    o = Oracle(p, m)
+    o.step(steps)
+    assert o.residual() == 0.0 or o.step(1).residual() < 1e-13    # steady
+    return o, dict(dx=dx, dt=dt, c_tot=c_tot, H=H, sigma=sigma, alpha_T=alpha_T)
+
+
+def wall_value(col, y0, y1, y):
+    """Value at height y of the line through two cells' values (cell j at
+    height j + 1/2)."""
+    s = (col[y1] - col[y0]) / (y1 - y0)
+    return col[y0] + s * (y - (y0 + 0.5)), s
+
+
+def test_thin_film_current_obeys_fick_tafel_fourier_and_eq15():
+    """Steady column with the catalyst film on the bottom wall:
+    - Fick: i = 4 F D_O2 c_tot (x_top - x_w)/L, with the printed D_O2;
+    - Eq. 13 at the wall: i = aj0(T) delta (x_w/x_ref) exp(-alpha_c F eta/(R T));
+    - Eq. 15-16: heat = i (V - 0.2329);
+    - Fourier: heat = k_eff (T_w - T_top)/L, k_eff = alpha sigma (rho c_p)_f.
+    All in physical units (A/cm^2, W/cm^2)."""
+    gv = golden()
+    o, s = steady_column(0)
+    F, H, dx = gv["F_C_mol"], s["H"], s["dx"]
+    L = H * dx
+    fl = o.fields()
+    C, T = fl["C_O2"][:, 0], fl["T"][:, 0]
+    x_w, sl = wall_value(C, 0, 1, 0.0)
+    x_top, _ = wall_value(C, H - 2, H - 1, H)
+    assert x_top == pytest.approx(0.21, rel=1e-11)
+    T_w, _ = wall_value(T, 0, 1, 0.0)
+    i_avg, heat, ix = o.current_density()
+    assert 0.1 < x_w / 0.21 < 0.9        # neither transport- nor kinetics-free
+    assert i_avg == pytest.approx(4 * F * gv["D_O2_cm2_s"] * s["c_tot"] * (x_top - x_w) / L,
+                                  rel=1e-9)
+    T_c = T[0]                           # the rate takes the catalyst cell's T
+    delta = 10e-4
+    assert i_avg == pytest.approx(hand_kinetics(0.6, T_c) * delta * x_w, rel=1e-9)
+    assert heat == pytest.approx(i_avg * (0.6 - gv["U0_intercept_V"]), rel=1e-12)
+    alpha_phys = s["alpha_T"] * dx ** 2 / s["dt"]
+    k_eff = alpha_phys * s["sigma"] * 29.3 * s["c_tot"]
+    T_top, _ = wall_value(T, H - 2, H - 1, H)
+    assert T_top == pytest.approx(343.0, rel=1e-12)
+    assert heat == pytest.approx(k_eff * (T_w - T_top) / L, rel=1e-9)
+    assert T_w - T_top > 1.0
+
+
+def test_volumetric_current_obeys_fick_and_tafel():
+    """Steady column whose bottom rows are catalyst: the current equals the
+    O2 flux through the gas above them by Fick's law, and the sum over the
+    catalyst rows of Eq. 13 per unit volume times the row height, at the
+    backward-Euler concentration C/(1 + k_v) of each cell (k_v the lattice
+    rate of the hand evaluation)."""
+    gv = golden()
+    ny_cl = 4
+    o, s = steady_column(1, ny_cl=ny_cl)
+    F, H, dx, dt, c_tot = gv["F_C_mol"], s["H"], s["dx"], s["dt"], s["c_tot"]
+    fl = o.fields()
+    C = fl["C_O2"][:, 0]
+    _, sl = wall_value(C, ny_cl + 2, ny_cl + 5, 0.0)
+    i_avg, heat, _ = o.current_density()
+    assert i_avg == pytest.approx(4 * F * gv["D_O2_cm2_s"] * c_tot * sl / dx, rel=1e-9)
+    mom = o.state_moments()                  # post-collision sums of the step
+    i_tafel = 0.0
+    for y in range(ny_cl):
+        T_c, C_c = mom[2][y, 0], mom[3][y, 0]
+        j1 = hand_kinetics(0.6, T_c)
+        k_v = j1 / (4 * F * c_tot) * dt
+        i_tafel += j1 * C_c / (1 + k_v) * dx
+    assert i_avg == pytest.approx(i_tafel, rel=1e-9)
+    assert heat == pytest.approx(i_avg * (0.6 - gv["U0_intercept_V"]), rel=1e-12)
+
+
+# ---------------------------------------------------- residual (reading)
+
+def test_residual_special_cases():
+    """The steady-state residual max_X ||X - X_prev|| / ||X|| over
+    X = (j_x, j_y, T - T_in, C_O2, C_H2O): zero for an unchanged state; a
+    field scaled by 1 + a changes by a/(1 + a) of its new norm; a field that
+    was zero and is not has residual 1; the largest of the five is taken;
+    the snapshot is replaced on every call."""
+    case = workloads.small_cathode(nx=24, ny=10, reaction_mode=0, V_op=0.4)
+    params, material, solid = lattice_problem(case)
+    o = Oracle(params, material, solid)
+    assert o.residual() == 0.0                      # same state as at reset
+    # at reset T = T_in, j = 0 and C_H2O = 0: heating by 0.5 K gives T - T_in
+    # residual 1 (0.5 against 0); scaling O2 by 1.5 gives 1/3
+    o.g[1] *= 1.5
+    assert o.residual() == pytest.approx(1 / 3, rel=1e-14)
+    o.g[0] += 0.5 * o.g[0] / o.g[0].sum(axis=0)      # T -> T + 0.5 in every cell
+    assert o.residual() == pytest.approx(1.0, rel=1e-14)
+    assert o.residual() == 0.0
+    o.step(40)
+    o.residual()
+    o.g[1] *= 1.25                                  # O2: 0.2
+    o.g[2] *= 1.5                                   # H2O: 1/3
+    assert o.residual() == pytest.approx(1 / 3, rel=1e-13)
+    # momentum: reversing the flow changes j by 2 j
+    o.f[[1, 2, 3, 4, 5, 6, 7, 8]] = o.f[[3, 4, 1, 2, 7, 8, 5, 6]]
+    assert o.residual() == pytest.approx(2.0, rel=1e-13)
