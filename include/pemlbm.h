@@ -352,25 +352,29 @@ lbm_status lbm_batch_step(lbm_batch *b, int64_t nsteps);
 lbm_status lbm_batch_time_steps(lbm_batch *b, int64_t nsteps, double *elapsed_ms);
 
 /* The steady-state residual of lbm_residual, computed without allocating.
- * This entry point has no counterpart in the paper.  It serves callers that
- * cannot call cudaMalloc when they need the residual: code under CUDA stream
- * capture, real-time loops that forbid allocation after start-up, hosts that
- * own all device memory through their own pool.  It calls no cudaMalloc,
- * cudaFree or allocating library routine.
+ * The paper has no counterpart of this entry point.  It is for callers that
+ * must not let the library allocate device memory once they are running:
+ * real-time loops, where a cudaMalloc can stall the device's streams for an
+ * unbounded time, and host programs that hand out all device memory from a
+ * pool of their own and account for every byte of it.  It calls no
+ * cudaMalloc, cudaFree or allocating library routine.
  *   snapshot  device memory owned by the caller, [5][ny][nx] values of the
  *             domain's arithmetic type (double for LBM_FP64, float otherwise):
  *             the moments of the previous call (zeros before the first one);
- *             read, then overwritten with the current moments
+ *             read, then overwritten with the current moments.  The library
+ *             cannot check this buffer: its type, size and device are the
+ *             caller's responsibility.
  *   res       host: ||X - X_prev|| / ||X|| maximised over the five moments
  * The reduction's block partial sums live in one file-scope device array of
  * 16384 blocks x 10 doubles (1.31 MB), which every GPU that loads the library
  * holds until the process exits; lattices needing more than 16384 blocks of
  * 128 x 2 cells (about 4.19 M cells) are rejected with EINVAL.  The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.
- * All calls share the array and it keeps the last call's contents (the flag
- * word is cleared on each call): calls that overlap on the GPU, on any
- * domain, race.  Synchronises the domain's stream.  EDIVERGED on non-finite
+ * with that device current and keeps it; make that first call before any
+ * stream capture.  All calls share the array, and it keeps the last call's
+ * contents (each call clears the flag word that must start at zero): calls
+ * that overlap on the GPU, on any domain, race.  The call is synchronous: it
+ * waits for the domain's stream before it returns.  EDIVERGED on non-finite
  * values. */
 lbm_status lbm_residual_noalloc(lbm_domain *d, void *snapshot, double *res);
 

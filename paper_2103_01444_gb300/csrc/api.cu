@@ -1879,13 +1879,12 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, int32_t *schedule, 
 // ---------------------------------------------------------------------------
 // Residual without allocation.
 //
-// Some callers cannot call cudaMalloc when they need the steady-state
-// residual: code running under CUDA stream capture (an allocation there
-// breaks the capture), real-time loops that forbid allocation after start-up,
-// and hosts whose device memory comes only from their own pool.  For them the
-// block partial sums of the residual reduction live in this file-scope device
-// array instead of in memory the library allocates.  Every GPU that loads the
-// library holds it (1.31 MB) until the process exits.
+// Some callers must not let the library allocate device memory once they are
+// running: real-time loops, where a cudaMalloc can stall the device's streams
+// for an unbounded time, and hosts whose device memory comes only from their
+// own pool.  For them the block partial sums of the residual reduction live in
+// this file-scope device array instead of in memory the library allocates.
+// Every GPU that loads the library holds it (1.31 MB) until the process exits.
 namespace {
 
 constexpr int kNoAllocBlocks = 16384;    // residual blocks of 128 x 2 cells: 4.19 M cells
@@ -1919,6 +1918,7 @@ lbm_status noalloc_scratch(double **out) {
 }  // namespace
 
 extern "C" lbm_status lbm_residual_noalloc(lbm_domain *d, void *snapshot, double *res) {
+  NvtxRange nvtx_("pemlbm.residual_noalloc");
   if (!d || !snapshot || !res) return fail(LBM_EINVAL, "null argument");
   if (!d->have_state) return fail(LBM_ESTATE, "call lbm_reset first");
   const int nblocks = residual_blocks(d->nx, d->ny);

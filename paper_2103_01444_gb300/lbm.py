@@ -120,6 +120,34 @@ def _dp(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
+def check_device_buffer(t, dtype: str, shape: tuple, device, name: str = "buffer"):
+    """Refuses (LbmError EINVAL) a tensor that the library would read or
+    write through a bare device pointer unless it is a contiguous CUDA tensor
+    of the given dtype name and shape on the given device index."""
+    bad = None
+    if not getattr(t, "is_cuda", False):
+        bad = "is not a CUDA tensor"
+    elif device is not None and t.device.index != device:
+        bad = f"is on cuda:{t.device.index}, the domain on cuda:{device}"
+    elif str(t.dtype).replace("torch.", "") != dtype:
+        bad = f"has dtype {t.dtype}, needs {dtype}"
+    elif tuple(t.shape) != tuple(shape):
+        bad = f"has shape {tuple(t.shape)}, needs {tuple(shape)}"
+    elif not t.is_contiguous():
+        bad = "is not contiguous"
+    if bad:
+        raise LbmError(1, f"{name} {bad}")
+
+
+def _current_device():
+    """The current CUDA device index (the device a new domain lives on)."""
+    try:
+        import torch
+        return torch.cuda.current_device() if torch.cuda.is_available() else None
+    except ImportError:
+        return None
+
+
 class Domain:
     """One cathode lattice on the GPU (wraps an lbm_domain handle)."""
 
@@ -140,6 +168,7 @@ class Domain:
         _check(self.L.lbm_create_domain(C.byref(desc), C.byref(h)))
         self.h = h
         self.precision = desc.precision
+        self.device = _current_device()
 
     @classmethod
     def from_case(cls, case: dict, precision="fp32", forchheimer: int = 1, stream=None,
@@ -240,7 +269,11 @@ class Domain:
     def residual_noalloc(self, snapshot) -> float:
         """Residual of lbm_residual against a caller-held snapshot (a CUDA
         tensor of shape (5, ny, nx), float64 for FP64 domains, float32
-        otherwise), computed with the library's static scratch."""
+        otherwise), computed with the library's static scratch.  The C call
+        cannot check the buffer it is given, so its type, shape, layout and
+        device are checked here before anything runs (EINVAL)."""
+        check_device_buffer(snapshot, "float64" if self.precision == FP64 else "float32",
+                            (5, self.ny, self.nx), self.device, "snapshot")
         r = C.c_double()
         _check(self.L.lbm_residual_noalloc(self.h, C.c_void_p(snapshot.data_ptr()), C.byref(r)))
         return r.value

@@ -114,3 +114,50 @@ def test_workloads_are_seeded_and_shaped():
     g = workloads.cathode_grains(256, 64)
     assert g["solid"][:, :4].sum() == 0 and g["solid"][:, -4:].sum() == 0
     assert 0.2 < g["solid"][:g["ny_gdl"]].mean() < 0.4
+
+
+class _FakeTensor:
+    """Stands in for a torch tensor: the attributes the binding checks."""
+
+    def __init__(self, is_cuda=True, index=0, dtype="torch.float32", shape=(5, 8, 16),
+                 contiguous=True):
+        self.is_cuda = is_cuda
+        self.device = type("dev", (), {"index": index})()
+        self.dtype = dtype
+        self.shape = shape
+        self._contig = contiguous
+
+    def is_contiguous(self):
+        return self._contig
+
+    def data_ptr(self):
+        raise AssertionError("the pointer must not be taken from a refused buffer")
+
+
+class _NoCalls:
+    def __getattr__(self, name):
+        raise AssertionError(f"{name} must not be called for a refused buffer")
+
+
+@pytest.mark.parametrize("bad,what", [
+    (dict(is_cuda=False), "not a CUDA tensor"),
+    (dict(index=1), "cuda:1"),
+    (dict(dtype="torch.float64"), "dtype"),
+    (dict(shape=(5, 8, 15)), "shape"),
+    (dict(shape=(4, 8, 16)), "shape"),
+    (dict(contiguous=False), "contiguous"),
+])
+def test_residual_noalloc_refuses_bad_snapshots_before_any_call(bad, what):
+    """The C entry point takes a bare device pointer and cannot check it; the
+    binding refuses a snapshot of the wrong kind, device, dtype, shape or
+    layout with EINVAL before it reaches the library."""
+    d = lbm.Domain.__new__(lbm.Domain)
+    d.L, d.h = _NoCalls(), None
+    d.nx, d.ny, d.precision, d.device = 16, 8, lbm.FP32, 0
+    with pytest.raises(lbm.LbmError, match=what) as e:
+        d.residual_noalloc(_FakeTensor(**bad))
+    assert e.value.status == 1
+    d.precision = lbm.FP64          # an FP64 domain needs float64
+    with pytest.raises(lbm.LbmError, match="dtype"):
+        d.residual_noalloc(_FakeTensor())
+    d.h = None
