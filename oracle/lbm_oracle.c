@@ -53,6 +53,10 @@
  *     + k_a)/(1 + kappa), the sink S = (k_va - k_v C)/(1 + k_v).
  *   - k(T), C and T in the reaction terms use the cell's previous
  *     post-collision sums (C^n = sum g*(x)).
+ *   - Optionally (scalar_advection 1) the flux moments of the D2Q5
+ *     equilibria carry u (C - C_in) instead of u C: the same continuum
+ *     equation where div u = 0, without the source C_in div u that the weakly
+ *     compressible flow's small divergence would add.
  *   - Eq. 10 with a per-cell b and fixed Q (the default) diffuses alpha C,
  *     so alpha C, not C, is continuous across the GDL/channel interface; an
  *     optional Fickian interface mode keeps one b per scalar and sets each
@@ -190,6 +194,9 @@ typedef struct {
                                (Sec. 3): force per unit mass (buoy_gx, buoy_gy)(T - T_buoy) */
   double T_buoy;
   double C_wall[9];         /* wall values of wall_dirichlet, [wall][scalar] */
+  int32_t scalar_advection; /* flux moments of the D2Q5 equilibria (Eq. 10):
+                               0 u C as printed; 1 u (C - C_in), relative to the
+                               scalar's inlet value */
 } orc_params;
 
 /* Per-cell material, lattice units. K = +inf marks clear fluid.  sigma is
@@ -743,6 +750,7 @@ void orc_step(const orc_params *P, const orc_material *mat, const uint8_t *mask,
   if (diag) memcpy(diag, dloc, sizeof dloc);
 
   double tau = 3.0 * P->nu + 0.5, S[9], Q[5], amax[3];
+  const double Cin[3] = {P->T_in, P->C_O2_in, P->C_H2O_in};
   flow_S(tau, S);
   scalar_Q(Q);
   max_diffusivities(P, mat, mask, amax);
@@ -784,7 +792,11 @@ void orc_step(const orc_params *P, const orc_material *mat, const uint8_t *mask,
         scalar_coef sc = scalar_coefficients(P, alpha[s], amax[s]);
         double b = sc.b, Qs[5] = {Q[0], sc.q1, sc.q1, Q[3], Q[4]};
         double C = mc.C[s];
-        double nv[5], neq[5] = {C, mc.usx * C, mc.usy * C, b * C, 0.0}, ns[5];
+        /* the advected value: C itself (Eq. 10 as printed) or its excess over
+         * the inlet value; the two give the same continuum equation where
+         * div u = 0, which the flow of Sec. 2.1 is built to satisfy */
+        double Ca = P->scalar_advection ? C - Cin[s] : C;
+        double nv[5], neq[5] = {C, mc.usx * Ca, mc.usy * Ca, b * C, 0.0}, ns[5];
         for (int k = 0; k < 5; ++k) {
           nv[k] = 0;
           for (int i = 0; i < 5; ++i) nv[k] += N5[k][i] * g[(s * 5 + i) * n + c];

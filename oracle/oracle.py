@@ -52,6 +52,7 @@ class Params(C.Structure):
         ("c_tot", C.c_double), ("rho_cp_f", C.c_double), ("dp_in", C.c_double),
         ("alpha_a", C.c_double), ("buoy_gx", C.c_double), ("buoy_gy", C.c_double),
         ("T_buoy", C.c_double), ("C_wall", C.c_double * 9),
+        ("scalar_advection", C.c_int32),
     ]
 
 

@@ -104,6 +104,9 @@ def lattice_problem(case: dict, forchheimer: int = 1, interface_mode: int = 0):
         # kinetics: Tafel (Eq. 13) unless the case gives an anodic transfer
         # coefficient for the Butler-Volmer branch
         alpha_a=float(case.get("alpha_a", 0.0)),
+        # advective flux of the scalars: u C as printed in Eq. 10 (0), or
+        # relative to the inlet values, u (C - C_in) (1)
+        scalar_advection=int(case.get("scalar_advection", 0)),
     )
     return params, material, case.get("solid")
 
@@ -117,7 +120,7 @@ def base_params(nx, ny, **kw):
              F=FARADAY, R=R_GAS, dU0dT=DU0_DT, U0_0=U0_0, x_ref=X_REF, dx_cm=1e-3,
              dt_s=1e-6, delta_cl_cm=DELTA_CL_CM, c_tot=C_TOT, rho_cp_f=RHO_CP_F,
              inlet_mode=0, dp_in=0.0, alpha_a=0.0, closed_x=0, wall_dirichlet=0, buoy_gx=0.0,
-             buoy_gy=0.0, T_buoy=343.0, C_wall=[0.0] * 9)
+             buoy_gy=0.0, T_buoy=343.0, C_wall=[0.0] * 9, scalar_advection=0)
     p.update(kw)
     return p
 
@@ -155,7 +158,7 @@ def validation_problem(case: dict, forchheimer: int = 1, interface_mode: int = 0
                     forchheimer=forchheimer, interface_mode=interface_mode,
                     E_act=0.0, alpha_c=0.0, dU0dT=0.0, U0_0=0.0, V_op=0.0, T_ref_kin=343.0,
                     x_ref=1.0, F=0.25, c_tot=1.0, delta_cl_cm=1.0, dx_cm=1.0, dt_s=1.0,
-                    rho_cp_f=1.0)
+                    rho_cp_f=1.0, scalar_advection=int(case.get("scalar_advection", 0)))
     ones = np.ones((ny, nx))
     if case["kind"] == "cavity":
         L = float(nx)

@@ -370,27 +370,69 @@ def test_layered_diffusion_fickian_mode():
         np.testing.assert_allclose(C, ex, atol=1e-12)
 
 
-def advection_error(H, Pe):
+def advection_profile(H, Pe, scalar_advection=0):
     a = 0.05
     mat = uniform_material(4, H, D_O2=a)
     ui = np.zeros((2, H, 4))
     ui[1] = Pe * a / H
     mat["u_imposed"] = ui
-    o = Oracle(scalar_case(H, aj0_ref=1e30), mat)
+    o = Oracle(scalar_case(H, aj0_ref=1e30, scalar_advection=scalar_advection), mat)
     o.step(int(6 * H * H / a))
-    C = o.fields()["C_O2"][:, 0]
+    return o.fields()["C_O2"][:, 0]
+
+
+def advection_error(H, Pe, scalar_advection=0):
+    C = advection_profile(H, Pe, scalar_advection)
     s = (np.arange(H) + 0.5) / H
     ex = (np.exp(Pe * s) - 1) / (np.exp(Pe) - 1)
     return np.abs(C - ex).max()
 
 
+@pytest.mark.parametrize("scalar_advection", [0, 1])
 @pytest.mark.parametrize("Pe", [4.0, -4.0])
-def test_advection_diffusion_second_order(Pe):
+def test_advection_diffusion_second_order(Pe, scalar_advection):
     """Uniform imposed u_y, C = 0 and 1 on the walls:
-    C = (exp(Pe s) - 1)/(exp(Pe) - 1), Pe = u H/alpha."""
-    e16, e32 = advection_error(16, Pe), advection_error(32, Pe)
+    C = (exp(Pe s) - 1)/(exp(Pe) - 1), Pe = u H/alpha; with the flux taken
+    relative to the inlet value (0.21 here) too."""
+    e16 = advection_error(16, Pe, scalar_advection)
+    e32 = advection_error(32, Pe, scalar_advection)
     assert e32 < 2.5e-3
     assert 3.3 < e16 / e32 < 4.5
+
+
+def test_relative_advection_equals_eq10_for_a_solenoidal_flow():
+    """Where div u = 0 exactly (a uniform imposed velocity), advecting C or
+    C - C_in gives the same discrete solution: the constant flux u C_in
+    streams through unchanged."""
+    for Pe in (4.0, -2.0):
+        np.testing.assert_allclose(advection_profile(16, Pe, 1), advection_profile(16, Pe, 0),
+                                   rtol=0, atol=1e-13)
+
+
+def test_relative_advection_keeps_uniform_inlet_values():
+    """A gas entering at uniform T_in and mole fractions, with no reaction,
+    is a steady solution of the continuum scalar equations for any flow.
+    Advected relative to the inlet values, the scalars stay exactly uniform
+    through the channel and the porous layer; with the flux u C of Eq. 10 as
+    printed, the small divergence of the lattice flow acts as a source
+    C_in div u and moves them away from the inlet values.  (Fickian
+    interfaces: with Eq. 10's per-cell b, alpha C diffuses, so a uniform C
+    over a varying diffusivity is not steady.)"""
+    case = workloads.small_cathode(nx=48, ny=16, reaction_mode=0)
+    dev = {}
+    for sa in (0, 1):
+        params, material, solid = lattice_problem(dict(case, scalar_advection=sa),
+                                                  interface_mode=1)
+        params["aj0_ref"] = 0.0
+        o = Oracle(params, material, solid).step(1500)
+        fl = o.fields()
+        live = (o.mask & 3) != 3
+        dev[sa] = max(np.abs(fl["T"] - params["T_in"])[live].max() / params["T_in"],
+                      np.abs(fl["C_O2"] - params["C_O2_in"])[live].max() / params["C_O2_in"],
+                      np.abs(fl["C_H2O"])[live].max())
+        assert np.abs(fl["ux"]).max() > 1e-3               # the gas does flow
+    assert dev[1] < 1e-13
+    assert dev[0] > 1e-6
 
 
 def cosh_error(H, oracle_lib):
@@ -483,15 +525,18 @@ def test_butler_volmer_off_is_tafel():
 
 # --------------------------------------------------------------- balances
 
+@pytest.mark.parametrize("scalar_advection", [0, 1])
 @pytest.mark.parametrize("alpha_a", [0.0, 0.5])
 @pytest.mark.parametrize("mode", [0, 1])
-def test_closed_box_stoichiometric_and_energy_invariants(mode, alpha_a, oracle_lib):
+def test_closed_box_stoichiometric_and_energy_invariants(mode, alpha_a, scalar_advection,
+                                                         oracle_lib):
     """Periodic x, insulated walls, reaction on: every O2 consumed makes two
     H2O (Eq. 12) and releases Eq. 15's heat, so sum(C_H2O + 2 C_O2) and
     sum(T + h C_O2) stay constant, and so does the flow mass."""
     nx, ny = 12, 10
     p = base_params(nx, ny, reaction_mode=mode, ny_cl=3 if mode else 0, V_op=0.5,
-                    aj0_ref=1e-4, dt_s=2e-5, dx_cm=2e-3, body_force_x=1e-5, alpha_a=alpha_a)
+                    aj0_ref=1e-4, dt_s=2e-5, dx_cm=2e-3, body_force_x=1e-5, alpha_a=alpha_a,
+                    scalar_advection=scalar_advection)
     o = Oracle(p, uniform_material(nx, ny, phi=0.6, K=1.0, D_O2=0.03, D_H2O=0.04,
                                    alpha_T=0.02))
     h = oracle_lib.orc_heat_per_O2(ctypes.byref(o.P), 343.0)
