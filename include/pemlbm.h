@@ -76,6 +76,20 @@ typedef struct {
                               NULL = none.  Solids may not touch column 0 or the last
                               two columns. */
   void *cuda_stream;       /* borrowed cudaStream_t; NULL = the library's own stream */
+  int32_t x_begin, x_end;  /* x-slab decomposition of a long channel (the geometry of Sec. 4,
+                              Fig. 4): with x_end > 0 the domain holds only the columns
+                              [x_begin, x_end) of the nx-column lattice described here
+                              (at least 4 of them).  Positions, the inlet and outlet
+                              columns, solid cells (solid is the whole [ny][nx] lattice)
+                              and, in lbm_set_fields, the material arrays and the
+                              palette are the whole lattice's, so that neighbouring
+                              slabs agree cell for cell.  A side inside the lattice
+                              borders a neighbour slab: its pulls read a ghost column
+                              that lbm_halo_exchange (same device) or lbm_halo_unpack
+                              fills before each step.  Per-cell arrays of the other
+                              calls cover the slab's own columns.  Not with
+                              periodic_x, lbm_grad, lbm_vjp, batches or device
+                              material.  0, 0: the whole lattice. */
 } lbm_domain_desc;
 
 /* Operating point and closure constants.  Lattice units unless a unit is
@@ -133,6 +147,14 @@ typedef struct {
                                   heat adds to a fixed bottom temperature.  lbm_grad and
                                   lbm_vjp need 0. */
   double C_wall[3][3];         /* wall values of wall_dirichlet: K and mole fractions */
+  int32_t scalar_advection;    /* flux moments of the D2Q5 equilibria of Eq. 10: 0 u C as
+                                  printed; 1 u (C - C_in), each scalar advected relative to
+                                  its inlet value.  Both give the same continuum equation
+                                  where div u = 0, which the incompressible flow of Sec. 2.1
+                                  satisfies; 1 drops the source C_in div u that the lattice
+                                  flow's small divergence adds (a uniform field at the inlet
+                                  value then stays exactly uniform), and keeps the flux
+                                  populations small in the deviation storage. */
 } lbm_params;
 
 typedef struct lbm_domain lbm_domain; /* opaque */
@@ -156,7 +178,7 @@ lbm_status lbm_destroy_domain(lbm_domain *d);
  * and H2O bits 0 with the thin film), finite buoyancy. */
 lbm_status lbm_set_params(lbm_domain *d, const lbm_params *p);
 
-/* Per-cell material, host arrays [ny][nx] of doubles, lattice units:
+/* Per-cell material, arrays [ny][nx] of doubles, lattice units:
  *   phi           porosity, 0 < phi <= 1 (Eq. 5, 7)
  *   K             permeability; +INFINITY marks clear fluid (no drag) (Eq. 7)
  *   alpha_T       effective thermal diffusivity (Eq. 19)
@@ -165,13 +187,19 @@ lbm_status lbm_set_params(lbm_domain *d, const lbm_params *p);
  *   rho_cp_ratio  (rho c_p)_eff / (rho c_p)_f of Eq. 19, >= 1e-6; the
  *                 reaction heat enters the temperature equation divided by
  *                 it.  NULL = 1 everywhere.
- * Each diffusivity must lie in (0, 5/(20 sqrt 3)] so that the D2Q5 rest
- * weight (1-b)/5 of Eq. 10 is non-negative.  Solid cells are ignored.
- * Distinct material tuples are collected into a palette of at most 65535
- * entries (EINVAL beyond that). */
+ * on_device = 0: host arrays.  on_device = 1: device arrays on the domain's
+ * device, read on the domain's stream (ordered after work already queued
+ * there); the material palette is then built by kernels, and only the
+ * palette (at most 65535 tuples) is copied to the host.  Both give the same
+ * palette, entry for entry.  Each diffusivity must lie in
+ * (0, 5/(20 sqrt 3)] so that the D2Q5 rest weight (1-b)/5 of Eq. 10 is
+ * non-negative.  Solid cells are ignored.  Distinct material tuples are
+ * collected into a palette of at most 65535 entries (EINVAL beyond that).
+ * EINVAL leaves the domain's previous material unchanged.  Synchronises
+ * the stream. */
 lbm_status lbm_set_fields(lbm_domain *d, const double *phi, const double *K,
                           const double *alpha_T, const double *D_O2, const double *D_H2O,
-                          const double *rho_cp_ratio);
+                          const double *rho_cp_ratio, int32_t on_device);
 
 /* Initial state: f_i = w_i rho0 (rest), g = D2Q5 equilibrium of the inlet
  * values at rest with each cell's own b.  Step counter := 0. */
@@ -297,14 +325,17 @@ lbm_status lbm_bytes_per_cell(lbm_domain *d, double *bytes);
  * checkpoints every `segment` steps (<= 0: ceil(sqrt(nsteps))).  Memory:
  * about (nsteps/segment + segment) population states.  The gradient of the
  * Fickian interface mode treats each scalar's b (that of its largest
- * diffusivity) as fixed.  J and the gradients go to host memory: dphi, dK,
- * dD_O2 are [ny][nx] doubles (NULL to skip), du_in one double.  EINVAL for
+ * diffusivity) as fixed.  dphi, dK, dD_O2 are [ny][nx] doubles (NULL to
+ * skip): host memory with on_device = 0, device memory written on the
+ * domain's stream with on_device = 1.  J and du_in (one double each) are
+ * host values either way; the call synchronises the stream.  EINVAL for
  * objective outside {0, 1}, nsteps outside [2, 2^30], stochastic rounding
  * (lbm_domain_desc.rounding 1), closed_x, buoyancy or fixed wall values
  * (the natural-convection and validation set-ups); ENOMEM if the
  * checkpoints do not fit. */
 lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t segment,
-                    double *J, double *dphi, double *dK, double *dD_O2, double *du_in);
+                    double *J, double *dphi, double *dK, double *dD_O2, double *du_in,
+                    int32_t on_device);
 
 /* One transposed step at the current state s: given lam_next (host
  * [24][ny][nx], the adjoint of the state after one step), writes lam_prev =
@@ -350,6 +381,37 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, int32_t *schedule, 
 lbm_status lbm_batch_step(lbm_batch *b, int64_t nsteps);
 /* lbm_batch_step bracketed by CUDA events on the batch stream; elapsed ms. */
 lbm_status lbm_batch_time_steps(lbm_batch *b, int64_t nsteps, double *elapsed_ms);
+
+/* x-slabs (lbm_domain_desc.x_begin, x_end).  The step pulls, at a slab side,
+ * six populations per row from the neighbouring slab's edge column: the +x
+ * movers (f1, f5, f8 and the D2Q5 link-1 populations of T, O2, H2O, Eq. 2
+ * and 9 orders) enter through the low side, the -x movers (f3, f6, f7 and
+ * the link-3 populations) through the high side.  After every step (and
+ * after lbm_reset), before the next step, each side's ghost column must be
+ * filled from the neighbour's state of the same step:
+ *   lbm_halo_exchange(left, right): both directions between two slabs of one
+ *     lattice on the same device (left's x_end = right's x_begin).  Ordered
+ *     after both slabs' queued work by events; the copies run on left's
+ *     stream and right's stream waits for them.  EINVAL unless they are
+ *     neighbours with equal storage and deviation references (the same
+ *     lattice arrays and parameters); ESTATE before reset or at different
+ *     step counts.
+ *   lbm_halo_pack(d, side, buf): writes the six populations leaving d through
+ *     side (0 low x, 1 high x) into buf, device memory of [6][ny] values of
+ *     the storage type, in the order above;
+ *   lbm_halo_unpack(d, side, buf): fills side's ghost column from such an
+ *     array packed by the neighbour on its facing side.
+ *   Both are asynchronous on d's stream; for slabs in different processes
+ *   the caller moves buf between them.  EINVAL for a side that borders no
+ *   slab.  The values are the storage's deviations, which agree between
+ *   slabs set up from the same lattice arrays and parameters.
+ * Reductions are per slab: lbm_current_density averages over the slab's
+ * columns (the lattice's mean weights each slab by its width),
+ * lbm_balances reports zero flow through a slab side, lbm_residual compares
+ * the slab's own moments. */
+lbm_status lbm_halo_exchange(lbm_domain *left, lbm_domain *right);
+lbm_status lbm_halo_pack(lbm_domain *d, int32_t side, void *buf);
+lbm_status lbm_halo_unpack(lbm_domain *d, int32_t side, const void *buf);
 
 /* The steady-state residual of lbm_residual, computed without allocating.
  * The paper has no counterpart of this entry point.  It is for callers that

@@ -145,6 +145,12 @@ struct lbm_domain {
   cudaEvent_t obs_done[2] = {nullptr, nullptr};
   cudaStream_t obs_side = nullptr;             // the reductions, beside the steps
   cudaEvent_t obs_fork = nullptr, obs_join = nullptr;
+  // x-slab of a larger lattice: columns [x0, x0 + nx) of nxg; a side that
+  // borders a neighbour slab reads the ghost column the exchange fills
+  int x0 = 0, nxg = 0;
+  bool halo_lo = false, halo_hi = false;
+  std::vector<uint8_t> hsolid;                 // the whole lattice's solids (slabs)
+  cudaEvent_t ev_halo = nullptr;
 };
 
 namespace {
@@ -173,6 +179,8 @@ KArgs make_args(const lbm_domain *d) {
   a.gam_y = p.buoy_gy;
   a.buoy_off = d->Cref[0] - p.T_buoy;
   a.closed_x = d->desc.closed_x;
+  a.halo_lo = d->halo_lo;
+  a.halo_hi = d->halo_hi;
   a.wall_dir = p.wall_dirichlet;
   for (int k = 0; k < 3; ++k)
     for (int s = 0; s < 3; ++s) a.Cwall[k][s] = p.C_wall[k][s];
@@ -190,6 +198,7 @@ KArgs make_args(const lbm_domain *d) {
     a.wr1[s] = (4.0 + d->bref[s]) / 20.0;
     a.Cin[s] = Cin[s];
     a.Ctop[s] = Ctop[s];
+    a.adv_off[s] = d->Cref[s] - (p.scalar_advection ? Cin[s] : 0.0);
   }
   // Tafel rate (Eq. 13, 14, 16, 17) per unit O2 mole fraction:
   //   k(T) = A exp(-E (1/T - 1/T_ref) + alpha_c F (U0(T) - V)/(R T))
@@ -410,13 +419,28 @@ lbm_status lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
       for (int x : {0, D.nx - 2, D.nx - 1})
         if (D.solid[(size_t)y * D.nx + x]) return fail(LBM_EINVAL, "solid cell on an end column x=%d", x);
   }
+  const bool slab = D.x_begin != 0 || D.x_end != 0;
+  if (slab) {
+    if (!(D.x_begin >= 0 && D.x_begin < D.x_end && D.x_end <= D.nx))
+      return fail(LBM_EINVAL, "slab [%d, %d) outside the lattice of %d columns", D.x_begin, D.x_end, D.nx);
+    if (D.x_end - D.x_begin < 4) return fail(LBM_EINVAL, "a slab needs at least 4 columns");
+    if (D.periodic_x) return fail(LBM_EINVAL, "x-slabs of a periodic lattice are not supported");
+  }
   lbm_domain *d = new lbm_domain();
   d->desc = D;
   d->desc.solid = nullptr;
-  d->nx = D.nx;
+  d->x0 = slab ? D.x_begin : 0;
+  d->nxg = D.nx;
+  d->nx = slab ? D.x_end - D.x_begin : D.nx;
+  d->halo_lo = slab && D.x_begin > 0;
+  d->halo_hi = slab && D.x_end < D.nx;
+  if (slab && D.solid) d->hsolid.assign(D.solid, D.solid + (size_t)D.nx * D.ny);
   d->ny = D.ny;
   const int align = 64;   // 128-byte rows for every storage type
-  d->nxp = (D.nx + align - 1) / align * align;
+  // a slab side's ghost column lives in the row padding: x = nx on the high
+  // side, x = nxp - 1 of the row below on the low side (two spare columns)
+  const int need = d->nx + ((d->halo_lo || d->halo_hi) ? 2 : 0);
+  d->nxp = (need + align - 1) / align * align;
   d->plane = (long long)d->nxp * D.ny;
   d->esize = elem_size(D.precision);
   // untuned default: 64 x 2 cells at 8 blocks per SM for FP32 storage (the
@@ -440,12 +464,12 @@ lbm_status lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
       dmalloc(&d->mask, 2 * cells) != cudaSuccess || dmalloc(&d->mid, cells * 2) != cudaSuccess ||
       dmalloc(&d->pal, coef * kMaxPalette) != cudaSuccess ||
       dmalloc(&d->raw, sizeof(MatRaw) * kMaxPalette) != cudaSuccess ||
-      dmalloc(&d->snap, rsize * 5 * (size_t)D.nx * D.ny) != cudaSuccess ||
-      dmalloc(&d->partial, sizeof(double) * 10 * residual_blocks(D.nx, D.ny)) != cudaSuccess ||
-      dmalloc(&d->colsum, sizeof(double) * 2 * D.nx) != cudaSuccess ||
+      dmalloc(&d->snap, rsize * 5 * (size_t)d->nx * D.ny) != cudaSuccess ||
+      dmalloc(&d->partial, sizeof(double) * 10 * residual_blocks(d->nx, D.ny)) != cudaSuccess ||
+      dmalloc(&d->colsum, sizeof(double) * 2 * d->nx) != cudaSuccess ||
       dmalloc(&d->dsmall, sizeof(double) * 16) != cudaSuccess || dmalloc(&d->dbad, sizeof(int)) != cudaSuccess ||
       dmalloc(&d->dseed, 256) != cudaSuccess ||
-      dmalloc(&d->dprofile, sizeof(float) * D.nx) != cudaSuccess ||
+      dmalloc(&d->dprofile, sizeof(float) * d->nx) != cudaSuccess ||
       hmalloc(&d->hsmall, sizeof(double) * 16) != cudaSuccess) {
     cudaGetLastError();
     return cleanup(fail(LBM_ENOMEM, "device allocation of %.1f MB failed", 2.0 * pop_bytes / 1e6));
@@ -460,8 +484,8 @@ lbm_status lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
   cudaMemsetAsync(d->mid, 0, cells * 2, d->stream);
   cudaMemsetAsync(d->pop[0], 0, pop_bytes, d->stream);
   cudaMemsetAsync(d->pop[1], 0, pop_bytes, d->stream);
-  launch_build_mask(d->mask, dsolid, D.nx, D.ny, d->nxp, D.ny_cl, D.ny_gdl, D.reaction_mode,
-                    D.periodic_x, D.closed_x, d->stream);
+  launch_build_mask(d->mask, dsolid, d->nx, D.ny, d->nxp, D.ny_cl, D.ny_gdl, D.reaction_mode,
+                    D.periodic_x, D.closed_x, d->x0, D.nx, d->stream);
   cudaError_t e = cudaStreamSynchronize(d->stream);
   if (dsolid) cudaFree(dsolid);
   if (e != cudaSuccess) return cleanup(fail(LBM_ECUDA, "mask build: %s", cudaGetErrorString(e)));
@@ -484,6 +508,7 @@ lbm_status lbm_destroy_domain(lbm_domain *d) {
   if (d->obs_side) cudaStreamDestroy(d->obs_side);
   if (d->ev0) cudaEventDestroy(d->ev0);
   if (d->ev1) cudaEventDestroy(d->ev1);
+  if (d->ev_halo) cudaEventDestroy(d->ev_halo);
   if (d->own_stream && d->stream) cudaStreamDestroy(d->stream);
   delete d;
   return LBM_OK;
@@ -503,6 +528,8 @@ lbm_status lbm_set_params(lbm_domain *d, const lbm_params *p) {
       !(p->x_ref > 0) || !(p->R > 0) || !(p->F > 0) || !(p->T_ref_kin > 0) || !(p->aj0_ref >= 0))
     return fail(LBM_EINVAL, "non-positive physical constant");
   if (p->interface_mode != 0 && p->interface_mode != 1) return fail(LBM_EINVAL, "interface_mode must be 0 or 1");
+  if (p->scalar_advection != 0 && p->scalar_advection != 1)
+    return fail(LBM_EINVAL, "scalar_advection must be 0 or 1");
   if (p->wall_dirichlet & ~0x1ff) return fail(LBM_EINVAL, "wall_dirichlet has bits beyond 8");
   if ((p->wall_dirichlet & 0x38) && !d->desc.closed_x)
     return fail(LBM_EINVAL, "fixed values on the x = nx - 1 wall need closed_x");
@@ -523,16 +550,116 @@ lbm_status lbm_set_params(lbm_domain *d, const lbm_params *p) {
   return LBM_OK;
 }
 
+// EINVAL with a message unless the material tuple of cell (x, y) lies in the
+// ranges lbm_set_fields accepts.
+lbm_status check_tuple(const MatRaw &t, int x, int y) {
+  const double amax = 5.0 / (20.0 * std::sqrt(3.0));
+  if (!(t.phi > 0 && t.phi <= 1)) return fail(LBM_EINVAL, "porosity %g at (%d,%d) outside (0,1]", t.phi, x, y);
+  if (!(t.K > 0)) return fail(LBM_EINVAL, "permeability %g at (%d,%d) must be > 0", t.K, x, y);
+  if (!(t.sigma >= 1e-6) || std::isinf(t.sigma))
+    return fail(LBM_EINVAL, "heat-capacity ratio %g at (%d,%d) must be finite and >= 1e-6", t.sigma, x, y);
+  for (int s = 0; s < 3; ++s)
+    if (!(t.alpha[s] > 0 && t.alpha[s] <= amax))
+      return fail(LBM_EINVAL, "diffusivity %g at (%d,%d) outside (0, %g]", t.alpha[s], x, y, amax);
+  return LBM_OK;
+}
+
+// Palette of device-resident fields: built by the palette kernels into
+// scratch first, so that a refused set leaves the domain's material as it
+// was; only the palette itself (at most 65535 tuples) comes to the host.
+lbm_status set_fields_device(lbm_domain *d, const double *phi, const double *K,
+                             const double *alpha_T, const double *D_O2, const double *D_H2O,
+                             const double *rho_cp_ratio) {
+  const int nx = d->nx, ny = d->ny;
+  struct Scratch {
+    void *p = nullptr;
+    ~Scratch() {
+      if (p) cudaFree(p);
+    }
+  } sc;
+  const size_t mid_bytes = sizeof(uint16_t) * (size_t)d->plane;
+  const size_t raw_bytes = sizeof(MatRaw) * kMaxPalette;
+  const size_t work = palette_scratch_bytes(nx, ny);
+  const size_t off_mid = (work + 255) / 256 * 256, off_raw = (off_mid + mid_bytes + 255) / 256 * 256,
+               off_st = (off_raw + raw_bytes + 255) / 256 * 256;
+  if (dmalloc(&sc.p, off_st + sizeof(PalStatus)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(LBM_ENOMEM, "palette scratch of %.1f MB", (off_st + 256) / 1e6);
+  }
+  char *base = (char *)sc.p;
+  uint16_t *mid = (uint16_t *)(base + off_mid);
+  MatRaw *raw = (MatRaw *)(base + off_raw);
+  PalStatus *st = (PalStatus *)(base + off_st);
+  const PalFields f{phi, K, alpha_T, D_O2, D_H2O, rho_cp_ratio};
+  CK(launch_device_palette(f, d->mask, nx, ny, d->nxp, mid, raw, kMaxPalette, sc.p, st, d->stream));
+  PalStatus h{};
+  CK(cudaMemcpyAsync(&h, st, sizeof h, cudaMemcpyDeviceToHost, d->stream));
+  CK(cudaStreamSynchronize(d->stream));
+  if (h.flags & kPalInvalid) {
+    // the first invalid cell in row-major order, for the message
+    const int x = h.bad_cell % nx, y = h.bad_cell / nx;
+    MatRaw t{};
+    t.sigma = 1.0;
+    const double *src[6] = {phi, K, alpha_T, D_O2, D_H2O, rho_cp_ratio};
+    double *dst[6] = {&t.phi, &t.K, &t.alpha[0], &t.alpha[1], &t.alpha[2], &t.sigma};
+    for (int k = 0; k < 6; ++k)
+      if (src[k]) CK(cudaMemcpy(dst[k], src[k] + h.bad_cell, sizeof(double), cudaMemcpyDeviceToHost));
+    lbm_status s = check_tuple(t, x, y);
+    return s != LBM_OK ? s : fail(LBM_EINVAL, "invalid material at (%d,%d)", x, y);
+  }
+  if ((h.flags & kPalTooMany) || h.npal > kMaxPalette)
+    return fail(LBM_EINVAL, "more than %d distinct materials", kMaxPalette);
+  if (h.flags & kPalCollision) return fail(LBM_ECUDA, "material hash collision in the palette build");
+  if (h.npal == 0) return fail(LBM_EINVAL, "no fluid cells");
+  std::vector<MatRaw> hraw((size_t)h.npal);
+  CK(cudaMemcpyAsync(hraw.data(), raw, sizeof(MatRaw) * hraw.size(), cudaMemcpyDeviceToHost, d->stream));
+  // reference material: the top fluid cell of the inlet column, as the host build
+  std::vector<uint8_t> col_mask((size_t)ny);
+  std::vector<uint16_t> col_mid((size_t)ny);
+  CK(cudaMemcpy2DAsync(col_mask.data(), 1, d->mask, d->nxp, 1, ny, cudaMemcpyDeviceToHost, d->stream));
+  CK(cudaMemcpy2DAsync(col_mid.data(), 2, mid, 2 * (size_t)d->nxp, 2, ny, cudaMemcpyDeviceToHost, d->stream));
+  CK(cudaMemcpyAsync(d->raw, raw, sizeof(MatRaw) * hraw.size(), cudaMemcpyDeviceToDevice, d->stream));
+  CK(cudaMemcpyAsync(d->mid, mid, mid_bytes, cudaMemcpyDeviceToDevice, d->stream));
+  CK(cudaStreamSynchronize(d->stream));
+  d->npal = h.npal;
+  d->ref_entry = 0;
+  for (int y = ny - 1; y >= 0; --y)
+    if ((col_mask[y] & REG_MASK) != REG_SOLID) {
+      d->ref_entry = col_mid[y];
+      break;
+    }
+  d->hraw = std::move(hraw);
+  lbm_status st2 = prep_palette(d);
+  if (st2 != LBM_OK) return st2;
+  d->have_fields = true;
+  drop_graphs(d);
+  return LBM_OK;
+}
+
 lbm_status lbm_set_fields(lbm_domain *d, const double *phi, const double *K, const double *alpha_T,
-                          const double *D_O2, const double *D_H2O, const double *rho_cp_ratio) {
+                          const double *D_O2, const double *D_H2O, const double *rho_cp_ratio,
+                          int32_t on_device) {
   NvtxRange nvtx_("pemlbm.set_fields");
   if (!d || !phi || !K || !alpha_T || !D_O2 || !D_H2O) return fail(LBM_EINVAL, "null argument");
   if (!d->have_params) return fail(LBM_ESTATE, "call lbm_set_params before lbm_set_fields");
-  const int nx = d->nx, ny = d->ny;
-  std::vector<uint8_t> mask((size_t)d->plane);
-  CK(cudaMemcpyAsync(mask.data(), d->mask, mask.size(), cudaMemcpyDeviceToHost, d->stream));
-  CK(cudaStreamSynchronize(d->stream));
-  const double amax = 5.0 / (20.0 * std::sqrt(3.0));
+  if (on_device != 0 && on_device != 1) return fail(LBM_EINVAL, "on_device must be 0 or 1");
+  const bool slab = d->nx != d->nxg;
+  if (on_device && slab) return fail(LBM_EINVAL, "an x-slab takes its material from host arrays");
+  if (on_device) return set_fields_device(d, phi, K, alpha_T, D_O2, D_H2O, rho_cp_ratio);
+  // an x-slab takes the whole lattice's arrays: its palette is the whole
+  // lattice's, so that every slab holds the same entries and the same
+  // deviation references, and it keeps the indices of its own columns
+  const int nx = d->nxg, ny = d->ny;
+  std::vector<uint8_t> mask;
+  if (!slab) {
+    mask.resize((size_t)d->plane);
+    CK(cudaMemcpyAsync(mask.data(), d->mask, mask.size(), cudaMemcpyDeviceToHost, d->stream));
+    CK(cudaStreamSynchronize(d->stream));
+  }
+  auto solid_at = [&](int x, int y) {
+    if (!slab) return (mask[(size_t)y * d->nxp + x] & REG_MASK) == REG_SOLID;
+    return !d->hsolid.empty() && d->hsolid[(size_t)y * nx + x] != 0;
+  };
   std::unordered_map<MatRaw, int, TupleHash, TupleEq> index;
   std::vector<MatRaw> raw;
   std::vector<uint16_t> mid((size_t)d->plane, 0);
@@ -541,20 +668,15 @@ lbm_status lbm_set_fields(lbm_domain *d, const double *phi, const double *K, con
   for (int y = 0; y < ny; ++y)
     for (int x = 0; x < nx; ++x) {
       const size_t o = (size_t)y * nx + x;
-      if ((mask[(size_t)y * d->nxp + x] & REG_MASK) == REG_SOLID) continue;
+      if (solid_at(x, y)) continue;
       const MatRaw t{phi[o], K[o], {alpha_T[o], D_O2[o], D_H2O[o]},
                      rho_cp_ratio ? rho_cp_ratio[o] : 1.0};
       int k;
       if (prev_k >= 0 && TupleEq()(t, prev)) {
         k = prev_k;   // same material as the previous cell: the common case
       } else {
-        if (!(t.phi > 0 && t.phi <= 1)) return fail(LBM_EINVAL, "porosity %g at (%d,%d) outside (0,1]", t.phi, x, y);
-        if (!(t.K > 0)) return fail(LBM_EINVAL, "permeability %g at (%d,%d) must be > 0", t.K, x, y);
-        if (!(t.sigma >= 1e-6) || std::isinf(t.sigma))
-          return fail(LBM_EINVAL, "heat-capacity ratio %g at (%d,%d) must be finite and >= 1e-6", t.sigma, x, y);
-        for (int s = 0; s < 3; ++s)
-          if (!(t.alpha[s] > 0 && t.alpha[s] <= amax))
-            return fail(LBM_EINVAL, "diffusivity %g at (%d,%d) outside (0, %g]", t.alpha[s], x, y, amax);
+        lbm_status vs = check_tuple(t, x, y);
+        if (vs != LBM_OK) return vs;
         auto it = index.find(t);
         if (it == index.end()) {
           k = (int)raw.size();
@@ -567,7 +689,8 @@ lbm_status lbm_set_fields(lbm_domain *d, const double *phi, const double *K, con
         prev = t;
         prev_k = k;
       }
-      mid[(size_t)y * d->nxp + x] = (uint16_t)k;
+      const int lx = x - d->x0;
+      if (lx >= 0 && lx < d->nx) mid[(size_t)y * d->nxp + lx] = (uint16_t)k;
     }
   if (raw.empty()) return fail(LBM_EINVAL, "no fluid cells");
   // cells that carry no material (solids, padding) point at entry 0
@@ -578,8 +701,11 @@ lbm_status lbm_set_fields(lbm_domain *d, const double *phi, const double *K, con
   // inlet column (the channel gas), else entry 0
   d->ref_entry = 0;
   for (int y = ny - 1; y >= 0; --y)
-    if ((mask[(size_t)y * d->nxp] & REG_MASK) != REG_SOLID) {
-      d->ref_entry = mid[(size_t)y * d->nxp];
+    if (!solid_at(0, y)) {
+      const size_t o = (size_t)y * nx;
+      const MatRaw t{phi[o], K[o], {alpha_T[o], D_O2[o], D_H2O[o]},
+                     rho_cp_ratio ? rho_cp_ratio[o] : 1.0};
+      d->ref_entry = index.at(t);   // every fluid cell's tuple is in the index
       break;
     }
   d->hraw = std::move(raw);
@@ -1140,12 +1266,13 @@ void finish_lambda(lbm_domain *d, AdjWork &w, int cur) {
 }
 
 lbm_status copy_grads_out(lbm_domain *d, AdjWork &w, double *dphi, double *dK, double *dD,
-                          double *du) {
+                          double *du, bool on_device = false) {
   const size_t row = sizeof(double) * d->nx, pitch = sizeof(double) * d->nxp;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   fold_grads(d, w);
-  if (dphi) CK(cudaMemcpy2DAsync(dphi, row, w.tphi.p, pitch, row, d->ny, cudaMemcpyDeviceToHost, d->stream));
-  if (dK) CK(cudaMemcpy2DAsync(dK, row, w.tK.p, pitch, row, d->ny, cudaMemcpyDeviceToHost, d->stream));
-  if (dD) CK(cudaMemcpy2DAsync(dD, row, w.tD.p, pitch, row, d->ny, cudaMemcpyDeviceToHost, d->stream));
+  if (dphi) CK(cudaMemcpy2DAsync(dphi, row, w.tphi.p, pitch, row, d->ny, kind, d->stream));
+  if (dK) CK(cudaMemcpy2DAsync(dK, row, w.tK.p, pitch, row, d->ny, kind, d->stream));
+  if (dD) CK(cudaMemcpy2DAsync(dD, row, w.tD.p, pitch, row, d->ny, kind, d->stream));
   if (du) CK(cudaMemcpyAsync(du, w.gU.p, sizeof(double), cudaMemcpyDeviceToHost, d->stream));
   CK(cudaStreamSynchronize(d->stream));
   return LBM_OK;
@@ -1175,6 +1302,7 @@ lbm_status adjoint_covers(const lbm_domain *d) {
   const lbm_params &p = d->prm;
   if (d->desc.closed_x || p.buoy_gx != 0.0 || p.buoy_gy != 0.0 || p.wall_dirichlet != 0)
     return fail(LBM_EINVAL, "the adjoint does not cover closed_x, buoyancy or fixed wall values");
+  if (d->nx != d->nxg) return fail(LBM_EINVAL, "the adjoint does not cover x-slabs");
   return LBM_OK;
 }
 lbm_status lam_download(lbm_domain *d, const void *dev, double *host) {
@@ -1216,10 +1344,12 @@ lbm_status lbm_vjp(lbm_domain *d, const double *lam_next, double *lam_prev, doub
 }
 
 lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t segment,
-                    double *J, double *dphi, double *dK, double *dD_O2, double *du_in) {
+                    double *J, double *dphi, double *dK, double *dD_O2, double *du_in,
+                    int32_t on_device) {
   NvtxRange nvtx_("pemlbm.grad");
   lbm_status s = check_ready(d);
   if (s != LBM_OK) return s;
+  if (on_device != 0 && on_device != 1) return fail(LBM_EINVAL, "on_device must be 0 or 1");
   if (objective != 0 && objective != 1) return fail(LBM_EINVAL, "objective must be 0 or 1");
   if (d->desc.rounding != 0) return fail(LBM_EINVAL, "the adjoint needs round-to-nearest storage");
   if ((s = adjoint_covers(d)) != LBM_OK) return s;
@@ -1425,7 +1555,7 @@ lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t se
     CK(cudaGetLastError());
   }
   finish_lambda(d, w, cur);   // adds the last step's outlet term to gphi
-  return copy_grads_out(d, w, dphi, dK, dD_O2, du_in);
+  return copy_grads_out(d, w, dphi, dK, dD_O2, du_in, on_device == 1);
 }
 
 }  // extern "C"
@@ -1724,6 +1854,8 @@ lbm_status lbm_create_batch(lbm_domain *const *domains, int32_t ncases, lbm_batc
     if (needs_extended(make_args(domains[c])))
       return fail(LBM_EINVAL, "batched domains step the cathode set-up (no closed_x, buoyancy "
                   "or fixed wall values)");
+    if (domains[c]->nx != domains[c]->nxg)
+      return fail(LBM_EINVAL, "batched domains are whole lattices, not x-slabs");
     for (int k = 0; k < c; ++k)
       if (domains[k] == domains[c]) return fail(LBM_EINVAL, "domain %d appears twice", c);
   }
@@ -1877,6 +2009,87 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, int32_t *schedule, 
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// ------------------------------------------------------------- x-slabs
+namespace {
+
+lbm_status slab_pair_check(const lbm_domain *l, const lbm_domain *r) {
+  if (!l || !r || l == r) return fail(LBM_EINVAL, "need two distinct slabs");
+  if (!l->have_state || !r->have_state) return fail(LBM_ESTATE, "reset both slabs first");
+  if (!l->halo_hi || !r->halo_lo || l->x0 + l->nx != r->x0 || l->nxg != r->nxg || l->ny != r->ny)
+    return fail(LBM_EINVAL, "slabs [%d, %d) and [%d, %d) are not neighbours of one lattice", l->x0,
+                l->x0 + l->nx, r->x0, r->x0 + r->nx);
+  if (l->desc.precision != r->desc.precision) return fail(LBM_EINVAL, "slabs of different storage");
+  for (int s = 0; s < 3; ++s)
+    if (l->Cref[s] != r->Cref[s] || l->bref[s] != r->bref[s])
+      return fail(LBM_EINVAL, "slabs with different deviation references (set both from the "
+                  "same lattice arrays and parameters)");
+  if (l->steps != r->steps) return fail(LBM_ESTATE, "slabs at different steps (%lld, %lld)",
+                                        (long long)l->steps, (long long)r->steps);
+  return LBM_OK;
+}
+
+HaloSide edge_of(lbm_domain *d, bool high) {   // the edge column a side sends from
+  return HaloSide{d->pop[d->cur], d->plane, d->nxp, high ? (long long)d->nx - 1 : 0, 0};
+}
+HaloSide ghost_of(lbm_domain *d, bool high) {  // the ghost column a side receives into
+  return HaloSide{d->pop[d->cur], d->plane, d->nxp, high ? (long long)d->nx : -1, 0};
+}
+
+lbm_status ensure_halo_event(lbm_domain *d) {
+  if (!d->ev_halo && cudaEventCreateWithFlags(&d->ev_halo, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    d->ev_halo = nullptr;
+    return fail(LBM_ECUDA, "cudaEventCreate failed");
+  }
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" lbm_status lbm_halo_exchange(lbm_domain *left, lbm_domain *right) {
+  NvtxRange nvtx_("pemlbm.halo_exchange");
+  lbm_status s = slab_pair_check(left, right);
+  if (s != LBM_OK) return s;
+  if ((s = ensure_halo_event(left)) != LBM_OK || (s = ensure_halo_event(right)) != LBM_OK) return s;
+  // both slabs' last steps finish before the copies, which run on the left
+  // slab's stream; the right slab's next step waits for them
+  CK(cudaEventRecord(right->ev_halo, right->stream));
+  CK(cudaStreamWaitEvent(left->stream, right->ev_halo, 0));
+  const int es = (int)left->esize;
+  launch_halo_copy(edge_of(left, true), ghost_of(right, false), left->ny, 1, es, left->stream);
+  launch_halo_copy(edge_of(right, false), ghost_of(left, true), left->ny, 0, es, left->stream);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(left->ev_halo, left->stream));
+  CK(cudaStreamWaitEvent(right->stream, left->ev_halo, 0));
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_halo_pack(lbm_domain *d, int32_t side, void *buf) {
+  NvtxRange nvtx_("pemlbm.halo_pack");
+  if (!d || !buf) return fail(LBM_EINVAL, "null argument");
+  if (side != 0 && side != 1) return fail(LBM_EINVAL, "side must be 0 (low x) or 1 (high x)");
+  if (!(side ? d->halo_hi : d->halo_lo)) return fail(LBM_EINVAL, "side %d borders no slab", side);
+  if (!d->have_state) return fail(LBM_ESTATE, "call lbm_reset first");
+  launch_halo_copy(edge_of(d, side == 1), HaloSide{buf, 0, 0, 0, 1}, d->ny, side == 1 ? 1 : 0,
+                   (int)d->esize, d->stream);
+  CK(cudaGetLastError());
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_halo_unpack(lbm_domain *d, int32_t side, const void *buf) {
+  NvtxRange nvtx_("pemlbm.halo_unpack");
+  if (!d || !buf) return fail(LBM_EINVAL, "null argument");
+  if (side != 0 && side != 1) return fail(LBM_EINVAL, "side must be 0 (low x) or 1 (high x)");
+  if (!(side ? d->halo_hi : d->halo_lo)) return fail(LBM_EINVAL, "side %d borders no slab", side);
+  if (!d->have_state) return fail(LBM_ESTATE, "call lbm_reset first");
+  // into the low ghost come the +x movers of the left neighbour, into the
+  // high ghost the -x movers of the right neighbour
+  launch_halo_copy(HaloSide{(void *)buf, 0, 0, 0, 1}, ghost_of(d, side == 1), d->ny,
+                   side == 1 ? 0 : 1, (int)d->esize, d->stream);
+  CK(cudaGetLastError());
+  return LBM_OK;
+}
+
 // Residual without allocation.
 //
 // Some callers must not let the library allocate device memory once they are

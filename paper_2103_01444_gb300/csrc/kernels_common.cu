@@ -5,42 +5,46 @@ namespace pemlbm {
 
 // Node mask (Sec. 4 geometry): region by rows, boundary bits by position,
 // explicit solids, and a flag for cells with a solid D2Q9 neighbour; a
-// second plane of the same size says which neighbours are solid.
+// second plane of the same size says which neighbours are solid.  The
+// domain may be the x-slab [x0, x0 + nx) of a lattice nxg wide: positions,
+// boundary bits and solid neighbours are those of the whole lattice (solid
+// is [ny][nxg]), and a slab side inside the lattice gets no x bits.
 __global__ void k_build_mask(uint8_t *__restrict__ mask, const uint8_t *__restrict__ solid, int nx,
                              int ny, int nxp, int ny_cl, int ny_gdl, int mode, int periodic,
-                             int closed) {
+                             int closed, int x0, int nxg) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   if (x >= nxp || y >= ny) return;
   const long long c = (long long)y * nxp + x;
   const long long plane = (long long)nxp * ny;
   if (x >= nx) {
-    mask[c] = REG_SOLID;   // padding: never updated, never a pull source
+    mask[c] = REG_SOLID;   // padding and ghost columns: never updated
     mask[plane + c] = 0;
     return;
   }
-  auto is_solid = [&](int xx, int yy) { return solid && solid[(long long)yy * nx + xx]; };
+  const int gx = x0 + x;
+  auto is_solid = [&](int xx, int yy) { return solid && solid[(long long)yy * nxg + xx]; };
   uint8_t reg;
-  if (is_solid(x, y)) reg = REG_SOLID;
+  if (is_solid(gx, y)) reg = REG_SOLID;
   else if (mode == 1 && y < ny_cl) reg = REG_CATALYST;
   else if (y < ny_cl + ny_gdl) reg = REG_POROUS;
   else reg = REG_CLEAR;
   uint8_t m = reg;
-  if (x == 0) m |= M_XLO;
-  if (x == nx - 1) m |= M_XHI;
+  if (gx == 0) m |= M_XLO;
+  if (gx == nxg - 1) m |= M_XHI;
   if (y == ny - 1) m |= M_YHI;
   if (y == 0) m |= M_YLO;
-  if (reg == REG_CLEAR && x == 0 && !periodic && !closed) m |= M_INLET;
+  if (reg == REG_CLEAR && gx == 0 && !periodic && !closed) m |= M_INLET;
   // second plane: bit i - 1 set when the source x - e_i of flow link i
   // (i = 1..8, Eq. 2 order) is a solid cell inside the lattice
   uint8_t nb = 0;
   if (reg != REG_SOLID && solid) {
     const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1}, ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
     for (int i = 1; i < 9; ++i) {
-      int sx = x - ex[i];
+      int sx = gx - ex[i];
       const int sy = y - ey[i];
       if (sy < 0 || sy >= ny) continue;
-      if (periodic) sx = (sx + nx) % nx;
-      if (sx < 0 || sx >= nx) continue;
+      if (periodic) sx = (sx + nxg) % nxg;
+      if (sx < 0 || sx >= nxg) continue;
       if (is_solid(sx, sy)) nb |= (uint8_t)(1u << (i - 1));
     }
     if (nb) m |= M_NEAR_SOLID;
@@ -49,15 +53,53 @@ __global__ void k_build_mask(uint8_t *__restrict__ mask, const uint8_t *__restri
   mask[plane + c] = nb;
 }
 
+// Ghost columns of x-slabs.  Six populations cross a slab side: those
+// moving +x (f1, f5, f8 and the D2Q5 link-1 planes of T, O2, H2O) leave
+// through the high side into the right neighbour's low ghost column, those
+// moving -x (f3, f6, f7 and the link-3 planes) through the low side into
+// the left neighbour's high ghost column.  Plane q's ghost of row y sits at
+// y nxp - 1 (low side; row 0's is the previous plane's last element) or
+// y nxp + nx (high side) from the plane's start, inside the row padding.
+// One copy moves one direction's six planes for every row: from column col
+// of a lattice buffer (or a packed [6][ny] array) to offset off of a lattice
+// buffer (or a packed array).
+template <typename S>
+__global__ void k_halo_copy(const S *__restrict__ src, long long src_plane, int src_nxp,
+                            long long src_off, int src_packed, S *__restrict__ dst,
+                            long long dst_plane, int dst_nxp, long long dst_off, int dst_packed,
+                            int ny, int plus) {
+  const int y = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+  if (y >= ny || k >= 6) return;
+  const int mv_plus[6] = {1, 5, 8, 10, 15, 20}, mv_minus[6] = {3, 6, 7, 12, 17, 22};
+  const long long q = plus ? mv_plus[k] : mv_minus[k];
+  const long long si = src_packed ? (long long)k * ny + y : q * src_plane + (long long)y * src_nxp + src_off;
+  const long long di = dst_packed ? (long long)k * ny + y : q * dst_plane + (long long)y * dst_nxp + dst_off;
+  dst[di] = src[si];
+}
+
 __global__ void k_seed_advance(unsigned *ctr) { *ctr += 1u; }
 
 void launch_seed_advance(unsigned *ctr, cudaStream_t st) { k_seed_advance<<<1, 1, 0, st>>>(ctr); }
 
 void launch_build_mask(uint8_t *mask, const uint8_t *solid, int nx, int ny, int nxp, int ny_cl,
-                       int ny_gdl, int mode, int periodic, int closed, cudaStream_t st) {
+                       int ny_gdl, int mode, int periodic, int closed, int x0, int nxg,
+                       cudaStream_t st) {
   dim3 grid((nxp + 127) / 128, ny);
   k_build_mask<<<grid, 128, 0, st>>>(mask, solid, nx, ny, nxp, ny_cl, ny_gdl, mode, periodic,
-                                     closed);
+                                     closed, x0, nxg);
+}
+
+void launch_halo_copy(const HaloSide &src, const HaloSide &dst, int ny, int plus, int esize,
+                      cudaStream_t st) {
+  dim3 grid((ny + 127) / 128, 6);
+#define PEMLBM_HALO(T)                                                                         \
+  k_halo_copy<T><<<grid, 128, 0, st>>>((const T *)src.p, src.plane, src.nxp, src.off,          \
+                                       src.packed, (T *)dst.p, dst.plane, dst.nxp, dst.off,   \
+                                       dst.packed, ny, plus)
+  if (esize == 8) PEMLBM_HALO(double);
+  else if (esize == 4) PEMLBM_HALO(float);
+  else PEMLBM_HALO(uint16_t);
+#undef PEMLBM_HALO
 }
 
 // Per-material coefficients: Darcy and Forchheimer terms of Eq. 7, the l0,

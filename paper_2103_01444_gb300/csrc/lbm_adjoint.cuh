@@ -88,7 +88,7 @@ __device__ __forceinline__ void collide_scalar_rev(const KArgsT<R> &a, const Mat
                                                    const R lo[5], R ld[5], R &lux, R &luy,
                                                    R &lsrc, R &lb, R &lw1, R &lq1) {
   const R Q1 = mc.q1[s], Q3 = R(a.Q3), b = mc.b[s], w1 = mc.w1[s], w0 = R(1) - R(4) * w1;
-  const R C = Cdev + R(a.Cref[s]);
+  const R C = Cdev + R(a.Cref[s]), Ca = Cdev + R(a.adv_off[s]);
   const R n1 = d[1] - d[3], n2 = d[2] - d[4];
   const R e13 = d[1] + d[3], e24 = d[2] + d[4];
   const R n3 = R(-4) * d[0] + (e13 + e24);
@@ -105,10 +105,10 @@ __device__ __forceinline__ void collide_scalar_rev(const KArgsT<R> &a, const Mat
   lb += Q3 * C * ln3p;
   R lC = Q3 * b * ln3p;
   const R ln1 = (R(1) - Q1) * ln1p, ln2 = (R(1) - Q1) * ln2p;
-  lux += Q1 * C * ln1p;
-  luy += Q1 * C * ln2p;
+  lux += Q1 * Ca * ln1p;
+  luy += Q1 * Ca * ln2p;
   lC += Q1 * ux * ln1p + Q1 * uy * ln2p;
-  lq1 += (ux * C - n1) * ln1p + (uy * C - n2) * ln2p;
+  lq1 += (ux * Ca - n1) * ln1p + (uy * Ca - n2) * ln2p;
   const R lCdev = lC + ln0;
   const R le13 = ln3 + ln4, le24 = ln3 - ln4;
   ld[0] += R(-4) * ln3 + lCdev;

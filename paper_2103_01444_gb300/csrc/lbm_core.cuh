@@ -134,6 +134,8 @@ template <typename F> struct KArgsT {
   F dp_in;
   F Q3;                     // Eq. 10 rate of the energy moments
   F Cref[3], wr0[3], wr1[3], bref[3];  // deviation references
+  F adv_off[3];             // advected value of scalar s = deviation sum + adv_off[s]:
+                            // Cref (u C, Eq. 10 as printed) or Cref - C_in (u (C - C_in))
   F Cin[3], Ctop[3];
   // kinetics: k(T) = A exp(e_in - c1 (T - T_in)/(T T_in)), Eq. 13, 14, 16, 17
   F kA_surf, kA_vol, k_ein, k_c1, T_in;
@@ -147,6 +149,8 @@ template <typename F> struct KArgsT {
   // with T - T_buoy = C_T + buoy_off (C_T the deviation sum of the T lattice)
   F gam_x, gam_y, buoy_off;
   int closed_x;             // 1: both x ends are no-slip walls
+  int halo_lo, halo_hi;     // x-slab sides that border a neighbour slab: pulls across
+                            // them read the ghost column (x = -1 or nx) the exchange fills
   int wall_dir;             // bit 3 k + s: scalar s fixed to Cwall[k][s] on wall k
   F Cwall[3][3];            // k: 0 the x = 0 end, 1 the x = nx - 1 end, 2 the bottom
 };
@@ -166,11 +170,13 @@ template <typename F> __host__ __device__ inline KArgsT<F> narrow_args(const KAr
   r.inlet_pressure = a.inlet_pressure; r.dp_in = F(a.dp_in);
   r.gam_x = F(a.gam_x); r.gam_y = F(a.gam_y); r.buoy_off = F(a.buoy_off);
   r.closed_x = a.closed_x; r.wall_dir = a.wall_dir;
+  r.halo_lo = a.halo_lo; r.halo_hi = a.halo_hi;
   for (int k = 0; k < 3; ++k)
     for (int s = 0; s < 3; ++s) r.Cwall[k][s] = F(a.Cwall[k][s]);
   for (int s = 0; s < 3; ++s) {
     r.Cref[s] = F(a.Cref[s]); r.wr0[s] = F(a.wr0[s]); r.wr1[s] = F(a.wr1[s]);
     r.bref[s] = F(a.bref[s]); r.Cin[s] = F(a.Cin[s]); r.Ctop[s] = F(a.Ctop[s]);
+    r.adv_off[s] = F(a.adv_off[s]);
   }
   r.kA_surf = F(a.kA_surf); r.kA_vol = F(a.kA_vol); r.k_ein = F(a.k_ein); r.k_c1 = F(a.k_c1);
   r.T_in = F(a.T_in); r.theta0 = F(a.theta0); r.hpo = F(a.hpo);
@@ -240,6 +246,12 @@ __device__ R pull_flow_edge(const Pops<S, CG> &src, const KArgsT<R> &a, const ui
   const int EX[9] = EX9_TAB, EY[9] = EY9_TAB, OP[9] = OP9_TAB;
   int sx = x - EX[i], sy = y - EY[i];
   if (sy < 0 || sy >= a.ny) return R(src.at(OP[i], x, y));            // wall
+  if ((sx < 0 && a.halo_lo) || (sx >= a.nx && a.halo_hi)) {
+    // the neighbour slab's ghost, unless that cell is solid (second mask plane)
+    if ((m & M_NEAR_SOLID) && ((mask[a.plane + (long long)y * a.nxp + x] >> (i - 1)) & 1u))
+      return R(src.at(OP[i], x, y));
+    return v;
+  }
   if (sx < 0 || sx >= a.nx) {
     if (a.periodic) {
       sx = sx < 0 ? sx + a.nx : sx - a.nx;
@@ -309,6 +321,12 @@ __device__ R pull_scalar_edge(const Pops<S, CG> &src, const KArgsT<R> &a, const 
     if (a.top_dirichlet)
       w = wall_value<R>(a, mc, s, w, R(a.Ctop[s]));
     return w;
+  }
+  if ((sx < 0 && a.halo_lo) || (sx >= a.nx && a.halo_hi)) {
+    // the neighbour slab's ghost, unless that cell is solid (second mask plane)
+    if ((m & M_NEAR_SOLID) && ((mask[a.plane + (long long)y * a.nxp + x] >> (i - 1)) & 1u))
+      return R(src.at(q + OP[i], x, y));
+    return v;
   }
   if (sx < 0 || sx >= a.nx) {
     if (a.periodic) {
@@ -553,16 +571,25 @@ __device__ __forceinline__ void collide_flow(const KArgsT<R> &a, const MatCoef<R
   R a0 = m0 * R(1.0 / 9), a1 = m1 * R(1.0 / 36), a2 = m2 * R(1.0 / 36);
   R a3 = m3 * R(1.0 / 6), a4 = m4 * R(1.0 / 12), a5 = m5 * R(1.0 / 6), a6 = m6 * R(1.0 / 12);
   R a7 = m7 * R(0.25), a8 = m8 * R(0.25);
+  // The conserved moments are closed by remainders: 1/6 and 1/9 are not
+  // binary fractions, so 6 * (m3 / 6) != m3 in floating point, and a collision
+  // built only from the scaled moments would multiply the momentum (and the
+  // mass) by the same constant factor at every cell and step, a coherent
+  // source.  Instead the axis pairs carry what the diagonals leave of m3 and
+  // m5, and the rest population what the others leave of m0 (identical in
+  // exact arithmetic; rounding then stays local and unbiased).
   R axs = a0 - a1 - R(2) * a2, dgs = a0 + R(2) * a1 + a2;
-  o[0] = a0 - R(4) * a1 + R(4) * a2;
-  o[1] = axs + a3 - R(2) * a4 + a7;
-  o[2] = axs + a5 - R(2) * a6 - a7;
-  o[3] = axs - a3 + R(2) * a4 + a7;
-  o[4] = axs - a5 + R(2) * a6 - a7;
   o[5] = dgs + a3 + a4 + a5 + a6 + a8;
   o[6] = dgs - a3 - a4 + a5 + a6 - a8;
   o[7] = dgs - a3 - a4 - a5 - a6 + a8;
   o[8] = dgs + a3 + a4 - a5 - a6 - a8;
+  const R hx = R(0.5) * (m3 - ((o[5] - o[7]) + (o[8] - o[6])));
+  const R hy = R(0.5) * (m5 - ((o[5] - o[7]) + (o[6] - o[8])));
+  o[1] = (axs + a7) + hx;
+  o[3] = (axs + a7) - hx;
+  o[2] = (axs - a7) + hy;
+  o[4] = (axs - a7) - hy;
+  o[0] = m0 - (((o[1] + o[3]) + (o[2] + o[4])) + ((o[5] + o[7]) + (o[6] + o[8])));
 }
 
 // D2Q5 MRT collision of scalar s in deviation moments (Eq. 10), plus a
@@ -571,26 +598,32 @@ template <typename R>
 __device__ __forceinline__ void collide_scalar(const KArgsT<R> &a, const MatCoef<R> &mc, int s,
                                                R ux, R uy, R Cdev, const R d[5], R srcv, R o[5]) {
   const R Q1 = mc.q1[s], Q3 = R(a.Q3);
-  R C = Cdev + R(a.Cref[s]);
+  // the advected value: C, or its excess over the inlet value (then about
+  // zero in the deviation storage, so the flux populations stay small)
+  R Ca = Cdev + R(a.adv_off[s]);
   R n0 = Cdev;
   R n1 = d[1] - d[3], n2 = d[2] - d[4];
   R e13 = d[1] + d[3], e24 = d[2] + d[4];
   R n3 = R(-4) * d[0] + (e13 + e24);
   R n4 = e13 - e24;
   R b = mc.b[s];
-  n1 -= Q1 * (n1 - ux * C);
-  n2 -= Q1 * (n2 - uy * C);
+  n1 -= Q1 * (n1 - ux * Ca);
+  n2 -= Q1 * (n2 - uy * Ca);
   n3 -= Q3 * (n3 - (b * Cdev + (b - R(a.bref[s])) * R(a.Cref[s])));
   n4 -= Q3 * n4;
-  R w1 = mc.w1[s], w0 = R(1) - R(4) * w1;
-  // even parts first, the large odd (advective) part added last
+  R w1 = mc.w1[s];
+  // even parts first, the large odd (advective) part added last; the rest
+  // population takes what the moving ones leave of n0 + src, so that the
+  // collision conserves C up to one local rounding (5 * 0.2 != 1 in binary:
+  // the scaled form would multiply every cell's C by the same factor at
+  // every step)
   R ev = n0 * R(0.2) + n3 * R(0.05) + w1 * srcv;
   R ex = ev + R(0.25) * n4, ey = ev - R(0.25) * n4;
-  o[0] = (n0 - n3) * R(0.2) + w0 * srcv;
   o[1] = ex + R(0.5) * n1;
   o[3] = ex - R(0.5) * n1;
   o[2] = ey + R(0.5) * n2;
   o[4] = ey - R(0.5) * n2;
+  o[0] = (n0 + srcv) - ((o[1] + o[3]) + (o[2] + o[4]));
 }
 
 }  // namespace pemlbm

@@ -192,6 +192,7 @@ k_balances(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
   if (!a.periodic) {
     for (int y = threadIdx.x; y < a.ny; y += blockDim.x) {
       for (int side = 0; side < 2; ++side) {
+        if (side ? a.halo_hi : a.halo_lo) continue;   // a slab side: no flow out of the lattice
         const int x = side ? a.nx - 1 : 0;
         const long long c = (long long)y * a.nxp + x;
         const uint8_t m = mask[c];

@@ -79,9 +79,34 @@ template <typename S> void launch_adj_seed_current(const void *src, const DevGeo
 // Advances the step counter that seeds stochastic 16-bit rounding.
 void launch_seed_advance(unsigned *ctr, cudaStream_t st);
 
-// Node mask from the geometry (solid may be NULL).
+// Material palette built on the device from per-cell fields in device
+// memory ([ny][nx] doubles; sigma may be NULL = 1): the distinct tuples in
+// row-major order of first occurrence into raw (at most max_pal), and every
+// fluid cell's entry into mid ([ny][nxp]; other cells 0).  The outcome is
+// left in *st (device memory): flags (kPal*), the smallest invalid cell
+// (row-major index) and the palette size.  scratch: palette_scratch_bytes.
+struct PalFields { const double *phi, *K, *aT, *DO2, *DH2O, *sigma; };
+struct PalStatus { int flags, bad_cell, claimed, npal; };
+enum { kPalInvalid = 1, kPalTooMany = 2, kPalCollision = 4 };
+constexpr int kPalTable = 1 << 18;   // hash slots: 4 x the largest palette
+size_t palette_scratch_bytes(int nx, int ny);
+cudaError_t launch_device_palette(const PalFields &f, const uint8_t *mask, int nx, int ny, int nxp,
+                                  uint16_t *mid, MatRaw *raw, int max_pal, void *scratch,
+                                  PalStatus *st, cudaStream_t s);
+
+// Node mask from the geometry (solid may be NULL): the domain is the x-slab
+// [x0, x0 + nx) of a lattice nxg wide, solid is [ny][nxg].
 void launch_build_mask(uint8_t *mask, const uint8_t *solid, int nx, int ny, int nxp, int ny_cl,
-                       int ny_gdl, int mode, int periodic, int closed, cudaStream_t st);
+                       int ny_gdl, int mode, int periodic, int closed, int x0, int nxg,
+                       cudaStream_t st);
+// One end of a halo copy: a lattice buffer (plane stride, row pitch, offset
+// of the column within a row: nx - 1 or 0 to read an edge column, -1 or nx
+// to write a ghost column) or a packed [6][ny] array (packed = 1).
+struct HaloSide { void *p; long long plane; int nxp; long long off; int packed; };
+// Copies the six populations that move +x (plus = 1) or -x (plus = 0) across
+// a slab side, for every row; element size esize (2, 4, 8).
+void launch_halo_copy(const HaloSide &src, const HaloSide &dst, int ny, int plus, int esize,
+                      cudaStream_t st);
 // Derived material coefficients of a palette (Eq. 7, 8, 10): R = double if
 // fp64 else float.
 void launch_prep_palette(void *pal, const MatRaw *raw, int npal, double nu, int forchheimer,

@@ -27,7 +27,8 @@ EXPORTS = ("lbm_create_domain", "lbm_destroy_domain", "lbm_set_params", "lbm_set
            "lbm_set_variant", "lbm_residual_noalloc", "lbm_balances", "lbm_step_observe",
            "lbm_create_batch", "lbm_destroy_batch",
            "lbm_batch_set_schedule", "lbm_batch_tune", "lbm_batch_step", "lbm_batch_time_steps",
-           "lbm_grad", "lbm_vjp", "lbm_last_error")
+           "lbm_grad", "lbm_vjp", "lbm_halo_exchange", "lbm_halo_pack", "lbm_halo_unpack",
+           "lbm_last_error")
 
 
 class LbmError(RuntimeError):
@@ -40,7 +41,8 @@ class lbm_domain_desc(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("ny_cl", C.c_int32),
                 ("ny_gdl", C.c_int32), ("reaction_mode", C.c_int32), ("periodic_x", C.c_int32),
                 ("closed_x", C.c_int32), ("precision", C.c_int32), ("rounding", C.c_int32),
-                ("solid", C.POINTER(C.c_uint8)), ("cuda_stream", C.c_void_p)]
+                ("solid", C.POINTER(C.c_uint8)), ("cuda_stream", C.c_void_p),
+                ("x_begin", C.c_int32), ("x_end", C.c_int32)]
 
 
 _PARAM_DOUBLES = ("nu", "u_in_avg", "body_force_x", "V_op", "T_in", "C_O2_in", "C_H2O_in",
@@ -54,7 +56,8 @@ class lbm_params(C.Structure):
         ("forchheimer", C.c_int32), ("top_dirichlet", C.c_int32),
         ("interface_mode", C.c_int32), ("inlet_mode", C.c_int32), ("dp_in", C.c_double),
         ("alpha_a", C.c_double), ("buoy_gx", C.c_double), ("buoy_gy", C.c_double),
-        ("T_buoy", C.c_double), ("wall_dirichlet", C.c_int32), ("C_wall", (C.c_double * 3) * 3)]
+        ("T_buoy", C.c_double), ("wall_dirichlet", C.c_int32), ("C_wall", (C.c_double * 3) * 3),
+        ("scalar_advection", C.c_int32)]
 
 
 _lib = None
@@ -73,7 +76,8 @@ def load_library(path: str = LIB_PATH):
         "lbm_create_domain": [C.POINTER(lbm_domain_desc), C.POINTER(P)],
         "lbm_destroy_domain": [P],
         "lbm_set_params": [P, C.POINTER(lbm_params)],
-        "lbm_set_fields": [P, d, d, d, d, d, d],
+        "lbm_set_fields": [P, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                           C.c_void_p, C.c_int32],
         "lbm_reset": [P],
         "lbm_step": [P, C.c_int64],
         "lbm_current_density": [P, d, d, C.POINTER(C.c_float)],
@@ -98,8 +102,12 @@ def load_library(path: str = LIB_PATH):
         "lbm_batch_tune": [P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), d],
         "lbm_batch_step": [P, C.c_int64],
         "lbm_batch_time_steps": [P, C.c_int64, d],
-        "lbm_grad": [P, C.c_int32, C.c_int64, C.c_int32, d, d, d, d, d],
+        "lbm_grad": [P, C.c_int32, C.c_int64, C.c_int32, d, C.c_void_p, C.c_void_p, C.c_void_p, d,
+                     C.c_int32],
         "lbm_vjp": [P, d, d, d, d, d, d],
+        "lbm_halo_exchange": [P, P],
+        "lbm_halo_pack": [P, C.c_int32, C.c_void_p],
+        "lbm_halo_unpack": [P, C.c_int32, C.c_void_p],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -152,18 +160,25 @@ class Domain:
     """One cathode lattice on the GPU (wraps an lbm_domain handle)."""
 
     def __init__(self, nx, ny, ny_cl=0, ny_gdl=0, reaction_mode=0, periodic_x=0,
-                 precision="fp32", solid=None, stream=None, rounding="nearest", closed_x=0):
-        """rounding: "nearest" or "stochastic" (16-bit storage only)."""
+                 precision="fp32", solid=None, stream=None, rounding="nearest", closed_x=0,
+                 x_begin=0, x_end=0):
+        """rounding: "nearest" or "stochastic" (16-bit storage only);
+        x_begin, x_end: the x-slab of the nx-column lattice this domain owns
+        (0, 0: all of it); nx, ny and solid describe the whole lattice."""
         self.L = load_library()
         self.nx, self.ny = int(nx), int(ny)
         self._solid = None if solid is None else np.ascontiguousarray(solid, np.uint8)
+        self.nx_lattice = self.nx
+        if x_end:
+            self.nx = int(x_end) - int(x_begin)
         desc = lbm_domain_desc(
-            nx=self.nx, ny=self.ny, ny_cl=int(ny_cl), ny_gdl=int(ny_gdl),
+            nx=self.nx_lattice, ny=self.ny, ny_cl=int(ny_cl), ny_gdl=int(ny_gdl),
             reaction_mode=int(reaction_mode), periodic_x=int(periodic_x), closed_x=int(closed_x),
             precision=PRECISION[precision] if isinstance(precision, str) else int(precision),
             rounding={"nearest": 0, "stochastic": 1}[rounding],
             solid=None if self._solid is None else self._solid.ctypes.data_as(C.POINTER(C.c_uint8)),
-            cuda_stream=None if stream is None else C.c_void_p(int(stream)))
+            cuda_stream=None if stream is None else C.c_void_p(int(stream)),
+            x_begin=int(x_begin), x_end=int(x_end))
         h = C.c_void_p()
         _check(self.L.lbm_create_domain(C.byref(desc), C.byref(h)))
         self.h = h
@@ -203,14 +218,28 @@ class Domain:
         _check(self.L.lbm_set_params(self.h, C.byref(lbm_params(**p))))
 
     def set_fields(self, phi, K, alpha_T, D_O2, D_H2O, rho_cp_ratio=None):
-        arrs = [np.ascontiguousarray(np.broadcast_to(np.asarray(a, np.float64), (self.ny, self.nx)))
-                for a in (phi, K, alpha_T, D_O2, D_H2O)]
-        sig = None
-        if rho_cp_ratio is not None:
-            sig = np.ascontiguousarray(np.broadcast_to(np.asarray(rho_cp_ratio, np.float64),
-                                                       (self.ny, self.nx)))
-        _check(self.L.lbm_set_fields(self.h, *[_dp(a) for a in arrs],
-                                     None if sig is None else _dp(sig)))
+        """Per-cell material.  Host values (arrays or scalars) are copied from
+        the host; if every given field is a CUDA tensor (float64, (ny, nx),
+        contiguous, on the domain's device) the library reads them in place
+        on the domain's stream and builds the palette on the device.  An
+        x-slab takes the whole lattice's host arrays."""
+        given = [a for a in (phi, K, alpha_T, D_O2, D_H2O, rho_cp_ratio) if a is not None]
+        if all(getattr(a, "is_cuda", False) for a in given):
+            for name, a in zip(("phi", "K", "alpha_T", "D_O2", "D_H2O", "rho_cp_ratio"),
+                               (phi, K, alpha_T, D_O2, D_H2O, rho_cp_ratio)):
+                if a is not None:
+                    check_device_buffer(a, "float64", (self.ny, self.nx), self.device, name)
+            ptr = lambda a: None if a is None else C.c_void_p(a.data_ptr())  # noqa: E731
+            _check(self.L.lbm_set_fields(self.h, ptr(phi), ptr(K), ptr(alpha_T), ptr(D_O2),
+                                         ptr(D_H2O), ptr(rho_cp_ratio), 1))
+            return
+        shape = (self.ny, self.nx_lattice)
+        host = lambda a: np.ascontiguousarray(  # noqa: E731
+            np.broadcast_to(np.asarray(a.cpu() if hasattr(a, "cpu") else a, np.float64), shape))
+        arrs = [host(a) for a in (phi, K, alpha_T, D_O2, D_H2O)]
+        sig = None if rho_cp_ratio is None else host(rho_cp_ratio)
+        _check(self.L.lbm_set_fields(self.h, *[a.ctypes.data_as(C.c_void_p) for a in arrs],
+                                     None if sig is None else sig.ctypes.data_as(C.c_void_p), 0))
 
     def reset(self):
         _check(self.L.lbm_reset(self.h))
@@ -278,15 +307,26 @@ class Domain:
         _check(self.L.lbm_residual_noalloc(self.h, C.c_void_p(snapshot.data_ptr()), C.byref(r)))
         return r.value
 
-    def grad(self, objective: int = 0, nsteps: int = 100, segment: int = 0):
+    def grad(self, objective: int = 0, nsteps: int = 100, segment: int = 0, out=None):
         """Objective after nsteps from the current state and its gradient:
         (J, {"phi", "K", "D_O2": [ny][nx] arrays, "u_in": float}); "u_in" is
         the derivative by the inlet drive, u_in_avg (inlet_mode 0) or dp_in
-        (inlet_mode 1)."""
+        (inlet_mode 1).  With ``out`` (a dict of CUDA float64 tensors of shape
+        (ny, nx) under "phi", "K", "D_O2") the gradients are written there on
+        the domain's stream instead of to host arrays."""
         J, du = C.c_double(), C.c_double()
-        g = {k: np.zeros((self.ny, self.nx)) for k in ("phi", "K", "D_O2")}
+        keys = ("phi", "K", "D_O2")
+        if out is not None:
+            for k in keys:
+                check_device_buffer(out[k], "float64", (self.ny, self.nx), self.device, "d" + k)
+            ptrs = [C.c_void_p(out[k].data_ptr()) for k in keys]
+            g, on_device = dict(out), 1
+        else:
+            g = {k: np.zeros((self.ny, self.nx)) for k in keys}
+            ptrs = [g[k].ctypes.data_as(C.c_void_p) for k in keys]
+            on_device = 0
         _check(self.L.lbm_grad(self.h, int(objective), int(nsteps), int(segment), C.byref(J),
-                               _dp(g["phi"]), _dp(g["K"]), _dp(g["D_O2"]), C.byref(du)))
+                               *ptrs, C.byref(du), on_device))
         g["u_in"] = du.value
         return J.value, g
 
@@ -415,14 +455,29 @@ def cathode_objective():
             p = dict(params)
             p["dp_in" if p.get("inlet_mode", 0) == 1 else "u_in_avg"] = float(u_in)
             domain.set_params(p)
-            domain.set_fields(phi.detach().cpu().double().numpy(), K.detach().cpu().double().numpy(),
-                              fields["alpha_T"], D_O2.detach().cpu().double().numpy(),
-                              fields["D_H2O"], fields.get("rho_cp_ratio"))
-            domain.reset()
-            J, g = domain.grad(objective, nsteps, segment)
             dev = phi.device
-            ctx.save_for_backward(torch.from_numpy(g["phi"]).to(dev), torch.from_numpy(g["K"]).to(dev),
-                                  torch.from_numpy(g["D_O2"]).to(dev),
+            if phi.is_cuda:
+                # CUDA tensors stay on the device: the library reads the
+                # material in place and writes the gradients into tensors
+                # allocated here, all on the domain's stream
+                on = lambda a: torch.as_tensor(a, dtype=torch.float64, device=dev).contiguous()  # noqa: E731
+                sig = fields.get("rho_cp_ratio")
+                domain.set_fields(phi.detach().contiguous(), K.detach().contiguous(),
+                                  on(fields["alpha_T"]), D_O2.detach().contiguous(),
+                                  on(fields["D_H2O"]), None if sig is None else on(sig))
+                domain.reset()
+                out = {k: torch.empty((domain.ny, domain.nx), dtype=torch.float64, device=dev)
+                       for k in ("phi", "K", "D_O2")}
+                J, g = domain.grad(objective, nsteps, segment, out=out)
+                gphi, gK, gD = g["phi"], g["K"], g["D_O2"]
+            else:
+                domain.set_fields(phi.detach().double().numpy(), K.detach().double().numpy(),
+                                  fields["alpha_T"], D_O2.detach().double().numpy(),
+                                  fields["D_H2O"], fields.get("rho_cp_ratio"))
+                domain.reset()
+                J, g = domain.grad(objective, nsteps, segment)
+                gphi, gK, gD = (torch.from_numpy(g[k]) for k in ("phi", "K", "D_O2"))
+            ctx.save_for_backward(gphi, gK, gD,
                                   torch.tensor(g["u_in"], dtype=torch.float64, device=dev))
             return torch.tensor(J, dtype=torch.float64, device=dev)
 

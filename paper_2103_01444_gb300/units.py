@@ -85,6 +85,9 @@ def cathode_params(case: dict, forchheimer: int = 1, interface_mode: int = 0):
         # kinetics: Tafel (Eq. 13) unless an anodic transfer coefficient is
         # given for the Butler-Volmer branch
         alpha_a=float(case.get("alpha_a", 0.0)),
+        # advective flux of the scalars in Eq. 10: u C as printed (0) or
+        # relative to the inlet values, u (C - C_in) (1)
+        scalar_advection=int(case.get("scalar_advection", 0)),
     )
     geometry = dict(nx=nx, ny=ny, ny_cl=ny_cl, ny_gdl=ny_gdl,
                     reaction_mode=int(case["reaction_mode"]),
@@ -110,7 +113,7 @@ def _lattice_base(nx, ny, forchheimer, interface_mode, **kw):
              x_ref=1.0, dx_cm=1.0, dt_s=1.0, delta_cl_cm=1.0, c_tot=1.0, rho_cp_f=1.0,
              forchheimer=forchheimer, top_dirichlet=0, interface_mode=interface_mode,
              inlet_mode=0, dp_in=0.0, alpha_a=0.0, buoy_gx=0.0, buoy_gy=0.0, T_buoy=343.0,
-             wall_dirichlet=0, C_wall=[[0.0] * 3 for _ in range(3)])
+             wall_dirichlet=0, C_wall=[[0.0] * 3 for _ in range(3)], scalar_advection=0)
     p.update(kw)
     return p
 
@@ -127,6 +130,7 @@ def validation_params(case: dict, forchheimer: int = 1, interface_mode: int = 0)
       kang: k = Da D / ny on the bottom film, C0 held on the left wall."""
     nx, ny = int(case["nx"]), int(case["ny"])
     full = lambda v: np.full((ny, nx), float(v))  # noqa: E731
+    sa = int(case.get("scalar_advection", 0))
     if case["kind"] == "cavity":
         L = float(nx)
         dT = case["T_hot"] - case["T_cold"]
@@ -143,7 +147,7 @@ def validation_params(case: dict, forchheimer: int = 1, interface_mode: int = 0)
                 [case["T_hot"], 0.21, 0.0]]
         params = _lattice_base(nx, ny, forchheimer, interface_mode, nu=nu, T_in=Tm, T_top=Tm,
                                buoy_gy=case["Ra"] * nu * alpha / (dT * L ** 3), T_buoy=Tm,
-                               wall_dirichlet=bits, C_wall=wall)
+                               wall_dirichlet=bits, C_wall=wall, scalar_advection=sa)
         geometry = dict(nx=nx, ny=ny, ny_cl=0, ny_gdl=ny if porous else 0, reaction_mode=0,
                         periodic_x=0, closed_x=1, solid=None)
         return params, fields, geometry
@@ -154,7 +158,8 @@ def validation_params(case: dict, forchheimer: int = 1, interface_mode: int = 0)
         params = _lattice_base(nx, ny, forchheimer, interface_mode, C_O2_in=case["C0"],
                                C_O2_top=case["C0"], aj0_ref=case["Da"] * D / ny,
                                wall_dirichlet=0b111, C_wall=[[343.0, case["C0"], 0.0],
-                                                             [0.0] * 3, [0.0] * 3])
+                                                             [0.0] * 3, [0.0] * 3],
+                               scalar_advection=sa)
         geometry = dict(nx=nx, ny=ny, ny_cl=0, ny_gdl=0, reaction_mode=0, periodic_x=0,
                         closed_x=1, solid=None)
         return params, fields, geometry

@@ -145,3 +145,55 @@ def test_pressure_sweep_batched(schedule):
     # the flow rate grows with the pressure difference
     q = [float(d.fields()["ux"][:, d.nx // 2].sum()) for d in ds[:3]]
     assert 0 < q[0] < q[1] < q[2]
+
+
+def oracle_sweep():
+    """Five uneven cases of an operating-point sweep (Sec. 5) that differ in
+    more than the voltage: thin film, volumetric catalyst, pressure drive,
+    Butler-Volmer kinetics, pore-scale grains, scalars advected relative to
+    their inlet values; interface modes alternate."""
+    base = cases()
+    sweep = [dict(base[0]),
+             dict(base[1], inlet="pressure", dp_in=8e-4),
+             dict(base[2], alpha_a=0.5, V_op=1.0),
+             workloads.small_cathode(nx=70, ny=24, reaction_mode=0, grains=True, seed=9,
+                                     V_op=0.45),
+             dict(base[4], scalar_advection=1)]
+    return [(c, k % 2) for k, c in enumerate(sweep)]
+
+
+@pytest.fixture(scope="module")
+def sweep_oracles():
+    from oracle import Oracle
+    from oracle.params import lattice_problem
+    out = []
+    for c, mode in oracle_sweep():
+        params, material, solid = lattice_problem(c, interface_mode=mode)
+        out.append(Oracle(params, material, solid).step(151))
+    return out
+
+
+@pytest.mark.parametrize("schedule", ["graph", "persistent", "per-case", "concurrent"])
+def test_batched_fp64_states_match_the_oracle(schedule, sweep_oracles):
+    """FP64 storage: after 151 batched steps every population of every case
+    agrees with the FP64 oracle's own stepping of that case to round-off
+    (1e-11 of each plane's scale), and so does its current density."""
+    from paper_2103_01444_gb300.build import build
+    from paper_2103_01444_gb300.lbm import Batch, Domain
+    build()
+    ds = [Domain.from_case(c, precision="fp64", interface_mode=m) for c, m in oracle_sweep()]
+    b = Batch(ds)
+    b.set_schedule(schedule, variant=6)
+    b.step(150)
+    b.step(1)
+    for d, o in zip(ds, sweep_oracles):
+        live = (o.mask & 3) != 3
+        st = d.state()
+        ref = np.concatenate([o.f, o.g.reshape(15, o.ny, o.nx)], axis=0)
+        for q in range(24):
+            scale = np.abs(ref[q][live]).max()
+            np.testing.assert_allclose(st[q][live], ref[q][live], rtol=0, atol=1e-11 * scale,
+                                       err_msg=f"plane {q}")
+        i_g = d.current_density()[0]
+        i_o = o.current_density()[0]
+        assert i_g == pytest.approx(i_o, rel=1e-11)

@@ -81,14 +81,17 @@ def test_initial_state(name):
     np.testing.assert_allclose(st[:, live], ref[:, live], rtol=1e-14, atol=1e-14)
 
 
+@pytest.mark.parametrize("sa", [0, 1])
 @pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("name,steps", [("film-64x16", 300), ("vol-77x20", 300),
                                         ("grains-70x24", 300), ("blocks-300x64", 120)])
-def test_fp64_state_matches_oracle(name, steps, mode):
+def test_fp64_state_matches_oracle(name, steps, mode, sa):
     """FP64 storage: every population agrees with the oracle to round-off,
-    in both interface modes of Eq. 10."""
+    in both interface modes of Eq. 10 and with the scalars advected as
+    printed (sa 0) or relative to their inlet values (sa 1)."""
     case = CASES[name]()
     case["V_op"] = 0.4   # strong reaction: exercises the implicit Tafel links
+    case["scalar_advection"] = sa
     d = gpu_domain(case, "fp64", interface_mode=mode)
     o = oracle_of(case, interface_mode=mode)
     d.step(steps)
@@ -295,6 +298,60 @@ def test_cathode_200x40_fp32_after_5000_steps(cathode_200x40_oracles, mode):
     assert not bad, (e, tol)
 
 
+@pytest.mark.xfail(reason="Eq. 10's flux u T with T near 343 K: FP32 rounding of u T, amplified "
+                          "by the Tafel-Arrhenius rate, leaves the current about 2.5e-4 off",
+                   strict=False)
+@pytest.mark.parametrize("mode", [0, 1])
+def test_cathode_200x40_fp32_printed_advection_within_1e5(cathode_200x40_oracles, mode):
+    """The 1e-5 target on every field and the current with the advective
+    flux u C exactly as printed in Eq. 10 (kept visible: not met)."""
+    case, oracles = cathode_200x40_oracles
+    d = gpu_domain(case, "fp32", interface_mode=mode)
+    d.step(case["steps"])
+    e = errors_vs_oracle(d, oracles[mode])
+    e.pop("i(x)")
+    assert max(e.values()) < 1e-5, e
+
+
+@pytest.fixture(scope="module")
+def cathode_200x40_relative_oracles():
+    case = dict(workloads.cathode_200x40(), scalar_advection=1)
+    out = {}
+    for mode in (0, 1):
+        o = oracle_of(case, interface_mode=mode)
+        o.step(case["steps"])
+        out[mode] = o
+    return case, out
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_cathode_200x40_relative_advection_fp64_and_fp32(cathode_200x40_relative_oracles, mode):
+    """The 200 x 40 cathode with the scalars advected relative to their
+    inlet values, after 5000 steps: FP64 within 1e-9 of the oracle.  FP32
+    with Fickian interfaces: within relative L2 1e-5 on u, T, C_O2, C_H2O,
+    the mean current density and the heat.  With Eq. 10's per-cell b
+    (alpha C continuous, the GDL between about 60 K and 25 T_in) u, T and
+    C_O2 hold 1e-5 and the reaction-integrated quantities the bound of the
+    temperature-sensitive Tafel rate (fp32_reaction_bound)."""
+    case, oracles = cathode_200x40_relative_oracles
+    o = oracles[mode]
+    d = gpu_domain(case, "fp64", interface_mode=mode)
+    d.step(case["steps"])
+    e = errors_vs_oracle(d, o)
+    assert e.pop("i(x)") < 2e-7
+    assert max(e.values()) < 1e-9, e
+    d = gpu_domain(case, "fp32", interface_mode=mode)
+    d.step(case["steps"])
+    e = errors_vs_oracle(d, o)
+    e.pop("i(x)")                   # float32 profile: its own rounding
+    if mode == 1:
+        assert max(e.values()) < 1e-5, e
+    else:
+        bound = fp32_reaction_bound(o, case["steps"])
+        tol = {k: (1e-5 if k in FIELDS else bound) for k in e}
+        assert all(e[k] < tol[k] for k in e), (e, tol)
+
+
 def test_fp32_volumetric_and_grains_short_runs():
     for name, steps in (("vol-77x20", 1500), ("grains-70x24", 1500)):
         for mode in (0, 1):
@@ -369,6 +426,23 @@ def test_save_load_roundtrip():
     assert b.steps == 37
     b.step(20)
     np.testing.assert_array_equal(b.state(), ref)
+
+
+@pytest.mark.parametrize("name,mode", [("film-64x16", 0), ("vol-77x20", 1), ("grains-70x24", 1)])
+def test_fp64_residual_matches_oracle(name, mode):
+    """The steady-state residual (max over j_x, j_y, T - T_in, C_O2, C_H2O
+    of ||X - X_prev|| / ||X||, each call against the previous one, the first
+    against the reset state) equals the FP64 oracle's call after call."""
+    case = dict(CASES[name](), V_op=0.45)
+    d = gpu_domain(case, "fp64", interface_mode=mode)
+    o = oracle_of(case, interface_mode=mode)
+    for n in (1, 40, 100, 100, 7):
+        d.step(n)
+        o.step(n)
+        r_g, r_o = d.residual(), o.residual()
+        assert r_o > 0
+        assert r_g == pytest.approx(r_o, rel=1e-12), n
+    assert d.residual() == o.residual() == 0.0
 
 
 def test_residual_decreases_and_detects_divergence():
@@ -476,3 +550,53 @@ def test_step_observe_reports_every_step():
         assert ha[k] == pytest.approx(h_o, rel=1e-11)
     assert a.L.lbm_step_observe(a.h, 5, None, None) == 1     # EINVAL: nothing to observe
     assert a.L.lbm_step_observe(a.h, -1, None, None) == 1
+
+
+@pytest.mark.parametrize("name", ["grains-70x24", "blocks-300x64"])
+def test_device_material_gives_the_host_palette(name):
+    """lbm_set_fields with the material in device memory (the palette built
+    by kernels) steps bit for bit like the host-built palette, solids and
+    block materials included."""
+    import torch
+    from paper_2103_01444_gb300.units import cathode_params
+    case = CASES[name]()
+    params, fields, _ = cathode_params(case, interface_mode=1)
+    a = gpu_domain(case, "fp32", interface_mode=1)
+    b = gpu_domain(case, "fp32", interface_mode=1)
+    dev = {k: torch.as_tensor(v, dtype=torch.float64, device="cuda").contiguous()
+           for k, v in fields.items()}
+    b.set_fields(**dev)
+    b.reset()
+    a.step(60)
+    b.step(60)
+    np.testing.assert_array_equal(a.state(), b.state())
+
+
+def test_device_material_refusals_keep_the_previous_material():
+    """Invalid device material (a porosity above 1, more than 65535 distinct
+    tuples) is refused with EINVAL and leaves the domain as it was."""
+    import torch
+    from paper_2103_01444_gb300.lbm import LbmError
+    from paper_2103_01444_gb300.units import cathode_params
+    case = CASES["blocks-300x64"]()
+    params, fields, _ = cathode_params(case, interface_mode=1)
+    d = gpu_domain(case, "fp32", interface_mode=1)
+    ref = gpu_domain(case, "fp32", interface_mode=1)
+    dev = {k: torch.as_tensor(v, dtype=torch.float64, device="cuda").contiguous()
+           for k, v in fields.items()}
+    bad = dict(dev, phi=dev["phi"].clone())
+    bad["phi"][40, 123] = 1.5
+    with pytest.raises(LbmError, match=r"EINVAL.*porosity 1.5 at \(123,40\)"):
+        d.set_fields(**bad)
+    big_case = workloads.cathode_blocks(nx=320, ny=256)      # 81920 cells
+    _, big_fields, _ = cathode_params(big_case, interface_mode=1)
+    big = gpu_domain(big_case, "fp32", interface_mode=1)
+    many = {k: torch.as_tensor(v, dtype=torch.float64, device="cuda").contiguous()
+            for k, v in big_fields.items()}
+    many["phi"] = 0.4 + 0.5 * torch.rand((big.ny, big.nx), dtype=torch.float64, device="cuda")
+    with pytest.raises(LbmError, match="EINVAL.*65535"):
+        big.set_fields(**many)
+    d.reset()
+    d.step(40)
+    ref.step(40)
+    np.testing.assert_array_equal(d.state(), ref.state())
