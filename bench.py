@@ -60,8 +60,14 @@ def parse():
                          "kang: the validation set-ups of Sec. 3 (2048x2048 cavities at "
                          "Ra 1e6, clear with a heated bottom or porous with Da 1e-2; "
                          "a 4096x1024 surface-reaction box), their own line")
-    ap.add_argument("--interface", type=int, default=0, choices=[0, 1],
-                    help="0: Eq. 10 as printed (per-cell b); 1: Fickian interfaces")
+    ap.add_argument("--interface", type=int, default=1, choices=[0, 1],
+                    help="0: Eq. 10 as printed (per-cell b, alpha C continuous across the "
+                         "GDL/channel interface); 1: Fickian interfaces (the default)")
+    ap.add_argument("--advection", default="relative", choices=["printed", "relative"],
+                    help="flux moments of the D2Q5 equilibria: u C as printed in Eq. 10, or "
+                         "u (C - C_in) relative to the inlet values (the default)")
+    ap.add_argument("--residual-every", type=int, default=128,
+                    help="steps between the residual checks inside the timed region")
     ap.add_argument("--inlet", default="velocity", choices=["velocity", "pressure"],
                     help="drive of the flow: parabolic inlet velocity at Re, or the pressure "
                          "difference of Sec. 4 (--dp-in, lattice units)")
@@ -126,6 +132,8 @@ def workload(args):
         case = workloads.cathode_blocks(nx=args.nx, ny=args.ny)
     if getattr(args, "inlet", "velocity") == "pressure":
         case = dict(case, inlet="pressure", dp_in=args.dp_in)
+    if getattr(args, "advection", "printed") == "relative":
+        case = dict(case, scalar_advection=1)
     return case
 
 
@@ -241,12 +249,12 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def cpu_baseline(case, seconds_target=15.0):
+def cpu_baseline(case, seconds_target=15.0, interface_mode=0):
     """The FP64 oracle as it stands, on the host cores, over a bounded number
     of steps of the same workload; returns (MLUPS, cores, sample text)."""
     from oracle import Oracle
     from oracle.params import lattice_problem
-    params, material, solid = lattice_problem(case)
+    params, material, solid = lattice_problem(case, interface_mode=interface_mode)
     o = Oracle(params, material, solid)
     cells = case["nx"] * case["ny"]
     t0 = time.perf_counter()
@@ -316,7 +324,9 @@ def reference_sample(args, budget_s=90.0):
     total = max(args.warmup, 3) + max(args.steps, 1)
     while True:
         case = workloads.cathode_blocks(nx=nx, ny=ny)
-        params, material, solid = lattice_problem(case)
+        if args.advection == "relative":
+            case = dict(case, scalar_advection=1)
+        params, material, solid = lattice_problem(case, interface_mode=args.interface)
         o = Oracle(params, material, solid)
         t0 = time.perf_counter()
         o.step(1)
@@ -346,7 +356,10 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": f"cathode-{args.nx}x{args.ny}-blocks",
-                       "sample_nx": case["nx"], "sample_ny": case["ny"], "storage": "fp64"},
+                       "sample_nx": case["nx"], "sample_ny": case["ny"], "storage": "fp64",
+                       "interface_mode": args.interface,
+                       "scalar_advection": ("u (C - C_in)" if args.advection == "relative"
+                                            else "u C (Eq. 10 as printed)")},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -378,7 +391,7 @@ def run_ours(args):
     barrier(pg, dev)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        ms = d.time_steps(K)          # CUDA events on the domain's stream
+        ms, launches = timed_steps(d, K, stream, args.residual_every)
     torch.cuda.synchronize()
     barrier(pg, dev)
     ms_max = max_over_ranks(ms, pg, dev)
@@ -416,6 +429,8 @@ def run_ours(args):
                    "reaction": ("volumetric catalyst rows" if case["reaction_mode"] == 1
                                 else "thin catalyst film"),
                    "interface_mode": args.interface,
+                   "scalar_advection": ("u (C - C_in)" if case.get("scalar_advection")
+                                        else "u C (Eq. 10 as printed)"),
                    "step_variant": variant,
                    "V_op": case["V_op"],
                    "inlet": (f"pressure, dp_in {case['dp_in']:g}" if case.get("inlet") == "pressure"
@@ -425,7 +440,10 @@ def run_ours(args):
                      "frac": achieved / peak, "traffic": traffic_from_profiles(),
                      "peak_source": peak_kind, "bytes_per_cell": bpc,
                      "kernel": "k_step (coupled collide+stream)"},
-        "gpu_launches": K,
+        "gpu_launches": launches,
+        "step": ("coupled update of every cell (a1-a7) with the per-step current-density and "
+                 f"heat reduction copied to the host (a8), and the residual every "
+                 f"{args.residual_every} steps"),
         "clocks": clocks,
         "state_check": {"i_avg_A_cm2": i_avg, "heat_W_cm2": heat, "residual": res},
     }
@@ -436,17 +454,46 @@ def run_ours(args):
     if not args.no_adjoint and args.workload == "blocks":
         line["adjoint"] = adjoint_ratio(args, stream)
     if world == 1 and not args.no_cpu_baseline:
-        v, cores, sample = cpu_baseline(case)
+        v, cores, sample = cpu_baseline(case, interface_mode=args.interface)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": sample, "other_samples": cpu_baseline_extra()}
     print(json.dumps(line), flush=True)
+
+
+def timed_steps(d, K, stream, residual_every):
+    """K steps of the whole hot path, timed with CUDA events on the domain's
+    stream: each step's coupled update, its current-density and heat
+    reduction copied to pinned host memory as the step completes
+    (lbm_step_observe), and the steady-state residual every residual_every
+    steps.  Returns (ms, kernel launches)."""
+    import torch
+    i_buf = torch.zeros(K, dtype=torch.float64).pin_memory().numpy()
+    h_buf = torch.zeros(K, dtype=torch.float64).pin_memory().numpy()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    done, checks = 0, 0
+    while done < K:
+        n = min(residual_every, K - done)
+        d.step_observe(n, i_buf[done:done + n], h_buf[done:done + n])
+        done += n
+        if n == residual_every:
+            d.residual()
+            checks += 1
+    e1.record(stream)
+    e1.synchronize()
+    assert np.isfinite(i_buf).all()
+    # per step: the step kernel, the catalyst reduction and its column sum;
+    # per check: the residual kernel and its block sum
+    return e0.elapsed_time(e1), 3 * K + 2 * checks
 
 
 def sweep_run(cases, args, stream):
     """Cases x steps per second for the tuned batched schedule, for one
     launch per case and step (same kernel, no graph), and their ratio."""
     from paper_2103_01444_gb300.lbm import Batch, Domain
-    doms = [Domain.from_case(c, precision=args.precision, stream=stream.cuda_stream)
+    sa = 1 if args.advection == "relative" else 0
+    doms = [Domain.from_case(dict(c, scalar_advection=sa), precision=args.precision,
+                             stream=stream.cuda_stream, interface_mode=args.interface)
             for c in cases]
     cells = sum(c["nx"] * c["ny"] for c in cases)
     b = Batch(doms)
@@ -497,7 +544,10 @@ def adjoint_ratio(args, stream):
     import torch
     from paper_2103_01444_gb300.lbm import Domain
     case = workloads.cathode_blocks(nx=1024, ny=256, seed=4)
-    d = Domain.from_case(case, precision=args.precision, stream=stream.cuda_stream)
+    if args.advection == "relative":
+        case = dict(case, scalar_advection=1)
+    d = Domain.from_case(case, precision=args.precision, stream=stream.cuda_stream,
+                         interface_mode=args.interface)
     d.tune(10)
     N = args.adjoint_steps
     d.step(20)
@@ -530,13 +580,18 @@ def end_to_end(case, precision, K, stream, interface_mode=0):
     from paper_2103_01444_gb300.units import cathode_params
     from paper_2103_01444_gb300.lbm import Domain
     params, fields, geo = cathode_params(case, interface_mode=interface_mode)
-    pinned = {k: torch.from_numpy(v).pin_memory().numpy() for k, v in fields.items()}
+    pinned = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in fields.items()}
     cells = case["nx"] * case["ny"]
     d = Domain(precision=precision, stream=stream.cuda_stream, **geo)
     d.set_params(params)
+    fields_host = torch.empty((6, case["ny"], case["nx"]), dtype=torch.float64).pin_memory()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    d.set_fields(**pinned)
+    # the material goes up as six copies from pinned memory; the library
+    # builds the palette from them on the device (lbm_set_fields, on_device)
+    with torch.cuda.stream(stream):
+        dev = {k: v.to("cuda", non_blocking=True) for k, v in pinned.items()}
+    d.set_fields(**dev)
     d.reset()
     torch.cuda.synchronize()
     t1 = time.perf_counter()
@@ -546,20 +601,24 @@ def end_to_end(case, precision, K, stream, interface_mode=0):
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     assert np.isfinite(i_avg).all() and i_avg[-1] > 0
-    out = d.fields()
-    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        out = torch.empty((6, case["ny"], case["nx"]), dtype=torch.float64, device="cuda")
+        d.fields(out=out)                 # written on the domain's stream
+        fields_host.copy_(out, non_blocking=True)
+    stream.synchronize()
     t3 = time.perf_counter()
     dt = t3 - t0
-    assert np.isfinite(out["T"]).all()
-    h2d = 5 * 8 * cells + 2 * cells   # material arrays + palette indices
+    assert torch.isfinite(fields_host[3]).all()
+    h2d = 6 * 8 * cells                   # the six material arrays
     d2h = K * 2 * 8 + 6 * 8 * cells
     d.close()
     return {"seconds": dt, "unit": UNIT,
             "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
             "breakdown_s": {"upload_and_reset": t1 - t0, "steps_with_reads": t2 - t1,
                             "fields_read": t3 - t2},
-            "includes": "material upload, reset, per-step current-density and heat copy to the "
-                        "host (lbm_step_observe), final fields read"}
+            "includes": "material upload from pinned memory (palette built on the device), "
+                        "reset, per-step current-density and heat copy to the host "
+                        "(lbm_step_observe), final fields read into pinned memory"}
 
 
 def run_cavity_study(args):
@@ -787,10 +846,13 @@ def run_validation(args):
                      "bytes_per_cell": bpc,
                      "kernel": "k_step, extended instantiation (" +
                                ("128 x 2" if variant <= 2 else "64 x 2") + " threads per block)"},
-        "gpu_launches": K, "clocks": clk.summary(), "state_check": state,
+        "gpu_launches": launches,
+        "step": ("coupled update of every cell (a1-a7) with the per-step current-density and "
+                 f"heat reduction copied to the host (a8), and the residual every "
+                 f"{args.residual_every} steps"), "clocks": clk.summary(), "state_check": state,
     }
     if world == 1 and not args.no_cpu_baseline:
-        v, cores, sample = cpu_baseline(case)
+        v, cores, sample = cpu_baseline(case, interface_mode=args.interface)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": sample}
     print(json.dumps(line), flush=True)
