@@ -216,32 +216,34 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def traffic_from_profiles(name="k_step_cathode-4096x1024-fp32.json"):
+def traffic_from_profiles(workload="cathode-4096x1024", precision="fp32"):
     """DRAM bytes per launch of the step kernel from the committed ncu
-    summary of a workload, if one exists for the current kernel."""
-    path = os.path.join(ROOT, "profiles", name)
+    summary of a workload and storage, if one exists for the current kernel."""
+    path = os.path.join(ROOT, "profiles", f"k_step_{workload}-{precision}.json")
     if os.path.exists(path):
         try:
             j = json.load(open(path))
-            if j.get("kernel_source_hash") == kernel_source_hash():
+            if j.get("kernel_source_hash") == kernel_source_hash(precision):
                 return float(j["dram_bytes_per_launch"])
         except Exception:
             pass
     return None
 
 
-STEP_SOURCES = ("lbm_core.cuh", "lbm_step.cuh", "kernels_f32.cu")
+STEP_SOURCES = ("lbm_core.cuh", "lbm_step.cuh")
+STORAGE_UNIT = {"fp32": "kernels_f32.cu", "fp64": "kernels_f64.cu", "bf16": "kernels_bf16.cu",
+                "fp16": "kernels_fp16.cu"}
 
 
-def kernel_source_hash():
-    """Hash of the sources that make the FP32 step kernel (its device code,
-    its launcher and its launch shapes): a committed DRAM count is used only
-    while these are unchanged."""
+def kernel_source_hash(precision="fp32"):
+    """Hash of the sources that make the step kernel of one storage type (its
+    device code, its launcher and its launch shapes): a committed DRAM count
+    is used only while these are unchanged."""
     import hashlib
     import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2103_01444_gb300", "csrc")
-    for name in STEP_SOURCES:
+    for name in STEP_SOURCES + (STORAGE_UNIT[precision],):
         h.update(open(os.path.join(csrc, name), "rb").read())
     launch = open(os.path.join(csrc, "lbm_launch.h")).read()
     shapes = re.search(r"kStepShapes\[kStepVariants\] = \{[^;]*;", launch)
@@ -437,7 +439,10 @@ def run_ours(args):
                              else f"velocity, Re {case['Re']:g}"),
                    "T_in": case["T_in"]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic_from_profiles(),
+                     "frac": achieved / peak,
+                     "traffic": (traffic_from_profiles(precision=args.precision)
+                                 if args.workload == "blocks" and (args.nx, args.ny) == (NX, NY)
+                                 else None),
                      "peak_source": peak_kind, "bytes_per_cell": bpc,
                      "kernel": "k_step (coupled collide+stream)"},
         "gpu_launches": launches,

@@ -221,3 +221,43 @@ def test_stochastic_rounding_picks_a_neighbour_without_bias(precision):
     # each draw's offset has variance p(1 - p) <= 1/4; the mean of n K draws
     # is within 6 sigma of zero
     assert abs(frac.mean()) < 6 * 0.5 / np.sqrt(K * frac.size), frac.mean()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_fp32_collision_conserves_scalar_totals(mode):
+    """A closed periodic box at rest with no reaction: every scalar total is
+    conserved exactly by the step (the D2Q5 collision conserves C, the walls
+    bounce back).  In FP32 it may change only by local rounding: the rest
+    population closes each cell's sum, so no step multiplies the totals by a
+    common factor (5 fl(0.2) = 1 + 1.5e-8 would give a drift of 3e-5 of the
+    deviation total over these 2000 steps).  What remains is the rounding of
+    the stored deviations: with Eq. 10's per-cell b (mode 0) the GDL's
+    temperature populations sit about 10 K from their references and drift
+    by 3e-6 of the total; Fickian interfaces keep them near zero (below
+    1e-6)."""
+    from paper_2103_01444_gb300 import workloads
+    case = dict(workloads.small_cathode(nx=96, ny=32, reaction_mode=0, seed=3), periodic_x=1)
+    d = _domain(case, "fp32", mode)
+    p = dict(d.params, aj0_ref=0.0)
+    d.set_params(p)
+    d.reset()
+    st = d.state()
+    ny, nx = st.shape[1:]
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    bump = 1.0 + 0.3 * (1.0 + np.sin(2 * np.pi * xx / nx) * np.cos(np.pi * yy / ny))
+    st[9:24] *= bump                      # T, O2 and H2O raised by up to 60 %
+    st[19:24] += 0.02 * st[14:19] * bump  # and water where there was none
+    d.set_state(st)
+    refs = (p["T_in"], p["C_O2_in"], p["C_H2O_in"])
+    live = (d.mask() & 3) != 3
+
+    def deviation_totals():
+        f = d.fields()
+        return [float((f[k] - r)[live].sum()) for k, r in zip(("T", "C_O2", "C_H2O"), refs)]
+
+    d.step(1)
+    t0 = deviation_totals()
+    d.step(2000)
+    t1 = deviation_totals()
+    for a, b in zip(t0, t1):
+        assert abs(b - a) <= 1e-5 * abs(a), (t0, t1)
