@@ -280,9 +280,14 @@ lbm_status lbm_get_mask(lbm_domain *d, uint8_t *mask_host);
 lbm_status lbm_get_step(lbm_domain *d, int64_t *steps);
 
 /* Checkpoint of the state: with buf == NULL, *bytes receives the size; else
- * writes a header (sizes, precision, step) and the raw populations of both
- * buffers.  lbm_load_state restores a blob taken from a domain of the same
- * geometry and precision (EINVAL otherwise). */
+ * writes an 80-byte header (sizes, precision, step) and the raw populations
+ * of both buffers in the storage layout of the step: per buffer, five planes
+ * of 4-value groups (link i = 0..4 of the flow, T, O2 and H2O, in that order,
+ * for every cell) followed by the four planes of flow links 5-8; a plane
+ * holds ny rows of the padded row length, x fastest, and every value is a
+ * deviation from its direction's reference.  lbm_load_state restores a blob
+ * taken from a domain of the same geometry and precision (EINVAL otherwise,
+ * and for blobs of an earlier storage layout). */
 lbm_status lbm_save_state(lbm_domain *d, void *buf, size_t *bytes);
 lbm_status lbm_load_state(lbm_domain *d, const void *buf, size_t bytes);
 

@@ -1005,7 +1005,7 @@ lbm_status lbm_save_state(lbm_domain *d, void *buf, size_t *bytes) {
   }
   if (*bytes < need) return fail(LBM_EINVAL, "buffer of %zu bytes, need %zu", *bytes, need);
   StateHeader h{};
-  std::memcpy(h.magic, "PEMLBM1", 8);
+  std::memcpy(h.magic, "PEMLBM2", 8);
   h.nx = d->nx; h.ny = d->ny; h.precision = d->desc.precision; h.cur = d->cur; h.steps = d->steps;
   for (int k = 0; k < 3; ++k) { h.Cref[k] = d->Cref[k]; h.bref[k] = d->bref[k]; }
   std::memcpy(buf, &h, sizeof h);
@@ -1025,7 +1025,7 @@ lbm_status lbm_load_state(lbm_domain *d, const void *buf, size_t bytes) {
   StateHeader h;
   if (bytes != sizeof h + 2 * pop_bytes) return fail(LBM_EINVAL, "blob of %zu bytes does not match this domain", bytes);
   std::memcpy(&h, buf, sizeof h);
-  if (std::memcmp(h.magic, "PEMLBM1", 8) || h.nx != d->nx || h.ny != d->ny || h.precision != d->desc.precision)
+  if (std::memcmp(h.magic, "PEMLBM2", 8) || h.nx != d->nx || h.ny != d->ny || h.precision != d->desc.precision)
     return fail(LBM_EINVAL, "blob was taken from another geometry or precision");
   const char *p = (const char *)buf + sizeof h;
   CK(cudaMemcpyAsync(d->pop[0], p, pop_bytes, cudaMemcpyHostToDevice, d->stream));

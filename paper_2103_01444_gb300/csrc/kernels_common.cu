@@ -57,9 +57,10 @@ __global__ void k_build_mask(uint8_t *__restrict__ mask, const uint8_t *__restri
 // moving +x (f1, f5, f8 and the D2Q5 link-1 planes of T, O2, H2O) leave
 // through the high side into the right neighbour's low ghost column, those
 // moving -x (f3, f6, f7 and the link-3 planes) through the low side into
-// the left neighbour's high ghost column.  Plane q's ghost of row y sits at
-// y nxp - 1 (low side; row 0's is the previous plane's last element) or
-// y nxp + nx (high side) from the plane's start, inside the row padding.
+// the left neighbour's high ghost column.  Population q's ghost of row y is
+// cell y nxp - 1 (low side) or cell y nxp + nx (high side), inside the row
+// padding; row 0's low ghost is cell -1, which pop_index places in the last
+// padding cell of the plane (or group plane) stored before.
 // One copy moves one direction's six planes for every row: from column col
 // of a lattice buffer (or a packed [6][ny] array) to offset off of a lattice
 // buffer (or a packed array).
@@ -72,8 +73,10 @@ __global__ void k_halo_copy(const S *__restrict__ src, long long src_plane, int 
   if (y >= ny || k >= 6) return;
   const int mv_plus[6] = {1, 5, 8, 10, 15, 20}, mv_minus[6] = {3, 6, 7, 12, 17, 22};
   const long long q = plus ? mv_plus[k] : mv_minus[k];
-  const long long si = src_packed ? (long long)k * ny + y : q * src_plane + (long long)y * src_nxp + src_off;
-  const long long di = dst_packed ? (long long)k * ny + y : q * dst_plane + (long long)y * dst_nxp + dst_off;
+  const long long si = src_packed ? (long long)k * ny + y
+                                  : pop_index(q, (long long)y * src_nxp + src_off, src_plane);
+  const long long di = dst_packed ? (long long)k * ny + y
+                                  : pop_index(q, (long long)y * dst_nxp + dst_off, dst_plane);
   dst[di] = src[si];
 }
 

@@ -579,7 +579,7 @@ k_adj_edge(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
   // ---- phase 1 (lane q): pull link q, read lambda^n of link q
   if (lane < 24) {
     const int q = lane, l = plane_link(q);
-    R v = R(ldp<false>(src_p + q * P + c - ey9(l) * W - ex9(l)));   // interior pull
+    R v = R(ldp<false>(src_p + pop_index(q, c - ey9(l) * W - ex9(l), P)));   // interior pull
     if (l != 0) {
       if (q < 9) v = pull_flow_edge<S, R>(src, a, mask, mid, pal, q, x, y, m, v);
       else v = pull_scalar_edge<S, R>(src, a, mask, mc, (q - 9) / 5, l, x, y, m, v);

@@ -8,13 +8,19 @@
 // catalyst sources (Eq. 12-17) and writes the 24 post-collision values to
 // the other buffer.
 //
-// Storage: structure of arrays, 24 planes of ny rows x nxp (padded) columns,
-// x fastest.  Each plane holds DEVIATIONS from a fixed per-direction
-// reference: f_i - w_i rho0 for the flow and g_i - wref_{s,i} Cref_s for
-// scalar s, where wref are the D2Q5 equilibrium weights of one reference b
-// per scalar.  The references do not depend on the cell, so a pull never
-// needs the source cell's material, and all arithmetic runs on small
-// numbers (the collision is written directly in deviation moments).
+// Storage: a buffer of 24 planes' worth of values, each plane ny rows x nxp
+// (padded) columns, x fastest.  Links 0-4 of the flow (Eq. 2) and of the
+// three scalars (Eq. 9) point the same way, so the four values of link i of a
+// cell (f_i, g_T,i, g_O2,i, g_H2O,i) are kept side by side: five planes of
+// 4-value groups, then the diagonal flow links 5-8 as plain planes
+// (pop_index).  An interior pull of links 0-4 is then one vector load from
+// the source cell, and the store of the cell's links 0-4 one vector store.
+// Every value is a DEVIATION from a fixed per-direction reference:
+// f_i - w_i rho0 for the flow and g_i - wref_{s,i} Cref_s for scalar s,
+// where wref are the D2Q5 equilibrium weights of one reference b per scalar.
+// The references do not depend on the cell, so a pull never needs the
+// source cell's material, and all arithmetic runs on small numbers (the
+// collision is written directly in deviation moments).
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -22,6 +28,14 @@
 #include <stdint.h>
 
 namespace pemlbm {
+
+// Element offset of population q (0-8 flow, 9 + 5 s + i link i of scalar s)
+// of cell c in a buffer whose planes hold P cells each.
+__host__ __device__ __forceinline__ constexpr long long pop_index(int q, long long c, long long P) {
+  return q < 5 ? 4 * (q * P + c)
+       : q < 9 ? (15 + q) * P + c
+               : 4 * (((q - 9) % 5) * P + c) + 1 + (q - 9) / 5;
+}
 
 // ------------------------------------------------------------------ mask
 enum : uint8_t {
@@ -68,15 +82,18 @@ template <bool CG, typename S> __device__ __forceinline__ auto ldp(const S *p) {
 // exponent E of a normal FP16 value and 2^-24 below 2^-14; the FP32 sum
 // v + sign(v) u spacing rounds at 2^-13 of that spacing or finer, a bias
 // below 1e-4 of one rounding step.
-__device__ __forceinline__ void st_sr(__nv_bfloat16 *p, float v, unsigned r16) {
-  const unsigned b = __float_as_uint(v) + r16;
-  *reinterpret_cast<unsigned short *>(p) = (unsigned short)(b >> 16);
+// sr_bits returns the 16-bit pattern; the pointer only selects the format.
+__device__ __forceinline__ unsigned short sr_bits(const __nv_bfloat16 *, float v, unsigned r16) {
+  return (unsigned short)((__float_as_uint(v) + r16) >> 16);
 }
-__device__ __forceinline__ void st_sr(__half *p, float v, unsigned r16) {
+__device__ __forceinline__ unsigned short sr_bits(const __half *, float v, unsigned r16) {
   const unsigned e = __float_as_uint(v) & 0x7f800000u;
   const float spacing = __uint_as_float(max(e, 113u << 23) - (10u << 23));
   const float a = fmaf(copysignf(spacing, v), (float)r16 * (1.0f / 65536.0f), v);
-  *p = __float2half_rz(a);
+  return __half_as_ushort(__float2half_rz(a));
+}
+template <typename S> __device__ __forceinline__ void st_sr(S *p, float v, unsigned r16) {
+  *reinterpret_cast<unsigned short *>(p) = sr_bits(p, v, r16);
 }
 // Random bits for cell c of a step: a 32-bit integer hash of (c, seed), and
 // a xorshift stream from it for the cell's 24 stores.
@@ -95,10 +112,74 @@ __device__ __forceinline__ unsigned xorshift32(unsigned &s) {
   return s;
 }
 
+// One group of four values (links i of the flow and of the three scalars).
+template <typename R> struct Quad { R v[4]; };
+template <bool CG>
+__device__ __forceinline__ Quad<float> ldq(const float *p) {
+  const float4 *q = reinterpret_cast<const float4 *>(p);
+  const float4 t = CG ? __ldcg(q) : __ldg(q);
+  return Quad<float>{{t.x, t.y, t.z, t.w}};
+}
+template <bool CG>
+__device__ __forceinline__ Quad<double> ldq(const double *p) {
+  const double2 *q = reinterpret_cast<const double2 *>(p);
+  const double2 t0 = CG ? __ldcg(q) : __ldg(q), t1 = CG ? __ldcg(q + 1) : __ldg(q + 1);
+  return Quad<double>{{t0.x, t0.y, t1.x, t1.y}};
+}
+// 16-bit groups: one 8-byte load, the first value in the low half of the
+// first word; each conversion is exact (as __bfloat162float, __half2float)
+template <bool CG>
+__device__ __forceinline__ Quad<float> ldq(const __nv_bfloat16 *p) {
+  const uint2 *q = reinterpret_cast<const uint2 *>(p);
+  const uint2 t = CG ? __ldcg(q) : __ldg(q);
+  return Quad<float>{{__uint_as_float(t.x << 16), __uint_as_float(t.x & 0xffff0000u),
+                      __uint_as_float(t.y << 16), __uint_as_float(t.y & 0xffff0000u)}};
+}
+template <bool CG>
+__device__ __forceinline__ Quad<float> ldq(const __half *p) {
+  const uint2 *q = reinterpret_cast<const uint2 *>(p);
+  const uint2 t = CG ? __ldcg(q) : __ldg(q);
+  const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&t.x));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&t.y));
+  return Quad<float>{{a.x, a.y, b.x, b.y}};
+}
+
 __device__ __forceinline__ void st_r(float *p, float v) { *p = v; }
 __device__ __forceinline__ void st_r(double *p, double v) { *p = v; }
 __device__ __forceinline__ void st_r(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 __device__ __forceinline__ void st_r(__half *p, float v) { *p = __float2half_rn(v); }
+
+// Group stores (round to nearest even, as st_r).
+__device__ __forceinline__ void stq(float *p, float a, float b, float c, float d) {
+  *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void stq(double *p, double a, double b, double c, double d) {
+  reinterpret_cast<double2 *>(p)[0] = make_double2(a, b);
+  reinterpret_cast<double2 *>(p)[1] = make_double2(c, d);
+}
+__device__ __forceinline__ uint2 pack4(unsigned short a, unsigned short b, unsigned short c,
+                                       unsigned short d) {
+  return make_uint2((unsigned)a | ((unsigned)b << 16), (unsigned)c | ((unsigned)d << 16));
+}
+// (paired conversions: each half rounds as __float2bfloat16_rn / __float2half_rn)
+__device__ __forceinline__ void stq(__nv_bfloat16 *p, float a, float b, float c, float d) {
+  const __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
+  *reinterpret_cast<uint2 *>(p) = make_uint2(*reinterpret_cast<const unsigned *>(&lo),
+                                             *reinterpret_cast<const unsigned *>(&hi));
+}
+__device__ __forceinline__ void stq(__half *p, float a, float b, float c, float d) {
+  const __half2 lo = __floats2half2_rn(a, b), hi = __floats2half2_rn(c, d);
+  *reinterpret_cast<uint2 *>(p) = make_uint2(*reinterpret_cast<const unsigned *>(&lo),
+                                             *reinterpret_cast<const unsigned *>(&hi));
+}
+// Group stores with stochastic rounding; r01 and r23 each carry the 16
+// random bits of two values (low half first).
+template <typename S>
+__device__ __forceinline__ void stq_sr(S *p, float a, float b, float c, float d, unsigned r01,
+                                       unsigned r23) {
+  *reinterpret_cast<uint2 *>(p) = pack4(sr_bits(p, a, r01 & 0xffffu), sr_bits(p, b, r01 >> 16),
+                                        sr_bits(p, c, r23 & 0xffffu), sr_bits(p, d, r23 >> 16));
+}
 
 // Material coefficients of one palette entry, derived from (phi, K, alpha)
 // by k_prep_palette: 16 values so an entry is 4 x 16-byte vectors in FP32.
@@ -218,7 +299,7 @@ template <typename S, bool CG = false> struct Pops {
   long long plane;
   int nxp;
   __device__ __forceinline__ auto at(int q, int x, int y) const {
-    return ldp<CG>(p + (long long)q * plane + (long long)y * nxp + x);
+    return ldp<CG>(p + pop_index(q, (long long)y * nxp + x, plane));
   }
 };
 
@@ -423,26 +504,23 @@ __device__ __forceinline__ R volume_sink(const Pops<S, CG> &src, const KArgsT<R>
 template <typename S, typename R, bool CG = false>
 __device__ __forceinline__ void load_interior(const Pops<S, CG> &src, const KArgsT<R> &a, int x, int y,
                                               Cell<R> &c) {
-  const long long base = (long long)y * a.nxp + x, P = a.plane, W = a.nxp;
-  const S *p = src.p + base;
-  c.f[0] = ldp<CG>(p);
-  c.f[1] = ldp<CG>(p + 1 * P - 1);
-  c.f[2] = ldp<CG>(p + 2 * P - W);
-  c.f[3] = ldp<CG>(p + 3 * P + 1);
-  c.f[4] = ldp<CG>(p + 4 * P + W);
-  c.f[5] = ldp<CG>(p + 5 * P - W - 1);
-  c.f[6] = ldp<CG>(p + 6 * P - W + 1);
-  c.f[7] = ldp<CG>(p + 7 * P + W + 1);
-  c.f[8] = ldp<CG>(p + 8 * P + W - 1);
+  const long long c0 = (long long)y * a.nxp + x, P = a.plane, W = a.nxp;
+  // links 0-4: one group load from the source cell x - e_i; the offsets are
+  // pop_index's, written from two base addresses (fewer live registers)
+  const long long from[5] = {0, -1, -W, 1, W};
 #pragma unroll
-  for (int s = 0; s < 3; ++s) {
-    const S *q = p + (9 + 5 * s) * P;
-    c.g[s][0] = ldp<CG>(q);
-    c.g[s][1] = ldp<CG>(q + 1 * P - 1);
-    c.g[s][2] = ldp<CG>(q + 2 * P - W);
-    c.g[s][3] = ldp<CG>(q + 3 * P + 1);
-    c.g[s][4] = ldp<CG>(q + 4 * P + W);
+  for (int i = 0; i < 5; ++i) {
+    const auto v = ldq<CG>(src.p + 4 * (i * P + c0 + from[i]));
+    c.f[i] = v.v[0];
+    c.g[0][i] = v.v[1];
+    c.g[1][i] = v.v[2];
+    c.g[2][i] = v.v[3];
   }
+  const S *d = src.p + 20 * P + c0;
+  c.f[5] = ldp<CG>(d - W - 1);
+  c.f[6] = ldp<CG>(d + P - W + 1);
+  c.f[7] = ldp<CG>(d + 2 * P + W + 1);
+  c.f[8] = ldp<CG>(d + 3 * P + W - 1);
 }
 
 // Replaces the pulls of links that cross a wall, the inlet, the outlet, a

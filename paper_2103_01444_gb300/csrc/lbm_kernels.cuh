@@ -374,7 +374,7 @@ __global__ void k_init(S *__restrict__ pop, const uint8_t *__restrict__ mask,
   if (x >= a.nxp || y >= a.ny) return;
   const long long c = (long long)y * a.nxp + x;
   const bool live = x < a.nx && (mask[c] & REG_MASK) != REG_SOLID;
-  for (int i = 0; i < 9; ++i) st_r(pop + i * a.plane + c, R(0));
+  for (int i = 0; i < 9; ++i) st_r(pop + pop_index(i, c, a.plane), R(0));
   for (int s = 0; s < 3; ++s) {
     R w1 = live ? pal[mid[c]].w1[s] : R(a.wr1[s]);
     R w0 = R(1) - R(4) * w1;
@@ -382,8 +382,8 @@ __global__ void k_init(S *__restrict__ pop, const uint8_t *__restrict__ mask,
     R d0 = w0 * R(a.Cin[s]) - R(a.wr0[s]) * R(a.Cref[s]);
     R d1 = w1 * R(a.Cin[s]) - R(a.wr1[s]) * R(a.Cref[s]);
     if (!live) d0 = d1 = R(0);
-    st_r(pop + (9 + 5 * s) * a.plane + c, d0);
-    for (int i = 1; i < 5; ++i) st_r(pop + (9 + 5 * s + i) * a.plane + c, d1);
+    st_r(pop + pop_index(9 + 5 * s, c, a.plane), d0);
+    for (int i = 1; i < 5; ++i) st_r(pop + pop_index(9 + 5 * s + i, c, a.plane), d1);
   }
 }
 
@@ -404,7 +404,7 @@ __global__ void k_get_state(const S *__restrict__ pop, const uint8_t *__restrict
       const int s = (q - 9) / 5, i = (q - 9) % 5;
       ref = (double)(i == 0 ? a.wr0[s] : a.wr1[s]) * (double)a.Cref[s];
     }
-    out[q * n + o] = solid ? 0.0 : (double)ld_r(pop + q * a.plane + c) + ref;
+    out[q * n + o] = solid ? 0.0 : (double)ld_r(pop + pop_index(q, c, a.plane)) + ref;
   }
 }
 
@@ -425,7 +425,7 @@ __global__ void k_set_state(S *__restrict__ pop, const uint8_t *__restrict__ mas
       const int s = (q - 9) / 5, i = (q - 9) % 5;
       ref = (double)(i == 0 ? a.wr0[s] : a.wr1[s]) * (double)a.Cref[s];
     }
-    st_r(pop + q * a.plane + c, solid ? R(0) : R(in[q * n + o] - ref));
+    st_r(pop + pop_index(q, c, a.plane), solid ? R(0) : R(in[q * n + o] - ref));
   }
 }
 

@@ -41,40 +41,38 @@ __device__ __forceinline__ void cell_update(const S *__restrict__ src_p, S *__re
   R o[9];
   collide_flow<R, X>(a, mc, u, cell.f, o);
   // 16-bit storage with stochastic rounding: a random stream per cell and
-  // step (hash of the cell and the device step counter)
-  // (16 bits per store: each xorshift draw serves two stores)
-  unsigned rs = 0, rbits = 0;
-  bool rhalf = false;
+  // step (hash of the cell and the device step counter); each 32-bit
+  // xorshift draw rounds two stores
+  unsigned rs = 0;
   if constexpr (SR)
     rs = hash32((unsigned)c * 0x9e3779b9u ^ hash32(__ldg(a.seed_ctr) + 0x632be5abu)) | 1u;
-  auto store = [&](S *p, R v) {
+  const long long P = a.plane;
+  if (live) {   // the diagonal flow links
     if constexpr (SR) {
-      unsigned r16;
-      if (rhalf) {
-        r16 = rbits >> 16;
-      } else {
-        rbits = xorshift32(rs);
-        r16 = rbits & 0xffffu;
-      }
-      rhalf = !rhalf;
-      st_sr(p, v, r16);
+      const unsigned r0 = xorshift32(rs), r1 = xorshift32(rs);
+      st_sr(dst + pop_index(5, c, P), o[5], r0 & 0xffffu);
+      st_sr(dst + pop_index(6, c, P), o[6], r0 >> 16);
+      st_sr(dst + pop_index(7, c, P), o[7], r1 & 0xffffu);
+      st_sr(dst + pop_index(8, c, P), o[8], r1 >> 16);
     } else {
-      st_r(p, v);
-    }
-  };
-  S *out = dst + c;
-  if (live) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) store(out + (long long)i * a.plane, o[i]);
+      for (int i = 5; i < 9; ++i) st_r(dst + pop_index(i, c, P), o[i]);
+    }
   }
   const R srcv[3] = {-S_vol * R(a.hpo) * mc.inv_sigma, S_vol, R(-2) * S_vol};
+  R g[3][5];
 #pragma unroll
-  for (int s = 0; s < 3; ++s) {
-    R g[5];
-    collide_scalar<R>(a, mc, s, u.ux, u.uy, u.C[s], cell.g[s], srcv[s], g);
-    if (live) {
+  for (int s = 0; s < 3; ++s)
+    collide_scalar<R>(a, mc, s, u.ux, u.uy, u.C[s], cell.g[s], srcv[s], g[s]);
+  if (live) {   // links 0-4 of the flow and the three scalars, one group each
 #pragma unroll
-      for (int i = 0; i < 5; ++i) store(out + (long long)(9 + 5 * s + i) * a.plane, g[i]);
+    for (int i = 0; i < 5; ++i) {
+      if constexpr (SR) {
+        const unsigned r0 = xorshift32(rs), r1 = xorshift32(rs);
+        stq_sr(dst + pop_index(i, c, P), o[i], g[0][i], g[1][i], g[2][i], r0, r1);
+      } else {
+        stq(dst + pop_index(i, c, P), o[i], g[0][i], g[1][i], g[2][i]);
+      }
     }
   }
 }
