@@ -120,7 +120,8 @@ struct lbm_domain {
   int npal = 0;
   std::vector<MatRaw> hraw;    // host copy of the palette's raw tuples
   int ref_entry = 0;           // palette entry of the reference cell
-  void *snap = nullptr;        // residual snapshot [5][ny][nx], storage precision
+  void *snap = nullptr;        // two residual snapshots [2][5][ny][nx], arithmetic precision
+  int snap_cur = 0;            // the one the next lbm_residual compares with
   double *partial = nullptr;   // residual block partials [blocks][10]
   double *colsum = nullptr;    // catalyst column sums [2][nx]
   int variant = 0;             // launch shape of the step kernel (lbm_tune picks one)
@@ -464,7 +465,7 @@ lbm_status lbm_create_domain(const lbm_domain_desc *desc, lbm_domain **out) {
       dmalloc(&d->mask, 2 * cells) != cudaSuccess || dmalloc(&d->mid, cells * 2) != cudaSuccess ||
       dmalloc(&d->pal, coef * kMaxPalette) != cudaSuccess ||
       dmalloc(&d->raw, sizeof(MatRaw) * kMaxPalette) != cudaSuccess ||
-      dmalloc(&d->snap, rsize * 5 * (size_t)d->nx * D.ny) != cudaSuccess ||
+      dmalloc(&d->snap, 2 * rsize * 5 * (size_t)d->nx * D.ny) != cudaSuccess ||
       dmalloc(&d->partial, sizeof(double) * 10 * residual_blocks(d->nx, D.ny)) != cudaSuccess ||
       dmalloc(&d->colsum, sizeof(double) * 2 * d->nx) != cudaSuccess ||
       dmalloc(&d->dsmall, sizeof(double) * 16) != cudaSuccess || dmalloc(&d->dbad, sizeof(int)) != cudaSuccess ||
@@ -738,7 +739,8 @@ lbm_status lbm_reset(lbm_domain *d) {
   d->have_state = true;
   drop_graphs(d);
   // first residual snapshot: compare against zeros, keep only the snapshot
-  CK(cudaMemsetAsync(d->snap, 0, (fp64(d) ? 8 : 4) * 5 * (size_t)d->nx * d->ny, d->stream));
+  CK(cudaMemsetAsync(d->snap, 0, 2 * (fp64(d) ? 8 : 4) * 5 * (size_t)d->nx * d->ny, d->stream));
+  d->snap_cur = 0;
   double r;
   lbm_status s = lbm_residual(d, &r);
   if (s != LBM_OK && s != LBM_EDIVERGED) return s;
@@ -894,12 +896,18 @@ lbm_status lbm_residual(lbm_domain *d, double *res) {
   if (!d->have_state) return fail(LBM_ESTATE, "call lbm_reset first");
   const KArgs a = make_args(d);
   CK(cudaMemsetAsync(d->dbad, 0, sizeof(int), d->stream));
+  // compare with one snapshot, write the other (an in-place update of one
+  // buffer makes the kernel several times slower)
+  const size_t half = (fp64(d) ? 8 : 4) * 5 * (size_t)d->nx * d->ny;
+  char *snaps = (char *)d->snap;
   dispatch(d->desc.precision, [&](auto *tag) {
     using S = std::remove_pointer_t<decltype(tag)>;
-    launch_residual<S>(d->pop[d->cur], geom(d), a, d->snap, d->partial, d->dbad, d->dsmall,
+    launch_residual<S>(d->pop[d->cur], geom(d), a, snaps + d->snap_cur * half,
+                       snaps + (d->snap_cur ^ 1) * half, d->partial, d->dbad, d->dsmall,
                        d->stream);
   });
   CK(cudaGetLastError());
+  d->snap_cur ^= 1;
   CK(cudaMemcpyAsync(d->hsmall, d->dsmall, 10 * sizeof(double), cudaMemcpyDeviceToHost, d->stream));
   CK(cudaMemcpyAsync(d->hsmall + 10, d->dbad, sizeof(int), cudaMemcpyDeviceToHost, d->stream));
   CK(cudaStreamSynchronize(d->stream));
@@ -2150,7 +2158,8 @@ extern "C" lbm_status lbm_residual_noalloc(lbm_domain *d, void *snapshot, double
   const KArgs a = make_args(d);
   dispatch(d->desc.precision, [&](auto *tag) {
     using S = std::remove_pointer_t<decltype(tag)>;
-    launch_residual<S>(d->pop[d->cur], geom(d), a, snapshot, scratch, bad, sums, d->stream);
+    launch_residual<S>(d->pop[d->cur], geom(d), a, snapshot, snapshot, scratch, bad, sums,
+                       d->stream);
   });
   CK(cudaGetLastError());
   double h[11];

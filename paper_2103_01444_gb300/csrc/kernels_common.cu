@@ -158,16 +158,17 @@ void launch_prep_palette(void *pal, const MatRaw *raw, int npal, double nu, int 
                                                mode);
 }
 
+// Block k sums quantity k over the nblocks partials (rows of 10): each
+// thread adds its blocks in increasing order, then a fixed-order block sum.
 __global__ void __launch_bounds__(kReduceThreads)
 k_sum_partials(const double *__restrict__ partial, int nblocks, double *__restrict__ out) {
-  __shared__ double sm[10 * 32];
-  double acc[10];
-  for (int k = 0; k < 10; ++k) acc[k] = 0.0;
-  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
-    for (int k = 0; k < 10; ++k) acc[k] += partial[(long long)b * 10 + k];
-  block_sum<10>(acc, sm);
-  if (threadIdx.x == 0)
-    for (int k = 0; k < 10; ++k) out[k] = acc[k];
+  __shared__ double sm[32];
+  const int k = blockIdx.x;
+  double acc[1] = {0.0};
+#pragma unroll 4
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) acc[0] += partial[(long long)b * 10 + k];
+  block_sum<1>(acc, sm);
+  if (threadIdx.x == 0) out[k] = acc[0];
 }
 
 __global__ void __launch_bounds__(kReduceThreads)

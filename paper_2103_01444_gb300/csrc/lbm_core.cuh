@@ -523,6 +523,22 @@ __device__ __forceinline__ void load_interior(const Pops<S, CG> &src, const KArg
   c.f[8] = ldp<CG>(d + 3 * P + W - 1);
 }
 
+// The cell's own 24 stored values (no streaming), by groups.
+template <typename S, typename R, bool CG = false>
+__device__ __forceinline__ void load_own(const Pops<S, CG> &src, int x, int y, Cell<R> &c) {
+  const long long c0 = (long long)y * src.nxp + x, P = src.plane;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const auto v = ldq<CG>(src.p + pop_index(i, c0, P));
+    c.f[i] = v.v[0];
+    c.g[0][i] = v.v[1];
+    c.g[1][i] = v.v[2];
+    c.g[2][i] = v.v[3];
+  }
+#pragma unroll
+  for (int i = 5; i < 9; ++i) c.f[i] = ldp<CG>(src.p + pop_index(i, c0, P));
+}
+
 // Replaces the pulls of links that cross a wall, the inlet, the outlet, a
 // periodic seam or a solid grain (cells with any edge bit only).
 template <typename S, typename R, bool CG = false, bool X = false>

@@ -297,13 +297,16 @@ __global__ void k_sum_columns(const double *__restrict__ colsum, int nx, double 
 // Moments of the post-collision state: X = (j_x, j_y, T - T_in, C_O2, C_H2O).
 // One thread per cell: the change since the snapshot and the value are
 // squared, summed over the warp by shuffles, then over the block in FP64
-// (10 partial sums per block); the snapshot (storage precision R) is then
-// overwritten.  Non-finite values raise *bad.
+// (10 partial sums per block).  The values are compared with snap_in and
+// written to snap_out (arithmetic precision R).  The two may be one buffer
+// (updated in place), but distinct buffers are much faster: reading and then
+// writing the same addresses in one launch took about 4x the kernel's time at
+// 4096 x 1024.  Non-finite values raise *bad.
 template <typename S>
 __global__ void __launch_bounds__(kResidualBX * kResidualBY)
 k_residual(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
-           KArgsT<typename Real<S>::type> a,
-           typename Real<S>::type *__restrict__ snap, double *__restrict__ partial,
+           KArgsT<typename Real<S>::type> a, const typename Real<S>::type *snap_in,
+           typename Real<S>::type *snap_out, double *__restrict__ partial,
            int *__restrict__ bad) {
   using R = typename Real<S>::type;
   __shared__ R sm[10 * 32];
@@ -313,33 +316,37 @@ k_residual(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
   R v[10];
 #pragma unroll
   for (int k = 0; k < 10; ++k) v[k] = R(0);
-  if (x < a.nx && y < a.ny && (mask[(long long)y * a.nxp + x] & REG_MASK) != REG_SOLID) {
+  if (x < a.nx && y < a.ny) {
     const long long n = (long long)a.nx * a.ny, o = (long long)y * a.nx + x;
-    R d[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) d[k] = R(src.at(k, x, y));
+    // the cell's values are loaded without waiting for its mask
+    Cell<R> own;
+    load_own<S, R>(src, x, y, own);
+    const bool live = (mask[(long long)y * a.nxp + x] & REG_MASK) != REG_SOLID;
+    const R *d = own.f;
     R X[5];
     X[0] = d[1] - d[3] + d[5] - d[6] - d[7] + d[8];
     X[1] = d[2] - d[4] + d[5] + d[6] - d[7] - d[8];
-    X[2] = own_sum<S, R>(src, 0, x, y) + a.theta0;
-    X[3] = own_sum<S, R>(src, 1, x, y) + R(a.Cref[1]);
-    X[4] = own_sum<S, R>(src, 2, x, y) + R(a.Cref[2]);
-    // all five snapshot values are read before any is overwritten, so the
-    // loads overlap instead of waiting on each other's stores
+    X[2] = d2q5_sum<R>(own.g[0][0], own.g[0][1], own.g[0][2], own.g[0][3], own.g[0][4]) + a.theta0;
+    X[3] = d2q5_sum<R>(own.g[1][0], own.g[1][1], own.g[1][2], own.g[1][3], own.g[1][4]) + R(a.Cref[1]);
+    X[4] = d2q5_sum<R>(own.g[2][0], own.g[2][1], own.g[2][2], own.g[2][3], own.g[2][4]) + R(a.Cref[2]);
+    // all five snapshot values are read before any is written, so the loads
+    // overlap (and an in-place update reads the old values)
     R prev[5];
 #pragma unroll
-    for (int k = 0; k < 5; ++k) prev[k] = snap[k * n + o];
-    bool ok = true;
+    for (int k = 0; k < 5; ++k) prev[k] = snap_in[k * n + o];
+    if (live) {
+      bool ok = true;
 #pragma unroll
-    for (int k = 0; k < 5; ++k) {
-      ok = ok && isfinite(X[k]);
-      const R dv = X[k] - prev[k];
-      v[k] = dv * dv;
-      v[5 + k] = X[k] * X[k];
+      for (int k = 0; k < 5; ++k) {
+        ok = ok && isfinite(X[k]);
+        const R dv = X[k] - prev[k];
+        v[k] = dv * dv;
+        v[5 + k] = X[k] * X[k];
+      }
+#pragma unroll
+      for (int k = 0; k < 5; ++k) snap_out[k * n + o] = X[k];
+      if (!ok) *bad = 1;
     }
-#pragma unroll
-    for (int k = 0; k < 5; ++k) snap[k * n + o] = X[k];
-    if (!ok) *bad = 1;
   }
 #pragma unroll
   for (int k = 0; k < 10; ++k) {
@@ -359,7 +366,8 @@ k_residual(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
   }
 }
 
-// Sums nblocks x 10 partials in a fixed order.
+// Sums nblocks x 10 partials in a fixed order; 10 blocks, block k sums
+// quantity k into out[k].
 __global__ void k_sum_partials(const double *__restrict__ partial, int nblocks,
                                double *__restrict__ out);
 
@@ -374,17 +382,19 @@ __global__ void k_init(S *__restrict__ pop, const uint8_t *__restrict__ mask,
   if (x >= a.nxp || y >= a.ny) return;
   const long long c = (long long)y * a.nxp + x;
   const bool live = x < a.nx && (mask[c] & REG_MASK) != REG_SOLID;
-  for (int i = 0; i < 9; ++i) st_r(pop + pop_index(i, c, a.plane), R(0));
+  R d0[3], d1[3];
   for (int s = 0; s < 3; ++s) {
     R w1 = live ? pal[mid[c]].w1[s] : R(a.wr1[s]);
     R w0 = R(1) - R(4) * w1;
     // equilibrium of C_in at rest with the cell's own b, minus the reference
-    R d0 = w0 * R(a.Cin[s]) - R(a.wr0[s]) * R(a.Cref[s]);
-    R d1 = w1 * R(a.Cin[s]) - R(a.wr1[s]) * R(a.Cref[s]);
-    if (!live) d0 = d1 = R(0);
-    st_r(pop + pop_index(9 + 5 * s, c, a.plane), d0);
-    for (int i = 1; i < 5; ++i) st_r(pop + pop_index(9 + 5 * s + i, c, a.plane), d1);
+    d0[s] = w0 * R(a.Cin[s]) - R(a.wr0[s]) * R(a.Cref[s]);
+    d1[s] = w1 * R(a.Cin[s]) - R(a.wr1[s]) * R(a.Cref[s]);
+    if (!live) d0[s] = d1[s] = R(0);
   }
+  // flow deviations zero; links 0-4 by groups, then the diagonal flow links
+  stq(pop + pop_index(0, c, a.plane), R(0), d0[0], d0[1], d0[2]);
+  for (int i = 1; i < 5; ++i) stq(pop + pop_index(i, c, a.plane), R(0), d1[0], d1[1], d1[2]);
+  for (int i = 5; i < 9; ++i) st_r(pop + pop_index(i, c, a.plane), R(0));
 }
 
 // ------------------------------------------- full-value state in/out
@@ -585,13 +595,13 @@ void launch_catalyst(const void *src, const DevGeom &g, const KArgs &a, double i
 }
 
 template <typename S>
-void launch_residual(const void *src, const DevGeom &g, const KArgs &a, void *snap,
-                     double *partial, int *bad, double *out, cudaStream_t st) {
+void launch_residual(const void *src, const DevGeom &g, const KArgs &a, const void *snap_in,
+                     void *snap_out, double *partial, int *bad, double *out, cudaStream_t st) {
   dim3 grid((a.nx + kResidualBX - 1) / kResidualBX, (a.ny + kResidualBY - 1) / kResidualBY);
   k_residual<S><<<grid, kResidualBX * kResidualBY, 0, st>>>(
       (const S *)src, g.mask, narrow_args<typename Real<S>::type>(a),
-      (typename Real<S>::type *)snap, partial, bad);
-  k_sum_partials<<<1, kReduceThreads, 0, st>>>(partial, grid.x * grid.y, out);
+      (const typename Real<S>::type *)snap_in, (typename Real<S>::type *)snap_out, partial, bad);
+  k_sum_partials<<<10, kReduceThreads, 0, st>>>(partial, grid.x * grid.y, out);
 }
 
 template <typename S>
@@ -625,8 +635,8 @@ void launch_set_state(void *pop, const DevGeom &g, const KArgs &a, const double 
                                    cudaStream_t);                                                \
   template void launch_catalyst<S>(const void *, const DevGeom &, const KArgs &, double,        \
                                    float *, double *, double *, cudaStream_t);                  \
-  template void launch_residual<S>(const void *, const DevGeom &, const KArgs &, void *,        \
-                                   double *, int *, double *, cudaStream_t);                    \
+  template void launch_residual<S>(const void *, const DevGeom &, const KArgs &, const void *,  \
+                                   void *, double *, int *, double *, cudaStream_t);            \
   template void launch_init<S>(void *, const DevGeom &, const KArgs &, cudaStream_t);           \
   template void launch_get_state<S>(const void *, const DevGeom &, const KArgs &, double *,     \
                                     cudaStream_t);                                              \

@@ -45,7 +45,9 @@ template <typename S> void launch_step(const void *src, void *dst, const DevGeom
 template <typename S> void launch_fields(const void *src, const DevGeom &g, const KArgs &a, double *out, cudaStream_t st);
 template <typename S> void launch_balances(const void *src, const DevGeom &g, const KArgs &a, double *out, cudaStream_t st);
 template <typename S> void launch_catalyst(const void *src, const DevGeom &g, const KArgs &a, double i_scale, float *profile, double *colsum, double *out, cudaStream_t st);
-template <typename S> void launch_residual(const void *src, const DevGeom &g, const KArgs &a, void *snap, double *partial, int *bad, double *out, cudaStream_t st);
+// Residual of state src against snap_in, writing the new snapshot to snap_out
+// (the same buffer for an in-place update).
+template <typename S> void launch_residual(const void *src, const DevGeom &g, const KArgs &a, const void *snap_in, void *snap_out, double *partial, int *bad, double *out, cudaStream_t st);
 // Blocks of the residual kernel (= rows of its partial-sum buffer).
 inline int residual_blocks(int nx, int ny) {
   return ((nx + kResidualBX - 1) / kResidualBX) * ((ny + kResidualBY - 1) / kResidualBY);
