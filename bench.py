@@ -814,6 +814,7 @@ def run_validation(args):
     barrier(pg, dev)
     with ClockSampler(local) as clk:
         ms = d.time_steps(K)
+    launches = K   # one step kernel per step (no reductions in the timed region)
     torch.cuda.synchronize()
     ms_max = max_over_ranks(ms, pg, dev)
     b = d.balances()

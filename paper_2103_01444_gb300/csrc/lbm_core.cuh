@@ -172,13 +172,13 @@ __device__ __forceinline__ void stq(__half *p, float a, float b, float c, float 
   *reinterpret_cast<uint2 *>(p) = make_uint2(*reinterpret_cast<const unsigned *>(&lo),
                                              *reinterpret_cast<const unsigned *>(&hi));
 }
-// Group stores with stochastic rounding; r01 and r23 each carry the 16
-// random bits of two values (low half first).
+// Group stores with stochastic rounding; ra..rd are the 16 random bits of
+// each value.
 template <typename S>
-__device__ __forceinline__ void stq_sr(S *p, float a, float b, float c, float d, unsigned r01,
-                                       unsigned r23) {
-  *reinterpret_cast<uint2 *>(p) = pack4(sr_bits(p, a, r01 & 0xffffu), sr_bits(p, b, r01 >> 16),
-                                        sr_bits(p, c, r23 & 0xffffu), sr_bits(p, d, r23 >> 16));
+__device__ __forceinline__ void stq_sr(S *p, float a, float b, float c, float d, unsigned ra,
+                                       unsigned rb, unsigned rc, unsigned rd) {
+  *reinterpret_cast<uint2 *>(p) =
+      pack4(sr_bits(p, a, ra), sr_bits(p, b, rb), sr_bits(p, c, rc), sr_bits(p, d, rd));
 }
 
 // Material coefficients of one palette entry, derived from (phi, K, alpha)
