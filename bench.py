@@ -845,7 +845,7 @@ def run_validation(args):
                       if k in case}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": (traffic_from_profiles("k_step_cavity-2048x2048-fp32.json")
+                     "traffic": (traffic_from_profiles("cavity-2048x2048", "fp32")
                                  if args.workload == "cavity" and args.precision == "fp32"
                                  and case["nx"] == 2048 else None),
                      "peak_source": peak_kind,
