@@ -131,6 +131,7 @@ struct lbm_domain {
   unsigned *dseed = nullptr;   // step counter seeding stochastic 16-bit rounding
   double *hsmall = nullptr;    // pinned host mirror
   double *scratch = nullptr;   // [24][ny][nx] doubles, lazily allocated
+  void *pal_scratch = nullptr; // device palette build's work space, allocated at its first use
   float *dprofile = nullptr;   // [nx]
   // references of the deviation storage: part of the state's representation,
   // so they change only at reset (or with a loaded state)
@@ -500,7 +501,7 @@ lbm_status lbm_destroy_domain(lbm_domain *d) {
   drop_graphs(d);
   for (void *p : {d->pop[0], d->pop[1], (void *)d->mask, (void *)d->mid, d->pal, (void *)d->raw,
                   d->snap, (void *)d->partial, (void *)d->colsum, (void *)d->dsmall, (void *)d->dbad, (void *)d->dseed,
-                  (void *)d->scratch, (void *)d->dprofile, (void *)d->dobs})
+                  (void *)d->scratch, (void *)d->dprofile, (void *)d->dobs, d->pal_scratch})
     if (p) cudaFree(p);
   if (d->hsmall) cudaFreeHost(d->hsmall);
   if (d->hobs) cudaFreeHost(d->hobs);
@@ -572,27 +573,24 @@ lbm_status set_fields_device(lbm_domain *d, const double *phi, const double *K,
                              const double *alpha_T, const double *D_O2, const double *D_H2O,
                              const double *rho_cp_ratio) {
   const int nx = d->nx, ny = d->ny;
-  struct Scratch {
-    void *p = nullptr;
-    ~Scratch() {
-      if (p) cudaFree(p);
-    }
-  } sc;
   const size_t mid_bytes = sizeof(uint16_t) * (size_t)d->plane;
   const size_t raw_bytes = sizeof(MatRaw) * kMaxPalette;
   const size_t work = palette_scratch_bytes(nx, ny);
   const size_t off_mid = (work + 255) / 256 * 256, off_raw = (off_mid + mid_bytes + 255) / 256 * 256,
                off_st = (off_raw + raw_bytes + 255) / 256 * 256;
-  if (dmalloc(&sc.p, off_st + sizeof(PalStatus)) != cudaSuccess) {
+  // kept for later calls (freeing it would synchronise the device each time)
+  if (!d->pal_scratch && dmalloc(&d->pal_scratch, off_st + sizeof(PalStatus)) != cudaSuccess) {
+    d->pal_scratch = nullptr;
     cudaGetLastError();
     return fail(LBM_ENOMEM, "palette scratch of %.1f MB", (off_st + 256) / 1e6);
   }
-  char *base = (char *)sc.p;
+  char *base = (char *)d->pal_scratch;
   uint16_t *mid = (uint16_t *)(base + off_mid);
   MatRaw *raw = (MatRaw *)(base + off_raw);
   PalStatus *st = (PalStatus *)(base + off_st);
   const PalFields f{phi, K, alpha_T, D_O2, D_H2O, rho_cp_ratio};
-  CK(launch_device_palette(f, d->mask, nx, ny, d->nxp, mid, raw, kMaxPalette, sc.p, st, d->stream));
+  CK(launch_device_palette(f, d->mask, nx, ny, d->nxp, mid, raw, kMaxPalette, d->pal_scratch, st,
+                           d->stream));
   PalStatus h{};
   CK(cudaMemcpyAsync(&h, st, sizeof h, cudaMemcpyDeviceToHost, d->stream));
   CK(cudaStreamSynchronize(d->stream));

@@ -5,9 +5,10 @@
 // D_H2O, rho_cp_ratio) of the fluid cells in order of first occurrence in
 // row-major order, and every fluid cell's index into it: the same palette,
 // entry for entry, as the host build of the same fields.  Steps:
-//   1. insert: every fluid cell validates its tuple, hashes it into an
+//   1. insert: every fluid cell validates its tuple and hashes it into an
 //      open-addressing table (64-bit keys claimed with atomicCAS, linear
-//      probing) and records the smallest cell index of its slot;
+//      probing; the lanes of a warp with one tuple insert it once), and each
+//      slot records the smallest cell index of its tuple;
 //   2. count / scan: the cells that are their slot's smallest index are the
 //      first occurrences; a block count, one scan over the blocks and a
 //      rank within the block number them in row-major order;
@@ -77,41 +78,58 @@ __global__ void k_pal_clear(unsigned long long *keys, int *rep, int *slot_id, in
   }
 }
 
+// Lanes of a warp that hold the same tuple insert it once: the lowest of
+// them (the smallest cell index, since cells follow the lanes) probes the
+// table for the group and broadcasts the slot.  Every lane of the warp takes
+// part (a launch of whole warps), those without a valid fluid cell with key 0.
 __global__ void __launch_bounds__(kPalThreads)
 k_pal_insert(PalFields f, const uint8_t *__restrict__ mask, int nx, int ny, int nxp,
              unsigned long long *keys, int *rep, int *cellslot, int ts, int max_pal,
              PalStatus *st) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= (long long)nx * ny) return;
-  const int x = (int)(c % nx), y = (int)(c / nx);
-  if (!fluid(mask, nxp, x, y)) return;
-  const Tuple t = load_tuple(f, c);
-  if (!valid_tuple(t)) {
-    atomicOr(&st->flags, kPalInvalid);
-    atomicMin(&st->bad_cell, (int)c);
-    return;
-  }
-  if (*((volatile int *)&st->claimed) > max_pal) {     // too many materials already
-    atomicOr(&st->flags, kPalTooMany);
-    return;
-  }
-  const unsigned long long h = hash_tuple(t);
-  unsigned slot = (unsigned)(h & (unsigned long long)(ts - 1));
-  for (int probe = 0; probe < ts; ++probe) {
-    const unsigned long long old = atomicCAS(&keys[slot], 0ull, h);
-    if (old == h) break;
-    if (old == 0ull) {
-      if (atomicAdd(&st->claimed, 1) >= max_pal) atomicOr(&st->flags, kPalTooMany);
-      break;
+  unsigned long long h = 0ull;   // 0: nothing to insert
+  if (c < (long long)nx * ny) {
+    const int x = (int)(c % nx), y = (int)(c / nx);
+    if (fluid(mask, nxp, x, y)) {
+      const Tuple t = load_tuple(f, c);
+      if (valid_tuple(t)) {
+        h = hash_tuple(t);
+      } else {
+        atomicOr(&st->flags, kPalInvalid);
+        atomicMin(&st->bad_cell, (int)c);
+      }
     }
-    if (*((volatile int *)&st->claimed) > max_pal) {   // too many materials: stop probing
+  }
+  const unsigned peers = __match_any_sync(0xffffffffu, h);
+  const int leader = __ffs(peers) - 1;
+  int slot = -1;
+  if (h != 0ull && (int)(threadIdx.x & 31) == leader) {
+    if (*((volatile int *)&st->claimed) > max_pal) {        // too many materials already
       atomicOr(&st->flags, kPalTooMany);
-      return;
+    } else {
+      unsigned s = (unsigned)(h & (unsigned long long)(ts - 1));
+      for (int probe = 0; probe < ts; ++probe) {
+        const unsigned long long old = atomicCAS(&keys[s], 0ull, h);
+        if (old == h) {
+          slot = (int)s;
+          break;
+        }
+        if (old == 0ull) {
+          if (atomicAdd(&st->claimed, 1) >= max_pal) atomicOr(&st->flags, kPalTooMany);
+          slot = (int)s;
+          break;
+        }
+        if (*((volatile int *)&st->claimed) > max_pal) {    // too many materials: stop probing
+          atomicOr(&st->flags, kPalTooMany);
+          break;
+        }
+        s = (s + 1) & (unsigned)(ts - 1);
+      }
+      if (slot >= 0) atomicMin(&rep[slot], (int)c);
     }
-    slot = (slot + 1) & (unsigned)(ts - 1);
   }
-  cellslot[c] = (int)slot;
-  atomicMin(&rep[slot], (int)c);
+  slot = __shfl_sync(0xffffffffu, slot, leader);
+  if (h != 0ull && slot >= 0) cellslot[c] = slot;
 }
 
 // Whether cell c is its tuple's first occurrence (valid, fluid cells only).
