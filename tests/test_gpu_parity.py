@@ -428,6 +428,47 @@ def test_save_load_roundtrip():
     np.testing.assert_array_equal(b.state(), ref)
 
 
+def test_checkpoint_blob_holds_the_documented_layout():
+    """A checkpoint blob is an 80-byte header (magic, nx, ny, precision, the
+    current buffer, the step, C_ref and b_ref of the three scalars) and the two
+    population buffers.  Per buffer: five planes of 4-value groups (link i =
+    0..4 of the flow, T, O2 and H2O for every cell, rows of the padded length
+    nxp), then the planes of flow links 5-8; every value a deviation from
+    w_i (flow) or w_ref,i C_ref (scalars, w_ref the D2Q5 weights of b_ref).
+    Read this way, the current buffer plus its references is lbm_get_state
+    to FP64 rounding."""
+    case = workloads.small_cathode(nx=70, ny=24, reaction_mode=1, grains=True, seed=9)
+    d = gpu_domain(case, "fp64")
+    d.step(13)
+    blob = d.save_state()
+    assert blob[:8] == b"PEMLBM2\0"
+    nx, ny, prec, cur = np.frombuffer(blob, np.int32, 4, 8)
+    assert (nx, ny, int(np.frombuffer(blob, np.int64, 1, 24)[0])) == (d.nx, d.ny, 13)
+    cref = np.frombuffer(blob, np.float64, 3, 32)
+    bref = np.frombuffer(blob, np.float64, 3, 56)
+    raw = np.frombuffer(blob, np.float64, offset=80).reshape(2, -1)[cur]
+    P = raw.size // 24
+    nxp = P // ny
+    groups = raw[:20 * P].reshape(5, P, 4)
+    planes = np.empty((24, P))
+    planes[0:5] = groups[..., 0]
+    planes[5:9] = raw[20 * P:].reshape(4, P)
+    for s in range(3):
+        planes[9 + 5 * s:14 + 5 * s] = groups[..., 1 + s]
+    planes = planes.reshape(24, ny, nxp)[:, :, :nx]
+    ref = np.empty(24)
+    ref[:9] = [4 / 9] + [1 / 9] * 4 + [1 / 36] * 4
+    for s in range(3):
+        w1 = (4 + bref[s]) / 20
+        ref[9 + 5 * s] = (1 - 4 * w1) * cref[s]
+        ref[10 + 5 * s:14 + 5 * s] = w1 * cref[s]
+    fluid = (d.mask() & 3) != 3
+    full = planes + ref[:, None, None]
+    got = d.state()
+    err = np.abs(full - got)[:, fluid].max(axis=1) / np.abs(got[:, fluid]).max(axis=1)
+    assert err.max() < 1e-14, err
+
+
 @pytest.mark.parametrize("name,mode", [("film-64x16", 0), ("vol-77x20", 1), ("grains-70x24", 1)])
 def test_fp64_residual_matches_oracle(name, mode):
     """The steady-state residual (max over j_x, j_y, T - T_in, C_O2, C_H2O
