@@ -325,10 +325,20 @@ lbm_status lbm_bytes_per_cell(lbm_domain *d, double *bytes);
  * Its gradient with respect to the per-cell phi, K and D_O2 of
  * lbm_set_fields (lattice units; K of clear cells gets 0) and to the inlet
  * drive (the lattice inlet velocity u_in_avg, or dp_in with inlet_mode 1)
- * is computed by the transposed step, applied from
- * step N back to step 1, with the forward states recomputed from
- * checkpoints every `segment` steps (<= 0: ceil(sqrt(nsteps))).  Memory:
- * about (nsteps/segment + segment) population states.  The gradient of the
+ * is computed by the transposed step, applied from step N back to step 1.
+ * The transpose of step n needs from the forward run only the step's
+ * reverse records (per cell the Eq. 8 auxiliary velocity, the three scalar
+ * sums and two O2 flux moments, 8 values; per edge or catalyst cell its
+ * pulled values and own sums), a third of a population state.  The forward
+ * sweep keeps the records of its last segments of `segment` steps (<= 0:
+ * ceil(sqrt(nsteps))) in device memory, as many as the limit of
+ * lbm_set_grad_memory allows (by default all that fits in the free device
+ * memory but a reserve of max(1 GiB, 1/64 of the device)); every earlier
+ * segment is recomputed from a checkpoint of its first state.  The records
+ * are the same either way, so the result does not depend on the limit.
+ * Memory: the stored segments' records, plus, when some segment is
+ * recomputed, one population state per recomputed segment and two
+ * segments' records.  The gradient of the
  * Fickian interface mode treats each scalar's b (that of its largest
  * diffusivity) as fixed.  dphi, dK, dD_O2 are [ny][nx] doubles (NULL to
  * skip): host memory with on_device = 0, device memory written on the
@@ -341,6 +351,13 @@ lbm_status lbm_bytes_per_cell(lbm_domain *d, double *bytes);
 lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t segment,
                     double *J, double *dphi, double *dK, double *dD_O2, double *du_in,
                     int32_t on_device);
+
+/* Device memory lbm_grad may hold for the reverse records of stored
+ * segments (bytes): -1 (the default) for what is free less the reserve, 0
+ * to recompute every segment from its checkpoint.  The setting is the
+ * domain's and applies to its later lbm_grad calls.  EINVAL for a null
+ * domain or bytes < -1. */
+lbm_status lbm_set_grad_memory(lbm_domain *d, int64_t bytes);
 
 /* One transposed step at the current state s: given lam_next (host
  * [24][ny][nx], the adjoint of the state after one step), writes lam_prev =

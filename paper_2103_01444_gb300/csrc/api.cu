@@ -125,6 +125,7 @@ struct lbm_domain {
   double *partial = nullptr;   // residual block partials [blocks][10]
   double *colsum = nullptr;    // catalyst column sums [2][nx]
   int variant = 0;             // launch shape of the step kernel (lbm_tune picks one)
+  int64_t grad_mem_limit = -1; // device bytes lbm_grad may keep records in (-1: what is free)
   double tuned_ms[kStepVariants] = {};
   double *dsmall = nullptr;    // device results (16 doubles)
   int *dbad = nullptr;
@@ -1124,8 +1125,9 @@ struct DevBuf {
 
 // Reverse workspace of one domain.
 struct AdjWork {
-  DevBuf lam[2], O[2], V[2], gphi, gK, gD, gU, tphi, tK, tD, cells, pushed;
+  DevBuf lam[2], O[2], V[2], gphi, gK, gD, gU, tphi, tK, tD, cells, pushed, slot;
   int n_edge = 0, n_own = 0;
+  size_t rsize = 4;                             // bytes of the arithmetic type
   cudaStream_t side = nullptr;                  // edge-cell branch of each step
   cudaEvent_t fork = nullptr, join = nullptr;
   ~AdjWork() {
@@ -1182,6 +1184,14 @@ struct AdjWork {
       }
     }
     n_own = (int)list.size();
+    rsize = r;
+    // listed index of every cell (reverse records of own states), -1 for others
+    std::vector<int> slots((size_t)d->plane, -1);
+    for (size_t t = 0; t < list.size(); ++t) slots[(size_t)list[t]] = (int)t;
+    if ((s = slot.alloc(sizeof(int) * slots.size())) != LBM_OK) return s;
+    CK(cudaMemcpyAsync(slot.p, slots.data(), sizeof(int) * slots.size(), cudaMemcpyHostToDevice,
+                       d->stream));
+    CK(cudaStreamSynchronize(d->stream));
     // per edge cell, the links q whose consumer y + e_q is a fluid cell
     // (periodic seam included): only those are pushed by a consumer
     std::vector<uint32_t> bits(n_edge);
@@ -1212,6 +1222,20 @@ struct AdjWork {
     }
     CK(cudaStreamSynchronize(d->stream));
     return LBM_OK;
+  }
+  // Reverse records of one step (RecPtrs): the cell records, then the own
+  // records of the listed cells, then the pulled values of the edge cells,
+  // each part starting on a 256-byte boundary.
+  static size_t up256(size_t b) { return (b + 255) / 256 * 256; }
+  size_t rec_cell_bytes(const lbm_domain *d) const { return up256(8 * rsize * (size_t)d->plane); }
+  size_t rec_own_bytes() const { return up256(4 * rsize * (size_t)n_own); }
+  size_t rec_bytes(const lbm_domain *d) const {
+    return rec_cell_bytes(d) + rec_own_bytes() + up256(24 * rsize * (size_t)n_edge);
+  }
+  RecBufs recs(const lbm_domain *d, void *base) const {
+    char *b = (char *)base;
+    return RecBufs{b, b + rec_cell_bytes(d), b + rec_cell_bytes(d) + rec_own_bytes(),
+                   (const int *)slot.p};
   }
   lbm_status zero_grads(const lbm_domain *d) {
     const size_t r = fp64(d) ? 8 : 4;
@@ -1250,15 +1274,26 @@ void fold_grads(lbm_domain *d, AdjWork &w) {
 // lambda^{n-1} (w.lam[cur ^ 1]), gradients accumulated.
 // lam_complete: lambda^n = w.lam[cur] holds every link in full (uploaded or
 // seeded) rather than the pushed part of a previous reverse step.
-void reverse_step(lbm_domain *d, AdjWork &w, int cur, const void *src, long long seed_cell,
+void reverse_step(lbm_domain *d, AdjWork &w, int cur, const RecBufs &rec, long long seed_cell,
                   bool lam_complete = false) {
   const KArgs a = make_args(d);
   const int fick = d->prm.interface_mode == 1;
   const AdjPtrs b = w.ptrs(cur);
   dispatch(d->desc.precision, [&](auto *tag) {
     using S = std::remove_pointer_t<decltype(tag)>;
-    launch_adj_step<S>(src, geom(d), a, fick, b, seed_cell, lam_complete ? 1 : 0, d->stream,
+    launch_adj_step<S>(rec, geom(d), a, fick, b, seed_cell, lam_complete ? 1 : 0, d->stream,
                        w.side, w.fork, w.join);
+  });
+}
+
+// One forward step src -> dst on stream st that also writes its reverse
+// records into `rec` (RecPtrs).
+void step_with_records(lbm_domain *d, const void *src, void *dst, const RecBufs &rec,
+                       cudaStream_t st) {
+  const KArgs a = make_args(d);
+  dispatch(d->desc.precision, [&](auto *tag) {
+    using S = std::remove_pointer_t<decltype(tag)>;
+    launch_step_rec<S>(src, dst, geom(d), a, rec, st);
   });
 }
 
@@ -1342,7 +1377,12 @@ lbm_status lbm_vjp(lbm_domain *d, const double *lam_next, double *lam_prev, doub
   if ((s = w.alloc(d)) != LBM_OK) return s;
   if ((s = w.zero_grads(d)) != LBM_OK) return s;
   if ((s = lam_upload(d, lam_next, w.lam[0].p)) != LBM_OK) return s;
-  reverse_step(d, w, 0, d->pop[d->cur], -1, true);
+  // the step's reverse records (its new state is not kept)
+  DevBuf rec, next;
+  if ((s = rec.alloc(w.rec_bytes(d))) != LBM_OK) return s;
+  if ((s = next.alloc((24 * (size_t)d->plane + d->nxp + 64) * d->esize)) != LBM_OK) return s;
+  step_with_records(d, d->pop[d->cur], next.p, w.recs(d, rec.p), d->stream);
+  reverse_step(d, w, 0, w.recs(d, rec.p), -1, true);
   finish_lambda(d, w, 1);
   CK(cudaGetLastError());
   if ((s = lam_download(d, w.lam[1].p, lam_prev)) != LBM_OK) return s;
@@ -1361,20 +1401,50 @@ lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t se
   if ((s = adjoint_covers(d)) != LBM_OK) return s;
   if (nsteps < 2 || nsteps > (1LL << 30)) return fail(LBM_EINVAL, "nsteps outside [2, 2^30]");
   const int64_t N = nsteps;
+  // Reverse step n (lambda^n -> lambda^{n-1}) reads the records R^n of
+  // forward step n (s^{n-1} -> s^n).  Objective 0 is a function of s^{N-1}
+  // and seeds lambda^{N-1} directly; objective 1 reads the fields of step
+  // N, whose reverse (step N) needs R^N.
+  const int64_t nrec = objective == 1 ? N : N - 1;
   const int seg = segment > 0 ? segment : (int)std::ceil(std::sqrt((double)N));
-  const int64_t nck = (N + seg - 1) / seg;     // checkpoints of s^0, s^seg, ... (< N)
-  const size_t stride = 24 * (size_t)d->plane + d->nxp + 64;   // guard as in the domain
-  const size_t sbytes = stride * d->esize;
-  DevBuf ck, sgb[2];
-  if ((s = ck.alloc(sbytes * nck)) != LBM_OK) return s;
-  if ((s = sgb[0].alloc(sbytes * (seg + 1))) != LBM_OK) return s;
-  // A second segment buffer lets segment k - 1 be recomputed (on a stream
-  // of its own) while segment k is reversed; without room for it the two
-  // alternate on one buffer.
-  bool overlap = false;
-  if (nck > 1) {
-    if (dmalloc(&sgb[1].p, sbytes * (seg + 1)) == cudaSuccess) overlap = true;
-    else cudaGetLastError();
+  const int64_t nseg = (nrec + seg - 1) / seg;   // segment k: R^{k seg + 1} .. R^{min((k+1) seg, nrec)}
+  const size_t sbytes = (24 * (size_t)d->plane + d->nxp + 64) * d->esize;   // guard as in the domain
+  AdjWork w;
+  if ((s = w.alloc(d)) != LBM_OK) return s;
+  if ((s = w.zero_grads(d)) != LBM_OK) return s;
+  const size_t rbytes = w.rec_bytes(d), segbytes = rbytes * (size_t)seg;
+  DevBuf fs[2];   // forward states
+  for (auto &b : fs)
+    if ((s = b.alloc(sbytes)) != LBM_OK) return s;
+  // The last L segments keep the records their forward steps write; the
+  // others are recomputed from checkpoints (two record buffers, so that
+  // segment k - 1 is recomputed on a stream of its own while segment k is
+  // reversed).  L is as large as the memory limit allows.
+  size_t free_b = 0, total_b = 0;
+  CK(cudaMemGetInfo(&free_b, &total_b));
+  const size_t reserve = std::max<size_t>(total_b / 64, (size_t)1 << 30);
+  size_t budget = free_b > reserve ? free_b - reserve : 0;
+  if (d->grad_mem_limit >= 0) budget = std::min(budget, (size_t)d->grad_mem_limit);
+  int64_t L = 0;
+  if ((size_t)nseg <= budget / segbytes) {
+    L = nseg;
+  } else {
+    const size_t rec_overhead = 2 * segbytes + 2 * sbytes + (size_t)nseg * sbytes;
+    if (budget > rec_overhead) L = std::min<int64_t>(nseg - 1, (budget - rec_overhead) / segbytes);
+  }
+  DevBuf store;
+  while (L > 0 && dmalloc(&store.p, segbytes * (size_t)L) != cudaSuccess) {
+    cudaGetLastError();
+    L /= 2;
+  }
+  const int64_t k0 = nseg - L;            // segments k >= k0 are stored
+  DevBuf ck, rb[2], rs[2];
+  if (k0 > 0) {
+    if ((s = ck.alloc(sbytes * (size_t)k0)) != LBM_OK) return s;
+    for (auto *b : {&rb[0], &rb[1]})
+      if ((s = b->alloc(segbytes)) != LBM_OK) return s;
+    for (auto &b : rs)
+      if ((s = b.alloc(sbytes)) != LBM_OK) return s;
   }
   struct Sync {   // recompute stream and its two buffer events
     cudaStream_t rs = nullptr;
@@ -1385,7 +1455,7 @@ lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t se
       if (rs) cudaStreamDestroy(rs);
     }
   } sync;
-  if (overlap) {
+  if (k0 > 0) {
     if (cudaStreamCreateWithFlags(&sync.rs, cudaStreamNonBlocking) != cudaSuccess) {
       cudaGetLastError();
       return fail(LBM_ECUDA, "cudaStreamCreate failed");
@@ -1396,15 +1466,13 @@ lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t se
         return fail(LBM_ECUDA, "cudaEventCreate failed");
       }
   }
-  cudaStream_t rstream = overlap ? sync.rs : d->stream;
-  AdjWork w;
-  if ((s = w.alloc(d)) != LBM_OK) return s;
-  if ((s = w.zero_grads(d)) != LBM_OK) return s;
-  for (int b = 0; b < (overlap ? 2 : 1); ++b)
-    CK(cudaMemsetAsync(sgb[b].p, 0, sbytes * (seg + 1), d->stream));
-  auto CKP = [&](int64_t k) { return (void *)((char *)ck.p + k * sbytes); };
-  auto SEGB = [&](int b, int64_t j) {
-    return (void *)((char *)sgb[overlap ? b : 0].p + j * sbytes);
+  auto first_of = [&](int64_t k) { return k * seg; };                       // segment's start state
+  auto last_of = [&](int64_t k) { return std::min<int64_t>((k + 1) * seg, nrec); };
+  auto stored_recs = [&](int64_t k, int64_t n) {                            // R^n of a stored segment
+    return w.recs(d, (char *)store.p + ((size_t)(k - k0) * seg + (size_t)(n - 1 - first_of(k))) * rbytes);
+  };
+  auto buffer_recs = [&](int b, int64_t k, int64_t n) {
+    return w.recs(d, (char *)rb[b].p + (size_t)(n - 1 - first_of(k)) * rbytes);
   };
   const KArgs a = make_args(d);
   const DevGeom g = geom(d);
@@ -1414,154 +1482,107 @@ lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t se
       launch_step<S>(src, dst, g, a, d->variant, st);
     });
   };
-  // Work of a full segment is replayed from CUDA graphs: the same buffers
-  // and launches for every segment (only the checkpoint copied differs).
-  // Graphs are captured on the domain's stream and may be launched on any.
-  struct Graph {
-    cudaGraphExec_t g = nullptr;
-    ~Graph() {
-      if (g) cudaGraphExecDestroy(g);
-    }
-  };
-  auto capture = [&](Graph &gr, auto &&body) -> lbm_status {
-    if (gr.g) return LBM_OK;
-    cudaGraph_t raw_g = nullptr;
-    CK(cudaStreamBeginCapture(d->stream, cudaStreamCaptureModeThreadLocal));
-    body();
-    cudaError_t e = cudaStreamEndCapture(d->stream, &raw_g);
-    if (e != cudaSuccess) return fail(LBM_ECUDA, "adjoint graph capture: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&gr.g, raw_g, 0);
-    cudaGraphDestroy(raw_g);
-    if (e != cudaSuccess) return fail(LBM_ECUDA, "adjoint graph instantiate: %s", cudaGetErrorString(e));
-    return LBM_OK;
-  };
-  Graph g_fwd, g_rec[2], g_rev[2][2];
-  // forward s^0 .. s^{N-1}: segment k starts from SEGB(0, 0) = s^{k seg}
+  // ---- forward sweep s^0 .. s^{nrec}
   std::optional<NvtxRange> nvtx_fwd;
   nvtx_fwd.emplace("pemlbm.grad.forward");
-  CK(cudaMemcpyAsync(CKP(0), d->pop[d->cur], sbytes, cudaMemcpyDeviceToDevice, d->stream));
-  CK(cudaMemcpyAsync(SEGB(0, 0), d->pop[d->cur], sbytes, cudaMemcpyDeviceToDevice, d->stream));
-  for (int64_t k = 0; k + 1 < nck; ++k) {
-    // seg steps SEGB(0, 0) -> ... -> SEGB(0, seg & 1), then back into SEGB(0, 0)
-    auto body = [&] {
-      for (int j = 1; j <= seg; ++j) fwd(SEGB(0, (j - 1) & 1), SEGB(0, j & 1), d->stream);
-      if (seg & 1)
-        cudaMemcpyAsync(SEGB(0, 0), SEGB(0, 1), sbytes, cudaMemcpyDeviceToDevice, d->stream);
-    };
-    if ((s = capture(g_fwd, body)) != LBM_OK) return s;
-    CK(cudaGraphLaunch(g_fwd.g, d->stream));
-    CK(cudaMemcpyAsync(CKP(k + 1), SEGB(0, 0), sbytes, cudaMemcpyDeviceToDevice, d->stream));
+  CK(cudaMemcpyAsync(fs[0].p, d->pop[d->cur], sbytes, cudaMemcpyDeviceToDevice, d->stream));
+  int fc = 0;   // fs[fc] holds the latest state
+  for (int64_t k = 0; k < nseg; ++k) {
+    if (k < k0)
+      CK(cudaMemcpyAsync((char *)ck.p + (size_t)k * sbytes, fs[fc].p, sbytes,
+                         cudaMemcpyDeviceToDevice, d->stream));
+    for (int64_t n = first_of(k) + 1; n <= last_of(k); ++n) {
+      if (k >= k0) step_with_records(d, fs[fc].p, fs[fc ^ 1].p, stored_recs(k, n), d->stream);
+      else fwd(fs[fc].p, fs[fc ^ 1].p, d->stream);
+      fc ^= 1;
+    }
   }
   CK(cudaGetLastError());
-  // Segment k lives in buffer k & 1.  Its recompute (on rstream) waits until
-  // the reverse of segment k + 2, the last user of that buffer, has ended;
-  // its reverse (on the domain's stream) waits until the recompute is done.
-  if (overlap)
-    for (int b = 0; b < 2; ++b) CK(cudaEventRecord(sync.freed[b], d->stream));
-  auto span = [&](int64_t k, int64_t &first, int64_t &last) {
-    first = k * seg;
-    last = std::min<int64_t>(first + seg - 1, N - 1);
-    return last - first + 1 == seg && k != nck - 1;   // a full segment
-  };
+  nvtx_fwd.reset();
+  const void *sN1 = objective == 1 ? fs[fc ^ 1].p : fs[fc].p;   // s^{N-1}
+  // ---- segment recompute (rstream): R^n of segment k into buffer k & 1
   auto recompute = [&](int64_t k) -> lbm_status {
     const int b = (int)(k & 1);
-    int64_t first, last;
-    const bool full = span(k, first, last);
-    if (overlap) CK(cudaStreamWaitEvent(rstream, sync.freed[b], 0));
-    CK(cudaMemcpyAsync(SEGB(b, 0), CKP(k), sbytes, cudaMemcpyDeviceToDevice, rstream));
-    if (full) {
-      auto body = [&] {
-        for (int j = 1; j < seg; ++j) fwd(SEGB(b, j - 1), SEGB(b, j), d->stream);
-      };
-      if ((s = capture(g_rec[b], body)) != LBM_OK) return s;
-      CK(cudaGraphLaunch(g_rec[b].g, rstream));
-    } else {
-      for (int64_t n = first + 1; n <= last; ++n)
-        fwd(SEGB(b, n - 1 - first), SEGB(b, n - first), rstream);
+    CK(cudaStreamWaitEvent(sync.rs, sync.freed[b], 0));
+    CK(cudaMemcpyAsync(rs[0].p, (char *)ck.p + (size_t)k * sbytes, sbytes,
+                       cudaMemcpyDeviceToDevice, sync.rs));
+    int c = 0;
+    for (int64_t n = first_of(k) + 1; n <= last_of(k); ++n) {
+      step_with_records(d, rs[c].p, rs[c ^ 1].p, buffer_recs(b, k, n), sync.rs);
+      c ^= 1;
     }
-    if (overlap) CK(cudaEventRecord(sync.ready[b], rstream));
+    CK(cudaEventRecord(sync.ready[b], sync.rs));
     CK(cudaGetLastError());
     return LBM_OK;
   };
-  nvtx_fwd.reset();
-  // reverse, last segment first
+  if (k0 > 0)
+    for (int b = 0; b < 2; ++b) CK(cudaEventRecord(sync.freed[b], d->stream));
+  // ---- objective and its seed
   NvtxRange nvtx_rev("pemlbm.grad.reverse");
   int cur = 0;
   long long seed_cell = -1;
   bool fresh = true;   // lam[cur] is the seed, held in full (see reverse_step)
-  if ((s = recompute(nck - 1)) != LBM_OK) return s;
-  for (int64_t k = nck - 1; k >= 0; --k) {
-    if (k >= 1 && (s = recompute(k - 1)) != LBM_OK) return s;
+  const lbm_params &p = d->prm;
+  if (objective == 0) {
+    const double i_scale = 4.0 * p.F * p.c_tot * p.dx_cm / p.dt_s;
+    dispatch(d->desc.precision, [&](auto *tag) {
+      using S = std::remove_pointer_t<decltype(tag)>;
+      launch_catalyst<S>(sN1, g, a, i_scale, nullptr, d->colsum, d->dsmall, d->stream);
+      launch_adj_seed_current<S>(sN1, g, a, d->prm.interface_mode == 1, i_scale / d->nx,
+                                 w.ptrs(1), d->stream);   // writes lam[0]
+    });
+    CK(cudaMemcpyAsync(d->hsmall, d->dsmall, sizeof(double), cudaMemcpyDeviceToHost, d->stream));
+    CK(cudaStreamSynchronize(d->stream));
+    if (J) *J = d->hsmall[0] * i_scale / d->nx;
+  } else {
+    if ((s = ensure_scratch(d)) != LBM_OK) return s;
+    dispatch(d->desc.precision, [&](auto *tag) {
+      using S = std::remove_pointer_t<decltype(tag)>;
+      launch_fields<S>(sN1, g, a, d->scratch, d->stream);
+    });
+    std::vector<double> Trow(d->nx);
+    const size_t n = (size_t)d->nx * d->ny;
+    CK(cudaMemcpyAsync(Trow.data(), d->scratch + 3 * n, sizeof(double) * d->nx,
+                       cudaMemcpyDeviceToHost, d->stream));
+    CK(cudaStreamSynchronize(d->stream));
+    int xs = 0;
+    for (int x = 1; x < d->nx; ++x)
+      if (Trow[x] > Trow[xs]) xs = x;       // ties: the smallest x
+    if (J) *J = Trow[xs];
+    seed_cell = xs;                          // row 0
+    // lambda^N = 0 with the seed added by the reverse of step N
+    CK(cudaMemsetAsync(w.lam[0].p, 0, 24 * (size_t)d->plane * w.rsize, d->stream));
+  }
+  // ---- reverse sweep, last segment first
+  if (nseg - 1 < k0 && nseg - 1 >= 0 && (s = recompute(nseg - 1)) != LBM_OK) return s;
+  for (int64_t k = nseg - 1; k >= 0; --k) {
+    if (k - 1 >= 0 && k - 1 < k0 && (s = recompute(k - 1)) != LBM_OK) return s;
+    const bool stored = k >= k0;
     const int b = (int)(k & 1);
-    int64_t first, last;
-    bool full = span(k, first, last);
-    if (overlap) CK(cudaStreamWaitEvent(d->stream, sync.ready[b], 0));
-    if (k == nck - 1) {
-      // objective at step N from s^{N-1}, and its seed lambda^{N-1}
-      const void *sN1 = SEGB(b, N - 1 - first);
-      const lbm_params &p = d->prm;
-      const double i_scale = 4.0 * p.F * p.c_tot * p.dx_cm / p.dt_s;
-      if (objective == 0) {
-        dispatch(d->desc.precision, [&](auto *tag) {
-          using S = std::remove_pointer_t<decltype(tag)>;
-          launch_catalyst<S>(sN1, g, a, i_scale, nullptr, d->colsum, d->dsmall, d->stream);
-          launch_adj_seed_current<S>(sN1, g, a, d->prm.interface_mode == 1, i_scale / d->nx,
-                                     w.ptrs(1), d->stream);   // writes lam[0]
-        });
-        CK(cudaMemcpyAsync(d->hsmall, d->dsmall, sizeof(double), cudaMemcpyDeviceToHost, d->stream));
-        CK(cudaStreamSynchronize(d->stream));
-        if (J) *J = d->hsmall[0] * i_scale / d->nx;
+    if (!stored) CK(cudaStreamWaitEvent(d->stream, sync.ready[b], 0));
+    for (int64_t n = last_of(k); n >= first_of(k) + 1; --n) {
+      const RecBufs r = stored ? stored_recs(k, n) : buffer_recs(b, k, n);
+      if (objective == 1 && n == N) {
+        reverse_step(d, w, cur, r, seed_cell, true);   // lam[1] = lambda^{N-1}
       } else {
-        if ((s = ensure_scratch(d)) != LBM_OK) return s;
-        dispatch(d->desc.precision, [&](auto *tag) {
-          using S = std::remove_pointer_t<decltype(tag)>;
-          launch_fields<S>(sN1, g, a, d->scratch, d->stream);
-        });
-        std::vector<double> Trow(d->nx);
-        const size_t n = (size_t)d->nx * d->ny;
-        CK(cudaMemcpyAsync(Trow.data(), d->scratch + 3 * n, sizeof(double) * d->nx,
-                           cudaMemcpyDeviceToHost, d->stream));
-        CK(cudaStreamSynchronize(d->stream));
-        int xs = 0;
-        for (int x = 1; x < d->nx; ++x)
-          if (Trow[x] > Trow[xs]) xs = x;       // ties: the smallest x
-        if (J) *J = Trow[xs];
-        seed_cell = xs;                          // row 0
-        // lambda^{N-1}: the seed pulled through the reverse of the pull
-        CK(cudaMemsetAsync(w.lam[0].p, 0, 24 * (size_t)d->plane * (fp64(d) ? 8 : 4), d->stream));
-        reverse_step(d, w, 0, sN1, seed_cell, true);   // lam[1] = lambda^{N-1}
-        cur = 1;
-        fresh = false;
+        reverse_step(d, w, cur, r, -1, fresh);
       }
+      fresh = false;
+      cur ^= 1;
     }
-    const int64_t ntop = (k == nck - 1) ? N - 1 : last + 1;
-    if (fresh) full = false;   // the captured segment expects a pushed lambda
-    if (full) {
-      const int c0 = cur;
-      auto body = [&] {
-        int cc = c0;
-        for (int64_t n = ntop; n >= first + 1; --n) {
-          reverse_step(d, w, cc, SEGB(b, n - 1 - first), -1);
-          cc ^= 1;
-        }
-        fold_grads(d, w);
-      };
-      if ((s = capture(g_rev[c0][b], body)) != LBM_OK) return s;
-      CK(cudaGraphLaunch(g_rev[c0][b].g, d->stream));
-      cur ^= (int)(seg & 1);
-    } else {
-      for (int64_t n = ntop; n >= first + 1; --n) {
-        reverse_step(d, w, cur, SEGB(b, n - 1 - first), -1, fresh);
-        fresh = false;
-        cur ^= 1;
-      }
-      fold_grads(d, w);
-    }
-    if (overlap) CK(cudaEventRecord(sync.freed[b], d->stream));
+    fold_grads(d, w);
+    if (!stored) CK(cudaEventRecord(sync.freed[b], d->stream));
     CK(cudaGetLastError());
   }
   finish_lambda(d, w, cur);   // adds the last step's outlet term to gphi
   return copy_grads_out(d, w, dphi, dK, dD_O2, du_in, on_device == 1);
+}
+
+lbm_status lbm_set_grad_memory(lbm_domain *d, int64_t bytes) {
+  if (!d) return fail(LBM_EINVAL, "null domain");
+  if (bytes < -1) return fail(LBM_EINVAL, "bytes must be -1 (automatic) or >= 0");
+  d->grad_mem_limit = bytes;
+  return LBM_OK;
 }
 
 }  // extern "C"

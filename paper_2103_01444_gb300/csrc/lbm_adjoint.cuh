@@ -8,18 +8,23 @@
 // 8, 10) with the catalyst terms (Eq. 12-17).  Every plain link (y, q) of
 // s^{n-1} has exactly one consumer, the fluid cell y + e_q, so the transpose
 // of the pull is a push: the consumer writes the adjoint of what it pulled
-// straight into lambda^{n-1}(y, q).  Two kernels per step, run
-// concurrently (they write disjoint links):
-//   k_adj_interior (one thread per cell; cells without edge bits): recomputes
-//     the forward update of x from s^{n-1}, back-propagates lambda^n(x)
-//     through C_x, pushes the 24 link adjoints to the source cells and
-//     accumulates the parameter adjoints of x.  Catalyst cells of the
-//     volumetric mode also read their own state; that adjoint goes to O(x).
+// straight into lambda^{n-1}(y, q).  C_x is linear in the pulled values
+// once the velocity is known, so the reverse needs from the forward step
+// only its reverse records (RecPtrs, written by the step kernel's REC
+// instantiation): per cell the Eq. 8 auxiliary velocity, the scalar sums
+// and the O2 flux moments; per edge cell its pulled values; per edge or
+// catalyst cell its own sums.  Two kernels per step, run concurrently
+// (they write disjoint links):
+//   k_adj_interior (one thread per cell; cells without edge bits): back-
+//     propagates lambda^n(x) through C_x from the cell record, pushes the 24
+//     link adjoints to the source cells and accumulates the parameter
+//     adjoints of x.  Catalyst cells of the volumetric mode also read their
+//     own state (through their own record); that adjoint goes to O(x).
 //     Solid cells zero their own lambda^{n-1}.
 //   k_adj_edge (one warp per listed edge cell): the same for cells with
-//     boundary links; the adjoint of values taken from the cell's own state
-//     goes to O(x, q), a virtual column's uses of the cells above and below
-//     to V.
+//     boundary links, from their pulled values; the adjoint of values taken
+//     from the cell's own state goes to O(x, q), a virtual column's uses of
+//     the cells above and below to V.
 // At a cell that uses its own state, lambda^{n-1}(y, q) is therefore split:
 // the pushed value (only if y + e_q is a fluid consumer) + O(y, q) + the
 // virtual-column terms.  The next reverse step adds the parts when it reads lambda
@@ -81,17 +86,16 @@ template <typename R> struct AdjBufs {
 
 // Adjoint of the D2Q5 collision of scalar s (collide_scalar).  Given the
 // output adjoints lo[5], accumulates into ld[5] (pulled values), lux, luy,
-// and the adjoints of the source, b, w1 and q1.
+// and the adjoints of the source, b, w1 and q1.  The collision is linear in
+// the populations, so its reverse needs of them only the deviation sum
+// Cdev and the flux moments n1, n2 (the latter for the q1 adjoint).
 template <typename R>
 __device__ __forceinline__ void collide_scalar_rev(const KArgsT<R> &a, const MatCoef<R> &mc, int s,
-                                                   R ux, R uy, R Cdev, const R d[5], R srcv,
+                                                   R ux, R uy, R Cdev, R n1, R n2, R srcv,
                                                    const R lo[5], R ld[5], R &lux, R &luy,
                                                    R &lsrc, R &lb, R &lw1, R &lq1) {
   const R Q1 = mc.q1[s], Q3 = R(a.Q3), b = mc.b[s], w1 = mc.w1[s], w0 = R(1) - R(4) * w1;
   const R C = Cdev + R(a.Cref[s]), Ca = Cdev + R(a.adv_off[s]);
-  const R n1 = d[1] - d[3], n2 = d[2] - d[4];
-  const R e13 = d[1] + d[3], e24 = d[2] + d[4];
-  const R n3 = R(-4) * d[0] + (e13 + e24);
   // outputs: o0 = 0.2 (n0 - n3') + w0 src; o1,3 = ev +- 0.25 n4' ... (see forward)
   const R lex = lo[1] + lo[3], ley = lo[2] + lo[4];
   const R ln1p = R(0.5) * (lo[1] - lo[3]), ln2p = R(0.5) * (lo[2] - lo[4]);
@@ -116,28 +120,25 @@ __device__ __forceinline__ void collide_scalar_rev(const KArgsT<R> &a, const Mat
   ld[3] += -ln1 + le13 + lCdev;
   ld[2] += ln2 + le24 + lCdev;
   ld[4] += -ln2 + le24 + lCdev;
-  (void)n3;
 }
 
 // Adjoint of collide_flow + the flow part of macros (Eq. 1, 3-8).  Given the
 // output adjoints lo[9] and the adjoints lux, luy of the velocity coming
 // from the scalar collisions, accumulates ld[9] and the adjoints of phi
-// (direct), darcy, forch, l0, l1 and 1/phi.
+// (direct), darcy, forch, l0, l1 and 1/phi.  The collision is linear in the
+// populations once u is known, so the reverse needs of them only the
+// auxiliary velocity (vx, vy) of Eq. 8 (body-force half-step included).
 template <typename R>
-__device__ __forceinline__ void flow_rev(const KArgsT<R> &a, const MatCoef<R> &mc, const R d[9],
+__device__ __forceinline__ void flow_rev(const KArgsT<R> &a, const MatCoef<R> &mc, R vx, R vy,
                                          const R lo[9], R lux_in, R luy_in, R ld[9], R &lphi,
                                          R &ldarcy, R &lforch, R &ll0, R &ll1, R &lip) {
   const R sn = R(a.s_nu), sq = R(a.s_q), g = R(a.body_g), ip = mc.inv_phi;
-  // ---- forward recomputation of the macroscopic values (macros)
-  const R vx = d[1] - d[3] + d[5] - d[6] - d[7] + d[8] + R(0.5) * mc.phi * g;
-  const R vy = d[2] - d[4] + d[5] + d[6] - d[7] - d[8];
+  // ---- the macroscopic values of the forward step (macros)
   const R vn = sqrt(vx * vx + vy * vy);
   const R rr = sqrt(mc.l0 * mc.l0 + mc.l1 * vn);
   const R den = mc.l0 + rr;
   const R ux = vx / den, uy = vy / den;
-  const R s18 = ((d[1] + d[3]) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8]));
   const R u2 = ux * ux + uy * uy, un = sqrt(u2);
-  const R P = R(0.6) * s18 - R(0.4) * u2 * ip;
   const R Fx = -mc.darcy * ux - mc.forch * un * ux + mc.phi * g;
   const R Fy = -mc.darcy * uy - mc.forch * un * uy;
   const R uF = ux * Fx + uy * Fy;
@@ -295,14 +296,9 @@ template <typename R> __device__ __forceinline__ R dinlet_du(const KArgsT<R> &a,
 // of a warp reverses one link of the same cell (shared memory).
 template <typename R> __device__ __forceinline__ void acc_shared(R *p, R v) { atomicAdd(p, v); }
 
-// Columns whose cells feed a virtual column of the previous step: the outlet
-// (x = nx - 1) and, with the pressure inlet, x = 0.  Their cross-row
-// adjoints live in B.V as [side][down, up][10][ny], side 0 the outlet and 1
-// the inlet (vcol_side gives the offset of the side in units of ny).
-template <typename R>
-__device__ __forceinline__ bool has_vcol(const KArgsT<R> &a, int x) {
-  return !a.periodic && (x == a.nx - 1 || (x == 0 && a.inlet_pressure));
-}
+// Cross-row adjoints of the virtual columns (has_vcol) live in B.V as
+// [side][down, up][10][ny], side 0 the outlet and 1 the inlet (vcol_side
+// gives the offset of the side in units of ny).
 template <typename R>
 __device__ __forceinline__ int vcol_side(const KArgsT<R> &a, int x) {
   return x == a.nx - 1 ? 0 : 20;
@@ -313,8 +309,8 @@ __device__ __forceinline__ int vcol_side(const KArgsT<R> &a, int x) {
 // (plain link, `out`), or goes to Oacc (own populations), the virtual
 // cells' adjoints (outlet, pressure inlet) or the inlet drive.  Oacc, Vdn, Vup and lip_own
 // are shared by the lanes of the cell; lU is the lane's own.
-template <typename S, typename R>
-__device__ __forceinline__ void pull_flow_rev(const Pops<S> &src, const KArgsT<R> &a,
+template <typename R>
+__device__ __forceinline__ void pull_flow_rev(const RecPtrs<R> &rp, const KArgsT<R> &a,
                                               const uint8_t *__restrict__ mask,
                                               const uint16_t *__restrict__ mid,
                                               const MatCoef<R> *__restrict__ pal, int i, int x,
@@ -345,11 +341,11 @@ __device__ __forceinline__ void pull_flow_rev(const Pops<S> &src, const KArgsT<R
         acc_shared(&Oacc[opi], lam);
         return;
       }
-      R d[9];
-#pragma unroll
-      for (int k = 0; k < 9; ++k) d[k] = R(src.at(k, vx, sy));
-      const R jx = d[1] - d[3] + d[5] - d[6] - d[7] + d[8];
-      const R jy = d[2] - d[4] + d[5] + d[6] - d[7] - d[8];
+      // the momentum of the source cell's own flow populations (its own
+      // record; a solid cell keeps the rest state, zero deviations)
+      const int sv = rp.slot[vc];
+      const R jx = sv >= 0 ? rp.own[4LL * sv + 2] : R(0);
+      const R jy = sv >= 0 ? rp.own[4LL * sv + 3] : R(0);
       const R ipv = pal[mid[vc]].inv_phi;
       const R ldP = lam9<R>(i) * lam;
       if (in) lU += ldP;                               // d value / d dp_in
@@ -426,25 +422,42 @@ __device__ __forceinline__ void pull_scalar_rev(const KArgsT<R> &a, const uint8_
   out[(long long)(q + i) * a.plane + sc] = lam;
 }
 
+// Loads the 8-value cell record of cell c (two 4-value groups).
+template <typename R> struct CellRec { R v[8]; };
+__device__ __forceinline__ CellRec<float> ld_cell_rec(const float *r) {
+  const float4 a = __ldg(reinterpret_cast<const float4 *>(r));
+  const float4 b = __ldg(reinterpret_cast<const float4 *>(r) + 1);
+  return CellRec<float>{{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w}};
+}
+__device__ __forceinline__ CellRec<double> ld_cell_rec(const double *r) {
+  CellRec<double> o;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double2 t = __ldg(reinterpret_cast<const double2 *>(r) + k);
+    o.v[2 * k] = t.x;
+    o.v[2 * k + 1] = t.y;
+  }
+  return o;
+}
+
 // Reverse of the update of one fluid interior cell (no edge bits; see the
-// file comment).  Catalyst cells of the volumetric mode also read their
-// own state (the sink) and leave that adjoint in O.
-template <typename S>
-__device__ __forceinline__ void adj_interior_cell(
-    const S *__restrict__ src_p, const uint16_t *__restrict__ mid,
-    const MatCoef<typename Real<S>::type> *__restrict__ pal,
-    const KArgsT<typename Real<S>::type> &a, int fickian,
-    const AdjBufs<typename Real<S>::type> &B, int x, int y, long long c, uint8_t m) {
-  using R = typename Real<S>::type;
+// file comment) from its cell record.  Catalyst cells of the volumetric
+// mode also read their own state (the sink, from their own record) and
+// leave that adjoint in O.
+template <typename R>
+__device__ __forceinline__ void adj_interior_cell(const RecPtrs<R> &rp,
+                                                  const uint16_t *__restrict__ mid,
+                                                  const MatCoef<R> *__restrict__ pal,
+                                                  const KArgsT<R> &a, int fickian,
+                                                  const AdjBufs<R> &B, long long c, uint8_t m) {
   const long long P = a.plane, W = a.nxp;
-  const Pops<S> src{src_p, a.plane, a.nxp};
   const MatCoef<R> mc = pal[mid[c]];
   // this cell's segment gradients, read before any store of the thread so
-  // that their latency overlaps the population loads (no other thread of
-  // the launch touches them)
+  // that their latency overlaps the record loads (no other thread of the
+  // launch touches them)
   R gacc[3] = {B.gphi[c], B.gK[c], B.gD[c]};
-  Cell<R> cell;
-  load_interior<S, R>(src, a, x, y, cell);
+  const CellRec<R> rec = ld_cell_rec(rp.cell + 8 * c);
+  const R vx = rec.v[0], vy = rec.v[1], n1 = rec.v[5], n2 = rec.v[6];
   const bool vol = a.mode == 1 && (m & REG_MASK) == REG_CATALYST;
   // lambda^n of link q: every link of an interior cell is pushed; a
   // catalyst cell adds the own-use adjoint the previous step left in O_in
@@ -456,8 +469,9 @@ __device__ __forceinline__ void adj_interior_cell(
   // forward reaction terms (kept for the reverse)
   R theta = 0, k = 0, ka = 0, Cv = 0, S_vol = 0;
   if (vol) {
-    theta = own_sum<S, R>(src, 0, x, y) + a.theta0;
-    Cv = own_sum<S, R>(src, 1, x, y) + R(a.Cref[1]);
+    const R *ow = rp.own + 4LL * rp.slot[c];
+    theta = ow[0];
+    Cv = ow[1];
     k = rate<R>(a, R(a.kA_vol), theta);
     ka = rate_anodic<R>(a, R(a.kA_vol_a), theta);
     S_vol = (ka - k * Cv) / (R(1) + k);
@@ -470,7 +484,9 @@ __device__ __forceinline__ void adj_interior_cell(
   R lphi = 0, ldarcy = 0, lforch = 0, ll0 = 0, ll1 = 0, lip = 0;
   R lb[3] = {0, 0, 0}, lw1[3] = {0, 0, 0}, lq1[3] = {0, 0, 0}, lsrc[3] = {0, 0, 0};
   {
-    const Macro<R> u = macros<R>(a, mc, cell);
+    const R vn = sqrt(vx * vx + vy * vy);
+    const R den = mc.l0 + sqrt(mc.l0 * mc.l0 + mc.l1 * vn);
+    const R ux = vx / den, uy = vy / den;
     const R srcv[3] = {-S_vol * R(a.hpo) * mc.inv_sigma, S_vol, R(-2) * S_vol};
     R lux = 0, luy = 0;
 #pragma unroll
@@ -481,8 +497,9 @@ __device__ __forceinline__ void adj_interior_cell(
         lo[i] = lam_at(9 + 5 * s + i);
         lcg[i] = R(0);
       }
-      collide_scalar_rev<R>(a, mc, s, u.ux, u.uy, u.C[s], cell.g[s], srcv[s], lo, lcg, lux, luy,
-                            lsrc[s], lb[s], lw1[s], lq1[s]);
+      collide_scalar_rev<R>(a, mc, s, ux, uy, rec.v[2 + s], s == 1 ? n1 : R(0),
+                            s == 1 ? n2 : R(0), srcv[s], lo, lcg, lux, luy, lsrc[s], lb[s], lw1[s],
+                            lq1[s]);
 #pragma unroll
       for (int i = 0; i < 5; ++i)
         B.lam_out[(9 + 5 * s + i) * P + c - ey9(i) * W - ex9(i)] = lcg[i];
@@ -490,7 +507,7 @@ __device__ __forceinline__ void adj_interior_cell(
     R lo[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) lo[i] = lam_at(i);
-    flow_rev<R>(a, mc, cell.f, lo, lux, luy, lcf, lphi, ldarcy, lforch, ll0, ll1, lip);
+    flow_rev<R>(a, mc, vx, vy, lo, lux, luy, lcf, lphi, ldarcy, lforch, ll0, ll1, lip);
   }
 #pragma unroll
   for (int i = 0; i < 9; ++i) B.lam_out[i * P + c - ey9(i) * W - ex9(i)] = lcf[i];
@@ -515,14 +532,10 @@ __device__ __forceinline__ void adj_interior_cell(
 
 // Cells without edge bits, one thread per cell (grid over the lattice);
 // solid cells zero their own lambda^{n-1} (nothing is ever pushed there).
-template <typename S>
+template <typename R>
 __global__ void __launch_bounds__(128, 8)
-k_adj_interior(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
-               const uint16_t *__restrict__ mid,
-               const MatCoef<typename Real<S>::type> *__restrict__ pal,
-               KArgsT<typename Real<S>::type> a, int fickian,
-               AdjBufs<typename Real<S>::type> B) {
-  using R = typename Real<S>::type;
+k_adj_interior(RecPtrs<R> rp, const uint8_t *__restrict__ mask, const uint16_t *__restrict__ mid,
+               const MatCoef<R> *__restrict__ pal, KArgsT<R> a, int fickian, AdjBufs<R> B) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   if (x >= a.nx || y >= a.ny) return;
   const long long c = (long long)y * a.nxp + x;
@@ -533,7 +546,7 @@ k_adj_interior(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
     return;
   }
   if (m & M_EDGE) return;
-  adj_interior_cell<S>(src_p, mid, pal, a, fickian, B, x, y, c, m);
+  adj_interior_cell<R>(rp, mid, pal, a, fickian, B, c, m);
 }
 
 // Fluid cells with edge bits, one warp per entry of `cells` (linear cell
@@ -547,15 +560,12 @@ constexpr int kEdgeWarps = 4, kEdgeMinBlocks = 1;
 // Launch order of a reverse step: the edge kernel before (true) or after
 // the interior kernel; the first one's blocks are dispatched first.
 constexpr bool kAdjEdgeFirst = true;
-template <typename S>
+template <typename R>
 __global__ void __launch_bounds__(32 * kEdgeWarps, kEdgeMinBlocks)
-k_adj_edge(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
-           const uint16_t *__restrict__ mid,
-           const MatCoef<typename Real<S>::type> *__restrict__ pal,
-           KArgsT<typename Real<S>::type> a, int fickian, AdjBufs<typename Real<S>::type> B,
+k_adj_edge(RecPtrs<R> rp, const uint8_t *__restrict__ mask, const uint16_t *__restrict__ mid,
+           const MatCoef<R> *__restrict__ pal, KArgsT<R> a, int fickian, AdjBufs<R> B,
            const long long *__restrict__ cells, int ncells, long long seed_cell,
            int lam_complete) {
-  using R = typename Real<S>::type;
   struct Shared {
     R pulled[24];   // post-stream values of the cell
     R lin[24];      // lambda^n of the cell
@@ -572,19 +582,14 @@ k_adj_edge(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
   const long long c = cells[t], P = a.plane, W = a.nxp;
   const int y = (int)(c / a.nxp), x = (int)(c - (long long)y * a.nxp);
   const uint8_t m = mask[c];
-  const Pops<S> src{src_p, a.plane, a.nxp};
   const MatCoef<R> mc = pal[mid[c]];
   const bool vcol = has_vcol(a, x);
   const int vs = vcol_side(a, x);
-  // ---- phase 1 (lane q): pull link q, read lambda^n of link q
+  // ---- phase 1 (lane q): the pulled value of link q (the cell's record;
+  // its slot is its index t in the list), lambda^n of link q
   if (lane < 24) {
-    const int q = lane, l = plane_link(q);
-    R v = R(ldp<false>(src_p + pop_index(q, c - ey9(l) * W - ex9(l), P)));   // interior pull
-    if (l != 0) {
-      if (q < 9) v = pull_flow_edge<S, R>(src, a, mask, mid, pal, q, x, y, m, v);
-      else v = pull_scalar_edge<S, R>(src, a, mask, mc, (q - 9) / 5, l, x, y, m, v);
-    }
-    sh.pulled[q] = v;
+    const int q = lane;
+    sh.pulled[q] = rp.pulled[24LL * t + q];
     const uint32_t pbits = lam_complete ? 0xffffffffu : B.pushed[t];
     R lv = ((pbits >> q) & 1u) ? ld_r(B.lam + q * P + c) : R(0);
     lv += ld_r(B.O_in + q * P + c);
@@ -616,7 +621,7 @@ k_adj_edge(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
     const bool surf = a.mode == 0 && (m & M_YLO);
     const bool vol = a.mode == 1 && (m & REG_MASK) == REG_CATALYST;
     R theta = 0, k = 0, ka = 0, kappa = 0, gd = 0, Cv = 0, S_vol = 0;
-    if (surf || vol) theta = own_sum<S, R>(src, 0, x, y) + a.theta0;
+    if (surf || vol) theta = rp.own[4LL * t];
     if (surf) {
       k = rate<R>(a, R(a.kA_surf), theta);
       ka = rate_anodic<R>(a, R(a.kA_surf_a), theta);
@@ -628,7 +633,7 @@ k_adj_edge(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
       cell.g[2][2] += R(2) * Jv;
     }
     if (vol) {
-      Cv = own_sum<S, R>(src, 1, x, y) + R(a.Cref[1]);
+      Cv = rp.own[4LL * t + 1];
       k = rate<R>(a, R(a.kA_vol), theta);
       ka = rate_anodic<R>(a, R(a.kA_vol_a), theta);
       S_vol = (ka - k * Cv) / (R(1) + k);
@@ -649,13 +654,14 @@ k_adj_edge(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
           lo[i] = sh.lin[9 + 5 * s + i];
           lcg[s][i] = R(0);
         }
-        collide_scalar_rev<R>(a, mc, s, u.ux, u.uy, u.C[s], cell.g[s], srcv[s], lo, lcg[s], lux,
-                              luy, lsrc[s], lb[s], lw1[s], lq1[s]);
+        collide_scalar_rev<R>(a, mc, s, u.ux, u.uy, u.C[s], cell.g[s][1] - cell.g[s][3],
+                              cell.g[s][2] - cell.g[s][4], srcv[s], lo, lcg[s], lux, luy,
+                              lsrc[s], lb[s], lw1[s], lq1[s]);
       }
       R lo[9];
 #pragma unroll
       for (int i = 0; i < 9; ++i) lo[i] = sh.lin[i];
-      flow_rev<R>(a, mc, cell.f, lo, lux, luy, lcf, lphi, ldarcy, lforch, ll0, ll1, lip);
+      flow_rev<R>(a, mc, u.vx, u.vy, lo, lux, luy, lcf, lphi, ldarcy, lforch, ll0, ll1, lip);
     }
     if (vol) {   // volumetric sources (-S h / sigma, S, -2 S)
       const R lS = -R(a.hpo) * mc.inv_sigma * lsrc[0] + lsrc[1] - R(2) * lsrc[2];
@@ -701,8 +707,8 @@ k_adj_edge(const S *__restrict__ src_p, const uint8_t *__restrict__ mask,
   if (lane < 24) {
     const int q = lane;
     if (q < 9) {
-      pull_flow_rev<S, R>(src, a, mask, mid, pal, q, x, y, m, sh.lpull[q], B.lam_out, sh.O,
-                          sh.V, sh.V + 10, &sh.lip, lU);
+      pull_flow_rev<R>(rp, a, mask, mid, pal, q, x, y, m, sh.lpull[q], B.lam_out, sh.O, sh.V,
+                       sh.V + 10, &sh.lip, lU);
     } else {
       const int s = (q - 9) / 5;
       pull_scalar_rev<R>(a, mask, mc, s, q - 9 - 5 * s, x, y, m, sh.lpull[q], B.lam_out, sh.O,

@@ -279,6 +279,33 @@ template <typename F> struct BatchCaseT {
 };
 using BatchCase = BatchCaseT<double>;
 
+// Reverse records of one forward step: what the transpose of the step
+// (the discrete adjoint) needs from the state the step started from, so
+// that a reverse sweep reads these instead of stepping forward again.
+//   cell[8 c + 0..7]: per cell, the Eq. 8 auxiliary velocity (vx, vy), the
+//     three deviation sums of the post-stream scalars (T, O2, H2O) and the
+//     O2 flux moments n1, n2 of Eq. 10 (after the surface reaction), then
+//     one unused value: two 4-value groups;
+//   own[4 s + 0..3]: per listed cell s (fluid cells with edge bits, then
+//     catalyst cells of the volumetric mode): T - T_in and C_O2 of the
+//     cell's own state (the reaction's arguments, Eq. 13-17) and the
+//     momentum (jx, jy) of its own flow populations (what a virtual column
+//     of the outlet or of the pressure inlet takes from it);
+//   pulled[24 s + q]: per edge cell s, its 24 post-stream values before the
+//     surface reaction (population order of pop_index);
+//   slot[c]: the listed index of cell c, -1 for other cells.
+template <typename R> struct RecPtrs {
+  R *cell, *own, *pulled;
+  const int *slot;
+};
+
+// Columns whose cells feed a virtual column: the outlet (x = nx - 1) and,
+// with the pressure inlet, x = 0.
+template <typename R>
+__host__ __device__ __forceinline__ bool has_vcol(const KArgsT<R> &a, int x) {
+  return !a.periodic && (x == a.nx - 1 || (x == 0 && a.inlet_pressure));
+}
+
 // Velocity sets, Eq. 2 and Eq. 9 orders (folded by the compiler once the
 // loops over links are unrolled).
 #define EX9_TAB {0, 1, 0, -1, 0, 1, -1, -1, 1}
@@ -592,6 +619,7 @@ __device__ __forceinline__ void pull_cell(const Pops<S, CG> &src, const KArgsT<R
 template <typename R> struct Macro {
   R ux, uy, Pdev;   // velocity; phi p - rho0/3
   R C[3];           // deviation sums (value - Cref)
+  R vx, vy;         // auxiliary velocity of Eq. 8 (the reverse records keep it)
 };
 
 // Body force per unit mass at a cell whose T deviation sum is CT: the
@@ -618,6 +646,8 @@ __device__ __forceinline__ Macro<R> macros(const KArgsT<R> &a, const MatCoef<R> 
   if constexpr (X) vy += R(0.5) * mc.phi * Gy;
   R vn = sqrt(vx * vx + vy * vy);
   R den = mc.l0 + sqrt(mc.l0 * mc.l0 + mc.l1 * vn);
+  r.vx = vx;
+  r.vy = vy;
   r.ux = vx / den;
   r.uy = vy / den;
   R s18 = ((d[1] + d[3]) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8]));

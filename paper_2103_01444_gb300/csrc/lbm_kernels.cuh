@@ -504,25 +504,25 @@ void launch_adj_fold(const DevGeom &g, const KArgs &a, const AdjPtrs &b, cudaStr
 // are events, so the step can be captured into a graph (two parallel
 // branches).
 template <typename S>
-void launch_adj_step(const void *src, const DevGeom &g, const KArgs &a, int fickian,
+void launch_adj_step(const RecBufs &r, const DevGeom &g, const KArgs &a, int fickian,
                      const AdjPtrs &b, long long seed_cell, int lam_complete, cudaStream_t st,
                      cudaStream_t side, cudaEvent_t fork, cudaEvent_t join) {
   using R = typename Real<S>::type;
   const KArgsT<R> an = narrow_args<R>(a);
   const AdjBufs<R> B = adj_bufs<R>(b);
   const MatCoef<R> *pal = (const MatCoef<R> *)g.pal;
+  const RecPtrs<R> rp{(R *)r.cell, (R *)r.own, (R *)r.pulled, r.slot};
   auto edge = [&] {
     if (b.n_edge <= 0) return;
     cudaStreamWaitEvent(side, fork, 0);
-    k_adj_edge<S><<<(b.n_edge + kEdgeWarps - 1) / kEdgeWarps, 32 * kEdgeWarps, 0, side>>>(
-        (const S *)src, g.mask, g.mid, pal, an, fickian, B, b.cells, b.n_edge, seed_cell,
-        lam_complete);
+    k_adj_edge<R><<<(b.n_edge + kEdgeWarps - 1) / kEdgeWarps, 32 * kEdgeWarps, 0, side>>>(
+        rp, g.mask, g.mid, pal, an, fickian, B, b.cells, b.n_edge, seed_cell, lam_complete);
     cudaEventRecord(join, side);
   };
   if (b.n_edge > 0) cudaEventRecord(fork, st);
   if (kAdjEdgeFirst) edge();
-  k_adj_interior<S><<<dim3((a.nx + 127) / 128, a.ny), 128, 0, st>>>((const S *)src, g.mask, g.mid,
-                                                                    pal, an, fickian, B);
+  k_adj_interior<R><<<dim3((a.nx + 127) / 128, a.ny), 128, 0, st>>>(rp, g.mask, g.mid, pal, an,
+                                                                    fickian, B);
   if (!kAdjEdgeFirst) edge();
   if (b.n_edge > 0) cudaStreamWaitEvent(st, join, 0);
 }
@@ -647,7 +647,9 @@ void launch_set_state(void *pop, const DevGeom &g, const KArgs &a, const double 
   template cudaError_t launch_batch_persistent<S>(const BatchCase *, const int *, int, int, int, \
                                                   unsigned *, int *, long long, cudaStream_t);  \
   template void batch_upload<S>(const BatchCase *, int, void *, void *, cudaStream_t);         \
-  template void launch_adj_step<S>(const void *, const DevGeom &, const KArgs &, int,              \
+  template void launch_step_rec<S>(const void *, void *, const DevGeom &, const KArgs &,         \
+                                   const RecBufs &, cudaStream_t);                               \
+  template void launch_adj_step<S>(const RecBufs &, const DevGeom &, const KArgs &, int,          \
                                    const AdjPtrs &, long long, int, cudaStream_t, cudaStream_t,    \
                                    cudaEvent_t, cudaEvent_t);                                      \
   template void launch_adj_finish<S>(const DevGeom &, const KArgs &, const AdjPtrs &,            \

@@ -42,6 +42,14 @@ struct DevGeom {
 };
 
 template <typename S> void launch_step(const void *src, void *dst, const DevGeom &g, const KArgs &a, int variant, cudaStream_t st);
+// Reverse records of one step (device pointers, the arithmetic type of the
+// domain; layout as RecPtrs in lbm_core.cuh).
+struct RecBufs {
+  void *cell, *own, *pulled;
+  const int *slot;
+};
+// One step src -> dst that also writes its reverse records.
+template <typename S> void launch_step_rec(const void *src, void *dst, const DevGeom &g, const KArgs &a, const RecBufs &r, cudaStream_t st);
 template <typename S> void launch_fields(const void *src, const DevGeom &g, const KArgs &a, double *out, cudaStream_t st);
 template <typename S> void launch_balances(const void *src, const DevGeom &g, const KArgs &a, double *out, cudaStream_t st);
 template <typename S> void launch_catalyst(const void *src, const DevGeom &g, const KArgs &a, double i_scale, float *profile, double *colsum, double *out, cudaStream_t st);
@@ -73,7 +81,7 @@ struct AdjPtrs {
   const uint32_t *pushed;    // per edge cell: links that have a fluid consumer
   int n_edge, n_own;         // edge cells; all own-use cells
 };
-template <typename S> void launch_adj_step(const void *src, const DevGeom &g, const KArgs &a, int fickian, const AdjPtrs &b, long long seed_cell, int lam_complete, cudaStream_t st, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join);
+template <typename S> void launch_adj_step(const RecBufs &r, const DevGeom &g, const KArgs &a, int fickian, const AdjPtrs &b, long long seed_cell, int lam_complete, cudaStream_t st, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join);
 template <typename S> void launch_adj_finish(const DevGeom &g, const KArgs &a, const AdjPtrs &b, cudaStream_t st);
 template <typename S> void launch_adj_fold(const DevGeom &g, const KArgs &a, const AdjPtrs &b, cudaStream_t st);
 template <typename S> void launch_adj_seed_current(const void *src, const DevGeom &g, const KArgs &a, int fickian, double weight, const AdjPtrs &b, cudaStream_t st);

@@ -8,17 +8,51 @@
 
 namespace pemlbm {
 
+// Own-state and pulled records of a listed cell (see RecPtrs): the values
+// the reverse of its reaction and of its boundary links needs.  `cell`
+// holds the post-stream values before the surface reaction.
+template <typename S, typename R, bool CG>
+__device__ __forceinline__ void write_listed_records(const Pops<S, CG> &src, const KArgsT<R> &a,
+                                                     const RecPtrs<R> &rp, uint8_t m, long long c,
+                                                     int x, int y, const Cell<R> &cell) {
+  const bool cat = a.mode == 1 && (m & REG_MASK) == REG_CATALYST;
+  if (!(m & M_EDGE) && !cat) return;
+  const long long sl = rp.slot[c];
+  R th = 0, cv = 0, jx = 0, jy = 0;
+  if ((a.mode == 0 && (m & M_YLO)) || cat) th = own_sum<S, R, CG>(src, 0, x, y) + a.theta0;
+  if (cat) cv = own_sum<S, R, CG>(src, 1, x, y) + R(a.Cref[1]);
+  if (has_vcol(a, x)) {
+    R d[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) d[k] = R(src.at(k, x, y));
+    jx = d[1] - d[3] + d[5] - d[6] - d[7] + d[8];
+    jy = d[2] - d[4] + d[5] + d[6] - d[7] - d[8];
+  }
+  stq(rp.own + 4 * sl, th, cv, jx, jy);
+  if (m & M_EDGE) {
+    R *p = rp.pulled + 24 * sl;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) p[i] = cell.f[i];
+#pragma unroll
+    for (int s = 0; s < 3; ++s)
+#pragma unroll
+      for (int i = 0; i < 5; ++i) p[9 + 5 * s + i] = cell.g[s][i];
+  }
+}
+
 // ------------------------------------------------------------- step (K1)
 // One coupled update of cell (x, y): src -> dst.  Shared by the single-
 // domain step and the batched steps.  X: closed ends, fixed wall values and
-// buoyancy compiled in (see pull_flow_edge).
-template <typename S, bool CG = false, bool SR = false, bool X = false>
+// buoyancy compiled in (see pull_flow_edge).  REC: the step also writes
+// its reverse records (RecPtrs) for the discrete adjoint.
+template <typename S, bool CG = false, bool SR = false, bool X = false, bool REC = false>
 __device__ __forceinline__ void cell_update(const S *__restrict__ src_p, S *__restrict__ dst,
                                             const uint8_t *__restrict__ mask,
                                             const uint16_t *__restrict__ mid,
                                             const MatCoef<typename Real<S>::type> *__restrict__ pal,
                                             const KArgsT<typename Real<S>::type> &a, int x,
-                                            int y) {
+                                            int y,
+                                            const RecPtrs<typename Real<S>::type> &rp = {}) {
   using R = typename Real<S>::type;
   const long long c = (long long)y * a.nxp + x;
   const Pops<S, CG> src{src_p, a.plane, a.nxp};
@@ -34,10 +68,19 @@ __device__ __forceinline__ void cell_update(const S *__restrict__ src_p, S *__re
     if ((m & M_EDGE) == M_NEAR_SOLID) bounce_solid<S, R, CG>(src, x, y, mask[a.plane + c], cell);
     else fix_edges<S, R, CG, X>(src, a, mask, mid, pal, mc, x, y, m, cell);
   }
+  if constexpr (REC)
+    if (live) write_listed_records<S, R, CG>(src, a, rp, m, c, x, y, cell);
   if (a.mode == 0 && (m & M_YLO)) surface_reaction<S, R, CG>(src, a, mc, x, cell);
   R S_vol = 0;
   if (a.mode == 1 && (m & REG_MASK) == REG_CATALYST) S_vol = volume_sink<S, R, CG>(src, a, x, y);
   const Macro<R> u = macros<R, X>(a, mc, cell);
+  if constexpr (REC) {
+    if (live) {
+      R *r = rp.cell + 8 * c;
+      stq(r, u.vx, u.vy, u.C[0], u.C[1]);
+      stq(r + 4, u.C[2], cell.g[1][1] - cell.g[1][3], cell.g[1][2] - cell.g[1][4], R(0));
+    }
+  }
   R o[9];
   collide_flow<R, X>(a, mc, u, cell.f, o);
   // 16-bit storage with stochastic rounding: a random stream per cell and
@@ -97,6 +140,19 @@ k_step(const S *__restrict__ src_p, S *__restrict__ dst, const uint8_t *__restri
   cell_update<S, false, SR, X>(src_p, dst, mask, mid, pal, a, x, y);
 }
 
+// The step with its reverse records (plain cathode set-ups, round-to-
+// nearest storage: what the adjoint covers).
+template <typename S, int BX, int BY, int MINB>
+__global__ void __launch_bounds__(BX * BY, MINB)
+k_step_rec(const S *__restrict__ src_p, S *__restrict__ dst, const uint8_t *__restrict__ mask,
+           const uint16_t *__restrict__ mid, const MatCoef<typename Real<S>::type> *__restrict__ pal,
+           KArgsT<typename Real<S>::type> a, RecPtrs<typename Real<S>::type> rp) {
+  const int x = blockIdx.x * BX + (threadIdx.x % BX);
+  const int y = blockIdx.y * BY + (threadIdx.x / BX);
+  if (x >= a.nx || y >= a.ny) return;
+  cell_update<S, false, false, false, true>(src_p, dst, mask, mid, pal, a, x, y, rp);
+}
+
 // ------------------------------------------------------ launcher
 template <typename S, int V>
 void launch_step_v(const void *src, void *dst, const DevGeom &g, const KArgs &a, cudaStream_t st) {
@@ -121,6 +177,18 @@ void launch_step_v(const void *src, void *dst, const DevGeom &g, const KArgs &a,
   }
   k_step<S, sh.bx, sh.by, sh.minb><<<grid, sh.bx * sh.by, 0, st>>>(
       (const S *)src, (S *)dst, g.mask, g.mid, (const MatCoef<R> *)g.pal, narrow_args<R>(a));
+}
+
+constexpr StepShape kRecShape = {64, 2, 8};
+template <typename S>
+void launch_step_rec(const void *src, void *dst, const DevGeom &g, const KArgs &a,
+                     const RecBufs &r, cudaStream_t st) {
+  using R = typename Real<S>::type;
+  dim3 grid((a.nx + kRecShape.bx - 1) / kRecShape.bx, (a.ny + kRecShape.by - 1) / kRecShape.by);
+  const RecPtrs<R> rp{(R *)r.cell, (R *)r.own, (R *)r.pulled, r.slot};
+  k_step_rec<S, kRecShape.bx, kRecShape.by, kRecShape.minb><<<grid, kRecShape.bx * kRecShape.by,
+                                                              0, st>>>(
+      (const S *)src, (S *)dst, g.mask, g.mid, (const MatCoef<R> *)g.pal, narrow_args<R>(a), rp);
 }
 
 template <typename S>

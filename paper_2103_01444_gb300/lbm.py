@@ -27,7 +27,7 @@ EXPORTS = ("lbm_create_domain", "lbm_destroy_domain", "lbm_set_params", "lbm_set
            "lbm_set_variant", "lbm_residual_noalloc", "lbm_balances", "lbm_step_observe",
            "lbm_create_batch", "lbm_destroy_batch",
            "lbm_batch_set_schedule", "lbm_batch_tune", "lbm_batch_step", "lbm_batch_time_steps",
-           "lbm_grad", "lbm_vjp", "lbm_halo_exchange", "lbm_halo_pack", "lbm_halo_unpack",
+           "lbm_grad", "lbm_set_grad_memory", "lbm_vjp", "lbm_halo_exchange", "lbm_halo_pack", "lbm_halo_unpack",
            "lbm_last_error")
 
 
@@ -95,6 +95,7 @@ def load_library(path: str = LIB_PATH):
         "lbm_bytes_per_cell": [P, d],
         "lbm_tune": [P, C.c_int32, C.POINTER(C.c_int32), d],
         "lbm_set_variant": [P, C.c_int32],
+        "lbm_set_grad_memory": [P, C.c_int64],
         "lbm_residual_noalloc": [P, C.c_void_p, d],
         "lbm_create_batch": [C.POINTER(P), C.c_int32, C.POINTER(P)],
         "lbm_destroy_batch": [P],
@@ -329,6 +330,12 @@ class Domain:
                                *ptrs, C.byref(du), on_device))
         g["u_in"] = du.value
         return J.value, g
+
+    def set_grad_memory(self, nbytes: int):
+        """Device bytes grad() may keep reverse records in: -1 for what is
+        free (the default), 0 to recompute every segment from its
+        checkpoint."""
+        _check(self.L.lbm_set_grad_memory(self.h, int(nbytes)))
 
     def vjp(self, lam_next):
         """One transposed step at the current state: (lam_prev, gradients)."""

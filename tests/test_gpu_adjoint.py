@@ -271,3 +271,28 @@ def test_autograd_on_cuda_tensors_matches_host_gradients():
     np.testing.assert_array_equal(D.grad.cpu().numpy(), 3.0 * g["D_O2"])
     # the drive gradient is an FP64 atomic sum over cells: equal to rounding
     assert u.grad.item() == pytest.approx(3.0 * g["u_in"], rel=1e-12)
+
+
+@pytest.mark.parametrize("name,mode,objective,precision",
+                         [("film", 0, 0, "fp64"), ("vol", 1, 1, "fp64"),
+                          ("grains-p", 0, 0, "fp64"), ("vol-p-sa", 1, 0, "fp32")])
+def test_stored_and_recomputed_records_give_the_same_gradient(name, mode, objective, precision):
+    """The reverse sweep reads each step's records either from the forward
+    sweep (stored segments) or from a recompute of the segment from its
+    checkpoint: the same kernel writes both, so the gradient must not depend
+    on how much memory lbm_grad may use (all stored, a few, none)."""
+    case = case_of(name)
+    N, seg = 45, 7
+    d = gpu(case, precision, mode)
+    ref = None
+    for limit in (-1, 0, 200_000, 2_000_000, 8_000_000):
+        d.set_grad_memory(limit)
+        J, g = d.grad(objective, N, segment=seg)
+        if ref is None:
+            ref = (J, g)
+            continue
+        assert J == ref[0]
+        for k in ("phi", "K", "D_O2"):
+            np.testing.assert_array_equal(g[k], ref[1][k], err_msg=f"{k} at limit {limit}")
+        # (the inlet drive's gradient is summed with FP64 atomics in any order)
+        assert g["u_in"] == pytest.approx(ref[1]["u_in"], rel=1e-12)
