@@ -181,6 +181,12 @@ class ClockSampler:
         self.start_bytes = os.path.getsize(self.out.name)
         return self
 
+    def mark(self):
+        """Drops the samples taken so far (the timed region starts now)."""
+        if self.proc is not None and self.out is not None:
+            self.out.flush()
+            self.start_bytes = os.path.getsize(self.out.name)
+
     def __exit__(self, *exc):
         if self.proc is not None:
             self.proc.terminate()
@@ -388,11 +394,15 @@ def run_ours(args):
                          interface_mode=args.interface, rounding=args.rounding)
     variant, tune_ms = d.tune(20)       # launch shape of the step kernel
     W, K = max(args.warmup, 3), max(args.steps, 1)
-    warm_up(d, W)
-    torch.cuda.synchronize()
-    barrier(pg, dev)
-    torch.cuda.synchronize()
     with ClockSampler(local) as clk:
+        # the warm-up runs after the sampler has started (starting it leaves
+        # the GPU idle for a while), so that the timed steps start on a busy
+        # GPU; only samples taken from the timed region on are kept
+        warm_up(d, W)
+        torch.cuda.synchronize()
+        barrier(pg, dev)
+        torch.cuda.synchronize()
+        clk.mark()
         ms, launches = timed_steps(d, K, stream, args.residual_every)
     torch.cuda.synchronize()
     barrier(pg, dev)

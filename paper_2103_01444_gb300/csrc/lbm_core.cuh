@@ -51,8 +51,12 @@ template <> struct Real<double> { using type = double; };
 
 __device__ __forceinline__ float ld_r(const float *p) { return __ldg(p); }
 __device__ __forceinline__ double ld_r(const double *p) { return __ldg(p); }
-__device__ __forceinline__ float ld_r(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
-__device__ __forceinline__ float ld_r(const __half *p) { return __half2float(*p); }
+__device__ __forceinline__ float ld_r(const __nv_bfloat16 *p) {
+  return __uint_as_float((unsigned)__ldg(reinterpret_cast<const unsigned short *>(p)) << 16);
+}
+__device__ __forceinline__ float ld_r(const __half *p) {
+  return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short *>(p))));
+}
 
 // Loads that bypass L1 (L2 only).  Within one launch L1 is not coherent
 // across SMs, so a kernel that reads, across a grid barrier, what other SMs
