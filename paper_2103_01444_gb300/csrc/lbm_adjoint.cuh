@@ -134,11 +134,12 @@ __device__ __forceinline__ void flow_rev(const KArgsT<R> &a, const MatCoef<R> &m
                                          R &ldarcy, R &lforch, R &ll0, R &ll1, R &lip) {
   const R sn = R(a.s_nu), sq = R(a.s_q), g = R(a.body_g), ip = mc.inv_phi;
   // ---- the macroscopic values of the forward step (macros)
-  const R vn = sqrt(vx * vx + vy * vy);
-  const R rr = sqrt(mc.l0 * mc.l0 + mc.l1 * vn);
-  const R den = mc.l0 + rr;
-  const R ux = vx / den, uy = vy / den;
-  const R u2 = ux * ux + uy * uy, un = sqrt(u2);
+  // (the forward step's own operations, so that u is the forward value)
+  const R vn = vsqrt(vx * vx + vy * vy);
+  const R rr = vsqrt(mc.l0 * mc.l0 + mc.l1 * vn);
+  const R den = mc.l0 + rr, inv_den = vrcp(den);
+  const R ux = vx * inv_den, uy = vy * inv_den;
+  const R u2 = ux * ux + uy * uy, un = vn * inv_den;
   const R Fx = -mc.darcy * ux - mc.forch * un * ux + mc.phi * g;
   const R Fy = -mc.darcy * uy - mc.forch * un * uy;
   const R uF = ux * Fx + uy * Fy;
@@ -484,9 +485,9 @@ __device__ __forceinline__ void adj_interior_cell(const RecPtrs<R> &rp,
   R lphi = 0, ldarcy = 0, lforch = 0, ll0 = 0, ll1 = 0, lip = 0;
   R lb[3] = {0, 0, 0}, lw1[3] = {0, 0, 0}, lq1[3] = {0, 0, 0}, lsrc[3] = {0, 0, 0};
   {
-    const R vn = sqrt(vx * vx + vy * vy);
-    const R den = mc.l0 + sqrt(mc.l0 * mc.l0 + mc.l1 * vn);
-    const R ux = vx / den, uy = vy / den;
+    const R vn = vsqrt(vx * vx + vy * vy);
+    const R inv_den = vrcp(mc.l0 + vsqrt(mc.l0 * mc.l0 + mc.l1 * vn));
+    const R ux = vx * inv_den, uy = vy * inv_den;
     const R srcv[3] = {-S_vol * R(a.hpo) * mc.inv_sigma, S_vol, R(-2) * S_vol};
     R lux = 0, luy = 0;
 #pragma unroll

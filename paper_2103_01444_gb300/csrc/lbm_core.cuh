@@ -619,9 +619,31 @@ __device__ __forceinline__ void pull_cell(const Pops<S, CG> &src, const KArgsT<R
   if (m & M_EDGE) fix_edges<S, R, CG, X>(src, a, mask, mid, pal, mc, x, y, m, c);
 }
 
+// Square root and reciprocal of the Eq. 8 velocity in the FP32 arithmetic
+// path: the hardware approximations (PTX sqrt.approx.f32, rcp.approx.ftz.f32,
+// a few instructions each instead of the correctly rounded sequences, which
+// made up a large part of the 16-bit step's instruction-bound time).  Their
+// error is of the order of FP32 rounding itself, well below what storing the
+// populations in FP32 adds at every step; the argument of the reciprocal is
+// at least l0 >= 1/2, never subnormal.  FP64 keeps the correctly rounded
+// operations.
+__device__ __forceinline__ float vsqrt(float x) {
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ double vsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float vrcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ double vrcp(double x) { return 1.0 / x; }
+
 // Macroscopic values of a post-stream cell (Eq. 8, 11).
 template <typename R> struct Macro {
-  R ux, uy, Pdev;   // velocity; phi p - rho0/3
+  R ux, uy, un;     // velocity and its magnitude
+  R Pdev;           // phi p - rho0/3
   R C[3];           // deviation sums (value - Cref)
   R vx, vy;         // auxiliary velocity of Eq. 8 (the reverse records keep it)
 };
@@ -648,12 +670,15 @@ __device__ __forceinline__ Macro<R> macros(const KArgsT<R> &a, const MatCoef<R> 
   R vx = d[1] - d[3] + d[5] - d[6] - d[7] + d[8] + R(0.5) * mc.phi * Gx;
   R vy = d[2] - d[4] + d[5] + d[6] - d[7] - d[8];
   if constexpr (X) vy += R(0.5) * mc.phi * Gy;
-  R vn = sqrt(vx * vx + vy * vy);
-  R den = mc.l0 + sqrt(mc.l0 * mc.l0 + mc.l1 * vn);
+  // u = v / den with one reciprocal of den; |u| = |v| / den, so u's
+  // magnitude needs no square root of its own
+  R vn = vsqrt(vx * vx + vy * vy);
+  R inv_den = vrcp(mc.l0 + vsqrt(mc.l0 * mc.l0 + mc.l1 * vn));
   r.vx = vx;
   r.vy = vy;
-  r.ux = vx / den;
-  r.uy = vy / den;
+  r.ux = vx * inv_den;
+  r.uy = vy * inv_den;
+  r.un = vn * inv_den;
   R s18 = ((d[1] + d[3]) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8]));
   r.Pdev = R(0.6) * s18 - R(0.4) * (r.ux * r.ux + r.uy * r.uy) * mc.inv_phi;
 #pragma unroll
@@ -667,7 +692,7 @@ template <typename R, bool X = false>
 __device__ __forceinline__ void collide_flow(const KArgsT<R> &a, const MatCoef<R> &mc, const Macro<R> &u,
                                              const R d[9], R o[9]) {
   const R sn = R(a.s_nu), sq = R(a.s_q);
-  R ux = u.ux, uy = u.uy, u2 = ux * ux + uy * uy, un = sqrt(u2), ip = mc.inv_phi;
+  R ux = u.ux, uy = u.uy, u2 = ux * ux + uy * uy, un = u.un, ip = mc.inv_phi;
   R Gx, Gy;
   body_force<R, X>(a, u.C[0], Gx, Gy);
   R Fx = -mc.darcy * ux - mc.forch * un * ux + mc.phi * Gx;
