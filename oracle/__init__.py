@@ -3,4 +3,4 @@
 Only the tests, the package smoke check and the benchmark's CPU-baseline leg
 may import this package.  The product path never does.
 """
-from .oracle import Oracle, build_oracle, lib  # noqa: F401
+from .oracle import Oracle, TangentOracle, build_oracle, build_tangent, lib  # noqa: F401

@@ -69,26 +69,35 @@
  *
  * Storage: f[q][y][x] (9 planes), g[s][q][y][x] (3 scalars x 5 planes),
  * s = 0 temperature, 1 O2 mole fraction, 2 H2O mole fraction.  Full values,
- * never deviations.  Built with plain gcc, no fast-math.
+ * never deviations.  Built with plain gcc, no fast-math.  Every real number
+ * has the type `real` (double here; see below).
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
+/* The arithmetic type.  This file is plain C in double precision; the
+ * oracle's tangent (lbm_oracle_tangent.cc) compiles the same source as C++
+ * with `real` a forward-mode dual number, a value and its derivative along
+ * one direction of the inputs, and defines ORC_REAL_DEFINED. */
+#ifndef ORC_REAL_DEFINED
+typedef double real;
+#endif
+
 /* ---------------------------------------------------------------- lattices */
 
 /* D2Q9 velocity set, Eq. 2: rest, four axis links, four diagonals. */
 static const int EX9[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 static const int EY9[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-static const double W9[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+static const real W9[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
                              1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
 /* D2Q5 velocity set, Eq. 9. */
 static const int EX5[5] = {0, 1, 0, -1, 0};
 static const int EY5[5] = {0, 0, 1, 0, -1};
 
 /* Transformation matrix M, Eq. 3. */
-static const double M9[9][9] = {
+static const real M9[9][9] = {
     {1, 1, 1, 1, 1, 1, 1, 1, 1},
     {-4, -1, -1, -1, -1, 2, 2, 2, 2},
     {4, -2, -2, -2, -2, 1, 1, 1, 1},
@@ -100,7 +109,7 @@ static const double M9[9][9] = {
     {0, 0, 0, 0, 0, 1, -1, 1, -1}};
 
 /* Transformation matrix N, Eq. 10. */
-static const double N5[5][5] = {
+static const real N5[5][5] = {
     {1, 1, 1, 1, 1},
     {0, 1, 0, -1, 0},
     {0, 0, 1, 0, -1},
@@ -119,8 +128,8 @@ static int opposite5(int i) {
 }
 
 /* Gauss-Jordan inverse with partial pivoting of an n x n row-major matrix. */
-static int invert(int n, const double *a, double *inv) {
-  double w[9 * 18];
+static int invert(int n, const real *a, real *inv) {
+  real w[9 * 18];
   for (int r = 0; r < n; ++r)
     for (int c = 0; c < 2 * n; ++c)
       w[r * 2 * n + c] = c < n ? a[r * n + c] : (c - n == r ? 1.0 : 0.0);
@@ -131,15 +140,15 @@ static int invert(int n, const double *a, double *inv) {
     if (fabs(w[piv * 2 * n + c]) < 1e-12) return -1;
     if (piv != c)
       for (int k = 0; k < 2 * n; ++k) {
-        double t = w[c * 2 * n + k];
+        real t = w[c * 2 * n + k];
         w[c * 2 * n + k] = w[piv * 2 * n + k];
         w[piv * 2 * n + k] = t;
       }
-    double d = w[c * 2 * n + c];
+    real d = w[c * 2 * n + c];
     for (int k = 0; k < 2 * n; ++k) w[c * 2 * n + k] /= d;
     for (int r = 0; r < n; ++r) {
       if (r == c) continue;
-      double s = w[r * 2 * n + c];
+      real s = w[r * 2 * n + c];
       for (int k = 0; k < 2 * n; ++k) w[r * 2 * n + k] -= s * w[c * 2 * n + k];
     }
   }
@@ -148,8 +157,8 @@ static int invert(int n, const double *a, double *inv) {
   return 0;
 }
 
-static double MINV9[9][9];
-static double NINV5[5][5];
+static real MINV9[9][9];
+static real NINV5[5][5];
 static int g_inverted = 0;
 
 static void ensure_inverses(void) {
@@ -176,24 +185,24 @@ typedef struct {
   int32_t wall_dirichlet;   /* bit 3k+s: scalar s held at C_wall[3k+s] on wall k
                                (0 the x = 0 end outside inlet rows, 1 the x = nx-1 end,
                                2 the bottom); otherwise insulated */
-  double nu;                /* kinematic viscosity; 3 nu = tau - 1/2 (Eq. 8) */
-  double u_in_avg;          /* mean inlet velocity over the channel rows */
-  double body_force_x;      /* uniform body force per unit mass (tests only) */
-  double V_op, T_in, C_O2_in, C_H2O_in;
-  double T_top, C_O2_top, C_H2O_top;
-  double aj0_ref;           /* A/cm^3 at T_ref_kin (Eq. 13, 17) */
-  double T_ref_kin, E_act;  /* 353.15 K, 16456 K (Eq. 17) */
-  double alpha_c, F, R;     /* Eq. 13 */
-  double dU0dT, U0_0;       /* Eq. 16 */
-  double x_ref;             /* reference O2 mole fraction (C_O2,ref) */
-  double dx_cm, dt_s, delta_cl_cm, c_tot, rho_cp_f;
-  double dp_in;             /* pressure inlet: phi p there is rho0/3 + dp_in */
-  double alpha_a;           /* anodic transfer coefficient of the Butler-Volmer
+  real nu;                /* kinematic viscosity; 3 nu = tau - 1/2 (Eq. 8) */
+  real u_in_avg;          /* mean inlet velocity over the channel rows */
+  real body_force_x;      /* uniform body force per unit mass (tests only) */
+  real V_op, T_in, C_O2_in, C_H2O_in;
+  real T_top, C_O2_top, C_H2O_top;
+  real aj0_ref;           /* A/cm^3 at T_ref_kin (Eq. 13, 17) */
+  real T_ref_kin, E_act;  /* 353.15 K, 16456 K (Eq. 17) */
+  real alpha_c, F, R;     /* Eq. 13 */
+  real dU0dT, U0_0;       /* Eq. 16 */
+  real x_ref;             /* reference O2 mole fraction (C_O2,ref) */
+  real dx_cm, dt_s, delta_cl_cm, c_tot, rho_cp_f;
+  real dp_in;             /* pressure inlet: phi p there is rho0/3 + dp_in */
+  real alpha_a;           /* anodic transfer coefficient of the Butler-Volmer
                                branch; 0 = Tafel kinetics, Eq. 13 as printed */
-  double buoy_gx, buoy_gy;  /* Boussinesq buoyancy of the natural-convection cases
+  real buoy_gx, buoy_gy;  /* Boussinesq buoyancy of the natural-convection cases
                                (Sec. 3): force per unit mass (buoy_gx, buoy_gy)(T - T_buoy) */
-  double T_buoy;
-  double C_wall[9];         /* wall values of wall_dirichlet, [wall][scalar] */
+  real T_buoy;
+  real C_wall[9];         /* wall values of wall_dirichlet, [wall][scalar] */
   int32_t scalar_advection; /* flux moments of the D2Q5 equilibria (Eq. 10):
                                0 u C as printed; 1 u (C - C_in), relative to the
                                scalar's inlet value */
@@ -204,9 +213,9 @@ typedef struct {
  * the temperature equation, whose diffusivity is k_eff/(rho c_p)_eff,
  * divided by the same effective heat capacity. */
 typedef struct {
-  const double *phi, *K, *alpha_T, *D_O2, *D_H2O;
-  const double *u_imposed; /* optional [2][ny][nx]: freeze flow (tests) */
-  const double *sigma;     /* optional [ny][nx] heat-capacity ratio */
+  const real *phi, *K, *alpha_T, *D_O2, *D_H2O;
+  const real *u_imposed; /* optional [2][ny][nx]: freeze flow (tests) */
+  const real *sigma;     /* optional [ny][nx] heat-capacity ratio */
 } orc_material;
 
 /* Mask bits (one byte per cell). */
@@ -254,16 +263,16 @@ void orc_build_mask(const orc_params *P, const uint8_t *solid, uint8_t *mask) {
 /* ------------------------------------------------------- closures (Sec. 4) */
 
 /* Eq. 16 */
-double orc_U0(const orc_params *P, double T) { return P->dU0dT * T + P->U0_0; }
+real orc_U0(const orc_params *P, real T) { return P->dU0dT * T + P->U0_0; }
 /* Eq. 14 */
-double orc_eta(const orc_params *P, double T) { return P->V_op - orc_U0(P, T); }
+real orc_eta(const orc_params *P, real T) { return P->V_op - orc_U0(P, T); }
 /* Eq. 17 */
-double orc_aj0(const orc_params *P, double T) {
+real orc_aj0(const orc_params *P, real T) {
   return P->aj0_ref * exp(-P->E_act * (1.0 / T - 1.0 / P->T_ref_kin));
 }
 /* Eq. 13: volumetric current density (A/cm^3, negative = cathodic) at O2
  * mole fraction x and temperature T. */
-double orc_tafel_j(const orc_params *P, double x, double T) {
+real orc_tafel_j(const orc_params *P, real x, real T) {
   return -orc_aj0(P, T) * (x / P->x_ref) *
          exp(-P->alpha_c * P->F / (P->R * T) * orc_eta(P, T));
 }
@@ -271,45 +280,45 @@ double orc_tafel_j(const orc_params *P, double x, double T) {
  * oxidation), taken at unit reactant activity: aj0(T) exp(alpha_a F eta/(RT))
  * in A/cm^3; zero when alpha_a = 0 (Tafel, Eq. 13 alone).  The full current
  * is j = orc_tafel_j + orc_anodic_j. */
-double orc_anodic_j(const orc_params *P, double T) {
+real orc_anodic_j(const orc_params *P, real T) {
   if (P->alpha_a == 0.0) return 0.0;
   return orc_aj0(P, T) * exp(P->alpha_a * P->F / (P->R * T) * orc_eta(P, T));
 }
 /* Eq. 15: heat per unit volume (W/cm^3) released by current j at T. */
-double orc_heat_Q(const orc_params *P, double j, double T) {
+real orc_heat_Q(const orc_params *P, real j, real T) {
   return -j * (orc_eta(P, T) + T * P->dU0dT);
 }
 
 /* Lattice rate constant of the thin film: O2 mole-fraction flux per step
  * through one wall link, per unit wall mole fraction. */
-static double k_surface(const orc_params *P, double T) {
-  double j1 = -orc_tafel_j(P, P->x_ref, T) / P->x_ref; /* A/cm^3 per unit x */
-  double flux = j1 * P->delta_cl_cm / (4.0 * P->F * P->c_tot); /* cm/s */
+static real k_surface(const orc_params *P, real T) {
+  real j1 = -orc_tafel_j(P, P->x_ref, T) / P->x_ref; /* A/cm^3 per unit x */
+  real flux = j1 * P->delta_cl_cm / (4.0 * P->F * P->c_tot); /* cm/s */
   return flux * P->dt_s / P->dx_cm;
 }
 /* Lattice rate of the volumetric catalyst: fraction of O2 per step. */
-static double k_volume(const orc_params *P, double T) {
-  double j1 = -orc_tafel_j(P, P->x_ref, T) / P->x_ref;
+static real k_volume(const orc_params *P, real T) {
+  real j1 = -orc_tafel_j(P, P->x_ref, T) / P->x_ref;
   return j1 / (4.0 * P->F * P->c_tot) * P->dt_s;
 }
 /* The anodic branch as O2 mole fraction produced per step: through one
  * wall link of the thin film, and per cell of the volumetric catalyst. */
-static double k_surface_anodic(const orc_params *P, double T) {
+static real k_surface_anodic(const orc_params *P, real T) {
   return orc_anodic_j(P, T) * P->delta_cl_cm / (4.0 * P->F * P->c_tot) * P->dt_s / P->dx_cm;
 }
-static double k_volume_anodic(const orc_params *P, double T) {
+static real k_volume_anodic(const orc_params *P, real T) {
   return orc_anodic_j(P, T) / (4.0 * P->F * P->c_tot) * P->dt_s;
 }
 /* Temperature rise (K) per unit of O2 mole fraction consumed, Eq. 15 with
  * j = -4 F c_tot (consumed flux). */
-static double heat_per_O2(const orc_params *P, double T) {
+static real heat_per_O2(const orc_params *P, real T) {
   return 4.0 * P->F * P->c_tot * (orc_eta(P, T) + T * P->dU0dT) / P->rho_cp_f;
 }
 
 /* ------------------------------------------------- moment-space pieces */
 
 /* b of Eq. 10 for diffusivity alpha */
-double orc_b_of_alpha(double alpha) { return 20.0 * sqrt(3.0) * alpha - 4.0; }
+real orc_b_of_alpha(real alpha) { return 20.0 * sqrt(3.0) * alpha - 4.0; }
 
 /* D2Q5 coefficients of one cell and scalar: the b of its equilibrium and
  * the relaxation rate of the flux moments.  Eq. 10 as printed sets b from
@@ -317,12 +326,12 @@ double orc_b_of_alpha(double alpha) { return 20.0 * sqrt(3.0) * alpha - 4.0; }
  * Fickian interface mode every cell takes the b of the largest diffusivity
  * of that scalar (alpha_max) and the cell's diffusivity enters through the
  * flux rate instead: alpha = c_s^2 (1/s_1 - 1/2), c_s^2 = (4 + b)/10. */
-typedef struct { double b, q1; } scalar_coef;
-static scalar_coef scalar_coefficients(const orc_params *P, double alpha, double alpha_max) {
+typedef struct { real b, q1; } scalar_coef;
+static scalar_coef scalar_coefficients(const orc_params *P, real alpha, real alpha_max) {
   scalar_coef r;
   if (P->interface_mode == 1) {
     r.b = orc_b_of_alpha(alpha_max);
-    double cs2 = (4.0 + r.b) / 10.0;
+    real cs2 = (4.0 + r.b) / 10.0;
     r.q1 = 1.0 / (alpha / cs2 + 0.5);
   } else {
     r.b = orc_b_of_alpha(alpha);
@@ -333,7 +342,7 @@ static scalar_coef scalar_coefficients(const orc_params *P, double alpha, double
 
 /* Largest diffusivity of each scalar over the fluid cells. */
 static void max_diffusivities(const orc_params *P, const orc_material *mat, const uint8_t *mask,
-                              double amax[3]) {
+                              real amax[3]) {
   size_t n = (size_t)P->nx * P->ny;
   amax[0] = amax[1] = amax[2] = 0.0;
   for (size_t c = 0; c < n; ++c) {
@@ -345,8 +354,8 @@ static void max_diffusivities(const orc_params *P, const orc_material *mat, cons
 }
 
 /* D2Q5 equilibrium populations N^-1 n_eq for value C, velocity u, b. */
-static void d2q5_equilibrium(double C, double ux, double uy, double b, double geq[5]) {
-  double neq[5] = {C, ux * C, uy * C, b * C, 0.0};
+static void d2q5_equilibrium(real C, real ux, real uy, real b, real geq[5]) {
+  real neq[5] = {C, ux * C, uy * C, b * C, 0.0};
   for (int i = 0; i < 5; ++i) {
     geq[i] = 0;
     for (int k = 0; k < 5; ++k) geq[i] += NINV5[i][k] * neq[k];
@@ -354,9 +363,9 @@ static void d2q5_equilibrium(double C, double ux, double uy, double b, double ge
 }
 
 /* Eq. 5 equilibrium moments. */
-static void flow_meq(double phi, double p, double ux, double uy, double meq[9]) {
-  const double rho0 = 1.0;
-  double u2 = ux * ux + uy * uy;
+static void flow_meq(real phi, real p, real ux, real uy, real meq[9]) {
+  const real rho0 = 1.0;
+  real u2 = ux * ux + uy * uy;
   meq[0] = rho0;
   meq[1] = -4 * rho0 + 6 * phi * p + 3 * rho0 * u2 / phi;
   meq[2] = 4 * rho0 - 9 * phi * p - 3 * rho0 * u2 / phi;
@@ -369,9 +378,9 @@ static void flow_meq(double phi, double p, double ux, double uy, double meq[9]) 
 }
 
 /* Eq. 6 forcing moments (G7, G8 in the form derived from Guo's forcing). */
-static void flow_G(double phi, double ux, double uy, double Fx, double Fy, double G[9]) {
-  const double rho0 = 1.0;
-  double uF = ux * Fx + uy * Fy;
+static void flow_G(real phi, real ux, real uy, real Fx, real Fy, real G[9]) {
+  const real rho0 = 1.0;
+  real uF = ux * Fx + uy * Fy;
   G[0] = 0;
   G[1] = 6 * rho0 * uF / phi;
   G[2] = -6 * rho0 * uF / phi;
@@ -389,28 +398,28 @@ static void flow_G(double phi, double ux, double uy, double Fx, double Fy, doubl
  * linearly unstable (von Neumann amplification 1.43 at tau = 0.65).  The
  * mass moment relaxes at 1/tau instead, as in the BGK limit of the same
  * incompressible equilibrium. */
-static void flow_S(double tau, double S[9]) {
-  double sq = 8.0 * (2.0 - 1.0 / tau) / (8.0 - 1.0 / tau);
-  double s[9] = {1 / tau, 1 / tau, 1 / tau, 0, sq, 0, sq, 1 / tau, 1 / tau};
+static void flow_S(real tau, real S[9]) {
+  real sq = 8.0 * (2.0 - 1.0 / tau) / (8.0 - 1.0 / tau);
+  real s[9] = {1 / tau, 1 / tau, 1 / tau, 0, sq, 0, sq, 1 / tau, 1 / tau};
   memcpy(S, s, sizeof s);
 }
 
 /* Q of Eq. 10. */
-static void scalar_Q(double Q[5]) {
-  double a = 6.0 / (3.0 + sqrt(3.0)), c = 6.0 / (3.0 + 2.0 * sqrt(3.0));
-  double q[5] = {0, a, a, c, c};
+static void scalar_Q(real Q[5]) {
+  real a = 6.0 / (3.0 + sqrt(3.0)), c = 6.0 / (3.0 + 2.0 * sqrt(3.0));
+  real q[5] = {0, a, a, c, c};
   memcpy(Q, q, sizeof q);
 }
 
 /* Darcy-Forchheimer coefficients of Eq. 7/8 for one cell. */
-typedef struct { double phi, darcy, forch, l0, l1; } porous_coef;
-static porous_coef porous(const orc_params *P, double phi, double K) {
+typedef struct { real phi, darcy, forch, l0, l1; } porous_coef;
+static porous_coef porous(const orc_params *P, real phi, real K) {
   porous_coef c;
   c.phi = phi;
   if (isinf(K)) {
     c.darcy = 0; c.forch = 0;
   } else {
-    double Fphi = 0.143 * pow(phi, -1.5);
+    real Fphi = 0.143 * pow(phi, -1.5);
     c.darcy = phi * P->nu / K;
     c.forch = P->forchheimer ? phi * Fphi / sqrt(K) : 0.0;
   }
@@ -421,9 +430,9 @@ static porous_coef porous(const orc_params *P, double phi, double K) {
 }
 
 /* Eq. 8: velocity from the auxiliary velocity v. */
-void orc_velocity(double l0, double l1, double vx, double vy, double *ux, double *uy) {
-  double vn = sqrt(vx * vx + vy * vy);
-  double den = l0 + sqrt(l0 * l0 + l1 * vn);
+void orc_velocity(real l0, real l1, real vx, real vy, real *ux, real *uy) {
+  real vn = sqrt(vx * vx + vy * vy);
+  real den = l0 + sqrt(l0 * l0 + l1 * vn);
   *ux = vx / den;
   *uy = vy / den;
 }
@@ -431,10 +440,10 @@ void orc_velocity(double l0, double l1, double vx, double vy, double *ux, double
 /* Inlet velocity profile: parabola over the channel rows, mean u_in_avg,
  * evaluated at height y (cell centres at integer y, channel from y0 - 1/2
  * to ny - 1/2); zero outside the channel. */
-static double inlet_u(const orc_params *P, double y) {
+static real inlet_u(const orc_params *P, real y) {
   int y0 = P->ny_cl + P->ny_gdl;
-  double h = P->ny - y0;
-  double s = (y - y0 + 0.5) / h;
+  real h = P->ny - y0;
+  real s = (y - y0 + 0.5) / h;
   if (s <= 0.0 || s >= 1.0) return 0.0;
   return 6.0 * P->u_in_avg * s * (1.0 - s);
 }
@@ -448,7 +457,7 @@ static int wall_fixed(const orc_params *P, int k, int s) {
 /* Body force per unit mass at temperature T: the uniform force along x of
  * the closed-form tests plus the Boussinesq buoyancy of Sec. 3's
  * natural-convection cases, gamma (T - T_buoy). */
-static void body_force(const orc_params *P, double T, double *Gx, double *Gy) {
+static void body_force(const orc_params *P, real T, real *Gx, real *Gy) {
   *Gx = P->body_force_x + P->buoy_gx * (T - P->T_buoy);
   *Gy = P->buoy_gy * (T - P->T_buoy);
 }
@@ -458,11 +467,11 @@ static void body_force(const orc_params *P, double T, double *Gx, double *Gy) {
 /* Initial state: f = w rho0 (rest), g = D2Q5 equilibrium of the inlet values
  * at rest with the cell's own b. */
 void orc_init(const orc_params *P, const orc_material *mat, const uint8_t *mask,
-              double *f, double *g) {
+              real *f, real *g) {
   ensure_inverses();
   int nx = P->nx, ny = P->ny;
   size_t n = (size_t)nx * ny;
-  double Cin[3] = {P->T_in, P->C_O2_in, P->C_H2O_in}, amax[3];
+  real Cin[3] = {P->T_in, P->C_O2_in, P->C_H2O_in}, amax[3];
   max_diffusivities(P, mat, mask, amax);
   for (size_t c = 0; c < n; ++c) {
     if ((mask[c] & 3) == REG_SOLID) {
@@ -471,9 +480,9 @@ void orc_init(const orc_params *P, const orc_material *mat, const uint8_t *mask,
       continue;
     }
     for (int i = 0; i < 9; ++i) f[i * n + c] = W9[i];
-    double alpha[3] = {mat->alpha_T[c], mat->D_O2[c], mat->D_H2O[c]};
+    real alpha[3] = {mat->alpha_T[c], mat->D_O2[c], mat->D_H2O[c]};
     for (int s = 0; s < 3; ++s) {
-      double geq[5];
+      real geq[5];
       d2q5_equilibrium(Cin[s], 0, 0, scalar_coefficients(P, alpha[s], amax[s]).b, geq);
       for (int i = 0; i < 5; ++i) g[(s * 5 + i) * n + c] = geq[i];
     }
@@ -482,14 +491,14 @@ void orc_init(const orc_params *P, const orc_material *mat, const uint8_t *mask,
 
 /* d f_i^eq / d(phi p) of the Eq. 5 equilibrium (M^-1 applied to the p
  * column of m_eq): 1/3 on axis links, 1/12 on diagonals. */
-static double pressure_weight(int i) {
-  double dm[9] = {0, 6, -9, 0, 0, 0, 0, 0, 0}, v = 0;
+static real pressure_weight(int i) {
+  real dm[9] = {0, 6, -9, 0, 0, 0, 0, 0, 0}, v = 0;
   for (int k = 0; k < 9; ++k) v += MINV9[i][k] * dm[k];
   return v;
 }
 /* phi p of a cell's post-collision populations (Eq. 8 applied to f*). */
-static double post_pressure(double phi, const double *fs, size_t n, size_t c) {
-  double jx = 0, jy = 0, s18 = 0;
+static real post_pressure(real phi, const real *fs, size_t n, size_t c) {
+  real jx = 0, jy = 0, s18 = 0;
   for (int k = 0; k < 9; ++k) {
     jx += EX9[k] * fs[k * n + c];
     jy += EY9[k] * fs[k * n + c];
@@ -512,17 +521,17 @@ enum {
  * fluxes go into the incoming links; the volumetric sinks (S per cell and
  * scalar) are returned in src[3][ny][nx] for the collision to add. */
 static void stream(const orc_params *P, const orc_material *mat, const uint8_t *mask,
-                   const double *fs, const double *gs, double *f, double *g,
-                   double *src, double *diag, double *Jx, double *qx) {
+                   const real *fs, const real *gs, real *f, real *g,
+                   real *src, real *diag, real *Jx, real *qx) {
   int nx = P->nx, ny = P->ny;
   size_t n = (size_t)nx * ny;
-  double Cin[3] = {P->T_in, P->C_O2_in, P->C_H2O_in};
-  double Ctop[3] = {P->T_top, P->C_O2_top, P->C_H2O_top}, amax[3];
+  real Cin[3] = {P->T_in, P->C_O2_in, P->C_H2O_in};
+  real Ctop[3] = {P->T_top, P->C_O2_top, P->C_H2O_top}, amax[3];
   max_diffusivities(P, mat, mask, amax);
   for (int k = 0; k < D_NDIAG; ++k) diag[k] = 0;
   if (Jx) for (int x = 0; x < nx; ++x) Jx[x] = 0;
   if (qx) for (int x = 0; x < nx; ++x) qx[x] = 0;
-  memset(src, 0, sizeof(double) * 3 * n);
+  memset(src, 0, sizeof(real) * 3 * n);
 
   for (int y = 0; y < ny; ++y)
     for (int x = 0; x < nx; ++x) {
@@ -534,19 +543,19 @@ static void stream(const orc_params *P, const orc_material *mat, const uint8_t *
         continue;
       }
       /* previous post-collision sums at this cell (C^n, T^n) */
-      double Cn[3];
+      real Cn[3];
       for (int s = 0; s < 3; ++s) {
         Cn[s] = 0;
         for (int i = 0; i < 5; ++i) Cn[s] += gs[(s * 5 + i) * n + c];
       }
-      double bcell[3] = {scalar_coefficients(P, mat->alpha_T[c], amax[0]).b,
+      real bcell[3] = {scalar_coefficients(P, mat->alpha_T[c], amax[0]).b,
                          scalar_coefficients(P, mat->D_O2[c], amax[1]).b,
                          scalar_coefficients(P, mat->D_H2O[c], amax[2]).b};
 
       /* ---- D2Q9 flow links */
       for (int i = 0; i < 9; ++i) {
         int sx = x - EX9[i], sy = y - EY9[i], io = opposite9(i);
-        double val;
+        real val;
         if (sy < 0 || sy >= ny) {
           val = fs[io * n + c];                               /* wall */
         } else {
@@ -568,7 +577,7 @@ static void stream(const orc_params *P, const orc_material *mat, const uint8_t *
               }
             } else if (m & B_INLET) {                         /* moving-wall inlet */
               /* link crosses the inlet plane at height y - e_iy/2 */
-              double uin = inlet_u(P, y - 0.5 * EY9[i]);
+              real uin = inlet_u(P, y - 0.5 * EY9[i]);
               val = fs[io * n + c] + 6.0 * W9[i] * 1.0 * (EX9[i] * uin);
               diag[D_IN + 0] += val - fs[io * n + c];
             } else {
@@ -603,23 +612,23 @@ static void stream(const orc_params *P, const orc_material *mat, const uint8_t *
       }
 
       /* ---- reaction rate at this cell (uses T^n and C^n) */
-      double kS = 0, kV = 0, kSa = 0, kVa = 0;
+      real kS = 0, kV = 0, kSa = 0, kVa = 0;
       int surface = (P->reaction_mode == 0) && (m & B_YLO);
       int volume = (P->reaction_mode == 1) && ((m & 3) == REG_CATALYST);
       if (surface) { kS = k_surface(P, Cn[0]); kSa = k_surface_anodic(P, Cn[0]); }
       if (volume) { kV = k_volume(P, Cn[0]); kVa = k_volume_anodic(P, Cn[0]); }
-      double hpo = (surface || volume) ? heat_per_O2(P, Cn[0]) : 0.0;   /* gas K per O2 */
-      double sig = mat->sigma ? mat->sigma[c] : 1.0;
+      real hpo = (surface || volume) ? heat_per_O2(P, Cn[0]) : 0.0;   /* gas K per O2 */
+      real sig = mat->sigma ? mat->sigma[c] : 1.0;
 
       /* ---- D2Q5 scalar links */
-      double Jsurf = 0;
+      real Jsurf = 0;
       for (int s = 0; s < 3; ++s) {
-        double w1 = (4.0 + bcell[s]) / 20.0;
+        real w1 = (4.0 + bcell[s]) / 20.0;
         for (int i = 0; i < 5; ++i) {
           int sx = x - EX5[i], sy = y - EY5[i], io = opposite5(i);
-          const double *gq = gs + (size_t)(s * 5) * n;
-          double own_out = gq[io * n + c];
-          double val;
+          const real *gq = gs + (size_t)(s * 5) * n;
+          real own_out = gq[io * n + c];
+          real val;
           if (sy < 0) {
             if (wall_fixed(P, 2, s)) {
               /* fixed bottom value (anti-bounce-back at the halfway wall) */
@@ -628,7 +637,7 @@ static void stream(const orc_params *P, const orc_material *mat, const uint8_t *
               if (s == 1) {
                 /* net O2 flux J = kS C_w - kSa with the wall value
                  * C_w = (own_out + val)/(2 w1) and J = own_out - val */
-                double kappa = kS / (2.0 * w1);
+                real kappa = kS / (2.0 * w1);
                 val = (own_out * (1.0 - kappa) + kSa) / (1.0 + kappa);
                 Jsurf = own_out - val;
               } else {
@@ -671,7 +680,7 @@ static void stream(const orc_params *P, const orc_material *mat, const uint8_t *
         }
         if (!P->periodic_x) {
           for (int i = 0; i < 5; ++i) {
-            const double *gq = gs + (size_t)(s * 5) * n;
+            const real *gq = gs + (size_t)(s * 5) * n;
             if (x + EX5[i] >= nx) diag[D_OUT + 1 + s] -= gq[i * n + c];
           }
         }
@@ -688,7 +697,7 @@ static void stream(const orc_params *P, const orc_material *mat, const uint8_t *
       }
       if (volume) {
         /* backward Euler for dC/dt = kVa - kV C */
-        double S = (kVa - kV * Cn[1]) / (1.0 + kV);
+        real S = (kVa - kV * Cn[1]) / (1.0 + kV);
         src[0 * n + c] = -S * hpo / sig;
         src[1 * n + c] = S;
         src[2 * n + c] = -2.0 * S;
@@ -701,14 +710,14 @@ static void stream(const orc_params *P, const orc_material *mat, const uint8_t *
 }
 
 /* Macroscopic fields of a post-stream state (Eq. 8, 11).  out may be NULL. */
-typedef struct { double ux, uy, p, C[3], usx, usy; } cell_macro;
+typedef struct { real ux, uy, p, C[3], usx, usy; } cell_macro;
 
 static cell_macro macros_at(const orc_params *P, const orc_material *mat, size_t n, size_t c,
-                            const double *f, const double *g) {
+                            const real *f, const real *g) {
   cell_macro r;
   porous_coef pc = porous(P, mat->phi[c], mat->K[c]);
-  const double rho0 = 1.0;
-  double vx = 0, vy = 0, s18 = 0;
+  const real rho0 = 1.0;
+  real vx = 0, vy = 0, s18 = 0;
   for (int i = 0; i < 9; ++i) {
     vx += EX9[i] * f[i * n + c] / rho0;
     vy += EY9[i] * f[i * n + c] / rho0;
@@ -716,7 +725,7 @@ static cell_macro macros_at(const orc_params *P, const orc_material *mat, size_t
   }
   /* the force enters Eq. 8's auxiliary velocity with half a time step; the
    * buoyancy takes the cell's temperature after streaming */
-  double T = 0, Gx, Gy;
+  real T = 0, Gx, Gy;
   for (int i = 0; i < 5; ++i) T += g[(0 * 5 + i) * n + c];
   body_force(P, T, &Gx, &Gy);
   vx += 0.5 * pc.phi * Gx;
@@ -725,7 +734,7 @@ static cell_macro macros_at(const orc_params *P, const orc_material *mat, size_t
   /* velocity carried by the scalars: the flow's, or an imposed one (tests) */
   r.usx = mat->u_imposed ? mat->u_imposed[c] : r.ux;
   r.usy = mat->u_imposed ? mat->u_imposed[n + c] : r.uy;
-  double u2 = r.ux * r.ux + r.uy * r.uy;
+  real u2 = r.ux * r.ux + r.uy * r.uy;
   r.p = 0.6 / pc.phi * s18 - 6.0 * rho0 * u2 / (15.0 * pc.phi * pc.phi);
   for (int s = 0; s < 3; ++s) {
     r.C[s] = 0;
@@ -737,20 +746,20 @@ static cell_macro macros_at(const orc_params *P, const orc_material *mat, size_t
 /* One coupled time step: (fs, gs) post-collision at t -> (fo, go) at t+1.
  * diag[D_NDIAG], Jx[nx], qx[nx] may be NULL. */
 void orc_step(const orc_params *P, const orc_material *mat, const uint8_t *mask,
-              const double *fs, const double *gs, double *fo, double *go, double *diag,
-              double *Jx, double *qx) {
+              const real *fs, const real *gs, real *fo, real *go, real *diag,
+              real *Jx, real *qx) {
   ensure_inverses();
   int nx = P->nx, ny = P->ny;
   size_t n = (size_t)nx * ny;
-  double *f = malloc(sizeof(double) * 9 * n);
-  double *g = malloc(sizeof(double) * 15 * n);
-  double *src = malloc(sizeof(double) * 3 * n);
-  double dloc[D_NDIAG];
+  real *f = (real *)malloc(sizeof(real) * 9 * n);
+  real *g = (real *)malloc(sizeof(real) * 15 * n);
+  real *src = (real *)malloc(sizeof(real) * 3 * n);
+  real dloc[D_NDIAG];
   stream(P, mat, mask, fs, gs, f, g, src, dloc, Jx, qx);
   if (diag) memcpy(diag, dloc, sizeof dloc);
 
-  double tau = 3.0 * P->nu + 0.5, S[9], Q[5], amax[3];
-  const double Cin[3] = {P->T_in, P->C_O2_in, P->C_H2O_in};
+  real tau = 3.0 * P->nu + 0.5, S[9], Q[5], amax[3];
+  const real Cin[3] = {P->T_in, P->C_O2_in, P->C_H2O_in};
   flow_S(tau, S);
   scalar_Q(Q);
   max_diffusivities(P, mat, mask, amax);
@@ -767,12 +776,12 @@ void orc_step(const orc_params *P, const orc_material *mat, const uint8_t *mask,
       cell_macro mc = macros_at(P, mat, n, c, f, g);
       porous_coef pc = porous(P, mat->phi[c], mat->K[c]);
       /* Eq. 7 force plus phi times the body force (uniform and buoyant) */
-      double un = sqrt(mc.ux * mc.ux + mc.uy * mc.uy), Gx, Gy;
+      real un = sqrt(mc.ux * mc.ux + mc.uy * mc.uy), Gx, Gy;
       body_force(P, mc.C[0], &Gx, &Gy);
-      double Fx = -pc.darcy * mc.ux - pc.forch * un * mc.ux + pc.phi * Gx;
-      double Fy = -pc.darcy * mc.uy - pc.forch * un * mc.uy + pc.phi * Gy;
+      real Fx = -pc.darcy * mc.ux - pc.forch * un * mc.ux + pc.phi * Gx;
+      real Fy = -pc.darcy * mc.uy - pc.forch * un * mc.uy + pc.phi * Gy;
       /* Eq. 1 in moment space */
-      double m[9], meq[9], G[9], ms[9];
+      real m[9], meq[9], G[9], ms[9];
       for (int k = 0; k < 9; ++k) {
         m[k] = 0;
         for (int i = 0; i < 9; ++i) m[k] += M9[k][i] * f[i * n + c];
@@ -782,30 +791,30 @@ void orc_step(const orc_params *P, const orc_material *mat, const uint8_t *mask,
       for (int k = 0; k < 9; ++k)
         ms[k] = m[k] - S[k] * (m[k] - meq[k]) + (1.0 - 0.5 * S[k]) * G[k];
       for (int i = 0; i < 9; ++i) {
-        double v = 0;
+        real v = 0;
         for (int k = 0; k < 9; ++k) v += MINV9[i][k] * ms[k];
         fo[i * n + c] = v;
       }
       /* Eq. 10 for T, O2, H2O */
-      double alpha[3] = {mat->alpha_T[c], mat->D_O2[c], mat->D_H2O[c]};
+      real alpha[3] = {mat->alpha_T[c], mat->D_O2[c], mat->D_H2O[c]};
       for (int s = 0; s < 3; ++s) {
         scalar_coef sc = scalar_coefficients(P, alpha[s], amax[s]);
-        double b = sc.b, Qs[5] = {Q[0], sc.q1, sc.q1, Q[3], Q[4]};
-        double C = mc.C[s];
+        real b = sc.b, Qs[5] = {Q[0], sc.q1, sc.q1, Q[3], Q[4]};
+        real C = mc.C[s];
         /* the advected value: C itself (Eq. 10 as printed) or its excess over
          * the inlet value; the two give the same continuum equation where
          * div u = 0, which the flow of Sec. 2.1 is built to satisfy */
-        double Ca = P->scalar_advection ? C - Cin[s] : C;
-        double nv[5], neq[5] = {C, mc.usx * Ca, mc.usy * Ca, b * C, 0.0}, ns[5];
+        real Ca = P->scalar_advection ? C - Cin[s] : C;
+        real nv[5], neq[5] = {C, mc.usx * Ca, mc.usy * Ca, b * C, 0.0}, ns[5];
         for (int k = 0; k < 5; ++k) {
           nv[k] = 0;
           for (int i = 0; i < 5; ++i) nv[k] += N5[k][i] * g[(s * 5 + i) * n + c];
         }
         for (int k = 0; k < 5; ++k) ns[k] = nv[k] - Qs[k] * (nv[k] - neq[k]);
-        double wsrc[5] = {(1.0 - b) / 5.0, (4.0 + b) / 20.0, (4.0 + b) / 20.0,
+        real wsrc[5] = {(1.0 - b) / 5.0, (4.0 + b) / 20.0, (4.0 + b) / 20.0,
                           (4.0 + b) / 20.0, (4.0 + b) / 20.0};
         for (int i = 0; i < 5; ++i) {
-          double v = 0;
+          real v = 0;
           for (int k = 0; k < 5; ++k) v += NINV5[i][k] * ns[k];
           go[(s * 5 + i) * n + c] = v + wsrc[i] * src[s * n + c];
         }
@@ -820,15 +829,15 @@ void orc_step(const orc_params *P, const orc_material *mat, const uint8_t *mask,
  * macroscopic values the collision of that step uses.
  * out: [6][ny][nx] = ux, uy, p, T, C_O2, C_H2O.  Solid cells give zeros. */
 void orc_fields(const orc_params *P, const orc_material *mat, const uint8_t *mask,
-                const double *fs, const double *gs, double *out, double *diag, double *Jx,
-                double *qx) {
+                const real *fs, const real *gs, real *out, real *diag, real *Jx,
+                real *qx) {
   ensure_inverses();
   int nx = P->nx, ny = P->ny;
   size_t n = (size_t)nx * ny;
-  double *f = malloc(sizeof(double) * 9 * n);
-  double *g = malloc(sizeof(double) * 15 * n);
-  double *src = malloc(sizeof(double) * 3 * n);
-  double dloc[D_NDIAG];
+  real *f = (real *)malloc(sizeof(real) * 9 * n);
+  real *g = (real *)malloc(sizeof(real) * 15 * n);
+  real *src = (real *)malloc(sizeof(real) * 3 * n);
+  real dloc[D_NDIAG];
   stream(P, mat, mask, fs, gs, f, g, src, dloc, Jx, qx);
   if (diag) memcpy(diag, dloc, sizeof dloc);
   for (size_t c = 0; c < n; ++c) {
@@ -849,12 +858,12 @@ void orc_fields(const orc_params *P, const orc_material *mat, const uint8_t *mas
 
 /* Moments of a post-collision state used by the steady-state residual:
  * out [5][ny][nx] = sum e_x f*, sum e_y f*, sum g*_T, sum g*_O2, sum g*_H2O. */
-void orc_state_moments(const orc_params *P, const uint8_t *mask, const double *fs,
-                       const double *gs, double *out) {
+void orc_state_moments(const orc_params *P, const uint8_t *mask, const real *fs,
+                       const real *gs, real *out) {
   int nx = P->nx, ny = P->ny;
   size_t n = (size_t)nx * ny;
   for (size_t c = 0; c < n; ++c) {
-    double jx = 0, jy = 0, C[3] = {0, 0, 0};
+    real jx = 0, jy = 0, C[3] = {0, 0, 0};
     if ((mask[c] & 3) != REG_SOLID) {
       for (int i = 0; i < 9; ++i) {
         jx += EX9[i] * fs[i * n + c];
@@ -876,57 +885,57 @@ void orc_state_moments(const orc_params *P, const uint8_t *mask, const double *f
  * [5][ny][nx]; r = max over the five of ||X - X_prev||_2 / ||X||_2, with
  * 0/0 read as 0 and x/0 (x > 0) as +inf.  The snapshot is then replaced by
  * the current moments.  Sums in FP64, cell by cell in row-major order. */
-double orc_residual(const orc_params *P, const uint8_t *mask, const double *fs,
-                    const double *gs, double *snapshot) {
+real orc_residual(const orc_params *P, const uint8_t *mask, const real *fs,
+                    const real *gs, real *snapshot) {
   int nx = P->nx, ny = P->ny;
   size_t n = (size_t)nx * ny;
-  double *X = malloc(sizeof(double) * 5 * n);
+  real *X = (real *)malloc(sizeof(real) * 5 * n);
   orc_state_moments(P, mask, fs, gs, X);
   for (size_t c = 0; c < n; ++c)
     if ((mask[c] & 3) != REG_SOLID) X[2 * n + c] -= P->T_in;
-  double r = 0.0;
+  real r = 0.0;
   for (int k = 0; k < 5; ++k) {
-    double num = 0.0, den = 0.0;
+    real num = 0.0, den = 0.0;
     for (size_t c = 0; c < n; ++c) {
-      double d = X[k * n + c] - snapshot[k * n + c];
+      real d = X[k * n + c] - snapshot[k * n + c];
       num += d * d;
       den += X[k * n + c] * X[k * n + c];
     }
-    double rk = den > 0 ? sqrt(num / den) : (num > 0 ? INFINITY : 0.0);
+    real rk = den > 0 ? sqrt(num / den) : (num > 0 ? INFINITY : 0.0);
     if (rk > r || isnan(rk)) r = rk;
   }
-  memcpy(snapshot, X, sizeof(double) * 5 * n);
+  memcpy(snapshot, X, sizeof(real) * 5 * n);
   free(X);
   return r;
 }
 
 /* ----------------------------------------- exposed pieces for the pins */
 
-void orc_matrices(double *M, double *Minv, double *N, double *Ninv) {
+void orc_matrices(real *M, real *Minv, real *N, real *Ninv) {
   ensure_inverses();
   memcpy(M, M9, sizeof M9);
   memcpy(Minv, MINV9, sizeof MINV9);
   memcpy(N, N5, sizeof N5);
   memcpy(Ninv, NINV5, sizeof NINV5);
 }
-void orc_flow_meq(double phi, double p, double ux, double uy, double *meq) {
+void orc_flow_meq(real phi, real p, real ux, real uy, real *meq) {
   flow_meq(phi, p, ux, uy, meq);
 }
-void orc_flow_G(double phi, double ux, double uy, double Fx, double Fy, double *G) {
+void orc_flow_G(real phi, real ux, real uy, real Fx, real Fy, real *G) {
   flow_G(phi, ux, uy, Fx, Fy, G);
 }
-void orc_flow_S(double tau, double *S) { flow_S(tau, S); }
-void orc_scalar_Q(double *Q) { scalar_Q(Q); }
-void orc_d2q5_eq(double C, double ux, double uy, double b, double *geq) {
+void orc_flow_S(real tau, real *S) { flow_S(tau, S); }
+void orc_scalar_Q(real *Q) { scalar_Q(Q); }
+void orc_d2q5_eq(real C, real ux, real uy, real b, real *geq) {
   ensure_inverses();
   d2q5_equilibrium(C, ux, uy, b, geq);
 }
-double orc_k_surface(const orc_params *P, double T) { return k_surface(P, T); }
-double orc_k_volume(const orc_params *P, double T) { return k_volume(P, T); }
-double orc_heat_per_O2(const orc_params *P, double T) { return heat_per_O2(P, T); }
-double orc_k_surface_anodic(const orc_params *P, double T) { return k_surface_anodic(P, T); }
-double orc_k_volume_anodic(const orc_params *P, double T) { return k_volume_anodic(P, T); }
-void orc_porous(const orc_params *P, double phi, double K, double *out5) {
+real orc_k_surface(const orc_params *P, real T) { return k_surface(P, T); }
+real orc_k_volume(const orc_params *P, real T) { return k_volume(P, T); }
+real orc_heat_per_O2(const orc_params *P, real T) { return heat_per_O2(P, T); }
+real orc_k_surface_anodic(const orc_params *P, real T) { return k_surface_anodic(P, T); }
+real orc_k_volume_anodic(const orc_params *P, real T) { return k_volume_anodic(P, T); }
+void orc_porous(const orc_params *P, real phi, real K, real *out5) {
   porous_coef c = porous(P, phi, K);
   out5[0] = c.phi; out5[1] = c.darcy; out5[2] = c.forch; out5[3] = c.l0; out5[4] = c.l1;
 }

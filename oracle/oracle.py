@@ -19,8 +19,11 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
 _OUT = os.path.join(_HERE, "_build", "liboracle.so")
+_TSRC = os.path.join(_HERE, "lbm_oracle_tangent.cc")
+_TOUT = os.path.join(_HERE, "_build", "liboracle_tangent.so")
 _lock = threading.Lock()
 _lib = None
+_tlib = None
 
 
 def build_oracle(force: bool = False) -> str:
@@ -32,6 +35,19 @@ def build_oracle(force: bool = False) -> str:
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _OUT)
     return _OUT
+
+
+def build_tangent(force: bool = False) -> str:
+    """Compile the oracle's tangent (lbm_oracle.c as C++ with dual numbers,
+    lbm_oracle_tangent.cc) with plain g++ into oracle/_build."""
+    os.makedirs(os.path.dirname(_TOUT), exist_ok=True)
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_TSRC))
+    if force or not os.path.exists(_TOUT) or os.path.getmtime(_TOUT) < newest:
+        tmp = _TOUT + f".{os.getpid()}.tmp"
+        subprocess.check_call(["g++", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c++17",
+                               "-o", tmp, _TSRC, "-lm"])
+        os.replace(tmp, _TOUT)
+    return _TOUT
 
 
 class Params(C.Structure):
@@ -204,3 +220,150 @@ class Oracle:
         ix = self.Jx * scale
         heat = self.qx * P.rho_cp_f * P.dx_cm / P.dt_s
         return float(ix.mean()), float(heat.mean()), ix
+
+
+# ----------------------------------------------------------------- tangent
+
+class Dual(C.Structure):
+    """One real number of the tangent build: value and directional derivative."""
+    _fields_ = [("v", C.c_double), ("d", C.c_double)]
+
+
+def _dual_struct(name, base):
+    """The layout of a struct of the tangent build: every double of `base`
+    becomes a Dual, arrays of doubles arrays of Duals."""
+    fields = []
+    for fname, t in base._fields_:
+        if t is C.c_double:
+            fields.append((fname, Dual))
+        elif isinstance(t, type) and issubclass(t, C.Array) and t._type_ is C.c_double:
+            fields.append((fname, Dual * t._length_))
+        elif t is C.POINTER(C.c_double):
+            fields.append((fname, C.POINTER(Dual)))
+        else:
+            fields.append((fname, t))
+    return type(name, (C.Structure,), {"_fields_": fields})
+
+
+TParams = _dual_struct("TParams", Params)
+TMaterial = _dual_struct("TMaterial", Material)
+_dd = C.POINTER(Dual)
+
+
+def tangent_lib():
+    global _tlib
+    with _lock:
+        if _tlib is None:
+            L = C.CDLL(build_tangent())
+            L.orc_build_mask.argtypes = [_P(TParams), _u8, _u8]
+            L.orc_init.argtypes = [_P(TParams), _P(TMaterial), _u8, _dd, _dd]
+            L.orc_step.argtypes = [_P(TParams), _P(TMaterial), _u8, _dd, _dd, _dd, _dd, _dd,
+                                   _dd, _dd]
+            L.orc_fields.argtypes = [_P(TParams), _P(TMaterial), _u8, _dd, _dd, _dd, _dd, _dd,
+                                     _dd]
+            _tlib = L
+    return _tlib
+
+
+def _pair(value, deriv=None):
+    """(..., 2) array of value and derivative parts."""
+    value = np.asarray(value, np.float64)
+    out = np.zeros(value.shape + (2,))
+    out[..., 0] = value
+    if deriv is not None:
+        out[..., 1] = np.broadcast_to(np.asarray(deriv, np.float64), value.shape)
+    return out
+
+
+class TangentOracle:
+    """The oracle run in dual numbers: every quantity carries its derivative
+    along one direction w of the inputs, so N steps give the state after N
+    steps and its directional derivative J_N w (forward mode, exact up to
+    rounding; the oracle's own derivative of its step).
+
+    ``dparams`` maps parameter names (e.g. "u_in_avg", "dp_in") to their
+    direction components, ``dmaterial`` material names ("phi", "K",
+    "alpha_T", "D_O2", "D_H2O") to per-cell direction arrays; the state's
+    direction is given with ``set_state``.  State arrays have a trailing
+    axis of two: value, derivative.
+    """
+
+    def __init__(self, params: dict, material: dict, solid=None, dparams=None, dmaterial=None):
+        self.L = tangent_lib()
+        dparams, dmaterial = dparams or {}, dmaterial or {}
+        p = dict(params)
+        vals = {}
+        for name, t in TParams._fields_:
+            if name not in p:
+                continue
+            if t is Dual:
+                vals[name] = Dual(float(p[name]), float(dparams.get(name, 0.0)))
+            elif isinstance(t, type) and issubclass(t, C.Array):
+                v = np.asarray(p[name], np.float64).ravel()
+                dv = np.asarray(dparams.get(name, np.zeros_like(v)), np.float64).ravel()
+                vals[name] = (Dual * t._length_)(*[Dual(a, b) for a, b in zip(v, dv)])
+            else:
+                vals[name] = p[name]
+        self.P = TParams(**vals)
+        self.Pv = Params(**{k: v for k, v in params.items() if k != "C_wall"})
+        nx, ny = self.P.nx, self.P.ny
+        self.nx, self.ny = nx, ny
+        self._mat = {}
+        for k in ("phi", "K", "alpha_T", "D_O2", "D_H2O"):
+            v = np.broadcast_to(np.asarray(material[k], np.float64), (ny, nx))
+            self._mat[k] = np.ascontiguousarray(_pair(v, dmaterial.get(k)))
+        if material.get("u_imposed") is not None:
+            self._mat["u_imposed"] = np.ascontiguousarray(_pair(material["u_imposed"]))
+        if material.get("sigma") is not None:
+            v = np.broadcast_to(np.asarray(material["sigma"], np.float64), (ny, nx))
+            self._mat["sigma"] = np.ascontiguousarray(_pair(v))
+        self.M = TMaterial(**{k: v.ctypes.data_as(_dd) for k, v in self._mat.items()})
+        self.solid = None if solid is None else np.ascontiguousarray(solid, np.uint8)
+        self.mask = np.zeros((ny, nx), np.uint8)
+        self.L.orc_build_mask(C.byref(self.P),
+                              None if self.solid is None else _ptr(self.solid, C.c_uint8),
+                              _ptr(self.mask, C.c_uint8))
+        self.f = np.zeros((9, ny, nx, 2))
+        self.g = np.zeros((3, 5, ny, nx, 2))
+        self.L.orc_init(C.byref(self.P), C.byref(self.M), _ptr(self.mask, C.c_uint8),
+                        self.f.ctypes.data_as(_dd), self.g.ctypes.data_as(_dd))
+        self.f_prev, self.g_prev = self.f.copy(), self.g.copy()
+        self.Jx = np.zeros((self.nx, 2))
+        self.qx = np.zeros((self.nx, 2))
+        self.diag = np.zeros((10, 2))
+
+    def set_state(self, f, g, df=None, dg=None):
+        """State (full values, f (9, ny, nx), g (3, 5, ny, nx)) and its
+        direction."""
+        self.f = np.ascontiguousarray(_pair(f, df))
+        self.g = np.ascontiguousarray(_pair(g, dg))
+        return self
+
+    def step(self, n: int = 1):
+        for _ in range(n):
+            fo, go = np.empty_like(self.f), np.empty_like(self.g)
+            self.L.orc_step(C.byref(self.P), C.byref(self.M), _ptr(self.mask, C.c_uint8),
+                            self.f.ctypes.data_as(_dd), self.g.ctypes.data_as(_dd),
+                            fo.ctypes.data_as(_dd), go.ctypes.data_as(_dd),
+                            self.diag.ctypes.data_as(_dd), self.Jx.ctypes.data_as(_dd),
+                            self.qx.ctypes.data_as(_dd))
+            self.f_prev, self.g_prev, self.f, self.g = self.f, self.g, fo, go
+        return self
+
+    def fields(self):
+        """Fields of the last step (as Oracle.fields), each a (value,
+        derivative) pair of arrays."""
+        out = np.zeros((6, self.ny, self.nx, 2))
+        diag, Jx, qx = np.zeros((10, 2)), np.zeros((self.nx, 2)), np.zeros((self.nx, 2))
+        self.L.orc_fields(C.byref(self.P), C.byref(self.M), _ptr(self.mask, C.c_uint8),
+                          self.f_prev.ctypes.data_as(_dd), self.g_prev.ctypes.data_as(_dd),
+                          out.ctypes.data_as(_dd), diag.ctypes.data_as(_dd),
+                          Jx.ctypes.data_as(_dd), qx.ctypes.data_as(_dd))
+        names = ("ux", "uy", "p", "T", "C_O2", "C_H2O")
+        return {k: (out[i, ..., 0], out[i, ..., 1]) for i, k in enumerate(names)}
+
+    def current_density(self):
+        """(i_avg, d i_avg) in A/cm^2 of the last step's reaction."""
+        P = self.Pv
+        scale = 4.0 * P.F * P.c_tot * P.dx_cm / P.dt_s
+        return float(self.Jx[:, 0].mean() * scale), float(self.Jx[:, 1].mean() * scale)

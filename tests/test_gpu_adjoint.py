@@ -2,15 +2,17 @@
 
 1. One transposed step against finite differences of the FP64 GPU step and
    of the independent FP64 oracle's step (dot-product test) in state and
-   parameter directions.
+   parameter directions, and against the oracle's own derivative of its
+   step (its tangent, the step run in dual numbers) to rounding.
 2. Gradients of the objectives (mean current density, hottest catalyst-row
    temperature) after N steps against FP64 central finite differences of the
-   independent oracle, within 1e-3 relative.
+   independent oracle, within 1e-3 relative, and against the oracle's
+   tangent through the same steps, within 1e-9.
 """
 import numpy as np
 import pytest
 
-from oracle import Oracle
+from oracle import Oracle, TangentOracle
 from oracle.params import lattice_problem
 from paper_2103_01444_gb300 import workloads
 
@@ -135,6 +137,93 @@ def test_one_step_transpose_dot_product(name, mode):
             step_from(s0, params=dict(params, **{key: params[key] - h})))
     fdu = np.sum(lam * diff) / (2 * h)
     assert abs(fdu - g["u_in"]) <= 1e-4 * max(abs(fdu), 1e-12), (fdu, g["u_in"])
+
+
+def tangent_direction(case, params, mat, live, rng):
+    """A direction over the GDL's phi, K and D_O2 (relative to each field)
+    and the inlet drive (relative to its value).  The GDL lies below the
+    channel, whose clear fluid holds each scalar's largest diffusivity, so the
+    direction leaves the Fickian mode's per-scalar b fixed, as the adjoint
+    treats it."""
+    gdl = np.zeros((case["ny"], case["nx"]), bool)
+    gdl[case["ny_cl"]:case["ny_cl"] + case["ny_gdl"]] = True
+    gdl &= live
+    w = {k: np.where(gdl, rng.standard_normal(gdl.shape) * mat[k], 0.0)
+         for k in ("phi", "K", "D_O2")}
+    w["u_in"] = params[drive_key(case)]
+    return w
+
+
+@pytest.mark.parametrize("name", ["film", "vol", "grains", "film-bv", "vol-bv", "film-p",
+                                  "grains-p", "film-sa", "vol-sa", "grains-p-sa"])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_one_step_transpose_is_the_transpose_of_the_oracle_tangent(name, mode):
+    """<lam, J w> from the oracle's own derivative of its step (its tangent:
+    the step run in dual numbers) equals <J^T lam, w> from lbm_vjp, with w a
+    direction in the state, phi, K, D_O2 and the inlet drive at once (FP64
+    storage): the transposed step is the transpose of the oracle's step to
+    rounding, not only to a finite difference's accuracy."""
+    case = case_of(name)
+    d = gpu(case, mode=mode)
+    d.step(25)
+    s0 = d.state()
+    ny, nx = case["ny"], case["nx"]
+    live = (d.mask() & 3) != 3
+    rng = np.random.default_rng(17)
+    lam = rng.standard_normal(s0.shape) * live
+    lam_prev, g = d.vjp(lam)
+    params, mat, solid = lattice_problem(case, interface_mode=mode)
+    w = tangent_direction(case, params, mat, live, rng)
+    ws = rng.standard_normal(s0.shape) * live
+    t = TangentOracle(params, mat, solid, dparams={drive_key(case): w["u_in"]},
+                      dmaterial={k: w[k] for k in ("phi", "K", "D_O2")})
+    t.set_state(s0[:9], s0[9:].reshape(3, 5, ny, nx), ws[:9], ws[9:].reshape(3, 5, ny, nx))
+    t.step(1)
+    Jw = np.concatenate([t.f[..., 1], t.g[..., 1].reshape(15, ny, nx)]) * live
+    lhs = np.sum(lam * Jw)
+    terms = [lam_prev * ws] + [g[k] * w[k] for k in ("phi", "K", "D_O2")]
+    rhs = sum(float(np.sum(x)) for x in terms) + g["u_in"] * w["u_in"]
+    scale = sum(float(np.abs(x).sum()) for x in terms) + abs(g["u_in"] * w["u_in"])
+    assert abs(lhs - rhs) <= 1e-11 * scale, (lhs, rhs, scale)
+
+
+@pytest.mark.parametrize("name,mode,objective", [("film", 0, 0), ("film", 1, 1), ("vol", 1, 0),
+                                                 ("grains", 0, 1), ("film-bv1", 0, 0),
+                                                 ("vol-bv1", 1, 0), ("film-p", 1, 0),
+                                                 ("grains-p", 1, 1), ("vol-p-sa", 1, 1)])
+def test_gradient_is_the_oracle_tangent_of_the_objective(name, mode, objective):
+    """lbm_grad over 40 steps (checkpoint segments of 7, records recomputed
+    and kept) against the oracle's tangent through the same 40 steps from the
+    same state: <grad, w> equals the objective's derivative along w, for w
+    over the GDL's phi, K, D_O2 and the inlet drive, to 1e-9."""
+    case = case_of(name)
+    N = 40
+    d = gpu(case, mode=mode)
+    s0 = d.state()
+    ny, nx = case["ny"], case["nx"]
+    live = (d.mask() & 3) != 3
+    params, mat, solid = lattice_problem(case, interface_mode=mode)
+    rng = np.random.default_rng(23)
+    w = tangent_direction(case, params, mat, live, rng)
+    t = TangentOracle(params, mat, solid, dparams={drive_key(case): w["u_in"]},
+                      dmaterial={k: w[k] for k in ("phi", "K", "D_O2")})
+    t.set_state(s0[:9], s0[9:].reshape(3, 5, ny, nx))
+    t.step(N)
+    if objective == 0:
+        Jt, dJ = t.current_density()
+    else:
+        T, dT = t.fields()["T"]
+        xs = int(np.argmax(T[0]))
+        Jt, dJ = T[0, xs], dT[0, xs]
+    for limit in (-1, 0):          # records kept, and every segment recomputed
+        d.set_grad_memory(limit)
+        J, g = d.grad(objective, N, segment=7)
+        assert J == pytest.approx(Jt, rel=1e-9)
+        terms = [float(np.sum(g[k] * w[k])) for k in ("phi", "K", "D_O2")]
+        terms.append(g["u_in"] * w["u_in"])
+        scale = sum(float(np.abs(g[k] * w[k]).sum()) for k in ("phi", "K", "D_O2"))
+        scale += abs(g["u_in"] * w["u_in"])
+        assert abs(sum(terms) - dJ) <= 1e-9 * max(abs(dJ), scale), (sum(terms), dJ, scale)
 
 
 def oracle_objective(case, mode, objective, N, material=None, drive=None, x_star=None):
