@@ -40,6 +40,15 @@ def test_binding_loads_without_gpu(libpath):
     assert L.lbm_last_error() is not None
 
 
+def test_grad_memory_limit_argument_checks(libpath):
+    """lbm_set_grad_memory refuses a null domain with EINVAL before touching
+    any device (no GPU needed); the limit itself is checked by the GPU tests."""
+    L = lbm.load_library(libpath)
+    einval = next(k for k, v in lbm.STATUS.items() if v == "LBM_EINVAL")
+    assert L.lbm_set_grad_memory(None, 0) == einval
+    assert b"null" in L.lbm_last_error()
+
+
 def test_param_structs_match_header(tmp_path):
     """The ctypes mirrors have the header's field names, offsets and sizes
     (a C program compiled against the header prints them)."""

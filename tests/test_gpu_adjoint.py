@@ -373,6 +373,9 @@ def test_stored_and_recomputed_records_give_the_same_gradient(name, mode, object
     case = case_of(name)
     N, seg = 45, 7
     d = gpu(case, precision, mode)
+    from paper_2103_01444_gb300.lbm import LbmError
+    with pytest.raises(LbmError):
+        d.set_grad_memory(-2)
     ref = None
     for limit in (-1, 0, 200_000, 2_000_000, 8_000_000):
         d.set_grad_memory(limit)
