@@ -359,6 +359,20 @@ lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t se
  * domain or bytes < -1. */
 lbm_status lbm_set_grad_memory(lbm_domain *d, int64_t bytes);
 
+/* Self-check of the device code's indexing (no counterpart in the paper; it
+ * stands in for a memory checker).  A library built with bounds checks
+ * (paper_2103_01444_gb300.build.build(bounds_check=True), which compiles
+ * with -DPEMLBM_BOUNDS_CHECK into libpemlbm_checked.so) tests the index of
+ * every population, mask, material-index and palette access of the step
+ * kernels, and the lambda and record accesses of the adjoint kernels,
+ * against the extent of its buffer; an access outside it is skipped (no
+ * trap) and the first one recorded.  This call waits for the device, writes
+ * the first recorded access since the previous call to *first_bad (site <<
+ * 48 | index; 0 for none) and clears the record.  EINVAL for a null
+ * argument; ESTATE (and *first_bad = 0) in a library built without the
+ * checks. */
+lbm_status lbm_bounds_check(uint64_t *first_bad);
+
 /* One transposed step at the current state s: given lam_next (host
  * [24][ny][nx], the adjoint of the state after one step), writes lam_prev =
  * (d step / d s)^T lam_next and the parameter gradients of

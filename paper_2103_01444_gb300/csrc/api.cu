@@ -185,6 +185,7 @@ KArgs make_args(const lbm_domain *d) {
   a.halo_lo = d->halo_lo;
   a.halo_hi = d->halo_hi;
   a.wall_dir = p.wall_dirichlet;
+  a.npal = d->npal;
   for (int k = 0; k < 3; ++k)
     for (int s = 0; s < 3; ++s) a.Cwall[k][s] = p.C_wall[k][s];
   a.u_in_avg = p.inlet_mode == 0 ? p.u_in_avg : 0.0;
@@ -1576,6 +1577,22 @@ lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t se
   }
   finish_lambda(d, w, cur);   // adds the last step's outlet term to gphi
   return copy_grads_out(d, w, dphi, dK, dD_O2, du_in, on_device == 1);
+}
+
+lbm_status lbm_bounds_check(uint64_t *first_bad) {
+  if (!first_bad) return fail(LBM_EINVAL, "null argument");
+  *first_bad = 0;
+#ifndef PEMLBM_BOUNDS_CHECK
+  return fail(LBM_ESTATE, "this library was built without bounds checks");
+#else
+  CK(cudaDeviceSynchronize());
+  const unsigned long long v[4] = {bounds_first_bad<float>(), bounds_first_bad<double>(),
+                                   bounds_first_bad<__nv_bfloat16>(), bounds_first_bad<__half>()};
+  for (unsigned long long x : v)
+    if (x && !*first_bad) *first_bad = x;
+  CK(cudaGetLastError());
+  return LBM_OK;
+#endif
 }
 
 lbm_status lbm_set_grad_memory(lbm_domain *d, int64_t bytes) {

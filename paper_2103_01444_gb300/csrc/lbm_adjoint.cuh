@@ -374,6 +374,9 @@ __device__ __forceinline__ void pull_flow_rev(const RecPtrs<R> &rp, const KArgsT
     acc_shared(&Oacc[opi], lam);
     return;
   }
+#ifdef PEMLBM_BOUNDS_CHECK
+  if (!in_bounds((long long)i * a.plane + sc, 24 * a.plane, 33)) return;
+#endif
   out[(long long)i * a.plane + sc] = lam;
 }
 
@@ -420,6 +423,9 @@ __device__ __forceinline__ void pull_scalar_rev(const KArgsT<R> &a, const uint8_
     acc_shared(&Oacc[q + opi], lam);
     return;
   }
+#ifdef PEMLBM_BOUNDS_CHECK
+  if (!in_bounds((long long)(q + i) * a.plane + sc, 24 * a.plane, 34)) return;
+#endif
   out[(long long)(q + i) * a.plane + sc] = lam;
 }
 
@@ -457,15 +463,21 @@ __device__ __forceinline__ void adj_interior_cell(const RecPtrs<R> &rp,
   // that their latency overlaps the record loads (no other thread of the
   // launch touches them)
   R gacc[3] = {B.gphi[c], B.gK[c], B.gD[c]};
-  const CellRec<R> rec = ld_cell_rec(rp.cell + 8 * c);
+  const CellRec<R> rec = in_bounds(8 * c + 7, 8 * P, 32) ? ld_cell_rec(rp.cell + 8 * c)
+                                                         : CellRec<R>{};
   const R vx = rec.v[0], vy = rec.v[1], n1 = rec.v[5], n2 = rec.v[6];
   const bool vol = a.mode == 1 && (m & REG_MASK) == REG_CATALYST;
   // lambda^n of link q: every link of an interior cell is pushed; a
   // catalyst cell adds the own-use adjoint the previous step left in O_in
   auto lam_at = [&](int q) -> R {
+    if (!in_bounds(q * P + c, 24 * P, 30)) return R(0);
     R v = ld_r(B.lam + q * P + c);
     if (vol && q >= 9 && q < 19) v += ld_r(B.O_in + q * P + c);
     return v;
+  };
+  // pushes into lambda^{n-1} (the bounds-checked build skips one outside it)
+  auto push = [&](long long k, R v) {
+    if (in_bounds(k, 24 * P, 31)) B.lam_out[k] = v;
   };
   // forward reaction terms (kept for the reverse)
   R theta = 0, k = 0, ka = 0, Cv = 0, S_vol = 0;
@@ -502,8 +514,7 @@ __device__ __forceinline__ void adj_interior_cell(const RecPtrs<R> &rp,
                             s == 1 ? n2 : R(0), srcv[s], lo, lcg, lux, luy, lsrc[s], lb[s], lw1[s],
                             lq1[s]);
 #pragma unroll
-      for (int i = 0; i < 5; ++i)
-        B.lam_out[(9 + 5 * s + i) * P + c - ey9(i) * W - ex9(i)] = lcg[i];
+      for (int i = 0; i < 5; ++i) push((9 + 5 * s + i) * P + c - ey9(i) * W - ex9(i), lcg[i]);
     }
     R lo[9];
 #pragma unroll
@@ -511,7 +522,7 @@ __device__ __forceinline__ void adj_interior_cell(const RecPtrs<R> &rp,
     flow_rev<R>(a, mc, vx, vy, lo, lux, luy, lcf, lphi, ldarcy, lforch, ll0, ll1, lip);
   }
 #pragma unroll
-  for (int i = 0; i < 9; ++i) B.lam_out[i * P + c - ey9(i) * W - ex9(i)] = lcf[i];
+  for (int i = 0; i < 9; ++i) push(i * P + c - ey9(i) * W - ex9(i), lcf[i]);
   // volumetric sources (-S h / sigma, S, -2 S): own-use adjoints of theta, C_O2
   if (vol) {
     const R lS = -R(a.hpo) * mc.inv_sigma * lsrc[0] + lsrc[1] - R(2) * lsrc[2];

@@ -29,6 +29,31 @@
 
 namespace pemlbm {
 
+// ------------------------------------------------------------ bounds checks
+// A build with -DPEMLBM_BOUNDS_CHECK (the checked library of build.py) tests
+// the index of every population, mask, material-index and palette access of
+// the step's device code, and of the adjoint's lambda accesses, against the
+// extent of its buffer.  An access outside it is skipped (a load gives 0, a
+// mask load a solid cell) and the first one of each translation unit is
+// recorded as site << 48 | (index & (2^48 - 1)) for lbm_bounds_check.
+// Nothing traps.  Without the flag every check is the constant true.
+#ifdef PEMLBM_BOUNDS_CHECK
+static __device__ unsigned long long g_bounds_first_bad = 0;
+__device__ __forceinline__ bool in_bounds(long long i, long long n, unsigned site) {
+  if (i >= 0 && i < n) return true;
+  atomicCAS(&g_bounds_first_bad, 0ull,
+            ((unsigned long long)site << 48) | ((unsigned long long)i & 0xffffffffffffull));
+  return false;
+}
+#else
+__device__ __forceinline__ constexpr bool in_bounds(long long, long long, unsigned) { return true; }
+#endif
+// Elements of a population buffer: 24 planes and the guard that keeps the
+// unconditional pulls of the top row inside the allocation.
+__host__ __device__ __forceinline__ constexpr long long pop_extent(long long plane, int nxp) {
+  return 24 * plane + nxp + 64;
+}
+
 // Element offset of population q (0-8 flow, 9 + 5 s + i link i of scalar s)
 // of cell c in a buffer whose planes hold P cells each.
 __host__ __device__ __forceinline__ constexpr long long pop_index(int q, long long c, long long P) {
@@ -238,6 +263,7 @@ template <typename F> struct KArgsT {
                             // them read the ghost column (x = -1 or nx) the exchange fills
   int wall_dir;             // bit 3 k + s: scalar s fixed to Cwall[k][s] on wall k
   F Cwall[3][3];            // k: 0 the x = 0 end, 1 the x = nx - 1 end, 2 the bottom
+  int npal;                 // palette entries (the bounds-checked build tests indices)
 };
 using KArgs = KArgsT<double>;
 
@@ -254,7 +280,7 @@ template <typename F> __host__ __device__ inline KArgsT<F> narrow_args(const KAr
   r.h_ch = F(a.h_ch); r.Q3 = F(a.Q3);
   r.inlet_pressure = a.inlet_pressure; r.dp_in = F(a.dp_in);
   r.gam_x = F(a.gam_x); r.gam_y = F(a.gam_y); r.buoy_off = F(a.buoy_off);
-  r.closed_x = a.closed_x; r.wall_dir = a.wall_dir;
+  r.closed_x = a.closed_x; r.wall_dir = a.wall_dir; r.npal = a.npal;
   r.halo_lo = a.halo_lo; r.halo_hi = a.halo_hi;
   for (int k = 0; k < 3; ++k)
     for (int s = 0; s < 3; ++s) r.Cwall[k][s] = F(a.Cwall[k][s]);
@@ -269,6 +295,28 @@ template <typename F> __host__ __device__ inline KArgsT<F> narrow_args(const KAr
   r.kA_surf_a = F(a.kA_surf_a); r.kA_vol_a = F(a.kA_vol_a);
   r.k_ein_a = F(a.k_ein_a); r.k_c1_a = F(a.k_c1_a);
   return r;
+}
+
+// Mask, material-index and palette loads of the step (checked in the
+// bounds-checked build; the mask has two planes).
+template <typename F>
+__device__ __forceinline__ uint8_t ld_mask(const uint8_t *__restrict__ mask, long long i,
+                                           const KArgsT<F> &a, unsigned site) {
+#ifdef PEMLBM_BOUNDS_CHECK
+  if (!in_bounds(i, 2 * a.plane, site)) return uint8_t(REG_SOLID);
+#endif
+  return mask[i];
+}
+template <typename F>
+__device__ __forceinline__ uint16_t ld_mid(const uint16_t *__restrict__ mid, long long i,
+                                           const KArgsT<F> &a, unsigned site) {
+#ifdef PEMLBM_BOUNDS_CHECK
+  if (!in_bounds(i, a.plane, site)) return uint16_t(0);
+  const uint16_t k = mid[i];
+  return in_bounds(k, a.npal, site + 1) ? k : uint16_t(0);
+#else
+  return mid[i];
+#endif
 }
 
 // One case of a batched step (device table entry).
@@ -330,6 +378,11 @@ template <typename S, bool CG = false> struct Pops {
   long long plane;
   int nxp;
   __device__ __forceinline__ auto at(int q, int x, int y) const {
+#ifdef PEMLBM_BOUNDS_CHECK
+    const long long i = pop_index(q, (long long)y * nxp + x, plane);
+    using V = decltype(ldp<CG>(p));
+    if (!in_bounds(i, pop_extent(plane, nxp), 1)) return V(0);
+#endif
     return ldp<CG>(p + pop_index(q, (long long)y * nxp + x, plane));
   }
 };
@@ -360,7 +413,7 @@ __device__ R pull_flow_edge(const Pops<S, CG> &src, const KArgsT<R> &a, const ui
   if (sy < 0 || sy >= a.ny) return R(src.at(OP[i], x, y));            // wall
   if ((sx < 0 && a.halo_lo) || (sx >= a.nx && a.halo_hi)) {
     // the neighbour slab's ghost, unless that cell is solid (second mask plane)
-    if ((m & M_NEAR_SOLID) && ((mask[a.plane + (long long)y * a.nxp + x] >> (i - 1)) & 1u))
+    if ((m & M_NEAR_SOLID) && ((ld_mask(mask, a.plane + (long long)y * a.nxp + x, a, 10) >> (i - 1)) & 1u))
       return R(src.at(OP[i], x, y));
     return v;
   }
@@ -383,22 +436,22 @@ __device__ R pull_flow_edge(const Pops<S, CG> &src, const KArgsT<R> &a, const ui
       // end wall
       const int vx = in ? 0 : a.nx - 1;
       const long long vc = (long long)sy * a.nxp + vx;
-      if (in && !(mask[vc] & M_INLET)) return R(src.at(OP[i], x, y));
+      if (in && !(ld_mask(mask, vc, a, 11) & M_INLET)) return R(src.at(OP[i], x, y));
       R d[9];
 #pragma unroll
       for (int k = 0; k < 9; ++k) d[k] = R(src.at(k, vx, sy));
       R jx = d[1] - d[3] + d[5] - d[6] - d[7] + d[8];
       R jy = d[2] - d[4] + d[5] + d[6] - d[7] - d[8];
       R s18 = ((d[1] + d[3]) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8]));
-      R inv_phi = pal[mid[vc]].inv_phi;
+      R inv_phi = pal[ld_mid(mid, vc, a, 12)].inv_phi;
       R dP = (in ? R(a.dp_in) : R(0)) + (R(-0.6) * s18 + R(0.4) * (jx * jx + jy * jy) * inv_phi);
       return d[i] + lam9<R>(i) * dP;
     }
-    if ((m & M_NEAR_SOLID) && (mask[(long long)sy * a.nxp + sx] & REG_MASK) == REG_SOLID)
+    if ((m & M_NEAR_SOLID) && (ld_mask(mask, (long long)sy * a.nxp + sx, a, 14) & REG_MASK) == REG_SOLID)
       return R(src.at(OP[i], x, y));
     return R(src.at(i, sx, sy));                                      // periodic wrap
   }
-  if ((m & M_NEAR_SOLID) && (mask[(long long)sy * a.nxp + sx] & REG_MASK) == REG_SOLID)
+  if ((m & M_NEAR_SOLID) && (ld_mask(mask, (long long)sy * a.nxp + sx, a, 14) & REG_MASK) == REG_SOLID)
     return R(src.at(OP[i], x, y));                                    // solid grain
   return v;
 }
@@ -436,7 +489,7 @@ __device__ R pull_scalar_edge(const Pops<S, CG> &src, const KArgsT<R> &a, const 
   }
   if ((sx < 0 && a.halo_lo) || (sx >= a.nx && a.halo_hi)) {
     // the neighbour slab's ghost, unless that cell is solid (second mask plane)
-    if ((m & M_NEAR_SOLID) && ((mask[a.plane + (long long)y * a.nxp + x] >> (i - 1)) & 1u))
+    if ((m & M_NEAR_SOLID) && ((ld_mask(mask, a.plane + (long long)y * a.nxp + x, a, 15) >> (i - 1)) & 1u))
       return R(src.at(q + OP[i], x, y));
     return v;
   }
@@ -458,11 +511,11 @@ __device__ R pull_scalar_edge(const Pops<S, CG> &src, const KArgsT<R> &a, const 
     } else {
       return R(src.at(q + i, a.nx - 1, y));                           // fully developed
     }
-    if ((m & M_NEAR_SOLID) && (mask[(long long)sy * a.nxp + sx] & REG_MASK) == REG_SOLID)
+    if ((m & M_NEAR_SOLID) && (ld_mask(mask, (long long)sy * a.nxp + sx, a, 14) & REG_MASK) == REG_SOLID)
       return R(src.at(q + OP[i], x, y));
     return R(src.at(q + i, sx, sy));
   }
-  if ((m & M_NEAR_SOLID) && (mask[(long long)sy * a.nxp + sx] & REG_MASK) == REG_SOLID)
+  if ((m & M_NEAR_SOLID) && (ld_mask(mask, (long long)sy * a.nxp + sx, a, 14) & REG_MASK) == REG_SOLID)
     return R(src.at(q + OP[i], x, y));
   return v;
 }
@@ -541,6 +594,13 @@ __device__ __forceinline__ void load_interior(const Pops<S, CG> &src, const KArg
   const long long from[5] = {0, -1, -W, 1, W};
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
+#ifdef PEMLBM_BOUNDS_CHECK
+    const long long k = 4 * (i * P + c0 + from[i]), n = pop_extent(P, a.nxp);
+    if (!in_bounds(k, n, 2) || !in_bounds(k + 3, n, 2)) {
+      c.f[i] = c.g[0][i] = c.g[1][i] = c.g[2][i] = R(0);
+      continue;
+    }
+#endif
     const auto v = ldq<CG>(src.p + 4 * (i * P + c0 + from[i]));
     c.f[i] = v.v[0];
     c.g[0][i] = v.v[1];
@@ -548,6 +608,15 @@ __device__ __forceinline__ void load_interior(const Pops<S, CG> &src, const KArg
     c.g[2][i] = v.v[3];
   }
   const S *d = src.p + 20 * P + c0;
+#ifdef PEMLBM_BOUNDS_CHECK
+  const long long n = pop_extent(P, a.nxp), dk[4] = {20 * P + c0 - W - 1, 21 * P + c0 - W + 1,
+                                                     22 * P + c0 + W + 1, 23 * P + c0 + W - 1};
+  if (!in_bounds(dk[0], n, 3) || !in_bounds(dk[1], n, 3) || !in_bounds(dk[2], n, 3) ||
+      !in_bounds(dk[3], n, 3)) {
+    c.f[5] = c.f[6] = c.f[7] = c.f[8] = R(0);
+    return;
+  }
+#endif
   c.f[5] = ldp<CG>(d - W - 1);
   c.f[6] = ldp<CG>(d + P - W + 1);
   c.f[7] = ldp<CG>(d + 2 * P + W + 1);
@@ -560,6 +629,13 @@ __device__ __forceinline__ void load_own(const Pops<S, CG> &src, int x, int y, C
   const long long c0 = (long long)y * src.nxp + x, P = src.plane;
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
+#ifdef PEMLBM_BOUNDS_CHECK
+    const long long k = pop_index(i, c0, P), n = pop_extent(P, src.nxp);
+    if (!in_bounds(k, n, 4) || !in_bounds(k + 3, n, 4)) {
+      c.f[i] = c.g[0][i] = c.g[1][i] = c.g[2][i] = R(0);
+      continue;
+    }
+#endif
     const auto v = ldq<CG>(src.p + pop_index(i, c0, P));
     c.f[i] = v.v[0];
     c.g[0][i] = v.v[1];
@@ -567,7 +643,15 @@ __device__ __forceinline__ void load_own(const Pops<S, CG> &src, int x, int y, C
     c.g[2][i] = v.v[3];
   }
 #pragma unroll
-  for (int i = 5; i < 9; ++i) c.f[i] = ldp<CG>(src.p + pop_index(i, c0, P));
+  for (int i = 5; i < 9; ++i) {
+#ifdef PEMLBM_BOUNDS_CHECK
+    if (!in_bounds(pop_index(i, c0, P), pop_extent(P, src.nxp), 4)) {
+      c.f[i] = R(0);
+      continue;
+    }
+#endif
+    c.f[i] = ldp<CG>(src.p + pop_index(i, c0, P));
+  }
 }
 
 // Replaces the pulls of links that cross a wall, the inlet, the outlet, a

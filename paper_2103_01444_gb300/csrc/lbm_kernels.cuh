@@ -626,7 +626,19 @@ void launch_set_state(void *pop, const DevGeom &g, const KArgs &a, const double 
                                         in);
 }
 
+template <typename S> unsigned long long bounds_first_bad() {
+#ifdef PEMLBM_BOUNDS_CHECK
+  unsigned long long v = 0, zero = 0;
+  cudaMemcpyFromSymbol(&v, g_bounds_first_bad, sizeof v);
+  cudaMemcpyToSymbol(g_bounds_first_bad, &zero, sizeof zero);
+  return v;
+#else
+  return 0;
+#endif
+}
+
 #define PEMLBM_INSTANTIATE(S)                                                                   \
+  template unsigned long long bounds_first_bad<S>();                                           \
   template void launch_step<S>(const void *, void *, const DevGeom &, const KArgs &, int,       \
                                cudaStream_t);                                                   \
   template void launch_fields<S>(const void *, const DevGeom &, const KArgs &, double *,        \

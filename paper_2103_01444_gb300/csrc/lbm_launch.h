@@ -86,6 +86,11 @@ template <typename S> void launch_adj_finish(const DevGeom &g, const KArgs &a, c
 template <typename S> void launch_adj_fold(const DevGeom &g, const KArgs &a, const AdjPtrs &b, cudaStream_t st);
 template <typename S> void launch_adj_seed_current(const void *src, const DevGeom &g, const KArgs &a, int fickian, double weight, const AdjPtrs &b, cudaStream_t st);
 
+// The first out-of-range access that this storage type's kernels recorded
+// (the bounds-checked build; site << 48 | index, 0 for none, and always 0 in
+// the plain build), cleared when read.
+template <typename S> unsigned long long bounds_first_bad();
+
 // Advances the step counter that seeds stochastic 16-bit rounding.
 void launch_seed_advance(unsigned *ctr, cudaStream_t st);
 

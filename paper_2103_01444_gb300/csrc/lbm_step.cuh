@@ -56,16 +56,17 @@ __device__ __forceinline__ void cell_update(const S *__restrict__ src_p, S *__re
   using R = typename Real<S>::type;
   const long long c = (long long)y * a.nxp + x;
   const Pops<S, CG> src{src_p, a.plane, a.nxp};
-  const uint8_t m = mask[c];
+  const uint8_t m = ld_mask(mask, c, a, 20);
   Cell<R> cell;
   load_interior<S, R, CG>(src, a, x, y, cell);
   // solid cells run the same arithmetic on their (unused) values and only
   // skip the stores, so no branch stands between the mask and the loads
   const bool live = (m & REG_MASK) != REG_SOLID;
-  const MatCoef<R> mc = pal[mid[c]];
+  const MatCoef<R> mc = pal[ld_mid(mid, c, a, 21)];
   if (m & M_EDGE) {
     // next to grains but away from the lattice's edges: bounce-back only
-    if ((m & M_EDGE) == M_NEAR_SOLID) bounce_solid<S, R, CG>(src, x, y, mask[a.plane + c], cell);
+    if ((m & M_EDGE) == M_NEAR_SOLID)
+      bounce_solid<S, R, CG>(src, x, y, ld_mask(mask, a.plane + c, a, 23), cell);
     else fix_edges<S, R, CG, X>(src, a, mask, mid, pal, mc, x, y, m, cell);
   }
   if constexpr (REC)
@@ -100,13 +101,17 @@ __device__ __forceinline__ void cell_update(const S *__restrict__ src_p, S *__re
   }
   auto r16 = [&](int q) { return (q & 1) ? rnd[q >> 1] >> 16 : rnd[q >> 1] & 0xffffu; };
   const long long P = a.plane;
+  // (the bounds-checked build skips a store outside the 24 planes)
+  auto st_ok = [&](long long k, int width) { return in_bounds(k, 24 * P, 24) && in_bounds(k + width - 1, 24 * P, 24); };
   if (live) {   // the diagonal flow links
     if constexpr (SR) {
 #pragma unroll
-      for (int i = 5; i < 9; ++i) st_sr(dst + pop_index(i, c, P), o[i], r16(i));
+      for (int i = 5; i < 9; ++i)
+        if (st_ok(pop_index(i, c, P), 1)) st_sr(dst + pop_index(i, c, P), o[i], r16(i));
     } else {
 #pragma unroll
-      for (int i = 5; i < 9; ++i) st_r(dst + pop_index(i, c, P), o[i]);
+      for (int i = 5; i < 9; ++i)
+        if (st_ok(pop_index(i, c, P), 1)) st_r(dst + pop_index(i, c, P), o[i]);
     }
   }
   const R srcv[3] = {-S_vol * R(a.hpo) * mc.inv_sigma, S_vol, R(-2) * S_vol};
@@ -117,6 +122,7 @@ __device__ __forceinline__ void cell_update(const S *__restrict__ src_p, S *__re
   if (live) {   // links 0-4 of the flow and the three scalars, one group each
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
+      if (!st_ok(pop_index(i, c, P), 4)) continue;
       if constexpr (SR) {
         stq_sr(dst + pop_index(i, c, P), o[i], g[0][i], g[1][i], g[2][i], r16(i), r16(9 + i),
                r16(14 + i), r16(19 + i));

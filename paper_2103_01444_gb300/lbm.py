@@ -13,6 +13,9 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpemlbm.so")
+# PEMLBM_LIB selects another build of the same library (the bounds-checked
+# libpemlbm_checked.so of build.build(bounds_check=True)); it must exist.
+LIB_PATH = os.environ.get("PEMLBM_LIB", LIB_PATH)
 
 FP64, FP32, BF16, FP16 = 0, 1, 2, 3
 PRECISION = {"fp64": FP64, "fp32": FP32, "bf16": BF16, "fp16": FP16}
@@ -27,7 +30,8 @@ EXPORTS = ("lbm_create_domain", "lbm_destroy_domain", "lbm_set_params", "lbm_set
            "lbm_set_variant", "lbm_residual_noalloc", "lbm_balances", "lbm_step_observe",
            "lbm_create_batch", "lbm_destroy_batch",
            "lbm_batch_set_schedule", "lbm_batch_tune", "lbm_batch_step", "lbm_batch_time_steps",
-           "lbm_grad", "lbm_set_grad_memory", "lbm_vjp", "lbm_halo_exchange", "lbm_halo_pack", "lbm_halo_unpack",
+           "lbm_grad", "lbm_set_grad_memory", "lbm_bounds_check", "lbm_vjp",
+           "lbm_halo_exchange", "lbm_halo_pack", "lbm_halo_unpack",
            "lbm_last_error")
 
 
@@ -96,6 +100,7 @@ def load_library(path: str = LIB_PATH):
         "lbm_tune": [P, C.c_int32, C.POINTER(C.c_int32), d],
         "lbm_set_variant": [P, C.c_int32],
         "lbm_set_grad_memory": [P, C.c_int64],
+        "lbm_bounds_check": [C.POINTER(C.c_uint64)],
         "lbm_residual_noalloc": [P, C.c_void_p, d],
         "lbm_create_batch": [C.POINTER(P), C.c_int32, C.POINTER(P)],
         "lbm_destroy_batch": [P],
@@ -494,3 +499,13 @@ def cathode_objective():
             return gJ * gphi, gJ * gK, gJ * gD, gJ * gU, None, None, None, None, None, None
 
     return CathodeObjective
+
+
+def bounds_check() -> int:
+    """First out-of-range device access recorded since the last call by a
+    bounds-checked build (site << 48 | index; 0 for none); LbmError ESTATE
+    in the plain build."""
+    L = load_library()
+    v = C.c_uint64()
+    _check(L.lbm_bounds_check(C.byref(v)))
+    return v.value

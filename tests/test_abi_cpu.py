@@ -49,6 +49,17 @@ def test_grad_memory_limit_argument_checks(libpath):
     assert b"null" in L.lbm_last_error()
 
 
+def test_bounds_check_needs_the_checked_build(libpath):
+    """The plain library answers lbm_bounds_check with ESTATE (and a zero
+    record) without touching the device; a null argument is EINVAL."""
+    L = lbm.load_library(libpath)
+    v = ctypes.c_uint64(7)
+    estate = next(k for k, s in lbm.STATUS.items() if s == "LBM_ESTATE")
+    einval = next(k for k, s in lbm.STATUS.items() if s == "LBM_EINVAL")
+    assert L.lbm_bounds_check(ctypes.byref(v)) == estate and v.value == 0
+    assert L.lbm_bounds_check(None) == einval
+
+
 def test_param_structs_match_header(tmp_path):
     """The ctypes mirrors have the header's field names, offsets and sizes
     (a C program compiled against the header prints them)."""
