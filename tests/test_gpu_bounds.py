@@ -89,10 +89,10 @@ for prec in ("fp64", "fp32", "bf16"):
     check(f"x-slabs {prec}")
 doms = [Domain.from_case(c, precision="fp32") for c in (cases["film"], cases["vol"], cases["grains"])]
 b = Batch(doms)
+b.tune(2)                                        # (between the reset and the first step)
 for sched in ("graph", "persistent", "per-case", "concurrent"):
     b.set_schedule(sched)
     b.step(10)
-b.tune(2)
 b.close()
 for d in doms:
     d.close()
