@@ -1477,13 +1477,13 @@ lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t se
   };
   const KArgs a = make_args(d);
   const DevGeom g = geom(d);
-  auto fwd = [&](const void *src, void *dst, cudaStream_t st) {
-    dispatch(d->desc.precision, [&](auto *tag) {
-      using S = std::remove_pointer_t<decltype(tag)>;
-      launch_step<S>(src, dst, g, a, d->variant, st);
-    });
-  };
   // ---- forward sweep s^0 .. s^{nrec}
+  // Every forward step, stored or not, runs the record kernel (the records
+  // of a segment that is not stored go to a record buffer the recompute
+  // overwrites later): the recompute then repeats exactly the steps of the
+  // sweep, so the gradient does not depend on how many segments are
+  // stored.  (A separately compiled kernel, like the plain step, need not
+  // round every value the same way.)
   std::optional<NvtxRange> nvtx_fwd;
   nvtx_fwd.emplace("pemlbm.grad.forward");
   CK(cudaMemcpyAsync(fs[0].p, d->pop[d->cur], sbytes, cudaMemcpyDeviceToDevice, d->stream));
@@ -1493,8 +1493,8 @@ lbm_status lbm_grad(lbm_domain *d, int32_t objective, int64_t nsteps, int32_t se
       CK(cudaMemcpyAsync((char *)ck.p + (size_t)k * sbytes, fs[fc].p, sbytes,
                          cudaMemcpyDeviceToDevice, d->stream));
     for (int64_t n = first_of(k) + 1; n <= last_of(k); ++n) {
-      if (k >= k0) step_with_records(d, fs[fc].p, fs[fc ^ 1].p, stored_recs(k, n), d->stream);
-      else fwd(fs[fc].p, fs[fc ^ 1].p, d->stream);
+      step_with_records(d, fs[fc].p, fs[fc ^ 1].p,
+                        k >= k0 ? stored_recs(k, n) : buffer_recs(0, k, n), d->stream);
       fc ^= 1;
     }
   }

@@ -185,7 +185,7 @@ void launch_step_v(const void *src, void *dst, const DevGeom &g, const KArgs &a,
       (const S *)src, (S *)dst, g.mask, g.mid, (const MatCoef<R> *)g.pal, narrow_args<R>(a));
 }
 
-constexpr StepShape kRecShape = {64, 2, 8};
+constexpr StepShape kRecShape = {64, 2, 6};
 template <typename S>
 void launch_step_rec(const void *src, void *dst, const DevGeom &g, const KArgs &a,
                      const RecBufs &r, cudaStream_t st) {
