@@ -364,7 +364,8 @@ lbm_status lbm_set_grad_memory(lbm_domain *d, int64_t bytes);
  * (paper_2103_01444_gb300.build.build(bounds_check=True), which compiles
  * with -DPEMLBM_BOUNDS_CHECK into libpemlbm_checked.so) tests the index of
  * every population, mask, material-index and palette access of the step
- * kernels, and the lambda and record accesses of the adjoint kernels,
+ * kernels, and the lambda, own-use, gradient and record accesses of the
+ * adjoint kernels (directly, or through the cell index that bounds them),
  * against the extent of its buffer; an access outside it is skipped (no
  * trap) and the first one recorded.  This call waits for the device, writes
  * the first recorded access since the previous call to *first_bad (site <<

@@ -592,6 +592,11 @@ k_adj_edge(RecPtrs<R> rp, const uint8_t *__restrict__ mask, const uint16_t *__re
   if (t >= ncells) return;   // whole warps leave
   Shared &sh = sh_all[w];
   const long long c = cells[t], P = a.plane, W = a.nxp;
+#ifdef PEMLBM_BOUNDS_CHECK
+  // every lambda, own-use, gradient and virtual-column access of the cell is
+  // c + q P (q < 24), c itself or indexed by its row: bounded by c < P
+  if (!in_bounds(c, P, 35)) return;   // (the whole warp: one cell)
+#endif
   const int y = (int)(c / a.nxp), x = (int)(c - (long long)y * a.nxp);
   const uint8_t m = mask[c];
   const MatCoef<R> mc = pal[mid[c]];
@@ -771,6 +776,9 @@ k_adj_fix(const uint8_t *__restrict__ mask, const uint16_t *__restrict__ mid,
   if (t >= 24LL * ncells) return;
   const int q = (int)(t / ncells);
   const long long c = cells[t - (long long)q * ncells], P = a.plane;
+#ifdef PEMLBM_BOUNDS_CHECK
+  if (!in_bounds(c, P, 36)) return;
+#endif
   const int y = (int)(c / a.nxp), x = (int)(c - (long long)y * a.nxp);
   const bool vcol = has_vcol(a, x);
   const int vs = vcol_side(a, x);
