@@ -60,6 +60,16 @@ def test_bounds_check_needs_the_checked_build(libpath):
     assert L.lbm_bounds_check(None) == einval
 
 
+def test_checked_build_compiles_and_exports_the_same_symbols():
+    """The self-checking build (-DPEMLBM_BOUNDS_CHECK) compiles here, with no
+    GPU, and exports every symbol of the header, like the plain build."""
+    from paper_2103_01444_gb300.build import build
+    path = build(bounds_check=True)
+    L = ctypes.CDLL(path)
+    for s in declared_symbols():
+        assert hasattr(L, s), s
+
+
 def test_param_structs_match_header(tmp_path):
     """The ctypes mirrors have the header's field names, offsets and sizes
     (a C program compiled against the header prints them)."""
